@@ -1,0 +1,247 @@
+"""CPU oracle for the model-based ultrasound render (SonoGym, App. B.2).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, the smoke check and the
+CPU-baseline leg of ``bench.py``; never by the product path.
+
+* ``ussim_oracle.c`` (O1): FP64 C renderer, one frame at a time, OpenMP over
+  frames for the CPU baseline.  Loaded here through ctypes; compiled on
+  first use (or by ``build()``) with ``-ffp-contract=off``.
+* ``brute.py`` (O2): pure-Python restatement on tiny inputs (direct sums,
+  full 2-D PSF, its own Philox and Box-Muller).
+* ``surrogate_ref.py`` (O3): FP64 numpy convolution / loss / optimiser
+  references for the learned surrogate.
+
+Nothing here shares code with the CUDA path.  The synthetic inputs come
+from ``paper_2507_01152_gb300.scene``, which holds none of the method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ussim_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libussim_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (FP32 index path must not be contracted)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class OrVolume(C.Structure):
+    _fields_ = [("labels", C.c_void_p), ("hu", C.c_void_p), ("nx", C.c_int32),
+                ("ny", C.c_int32), ("nz", C.c_int32), ("voxel_mm", C.c_float)]
+
+
+class OrTissue(C.Structure):
+    _fields_ = [("alpha_db_cm_mhz", C.c_float), ("z_mrayl", C.c_float), ("mu0", C.c_float),
+                ("sigma0", C.c_float), ("mu1", C.c_float)]
+
+
+class OrProbe(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_lines", C.c_int32), ("n_samples", C.c_int32),
+                ("depth_mm", C.c_float), ("pitch_mm", C.c_float), ("fan_deg", C.c_float),
+                ("radius_mm", C.c_float), ("out_w", C.c_int32), ("out_h", C.c_int32),
+                ("f_mhz", C.c_float), ("e0", C.c_float), ("psf_sigma_ax_mm", C.c_float),
+                ("psf_sigma_lat_mm", C.c_float), ("dyn_range_db", C.c_float)]
+
+
+class OrOptions(C.Structure):
+    _fields_ = [("refl_power", C.c_int32), ("transmission", C.c_int32),
+                ("z_mode", C.c_int32), ("speckle", C.c_int32)]
+
+
+class OrFrameOut(C.Structure):
+    _fields_ = [("frame", C.c_void_p), ("envelope", C.c_void_p), ("logimg", C.c_void_p),
+                ("S", C.c_void_p), ("E", C.c_void_p), ("cos_theta", C.c_void_p),
+                ("hu", C.c_void_p), ("nn_index", C.c_void_p), ("label", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.oracle_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            L.oracle_speckle_words.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+                                               C.c_uint32, C.c_void_p]
+            L.oracle_n0.argtypes = [C.c_void_p, C.c_uint32]
+            L.oracle_n0.restype = C.c_double
+            L.oracle_n1_threshold.argtypes = [C.c_double]
+            L.oracle_n1_threshold.restype = C.c_uint64
+            L.oracle_psf_taps.argtypes = [C.c_double, C.c_double, C.c_void_p, C.c_int]
+            L.oracle_psf_taps.restype = C.c_int
+            L.oracle_scan_convert.argtypes = [C.POINTER(OrProbe), C.c_void_p, C.c_void_p]
+            L.oracle_render_frame.argtypes = [C.POINTER(OrVolume), C.POINTER(OrTissue), C.c_int,
+                                              C.POINTER(OrProbe), C.POINTER(OrOptions), C.c_void_p,
+                                              C.c_uint32, C.c_uint64, C.c_uint64,
+                                              C.POINTER(OrFrameOut)]
+            L.oracle_render_frame.restype = C.c_int
+            L.oracle_render_batch.argtypes = [C.POINTER(OrVolume), C.c_int, C.POINTER(OrTissue),
+                                              C.c_int, C.POINTER(OrProbe), C.c_int,
+                                              C.POINTER(OrOptions), C.c_void_p, C.c_int, C.c_void_p,
+                                              C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p,
+                                              C.c_int]
+            L.oracle_render_batch.restype = C.c_int
+            L.oracle_touched_voxels.argtypes = [C.POINTER(OrVolume), C.c_int, C.POINTER(OrProbe),
+                                                C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+            L.oracle_touched_voxels.restype = C.c_int64
+            L.oracle_sample_coords.argtypes = [C.POINTER(OrProbe), C.c_void_p, C.c_float, C.c_int,
+                                               C.c_int, C.c_void_p]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- marshalling
+
+def or_probe(p) -> OrProbe:
+    return OrProbe(p.kind, p.n_lines, p.n_samples, p.depth_mm, p.pitch_mm, p.fan_deg,
+                   p.radius_mm, p.out_w, p.out_h, p.f_mhz, p.e0, p.psf_sigma_ax_mm,
+                   p.psf_sigma_lat_mm, p.dyn_range_db)
+
+
+def or_table(table):
+    arr = (OrTissue * len(table))()
+    for i, t in enumerate(table):
+        arr[i] = OrTissue(t.alpha_db_cm_mhz, t.z_mrayl, t.mu0, t.sigma0, t.mu1)
+    return arr
+
+
+def or_options(o) -> OrOptions:
+    return OrOptions(o.refl_power, o.transmission, o.z_mode, o.speckle)
+
+
+class _Vol:
+    """Keeps the numpy arrays alive next to the ctypes descriptor."""
+
+    def __init__(self, labels, hu, voxel_mm):
+        self.labels = np.ascontiguousarray(labels, np.uint8)
+        self.hu = np.ascontiguousarray(hu, np.int16)
+        nz, ny, nx = self.labels.shape
+        self.desc = OrVolume(self.labels.ctypes.data, self.hu.ctypes.data, nx, ny, nz, voxel_mm)
+
+
+# --------------------------------------------------------------------- API
+
+def philox4x32_10(ctr, key):
+    c = np.asarray(ctr, np.uint32)
+    k = np.asarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def speckle_words(seed, step, env, line, sample):
+    out = np.zeros(4, np.uint32)
+    lib().oracle_speckle_words(seed, step, env, line, sample, _ptr(out))
+    return out
+
+
+def n0(words, sample):
+    w = np.asarray(words, np.uint32)
+    return lib().oracle_n0(_ptr(w), sample)
+
+
+def n1_threshold(mu1):
+    return int(lib().oracle_n1_threshold(float(mu1)))
+
+
+def psf_taps(sigma_mm, spacing_mm, max_taps=4096):
+    t = np.zeros(max_taps)
+    K = lib().oracle_psf_taps(sigma_mm, spacing_mm, _ptr(t), max_taps)
+    if K < 0:
+        raise ValueError("too many taps")
+    return t[:2 * K + 1].copy()
+
+
+def sample_coords(probe, pose, voxel_mm, line, sample):
+    u = np.zeros(3, np.float32)
+    pr = or_probe(probe)
+    M = np.ascontiguousarray(pose, np.float32).reshape(12)
+    lib().oracle_sample_coords(C.byref(pr), _ptr(M), voxel_mm, line, sample, _ptr(u))
+    return u
+
+
+def scan_convert(probe, logimg):
+    pr = or_probe(probe)
+    y = np.ascontiguousarray(logimg, np.float64)
+    out = np.zeros((probe.out_h, probe.out_w), np.float64)
+    lib().oracle_scan_convert(C.byref(pr), _ptr(y), _ptr(out))
+    return out
+
+
+def render_frame(labels, hu, voxel_mm, table, probe, options, pose, env=0, seed=0, step=0):
+    """Render one frame; returns a dict of every export (numpy arrays)."""
+    vol = _Vol(labels, hu, voxel_mm)
+    NL, NS = probe.n_lines, probe.n_samples
+    res = {
+        "frame": np.zeros((probe.out_h, probe.out_w)),
+        "envelope": np.zeros((NL, NS)), "logimg": np.zeros((NL, NS)), "S": np.zeros((NL, NS)),
+        "E": np.zeros((NL, NS)), "cos_theta": np.zeros((NL, NS)), "hu": np.zeros((NL, NS)),
+        "nn_index": np.zeros((NL, NS), np.int32), "label": np.zeros((NL, NS), np.uint8),
+    }
+    o = OrFrameOut(*[res[k].ctypes.data for k in
+                     ("frame", "envelope", "logimg", "S", "E", "cos_theta", "hu", "nn_index", "label")])
+    tab = or_table(table)
+    pr = or_probe(probe)
+    op = or_options(options)
+    M = np.ascontiguousarray(pose, np.float32).reshape(12)
+    rc = lib().oracle_render_frame(C.byref(vol.desc), tab, len(table), C.byref(pr), C.byref(op),
+                                   _ptr(M), env, seed, step, C.byref(o))
+    if rc != 0:
+        raise ValueError(f"oracle_render_frame failed: {rc}")
+    return res
+
+
+def render_batch(volumes, table, probes, options, envs, poses, seed, step, n_threads=1):
+    """Render a batch.  volumes: list of (labels, hu, voxel_mm); envs int32
+    [B][2]; poses float32 [B][3][4].  Returns (frames float64 flat, offsets)."""
+    vols = [_Vol(l, h, v) for (l, h, v) in volumes]
+    vd = (OrVolume * len(vols))(*[v.desc for v in vols])
+    pd = (OrProbe * len(probes))(*[or_probe(p) for p in probes])
+    envs = np.ascontiguousarray(envs, np.int32)
+    B = envs.shape[0]
+    sizes = np.array([probes[e[1]].out_h * probes[e[1]].out_w for e in envs], np.int64)
+    offsets = np.zeros(B + 1, np.int64)
+    offsets[1:] = np.cumsum(sizes)
+    frames = np.zeros(int(offsets[-1]), np.float64)
+    P = np.ascontiguousarray(poses, np.float32).reshape(B, 12)
+    op = or_options(options)
+    rc = lib().oracle_render_batch(vd, len(vols), or_table(table), len(table), pd, len(probes),
+                                   C.byref(op), _ptr(envs), B, _ptr(P), seed, step,
+                                   _ptr(frames), _ptr(offsets), n_threads)
+    if rc != 0:
+        raise ValueError(f"oracle_render_batch failed: {rc}")
+    return frames, offsets
+
+
+def touched_voxels(volumes, probes, envs, poses):
+    """(union count over the batch, per-frame counts) of voxels read."""
+    vols = [_Vol(l, h, v) for (l, h, v) in volumes]
+    vd = (OrVolume * len(vols))(*[v.desc for v in vols])
+    pd = (OrProbe * len(probes))(*[or_probe(p) for p in probes])
+    envs = np.ascontiguousarray(envs, np.int32)
+    B = envs.shape[0]
+    per = np.zeros(B, np.int64)
+    P = np.ascontiguousarray(poses, np.float32).reshape(B, 12)
+    tot = lib().oracle_touched_voxels(vd, len(vols), pd, _ptr(envs), B, _ptr(P), _ptr(per))
+    return int(tot), per
