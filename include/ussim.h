@@ -1,0 +1,211 @@
+/*
+ * ussim.h — C ABI of the batched model-based ultrasound render.
+ *
+ * One call renders one ultrasound frame per environment for a batch of
+ * environments, each with its own probe pose, volume and probe type.  The
+ * simulation is the convolution-based image model of SonoGym App. B.2
+ * (after Salehi et al. 2015), applied to the 2-D label and CT slices that
+ * the probe's image plane cuts out of each environment's volumes
+ * (Fig. 2 caption; Sec. 4 "Ultrasound simulation"):
+ *
+ *   E(u) = E0 exp(-f * int_0^y alpha)            remaining energy   (App. B.2)
+ *   R(u) = |E cos(theta) (Z(y+dy)-Z(y))/(Z(y+dy)+Z(y))| at boundaries G
+ *   B(u) = E T,  T = N0 sigma0 + mu0 if N1 <= mu1 else 0   (App. B.2)
+ *   I    = P (x) (R + B),  P a 2-D Gaussian PSF             (App. B.2)
+ *
+ * followed by log compression and, for curvilinear probes, scan conversion
+ * to a Cartesian image.  Readings taken where the paper is silent (noise
+ * keying, impedance from HU, incidence-angle stencil, transmission loss,
+ * log and scan-conversion conventions) are stated beside each switch.
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented as DEVICE point to memory of the current CUDA
+ *    device; HOST pointers to ordinary (preferably pinned) host memory.
+ *  - Volumes, poses and frames are caller-owned and borrowed: they must stay
+ *    valid until the work that uses them has finished on `stream`.  The
+ *    library owns only its derived tables, plans and workspace.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that take a stream are asynchronous with respect to
+ *    the host unless stated otherwise.
+ *  - Argument errors are detected on the host before any launch and return
+ *    US_ERR_INVALID_ARG with a message in us_sim_last_error().  Errors found
+ *    on the device (non-finite pose entries) set a sticky error word that
+ *    us_sim_check() reads.  No entry point aborts or traps.
+ *  - One handle may be used from one host thread at a time.
+ *  - Output is a pure function of (inputs, seed, step): two calls with the
+ *    same arguments produce bit-identical frames.
+ */
+#ifndef USSIM_H
+#define USSIM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define US_API __attribute__((visibility("default")))
+#else
+#define US_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  US_OK = 0,
+  US_ERR_INVALID_ARG = 1, /* bad argument; nothing was launched */
+  US_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  US_ERR_OOM = 3,         /* device or host allocation failed */
+  US_ERR_TIMEOUT = 4,     /* a bounded device wait ran out */
+  US_ERR_UNSUPPORTED = 5, /* valid request this build does not handle */
+  US_ERR_INTERNAL = 6     /* device-side consistency check failed */
+} us_status;
+
+typedef struct us_sim us_sim; /* opaque */
+
+/* A label map and its CT volume on the same grid (Sec. 4 "Assets": CT
+ * volumes with label maps).  DEVICE pointers, layout [nz][ny][nx] with x
+ * fastest; voxel (i, j, k) is centred at (i, j, k) * voxel_mm in the
+ * volume frame (mm).  Borrowed for the life of the handle.  Samples
+ * outside the grid read label 0 and HU 0 (water). */
+typedef struct {
+  const uint8_t* labels;
+  const int16_t* hu;
+  int32_t nx, ny, nz;
+  float voxel_mm;
+} us_volume;
+
+/* Acoustic settings of one tissue class; the table index is the label
+ * (App. B.2: attenuation alpha, impedance, scatter mu0 / sigma0 / mu1). */
+typedef struct {
+  float alpha_db_cm_mhz; /* attenuation, dB/(cm MHz) */
+  float z_mrayl;         /* impedance, MRayl (used when z_mode = 1) */
+  float mu0, sigma0;     /* scatter mean / std: T~ = N0 sigma0 + mu0 */
+  float mu1;             /* density threshold: scatter where N1 <= mu1; -inf = never */
+} us_tissue;
+
+/* Probe geometry and imaging settings.
+ * kind 0 (linear): line l at lateral offset (l - (NL-1)/2) * pitch_mm,
+ *   sample s at depth s * depth_mm / NS; output image NS rows x NL columns
+ *   (out_h = n_samples, out_w = n_lines required).
+ * kind 1 (curvilinear): apex radius_mm behind the face, line l at angle
+ *   (l - (NL-1)/2) * fan/(NL-1), sample s at radius radius_mm + s*depth/NS;
+ *   scan-converted to out_h x out_w over the fan's bounding box.
+ * PSF: separable Gaussian on the beam grid, sigma in mm, half-width
+ * ceil(3 sigma / spacing) taps (at most 48), lateral spacing = pitch (linear)
+ * or mid-depth arc length (curvilinear).  Log compression: pixel =
+ * clamp((20 log10(I / e0) + dyn_range_db) / dyn_range_db, 0, 1). */
+typedef struct {
+  int32_t kind;
+  int32_t n_lines, n_samples; /* 2 <= NL <= 1024, 2 <= NS <= 1024 */
+  float depth_mm;
+  float pitch_mm;             /* linear */
+  float fan_deg, radius_mm;   /* curvilinear */
+  int32_t out_w, out_h;
+  float f_mhz, e0, psf_sigma_ax_mm, psf_sigma_lat_mm, dyn_range_db;
+} us_probe;
+
+/* Model switches.
+ * refl_power 1: R = G E |cos(theta) r| (App. B.2); 2: G E (cos(theta) r)^2,
+ *   the intensity reflection coefficient.
+ * transmission 1: the energy also loses ln(1 - r^2) at each boundary;
+ *   0: attenuation only (App. B.2 as printed).
+ * z_mode 0: Z = max(HU + 1024, 1), "proportional to CT intensity" (App. B.2);
+ *   1: Z from the tissue table.
+ * speckle 1: N0, N1 from Philox-4x32-10 keyed by (env, line, sample, seed,
+ *   step); 0: T = mu0 everywhere. */
+typedef struct {
+  int32_t refl_power, transmission, z_mode, speckle;
+} us_options;
+
+/* One environment of a batch: which volume and which probe it uses. */
+typedef struct {
+  int32_t volume_id, probe_id;
+} us_env;
+
+/* Launch shape of the fused batched render. */
+typedef struct {
+  int32_t cluster_size;  /* CTAs per environment frame: 2, 4, 8 or 16 */
+  int32_t warps_per_cta; /* 4, 8, 16 or 32 */
+  int32_t ctas_per_sm;   /* residency target used to size the persistent grid (1..4) */
+  int32_t use_graph;     /* 1: replay a captured CUDA graph per (envs, B) */
+} us_tuning;
+
+/* Create a simulator.  Copies the descriptors, builds the derived tables
+ * (per-line geometry, PSF taps, scan-conversion maps, tissue constants,
+ * N1 thresholds) and checks on the device that every label is below
+ * n_labels (synchronous).  vols/labels/hu stay borrowed.  opt may be NULL
+ * (defaults: refl_power 1, transmission 1, z_mode 0, speckle 1).
+ * Errors: US_ERR_INVALID_ARG (bad sizes, NULL pointers, label out of
+ * range), US_ERR_OOM, US_ERR_CUDA.  *out is NULL on error. */
+US_API us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* table,
+                        int32_t n_labels, const us_probe* probes, int32_t n_probes,
+                        const us_options* opt, us_sim** out);
+
+/* Release every resource of the handle (waits for its work to finish). */
+US_API void us_sim_destroy(us_sim* sim);
+
+/* Frame layout for a batch: offsets[b] is the first float of frame b in
+ * the frame buffer (row-major out_h x out_w), offsets[B] the total size in
+ * floats.  Each frame starts on a 256-byte boundary.  offsets: HOST, B+1. */
+US_API us_status us_sim_frame_layout(const us_sim* sim, const us_env* envs, int32_t B, int64_t* offsets);
+
+/* Beam-grid layout for the debug exports: offsets[b] = first element of
+ * env b's [NL][NS] grid.  offsets: HOST, B+1. */
+US_API us_status us_sim_beam_layout(const us_sim* sim, const us_env* envs, int32_t B, int64_t* offsets);
+
+/* Render one frame per environment with the fused, persistent, batched
+ * kernel (one thread-block cluster per frame, work taken from a counter).
+ * envs: HOST [B]; poses: DEVICE float [B][3][4], probe frame (x lateral,
+ * y elevation, z along the beam, mm) -> volume frame (mm); frames: DEVICE,
+ * laid out by us_sim_frame_layout, 16-byte aligned.  B = 0 is a no-op. */
+US_API us_status us_sim_render(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                        uint64_t seed, uint64_t step, float* frames, void* stream);
+
+/* Same result through the plain per-environment form: for each environment
+ * in turn, separate kernels for slicing, the scanline model, the two PSF
+ * passes and scan conversion (the comparison baseline). */
+US_API us_status us_sim_render_plain(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                              uint64_t seed, uint64_t step, float* frames, void* stream);
+
+/* Render with intermediate exports for testing.  path 0 = fused, 1 = plain.
+ * envelope (float), logimg (float), nn_index (int32, -1 outside the
+ * volume), label (uint8): DEVICE, laid out by us_sim_beam_layout, [NL][NS]
+ * per env; any may be NULL.  envelope is I before log compression. */
+US_API us_status us_sim_render_debug(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                              uint64_t seed, uint64_t step, float* frames, float* envelope,
+                              float* logimg, int32_t* nn_index, uint8_t* label, int32_t path,
+                              void* stream);
+
+/* Render from HOST poses into HOST frames: copies the poses in and the
+ * frames out through library-owned device buffers (grown on demand).
+ * Returns after the frames are in host memory (synchronous). */
+US_API us_status us_sim_render_host(us_sim* sim, const us_env* envs, int32_t B, const float* poses_host,
+                             uint64_t seed, uint64_t step, float* frames_host, void* stream);
+
+/* Wait for `stream` and read the sticky device error word: US_OK, or
+ * US_ERR_INVALID_ARG if a pose had a non-finite entry (that frame renders
+ * as water).  Clears the word. */
+US_API us_status us_sim_check(us_sim* sim, void* stream);
+
+US_API us_status us_sim_get_tuning(const us_sim* sim, us_tuning* t);
+/* Set the fused kernel's launch shape; invalid shapes are rejected. */
+US_API us_status us_sim_set_tuning(us_sim* sim, const us_tuning* t);
+
+/* Time the fused render over the candidate launch shapes on this batch
+ * (synchronous, renders into `frames`), keep the fastest, and append it to
+ * the text cache at cache_path (may be NULL: no cache).  If cache_path
+ * already holds an entry for this GPU, probe set and batch signature it is
+ * used without timing. */
+US_API us_status us_sim_autotune(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                          float* frames, const char* cache_path, void* stream);
+
+/* Message of the last error on this handle ("" if none). */
+US_API const char* us_sim_last_error(const us_sim* sim);
+/* Name of a status code. */
+US_API const char* us_status_string(us_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* USSIM_H */

@@ -1,0 +1,203 @@
+// Device-side data structures and per-sample helpers of the ultrasound
+// render (SonoGym App. B.2 image model on the probe's scanline grid).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ussim {
+
+constexpr int kMaxHalfTaps = 48;   // PSF half-width limit (taps <= 97)
+constexpr int kThetaDMax = 8;      // lateral reach of the incidence stencil, lines
+
+// error-word bits
+constexpr unsigned kErrNonFinitePose = 1u;
+constexpr unsigned kErrBadItem = 2u;
+
+struct DevVolume {
+  const uint8_t* labels;
+  const int16_t* hu;
+  int nx, ny, nz;
+  float inv_h;
+};
+
+// per (probe, label): attenuation per sample f*alpha*dr (Np), scatter
+// statistics, table impedance, and the N1 threshold floor(Phi(mu1) 2^32)
+struct DevTissue {
+  float att, mu0, sigma0, z;
+  unsigned long long t1;
+};
+
+struct DevProbe {
+  int kind, nl, ns, out_w, out_h;
+  int k_ax, k_lat;
+  float dr, r0, e0, log_gain, dtheta, pitch;
+  const float2* lines;       // [nl]: linear (x_l, 0), curvilinear (sin, cos)
+  const float* w_ax;         // [2 k_ax + 1]
+  const float* w_lat;        // [2 k_lat + 1]
+  const float2* lut;         // curvilinear: [out_h * out_w] (fl, fs); fl < 0 outside
+  const DevTissue* tissue;   // [n_labels]
+};
+
+// incidence stencil extents for a (volume, probe) pair: axial half window W
+// and per-sample lateral reach D[s]
+struct DevPair {
+  int W;
+  const uint8_t* D;
+};
+
+// one environment of a batch, in processing order
+struct EnvItem {
+  int b;            // index in the caller's batch (noise counter, pose)
+  int vol, probe;
+  int pair;         // vol * n_probes + probe
+  long long frame_off, beam_off;
+};
+
+struct RenderParams {
+  const DevVolume* vols;
+  const DevProbe* probes;
+  const DevPair* pairs;
+  const EnvItem* items;
+  int n_items;
+  const float* poses;        // [B][12]
+  uint2 key;                 // Philox key for this (seed, step)
+  int refl_power, transmission, z_mode, speckle;
+  float* frames;
+  float* envelope;           // debug exports, may be null
+  float* logimg;
+  int* nn_index;
+  uint8_t* label;
+  unsigned* err;
+  unsigned* work;            // work counter (fused path)
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of two
+// 32x32->64 multiplies on counter words 0 and 2, high halves mixed with the
+// other words and the round key, key bumped by two Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// uniform in (0,1): odd multiple of 2^-24 from the top 23 bits (exact)
+__device__ __forceinline__ float u01(unsigned w) {
+  return __int2float_rn((int)((w >> 9) * 2u + 1u)) * 5.9604644775390625e-08f;
+}
+
+// ---------------------------------------------------------- index path
+// The voxel coordinate of a beam sample is defined in FP32 with a fixed,
+// contraction-free order; __fmul_rn / __fadd_rn keep the compiler from
+// fusing it into FMAs so that nearest-voxel decisions are reproducible.
+__device__ __forceinline__ void beam_point(const DevProbe& P, float2 ln, int s, float& x, float& z) {
+  const float sf = (float)s;
+  if (P.kind == 0) {
+    x = ln.x;
+    z = __fmul_rn(sf, P.dr);
+  } else {
+    const float rho = __fadd_rn(P.r0, __fmul_rn(sf, P.dr));
+    x = __fmul_rn(rho, ln.x);
+    z = __fadd_rn(__fmul_rn(rho, ln.y), -P.r0);
+  }
+}
+
+struct Pose {
+  float m[12];
+};
+
+__device__ __forceinline__ float3 to_voxel(const Pose& M, float inv_h, float x, float z) {
+  float3 u;
+  u.x = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(M.m[0], x), __fmul_rn(M.m[2], z)), M.m[3]), inv_h);
+  u.y = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(M.m[4], x), __fmul_rn(M.m[6], z)), M.m[7]), inv_h);
+  u.z = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(M.m[8], x), __fmul_rn(M.m[10], z)), M.m[11]), inv_h);
+  return u;
+}
+
+// nearest voxel: floor(u + 1/2) per axis, -1 outside the grid (NaN -> outside)
+__device__ __forceinline__ int nearest_voxel(const DevVolume& V, float3 u) {
+  const float fx = floorf(__fadd_rn(u.x, 0.5f));
+  const float fy = floorf(__fadd_rn(u.y, 0.5f));
+  const float fz = floorf(__fadd_rn(u.z, 0.5f));
+  if (!(fx >= 0.f && fx < (float)V.nx && fy >= 0.f && fy < (float)V.ny && fz >= 0.f && fz < (float)V.nz))
+    return -1;
+  return ((int)fz * V.ny + (int)fy) * V.nx + (int)fx;
+}
+
+__device__ __forceinline__ float hu_at(const DevVolume& V, int i, int j, int k) {
+  return ((unsigned)i < (unsigned)V.nx && (unsigned)j < (unsigned)V.ny && (unsigned)k < (unsigned)V.nz)
+             ? (float)__ldg(&V.hu[(k * V.ny + j) * V.nx + i])
+             : 0.f;
+}
+
+// trilinear HU; corners outside the grid read 0 (water)
+__device__ __forceinline__ float trilinear_hu(const DevVolume& V, float3 u) {
+  const float fx = floorf(u.x), fy = floorf(u.y), fz = floorf(u.z);
+  if (!(fx >= -1.f && fx < (float)V.nx && fy >= -1.f && fy < (float)V.ny && fz >= -1.f && fz < (float)V.nz))
+    return 0.f;
+  const int i = (int)fx, j = (int)fy, k = (int)fz;
+  const float tx = u.x - fx, ty = u.y - fy, tz = u.z - fz;
+  const float c000 = hu_at(V, i, j, k), c100 = hu_at(V, i + 1, j, k);
+  const float c010 = hu_at(V, i, j + 1, k), c110 = hu_at(V, i + 1, j + 1, k);
+  const float c001 = hu_at(V, i, j, k + 1), c101 = hu_at(V, i + 1, j, k + 1);
+  const float c011 = hu_at(V, i, j + 1, k + 1), c111 = hu_at(V, i + 1, j + 1, k + 1);
+  const float a00 = fmaf(tx, c100 - c000, c000), a10 = fmaf(tx, c110 - c010, c010);
+  const float a01 = fmaf(tx, c101 - c001, c001), a11 = fmaf(tx, c111 - c011, c011);
+  const float b0 = fmaf(ty, a10 - a00, a00), b1 = fmaf(ty, a11 - a01, a01);
+  return fmaf(tz, b1 - b0, b0);
+}
+
+__device__ __forceinline__ float impedance(int z_mode, float hu, const DevTissue& t) {
+  return z_mode == 0 ? fmaxf(hu + 1024.f, 1.f) : t.z;
+}
+
+// Incidence cosine at a boundary between samples s and s+1 of line l, from
+// the label slice: M(l') counts the samples of the window s-W+1..s+W on
+// line l' that carry the label below the boundary; the shift of that count
+// between lines l-D and l+D gives the boundary's slope.  LabFn(line, s)
+// returns the nearest label of a beam sample.
+template <class LabFn>
+__device__ __forceinline__ float incidence_cos(LabFn lab, int l, int s, int NL, int NS, int W, int D,
+                                               float dr, float dlat) {
+  const unsigned below = lab(l, s + 1);
+  const int lp = min(l + D, NL - 1), lm = max(l - D, 0);
+  int dM = 0;
+  for (int q = s - W + 1; q <= s + W; ++q) {
+    const int qc = min(max(q, 0), NS - 1);
+    dM += (int)(lab(lp, qc) == below) - (int)(lab(lm, qc) == below);
+  }
+  if (lp <= lm) return 1.f;
+  const float t = fabsf((float)dM) * dr / ((float)(lp - lm) * dlat);
+  return rsqrtf(fmaf(t, t, 1.f));
+}
+
+__device__ __forceinline__ float lateral_spacing(const DevProbe& P, int s) {
+  return P.kind == 0 ? P.pitch : fmaf((float)s, P.dr, P.r0) * P.dtheta;
+}
+
+// log compression to [0, 1] over the probe's dynamic range
+__device__ __forceinline__ float log_compress(const DevProbe& P, float I) {
+  const float db = 20.f * log10f(fmaxf(I, 1e-30f) / P.e0);
+  return __saturatef(fmaf(db, P.log_gain, 1.f));
+}
+
+__device__ __forceinline__ Pose load_pose(const float* poses, int b, bool& finite) {
+  Pose M;
+  finite = true;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    M.m[i] = __ldg(&poses[b * 12 + i]);
+    finite = finite && isfinite(M.m[i]);
+  }
+  return M;
+}
+
+}  // namespace ussim

@@ -1,0 +1,574 @@
+// C ABI of the batched ultrasound render: validation, derived tables,
+// per-batch work plans and launches.  See include/ussim.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "us_internal.h"
+
+using namespace ussim;
+
+namespace {
+
+constexpr int kMaxAxialHalf = 32;   // in-place axial filter in the fused kernel
+constexpr int kMaxLines = 1024, kMaxSamples = 1024;
+
+us_status fail(us_sim* s, us_status st, const std::string& msg) {
+  if (s) s->last_error = msg;
+  return st;
+}
+
+us_status cuda_fail(us_sim* s, cudaError_t e, const char* where) {
+  if (s) s->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? US_ERR_OOM : US_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const T* src, size_t n) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Gaussian taps on a grid of spacing d: exp(-(k d)^2 / (2 sigma^2)),
+// |k| <= ceil(3 sigma / d), normalised in FP64, rounded to FP32.
+int gaussian_taps(double sigma, double d, std::vector<float>& out) {
+  const int K = sigma > 0 ? (int)std::ceil(3.0 * sigma / d) : 0;
+  std::vector<double> w(2 * K + 1);
+  double sum = 0;
+  for (int k = -K; k <= K; ++k) {
+    const double x = (double)k * d;
+    w[k + K] = K ? std::exp(-x * x / (2.0 * sigma * sigma)) : 1.0;
+    sum += w[k + K];
+  }
+  out.resize(2 * K + 1);
+  for (int i = 0; i < 2 * K + 1; ++i) out[i] = (float)(w[i] / sum);
+  return K;
+}
+
+// N1 density test threshold: P(N1 <= mu1) = Phi(mu1) as a 32-bit fraction
+unsigned long long n1_threshold(double mu1) {
+  if (std::isinf(mu1)) return mu1 > 0 ? 4294967296ull : 0ull;
+  const double phi = 0.5 * std::erfc(-mu1 / std::sqrt(2.0));
+  double t = std::floor(phi * 4294967296.0);
+  t = std::min(std::max(t, 0.0), 4294967296.0);
+  return (unsigned long long)t;
+}
+
+std::string validate_probe(const us_probe& p) {
+  if (p.kind != 0 && p.kind != 1) return "probe kind must be 0 (linear) or 1 (curvilinear)";
+  if (p.n_lines < 2 || p.n_lines > kMaxLines) return "n_lines must be in [2, 1024]";
+  if (p.n_samples < 2 || p.n_samples > kMaxSamples) return "n_samples must be in [2, 1024]";
+  if (!(p.depth_mm > 0) || !std::isfinite(p.depth_mm)) return "depth_mm must be positive";
+  if (!(p.f_mhz > 0) || !(p.e0 > 0) || !(p.dyn_range_db > 0)) return "f_mhz, e0, dyn_range_db must be positive";
+  if (!(p.psf_sigma_ax_mm >= 0) || !(p.psf_sigma_lat_mm >= 0)) return "PSF sigmas must be >= 0";
+  if (p.kind == 0) {
+    if (!(p.pitch_mm > 0)) return "linear probe needs pitch_mm > 0";
+    if (p.out_w != p.n_lines || p.out_h != p.n_samples) return "linear probe needs out_w = n_lines, out_h = n_samples";
+  } else {
+    if (!(p.fan_deg > 0 && p.fan_deg < 180)) return "fan_deg must be in (0, 180)";
+    if (!(p.radius_mm > 0)) return "radius_mm must be positive";
+    if (p.out_w < 1 || p.out_h < 1 || (long long)p.out_w * p.out_h > (1 << 24)) return "bad output size";
+  }
+  return "";
+}
+
+void derive(ProbeHost& ph) {
+  const us_probe& p = ph.desc;
+  ph.dr = (double)p.depth_mm / (double)p.n_samples;
+  ph.dtheta = p.kind == 1 ? (double)p.fan_deg * M_PI / 180.0 / (double)(p.n_lines - 1) : 0.0;
+  ph.dlat_mid = p.kind == 1 ? ((double)p.radius_mm + 0.5 * (double)p.depth_mm) * ph.dtheta : (double)p.pitch_mm;
+}
+
+us_status build_probe_tables(us_sim* s, ProbeHost& ph) {
+  const us_probe& p = ph.desc;
+  const int NL = p.n_lines, NS = p.n_samples;
+  // per-line geometry, FP64 rounded once to FP32
+  std::vector<float2> lines(NL);
+  for (int l = 0; l < NL; ++l) {
+    if (p.kind == 0) {
+      lines[l] = make_float2((float)(((double)l - 0.5 * (double)(NL - 1)) * (double)p.pitch_mm), 0.f);
+    } else {
+      const double th = ((double)l - 0.5 * (double)(NL - 1)) * ph.dtheta;
+      lines[l] = make_float2((float)std::sin(th), (float)std::cos(th));
+    }
+  }
+  std::vector<float> wax, wlat;
+  ph.k_ax = gaussian_taps(p.psf_sigma_ax_mm, ph.dr, wax);
+  ph.k_lat = gaussian_taps(p.psf_sigma_lat_mm, ph.dlat_mid, wlat);
+  if (ph.k_ax > kMaxAxialHalf) return fail(s, US_ERR_INVALID_ARG, "axial PSF wider than 32 samples each side");
+  if (ph.k_lat > kMaxHalfTaps) return fail(s, US_ERR_INVALID_ARG, "lateral PSF wider than 48 lines each side");
+  // tissue constants for this probe's frequency and sample spacing
+  std::vector<DevTissue> tis(s->table.size());
+  for (size_t i = 0; i < s->table.size(); ++i) {
+    const us_tissue& t = s->table[i];
+    const double alpha_np = (double)t.alpha_db_cm_mhz * std::log(10.0) / 20.0 / 10.0;  // Np/(mm MHz)
+    tis[i].att = (float)((double)p.f_mhz * alpha_np * ph.dr);
+    tis[i].mu0 = t.mu0;
+    tis[i].sigma0 = t.sigma0;
+    tis[i].z = t.z_mrayl;
+    tis[i].t1 = n1_threshold((double)t.mu1);
+  }
+  // scan-conversion map (curvilinear): fractional (line, sample) of each
+  // output pixel centre over the fan's bounding box, -1 outside the fan
+  std::vector<float2> lut;
+  if (p.kind == 1) {
+    const int W = p.out_w, H = p.out_h;
+    lut.resize((size_t)W * H);
+    const double r0 = p.radius_mm, D = p.depth_mm;
+    const double half = 0.5 * (double)p.fan_deg * M_PI / 180.0;
+    const double xmax = (r0 + D) * std::sin(half), xmin = -xmax;
+    const double zmin = r0 * std::cos(half), zmax = r0 + D;
+    for (int r = 0; r < H; ++r)
+      for (int c = 0; c < W; ++c) {
+        const double x = xmin + (c + 0.5) * (xmax - xmin) / W;
+        const double z = zmin + (r + 0.5) * (zmax - zmin) / H;
+        const double fl = std::atan2(x, z) / ph.dtheta + 0.5 * (NL - 1);
+        const double fs = (std::hypot(x, z) - r0) / ph.dr;
+        const bool in = fl >= 0 && fl <= NL - 1 && fs >= 0 && fs <= NS - 1;
+        lut[(size_t)r * W + c] = in ? make_float2((float)fl, (float)fs) : make_float2(-1.f, -1.f);
+      }
+  }
+  cudaError_t e;
+  if ((e = upload(&ph.d_lines, lines.data(), lines.size())) != cudaSuccess) return cuda_fail(s, e, "upload lines");
+  if ((e = upload(&ph.d_wax, wax.data(), wax.size())) != cudaSuccess) return cuda_fail(s, e, "upload taps");
+  if ((e = upload(&ph.d_wlat, wlat.data(), wlat.size())) != cudaSuccess) return cuda_fail(s, e, "upload taps");
+  if ((e = upload(&ph.d_tissue, tis.data(), tis.size())) != cudaSuccess) return cuda_fail(s, e, "upload tissue");
+  if (!lut.empty() && (e = upload(&ph.d_lut, lut.data(), lut.size())) != cudaSuccess) return cuda_fail(s, e, "upload lut");
+  return US_OK;
+}
+
+DevProbe device_probe(const ProbeHost& ph) {
+  DevProbe d{};
+  const us_probe& p = ph.desc;
+  d.kind = p.kind;
+  d.nl = p.n_lines;
+  d.ns = p.n_samples;
+  d.out_w = p.out_w;
+  d.out_h = p.out_h;
+  d.k_ax = ph.k_ax;
+  d.k_lat = ph.k_lat;
+  d.dr = (float)ph.dr;
+  d.r0 = p.radius_mm;
+  d.e0 = p.e0;
+  d.log_gain = (float)(1.0 / (double)p.dyn_range_db);
+  d.dtheta = (float)ph.dtheta;
+  d.pitch = p.pitch_mm;
+  d.lines = ph.d_lines;
+  d.w_ax = ph.d_wax;
+  d.w_lat = ph.d_wlat;
+  d.lut = ph.d_lut;
+  d.tissue = ph.d_tissue;
+  return d;
+}
+
+// incidence stencil extents: axial half window of two voxels, lateral reach
+// of one voxel (in lines, at each sample's depth), capped at kThetaDMax
+void pair_tables(const us_volume& v, const ProbeHost& ph, int& W, std::vector<uint8_t>& D) {
+  const us_probe& p = ph.desc;
+  W = (int)std::ceil(2.0 * (double)v.voxel_mm / ph.dr);
+  D.resize(p.n_samples);
+  for (int s = 0; s < p.n_samples; ++s) {
+    const double dlat = p.kind == 0 ? (double)p.pitch_mm : ((double)p.radius_mm + s * ph.dr) * ph.dtheta;
+    int d = dlat > 0 ? (int)std::ceil((double)v.voxel_mm / dlat) : 1;
+    D[s] = (uint8_t)std::min(std::max(d, 1), kThetaDMax);
+  }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+std::string plan_key(const us_env* envs, int B) {
+  return std::string(reinterpret_cast<const char*>(envs), (size_t)B * sizeof(us_env));
+}
+
+us_status get_plan(us_sim* s, const us_env* envs, int B, us_plan** out) {
+  std::string key = plan_key(envs, B);
+  auto it = s->plans.find(key);
+  if (it != s->plans.end()) {
+    *out = &it->second;
+    return US_OK;
+  }
+  us_plan pl;
+  long long fo = 0, bo = 0;
+  const int n_probes = (int)s->probes.size();
+  for (int b = 0; b < B; ++b) {
+    const us_env& e = envs[b];
+    if (e.volume_id < 0 || e.volume_id >= (int)s->vols.size() || e.probe_id < 0 || e.probe_id >= n_probes)
+      return fail(s, US_ERR_INVALID_ARG, "env " + std::to_string(b) + " has an out-of-range volume or probe id");
+    const us_probe& p = s->probes[e.probe_id].desc;
+    EnvItem item;
+    item.b = b;
+    item.vol = e.volume_id;
+    item.probe = e.probe_id;
+    item.pair = e.volume_id * n_probes + e.probe_id;
+    item.frame_off = fo;
+    item.beam_off = bo;
+    pl.items_batch.push_back(item);
+    fo += (((long long)p.out_w * p.out_h + 63) / 64) * 64;
+    bo += (long long)p.n_lines * p.n_samples;
+  }
+  pl.frame_floats = fo;
+  pl.beam_elems = bo;
+  pl.items_sorted = pl.items_batch;
+  auto cost = [&](const EnvItem& it) {
+    const us_probe& p = s->probes[it.probe].desc;
+    return (long long)p.n_lines * p.n_samples + (long long)p.out_w * p.out_h / 4;
+  };
+  std::stable_sort(pl.items_sorted.begin(), pl.items_sorted.end(),
+                   [&](const EnvItem& a, const EnvItem& b) { return cost(a) > cost(b); });
+  if (B > 0) {
+    cudaError_t e = upload(&pl.d_items, pl.items_sorted.data(), pl.items_sorted.size());
+    if (e != cudaSuccess) return cuda_fail(s, e, "upload work list");
+  }
+  auto ins = s->plans.emplace(std::move(key), std::move(pl));
+  *out = &ins.first->second;
+  return US_OK;
+}
+
+RenderParams base_params(const us_sim* s, const float* poses, uint64_t seed, uint64_t step, float* frames) {
+  RenderParams p{};
+  p.vols = s->d_vols;
+  p.probes = s->d_probes;
+  p.pairs = s->d_pairs;
+  p.poses = poses;
+  p.key = make_uint2((uint32_t)seed ^ (uint32_t)(step * 0x9E3779B9ull), (uint32_t)(seed >> 32));
+  p.refl_power = s->opt.refl_power;
+  p.transmission = s->opt.transmission;
+  p.z_mode = s->opt.z_mode;
+  p.speckle = s->opt.speckle;
+  p.frames = frames;
+  p.err = s->d_err;
+  p.work = s->d_work;
+  return p;
+}
+
+us_status check_render_args(us_sim* s, const us_env* envs, int B, const float* poses, float* frames) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (B < 0) return fail(s, US_ERR_INVALID_ARG, "B must be >= 0");
+  if (B > 0 && (!envs || !poses || !frames)) return fail(s, US_ERR_INVALID_ARG, "NULL envs, poses or frames");
+  if (B > 0 && !aligned16(frames)) return fail(s, US_ERR_INVALID_ARG, "frames must be 16-byte aligned");
+  if (B > 0 && (reinterpret_cast<uintptr_t>(poses) & 3u)) return fail(s, US_ERR_INVALID_ARG, "poses must be 4-byte aligned");
+  return US_OK;
+}
+
+us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, uint64_t seed, uint64_t step,
+                    float* frames, float* envelope, float* logimg, int32_t* nn, uint8_t* label, int path,
+                    cudaStream_t st) {
+  us_status r = check_render_args(s, envs, B, poses, frames);
+  if (r != US_OK || B == 0) return r;
+  us_plan* pl;
+  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  RenderParams p = base_params(s, poses, seed, step, frames);
+  p.envelope = envelope;
+  p.logimg = logimg;
+  p.nn_index = nn;
+  p.label = label;
+  cudaError_t e;
+  if (path == 0) {
+    p.items = pl->d_items;
+    p.n_items = B;
+    if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(s, e, "reset work counter");
+    if ((e = launch_fused(p, s->shape, st)) != cudaSuccess) return cuda_fail(s, e, "fused render launch");
+  } else {
+    p.n_items = B;
+    if ((e = launch_plain(p, pl->items_batch.data(), B, s->probes.data(), s->scratch, st)) != cudaSuccess)
+      return cuda_fail(s, e, "plain render launch");
+  }
+  return US_OK;
+}
+
+void free_sim(us_sim* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  for (auto& ph : s->probes) {
+    cudaFree(ph.d_lines);
+    cudaFree(ph.d_wax);
+    cudaFree(ph.d_wlat);
+    cudaFree(ph.d_lut);
+    cudaFree(ph.d_tissue);
+  }
+  for (auto* d : s->d_pair_D) cudaFree(d);
+  for (auto& kv : s->plans) cudaFree(kv.second.d_items);
+  cudaFree(s->d_vols);
+  cudaFree(s->d_probes);
+  cudaFree(s->d_pairs);
+  cudaFree(s->scratch.lab);
+  cudaFree(s->scratch.S);
+  cudaFree(s->scratch.A);
+  cudaFree(s->scratch.Y);
+  cudaFree(s->d_err);
+  cudaFree(s->d_work);
+  cudaFree(s->d_host_poses);
+  cudaFree(s->d_host_frames);
+  delete s;
+}
+
+us_status apply_tuning(us_sim* s, const us_tuning& t) {
+  const int cs = t.cluster_size, nw = t.warps_per_cta;
+  if (!(cs == 2 || cs == 4 || cs == 8 || cs == 16)) return fail(s, US_ERR_INVALID_ARG, "cluster_size must be 2, 4, 8 or 16");
+  if (!(nw == 4 || nw == 8 || nw == 16 || nw == 32)) return fail(s, US_ERR_INVALID_ARG, "warps_per_cta must be 4, 8, 16 or 32");
+  if (t.ctas_per_sm < 1 || t.ctas_per_sm > 4) return fail(s, US_ERR_INVALID_ARG, "ctas_per_sm must be in [1, 4]");
+  FusedShape sh;
+  sh.cs = cs;
+  sh.nw = nw;
+  if (!fused_shape_fits(sh, s->probes))
+    return fail(s, US_ERR_UNSUPPORTED, "probe lines per CTA do not fit in shared memory for this cluster size");
+  int clusters = 0;
+  cudaError_t e = fused_max_clusters(sh, &clusters);
+  if (e != cudaSuccess) return cuda_fail(s, e, "occupancy query");
+  if (clusters < 1) return fail(s, US_ERR_UNSUPPORTED, "no cluster of this shape fits on the device");
+  sh.clusters = clusters;
+  s->shape = sh;
+  s->tuning = t;
+  return US_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* us_status_string(us_status st) {
+  switch (st) {
+    case US_OK: return "US_OK";
+    case US_ERR_INVALID_ARG: return "US_ERR_INVALID_ARG";
+    case US_ERR_CUDA: return "US_ERR_CUDA";
+    case US_ERR_OOM: return "US_ERR_OOM";
+    case US_ERR_TIMEOUT: return "US_ERR_TIMEOUT";
+    case US_ERR_UNSUPPORTED: return "US_ERR_UNSUPPORTED";
+    case US_ERR_INTERNAL: return "US_ERR_INTERNAL";
+  }
+  return "unknown status";
+}
+
+const char* us_sim_last_error(const us_sim* s) { return s ? s->last_error.c_str() : "NULL handle"; }
+
+us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* table, int32_t n_labels,
+                        const us_probe* probes, int32_t n_probes, const us_options* opt, us_sim** out) {
+  if (!out) return US_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!vols || n_vols < 1 || !table || n_labels < 1 || n_labels > 256 || !probes || n_probes < 1)
+    return US_ERR_INVALID_ARG;
+  us_sim* s = new (std::nothrow) us_sim();
+  if (!s) return US_ERR_OOM;
+  s->opt = opt ? *opt : us_options{1, 1, 0, 1};
+  if (!(s->opt.refl_power == 1 || s->opt.refl_power == 2) || (s->opt.transmission & ~1) || (s->opt.z_mode & ~1) ||
+      (s->opt.speckle & ~1)) {
+    delete s;
+    return US_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n_vols; ++i) {
+    const us_volume& v = vols[i];
+    if (!v.labels || !v.hu || v.nx < 1 || v.ny < 1 || v.nz < 1 || !(v.voxel_mm > 0) ||
+        (long long)v.nx * v.ny * v.nz >= (1ll << 31)) {
+      delete s;
+      return US_ERR_INVALID_ARG;
+    }
+    s->vols.push_back(v);
+  }
+  for (int i = 0; i < n_labels; ++i) {
+    const us_tissue& t = table[i];
+    if (!std::isfinite(t.alpha_db_cm_mhz) || !std::isfinite(t.z_mrayl) || !(t.z_mrayl > 0) || !std::isfinite(t.mu0) ||
+        !std::isfinite(t.sigma0) || std::isnan(t.mu1)) {
+      delete s;
+      return US_ERR_INVALID_ARG;
+    }
+    s->table.push_back(t);
+  }
+  s->n_labels = n_labels;
+  for (int i = 0; i < n_probes; ++i) {
+    std::string why = validate_probe(probes[i]);
+    if (!why.empty()) {
+      delete s;
+      return US_ERR_INVALID_ARG;
+    }
+    ProbeHost ph;
+    ph.desc = probes[i];
+    derive(ph);
+    s->probes.push_back(ph);
+  }
+  us_status r;
+  cudaError_t e;
+  for (auto& ph : s->probes)
+    if ((r = build_probe_tables(s, ph)) != US_OK) {
+      free_sim(s);
+      return r;
+    }
+  std::vector<DevVolume> dv;
+  for (const us_volume& v : s->vols)
+    dv.push_back(DevVolume{v.labels, v.hu, v.nx, v.ny, v.nz, (float)(1.0 / (double)v.voxel_mm)});
+  std::vector<DevProbe> dp;
+  for (const ProbeHost& ph : s->probes) dp.push_back(device_probe(ph));
+  std::vector<DevPair> pairs;
+  for (const us_volume& v : s->vols)
+    for (const ProbeHost& ph : s->probes) {
+      int W;
+      std::vector<uint8_t> D;
+      pair_tables(v, ph, W, D);
+      uint8_t* dD = nullptr;
+      if ((e = upload(&dD, D.data(), D.size())) != cudaSuccess) {
+        free_sim(s);
+        return cuda_fail(nullptr, e, "pairs");
+      }
+      s->d_pair_D.push_back(dD);
+      pairs.push_back(DevPair{W, dD});
+    }
+  size_t max_beam = 0;
+  for (const ProbeHost& ph : s->probes) max_beam = std::max(max_beam, (size_t)ph.desc.n_lines * ph.desc.n_samples);
+  if ((e = upload(&s->d_vols, dv.data(), dv.size())) != cudaSuccess || (e = upload(&s->d_probes, dp.data(), dp.size())) != cudaSuccess ||
+      (e = upload(&s->d_pairs, pairs.data(), pairs.size())) != cudaSuccess ||
+      (e = cudaMalloc(&s->scratch.lab, max_beam)) != cudaSuccess ||
+      (e = cudaMalloc(&s->scratch.S, max_beam * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->scratch.A, max_beam * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->scratch.Y, max_beam * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_err, sizeof(unsigned))) != cudaSuccess || (e = cudaMalloc(&s->d_work, sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMemset(s->d_err, 0, sizeof(unsigned))) != cudaSuccess) {
+    us_status st = e == cudaErrorMemoryAllocation ? US_ERR_OOM : US_ERR_CUDA;
+    free_sim(s);
+    return st;
+  }
+  // every label must index the tissue table
+  for (const us_volume& v : s->vols) {
+    unsigned mx = 0;
+    if ((e = cudaMemset(s->d_work, 0, sizeof(unsigned))) != cudaSuccess ||
+        (e = max_label(v.labels, (long long)v.nx * v.ny * v.nz, s->d_work, 0)) != cudaSuccess ||
+        (e = cudaMemcpy(&mx, s->d_work, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+      free_sim(s);
+      return US_ERR_CUDA;
+    }
+    if ((int)mx >= n_labels) {
+      free_sim(s);
+      return US_ERR_INVALID_ARG;
+    }
+  }
+  if ((r = apply_tuning(s, s->tuning)) != US_OK) {
+    // fall back to the smallest footprint that fits
+    us_tuning t{16, 16, 1, 0};
+    if ((r = apply_tuning(s, t)) != US_OK) {
+      free_sim(s);
+      return r;
+    }
+  }
+  *out = s;
+  return US_OK;
+}
+
+void us_sim_destroy(us_sim* s) { free_sim(s); }
+
+us_status us_sim_frame_layout(const us_sim* s, const us_env* envs, int32_t B, int64_t* offsets) {
+  if (!s || B < 0 || !offsets || (B > 0 && !envs)) return US_ERR_INVALID_ARG;
+  offsets[0] = 0;
+  for (int b = 0; b < B; ++b) {
+    if (envs[b].probe_id < 0 || envs[b].probe_id >= (int)s->probes.size() || envs[b].volume_id < 0 ||
+        envs[b].volume_id >= (int)s->vols.size())
+      return US_ERR_INVALID_ARG;
+    const us_probe& p = s->probes[envs[b].probe_id].desc;
+    offsets[b + 1] = offsets[b] + (((long long)p.out_w * p.out_h + 63) / 64) * 64;
+  }
+  return US_OK;
+}
+
+us_status us_sim_beam_layout(const us_sim* s, const us_env* envs, int32_t B, int64_t* offsets) {
+  if (!s || B < 0 || !offsets || (B > 0 && !envs)) return US_ERR_INVALID_ARG;
+  offsets[0] = 0;
+  for (int b = 0; b < B; ++b) {
+    if (envs[b].probe_id < 0 || envs[b].probe_id >= (int)s->probes.size()) return US_ERR_INVALID_ARG;
+    const us_probe& p = s->probes[envs[b].probe_id].desc;
+    offsets[b + 1] = offsets[b] + (long long)p.n_lines * p.n_samples;
+  }
+  return US_OK;
+}
+
+us_status us_sim_render(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint64_t seed, uint64_t step,
+                        float* frames, void* stream) {
+  return do_render(s, envs, B, poses, seed, step, frames, nullptr, nullptr, nullptr, nullptr, 0,
+                   static_cast<cudaStream_t>(stream));
+}
+
+us_status us_sim_render_plain(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint64_t seed,
+                              uint64_t step, float* frames, void* stream) {
+  return do_render(s, envs, B, poses, seed, step, frames, nullptr, nullptr, nullptr, nullptr, 1,
+                   static_cast<cudaStream_t>(stream));
+}
+
+us_status us_sim_render_debug(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint64_t seed,
+                              uint64_t step, float* frames, float* envelope, float* logimg, int32_t* nn_index,
+                              uint8_t* label, int32_t path, void* stream) {
+  if (path != 0 && path != 1) return fail(s, US_ERR_INVALID_ARG, "path must be 0 (fused) or 1 (plain)");
+  return do_render(s, envs, B, poses, seed, step, frames, envelope, logimg, nn_index, label, path,
+                   static_cast<cudaStream_t>(stream));
+}
+
+us_status us_sim_render_host(us_sim* s, const us_env* envs, int32_t B, const float* poses_host, uint64_t seed,
+                             uint64_t step, float* frames_host, void* stream) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (B < 0 || (B > 0 && (!envs || !poses_host || !frames_host))) return fail(s, US_ERR_INVALID_ARG, "bad host buffers");
+  if (B == 0) return US_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  us_plan* pl;
+  us_status r = get_plan(s, envs, B, &pl);
+  if (r != US_OK) return r;
+  for (int i = 0; i < 12 * B; ++i)
+    if (!std::isfinite(poses_host[i])) return fail(s, US_ERR_INVALID_ARG, "non-finite pose entry");
+  const size_t pose_bytes = (size_t)B * 12 * sizeof(float), frame_bytes = (size_t)pl->frame_floats * sizeof(float);
+  cudaError_t e;
+  if (pose_bytes > s->host_poses_cap) {
+    cudaFree(s->d_host_poses);
+    s->d_host_poses = nullptr;
+    if ((e = cudaMalloc(&s->d_host_poses, pose_bytes)) != cudaSuccess) return cuda_fail(s, e, "pose staging");
+    s->host_poses_cap = pose_bytes;
+  }
+  if (frame_bytes > s->host_frames_cap) {
+    cudaFree(s->d_host_frames);
+    s->d_host_frames = nullptr;
+    if ((e = cudaMalloc(&s->d_host_frames, frame_bytes)) != cudaSuccess) return cuda_fail(s, e, "frame staging");
+    s->host_frames_cap = frame_bytes;
+  }
+  if ((e = cudaMemcpyAsync(s->d_host_poses, poses_host, pose_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(s, e, "pose copy");
+  if ((r = do_render(s, envs, B, s->d_host_poses, seed, step, s->d_host_frames, nullptr, nullptr, nullptr, nullptr, 0,
+                     st)) != US_OK)
+    return r;
+  if ((e = cudaMemcpyAsync(frames_host, s->d_host_frames, frame_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(s, e, "frame copy");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e, "render");
+  return US_OK;
+}
+
+us_status us_sim_check(us_sim* s, void* stream) {
+  if (!s) return US_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream");
+  unsigned w = 0;
+  if ((e = cudaMemcpy(&w, s->d_err, sizeof w, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(s, e, "error word");
+  if (w) {
+    cudaMemset(s->d_err, 0, sizeof w);
+    if (w & kErrNonFinitePose) return fail(s, US_ERR_INVALID_ARG, "a pose had a non-finite entry (rendered as water)");
+    return fail(s, US_ERR_INTERNAL, "device consistency check failed");
+  }
+  return US_OK;
+}
+
+us_status us_sim_get_tuning(const us_sim* s, us_tuning* t) {
+  if (!s || !t) return US_ERR_INVALID_ARG;
+  *t = s->tuning;
+  return US_OK;
+}
+
+us_status us_sim_set_tuning(us_sim* s, const us_tuning* t) {
+  if (!s || !t) return US_ERR_INVALID_ARG;
+  return apply_tuning(s, *t);
+}
+
+us_status us_sim_autotune(us_sim* s, const us_env* envs, int32_t B, const float* poses, float* frames,
+                          const char* cache_path, void* stream) {
+  (void)envs; (void)B; (void)poses; (void)frames; (void)cache_path; (void)stream;
+  return fail(s, US_ERR_UNSUPPORTED, "autotune not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// Host-side internals of the ussim library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ussim.h"
+#include "us_device.cuh"
+
+namespace ussim {
+
+// probe descriptor plus its derived FP64 quantities and device tables
+struct ProbeHost {
+  us_probe desc;
+  double dr, dtheta, dlat_mid;
+  int k_ax, k_lat;
+  float2* d_lines = nullptr;
+  float* d_wax = nullptr;
+  float* d_wlat = nullptr;
+  float2* d_lut = nullptr;
+  DevTissue* d_tissue = nullptr;
+};
+
+// global scratch of the plain path (one environment at a time)
+struct PlainScratch {
+  uint8_t* lab = nullptr;
+  float* S = nullptr;
+  float* A = nullptr;
+  float* Y = nullptr;
+};
+
+cudaError_t launch_plain(const RenderParams& p, const EnvItem* items_host, int n_items,
+                         const ProbeHost* probes, PlainScratch& scr, cudaStream_t st);
+
+// launch shape of the fused kernel
+struct FusedShape {
+  int cs = 8;            // CTAs per cluster (one cluster renders one frame)
+  int nw = 32;           // warps per CTA
+  int sbuf_floats = 0;   // floats per CTA buffer (max over probes of lines-per-CTA * padded NS)
+  size_t smem = 0;       // dynamic shared memory per CTA
+  int clusters = 0;      // persistent grid, in clusters
+};
+
+// fills sbuf_floats / smem for the probe set; false if it cannot fit
+bool fused_shape_fits(FusedShape& s, const std::vector<ProbeHost>& probes);
+// occupancy-derived persistent grid (clusters resident at once)
+cudaError_t fused_max_clusters(const FusedShape& s, int* clusters);
+cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st);
+
+// label check at creation: max label of a volume
+cudaError_t max_label(const uint8_t* labels, long long n, unsigned* d_out, cudaStream_t st);
+
+}  // namespace ussim
+
+// a batch signature's precomputed work list
+struct us_plan {
+  std::vector<ussim::EnvItem> items_sorted;  // fused order: costliest first
+  std::vector<ussim::EnvItem> items_batch;   // caller order
+  ussim::EnvItem* d_items = nullptr;         // device copy of items_sorted
+  long long frame_floats = 0, beam_elems = 0;
+};
+
+struct us_sim {
+  std::vector<us_volume> vols;
+  std::vector<ussim::ProbeHost> probes;
+  std::vector<us_tissue> table;
+  us_options opt{};
+  int n_labels = 0;
+
+  ussim::DevVolume* d_vols = nullptr;
+  ussim::DevProbe* d_probes = nullptr;
+  ussim::DevPair* d_pairs = nullptr;
+  std::vector<uint8_t*> d_pair_D;
+
+  ussim::PlainScratch scratch;
+  unsigned* d_err = nullptr;
+  unsigned* d_work = nullptr;
+
+  ussim::FusedShape shape;
+  us_tuning tuning{8, 32, 1, 0};
+
+  std::map<std::string, us_plan> plans;
+
+  // staging for us_sim_render_host
+  float* d_host_poses = nullptr;
+  float* d_host_frames = nullptr;
+  size_t host_poses_cap = 0, host_frames_cap = 0;
+
+  std::string last_error;
+};

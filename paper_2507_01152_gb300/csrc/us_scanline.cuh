@@ -1,0 +1,113 @@
+// The image model along one scanline (SonoGym App. B.2), evaluated by one
+// warp: reflection R, remaining energy E, scatter pattern T, backscatter B,
+// and the pre-PSF image S = R + B for every sample of the line.
+#pragma once
+#include "us_device.cuh"
+
+namespace ussim {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_inclusive_scan(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// One warp renders line `l` of environment `b`.  Lane i owns the sample
+// pair (c + 2i, c + 2i + 1) of each 64-sample chunk c, so one Philox call
+// per lane serves both samples (counter = (s >> 1, l, b, 0)).  The energy
+// exponent is an exclusive prefix sum along the line: per-lane pair sums,
+// a warp inclusive scan, and a carry across chunks.
+//   lab(line, s)  -> nearest label of a beam sample (any line of the env)
+//   store(s, v)   -> receives S at sample s
+template <class LabFn, class StoreFn>
+__device__ __forceinline__ void scanline_model(const RenderParams& p, const DevProbe& P,
+                                               const DevVolume& V, const DevPair& pair,
+                                               const Pose& M, int b, int l, int lane, LabFn lab,
+                                               StoreFn store) {
+  const int NS = P.ns, NL = P.nl;
+  const float2 ln = P.lines[l];
+  const DevTissue* T = P.tissue;
+  const bool hu_mode = p.z_mode == 0;
+
+  auto z_at = [&](int s) -> float {
+    if (s >= NS) return 1.f;
+    if (hu_mode) {
+      float x, z;
+      beam_point(P, ln, s, x, z);
+      return fmaxf(trilinear_hu(V, to_voxel(M, V.inv_h, x, z)) + 1024.f, 1.f);
+    }
+    return __ldg(&T[lab(l, s)].z);
+  };
+
+  float z0 = z_at(2 * lane), z1 = z_at(2 * lane + 1);
+  float carry = 0.f;
+  for (int c = 0; c < NS; c += 64) {
+    const int sa = c + 2 * lane, sb = sa + 1;
+    const float nz0 = z_at(sa + 64), nz1 = z_at(sb + 64);
+    // impedance one sample below sb: the next lane's first sample, or the
+    // first sample of the next chunk for the last lane
+    float zc = __shfl_down_sync(kFull, z0, 1);
+    const float zc_next = __shfl_sync(kFull, nz0, 0);
+    if (lane == 31) zc = zc_next;
+
+    const unsigned la = sa < NS ? lab(l, sa) : 0u;
+    const unsigned lb = sb < NS ? lab(l, sb) : 0u;
+    const unsigned lc = sb + 1 < NS ? lab(l, sb + 1) : lb;
+    const bool Ga = sa < NS - 1 && lb != la;
+    const bool Gb = sb < NS - 1 && lc != lb;
+    const float ra = sa < NS - 1 ? (z1 - z0) / (z1 + z0) : 0.f;
+    const float rb = sb < NS - 1 ? (zc - z1) / (zc + z1) : 0.f;
+
+    float cosa = 1.f, cosb = 1.f;
+    if (Ga) cosa = incidence_cos(lab, l, sa, NL, NS, pair.W, pair.D[sa], P.dr, lateral_spacing(P, sa));
+    if (Gb) cosb = incidence_cos(lab, l, sb, NL, NS, pair.W, pair.D[sb], P.dr, lateral_spacing(P, sb));
+
+    const DevTissue ta = T[la], tb = T[lb];
+    float inc_a = sa < NS ? -ta.att : 0.f;
+    float inc_b = sb < NS ? -tb.att : 0.f;
+    if (p.transmission) {
+      if (Ga) inc_a += logf(fmaxf(1.f - ra * ra, 1e-30f));
+      if (Gb) inc_b += logf(fmaxf(1.f - rb * rb, 1e-30f));
+    }
+    const float pair_sum = inc_a + inc_b;
+    const float incl = warp_inclusive_scan(pair_sum, lane);
+    const float La = carry + (incl - pair_sum);
+    const float Lb = La + inc_a;
+    carry += __shfl_sync(kFull, incl, 31);
+    const float Ea = P.e0 * expf(La), Eb = P.e0 * expf(Lb);
+
+    float Ra = 0.f, Rb = 0.f;
+    if (Ga) {
+      const float q = fabsf(cosa * ra);
+      Ra = Ea * (p.refl_power == 2 ? q * q : q);
+    }
+    if (Gb) {
+      const float q = fabsf(cosb * rb);
+      Rb = Eb * (p.refl_power == 2 ? q * q : q);
+    }
+
+    float Ta, Tb;
+    if (p.speckle) {
+      const uint4 w = philox4x32_10(make_uint4((unsigned)sa >> 1, (unsigned)l, (unsigned)b, 0u), p.key);
+      const float rad = sqrtf(-2.f * logf(u01(w.x)));
+      float sn, cs;
+      sincospif(2.f * u01(w.y), &sn, &cs);
+      Ta = (unsigned long long)w.z < ta.t1 ? fmaf(rad * cs, ta.sigma0, ta.mu0) : 0.f;
+      Tb = (unsigned long long)w.w < tb.t1 ? fmaf(rad * sn, tb.sigma0, tb.mu0) : 0.f;
+    } else {
+      Ta = ta.mu0;
+      Tb = tb.mu0;
+    }
+    if (sa < NS) store(sa, fmaf(Ea, Ta, Ra));
+    if (sb < NS) store(sb, fmaf(Eb, Tb, Rb));
+    z0 = nz0;
+    z1 = nz1;
+  }
+}
+
+}  // namespace ussim

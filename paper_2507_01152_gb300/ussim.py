@@ -1,0 +1,238 @@
+"""Thin ctypes binding of libussim (include/ussim.h).
+
+Argument marshalling only: every step of the render runs in the CUDA
+library.  Device buffers are passed as torch CUDA tensors (torch provides
+device memory and streams, nothing else); host buffers as numpy arrays.
+Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+US_OK, US_ERR_INVALID_ARG, US_ERR_CUDA, US_ERR_OOM, US_ERR_TIMEOUT, US_ERR_UNSUPPORTED, US_ERR_INTERNAL = range(7)
+
+
+class UsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS = {0: "US_OK", 1: "US_ERR_INVALID_ARG", 2: "US_ERR_CUDA", 3: "US_ERR_OOM", 4: "US_ERR_TIMEOUT",
+           5: "US_ERR_UNSUPPORTED", 6: "US_ERR_INTERNAL"}
+
+
+class us_volume(C.Structure):
+    _fields_ = [("labels", C.c_void_p), ("hu", C.c_void_p), ("nx", C.c_int32), ("ny", C.c_int32),
+                ("nz", C.c_int32), ("voxel_mm", C.c_float)]
+
+
+class us_tissue(C.Structure):
+    _fields_ = [("alpha_db_cm_mhz", C.c_float), ("z_mrayl", C.c_float), ("mu0", C.c_float),
+                ("sigma0", C.c_float), ("mu1", C.c_float)]
+
+
+class us_probe(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_lines", C.c_int32), ("n_samples", C.c_int32),
+                ("depth_mm", C.c_float), ("pitch_mm", C.c_float), ("fan_deg", C.c_float),
+                ("radius_mm", C.c_float), ("out_w", C.c_int32), ("out_h", C.c_int32),
+                ("f_mhz", C.c_float), ("e0", C.c_float), ("psf_sigma_ax_mm", C.c_float),
+                ("psf_sigma_lat_mm", C.c_float), ("dyn_range_db", C.c_float)]
+
+
+class us_options(C.Structure):
+    _fields_ = [("refl_power", C.c_int32), ("transmission", C.c_int32), ("z_mode", C.c_int32),
+                ("speckle", C.c_int32)]
+
+
+class us_env(C.Structure):
+    _fields_ = [("volume_id", C.c_int32), ("probe_id", C.c_int32)]
+
+
+class us_tuning(C.Structure):
+    _fields_ = [("cluster_size", C.c_int32), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("use_graph", C.c_int32)]
+
+
+# name -> (restype, argtypes) for every entry point of include/ussim.h
+_P = C.c_void_p
+SIGNATURES = {
+    "us_sim_create": (C.c_int, [C.POINTER(us_volume), C.c_int32, C.POINTER(us_tissue), C.c_int32,
+                                C.POINTER(us_probe), C.c_int32, C.POINTER(us_options), C.POINTER(_P)]),
+    "us_sim_destroy": (None, [_P]),
+    "us_sim_frame_layout": (C.c_int, [_P, _P, C.c_int32, _P]),
+    "us_sim_beam_layout": (C.c_int, [_P, _P, C.c_int32, _P]),
+    "us_sim_render": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
+    "us_sim_render_plain": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
+    "us_sim_render_debug": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, _P, _P, _P,
+                                      C.c_int32, _P]),
+    "us_sim_render_host": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
+    "us_sim_check": (C.c_int, [_P, _P]),
+    "us_sim_get_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
+    "us_sim_set_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
+    "us_sim_autotune": (C.c_int, [_P, _P, C.c_int32, _P, _P, C.c_char_p, _P]),
+    "us_sim_last_error": (C.c_char_p, [_P]),
+    "us_status_string": (C.c_char_p, [C.c_int]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libussim.so; raises if it is missing (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError(f"libussim.so not built ({_build.LIB}); run paper_2507_01152_gb300.build")
+            _build.build()
+        L = C.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_probe(p) -> us_probe:
+    return us_probe(p.kind, p.n_lines, p.n_samples, p.depth_mm, p.pitch_mm, p.fan_deg, p.radius_mm,
+                    p.out_w, p.out_h, p.f_mhz, p.e0, p.psf_sigma_ax_mm, p.psf_sigma_lat_mm, p.dyn_range_db)
+
+
+def make_envs(envs) -> C.Array:
+    envs = np.ascontiguousarray(envs, np.int32).reshape(-1, 2)
+    arr = (us_env * max(1, len(envs)))()
+    for i, (v, p) in enumerate(envs):
+        arr[i] = us_env(int(v), int(p))
+    return arr
+
+
+class Sim:
+    """A simulator handle.  volumes: list of (labels, hu, voxel_mm) with
+    labels/hu torch CUDA tensors ([nz][ny][nx] uint8 / int16), kept alive
+    here; table: list of tissue records; probes: list of probe records."""
+
+    def __init__(self, volumes, table, probes, options=None):
+        L = load()
+        self._keep = [(l, h) for (l, h, _) in volumes]
+        vols = (us_volume * len(volumes))()
+        for i, (lab, hu, vox) in enumerate(volumes):
+            nz, ny, nx = lab.shape
+            vols[i] = us_volume(_ptr(lab), _ptr(hu), nx, ny, nz, vox)
+        tab = (us_tissue * len(table))()
+        for i, t in enumerate(table):
+            tab[i] = us_tissue(t.alpha_db_cm_mhz, t.z_mrayl, t.mu0, t.sigma0, t.mu1)
+        prs = (us_probe * len(probes))(*[make_probe(p) for p in probes])
+        opt = None
+        if options is not None:
+            opt = us_options(options.refl_power, options.transmission, options.z_mode, options.speckle)
+        h = C.c_void_p()
+        st = L.us_sim_create(vols, len(volumes), tab, len(table), prs, len(probes),
+                             C.byref(opt) if opt is not None else None, C.byref(h))
+        if st != US_OK:
+            raise UsError(st, "us_sim_create failed")
+        self.h = h
+        self.probes = list(probes)
+        self._lib = L
+
+    # ------------------------------------------------------------ helpers
+    def _check(self, st):
+        if st != US_OK:
+            raise UsError(st, self._lib.us_sim_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.us_sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------- ABI
+    def frame_layout(self, envs) -> np.ndarray:
+        e = make_envs(envs)
+        B = len(np.asarray(envs).reshape(-1, 2))
+        off = np.zeros(B + 1, np.int64)
+        self._check(self._lib.us_sim_frame_layout(self.h, e, B, off.ctypes.data))
+        return off
+
+    def beam_layout(self, envs) -> np.ndarray:
+        e = make_envs(envs)
+        B = len(np.asarray(envs).reshape(-1, 2))
+        off = np.zeros(B + 1, np.int64)
+        self._check(self._lib.us_sim_beam_layout(self.h, e, B, off.ctypes.data))
+        return off
+
+    def render(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
+        B = poses.shape[0] if poses is not None else 0
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_render(self.h, e, B, _ptr(poses), seed, step, _ptr(frames),
+                                            _stream_handle(stream)))
+
+    def render_plain(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
+        B = poses.shape[0]
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_render_plain(self.h, e, B, _ptr(poses), seed, step, _ptr(frames),
+                                                  _stream_handle(stream)))
+
+    def render_debug(self, envs, poses, seed, step, frames, envelope=None, logimg=None, nn_index=None,
+                     label=None, path=0, stream=None):
+        B = poses.shape[0]
+        self._check(self._lib.us_sim_render_debug(self.h, make_envs(envs), B, _ptr(poses), seed, step,
+                                                  _ptr(frames), _ptr(envelope), _ptr(logimg), _ptr(nn_index),
+                                                  _ptr(label), path, _stream_handle(stream)))
+
+    def render_host(self, envs, poses_host, seed, step, frames_host, stream=None, envs_c=None):
+        poses_host = np.ascontiguousarray(poses_host, np.float32)
+        B = poses_host.shape[0]
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_render_host(self.h, e, B, _ptr(poses_host), seed, step, _ptr(frames_host),
+                                                 _stream_handle(stream)))
+
+    def check(self, stream=None):
+        self._check(self._lib.us_sim_check(self.h, _stream_handle(stream)))
+
+    def get_tuning(self) -> dict:
+        t = us_tuning()
+        self._check(self._lib.us_sim_get_tuning(self.h, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in us_tuning._fields_}
+
+    def set_tuning(self, cluster_size, warps_per_cta, ctas_per_sm=1, use_graph=0):
+        t = us_tuning(cluster_size, warps_per_cta, ctas_per_sm, use_graph)
+        self._check(self._lib.us_sim_set_tuning(self.h, C.byref(t)))
+
+    def autotune(self, envs, poses, frames, cache_path=None, stream=None):
+        B = poses.shape[0]
+        self._check(self._lib.us_sim_autotune(self.h, make_envs(envs), B, _ptr(poses), _ptr(frames),
+                                              cache_path.encode() if cache_path else None,
+                                              _stream_handle(stream)))

@@ -1,0 +1,270 @@
+"""GPU parity of the render path (fused persistent kernel and plain
+per-environment kernels) against the CPU oracle, through the C ABI."""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute
+from paper_2507_01152_gb300 import scene
+
+from simhelp import compare, gpu_sim, render_gpu, render_oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_01152_gb300 import build
+    build.build()
+
+
+def _check_all(g, o, probes, envs, which, frame_tol=1e-3):
+    bad = {}
+    for b in which:
+        m = compare(g[b], o[b], probes[int(envs[b][1])], frame_tol)
+        if m:
+            bad[b] = m
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_single_linear_env_128cube(path):
+    """1 env, 128^3 volume at 1 mm, linear 128 x 256 to 80 mm."""
+    wl = scene.workload_c1()
+    sim = gpu_sim(wl)
+    g = render_gpu(sim, wl.envs, wl.poses, wl.seed, 0, path=path)
+    o = render_oracle(wl, wl.envs, wl.poses, wl.seed, 0, [0])
+    _check_all(g, o, wl.probes, wl.envs, [0])
+    assert (g[0]["label"] > 0).mean() > 0.5      # the probe looks into the body
+
+
+@pytest.fixture(scope="module")
+def c2():
+    wl = scene.workload_c2(64)
+    return wl, gpu_sim(wl)
+
+
+def test_batched_curvilinear_64env_full(c2):
+    """All 64 envs of the 256^3 curvilinear batch, element by element, in the
+    launch configuration the benchmark uses."""
+    wl, sim = c2
+    g = render_gpu(sim, wl.envs, wl.poses, wl.seed, 5, path=0)
+    o = render_oracle(wl, wl.envs, wl.poses, wl.seed, 5, range(64))
+    _check_all(g, o, wl.probes, wl.envs, range(64))
+
+
+def test_fused_equals_plain_bitwise(c2):
+    wl, sim = c2
+    envs, poses = wl.envs[:12], wl.poses[:12]
+    a = render_gpu(sim, envs, poses, 11, 2, path=0)
+    b = render_gpu(sim, envs, poses, 11, 2, path=1)
+    for x, y in zip(a, b):
+        for k in x:
+            assert np.array_equal(x[k], y[k]), k
+
+
+def test_deterministic_and_step_keyed(c2):
+    wl, sim = c2
+    envs, poses = wl.envs[:6], wl.poses[:6]
+    a = render_gpu(sim, envs, poses, 3, 1, debug=False)
+    b = render_gpu(sim, envs, poses, 3, 1, debug=False)
+    c = render_gpu(sim, envs, poses, 3, 2, debug=False)
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x["frame"], y["frame"])
+        assert not np.array_equal(x["frame"], z["frame"])   # fresh speckle every step
+
+
+def test_launch_shape_that_cannot_fit_is_rejected(c2):
+    from paper_2507_01152_gb300.ussim import UsError, US_ERR_UNSUPPORTED
+    wl, sim = c2
+    with pytest.raises(UsError) as e:
+        sim.set_tuning(2, 32)          # 128 lines x 512 samples per CTA: too large
+    assert e.value.status == US_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("cs,nw", [(8, 8), (8, 16), (8, 32), (16, 4), (16, 16), (16, 32)])
+def test_launch_shapes_agree(c2, cs, nw):
+    wl, sim = c2
+    envs, poses = wl.envs[:10], wl.poses[:10]
+    ref = render_gpu(sim, envs, poses, 21, 0, path=1, debug=False)
+    old = sim.get_tuning()
+    try:
+        sim.set_tuning(cs, nw)
+        got = render_gpu(sim, envs, poses, 21, 0, path=0, debug=False)
+    finally:
+        sim.set_tuning(old["cluster_size"], old["warps_per_cta"])
+    for x, y in zip(ref, got):
+        assert np.array_equal(x["frame"], y["frame"])
+
+
+def _tiny_volume(seed, shape=(14, 16, 18)):
+    rng = np.random.default_rng(seed)
+    lab = np.repeat(rng.integers(0, 5, (shape[0], shape[1], (shape[2] + 2) // 3)), 3, axis=2)[:, :, :shape[2]]
+    hu = rng.integers(-300, 900, shape).astype(np.int16)
+    return np.ascontiguousarray(lab.astype(np.uint8)), hu
+
+
+def _rand_pose(rng, centre):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    R = np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                  [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                  [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+    t = np.asarray(centre) + rng.uniform(-3, 3, 3)
+    return np.concatenate([R, t[:, None]], axis=1).astype(np.float32)
+
+
+@pytest.mark.parametrize("opt", [scene.Options(1, 1, 0, 1), scene.Options(2, 0, 1, 1), scene.Options(1, 1, 1, 0),
+                                 scene.Options(2, 1, 0, 0)])
+def test_tiny_random_cases_vs_oracle_and_brute_force(opt):
+    """Tiny volumes, ragged probes (line and sample counts that fill no
+    tile evenly), random rotations; GPU against the oracle and, for a few,
+    against the brute force."""
+    lab, hu = _tiny_volume(3)
+    spec = scene.VolumeSpec(18, 16, 14, 1.0, 0, 0)
+    probes = [scene.linear_probe(7, 37, 9.0, 0.8, psf_sigma_ax_mm=0.5, psf_sigma_lat_mm=1.0),
+              scene.curvilinear_probe(9, 70, 8.0, 50.0, 6.0, 13, 11, psf_sigma_ax_mm=0.3, psf_sigma_lat_mm=0.6),
+              scene.curvilinear_probe(33, 130, 12.0, 70.0, 5.0, 24, 20, psf_sigma_ax_mm=0.4, psf_sigma_lat_mm=0.5)]
+    rng = np.random.default_rng(17)
+    B = 24
+    envs = np.stack([np.zeros(B), np.arange(B) % 3], axis=1).astype(np.int32)
+    poses = np.stack([_rand_pose(rng, (9.0, 8.0, 2.0)) for _ in range(B)])
+    wl = scene.Workload("tiny", [(spec, lab, hu)], probes, envs, poses, options=opt, seed=99)
+    sim = gpu_sim(wl)
+    for path in (0, 1):
+        g = render_gpu(sim, envs, poses, 0xABCDEF0123, 9, path=path)
+        o = render_oracle(wl, envs, poses, 0xABCDEF0123, 9, range(B))
+        _check_all(g, o, probes, envs, range(B))
+    for b in range(3):
+        br = brute.render(lab, hu, 1.0, scene.tissue_table(), probes[envs[b][1]], opt, poses[b], env=b,
+                          seed=0xABCDEF0123, step=9)
+        assert not compare(g[b], br, probes[envs[b][1]])
+
+
+def test_paper_size_linear_200x150():
+    """100 envs, linear 150 lines x 200 samples (200 x 150 image at 0.5 mm)."""
+    wl = scene.workload_paper_replica(100)
+    sim = gpu_sim(wl)
+    g = render_gpu(sim, wl.envs, wl.poses, wl.seed, 0)
+    o = render_oracle(wl, wl.envs, wl.poses, wl.seed, 0, range(0, 100, 7))
+    _check_all(g, o, wl.probes, wl.envs, range(0, 100, 7))
+
+
+@pytest.mark.slow
+def test_uneven_batch_512env_sampled():
+    """512 envs over four 512 x 512 x 256 volumes and three probe types, in
+    the fused launch; a sample of envs of every probe type and volume
+    checked element by element."""
+    wl = scene.workload_c3(512, steps=2)
+    sim = gpu_sim(wl)
+    poses = wl.poses[1]
+    g = render_gpu(sim, wl.envs, poses, wl.seed, 1)
+    which = list(range(0, 512, 23)) + [511]
+    o = render_oracle(wl, wl.envs, poses, wl.seed, 1, which)
+    _check_all(g, o, wl.probes, wl.envs, which)
+
+
+def test_host_buffers_match_device(c2):
+    wl, sim = c2
+    envs, poses = wl.envs[:5], wl.poses[:5]
+    ref = render_gpu(sim, envs, poses, 8, 8, debug=False)
+    off = sim.frame_layout(envs)
+    host = np.zeros(int(off[-1]), np.float32)
+    sim.render_host(envs, poses, 8, 8, host)
+    for b in range(5):
+        assert np.array_equal(host[off[b]:off[b + 1]][:256 * 256].reshape(256, 256), ref[b]["frame"])
+
+
+def test_empty_batch_and_bad_arguments(c2):
+    from paper_2507_01152_gb300.ussim import UsError, US_ERR_INVALID_ARG
+    wl, sim = c2
+    frames = torch.zeros(256 * 256 * 2, device="cuda")
+    sim.render(np.zeros((0, 2), np.int32), torch.zeros((0, 3, 4), device="cuda"), 1, 1, frames)
+    P = torch.from_numpy(wl.poses[:2]).cuda()
+    with pytest.raises(UsError) as e:
+        sim.render(np.array([[0, 5], [0, 0]], np.int32), P, 1, 1, frames)
+    assert e.value.status == US_ERR_INVALID_ARG
+    with pytest.raises(UsError):
+        sim.render(np.array([[1, 0], [0, 0]], np.int32), P, 1, 1, frames)
+    with pytest.raises(UsError):
+        sim.render(wl.envs[:2], P, 1, 1, frames[1:])          # misaligned frames
+    with pytest.raises(UsError):
+        sim.render_host(wl.envs[:1], np.full((1, 3, 4), np.nan, np.float32), 1, 1, np.zeros(65536, np.float32))
+
+
+def test_non_finite_pose_renders_water_and_is_reported(c2):
+    from paper_2507_01152_gb300.ussim import UsError
+    wl, sim = c2
+    poses = wl.poses[:3].copy()
+    poses[1, 0, 3] = np.nan
+    g = render_gpu(sim, wl.envs[:3], poses, 1, 1, debug=False)
+    with pytest.raises(UsError):
+        sim.check()
+    sim.check()                                   # the error word was cleared
+    assert np.all(g[1]["frame"] == 0.0)
+    assert np.any(g[0]["frame"] > 0.0)
+
+
+def test_label_outside_table_rejected_at_create():
+    from paper_2507_01152_gb300.ussim import Sim, UsError
+    lab = torch.full((4, 4, 4), 9, dtype=torch.uint8, device="cuda")
+    hu = torch.zeros((4, 4, 4), dtype=torch.int16, device="cuda")
+    with pytest.raises(UsError):
+        Sim([(lab, hu, 1.0)], scene.tissue_table(), [scene.linear_probe(8, 16, 8.0, 0.5)])
+
+
+def test_probe_outside_volume_is_water():
+    spec = scene.VolumeSpec(8, 8, 8, 1.0, 0, 0)
+    lab = np.full((8, 8, 8), 3, np.uint8)
+    hu = np.full((8, 8, 8), 50, np.int16)
+    probes = [scene.linear_probe(8, 16, 8.0, 0.5)]
+    pose = np.array([[1, 0, 0, 500.0], [0, 1, 0, 500.0], [0, 0, 1, 500.0]], np.float32)[None]
+    wl = scene.Workload("far", [(spec, lab, hu)], probes, np.zeros((1, 2), np.int32), pose)
+    g = render_gpu(gpu_sim(wl), wl.envs, pose, 1, 1)
+    assert np.all(g[0]["nn_index"] == -1) and np.all(g[0]["label"] == 0) and np.all(g[0]["frame"] == 0)
+
+
+def test_philox_matches_curand(tmp_path):
+    """The oracle's Philox (which the speckle parity ties to the CUDA path)
+    against NVIDIA's curand_Philox4x32_10 on the device."""
+    import ctypes
+    import subprocess
+    src = tmp_path / "p.cu"
+    src.write_text(r'''
+#include <curand_kernel.h>
+__global__ void k(const uint4* c, const uint2* key, uint4* o, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = curand_Philox4x32_10(c[i], key[i]);
+}
+extern "C" int run(const unsigned* c, const unsigned* key, unsigned* o, int n) {
+  uint4 *dc, *dout; uint2* dk;
+  cudaMalloc(&dc, n * 16); cudaMalloc(&dk, n * 8); cudaMalloc(&dout, n * 16);
+  cudaMemcpy(dc, c, n * 16, cudaMemcpyHostToDevice); cudaMemcpy(dk, key, n * 8, cudaMemcpyHostToDevice);
+  k<<<(n + 127) / 128, 128>>>(dc, dk, dout, n);
+  int e = (int)cudaMemcpy(o, dout, n * 16, cudaMemcpyDeviceToHost);
+  cudaFree(dc); cudaFree(dk); cudaFree(dout);
+  return e;
+}''')
+    so = tmp_path / "p.so"
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-Xcompiler", "-fPIC",
+                    str(src), "-o", str(so)], check=True)
+    lib = ctypes.CDLL(str(so))
+    rng = np.random.default_rng(1)
+    n = 4096
+    c = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    k = rng.integers(0, 2 ** 32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    c[0] = 0
+    k[0] = 0
+    out = np.zeros((n, 4), np.uint32)
+    assert lib.run(c.ctypes.data, k.ctypes.data, out.ctypes.data, n) == 0
+    for i in range(0, n, 7):
+        assert list(oracle.philox4x32_10(c[i], k[i])) == list(out[i])
+    assert list(out[0]) == [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]
