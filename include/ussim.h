@@ -167,6 +167,25 @@ US_API us_status us_sim_render(us_sim* sim, const us_env* envs, int32_t B, const
 US_API us_status us_sim_render_plain(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
                               uint64_t seed, uint64_t step, float* frames, void* stream);
 
+/* Render with no device allocation in the call.  The paper has no
+ * counterpart; this serves callers that must not allocate device memory
+ * while they render (a control loop whose allocations could stall, or a
+ * process whose device memory is already fully claimed by its own
+ * allocator).  Same frames as us_sim_render_plain (same kernels, frame
+ * layout of us_sim_frame_layout), but the per-environment scratch lives in
+ * a fixed 1.625 MiB array compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  Limit: each env's
+ * beam grid must have at most 256 x 512 = 131072 samples (n_lines x
+ * n_samples), else US_ERR_INVALID_ARG before any launch.  The call makes
+ * no cudaMalloc / cudaFree and no allocating library call.  The first call
+ * on a device looks up the array's device address (once per device); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race on it, so serialise them (one
+ * stream).  Nothing in it needs clearing; every element is written before
+ * it is read. */
+US_API us_status us_sim_render_plain_static(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                                            uint64_t seed, uint64_t step, float* frames, void* stream);
+
 /* Render with intermediate exports for testing.  path 0 = fused, 1 = plain.
  * envelope (float), logimg (float), nn_index (int32, -1 outside the
  * volume), label (uint8): DEVICE, laid out by us_sim_beam_layout, [NL][NS]

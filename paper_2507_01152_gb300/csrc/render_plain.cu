@@ -96,6 +96,18 @@ __global__ void plain_scan_convert(RenderParams p, EnvItem it, const float* Y) {
   out[q] = v;
 }
 
+cudaError_t launch_plain_env(const RenderParams& p, const EnvItem& it, const ProbeHost& ph,
+                             const PlainScratch& scr, cudaStream_t st) {
+  const int n = ph.desc.n_lines * ph.desc.n_samples;
+  const int nout = ph.desc.out_w * ph.desc.out_h;
+  plain_slice<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.lab);
+  plain_lines<<<(ph.desc.n_lines + 3) / 4, 128, 0, st>>>(p, it, scr.lab, scr.S);
+  plain_psf_axial<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.S, scr.A);
+  plain_psf_lateral_log<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.A, scr.Y);
+  plain_scan_convert<<<(nout + 255) / 256, 256, 0, st>>>(p, it, scr.Y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_plain(const RenderParams& p, const EnvItem* items_host, int n_items,
                          const ProbeHost* probes, PlainScratch& scr, cudaStream_t st) {
   for (int i = 0; i < n_items; ++i) {

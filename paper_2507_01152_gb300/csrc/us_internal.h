@@ -34,6 +34,9 @@ struct PlainScratch {
 
 cudaError_t launch_plain(const RenderParams& p, const EnvItem* items_host, int n_items,
                          const ProbeHost* probes, PlainScratch& scr, cudaStream_t st);
+// the same five kernels for one environment, on caller-given scratch
+cudaError_t launch_plain_env(const RenderParams& p, const EnvItem& it, const ProbeHost& ph,
+                             const PlainScratch& scr, cudaStream_t st);
 
 // launch shape of the fused kernel
 struct FusedShape {

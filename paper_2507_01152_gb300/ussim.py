@@ -69,6 +69,7 @@ SIGNATURES = {
     "us_sim_beam_layout": (C.c_int, [_P, _P, C.c_int32, _P]),
     "us_sim_render": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
     "us_sim_render_plain": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
+    "us_sim_render_plain_static": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
     "us_sim_render_debug": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, _P, _P, _P,
                                       C.c_int32, _P]),
     "us_sim_render_host": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
@@ -204,6 +205,12 @@ class Sim:
         e = envs_c if envs_c is not None else make_envs(envs)
         self._check(self._lib.us_sim_render_plain(self.h, e, B, _ptr(poses), seed, step, _ptr(frames),
                                                   _stream_handle(stream)))
+
+    def render_plain_static(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
+        B = poses.shape[0]
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_render_plain_static(self.h, e, B, _ptr(poses), seed, step, _ptr(frames),
+                                                         _stream_handle(stream)))
 
     def render_debug(self, envs, poses, seed, step, frames, envelope=None, logimg=None, nn_index=None,
                      label=None, path=0, stream=None):
