@@ -8,10 +8,12 @@
 // conversion) read them from the other CTAs through distributed shared
 // memory.  Nothing of a frame but the final image touches global memory.
 //
-// Per environment: (1) label slice of own lines, cluster barrier;
-// (2) scanline model + in-place axial PSF per own line, cluster barrier;
-// (3) lateral PSF + log compression, cluster barrier; (4) scan conversion
-// (curvilinear) or transposed store (linear) with streaming stores.
+// Per environment: (1) slice: nearest label and impedance of every sample
+// of own lines, cluster barrier; (2) scanline model + in-place axial PSF per
+// own line, cluster barrier; (3) lateral PSF + log compression, cluster
+// barrier; (4) scan conversion (curvilinear) or transposed store (linear)
+// with streaming stores.  Cross-CTA rows are reached through per-item
+// tables of row pointers into the owning CTA's shared memory.
 #include <cooperative_groups.h>
 
 #include "us_internal.h"
@@ -21,139 +23,182 @@ namespace cg = cooperative_groups;
 
 namespace ussim {
 
-// In-place axial PSF of one line held in shared memory, one warp.  Chunk
-// c's filtered values are written back only after chunk c+1 has been
-// computed, so every read sees unfiltered data (requires K <= 32).
-__device__ __forceinline__ void axial_psf_inplace(float* row, int NS, const float* w, int K, int lane) {
+// per-item context shared by the CTA (read through shared memory)
+struct ItemCtx {
+  EnvItem it;
+  DevProbe P;
+  DevVolume V;
+  DevPair pair;
+  Pose M;
+  int finite;
+};
+
+// In-place axial PSF of one line, one warp.  `prow` is the padded row: K
+// zeros, NS samples, K zeros, so every tap reads in bounds.  Chunk c's
+// results are written back only after chunk c+1 has been computed, so every
+// read sees unfiltered data (K <= 32).  Tap order matches the plain kernel.
+__device__ __forceinline__ void axial_psf_padded(float* prow, int NS, const float* w, int K, int lane) {
   float prev = 0.f;
   int prev_s = -1;
+  const int taps = 2 * K + 1;
   for (int c = 0; c < NS; c += 32) {
     const int s = c + lane;
     float acc = 0.f;
     if (s < NS) {
-      for (int k = -K; k <= K; ++k) {
-        const int ss = s + k;
-        if (ss >= 0 && ss < NS) acc = fmaf(__ldg(&w[k + K]), row[ss], acc);
-      }
+      const float* q = prow + s;
+      for (int k = 0; k < taps; ++k) acc = fmaf(w[k], q[k], acc);
     }
     __syncwarp();
-    if (prev_s >= 0 && prev_s < NS) row[prev_s] = prev;
+    if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
     __syncwarp();
     prev = acc;
     prev_s = s;
   }
-  if (prev_s >= 0 && prev_s < NS) row[prev_s] = prev;
+  if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
   __syncwarp();
 }
 
 template <int NW>
-__global__ void __launch_bounds__(NW * 32, 1) fused_render(RenderParams p, int sbuf_floats) {
+__global__ void __launch_bounds__(NW * 32, 1) fused_render(RenderParams p, FusedLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ItemCtx cx;
   __shared__ int slot[2];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int CS = (int)cl.num_blocks();
-  float* sbuf = reinterpret_cast<float*>(smem);   // pre-PSF, then axially filtered lines
-  float* ybuf = sbuf + sbuf_floats;                // log image of own lines
-  uint8_t* lbuf = reinterpret_cast<uint8_t*>(ybuf + sbuf_floats);  // labels of own lines
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* sbuf = reinterpret_cast<float*>(smem);                   // impedance, then S, then axially filtered S
+  float* ybuf = reinterpret_cast<float*>(smem + L.off_y);         // log image of own lines
+  uint8_t* lbuf = smem + L.off_lab;                               // labels of own lines
+  const uint8_t** lab_row = reinterpret_cast<const uint8_t**>(smem + L.off_lrow);  // any line -> its label row
+  const float** s_row = reinterpret_cast<const float**>(smem + L.off_srow);        // any line -> its filtered row
+  const float** y_row = reinterpret_cast<const float**>(smem + L.off_yrow);        // any line -> its log row
+  float* wax = reinterpret_cast<float*>(smem + L.off_wax);
+  float* wlat = reinterpret_cast<float*>(smem + L.off_wlat);     // zero-padded at both ends
+  DevTissue* tis = reinterpret_cast<DevTissue*>(smem + L.off_tis);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (rank == 0 && threadIdx.x == 0) slot[0] = (int)atomicAdd(p.work, 1u);
+  if (rank == 0 && tid == 0) slot[0] = (int)atomicAdd(p.work, 1u);
   cl.sync();
   int parity = 0;
   int idx = *cl.map_shared_rank(&slot[0], 0);
 
   while (idx < p.n_items) {
-    const EnvItem it = p.items[idx];
-    const DevProbe P = p.probes[it.probe];
-    const DevVolume V = p.vols[it.vol];
-    const DevPair pair = p.pairs[it.pair];
-    bool finite;
-    const Pose M = load_pose(p.poses, it.b, finite);
-    if (!finite && rank == 0 && threadIdx.x == 0) atomicOr(p.err, kErrNonFinitePose);
-    const int NL = P.nl, NS = P.ns, NSP = NS | 1;
+    __syncthreads();  // every thread is done with the previous item's context and tables
+    if (tid == 0) {
+      const EnvItem it = p.items[idx];
+      cx.it = it;
+      cx.P = p.probes[it.probe];
+      cx.V = p.vols[it.vol];
+      cx.pair = p.pairs[it.pair];
+      bool finite;
+      cx.M = load_pose(p.poses, it.b, finite);
+      cx.finite = finite;
+    }
+    __syncthreads();
+    const DevProbe& P = cx.P;
+    const int NL = P.nl, NS = P.ns, KA = P.k_ax, KL = P.k_lat;
+    const int RS = (NS + 2 * KA) | 1;             // padded row stride (odd: no bank conflicts across rows)
     const int LPC = (NL + CS - 1) / CS;
     const int lbeg = rank * LPC;
     const int n_own = max(0, min(NL - lbeg, LPC));
+    const int b = cx.it.b;
 
-    // (1) label slice
+    for (int t = tid; t < 2 * KA + 1; t += blockDim.x) wax[t] = __ldg(&P.w_ax[t]);
+    for (int t = tid; t < 2 * KL + 3; t += blockDim.x) wlat[t] = (t == 0 || t == 2 * KL + 2) ? 0.f : __ldg(&P.w_lat[t - 1]);
+    for (int t = tid; t < p.n_labels; t += blockDim.x) tis[t] = P.tissue[t];
+    for (int m = tid; m < NL; m += blockDim.x) {
+      const int r = m / LPC, row = m - r * LPC;
+      lab_row[m] = cl.map_shared_rank(lbuf, r) + row * NS;
+      s_row[m] = cl.map_shared_rank(sbuf, r) + row * RS + KA;
+      y_row[m] = cl.map_shared_rank(ybuf, r) + row * RS;
+    }
+    if (!cx.finite && rank == 0 && tid == 0) atomicOr(p.err, kErrNonFinitePose);
+    __syncthreads();
+
+    // (1) slice: nearest label and impedance of every sample of own lines
     for (int lr = warp; lr < n_own; lr += NW) {
       const int l = lbeg + lr;
       const float2 ln = P.lines[l];
+      float* zrow = sbuf + lr * RS + KA;
+      uint8_t* lrow = lbuf + lr * NS;
       for (int s = lane; s < NS; s += 32) {
         float x, z;
         beam_point(P, ln, s, x, z);
-        const int vi = nearest_voxel(V, to_voxel(M, V.inv_h, x, z));
-        const uint8_t lb = vi >= 0 ? __ldg(&V.labels[vi]) : (uint8_t)0;
-        lbuf[lr * NS + s] = lb;
-        if (p.nn_index) p.nn_index[it.beam_off + (long long)l * NS + s] = vi;
-        if (p.label) p.label[it.beam_off + (long long)l * NS + s] = lb;
+        const float3 u = to_voxel(cx.M, cx.V.inv_h, x, z);
+        const int vi = nearest_voxel(cx.V, u);
+        const uint8_t lb = vi >= 0 ? __ldg(&cx.V.labels[vi]) : (uint8_t)0;
+        lrow[s] = lb;
+        zrow[s] = p.z_mode == 0 ? fmaxf(trilinear_hu(cx.V, u) + 1024.f, 1.f) : tis[lb].z;
+        if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + s] = vi;
+        if (p.label) p.label[cx.it.beam_off + (long long)l * NS + s] = lb;
+      }
+      for (int q = lane; q < KA; q += 32) {
+        sbuf[lr * RS + q] = 0.f;
+        sbuf[lr * RS + KA + NS + q] = 0.f;
       }
     }
     cl.sync();
 
-    // (2) scanline model and axial PSF
-    auto labf = [&](int line, int s) -> unsigned {
-      const int r = line / LPC;
-      const int row = line - r * LPC;
-      const uint8_t* base = r == rank ? lbuf : cl.map_shared_rank(lbuf, r);
-      return base[row * NS + s];
-    };
-    for (int lr = warp; lr < n_own; lr += NW) {
-      float* row = sbuf + lr * NSP;
-      scanline_model(p, P, V, pair, M, it.b, lbeg + lr, lane, labf, [&](int s, float v) { row[s] = v; });
-      __syncwarp();
-      axial_psf_inplace(row, NS, P.w_ax, P.k_ax, lane);
-    }
-    cl.sync();
-
-    // (3) lateral PSF and log compression
+    // (2) scanline model, then the axial PSF in place
     for (int lr = warp; lr < n_own; lr += NW) {
       const int l = lbeg + lr;
-      const int lo = max(l - P.k_lat, 0), hi = min(l + P.k_lat, NL - 1);
-      const float* wl = P.w_lat + (P.k_lat - l);
-      for (int s = lane; s < NS; s += 32) {
-        int r = lo / LPC, row = lo - r * LPC;
-        const float* base = r == rank ? sbuf : cl.map_shared_rank(sbuf, r);
-        float acc = 0.f;
-        for (int ll = lo; ll <= hi; ++ll) {
-          acc = fmaf(__ldg(&wl[ll]), base[row * NSP + s], acc);
-          if (++row == LPC && ll < hi) {
-            row = 0;
-            ++r;
-            base = r == rank ? sbuf : cl.map_shared_rank(sbuf, r);
-          }
-        }
-        const float y = log_compress(P, acc);
-        ybuf[lr * NSP + s] = y;
-        if (p.envelope) p.envelope[it.beam_off + (long long)l * NS + s] = acc;
-        if (p.logimg) p.logimg[it.beam_off + (long long)l * NS + s] = y;
-      }
+      float* row = sbuf + lr * RS + KA;
+      const uint8_t* lrow = lbuf + lr * NS;
+      auto labf = [&](int line, int s) -> unsigned { return lab_row[line][s]; };
+      auto own = [&](int s) -> unsigned { return lrow[s]; };
+      auto zf = [&](int s) -> float { return row[s]; };
+      scanline_model(p, P, tis, cx.pair, b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; });
+      __syncwarp();
+      axial_psf_padded(sbuf + lr * RS, NS, wax, KA, lane);
     }
-    if (rank == 0 && threadIdx.x == 0) slot[parity ^ 1] = (int)atomicAdd(p.work, 1u);
     cl.sync();
 
-    // (4) output
-    float* out = p.frames + it.frame_off;
+    // (3) lateral PSF (two lines per thread) and log compression
+    {
+      const int nblk = (n_own + 1) >> 1, nch = (NS + 31) >> 5;
+      for (int u = warp; u < nblk * nch; u += NW) {
+        const int blk = u / nch, ch = u - blk * nch;
+        const int s = ch * 32 + lane;
+        if (s >= NS) continue;
+        const int lr0 = 2 * blk, l0 = lbeg + lr0;
+        const int mlo = max(l0 - KL, 0), mhi = min(l0 + 1 + KL, NL - 1);
+        float acc0 = 0.f, acc1 = 0.f;
+        for (int m = mlo; m <= mhi; ++m) {
+          const float v = s_row[m][s];
+          const int q = m - l0 + KL + 1;
+          acc0 = fmaf(wlat[q], v, acc0);
+          acc1 = fmaf(wlat[q - 1], v, acc1);
+        }
+        const float y0 = log_compress(P, acc0);
+        ybuf[lr0 * RS + s] = y0;
+        if (p.envelope) p.envelope[cx.it.beam_off + (long long)l0 * NS + s] = acc0;
+        if (p.logimg) p.logimg[cx.it.beam_off + (long long)l0 * NS + s] = y0;
+        if (lr0 + 1 < n_own) {
+          const float y1 = log_compress(P, acc1);
+          ybuf[(lr0 + 1) * RS + s] = y1;
+          if (p.envelope) p.envelope[cx.it.beam_off + (long long)(l0 + 1) * NS + s] = acc1;
+          if (p.logimg) p.logimg[cx.it.beam_off + (long long)(l0 + 1) * NS + s] = y1;
+        }
+      }
+    }
+    if (rank == 0 && tid == 0) slot[parity ^ 1] = (int)atomicAdd(p.work, 1u);
+    cl.sync();
+
+    // (4) output: scan conversion (curvilinear) or transposed store (linear)
+    float* out = p.frames + cx.it.frame_off;
     if (P.kind == 0) {
       for (int s = warp; s < NS; s += NW)
-        for (int lr = lane; lr < n_own; lr += 32) __stcs(&out[(long long)s * NL + lbeg + lr], ybuf[lr * NSP + s]);
+        for (int lr = lane; lr < n_own; lr += 32) __stcs(&out[(long long)s * NL + lbeg + lr], ybuf[lr * RS + s]);
     } else {
       const int W = P.out_w, H = P.out_h;
       auto fan_pixel = [&](float fl, float fs) -> float {
         if (fl < 0.f) return 0.f;
         const int la = min((int)fl, NL - 2), sa = min((int)fs, NS - 2);
         const float a = fl - (float)la, bb = fs - (float)sa;
-        const int r0 = la / LPC, row0 = la - r0 * LPC;
-        int r1 = r0, row1 = row0 + 1;
-        if (row1 == LPC) {
-          row1 = 0;
-          ++r1;
-        }
-        const float* b0 = r0 == rank ? ybuf : cl.map_shared_rank(ybuf, r0);
-        const float* b1 = r1 == rank ? ybuf : cl.map_shared_rank(ybuf, r1);
-        const float y00 = b0[row0 * NSP + sa], y01 = b0[row0 * NSP + sa + 1];
-        const float y10 = b1[row1 * NSP + sa], y11 = b1[row1 * NSP + sa + 1];
+        const float* r0 = y_row[la];
+        const float* r1 = y_row[la + 1];
+        const float y00 = r0[sa], y01 = r0[sa + 1];
+        const float y10 = r1[sa], y11 = r1[sa + 1];
         const float top = fmaf(a, y10 - y00, y00), bot = fmaf(a, y11 - y01, y01);
         return fmaf(bb, bot - top, top);
       };
@@ -161,7 +206,7 @@ __global__ void __launch_bounds__(NW * 32, 1) fused_render(RenderParams p, int s
       if ((W & 3) == 0) {
         const int n4 = W >> 2;
         const int total = nrows * n4;
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        for (int t = tid; t < total; t += blockDim.x) {
           const int ri = t / n4, c4 = t - ri * n4;
           const long long pix = (long long)(rank + ri * CS) * W + 4 * c4;
           const float4* lut4 = reinterpret_cast<const float4*>(P.lut + pix);
@@ -175,7 +220,7 @@ __global__ void __launch_bounds__(NW * 32, 1) fused_render(RenderParams p, int s
         }
       } else {
         const int total = nrows * W;
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        for (int t = tid; t < total; t += blockDim.x) {
           const int ri = t / W, c = t - ri * W;
           const long long pix = (long long)(rank + ri * CS) * W + c;
           const float2 f = __ldg(&P.lut[pix]);
@@ -189,18 +234,38 @@ __global__ void __launch_bounds__(NW * 32, 1) fused_render(RenderParams p, int s
   cl.sync();  // no CTA may leave while another can still read its shared memory
 }
 
-bool fused_shape_fits(FusedShape& s, const std::vector<ProbeHost>& probes) {
-  int sbuf = 0, lab = 0;
+bool fused_shape_fits(FusedShape& s, const std::vector<ProbeHost>& probes, int n_labels) {
+  long long sbuf = 0, lab = 0, max_nl = 0;
   for (const ProbeHost& ph : probes) {
     const int NL = ph.desc.n_lines, NS = ph.desc.n_samples;
     const int lpc = (NL + s.cs - 1) / s.cs;
-    sbuf = std::max(sbuf, lpc * (NS | 1));
-    lab = std::max(lab, lpc * NS);
+    const int rs = (NS + 2 * ph.k_ax) | 1;
+    sbuf = std::max(sbuf, (long long)lpc * rs);
+    lab = std::max(lab, (long long)lpc * NS);
+    max_nl = std::max(max_nl, (long long)NL);
   }
-  sbuf = (sbuf + 3) & ~3;
-  s.sbuf_floats = sbuf;
-  s.smem = (size_t)sbuf * 8 + (size_t)((lab + 15) & ~15);
-  return s.smem <= 227 * 1024;
+  auto up = [](long long x, long long a) { return (x + a - 1) / a * a; };
+  sbuf = up(sbuf, 4);
+  s.sbuf_floats = (int)sbuf;
+  long long off = sbuf * 4;
+  s.lay.off_y = (int)off;
+  off += sbuf * 4;
+  s.lay.off_lab = (int)off;
+  off = up(off + lab, 16);
+  s.lay.off_lrow = (int)off;
+  off += max_nl * 8;
+  s.lay.off_srow = (int)off;
+  off += max_nl * 8;
+  s.lay.off_yrow = (int)off;
+  off += max_nl * 8;
+  s.lay.off_wax = (int)off;
+  off = up(off + 4 * (2 * 32 + 1), 16);
+  s.lay.off_wlat = (int)off;
+  off = up(off + 4 * (2 * kMaxHalfTaps + 3), 16);
+  s.lay.off_tis = (int)off;
+  off = up(off + (long long)sizeof(DevTissue) * n_labels, 16);
+  s.smem = (size_t)off;
+  return s.smem <= 227 * 1024 - 1024;   // static shared memory (item context) takes the rest
 }
 
 template <int NW>
@@ -251,7 +316,7 @@ static cudaError_t launch_nw(const RenderParams& p, const FusedShape& s, cudaStr
   const int clusters = std::max(1, std::min(s.clusters, p.n_items));
   cfg.gridDim = dim3(clusters * s.cs);
   cfg.stream = st;
-  return cudaLaunchKernelEx(&cfg, fused_render<NW>, p, s.sbuf_floats);
+  return cudaLaunchKernelEx(&cfg, fused_render<NW>, p, s.lay);
 }
 
 cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st) {

@@ -38,9 +38,12 @@ __global__ void plain_lines(RenderParams p, EnvItem it, const uint8_t* lab, floa
   bool finite;
   const Pose M = load_pose(p.poses, it.b, finite);
   const int NS = P.ns;
+  const float2 ln = P.lines[l];
   auto labf = [&](int line, int s) -> unsigned { return lab[line * NS + s]; };
+  auto own = [&](int s) -> unsigned { return lab[l * NS + s]; };
+  auto zf = [&](int s) -> float { return sample_impedance(p.z_mode, P, V, M, ln, s, P.tissue, lab[l * NS + s]); };
   float* row = S + (size_t)l * NS;
-  scanline_model(p, P, V, pair, M, it.b, l, lane, labf, [&](int s, float v) { row[s] = v; });
+  scanline_model(p, P, P.tissue, pair, it.b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; });
 }
 
 __global__ void plain_psf_axial(RenderParams p, EnvItem it, const float* S, float* A) {

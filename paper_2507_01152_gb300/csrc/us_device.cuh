@@ -59,6 +59,7 @@ struct RenderParams {
   const DevPair* pairs;
   const EnvItem* items;
   int n_items;
+  int n_labels;
   const float* poses;        // [B][12]
   uint2 key;                 // Philox key for this (seed, step)
   int refl_power, transmission, z_mode, speckle;
@@ -138,17 +139,36 @@ __device__ __forceinline__ float hu_at(const DevVolume& V, int i, int j, int k) 
              : 0.f;
 }
 
-// trilinear HU; corners outside the grid read 0 (water)
+// trilinear HU; corners outside the grid read 0 (water).  Interior
+// footprints (the common case) skip the per-corner bounds checks.
 __device__ __forceinline__ float trilinear_hu(const DevVolume& V, float3 u) {
   const float fx = floorf(u.x), fy = floorf(u.y), fz = floorf(u.z);
   if (!(fx >= -1.f && fx < (float)V.nx && fy >= -1.f && fy < (float)V.ny && fz >= -1.f && fz < (float)V.nz))
     return 0.f;
   const int i = (int)fx, j = (int)fy, k = (int)fz;
   const float tx = u.x - fx, ty = u.y - fy, tz = u.z - fz;
-  const float c000 = hu_at(V, i, j, k), c100 = hu_at(V, i + 1, j, k);
-  const float c010 = hu_at(V, i, j + 1, k), c110 = hu_at(V, i + 1, j + 1, k);
-  const float c001 = hu_at(V, i, j, k + 1), c101 = hu_at(V, i + 1, j, k + 1);
-  const float c011 = hu_at(V, i, j + 1, k + 1), c111 = hu_at(V, i + 1, j + 1, k + 1);
+  float c000, c100, c010, c110, c001, c101, c011, c111;
+  if ((unsigned)i < (unsigned)(V.nx - 1) && (unsigned)j < (unsigned)(V.ny - 1) && (unsigned)k < (unsigned)(V.nz - 1)) {
+    const int sy = V.nx, sz = V.nx * V.ny;
+    const int16_t* b = V.hu + (k * V.ny + j) * V.nx + i;
+    c000 = (float)__ldg(b);
+    c100 = (float)__ldg(b + 1);
+    c010 = (float)__ldg(b + sy);
+    c110 = (float)__ldg(b + sy + 1);
+    c001 = (float)__ldg(b + sz);
+    c101 = (float)__ldg(b + sz + 1);
+    c011 = (float)__ldg(b + sz + sy);
+    c111 = (float)__ldg(b + sz + sy + 1);
+  } else {
+    c000 = hu_at(V, i, j, k);
+    c100 = hu_at(V, i + 1, j, k);
+    c010 = hu_at(V, i, j + 1, k);
+    c110 = hu_at(V, i + 1, j + 1, k);
+    c001 = hu_at(V, i, j, k + 1);
+    c101 = hu_at(V, i + 1, j, k + 1);
+    c011 = hu_at(V, i, j + 1, k + 1);
+    c111 = hu_at(V, i + 1, j + 1, k + 1);
+  }
   const float a00 = fmaf(tx, c100 - c000, c000), a10 = fmaf(tx, c110 - c010, c010);
   const float a01 = fmaf(tx, c101 - c001, c001), a11 = fmaf(tx, c111 - c011, c011);
   const float b0 = fmaf(ty, a10 - a00, a00), b1 = fmaf(ty, a11 - a01, a01);

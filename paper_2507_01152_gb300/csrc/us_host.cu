@@ -241,6 +241,7 @@ RenderParams base_params(const us_sim* s, const float* poses, uint64_t seed, uin
   p.transmission = s->opt.transmission;
   p.z_mode = s->opt.z_mode;
   p.speckle = s->opt.speckle;
+  p.n_labels = s->n_labels;
   p.frames = frames;
   p.err = s->d_err;
   p.work = s->d_work;
@@ -316,7 +317,7 @@ us_status apply_tuning(us_sim* s, const us_tuning& t) {
   FusedShape sh;
   sh.cs = cs;
   sh.nw = nw;
-  if (!fused_shape_fits(sh, s->probes))
+  if (!fused_shape_fits(sh, s->probes, s->n_labels))
     return fail(s, US_ERR_UNSUPPORTED, "probe lines per CTA do not fit in shared memory for this cluster size");
   int clusters = 0;
   cudaError_t e = fused_max_clusters(sh, &clusters);

@@ -38,17 +38,22 @@ cudaError_t launch_plain(const RenderParams& p, const EnvItem* items_host, int n
 cudaError_t launch_plain_env(const RenderParams& p, const EnvItem& it, const ProbeHost& ph,
                              const PlainScratch& scr, cudaStream_t st);
 
-// launch shape of the fused kernel
+// launch shape of the fused kernel and its dynamic shared-memory layout
+struct FusedLayout {
+  int off_y, off_lab, off_lrow, off_srow, off_yrow, off_wax, off_wlat, off_tis;  // byte offsets
+};
+
 struct FusedShape {
   int cs = 8;            // CTAs per cluster (one cluster renders one frame)
   int nw = 32;           // warps per CTA
-  int sbuf_floats = 0;   // floats per CTA buffer (max over probes of lines-per-CTA * padded NS)
+  int sbuf_floats = 0;   // floats per CTA row buffer (max over probes of lines-per-CTA * row stride)
+  FusedLayout lay{};
   size_t smem = 0;       // dynamic shared memory per CTA
   int clusters = 0;      // persistent grid, in clusters
 };
 
 // fills sbuf_floats / smem for the probe set; false if it cannot fit
-bool fused_shape_fits(FusedShape& s, const std::vector<ProbeHost>& probes);
+bool fused_shape_fits(FusedShape& s, const std::vector<ProbeHost>& probes, int n_labels);
 // occupancy-derived persistent grid (clusters resident at once)
 cudaError_t fused_max_clusters(const FusedShape& s, int* clusters);
 cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st);

@@ -22,27 +22,20 @@ __device__ __forceinline__ float warp_inclusive_scan(float v, int lane) {
 // per lane serves both samples (counter = (s >> 1, l, b, 0)).  The energy
 // exponent is an exclusive prefix sum along the line: per-lane pair sums,
 // a warp inclusive scan, and a carry across chunks.
+//   T             -> tissue constants of this probe, indexed by label
 //   lab(line, s)  -> nearest label of a beam sample (any line of the env)
+//   own(s)        -> nearest label of sample s on line l
+//   z_at(s)       -> impedance at sample s < NS of line l
 //   store(s, v)   -> receives S at sample s
-template <class LabFn, class StoreFn>
-__device__ __forceinline__ void scanline_model(const RenderParams& p, const DevProbe& P,
-                                               const DevVolume& V, const DevPair& pair,
-                                               const Pose& M, int b, int l, int lane, LabFn lab,
-                                               StoreFn store) {
+// A lane reads z_at only at its own samples (one chunk ahead) and gets the
+// next lane's value by shuffle, so store() may overwrite the storage z_at
+// reads from.
+template <class LabFn, class OwnFn, class ZFn, class StoreFn>
+__device__ __forceinline__ void scanline_model(const RenderParams& p, const DevProbe& P, const DevTissue* T,
+                                               const DevPair& pair, int b, int l, int lane, LabFn lab,
+                                               OwnFn own, ZFn z_at_in, StoreFn store) {
   const int NS = P.ns, NL = P.nl;
-  const float2 ln = P.lines[l];
-  const DevTissue* T = P.tissue;
-  const bool hu_mode = p.z_mode == 0;
-
-  auto z_at = [&](int s) -> float {
-    if (s >= NS) return 1.f;
-    if (hu_mode) {
-      float x, z;
-      beam_point(P, ln, s, x, z);
-      return fmaxf(trilinear_hu(V, to_voxel(M, V.inv_h, x, z)) + 1024.f, 1.f);
-    }
-    return __ldg(&T[lab(l, s)].z);
-  };
+  auto z_at = [&](int s) -> float { return s < NS ? z_at_in(s) : 1.f; };
 
   float z0 = z_at(2 * lane), z1 = z_at(2 * lane + 1);
   float carry = 0.f;
@@ -55,9 +48,9 @@ __device__ __forceinline__ void scanline_model(const RenderParams& p, const DevP
     const float zc_next = __shfl_sync(kFull, nz0, 0);
     if (lane == 31) zc = zc_next;
 
-    const unsigned la = sa < NS ? lab(l, sa) : 0u;
-    const unsigned lb = sb < NS ? lab(l, sb) : 0u;
-    const unsigned lc = sb + 1 < NS ? lab(l, sb + 1) : lb;
+    const unsigned la = sa < NS ? own(sa) : 0u;
+    const unsigned lb = sb < NS ? own(sb) : 0u;
+    const unsigned lc = sb + 1 < NS ? own(sb + 1) : lb;
     const bool Ga = sa < NS - 1 && lb != la;
     const bool Gb = sb < NS - 1 && lc != lb;
     const float ra = sa < NS - 1 ? (z1 - z0) / (z1 + z0) : 0.f;
@@ -108,6 +101,18 @@ __device__ __forceinline__ void scanline_model(const RenderParams& p, const DevP
     z0 = nz0;
     z1 = nz1;
   }
+}
+
+// impedance of a beam sample: Z = max(HU + 1024, 1) from the trilinear HU
+// (z_mode 0) or the tissue table (z_mode 1)
+__device__ __forceinline__ float sample_impedance(int z_mode, const DevProbe& P, const DevVolume& V, const Pose& M,
+                                                  float2 ln, int s, const DevTissue* T, unsigned label) {
+  if (z_mode == 0) {
+    float x, z;
+    beam_point(P, ln, s, x, z);
+    return fmaxf(trilinear_hu(V, to_voxel(M, V.inv_h, x, z)) + 1024.f, 1.f);
+  }
+  return T[label].z;
 }
 
 }  // namespace ussim
