@@ -124,10 +124,11 @@ typedef struct {
 
 /* Launch shape of the fused batched render. */
 typedef struct {
-  int32_t cluster_size;  /* CTAs per environment frame: 2, 4, 8 or 16 */
-  int32_t warps_per_cta; /* 4, 8, 16 or 32 */
-  int32_t ctas_per_sm;   /* residency target used to size the persistent grid (1..4) */
-  int32_t use_graph;     /* 1: replay a captured CUDA graph per (envs, B) */
+  int32_t cluster_size;  /* CTAs per environment frame: 4, 8 or 16 */
+  int32_t warps_per_cta; /* 8, 16 or 32 (4 / 8 / 16 clusters: 16-32 / 8-32 / 8-32) */
+  int32_t use_graph;     /* 1: replay a captured CUDA graph per batch signature
+                            (not on the legacy NULL stream, nor while the
+                            caller's stream is itself being captured) */
 } us_tuning;
 
 /* Create a simulator.  Copies the descriptors, builds the derived tables

@@ -58,14 +58,13 @@ __device__ __forceinline__ void axial_psf_padded(float* prow, int NS, const floa
   __syncwarp();
 }
 
-template <int NW>
-__global__ void __launch_bounds__(NW * 32, 1) fused_render(RenderParams p, FusedLayout L) {
+template <int CS, int NW>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_render(RenderParams p, FusedLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ItemCtx cx;
   __shared__ int slot[2];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const int CS = (int)cl.num_blocks();
   float* sbuf = reinterpret_cast<float*>(smem);                   // impedance, then S, then axially filtered S
   float* ybuf = reinterpret_cast<float*>(smem + L.off_y);         // log image of own lines
   uint8_t* lbuf = smem + L.off_lab;                               // labels of own lines
@@ -268,65 +267,48 @@ bool fused_shape_fits(FusedShape& s, const std::vector<ProbeHost>& probes, int n
   return s.smem <= 227 * 1024 - 1024;   // static shared memory (item context) takes the rest
 }
 
-template <int NW>
-static cudaError_t prepare(const FusedShape& s, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr) {
-  cudaError_t e = cudaFuncSetAttribute(fused_render<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
-  if (e != cudaSuccess) return e;
-  if (s.cs > 8) {
-    e = cudaFuncSetAttribute(fused_render<NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
-  cfg.blockDim = dim3(NW * 32);
-  cfg.dynamicSmemBytes = s.smem;
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = s.cs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaSuccess;
+// (cluster size, warps per CTA) instantiations; the cluster size is part of
+// the kernel (__cluster_dims__), so every launch of a given instantiation,
+// including a re-parameterised graph node, runs in clusters of that size
+#define US_FUSED_SHAPES(X) X(4, 16) X(4, 32) X(8, 8) X(8, 16) X(8, 32) X(16, 8) X(16, 16) X(16, 32)
+
+static const void* fused_fn(int cs, int nw) {
+#define US_PICK(C, N) \
+  if (cs == C && nw == N) return reinterpret_cast<const void*>(&fused_render<C, N>);
+  US_FUSED_SHAPES(US_PICK)
+#undef US_PICK
+  return nullptr;
 }
 
-template <int NW>
-static cudaError_t max_clusters_nw(const FusedShape& s, int* clusters) {
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cudaError_t e = prepare<NW>(s, cfg, attr);
+bool fused_shape_known(int cs, int nw) { return fused_fn(cs, nw) != nullptr; }
+
+cudaError_t fused_prepare(const FusedShape& s) {
+  const void* fn = fused_fn(s.cs, s.nw);
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
   if (e != cudaSuccess) return e;
-  cfg.gridDim = dim3(s.cs * 1024);
-  return cudaOccupancyMaxActiveClusters(clusters, fused_render<NW>, &cfg);
+  if (s.cs > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
 }
 
 cudaError_t fused_max_clusters(const FusedShape& s, int* clusters) {
-  switch (s.nw) {
-    case 4: return max_clusters_nw<4>(s, clusters);
-    case 8: return max_clusters_nw<8>(s, clusters);
-    case 16: return max_clusters_nw<16>(s, clusters);
-    case 32: return max_clusters_nw<32>(s, clusters);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <int NW>
-static cudaError_t launch_nw(const RenderParams& p, const FusedShape& s, cudaStream_t st) {
+  const void* fn = fused_fn(s.cs, s.nw);
+  if (!fn) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cudaError_t e = prepare<NW>(s, cfg, attr);
-  if (e != cudaSuccess) return e;
-  const int clusters = std::max(1, std::min(s.clusters, p.n_items));
-  cfg.gridDim = dim3(clusters * s.cs);
-  cfg.stream = st;
-  return cudaLaunchKernelEx(&cfg, fused_render<NW>, p, s.lay);
+  cfg.gridDim = dim3(s.cs * 1024);
+  cfg.blockDim = dim3(s.nw * 32);
+  cfg.dynamicSmemBytes = s.smem;
+  return cudaOccupancyMaxActiveClusters(clusters, fn, &cfg);
 }
 
 cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st) {
-  switch (s.nw) {
-    case 4: return launch_nw<4>(p, s, st);
-    case 8: return launch_nw<8>(p, s, st);
-    case 16: return launch_nw<16>(p, s, st);
-    case 32: return launch_nw<32>(p, s, st);
-    default: return cudaErrorInvalidValue;
-  }
+  const void* fn = fused_fn(s.cs, s.nw);
+  if (!fn) return cudaErrorInvalidValue;
+  const int clusters = std::max(1, std::min(s.clusters, p.n_items));
+  RenderParams pp = p;
+  FusedLayout lay = s.lay;
+  void* args[2] = {&pp, &lay};
+  return cudaLaunchKernel(fn, dim3(clusters * s.cs), dim3(s.nw * 32), args, s.smem, st);
 }
 
 // ---------------------------------------------------------------- checks

@@ -17,6 +17,9 @@ namespace {
 constexpr int kMaxAxialHalf = 32;   // in-place axial filter in the fused kernel
 constexpr int kMaxLines = 1024, kMaxSamples = 1024;
 
+us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream_t st);
+void drop_graph(us_plan& pl);
+
 us_status fail(us_sim* s, us_status st, const std::string& msg) {
   if (s) s->last_error = msg;
   return st;
@@ -273,6 +276,9 @@ us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, ui
   if (path == 0) {
     p.items = pl->d_items;
     p.n_items = B;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (st && cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
+    if (s->tuning.use_graph && st && cap == cudaStreamCaptureStatusNone) return graph_launch(s, pl, p, st);
     if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(s, e, "reset work counter");
     if ((e = launch_fused(p, s->shape, st)) != cudaSuccess) return cuda_fail(s, e, "fused render launch");
   } else {
@@ -294,7 +300,10 @@ void free_sim(us_sim* s) {
     cudaFree(ph.d_tissue);
   }
   for (auto* d : s->d_pair_D) cudaFree(d);
-  for (auto& kv : s->plans) cudaFree(kv.second.d_items);
+  for (auto& kv : s->plans) {
+    drop_graph(kv.second);
+    cudaFree(kv.second.d_items);
+  }
   cudaFree(s->d_vols);
   cudaFree(s->d_probes);
   cudaFree(s->d_pairs);
@@ -311,22 +320,86 @@ void free_sim(us_sim* s) {
 
 us_status apply_tuning(us_sim* s, const us_tuning& t) {
   const int cs = t.cluster_size, nw = t.warps_per_cta;
-  if (!(cs == 2 || cs == 4 || cs == 8 || cs == 16)) return fail(s, US_ERR_INVALID_ARG, "cluster_size must be 2, 4, 8 or 16");
-  if (!(nw == 4 || nw == 8 || nw == 16 || nw == 32)) return fail(s, US_ERR_INVALID_ARG, "warps_per_cta must be 4, 8, 16 or 32");
-  if (t.ctas_per_sm < 1 || t.ctas_per_sm > 4) return fail(s, US_ERR_INVALID_ARG, "ctas_per_sm must be in [1, 4]");
+  if (!fused_shape_known(cs, nw)) return fail(s, US_ERR_INVALID_ARG, "unsupported (cluster_size, warps_per_cta)");
+  if (t.use_graph & ~1) return fail(s, US_ERR_INVALID_ARG, "use_graph must be 0 or 1");
   FusedShape sh;
   sh.cs = cs;
   sh.nw = nw;
   if (!fused_shape_fits(sh, s->probes, s->n_labels))
     return fail(s, US_ERR_UNSUPPORTED, "probe lines per CTA do not fit in shared memory for this cluster size");
+  cudaError_t e = fused_prepare(sh);
+  if (e != cudaSuccess) return cuda_fail(s, e, "kernel attributes");
   int clusters = 0;
-  cudaError_t e = fused_max_clusters(sh, &clusters);
+  e = fused_max_clusters(sh, &clusters);
   if (e != cudaSuccess) return cuda_fail(s, e, "occupancy query");
   if (clusters < 1) return fail(s, US_ERR_UNSUPPORTED, "no cluster of this shape fits on the device");
   sh.clusters = clusters;
   s->shape = sh;
   s->tuning = t;
   return US_OK;
+}
+
+void drop_graph(us_plan& pl) {
+  if (pl.gexec) cudaGraphExecDestroy(pl.gexec);
+  if (pl.graph) cudaGraphDestroy(pl.graph);
+  pl.gexec = nullptr;
+  pl.graph = nullptr;
+  pl.gnode = nullptr;
+  pl.g_cs = pl.g_nw = 0;
+}
+
+// Capture [work-counter reset + fused launch] once per batch signature and
+// launch shape; later calls only swap the kernel node's arguments.
+us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream_t st) {
+  cudaError_t e;
+  if (!pl->gexec || pl->g_cs != s->shape.cs || pl->g_nw != s->shape.nw) {
+    drop_graph(*pl);
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(s, e, "graph capture");
+    cudaError_t e1 = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
+    cudaError_t e2 = launch_fused(p, s->shape, st);
+    e = cudaStreamEndCapture(st, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(s, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e), "graph capture");
+    }
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) cudaGraphGetNodes(g, nodes.data(), &n);
+    cudaGraphNode_t kn = nullptr;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) kn = nd;
+    }
+    if (!kn || (e = cudaGraphKernelNodeGetParams(kn, &pl->gkp)) != cudaSuccess ||
+        (e = cudaGraphInstantiate(&pl->gexec, g, 0)) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      pl->gexec = nullptr;
+      return cuda_fail(s, kn ? e : cudaErrorUnknown, "graph instantiate");
+    }
+    pl->graph = g;
+    pl->gnode = kn;
+    pl->g_cs = s->shape.cs;
+    pl->g_nw = s->shape.nw;
+    if ((e = cudaGraphLaunch(pl->gexec, st)) != cudaSuccess) return cuda_fail(s, e, "graph launch");
+    return US_OK;
+  }
+  RenderParams pp = p;
+  FusedLayout lay = s->shape.lay;
+  void* args[2] = {&pp, &lay};
+  cudaKernelNodeParams kp = pl->gkp;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  if ((e = cudaGraphExecKernelNodeSetParams(pl->gexec, pl->gnode, &kp)) != cudaSuccess) return cuda_fail(s, e, "graph update");
+  if ((e = cudaGraphLaunch(pl->gexec, st)) != cudaSuccess) return cuda_fail(s, e, "graph launch");
+  return US_OK;
+}
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* b = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
 }
 
 }  // namespace
@@ -448,7 +521,7 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
   }
   if ((r = apply_tuning(s, s->tuning)) != US_OK) {
     // fall back to the smallest footprint that fits
-    us_tuning t{16, 16, 1, 0};
+    us_tuning t{16, 16, 1};
     if ((r = apply_tuning(s, t)) != US_OK) {
       free_sim(s);
       return r;
@@ -568,8 +641,78 @@ us_status us_sim_set_tuning(us_sim* s, const us_tuning* t) {
 
 us_status us_sim_autotune(us_sim* s, const us_env* envs, int32_t B, const float* poses, float* frames,
                           const char* cache_path, void* stream) {
-  (void)envs; (void)B; (void)poses; (void)frames; (void)cache_path; (void)stream;
-  return fail(s, US_ERR_UNSUPPORTED, "autotune not built yet");
+  us_status r = check_render_args(s, envs, B, poses, frames);
+  if (r != US_OK) return r;
+  if (B == 0) return US_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  cudaDeviceProp prop;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess || (e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess)
+    return cuda_fail(s, e, "device query");
+  // signature: GPU, probe set, batch (env list)
+  uint64_t hp = 0;
+  for (const ProbeHost& ph : s->probes) hp = fnv1a(&ph.desc, sizeof ph.desc, hp ? hp : 1469598103934665603ull);
+  const uint64_t he = fnv1a(envs, sizeof(us_env) * (size_t)B);
+  char sig[512];
+  std::string gpu(prop.name);
+  for (char& c : gpu)
+    if (c == ' ') c = '_';
+  std::snprintf(sig, sizeof sig, "%s sm%d probes=%016llx envs=%016llx B=%d", gpu.c_str(), prop.multiProcessorCount,
+                (unsigned long long)hp, (unsigned long long)he, B);
+  const int keep_graph = s->tuning.use_graph;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[768];
+      int cs = 0, nw = 0;
+      bool found = false;
+      while (std::fgets(line, sizeof line, f)) {
+        const size_t n = std::strlen(sig);
+        if (std::strncmp(line, sig, n) == 0 && std::sscanf(line + n, " cs=%d nw=%d", &cs, &nw) == 2) found = true;
+      }
+      std::fclose(f);
+      if (found) {
+        us_tuning t{cs, nw, keep_graph};
+        if (apply_tuning(s, t) == US_OK) return US_OK;
+      }
+    }
+  }
+  static const int cand[][2] = {{8, 32}, {8, 16}, {8, 8}, {16, 32}, {16, 16}, {16, 8}, {4, 32}, {4, 16}};
+  float best = 1e30f;
+  int best_cs = 0, best_nw = 0;
+  cudaEvent_t a, b2;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b2)) != cudaSuccess) return cuda_fail(s, e, "events");
+  for (const auto& c : cand) {
+    us_tuning t{c[0], c[1], 0};
+    if (apply_tuning(s, t) != US_OK) continue;
+    bool ok = true;
+    for (int w = 0; w < 2 && ok; ++w)
+      ok = do_render(s, envs, B, poses, 0x5EEDull, (uint64_t)w, frames, nullptr, nullptr, nullptr, nullptr, 0, st) == US_OK;
+    cudaEventRecord(a, st);
+    for (int k = 0; k < 5 && ok; ++k)
+      ok = do_render(s, envs, B, poses, 0x5EEDull, (uint64_t)k, frames, nullptr, nullptr, nullptr, nullptr, 0, st) == US_OK;
+    cudaEventRecord(b2, st);
+    if (!ok || cudaEventSynchronize(b2) != cudaSuccess) continue;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b2);
+    if (ms < best) {
+      best = ms;
+      best_cs = c[0];
+      best_nw = c[1];
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b2);
+  if (!best_cs) return fail(s, US_ERR_UNSUPPORTED, "no launch shape fits this probe set");
+  us_tuning t{best_cs, best_nw, keep_graph};
+  if ((r = apply_tuning(s, t)) != US_OK) return r;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%s cs=%d nw=%d ms=%.4f\n", sig, best_cs, best_nw, best / 5.0f);
+      std::fclose(f);
+    }
+  }
+  return US_OK;
 }
 
 }  // extern "C"

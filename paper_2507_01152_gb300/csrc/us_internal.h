@@ -54,6 +54,10 @@ struct FusedShape {
 
 // fills sbuf_floats / smem for the probe set; false if it cannot fit
 bool fused_shape_fits(FusedShape& s, const std::vector<ProbeHost>& probes, int n_labels);
+// is (cs, nw) one of the compiled instantiations?
+bool fused_shape_known(int cs, int nw);
+// set the kernel's shared-memory / cluster attributes (outside any capture)
+cudaError_t fused_prepare(const FusedShape& s);
 // occupancy-derived persistent grid (clusters resident at once)
 cudaError_t fused_max_clusters(const FusedShape& s, int* clusters);
 cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st);
@@ -69,6 +73,12 @@ struct us_plan {
   std::vector<ussim::EnvItem> items_batch;   // caller order
   ussim::EnvItem* d_items = nullptr;         // device copy of items_sorted
   long long frame_floats = 0, beam_elems = 0;
+  // captured [work-counter reset + fused launch], re-parameterised per call
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphNode_t gnode = nullptr;
+  cudaKernelNodeParams gkp{};
+  int g_cs = 0, g_nw = 0;
 };
 
 struct us_sim {
@@ -88,7 +98,7 @@ struct us_sim {
   unsigned* d_work = nullptr;
 
   ussim::FusedShape shape;
-  us_tuning tuning{8, 32, 1, 0};
+  us_tuning tuning{8, 32, 1};
 
   std::map<std::string, us_plan> plans;
 

@@ -55,8 +55,7 @@ class us_env(C.Structure):
 
 
 class us_tuning(C.Structure):
-    _fields_ = [("cluster_size", C.c_int32), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("use_graph", C.c_int32)]
+    _fields_ = [("cluster_size", C.c_int32), ("warps_per_cta", C.c_int32), ("use_graph", C.c_int32)]
 
 
 # name -> (restype, argtypes) for every entry point of include/ussim.h
@@ -234,8 +233,10 @@ class Sim:
         self._check(self._lib.us_sim_get_tuning(self.h, C.byref(t)))
         return {k: getattr(t, k) for k, _ in us_tuning._fields_}
 
-    def set_tuning(self, cluster_size, warps_per_cta, ctas_per_sm=1, use_graph=0):
-        t = us_tuning(cluster_size, warps_per_cta, ctas_per_sm, use_graph)
+    def set_tuning(self, cluster_size, warps_per_cta, use_graph=None):
+        if use_graph is None:
+            use_graph = self.get_tuning()["use_graph"]
+        t = us_tuning(cluster_size, warps_per_cta, use_graph)
         self._check(self._lib.us_sim_set_tuning(self.h, C.byref(t)))
 
     def autotune(self, envs, poses, frames, cache_path=None, stream=None):

@@ -82,26 +82,73 @@ def test_deterministic_and_step_keyed(c2):
 
 
 def test_launch_shape_that_cannot_fit_is_rejected(c2):
-    from paper_2507_01152_gb300.ussim import UsError, US_ERR_UNSUPPORTED
+    from paper_2507_01152_gb300.ussim import UsError, US_ERR_UNSUPPORTED, US_ERR_INVALID_ARG
     wl, sim = c2
     with pytest.raises(UsError) as e:
-        sim.set_tuning(2, 32)          # 128 lines x 512 samples per CTA: too large
+        sim.set_tuning(4, 32)          # 64 lines x 512 samples per CTA: too large
     assert e.value.status == US_ERR_UNSUPPORTED
+    with pytest.raises(UsError) as e:
+        sim.set_tuning(2, 32)          # not a compiled shape
+    assert e.value.status == US_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("cs,nw", [(8, 8), (8, 16), (8, 32), (16, 4), (16, 16), (16, 32)])
+@pytest.mark.parametrize("cs,nw", [(8, 8), (8, 16), (8, 32), (16, 8), (16, 16), (16, 32)])
 def test_launch_shapes_agree(c2, cs, nw):
     wl, sim = c2
     envs, poses = wl.envs[:10], wl.poses[:10]
     ref = render_gpu(sim, envs, poses, 21, 0, path=1, debug=False)
     old = sim.get_tuning()
     try:
-        sim.set_tuning(cs, nw)
-        got = render_gpu(sim, envs, poses, 21, 0, path=0, debug=False)
+        for graph in (0, 1):
+            sim.set_tuning(cs, nw, graph)
+            got = render_gpu(sim, envs, poses, 21, 0, path=0, debug=False)
+            for x, y in zip(ref, got):
+                assert np.array_equal(x["frame"], y["frame"])
     finally:
-        sim.set_tuning(old["cluster_size"], old["warps_per_cta"])
+        sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
+
+
+def test_graph_replay_updates_arguments(c2):
+    """Replays of the captured graph take each call's poses, seed, step and
+    frame buffer; the result equals a direct launch every time."""
+    wl, sim = c2
+    envs = wl.envs[:8]
+    off = sim.frame_layout(envs)
+    st = torch.cuda.Stream()
+    outs = {}
+    for graph in (0, 1):
+        sim.set_tuning(8, 32, graph)
+        for k in range(4):
+            P = torch.from_numpy(wl.poses[8 * k:8 * k + 8]).cuda()
+            fr = torch.empty(int(off[-1]), device="cuda")
+            sim.render(envs, P, 100 + k, k, fr, stream=st)
+            st.synchronize()
+            outs[(graph, k)] = fr.cpu().numpy()
+    sim.set_tuning(8, 32, 1)
+    for k in range(4):
+        assert np.array_equal(outs[(0, k)], outs[(1, k)])
+    assert not np.array_equal(outs[(1, 0)], outs[(1, 1)])
+
+
+def test_autotune_picks_a_shape_and_caches_it(c2, tmp_path):
+    wl, sim = c2
+    envs, poses = wl.envs[:16], wl.poses[:16]
+    ref = render_gpu(sim, envs, poses, 5, 5, path=1, debug=False)
+    P = torch.from_numpy(poses).cuda()
+    off = sim.frame_layout(envs)
+    fr = torch.empty(int(off[-1]), device="cuda")
+    cache = tmp_path / "tune.txt"
+    sim.autotune(envs, P, fr, str(cache))
+    t1 = sim.get_tuning()
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and f"cs={t1['cluster_size']} nw={t1['warps_per_cta']}" in lines[0]
+    sim.set_tuning(16, 16)
+    sim.autotune(envs, P, fr, str(cache))          # read back from the cache, no new entry
+    assert sim.get_tuning() == t1 and len(cache.read_text().splitlines()) == 1
+    got = render_gpu(sim, envs, poses, 5, 5, path=0, debug=False)
     for x, y in zip(ref, got):
         assert np.array_equal(x["frame"], y["frame"])
+    sim.set_tuning(8, 32, 1)
 
 
 def _tiny_volume(seed, shape=(14, 16, 18)):
