@@ -78,6 +78,7 @@ SIGNATURES = {
     "us_sim_autotune": (C.c_int, [_P, _P, C.c_int32, _P, _P, C.c_char_p, _P]),
     "us_sim_last_error": (C.c_char_p, [_P]),
     "us_status_string": (C.c_char_p, [C.c_int]),
+    "us_gemm_bf16_nt": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P]),
 }
 
 _lib = None
@@ -119,6 +120,16 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def gemm_bf16_nt(A, B, C, err, stream=None):
+    """C = A B^T on the tcgen05 tile kernel (A [M][K], B [N][K] bf16; C fp32)."""
+    L = load()
+    M, K = A.shape
+    N = B.shape[0]
+    st = L.us_gemm_bf16_nt(_ptr(A), _ptr(B), _ptr(C), M, N, K, _ptr(err), _stream_handle(stream))
+    if st != US_OK:
+        raise UsError(st, "us_gemm_bf16_nt")
 
 
 def make_probe(p) -> us_probe:
