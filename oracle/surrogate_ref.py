@@ -1,0 +1,171 @@
+"""Oracle of the learned surrogate (O3): plain PyTorch CPU float64.
+
+TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU-baseline leg).
+
+The learning-based simulator of SonoGym (Sec. 4; App. B.2 "Learning-based
+approach") is a pix2pix U-Net from CT slices to ultrasound images, trained
+with an L1 term (weight 1).  The surrogate here is the same kind of
+network, an encoder-decoder with skip connections, mapping the label/HU
+slice on the output grid to the physics frame.  The paper's figure of the
+architecture is not in the text, so the layer list below is our reading:
+
+    levels l = 0..3 with c * 2^l channels (c = base channels)
+    encoder  level 0: conv3x3(8 -> c), conv3x3(c -> c)              -> e0
+             level l: conv3x3 stride 2 (c_{l-1} -> c_l), conv3x3 x2 -> e_l
+    decoder  level l = 2..0: convT2x2(c_{l+1} -> c_l), concat [up, e_l],
+             conv3x3(2 c_l -> c_l), conv3x3(c_l -> c_l)
+    head     1x1 conv (c -> 1), sigmoid
+    every conv and convT is followed by ReLU (the head by the sigmoid)
+
+Loss per frame (the pix2pix L1 term, plus the structural term that
+the benchmark spec asks for): L1 + (1 - SSIM), SSIM of Wang, Bovik, Sheikh,
+Simoncelli 2004 (11 x 11 Gaussian window, sigma 1.5, C1 = 0.01^2,
+C2 = 0.03^2, dynamic range 1, mean over the valid region).  Batch loss =
+mean over frames.  Optimiser: Adam (Kingma & Ba 2015).
+
+Tensor layouts follow the C ABI: activations NHWC; conv3x3 weights
+[Cout][3][3][Cin]; convT2x2 weights [(dy*2+dx)*Cout + co][Cin]; head
+weights [C]; the flat parameter vector lists, per layer in the order
+above, the weights then the bias.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+import torch.nn.functional as F
+
+DT = torch.float64
+IN_CH = 8          # input channels (2 used: label / 4, clamp(HU / 1000, -1, 3); 6 zero)
+SSIM_C1 = 0.01 ** 2
+SSIM_C2 = 0.03 ** 2
+
+
+def layer_specs(c: int, levels: int = 4):
+    """(name, kind, cin, cout, stride) in parameter order."""
+    ch = [c * (2 ** l) for l in range(levels)]
+    L = [("enc0a", "conv", IN_CH, ch[0], 1), ("enc0b", "conv", ch[0], ch[0], 1)]
+    for l in range(1, levels):
+        L += [(f"down{l}", "conv", ch[l - 1], ch[l], 2), (f"enc{l}a", "conv", ch[l], ch[l], 1),
+              (f"enc{l}b", "conv", ch[l], ch[l], 1)]
+    for l in range(levels - 2, -1, -1):
+        L += [(f"up{l}", "convT", ch[l + 1], ch[l], 2), (f"dec{l}a", "conv", 2 * ch[l], ch[l], 1),
+              (f"dec{l}b", "conv", ch[l], ch[l], 1)]
+    L += [("head", "head", ch[0], 1, 1)]
+    return L
+
+
+def param_shapes(c: int, levels: int = 4):
+    out = []
+    for name, kind, cin, cout, s in layer_specs(c, levels):
+        if kind == "conv":
+            out += [(name + ".w", (cout, 3, 3, cin)), (name + ".b", (cout,))]
+        elif kind == "convT":
+            out += [(name + ".w", (4 * cout, cin)), (name + ".b", (cout,))]
+        else:
+            out += [(name + ".w", (cin,)), (name + ".b", (1,))]
+    return out
+
+
+def n_params(c: int, levels: int = 4) -> int:
+    return sum(math.prod(s) for _, s in param_shapes(c, levels))
+
+
+def unflatten(flat, c: int, levels: int = 4):
+    flat = torch.as_tensor(flat, dtype=DT)
+    P, o = {}, 0
+    for name, shp in param_shapes(c, levels):
+        n = math.prod(shp)
+        P[name] = flat[o:o + n].reshape(shp)
+        o += n
+    assert o == flat.numel()
+    return P
+
+
+def conv3x3(x, w, b, stride, relu=True):
+    """x [B][H][W][Cin], w [Cout][3][3][Cin]; zero padding 1."""
+    y = F.conv2d(x.permute(0, 3, 1, 2), w.permute(0, 3, 1, 2), b, stride=stride, padding=1)
+    y = y.permute(0, 2, 3, 1)
+    return torch.relu(y) if relu else y
+
+
+def convT2x2(x, w4, b, relu=True):
+    """out[b, 2y+dy, 2x+dx, co] = sum_ci x[b, y, x, ci] w4[(2 dy + dx) Cout + co][ci] + bias[co]."""
+    cout = w4.shape[0] // 4
+    cin = w4.shape[1]
+    wt = w4.reshape(2, 2, cout, cin).permute(3, 2, 0, 1)      # [Cin][Cout][dy][dx]
+    y = F.conv_transpose2d(x.permute(0, 3, 1, 2), wt, b, stride=2).permute(0, 2, 3, 1)
+    return torch.relu(y) if relu else y
+
+
+def forward(P, x, c: int, levels: int = 4, keep=None):
+    """x [B][H][W][8] -> frame [B][H][W] in (0, 1)."""
+    h = conv3x3(x, P["enc0a.w"], P["enc0a.b"], 1)
+    skips = [conv3x3(h, P["enc0b.w"], P["enc0b.b"], 1)]
+    h = skips[0]
+    for l in range(1, levels):
+        h = conv3x3(h, P[f"down{l}.w"], P[f"down{l}.b"], 2)
+        h = conv3x3(h, P[f"enc{l}a.w"], P[f"enc{l}a.b"], 1)
+        h = conv3x3(h, P[f"enc{l}b.w"], P[f"enc{l}b.b"], 1)
+        skips.append(h)
+    h = skips[-1]
+    for l in range(levels - 2, -1, -1):
+        u = convT2x2(h, P[f"up{l}.w"], P[f"up{l}.b"])
+        h = torch.cat([u, skips[l]], dim=-1)
+        h = conv3x3(h, P[f"dec{l}a.w"], P[f"dec{l}a.b"], 1)
+        h = conv3x3(h, P[f"dec{l}b.w"], P[f"dec{l}b.b"], 1)
+        if keep is not None:
+            keep[f"dec{l}"] = h
+    z = (h * P["head.w"]).sum(-1) + P["head.b"]
+    if keep is not None:
+        keep["z"] = z
+    return torch.sigmoid(z)
+
+
+def gaussian_window(size=11, sigma=1.5):
+    k = torch.arange(size, dtype=DT) - (size - 1) / 2
+    g = torch.exp(-k * k / (2 * sigma * sigma))
+    g = g / g.sum()
+    return torch.outer(g, g)
+
+
+def ssim_map(x, y, size=11, sigma=1.5):
+    """x, y [B][H][W]; valid-region SSIM map [B][H-size+1][W-size+1]."""
+    w = gaussian_window(size, sigma)[None, None]
+    f = lambda t: F.conv2d(t[:, None], w)[:, 0]
+    mx, my = f(x), f(y)
+    sxx = f(x * x) - mx * mx
+    syy = f(y * y) - my * my
+    sxy = f(x * y) - mx * my
+    return ((2 * mx * my + SSIM_C1) * (2 * sxy + SSIM_C2)) / ((mx * mx + my * my + SSIM_C1) * (sxx + syy + SSIM_C2))
+
+
+def frame_losses(pred, target):
+    """per-frame (L1, SSIM)"""
+    l1 = (pred - target).abs().mean(dim=(1, 2))
+    ss = ssim_map(pred, target).mean(dim=(1, 2))
+    return l1, ss
+
+
+def loss(pred, target):
+    l1, ss = frame_losses(pred, target)
+    return (l1 + (1.0 - ss)).mean()
+
+
+def loss_and_grads(flat, x, target, c: int, levels: int = 4):
+    """(loss, d loss / d flat params) by reverse-mode differentiation."""
+    p = torch.as_tensor(flat, dtype=DT).clone().requires_grad_(True)
+    P = unflatten(p, c, levels)
+    out = forward(P, torch.as_tensor(x, dtype=DT), c, levels)
+    L = loss(out, torch.as_tensor(target, dtype=DT))
+    L.backward()
+    return float(L.detach()), p.grad.detach().clone(), out.detach()
+
+
+def adam_step(p, g, m, v, t, lr=2e-4, b1=0.9, b2=0.999, eps=1e-8):
+    """one Adam update (step count t >= 1); returns new (p, m, v)"""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return p - lr * mh / (torch.sqrt(vh) + eps), m, v

@@ -1,0 +1,133 @@
+"""Pins of the surrogate oracle (O3) against facts outside itself (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import surrogate_ref as S
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+@pytest.mark.parametrize("stride", [1, 2])
+def test_conv3x3_matches_direct_loops(stride):
+    r = _rng(stride)
+    B, H, W, Ci, Co = 2, 7, 6, 3, 4
+    x = r.normal(size=(B, H, W, Ci))
+    w = r.normal(size=(Co, 3, 3, Ci))
+    b = r.normal(size=Co)
+    got = S.conv3x3(torch.tensor(x), torch.tensor(w), torch.tensor(b), stride, relu=False).numpy()
+    Ho, Wo = (H - 1) // stride + 1, (W - 1) // stride + 1
+    ref = np.zeros((B, Ho, Wo, Co))
+    for n in range(B):
+        for yo in range(Ho):
+            for xo in range(Wo):
+                for co in range(Co):
+                    acc = b[co]
+                    for ky in range(3):
+                        for kx in range(3):
+                            yi, xi = yo * stride - 1 + ky, xo * stride - 1 + kx
+                            if 0 <= yi < H and 0 <= xi < W:
+                                acc += np.dot(w[co, ky, kx], x[n, yi, xi])
+                    ref[n, yo, xo, co] = acc
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_convT2x2_matches_direct_scatter():
+    r = _rng(3)
+    B, H, W, Ci, Co = 2, 3, 4, 5, 3
+    x = r.normal(size=(B, H, W, Ci))
+    w4 = r.normal(size=(4 * Co, Ci))
+    b = r.normal(size=Co)
+    got = S.convT2x2(torch.tensor(x), torch.tensor(w4), torch.tensor(b), relu=False).numpy()
+    ref = np.zeros((B, 2 * H, 2 * W, Co)) + b
+    for n in range(B):
+        for y in range(H):
+            for xx in range(W):
+                for dy in range(2):
+                    for dx in range(2):
+                        for co in range(Co):
+                            ref[n, 2 * y + dy, 2 * xx + dx, co] += np.dot(w4[(2 * dy + dx) * Co + co], x[n, y, xx])
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_ssim_identity_and_constant_images():
+    r = _rng(4)
+    x = torch.tensor(r.uniform(size=(2, 20, 24)))
+    assert torch.allclose(S.ssim_map(x, x), torch.ones(1, dtype=S.DT))
+    a, b = 0.3, 0.7
+    xa, xb = torch.full((1, 16, 16), a, dtype=S.DT), torch.full((1, 16, 16), b, dtype=S.DT)
+    want = (2 * a * b + S.SSIM_C1) / (a * a + b * b + S.SSIM_C1)     # sigmas vanish
+    assert torch.allclose(S.ssim_map(xa, xb), torch.tensor(want, dtype=S.DT))
+
+
+def test_ssim_map_matches_direct_window():
+    r = _rng(5)
+    x, y = r.uniform(size=(1, 17, 19)), r.uniform(size=(1, 17, 19))
+    m = S.ssim_map(torch.tensor(x), torch.tensor(y)).numpy()
+    k = np.arange(11) - 5.0
+    g1 = np.exp(-k * k / (2 * 1.5 ** 2))
+    g = np.outer(g1, g1)
+    g /= g.sum()
+    for (i, j) in [(0, 0), (3, 5), (6, 8)]:
+        px, py = x[0, i:i + 11, j:j + 11], y[0, i:i + 11, j:j + 11]
+        mx, my = (g * px).sum(), (g * py).sum()
+        vx = (g * (px - mx) ** 2).sum()
+        vy = (g * (py - my) ** 2).sum()
+        cxy = (g * (px - mx) * (py - my)).sum()
+        want = ((2 * mx * my + 1e-4) * (2 * cxy + 9e-4)) / ((mx * mx + my * my + 1e-4) * (vx + vy + 9e-4))
+        assert abs(m[0, i, j] - want) < 1e-12
+
+
+def test_parameter_count_by_hand():
+    c = 32
+    conv = lambda ci, co: co * 9 * ci + co
+    convT = lambda ci, co: 4 * co * ci + co
+    want = (conv(8, 32) + conv(32, 32)
+            + conv(32, 64) + 2 * conv(64, 64) + conv(64, 128) + 2 * conv(128, 128) + conv(128, 256) + 2 * conv(256, 256)
+            + convT(256, 128) + conv(256, 128) + conv(128, 128)
+            + convT(128, 64) + conv(128, 64) + conv(64, 64)
+            + convT(64, 32) + conv(64, 32) + conv(32, 32) + 33)
+    assert S.n_params(c) == want
+
+
+def test_loss_gradient_matches_finite_differences():
+    c, H = 2, 16
+    r = _rng(6)
+    shapes = S.param_shapes(c)
+    flat = np.concatenate([r.normal(0, 0.4, size=math.prod(s)) for _, s in shapes])
+    x = np.zeros((2, H, H, 8))
+    x[..., :2] = r.uniform(0, 1, size=(2, H, H, 2))
+    t = r.uniform(0.1, 0.9, size=(2, H, H))
+    L, g, _ = S.loss_and_grads(flat, x, t, c)
+    idx = r.choice(flat.size, 40, replace=False)
+    h = 1e-6
+    for i in idx:
+        fp, fm = flat.copy(), flat.copy()
+        fp[i] += h
+        fm[i] -= h
+        Lp = S.loss_and_grads(fp, x, t, c)[0]
+        Lm = S.loss_and_grads(fm, x, t, c)[0]
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - float(g[i])) <= 1e-6 + 1e-4 * abs(fd), (i, fd, float(g[i]))
+
+
+def test_adam_matches_torch_optimizer():
+    r = _rng(7)
+    p0 = torch.tensor(r.normal(size=50))
+    grads = [torch.tensor(r.normal(size=50)) for _ in range(5)]
+    q = p0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([q], lr=2e-4, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = p0.clone(), torch.zeros(50, dtype=S.DT), torch.zeros(50, dtype=S.DT)
+    for t, g in enumerate(grads, 1):
+        opt.zero_grad()
+        q.grad = g.clone()
+        opt.step()
+        p, m, v = S.adam_step(p, g, m, v, t)
+    assert torch.allclose(p, q.detach(), rtol=0, atol=1e-12)
+    # first step moves every coordinate by about lr against the gradient's sign
+    p1, _, _ = S.adam_step(p0, grads[0], torch.zeros(50, dtype=S.DT), torch.zeros(50, dtype=S.DT), 1)
+    assert torch.allclose(p1 - p0, -2e-4 * torch.sign(grads[0]), atol=1e-9)
