@@ -34,6 +34,55 @@ extern "C" {
 US_API us_status us_gemm_bf16_nt(const uint16_t* A, const uint16_t* B, float* C, int32_t M, int32_t N, int32_t K,
                                  uint32_t* err, void* stream);
 
+/* ---- convolution operators (implicit GEMM on tcgen05) -----------------
+ * Tensors are NHWC BF16 views: base pointer, channel stride (elements per
+ * pixel, multiple of 8) and channel offset (multiple of 8), so an operator
+ * can read or write a channel slice of a concatenated tensor.  Channel
+ * counts are multiples of 8 (Cout of the forward ops a multiple of 32 /
+ * 16 for convT).  All pointers 16-byte aligned.  `err` as above.
+ * The paper's U-Net (App. B.2, Fig. U-Net) is built from such layers:
+ * 3x3 convolutions (stride 1, or 2 to downsample, zero padding 1) and
+ * 2x2 stride-2 transposed convolutions to upsample. */
+
+/* y[b,yo,xo,co] = act(bias[co] + sum_{ky,kx,ci} x[b, yo*s-1+ky, xo*s-1+kx, ci] w[co][ky][kx][ci]);
+ * input B x H x W x Cin, output B x ceil(H/s) x ceil(W/s) x Cout; act = ReLU if relu. */
+US_API us_status us_conv3x3_fwd(const uint16_t* x, int32_t x_cs, int32_t x_co, const uint16_t* w, const float* bias,
+                                uint16_t* y, int32_t y_cs, int32_t y_co, int32_t B, int32_t H, int32_t W,
+                                int32_t Cin, int32_t Cout, int32_t stride, int32_t relu, uint32_t* err, void* stream);
+
+/* gradient w.r.t. the input of a 3x3 convolution whose input x is a
+ * post-ReLU activation: dx = [x > 0] * sum_{ky,kx,co} dy[b,(yi+1-ky)/s,(xi+1-kx)/s,co] w[co][ky][kx][ci]
+ * (terms with a non-integer quotient drop out); wd[ci][ky][kx][co] =
+ * w[co][ky][kx][ci].  accumulate = 1 adds to the values already in dx. */
+US_API us_status us_conv3x3_dgrad(const uint16_t* dy, int32_t dy_cs, int32_t dy_co, const uint16_t* wd,
+                                  const uint16_t* x, int32_t x_cs, int32_t x_co, uint16_t* dx, int32_t dx_cs,
+                                  int32_t dx_co, int32_t accumulate, int32_t B, int32_t H, int32_t W, int32_t Cin,
+                                  int32_t Cout, int32_t stride, uint32_t* err, void* stream);
+
+/* weight gradient, accumulated: gwt[(ky,kx,ci)][co] += sum_{b,yo,xo} x[b, yo*s-1+ky, xo*s-1+kx, ci] dy[b,yo,xo,co]
+ * (FP32, [9 Cin][Cout], the transpose of the weight layout). */
+US_API us_status us_conv3x3_wgrad(const uint16_t* x, int32_t x_cs, int32_t x_co, const uint16_t* dy, int32_t dy_cs,
+                                  int32_t dy_co, float* gwt, int32_t B, int32_t H, int32_t W, int32_t Cin,
+                                  int32_t Cout, int32_t stride, uint32_t* err, void* stream);
+
+/* y[b, 2y+dy, 2x+dx, co] = act(bias[co] + sum_ci x[b,y,x,ci] w4[(2 dy + dx) Cout + co][ci]);
+ * input B x H x W x Cin, output B x 2H x 2W x Cout. */
+US_API us_status us_convT2x2_fwd(const uint16_t* x, int32_t x_cs, int32_t x_co, const uint16_t* w4, const float* bias,
+                                 uint16_t* y, int32_t y_cs, int32_t y_co, int32_t B, int32_t H, int32_t W,
+                                 int32_t Cin, int32_t Cout, int32_t relu, uint32_t* err, void* stream);
+
+/* dx = [x > 0] * sum_{dy,dx,co} dy[b, 2y+dy, 2x+dx, co] w4[(2 dy + dx) Cout + co][ci];
+ * w4t[ci][(d, co)] = w4[(d, co)][ci]; x is the (post-ReLU) input, B x H x W x Cin. */
+US_API us_status us_convT2x2_dgrad(const uint16_t* dy, int32_t dy_cs, int32_t dy_co, const uint16_t* w4t,
+                                   const uint16_t* x, int32_t x_cs, int32_t x_co, uint16_t* dx, int32_t dx_cs,
+                                   int32_t dx_co, int32_t accumulate, int32_t B, int32_t H, int32_t W, int32_t Cin,
+                                   int32_t Cout, uint32_t* err, void* stream);
+
+/* g4[(d, co)][ci] += sum_{b,y,x} dy[b, 2y+dy, 2x+dx, co] x[b,y,x,ci]  (FP32, [4 Cout][Cin]) */
+US_API us_status us_convT2x2_wgrad(const uint16_t* x, int32_t x_cs, int32_t x_co, const uint16_t* dy, int32_t dy_cs,
+                                   int32_t dy_co, float* g4, int32_t B, int32_t H, int32_t W, int32_t Cin,
+                                   int32_t Cout, uint32_t* err, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,486 @@
+// Convolution operators of the surrogate on the tcgen05 tile GEMM.
+//
+//  conv3x3 forward   D[(b,yo,xo)][co]     = sum_(ky,kx,ci) X[b, yo*s-1+ky, xo*s-1+kx, ci] W[co][ky][kx][ci]
+//  conv3x3 dgrad     dX[(b,yi,xi)][ci]    = sum_(ky,kx,co) dY[b, (yi+1-ky)/s, (xi+1-kx)/s, co] W[co][ky][kx][ci]
+//                                          (terms whose (yi+1-ky)/s is not an integer drop out)
+//  conv3x3 wgrad     dW^T[(ky,kx,ci)][co] = sum_(b,yo,xo) X[b, yo*s-1+ky, xo*s-1+kx, ci] dY[b,yo,xo,co]
+//  convT2x2 forward  D[(b,y,x)][(d,co)]   = sum_ci X[b,y,x,ci] W4[(d,co)][ci], scattered to (2y+dy, 2x+dx)
+//  convT2x2 dgrad    dX[(b,y,x)][ci]      = sum_(d,co) dY[b, 2y+dy, 2x+dx, co] W4[(d,co)][ci]
+//  convT2x2 wgrad    dW4[(d,co)][ci]      = sum_(b,y,x) dY[b, 2y+dy, 2x+dx, co] X[b,y,x,ci]
+//
+// Activations are NHWC BF16 views (pointer, channel stride, channel offset),
+// so a layer reads or writes a channel slice of a concatenated tensor in
+// place.  Epilogues fuse bias + ReLU + BF16 conversion (forward), the ReLU
+// mask of the layer input (+ optional accumulation into an existing
+// gradient, for tensors that feed two layers) (dgrad), and FP32 atomic
+// reduction of split-K partial sums (wgrad).
+#include <cuda_bf16.h>
+
+#include "ussim_surrogate.h"
+#include "umma_gemm.cuh"
+
+namespace ussim {
+namespace surr {
+
+using namespace umma;
+using bf16 = __nv_bfloat16;
+
+struct View {
+  const bf16* p;
+  int cs, co;   // channel stride (elements per pixel) and channel offset
+};
+struct OutView {
+  bf16* p;
+  int cs, co;
+};
+
+// rows of an implicit GEMM walk the pixels of a B x H x W grid
+struct Grid {
+  int B, H, W;
+  __device__ __forceinline__ void pix(int m, int& b, int& y, int& x) const {
+    const int hw = H * W;
+    b = m / hw;
+    const int r = m - b * hw;
+    y = r / W;
+    x = r - y * W;
+  }
+};
+
+// each thread stages a fixed 16-byte column chunk kc of 8 rows per A tile
+// (rows r0 + 16 i), so per-row pixel coordinates are computed once per CTA
+__device__ __forceinline__ void a_chunk(int tid, int& kc, int& r0) {
+  kc = (tid >> 3) & 7;
+  r0 = (tid & 7) + ((tid >> 6) << 3);
+}
+
+// ------------------------------------------------------------ forward conv
+struct ConvFwdLoader {
+  View x;
+  const bf16* w;   // [N][K]
+  Grid in, out;
+  int Cin, K, N, stride, M, bn;
+  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+    int kc, r0;
+    a_chunk(tid, kc, r0);
+    const int k = kt * kBK + kc * 8;
+    const bool kval = k < K;
+    const int tap = kval ? k / Cin : 0, ci = k - tap * Cin;
+    const int ky = tap / 3, kx = tap - ky * 3;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + 16 * i, m = m0 + r;
+      const void* src = x.p;
+      uint32_t bytes = 0;
+      if (kval && m < M) {
+        int b, yo, xo;
+        out.pix(m, b, yo, xo);
+        const int yi = yo * stride - 1 + ky, xi = xo * stride - 1 + kx;
+        if ((unsigned)yi < (unsigned)in.H && (unsigned)xi < (unsigned)in.W) {
+          src = x.p + ((size_t)(b * in.H + yi) * in.W + xi) * x.cs + x.co + ci;
+          bytes = 16;
+        }
+      }
+      cp_async16(as + tile_off(r, kc, kBK), src, bytes);
+    }
+    for (int c = tid; c < bn * 8; c += kThreads) {
+      const int r = (c & 7) + ((c >> 6) << 3), kc2 = (c >> 3) & 7;
+      const int n = n0 + r, kk = kt * kBK + kc2 * 8;
+      const bool v = n < N && kk < K;
+      cp_async16(bs + tile_off(r, kc2, kBK), v ? (const void*)(w + (size_t)n * K + kk) : (const void*)w, v ? 16u : 0u);
+    }
+  }
+};
+
+struct BiasActStore {
+  OutView y;
+  const float* bias;
+  int relu;
+  __device__ void store(int m, int n0, const float* v, bool valid) const {
+    if (!valid) return;
+    __align__(16) bf16 o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float t = v[i] + __ldg(&bias[n0 + i]);
+      o[i] = __float2bfloat16_rn(relu ? fmaxf(t, 0.f) : t);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(y.p + (size_t)m * y.cs + y.co + n0);
+    dst[0] = reinterpret_cast<const uint4*>(o)[0];
+    dst[1] = reinterpret_cast<const uint4*>(o)[1];
+  }
+};
+
+// ------------------------------------------------------------ conv dgrad
+struct ConvDgradLoader {
+  View dy;
+  const bf16* wd;   // [Cin][9 Cout]: wd[ci][(ky,kx,co)] = W[co][ky][kx][ci]
+  Grid in, out;     // in = dX grid (forward input), out = dY grid
+  int Cout, K, N, stride, M, bn;
+  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+    int kc, r0;
+    a_chunk(tid, kc, r0);
+    const int k = kt * kBK + kc * 8;
+    const bool kval = k < K;
+    const int tap = kval ? k / Cout : 0, co = k - tap * Cout;
+    const int ky = tap / 3, kx = tap - ky * 3;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + 16 * i, m = m0 + r;
+      const void* src = dy.p;
+      uint32_t bytes = 0;
+      if (kval && m < M) {
+        int b, yi, xi;
+        in.pix(m, b, yi, xi);
+        const int ys = yi + 1 - ky, xs = xi + 1 - kx;
+        if (ys >= 0 && xs >= 0 && (ys % stride) == 0 && (xs % stride) == 0) {
+          const int yo = ys / stride, xo = xs / stride;
+          if (yo < out.H && xo < out.W) {
+            src = dy.p + ((size_t)(b * out.H + yo) * out.W + xo) * dy.cs + dy.co + co;
+            bytes = 16;
+          }
+        }
+      }
+      cp_async16(as + tile_off(r, kc, kBK), src, bytes);
+    }
+    for (int c = tid; c < bn * 8; c += kThreads) {
+      const int r = (c & 7) + ((c >> 6) << 3), kc2 = (c >> 3) & 7;
+      const int n = n0 + r, kk = kt * kBK + kc2 * 8;
+      const bool v = n < N && kk < K;
+      cp_async16(bs + tile_off(r, kc2, kBK), v ? (const void*)(wd + (size_t)n * K + kk) : (const void*)wd, v ? 16u : 0u);
+    }
+  }
+};
+
+// gradient w.r.t. a post-ReLU activation x: g * [x > 0], optionally added to
+// the gradient already stored there (the tensor also feeds another layer)
+struct MaskedGradStore {
+  OutView dx;
+  View x;
+  int accumulate;
+  __device__ void store(int m, int n0, const float* v, bool valid) const {
+    if (!valid) return;
+    const uint4* xp = reinterpret_cast<const uint4*>(x.p + (size_t)m * x.cs + x.co + n0);
+    __align__(16) bf16 xv[16];
+    reinterpret_cast<uint4*>(xv)[0] = __ldg(xp);
+    reinterpret_cast<uint4*>(xv)[1] = __ldg(xp + 1);
+    uint4* dst = reinterpret_cast<uint4*>(dx.p + (size_t)m * dx.cs + dx.co + n0);
+    __align__(16) bf16 old[16];
+    if (accumulate) {
+      reinterpret_cast<uint4*>(old)[0] = dst[0];
+      reinterpret_cast<uint4*>(old)[1] = dst[1];
+    }
+    __align__(16) bf16 o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float g = __bfloat162float(xv[i]) > 0.f ? v[i] : 0.f;
+      if (accumulate) g += __bfloat162float(old[i]);
+      o[i] = __float2bfloat16_rn(g);
+    }
+    dst[0] = reinterpret_cast<const uint4*>(o)[0];
+    dst[1] = reinterpret_cast<const uint4*>(o)[1];
+  }
+};
+
+// ------------------------------------------------------- transposed conv
+struct ConvTFwdLoader {
+  View x;
+  const bf16* w4;   // [4 Cout][Cin]
+  int Cin, N, M, bn;
+  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+    int kc, r0;
+    a_chunk(tid, kc, r0);
+    const int k = kt * kBK + kc * 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + 16 * i, m = m0 + r;
+      const bool v = m < M && k < Cin;
+      cp_async16(as + tile_off(r, kc, kBK), v ? (const void*)(x.p + (size_t)m * x.cs + x.co + k) : (const void*)x.p,
+                 v ? 16u : 0u);
+    }
+    for (int c = tid; c < bn * 8; c += kThreads) {
+      const int r = (c & 7) + ((c >> 6) << 3), kc2 = (c >> 3) & 7;
+      const int n = n0 + r, kk = kt * kBK + kc2 * 8;
+      const bool v = n < N && kk < Cin;
+      cp_async16(bs + tile_off(r, kc2, kBK), v ? (const void*)(w4 + (size_t)n * Cin + kk) : (const void*)w4,
+                 v ? 16u : 0u);
+    }
+  }
+};
+
+struct ConvTStore {
+  OutView y;
+  const float* bias;
+  Grid in;     // input grid; output is 2H x 2W
+  int Cout, relu;
+  __device__ void store(int m, int n0, const float* v, bool valid) const {
+    if (!valid) return;
+    const int d = n0 / Cout, co = n0 - d * Cout;   // 16 consecutive n stay in one (dy, dx)
+    const int dyy = d >> 1, dxx = d & 1;
+    int b, yy, xx;
+    in.pix(m, b, yy, xx);
+    const size_t op = ((size_t)(b * 2 * in.H + 2 * yy + dyy) * (2 * in.W) + 2 * xx + dxx);
+    __align__(16) bf16 o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float t = v[i] + __ldg(&bias[co + i]);
+      o[i] = __float2bfloat16_rn(relu ? fmaxf(t, 0.f) : t);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(y.p + op * y.cs + y.co + co);
+    dst[0] = reinterpret_cast<const uint4*>(o)[0];
+    dst[1] = reinterpret_cast<const uint4*>(o)[1];
+  }
+};
+
+struct ConvTDgradLoader {
+  View dy;
+  const bf16* w4t;   // [Cin][4 Cout]
+  Grid in;           // dX grid (convT input); dY is 2H x 2W
+  int Cout, K, N, M, bn;
+  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+    int kc, r0;
+    a_chunk(tid, kc, r0);
+    const int k = kt * kBK + kc * 8;
+    const bool kval = k < K;
+    const int d = kval ? k / Cout : 0, co = k - d * Cout;
+    const int dyy = d >> 1, dxx = d & 1;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + 16 * i, m = m0 + r;
+      const void* src = dy.p;
+      uint32_t bytes = 0;
+      if (kval && m < M) {
+        int b, yy, xx;
+        in.pix(m, b, yy, xx);
+        src = dy.p + ((size_t)(b * 2 * in.H + 2 * yy + dyy) * (2 * in.W) + 2 * xx + dxx) * dy.cs + dy.co + co;
+        bytes = 16;
+      }
+      cp_async16(as + tile_off(r, kc, kBK), src, bytes);
+    }
+    for (int c = tid; c < bn * 8; c += kThreads) {
+      const int r = (c & 7) + ((c >> 6) << 3), kc2 = (c >> 3) & 7;
+      const int n = n0 + r, kk = kt * kBK + kc2 * 8;
+      const bool v = n < N && kk < K;
+      cp_async16(bs + tile_off(r, kc2, kBK), v ? (const void*)(w4t + (size_t)n * K + kk) : (const void*)w4t,
+                 v ? 16u : 0u);
+    }
+  }
+};
+
+// --------------------------------------------------------------- wgrad
+// Both operands of a weight gradient are stored pixel-major (channels
+// contiguous), while the GEMM reduces over pixels.  The loader reads
+// 8 channels x 8 pixels (eight 16-byte loads), transposes the 8 x 8 BF16
+// block in registers with byte permutes, and stores 8 pixels x 8 channels.
+__device__ __forceinline__ void transpose8x8(const uint4* in, uint4* out) {
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(in);   // w[4 p + j]: channels 2j, 2j+1 of pixel p
+  uint32_t* o = reinterpret_cast<uint32_t*>(out);               // o[4 c + j]: pixels 2j, 2j+1 of channel c
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      o[4 * c + j] = __byte_perm(w[4 * (2 * j) + (c >> 1)], w[4 * (2 * j + 1) + (c >> 1)], (c & 1) ? 0x7632 : 0x5410);
+}
+
+// source of one operand of a weight gradient: channel group (8 channels)
+// `r8` of pixel p, or zeros
+struct ConvIm2col {   // rows (ky, kx, ci) of the forward input's im2col
+  View x;
+  Grid in, out;
+  int Cin, stride, rows;
+  __device__ __forceinline__ uint4 get(int row, int p, int P) const {
+    if (row >= rows || p >= P) return make_uint4(0, 0, 0, 0);
+    const int tap = row / Cin, ci = row - tap * Cin, ky = tap / 3, kx = tap - ky * 3;
+    int b, yo, xo;
+    out.pix(p, b, yo, xo);
+    const int yi = yo * stride - 1 + ky, xi = xo * stride - 1 + kx;
+    if ((unsigned)yi >= (unsigned)in.H || (unsigned)xi >= (unsigned)in.W) return make_uint4(0, 0, 0, 0);
+    return __ldg(reinterpret_cast<const uint4*>(x.p + ((size_t)(b * in.H + yi) * in.W + xi) * x.cs + x.co + ci));
+  }
+};
+struct PixelRows {    // rows = channels of a tensor on the reduction grid
+  View t;
+  int rows;
+  __device__ __forceinline__ uint4 get(int row, int p, int P) const {
+    if (row >= rows || p >= P) return make_uint4(0, 0, 0, 0);
+    return __ldg(reinterpret_cast<const uint4*>(t.p + (size_t)p * t.cs + t.co + row));
+  }
+};
+struct ConvTGather {  // rows (d, co) of the transposed conv's output gradient, on its input grid
+  View dy;
+  Grid in;
+  int Cout, rows;
+  __device__ __forceinline__ uint4 get(int row, int p, int P) const {
+    if (row >= rows || p >= P) return make_uint4(0, 0, 0, 0);
+    const int d = row / Cout, co = row - d * Cout;
+    int b, yy, xx;
+    in.pix(p, b, yy, xx);
+    const size_t op = (size_t)(b * 2 * in.H + 2 * yy + (d >> 1)) * (2 * in.W) + 2 * xx + (d & 1);
+    return __ldg(reinterpret_cast<const uint4*>(dy.p + op * dy.cs + dy.co + co));
+  }
+};
+
+template <class SrcA, class SrcB>
+struct WgradLoader {
+  SrcA a;
+  SrcB b;
+  int P, bn;   // pixels in the reduction
+  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+    const int p0 = kt * kBK;
+    {   // A: 16 row groups x 8 pixel groups = 128 blocks, one per thread
+      const int rg = tid >> 3, pg = tid & 7;
+      uint4 in[8], out[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) in[q] = a.get(m0 + rg * 8, p0 + pg * 8 + q, P);
+      transpose8x8(in, out);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(as + tile_off(rg * 8 + c, pg, kBK)) = out[c];
+    }
+    for (int blk = tid; blk < bn; blk += kThreads) {   // B: bn/8 row groups x 8 pixel groups
+      const int rg = blk >> 3, pg = blk & 7;
+      uint4 in[8], out[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) in[q] = b.get(n0 + rg * 8, p0 + pg * 8 + q, P);
+      transpose8x8(in, out);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(bs + tile_off(rg * 8 + c, pg, kBK)) = out[c];
+    }
+  }
+};
+
+struct AtomicF32Store {   // G[m][n] += v (FP32), rows < M
+  float* g;
+  int N, M;
+  __device__ void store(int m, int n0, const float* v, bool valid) const {
+    if (!valid || m >= M) return;
+    float* dst = g + (size_t)m * N + n0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) atomicAdd(dst + i, v[i]);
+  }
+};
+
+// --------------------------------------------------------------- launch
+template <class Ld, class Ep>
+cudaError_t gemm_bn(int bn, const Ld& ld, const Ep& ep, int M, int N, int K, unsigned* err, cudaStream_t st,
+                    int splits = 1) {
+  switch (bn) {
+    case 256: return launch_umma_gemm<256>(ld, ep, M, N, K, err, st, splits);
+    case 128: return launch_umma_gemm<128>(ld, ep, M, N, K, err, st, splits);
+    case 64: return launch_umma_gemm<64>(ld, ep, M, N, K, err, st, splits);
+    case 32: return launch_umma_gemm<32>(ld, ep, M, N, K, err, st, splits);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int pick_bn(int N) { return (N % 256 == 0) ? 256 : (N % 128 == 0) ? 128 : (N % 64 == 0) ? 64 : (N % 32 == 0) ? 32 : 0; }
+
+// split the pixel reduction of a weight gradient so that the grid covers
+// about four waves of the GPU
+int wgrad_splits(int mt, int nt, long long P) {
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = 4LL * sms;
+  long long s = (want + (long long)mt * nt - 1) / ((long long)mt * nt);
+  const long long ktot = (P + kBK - 1) / kBK;
+  if (s > ktot) s = ktot;
+  return (int)(s < 1 ? 1 : s);
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace surr
+}  // namespace ussim
+
+using namespace ussim;
+using namespace ussim::surr;
+
+#define US_CHECK(cond) \
+  do {                 \
+    if (!(cond)) return US_ERR_INVALID_ARG; \
+  } while (0)
+
+static us_status to_status(cudaError_t e) { return e == cudaSuccess ? US_OK : US_ERR_CUDA; }
+
+extern "C" {
+
+us_status us_conv3x3_fwd(const uint16_t* x, int32_t x_cs, int32_t x_co, const uint16_t* w, const float* bias,
+                         uint16_t* y, int32_t y_cs, int32_t y_co, int32_t B, int32_t H, int32_t W, int32_t Cin,
+                         int32_t Cout, int32_t stride, int32_t relu, uint32_t* err, void* stream) {
+  US_CHECK(x && w && bias && y && err && B > 0 && H > 0 && W > 0 && (stride == 1 || stride == 2));
+  US_CHECK(Cin % 8 == 0 && Cin > 0 && pick_bn(Cout) && x_cs % 8 == 0 && x_co % 8 == 0 && x_co + Cin <= x_cs);
+  US_CHECK(y_cs % 8 == 0 && y_co % 8 == 0 && y_co + Cout <= y_cs && aligned16(x) && aligned16(y) && aligned16(w));
+  const Grid in{B, H, W}, out{B, (H - 1) / stride + 1, (W - 1) / stride + 1};
+  const int M = B * out.H * out.W, K = 9 * Cin, bn = pick_bn(Cout);
+  ConvFwdLoader ld{{(const bf16*)x, x_cs, x_co}, (const bf16*)w, in, out, Cin, K, Cout, stride, M, bn};
+  BiasActStore ep{{(bf16*)y, y_cs, y_co}, bias, relu};
+  return to_status(gemm_bn(bn, ld, ep, M, Cout, K, err, (cudaStream_t)stream));
+}
+
+us_status us_conv3x3_dgrad(const uint16_t* dy, int32_t dy_cs, int32_t dy_co, const uint16_t* wd, const uint16_t* x,
+                           int32_t x_cs, int32_t x_co, uint16_t* dx, int32_t dx_cs, int32_t dx_co, int32_t accumulate,
+                           int32_t B, int32_t H, int32_t W, int32_t Cin, int32_t Cout, int32_t stride, uint32_t* err,
+                           void* stream) {
+  US_CHECK(dy && wd && x && dx && err && B > 0 && H > 0 && W > 0 && (stride == 1 || stride == 2));
+  US_CHECK(Cout % 8 == 0 && pick_bn(Cin) && dy_cs % 8 == 0 && dy_co % 8 == 0 && x_cs % 8 == 0 && x_co % 8 == 0);
+  US_CHECK(dx_cs % 8 == 0 && dx_co % 8 == 0 && aligned16(dy) && aligned16(wd) && aligned16(x) && aligned16(dx));
+  const Grid in{B, H, W}, out{B, (H - 1) / stride + 1, (W - 1) / stride + 1};
+  const int M = B * H * W, K = 9 * Cout, bn = pick_bn(Cin);
+  ConvDgradLoader ld{{(const bf16*)dy, dy_cs, dy_co}, (const bf16*)wd, in, out, Cout, K, Cin, stride, M, bn};
+  MaskedGradStore ep{{(bf16*)dx, dx_cs, dx_co}, {(const bf16*)x, x_cs, x_co}, accumulate};
+  return to_status(gemm_bn(bn, ld, ep, M, Cin, K, err, (cudaStream_t)stream));
+}
+
+us_status us_conv3x3_wgrad(const uint16_t* x, int32_t x_cs, int32_t x_co, const uint16_t* dy, int32_t dy_cs,
+                           int32_t dy_co, float* gwt, int32_t B, int32_t H, int32_t W, int32_t Cin, int32_t Cout,
+                           int32_t stride, uint32_t* err, void* stream) {
+  US_CHECK(x && dy && gwt && err && B > 0 && H > 0 && W > 0 && (stride == 1 || stride == 2));
+  US_CHECK(Cin % 8 == 0 && pick_bn(Cout) && x_cs % 8 == 0 && x_co % 8 == 0 && dy_cs % 8 == 0 && dy_co % 8 == 0);
+  US_CHECK(aligned16(x) && aligned16(dy));
+  const Grid in{B, H, W}, out{B, (H - 1) / stride + 1, (W - 1) / stride + 1};
+  const int rows = 9 * Cin, P = B * out.H * out.W, bn = pick_bn(Cout);
+  WgradLoader<ConvIm2col, PixelRows> ld{{{(const bf16*)x, x_cs, x_co}, in, out, Cin, stride, rows},
+                                        {{(const bf16*)dy, dy_cs, dy_co}, Cout}, P, bn};
+  AtomicF32Store ep{gwt, Cout, rows};
+  const int mt = (rows + kBM - 1) / kBM, nt = Cout / bn;
+  return to_status(gemm_bn(bn, ld, ep, rows, Cout, P, err, (cudaStream_t)stream, wgrad_splits(mt, nt, P)));
+}
+
+us_status us_convT2x2_fwd(const uint16_t* x, int32_t x_cs, int32_t x_co, const uint16_t* w4, const float* bias,
+                          uint16_t* y, int32_t y_cs, int32_t y_co, int32_t B, int32_t H, int32_t W, int32_t Cin,
+                          int32_t Cout, int32_t relu, uint32_t* err, void* stream) {
+  US_CHECK(x && w4 && bias && y && err && B > 0 && H > 0 && W > 0);
+  US_CHECK(Cin % 8 == 0 && Cout % 16 == 0 && pick_bn(4 * Cout) && x_cs % 8 == 0 && x_co % 8 == 0);
+  US_CHECK(y_cs % 8 == 0 && y_co % 8 == 0 && aligned16(x) && aligned16(w4) && aligned16(y));
+  const int M = B * H * W, N = 4 * Cout, bn = pick_bn(N);   // 16-column chunks never straddle a (dy, dx) block
+  ConvTFwdLoader ld{{(const bf16*)x, x_cs, x_co}, (const bf16*)w4, Cin, N, M, bn};
+  ConvTStore ep{{(bf16*)y, y_cs, y_co}, bias, {B, H, W}, Cout, relu};
+  return to_status(gemm_bn(bn, ld, ep, M, N, Cin, err, (cudaStream_t)stream));
+}
+
+us_status us_convT2x2_dgrad(const uint16_t* dy, int32_t dy_cs, int32_t dy_co, const uint16_t* w4t, const uint16_t* x,
+                            int32_t x_cs, int32_t x_co, uint16_t* dx, int32_t dx_cs, int32_t dx_co,
+                            int32_t accumulate, int32_t B, int32_t H, int32_t W, int32_t Cin, int32_t Cout,
+                            uint32_t* err, void* stream) {
+  US_CHECK(dy && w4t && x && dx && err && B > 0 && H > 0 && W > 0);
+  US_CHECK(Cout % 8 == 0 && pick_bn(Cin) && dy_cs % 8 == 0 && dy_co % 8 == 0 && x_cs % 8 == 0 && x_co % 8 == 0);
+  US_CHECK(dx_cs % 8 == 0 && dx_co % 8 == 0 && aligned16(dy) && aligned16(w4t) && aligned16(x) && aligned16(dx));
+  const int M = B * H * W, K = 4 * Cout, bn = pick_bn(Cin);
+  ConvTDgradLoader ld{{(const bf16*)dy, dy_cs, dy_co}, (const bf16*)w4t, {B, H, W}, Cout, K, Cin, M, bn};
+  MaskedGradStore ep{{(bf16*)dx, dx_cs, dx_co}, {(const bf16*)x, x_cs, x_co}, accumulate};
+  return to_status(gemm_bn(bn, ld, ep, M, Cin, K, err, (cudaStream_t)stream));
+}
+
+us_status us_convT2x2_wgrad(const uint16_t* x, int32_t x_cs, int32_t x_co, const uint16_t* dy, int32_t dy_cs,
+                            int32_t dy_co, float* g4, int32_t B, int32_t H, int32_t W, int32_t Cin, int32_t Cout,
+                            uint32_t* err, void* stream) {
+  US_CHECK(x && dy && g4 && err && B > 0 && H > 0 && W > 0);
+  US_CHECK(Cout % 8 == 0 && pick_bn(Cin) && x_cs % 8 == 0 && x_co % 8 == 0 && dy_cs % 8 == 0 && dy_co % 8 == 0);
+  US_CHECK(aligned16(x) && aligned16(dy));
+  const int rows = 4 * Cout, P = B * H * W, bn = pick_bn(Cin);
+  WgradLoader<ConvTGather, PixelRows> ld{{{(const bf16*)dy, dy_cs, dy_co}, {B, H, W}, Cout, rows},
+                                         {{(const bf16*)x, x_cs, x_co}, Cin}, P, bn};
+  AtomicF32Store ep{g4, Cin, rows};
+  const int mt = (rows + kBM - 1) / kBM, nt = Cin / bn;
+  return to_status(gemm_bn(bn, ld, ep, rows, Cin, P, err, (cudaStream_t)stream, wgrad_splits(mt, nt, P)));
+}
+
+}  // extern "C"

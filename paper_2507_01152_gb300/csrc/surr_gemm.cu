@@ -42,7 +42,6 @@ struct F32Store {
   }
 };
 
-unsigned* g_err_dev = nullptr;
 
 }  // namespace
 }  // namespace ussim

@@ -34,9 +34,11 @@ constexpr uint32_t tmem_cols() {
 }
 
 // Loader:   void load(uint8_t* a_stage, uint8_t* b_stage, int m0, int n0, int kt, int tid)
-//           issues cp.async for the 128 x 64 A tile rows m0.., and the BN x 64 B
-//           tile rows n0.., K step kt, into the K-major no-swizzle layout
-//           (use tile_off(r, kc, kBK) for 16-byte chunk kc of row r).
+//           stages the 128 x 64 A tile rows m0.., and the BN x 64 B tile rows
+//           n0.., K step kt, into the K-major no-swizzle layout (use
+//           tile_off(r, kc, kBK) for 16-byte chunk kc of row r), with cp.async
+//           or plain shared stores; steps past the end of K must load zeros.
+//           With split K (grid.z > 1), CTA z covers steps z*k_tiles .. +k_tiles.
 // Epilogue: void store(int m, int n0, const float* v16, bool valid)
 template <int BN, class Loader, class Epilogue>
 __global__ void __launch_bounds__(kThreads) umma_gemm_kernel(Loader ld, Epilogue ep, int M, int k_tiles,
@@ -63,8 +65,9 @@ __global__ void __launch_bounds__(kThreads) umma_gemm_kernel(Loader ld, Epilogue
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int kt0 = blockIdx.z * k_tiles;
 
-  ld.load(stage[0], stage[0] + kTileA, m0, n0, 0, tid);
+  ld.load(stage[0], stage[0] + kTileA, m0, n0, kt0, tid);
   cp_async_commit();
   bool ok = true;
   int t = 0;
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) umma_gemm_kernel(Loader ld, Epilogue
     if (t + 1 < k_tiles) {
       // the other stage was read by the MMAs of step t-1: wait for their commit
       if (t >= 1) ok = ok && mbar_wait(&bar[s ^ 1], ((t - 1) >> 1) & 1);
-      if (ok) ld.load(stage[s ^ 1], stage[s ^ 1] + kTileA, m0, n0, t + 1, tid);
+      if (ok) ld.load(stage[s ^ 1], stage[s ^ 1] + kTileA, m0, n0, kt0 + t + 1, tid);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
@@ -115,14 +118,19 @@ __global__ void __launch_bounds__(kThreads) umma_gemm_kernel(Loader ld, Epilogue
   if (warp == 0) tmem_dealloc(tmem, NCOL);
 }
 
+// splits > 1: split K into `splits` contiguous ranges (grid.z); the
+// epilogue then receives partial sums and must reduce them itself
 template <int BN, class Loader, class Epilogue>
 cudaError_t launch_umma_gemm(const Loader& ld, const Epilogue& ep, int M, int N, int K, unsigned* err,
-                             cudaStream_t st) {
+                             cudaStream_t st, int splits = 1) {
   auto kern = umma_gemm_kernel<BN, Loader, Epilogue>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes<BN>());
   if (e != cudaSuccess) return e;
-  const dim3 grid((M + kBM - 1) / kBM, N / BN);
-  const int k_tiles = (K + kBK - 1) / kBK;
+  const int k_total = (K + kBK - 1) / kBK;
+  splits = splits < 1 ? 1 : (splits > k_total ? k_total : splits);
+  const int k_tiles = (k_total + splits - 1) / splits;
+  splits = (k_total + k_tiles - 1) / k_tiles;
+  const dim3 grid((M + kBM - 1) / kBM, N / BN, splits);
   kern<<<grid, kThreads, gemm_smem_bytes<BN>(), st>>>(ld, ep, M, k_tiles, err);
   return cudaGetLastError();
 }

@@ -60,6 +60,7 @@ class us_tuning(C.Structure):
 
 # name -> (restype, argtypes) for every entry point of include/ussim.h
 _P = C.c_void_p
+_I = C.c_int32
 SIGNATURES = {
     "us_sim_create": (C.c_int, [C.POINTER(us_volume), C.c_int32, C.POINTER(us_tissue), C.c_int32,
                                 C.POINTER(us_probe), C.c_int32, C.POINTER(us_options), C.POINTER(_P)]),
@@ -79,6 +80,12 @@ SIGNATURES = {
     "us_sim_last_error": (C.c_char_p, [_P]),
     "us_status_string": (C.c_char_p, [C.c_int]),
     "us_gemm_bf16_nt": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P]),
+    "us_conv3x3_fwd": (C.c_int, [_P, _I, _I, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _I, _I, _P, _P]),
+    "us_conv3x3_dgrad": (C.c_int, [_P, _I, _I, _P, _P, _I, _I, _P, _I, _I, _I, _I, _I, _I, _I, _I, _I, _P, _P]),
+    "us_conv3x3_wgrad": (C.c_int, [_P, _I, _I, _P, _I, _I, _P, _I, _I, _I, _I, _I, _I, _P, _P]),
+    "us_convT2x2_fwd": (C.c_int, [_P, _I, _I, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _I, _P, _P]),
+    "us_convT2x2_dgrad": (C.c_int, [_P, _I, _I, _P, _P, _I, _I, _P, _I, _I, _I, _I, _I, _I, _I, _I, _P, _P]),
+    "us_convT2x2_wgrad": (C.c_int, [_P, _I, _I, _P, _I, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
 }
 
 _lib = None
@@ -130,6 +137,16 @@ def gemm_bf16_nt(A, B, C, err, stream=None):
     st = L.us_gemm_bf16_nt(_ptr(A), _ptr(B), _ptr(C), M, N, K, _ptr(err), _stream_handle(stream))
     if st != US_OK:
         raise UsError(st, "us_gemm_bf16_nt")
+
+
+def op(name, *args, stream=None):
+    """Call an operator entry point: tensors -> device pointers, ints as is;
+    the trailing stream argument is appended."""
+    L = load()
+    conv = [(_ptr(a) if not isinstance(a, (int, np.integer)) else int(a)) for a in args]
+    st = getattr(L, name)(*conv, _stream_handle(stream))
+    if st != US_OK:
+        raise UsError(st, name)
 
 
 def make_probe(p) -> us_probe:
