@@ -202,6 +202,16 @@ US_API us_status us_sim_render_debug(us_sim* sim, const us_env* envs, int32_t B,
 US_API us_status us_sim_render_host(us_sim* sim, const us_env* envs, int32_t B, const float* poses_host,
                              uint64_t seed, uint64_t step, float* frames_host, void* stream);
 
+/* Input of the learned surrogate (ussim_surrogate.h) for a batch: the
+ * label and CT slices on each env's output pixel grid (Fig. 2: the slices
+ * the simulators map to images).  out: DEVICE [B][out_h][out_w][8] BF16,
+ * channels (label / 4, clamp(HU / 1000, -1, 3), inside-fan flag, 0 x 5).
+ * Curvilinear probes: the scan-conversion grid; linear: the beam grid
+ * (row = sample, column = line).  Every env of the batch must have the
+ * same output size.  Same voxel-coordinate path as the render. */
+US_API us_status us_sim_sample_slices(us_sim* sim, const us_env* envs, int32_t B, const float* poses, uint16_t* out,
+                                      void* stream);
+
 /* Wait for `stream` and read the sticky device error word: US_OK, or
  * US_ERR_INVALID_ARG if a pose had a non-finite entry (that frame renders
  * as water).  Clears the word. */

@@ -83,6 +83,66 @@ US_API us_status us_convT2x2_wgrad(const uint16_t* x, int32_t x_cs, int32_t x_co
                                    int32_t dy_co, float* g4, int32_t B, int32_t H, int32_t W, int32_t Cin,
                                    int32_t Cout, uint32_t* err, void* stream);
 
+/* ---- the surrogate network ---------------------------------------------
+ * Encoder-decoder with skip connections (a U-Net as in App. B.2's
+ * learning-based simulator; the figure giving its exact widths is not in
+ * the text, this layer list is the library's reading):
+ *   level l = 0..3 has c 2^l channels (c = base_channels);
+ *   enc0: conv3x3(8 -> c), conv3x3(c -> c) -> e0;
+ *   enc l: conv3x3 stride 2 (c_{l-1} -> c_l), conv3x3, conv3x3 -> e_l;
+ *   dec l = 2..0: convT2x2(c_{l+1} -> c_l), concat [up, e_l],
+ *                 conv3x3(2 c_l -> c_l), conv3x3(c_l -> c_l);
+ *   head: 1x1 conv (c -> 1) + sigmoid; every conv / convT followed by ReLU.
+ * Input: [B][H][W][8] BF16 (channels: label / 4, clamp(HU / 1000, -1, 3),
+ * inside-fan mask, 5 zeros).  Output: [B][H][W] FP32 in (0, 1), the
+ * log-compressed frame.  Loss per frame L1 + (1 - SSIM) (Wang et al. 2004,
+ * 11 x 11 Gaussian window, sigma 1.5, C1 = 0.01^2, C2 = 0.03^2, valid
+ * region), batch mean; the paper's pix2pix training uses the L1 term.
+ * Adam (Kingma & Ba) on FP32 master weights; BF16 copies feed the tensor
+ * cores.  Parameter vector (FP32): per layer in the order above, weights
+ * ([Cout][3][3][Cin], convT [(2 dy + dx) Cout + co][Cin], head [c]) then
+ * bias. */
+typedef struct {
+  int32_t base_channels;  /* c: 16, 32, 48 or 64 */
+  int32_t height, width;  /* multiples of 8, >= 16 */
+  int32_t max_batch;      /* activations are allocated for this many frames */
+  float lr, beta1, beta2, eps;
+} us_surr_config;
+
+typedef struct us_surr us_surr;
+
+/* parameter segments in order (each layer: weights, then bias): offset,
+ * size and fan-in (0 for biases), so that a caller can draw the initial
+ * parameters.  Returns the number of segments (-1 on a bad config or if
+ * max_segs is too small); NULL arrays just return the count.  Host only. */
+US_API int32_t us_surr_param_segments(const us_surr_config* cfg, int32_t max_segs, int64_t* offsets,
+                                      int64_t* sizes, int32_t* fan_in);
+/* number of FP32 parameters of the network, or -1 for a bad config */
+US_API int64_t us_surr_num_params(const us_surr_config* cfg);
+/* init_params: HOST, us_surr_num_params floats (copied). */
+US_API us_status us_surr_create(const us_surr_config* cfg, const float* init_params, us_surr** out);
+US_API void us_surr_destroy(us_surr* s);
+US_API const char* us_surr_last_error(const us_surr* s);
+/* y[B][H][W] = net(x); x, y DEVICE. */
+US_API us_status us_surr_forward(us_surr* s, const uint16_t* x, float* y, int32_t B, void* stream);
+/* One training step on (x, target): forward, loss, backward, and (update =
+ * 1) an Adam update.  loss_out: DEVICE [1 + 2B]: batch loss, per-frame L1,
+ * per-frame SSIM (before the update). */
+US_API us_status us_surr_train_step(us_surr* s, const uint16_t* x, const float* target, int32_t B, float* loss_out,
+                                    int32_t update, void* stream);
+/* per-frame L1 and SSIM of any prediction: out DEVICE [1 + 2B] as above */
+US_API us_status us_surr_metrics(us_surr* s, const float* pred, const float* target, int32_t B, float* out,
+                                 void* stream);
+/* parameters / gradients of the last train step, HOST, parameter layout (synchronous) */
+US_API us_status us_surr_get_params(const us_surr* s, float* host_out);
+US_API us_status us_surr_get_grads(us_surr* s, float* host_out);
+/* wait for `stream`; US_ERR_TIMEOUT if a bounded tensor-core wait ran out */
+US_API us_status us_surr_check(us_surr* s, void* stream);
+/* checkpoint: config, step, parameters, Adam moments, CRC32; resuming
+ * reproduces the next step exactly */
+US_API us_status us_surr_save(const us_surr* s, const char* path);
+US_API us_status us_surr_load(us_surr* s, const char* path);
+
 #ifdef __cplusplus
 }
 #endif

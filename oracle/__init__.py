@@ -8,8 +8,8 @@ CPU-baseline leg of ``bench.py``; never by the product path.
   first use (or by ``build()``) with ``-ffp-contract=off``.
 * ``brute.py`` (O2): pure-Python restatement on tiny inputs (direct sums,
   full 2-D PSF, its own Philox and Box-Muller).
-* ``surrogate_ref.py`` (O3): FP64 numpy convolution / loss / optimiser
-  references for the learned surrogate.
+* ``surrogate_ref.py`` (O3): PyTorch CPU float64 network / loss / optimiser
+  reference of the learned surrogate.
 
 Nothing here shares code with the CUDA path.  The synthetic inputs come
 from ``paper_2507_01152_gb300.scene``, which holds none of the method.
@@ -103,6 +103,8 @@ def lib():
             L.oracle_touched_voxels.restype = C.c_int64
             L.oracle_sample_coords.argtypes = [C.POINTER(OrProbe), C.c_void_p, C.c_float, C.c_int,
                                                C.c_int, C.c_void_p]
+            L.oracle_sample_slice.argtypes = [C.POINTER(OrVolume), C.POINTER(OrProbe), C.c_void_p, C.c_void_p]
+            L.oracle_sample_slice.restype = C.c_int
             _lib = L
     return _lib
 
@@ -245,3 +247,14 @@ def touched_voxels(volumes, probes, envs, poses):
     P = np.ascontiguousarray(poses, np.float32).reshape(B, 12)
     tot = lib().oracle_touched_voxels(vd, len(vols), pd, _ptr(envs), B, _ptr(P), _ptr(per))
     return int(tot), per
+
+
+def sample_slice(labels, hu, voxel_mm, probe, pose):
+    """surrogate input of one env: [out_h][out_w][3] = (label / 4,
+    clamp(HU / 1000, -1, 3), inside-fan flag)"""
+    vol = _Vol(labels, hu, voxel_mm)
+    out = np.zeros((probe.out_h, probe.out_w, 3))
+    pr = or_probe(probe)
+    M = np.ascontiguousarray(pose, np.float32).reshape(12)
+    lib().oracle_sample_slice(C.byref(vol.desc), C.byref(pr), _ptr(M), _ptr(out))
+    return out

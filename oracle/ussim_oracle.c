@@ -546,3 +546,59 @@ void oracle_sample_coords(const or_probe* p, const float* pose, float voxel_mm, 
                           float u[3]) {
   or_sample_voxel_coords(p, pose, (float)(1.0 / (double)voxel_mm), line, sample, u);
 }
+
+
+/* Surrogate input on the output pixel grid (the learned simulator maps the
+ * CT / label slice to the image, Sec. 4; App. B.2): per output pixel, the
+ * nearest label / 4, clamp(trilinear HU / 1000, -1, 3), and an inside-fan
+ * flag.  Curvilinear: pixel centres of the scan-conversion grid, in the
+ * probe frame (apex coordinates shifted by -r0), computed in FP64 and
+ * rounded to FP32 once; linear: the beam grid (row = sample, column =
+ * line).  The voxel coordinate then follows the same FP32 path as the
+ * beam samples.  out: [out_h][out_w][3]. */
+int oracle_sample_slice(const or_volume* vol, const or_probe* p, const float* pose, double* out) {
+  const int W = p->out_w, H = p->out_h, NL = p->n_lines, NS = p->n_samples;
+  const float inv_h = (float)(1.0 / (double)vol->voxel_mm);
+  or_derived d;
+  or_derive(p, &d);
+  for (int r = 0; r < H; ++r) {
+    for (int c = 0; c < W; ++c) {
+      float x, z;
+      double mask = 1.0;
+      if (p->kind == 0) {
+        x = (float)(((double)c - 0.5 * (double)(NL - 1)) * (double)p->pitch_mm);
+        z = (float)r * (float)((double)p->depth_mm / (double)NS);
+      } else {
+        double r0 = p->radius_mm, D = p->depth_mm;
+        double half = 0.5 * (double)p->fan_deg * M_PI / 180.0;
+        double xmax = (r0 + D) * sin(half), xmin = -xmax;
+        double zmin = r0 * cos(half), zmax = r0 + D;
+        double xa = xmin + (c + 0.5) * (xmax - xmin) / W;
+        double za = zmin + (r + 0.5) * (zmax - zmin) / H;
+        double fl = atan2(xa, za) / d.dtheta + 0.5 * (NL - 1);
+        double fs = (hypot(xa, za) - r0) / d.dr;
+        mask = (fl >= 0 && fl <= NL - 1 && fs >= 0 && fs <= NS - 1) ? 1.0 : 0.0;
+        x = (float)xa;
+        z = (float)(za - r0);
+      }
+      float u[3];
+      for (int k = 0; k < 3; ++k) {
+        float a = pose[k * 4 + 0] * x;
+        float b = pose[k * 4 + 2] * z;
+        float q = a + b;
+        float pc = q + pose[k * 4 + 3];
+        u[k] = pc * inv_h;
+      }
+      int64_t idx = or_nearest(vol, u);
+      double lab = idx >= 0 ? (double)vol->labels[idx] : 0.0;
+      double hu = or_trilinear_hu(vol, u) / 1000.0;
+      if (hu < -1.0) hu = -1.0;
+      if (hu > 3.0) hu = 3.0;
+      double* o = out + ((int64_t)r * W + c) * 3;
+      o[0] = lab / 4.0;
+      o[1] = hu;
+      o[2] = mask;
+    }
+  }
+  return 0;
+}

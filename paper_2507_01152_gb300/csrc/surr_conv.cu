@@ -366,11 +366,14 @@ cudaError_t gemm_bn(int bn, const Ld& ld, const Ep& ep, int M, int N, int K, uns
     case 128: return launch_umma_gemm<128>(ld, ep, M, N, K, err, st, splits);
     case 64: return launch_umma_gemm<64>(ld, ep, M, N, K, err, st, splits);
     case 32: return launch_umma_gemm<32>(ld, ep, M, N, K, err, st, splits);
+    case 16: return launch_umma_gemm<16>(ld, ep, M, N, K, err, st, splits);
     default: return cudaErrorInvalidValue;
   }
 }
 
-int pick_bn(int N) { return (N % 256 == 0) ? 256 : (N % 128 == 0) ? 128 : (N % 64 == 0) ? 64 : (N % 32 == 0) ? 32 : 0; }
+int pick_bn(int N) {
+  return (N % 256 == 0) ? 256 : (N % 128 == 0) ? 128 : (N % 64 == 0) ? 64 : (N % 32 == 0) ? 32 : (N % 16 == 0) ? 16 : 0;
+}
 
 // split the pixel reduction of a weight gradient so that the grid covers
 // about four waves of the GPU

@@ -30,7 +30,7 @@ constexpr uint32_t gemm_smem_bytes() {
 }
 template <int BN>
 constexpr uint32_t tmem_cols() {
-  return BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));
+  return BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));   // TMEM allocations: powers of 2, >= 32
 }
 
 // Loader:   void load(uint8_t* a_stage, uint8_t* b_stage, int m0, int n0, int kt, int tid)

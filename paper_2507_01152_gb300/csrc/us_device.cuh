@@ -36,6 +36,8 @@ struct DevProbe {
   const float* w_lat;        // [2 k_lat + 1]
   const float2* lut;         // curvilinear: [out_h * out_w] (fl, fs); fl < 0 outside
   const DevTissue* tissue;   // [n_labels]
+  const float* px;           // curvilinear: [out_w] probe-frame x of output pixel columns
+  const float* pz;           // curvilinear: [out_h] probe-frame z of output pixel rows
 };
 
 // incidence stencil extents for a (volume, probe) pair: axial half window W

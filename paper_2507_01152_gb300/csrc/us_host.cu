@@ -118,8 +118,10 @@ us_status build_probe_tables(us_sim* s, ProbeHost& ph) {
     tis[i].t1 = n1_threshold((double)t.mu1);
   }
   // scan-conversion map (curvilinear): fractional (line, sample) of each
-  // output pixel centre over the fan's bounding box, -1 outside the fan
+  // output pixel centre over the fan's bounding box, -1 outside the fan;
+  // and the probe-frame coordinates of the pixel centres (surrogate input)
   std::vector<float2> lut;
+  std::vector<float> px, pz;
   if (p.kind == 1) {
     const int W = p.out_w, H = p.out_h;
     lut.resize((size_t)W * H);
@@ -127,6 +129,10 @@ us_status build_probe_tables(us_sim* s, ProbeHost& ph) {
     const double half = 0.5 * (double)p.fan_deg * M_PI / 180.0;
     const double xmax = (r0 + D) * std::sin(half), xmin = -xmax;
     const double zmin = r0 * std::cos(half), zmax = r0 + D;
+    px.resize(W);
+    pz.resize(H);
+    for (int c = 0; c < W; ++c) px[c] = (float)(xmin + (c + 0.5) * (xmax - xmin) / W);
+    for (int r = 0; r < H; ++r) pz[r] = (float)(zmin + (r + 0.5) * (zmax - zmin) / H - r0);
     for (int r = 0; r < H; ++r)
       for (int c = 0; c < W; ++c) {
         const double x = xmin + (c + 0.5) * (xmax - xmin) / W;
@@ -143,6 +149,9 @@ us_status build_probe_tables(us_sim* s, ProbeHost& ph) {
   if ((e = upload(&ph.d_wlat, wlat.data(), wlat.size())) != cudaSuccess) return cuda_fail(s, e, "upload taps");
   if ((e = upload(&ph.d_tissue, tis.data(), tis.size())) != cudaSuccess) return cuda_fail(s, e, "upload tissue");
   if (!lut.empty() && (e = upload(&ph.d_lut, lut.data(), lut.size())) != cudaSuccess) return cuda_fail(s, e, "upload lut");
+  if (!px.empty() && ((e = upload(&ph.d_px, px.data(), px.size())) != cudaSuccess ||
+                      (e = upload(&ph.d_pz, pz.data(), pz.size())) != cudaSuccess))
+    return cuda_fail(s, e, "upload pixel grid");
   return US_OK;
 }
 
@@ -167,6 +176,8 @@ DevProbe device_probe(const ProbeHost& ph) {
   d.w_lat = ph.d_wlat;
   d.lut = ph.d_lut;
   d.tissue = ph.d_tissue;
+  d.px = ph.d_px;
+  d.pz = ph.d_pz;
   return d;
 }
 
@@ -226,6 +237,7 @@ us_status get_plan(us_sim* s, const us_env* envs, int B, us_plan** out) {
                    [&](const EnvItem& a, const EnvItem& b) { return cost(a) > cost(b); });
   if (B > 0) {
     cudaError_t e = upload(&pl.d_items, pl.items_sorted.data(), pl.items_sorted.size());
+    if (e == cudaSuccess) e = upload(&pl.d_items_batch, pl.items_batch.data(), pl.items_batch.size());
     if (e != cudaSuccess) return cuda_fail(s, e, "upload work list");
   }
   auto ins = s->plans.emplace(std::move(key), std::move(pl));
@@ -298,11 +310,14 @@ void free_sim(us_sim* s) {
     cudaFree(ph.d_wlat);
     cudaFree(ph.d_lut);
     cudaFree(ph.d_tissue);
+    cudaFree(ph.d_px);
+    cudaFree(ph.d_pz);
   }
   for (auto* d : s->d_pair_D) cudaFree(d);
   for (auto& kv : s->plans) {
     drop_graph(kv.second);
     cudaFree(kv.second.d_items);
+    cudaFree(kv.second.d_items_batch);
   }
   cudaFree(s->d_vols);
   cudaFree(s->d_probes);
@@ -611,6 +626,23 @@ us_status us_sim_render_host(us_sim* s, const us_env* envs, int32_t B, const flo
     return cuda_fail(s, e, "frame copy");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e, "render");
   return US_OK;
+}
+
+us_status us_sim_sample_slices(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint16_t* out,
+                               void* stream) {
+  us_status r = check_render_args(s, envs, B, poses, reinterpret_cast<float*>(out));
+  if (r != US_OK || B == 0) return r;
+  us_plan* pl;
+  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  const us_probe& p0 = s->probes[envs[0].probe_id].desc;
+  for (int b = 1; b < B; ++b) {
+    const us_probe& pb = s->probes[envs[b].probe_id].desc;
+    if (pb.out_w != p0.out_w || pb.out_h != p0.out_h)
+      return fail(s, US_ERR_INVALID_ARG, "sample_slices needs one output size for the whole batch");
+  }
+  RenderParams p = base_params(s, poses, 0, 0, nullptr);
+  cudaError_t e = launch_slice_input(p, pl->d_items_batch, B, p0.out_h, p0.out_w, out, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? US_OK : cuda_fail(s, e, "slice sampling launch");
 }
 
 us_status us_sim_check(us_sim* s, void* stream) {

@@ -22,6 +22,8 @@ struct ProbeHost {
   float* d_wlat = nullptr;
   float2* d_lut = nullptr;
   DevTissue* d_tissue = nullptr;
+  float* d_px = nullptr;
+  float* d_pz = nullptr;
 };
 
 // global scratch of the plain path (one environment at a time)
@@ -62,6 +64,10 @@ cudaError_t fused_prepare(const FusedShape& s);
 cudaError_t fused_max_clusters(const FusedShape& s, int* clusters);
 cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st);
 
+// surrogate input of a batch on the output pixel grid: [B][H][W][8] BF16
+cudaError_t launch_slice_input(const RenderParams& p, const EnvItem* items_batch, int B, int H, int W, void* out,
+                               cudaStream_t st);
+
 // label check at creation: max label of a volume
 cudaError_t max_label(const uint8_t* labels, long long n, unsigned* d_out, cudaStream_t st);
 
@@ -72,6 +78,7 @@ struct us_plan {
   std::vector<ussim::EnvItem> items_sorted;  // fused order: costliest first
   std::vector<ussim::EnvItem> items_batch;   // caller order
   ussim::EnvItem* d_items = nullptr;         // device copy of items_sorted
+  ussim::EnvItem* d_items_batch = nullptr;   // device copy of items_batch
   long long frame_floats = 0, beam_elems = 0;
   // captured [work-counter reset + fused launch], re-parameterised per call
   cudaGraph_t graph = nullptr;

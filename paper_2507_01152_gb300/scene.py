@@ -409,3 +409,17 @@ def workload_paper_replica(B=100):
     return Workload("paper_replica_linear_200x150_100env", [(spec, lab, hu)],
                     [linear_probe(150, 200, 100.0, 0.5)], np.zeros((B, 2), np.int32),
                     dorsal_poses(spec, B, 2001), seed=0x5EED0004)
+
+
+# --------------------------------------------------------------------------
+# surrogate inputs
+# --------------------------------------------------------------------------
+
+def surrogate_init(sizes, fan_in, seed: int) -> np.ndarray:
+    """Initial network parameters: He-normal weights N(0, 2 / fan_in),
+    zero biases (fan_in 0), segment by segment, seeded."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for n, f in zip(sizes, fan_in):
+        out.append(rng.normal(0.0, math.sqrt(2.0 / f), int(n)) if f > 0 else np.zeros(int(n)))
+    return np.concatenate(out).astype(np.float32)

@@ -58,7 +58,13 @@ class us_tuning(C.Structure):
     _fields_ = [("cluster_size", C.c_int32), ("warps_per_cta", C.c_int32), ("use_graph", C.c_int32)]
 
 
-# name -> (restype, argtypes) for every entry point of include/ussim.h
+class us_surr_config(C.Structure):
+    _fields_ = [("base_channels", C.c_int32), ("height", C.c_int32), ("width", C.c_int32),
+                ("max_batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float)]
+
+
+# name -> (restype, argtypes) for every entry point of include/*.h
 _P = C.c_void_p
 _I = C.c_int32
 SIGNATURES = {
@@ -74,6 +80,7 @@ SIGNATURES = {
                                       C.c_int32, _P]),
     "us_sim_render_host": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
     "us_sim_check": (C.c_int, [_P, _P]),
+    "us_sim_sample_slices": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
     "us_sim_get_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
     "us_sim_set_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
     "us_sim_autotune": (C.c_int, [_P, _P, C.c_int32, _P, _P, C.c_char_p, _P]),
@@ -86,6 +93,19 @@ SIGNATURES = {
     "us_convT2x2_fwd": (C.c_int, [_P, _I, _I, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _I, _P, _P]),
     "us_convT2x2_dgrad": (C.c_int, [_P, _I, _I, _P, _P, _I, _I, _P, _I, _I, _I, _I, _I, _I, _I, _I, _P, _P]),
     "us_convT2x2_wgrad": (C.c_int, [_P, _I, _I, _P, _I, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
+    "us_surr_param_segments": (C.c_int32, [C.POINTER(us_surr_config), C.c_int32, _P, _P, _P]),
+    "us_surr_num_params": (C.c_int64, [C.POINTER(us_surr_config)]),
+    "us_surr_create": (C.c_int, [C.POINTER(us_surr_config), _P, C.POINTER(_P)]),
+    "us_surr_destroy": (None, [_P]),
+    "us_surr_last_error": (C.c_char_p, [_P]),
+    "us_surr_forward": (C.c_int, [_P, _P, _P, _I, _P]),
+    "us_surr_train_step": (C.c_int, [_P, _P, _P, _I, _P, _I, _P]),
+    "us_surr_metrics": (C.c_int, [_P, _P, _P, _I, _P, _P]),
+    "us_surr_get_params": (C.c_int, [_P, _P]),
+    "us_surr_get_grads": (C.c_int, [_P, _P]),
+    "us_surr_check": (C.c_int, [_P, _P]),
+    "us_surr_save": (C.c_int, [_P, C.c_char_p]),
+    "us_surr_load": (C.c_int, [_P, C.c_char_p]),
 }
 
 _lib = None
@@ -256,6 +276,12 @@ class Sim:
     def check(self, stream=None):
         self._check(self._lib.us_sim_check(self.h, _stream_handle(stream)))
 
+    def sample_slices(self, envs, poses, out, stream=None, envs_c=None):
+        """surrogate input [B][H][W][8] bf16 (out: torch bfloat16 CUDA tensor)"""
+        B = poses.shape[0]
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_sample_slices(self.h, e, B, _ptr(poses), _ptr(out), _stream_handle(stream)))
+
     def get_tuning(self) -> dict:
         t = us_tuning()
         self._check(self._lib.us_sim_get_tuning(self.h, C.byref(t)))
@@ -272,3 +298,81 @@ class Sim:
         self._check(self._lib.us_sim_autotune(self.h, make_envs(envs), B, _ptr(poses), _ptr(frames),
                                               cache_path.encode() if cache_path else None,
                                               _stream_handle(stream)))
+
+
+class Surrogate:
+    """Handle of the learned surrogate (include/ussim_surrogate.h)."""
+
+    def __init__(self, base_channels, height, width, max_batch, init_params, lr=2e-4, beta1=0.9, beta2=0.999,
+                 eps=1e-8):
+        L = load()
+        self.cfg = us_surr_config(base_channels, height, width, max_batch, lr, beta1, beta2, eps)
+        n = L.us_surr_num_params(C.byref(self.cfg))
+        init = np.ascontiguousarray(init_params, np.float32)
+        if n < 0 or init.size != n:
+            raise UsError(US_ERR_INVALID_ARG, f"expected {n} parameters, got {init.size}")
+        h = C.c_void_p()
+        st = L.us_surr_create(C.byref(self.cfg), init.ctypes.data, C.byref(h))
+        if st != US_OK:
+            raise UsError(st, "us_surr_create")
+        self.h, self.n_params, self._lib = h, n, L
+
+    @staticmethod
+    def segments(base_channels, height=256, width=256):
+        """(offsets, sizes, fan_in) of the parameter segments"""
+        L = load()
+        cfg = us_surr_config(base_channels, height, width, 1, 1e-3, 0.9, 0.999, 1e-8)
+        n = L.us_surr_param_segments(C.byref(cfg), 0, None, None, None)
+        off, size, fan = np.zeros(n, np.int64), np.zeros(n, np.int64), np.zeros(n, np.int32)
+        L.us_surr_param_segments(C.byref(cfg), n, off.ctypes.data, size.ctypes.data, fan.ctypes.data)
+        return off, size, fan
+
+    @staticmethod
+    def num_params(base_channels, height=256, width=256):
+        cfg = us_surr_config(base_channels, height, width, 1, 1e-3, 0.9, 0.999, 1e-8)
+        return load().us_surr_num_params(C.byref(cfg))
+
+    def _check(self, st):
+        if st != US_OK:
+            raise UsError(st, self._lib.us_surr_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.us_surr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, x, y, stream=None):
+        self._check(self._lib.us_surr_forward(self.h, _ptr(x), _ptr(y), x.shape[0], _stream_handle(stream)))
+
+    def train_step(self, x, target, loss_out, update=True, stream=None):
+        self._check(self._lib.us_surr_train_step(self.h, _ptr(x), _ptr(target), x.shape[0], _ptr(loss_out),
+                                                 1 if update else 0, _stream_handle(stream)))
+
+    def metrics(self, pred, target, out, stream=None):
+        self._check(self._lib.us_surr_metrics(self.h, _ptr(pred), _ptr(target), pred.shape[0], _ptr(out),
+                                              _stream_handle(stream)))
+
+    def params(self):
+        out = np.zeros(self.n_params, np.float32)
+        self._check(self._lib.us_surr_get_params(self.h, out.ctypes.data))
+        return out
+
+    def grads(self):
+        out = np.zeros(self.n_params, np.float32)
+        self._check(self._lib.us_surr_get_grads(self.h, out.ctypes.data))
+        return out
+
+    def check(self, stream=None):
+        self._check(self._lib.us_surr_check(self.h, _stream_handle(stream)))
+
+    def save(self, path):
+        self._check(self._lib.us_surr_save(self.h, path.encode()))
+
+    def load(self, path):
+        self._check(self._lib.us_surr_load(self.h, path.encode()))
