@@ -59,7 +59,28 @@ struct ConvFwdLoader {
   const bf16* w;   // [N][K]
   Grid in, out;
   int Cin, K, N, stride, M, bn;
-  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+  struct State {
+    int pix[8], y0[8], x0[8];   // per staged row: first pixel of its image (-1: row past M), yo*s-1, xo*s-1
+  };
+  __device__ void prepare(State& st, int m0, int, int tid) const {
+    int kc, r0;
+    a_chunk(tid, kc, r0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int m = m0 + r0 + 16 * i;
+      if (m < M) {
+        int b, yo, xo;
+        out.pix(m, b, yo, xo);
+        st.pix[i] = b * in.H * in.W;
+        st.y0[i] = yo * stride - 1;
+        st.x0[i] = xo * stride - 1;
+      } else {
+        st.pix[i] = -1;
+        st.y0[i] = st.x0[i] = 0;
+      }
+    }
+  }
+  __device__ void load(const State& st, uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
     int kc, r0;
     a_chunk(tid, kc, r0);
     const int k = kt * kBK + kc * 8;
@@ -68,21 +89,17 @@ struct ConvFwdLoader {
     const int ky = tap / 3, kx = tap - ky * 3;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int r = r0 + 16 * i, m = m0 + r;
+      const int r = r0 + 16 * i;
       const void* src = x.p;
       uint32_t bytes = 0;
-      if (kval && m < M) {
-        int b, yo, xo;
-        out.pix(m, b, yo, xo);
-        const int yi = yo * stride - 1 + ky, xi = xo * stride - 1 + kx;
-        if ((unsigned)yi < (unsigned)in.H && (unsigned)xi < (unsigned)in.W) {
-          src = x.p + ((size_t)(b * in.H + yi) * in.W + xi) * x.cs + x.co + ci;
-          bytes = 16;
-        }
+      const int yi = st.y0[i] + ky, xi = st.x0[i] + kx;
+      if (kval && st.pix[i] >= 0 && (unsigned)yi < (unsigned)in.H && (unsigned)xi < (unsigned)in.W) {
+        src = x.p + ((size_t)st.pix[i] + (size_t)yi * in.W + xi) * x.cs + x.co + ci;
+        bytes = 16;
       }
       cp_async16(as + tile_off(r, kc, kBK), src, bytes);
     }
-    for (int c = tid; c < bn * 8; c += kThreads) {
+    for (int c = tid; c < bn * 8; c += kProducers) {
       const int r = (c & 7) + ((c >> 6) << 3), kc2 = (c >> 3) & 7;
       const int n = n0 + r, kk = kt * kBK + kc2 * 8;
       const bool v = n < N && kk < K;
@@ -115,7 +132,28 @@ struct ConvDgradLoader {
   const bf16* wd;   // [Cin][9 Cout]: wd[ci][(ky,kx,co)] = W[co][ky][kx][ci]
   Grid in, out;     // in = dX grid (forward input), out = dY grid
   int Cout, K, N, stride, M, bn;
-  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+  struct State {
+    int pix[8], yi[8], xi[8];   // per staged row: first pixel of its dY image (-1: past M), and its dX pixel
+  };
+  __device__ void prepare(State& st, int m0, int, int tid) const {
+    int kc, r0;
+    a_chunk(tid, kc, r0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int m = m0 + r0 + 16 * i;
+      if (m < M) {
+        int b, yi, xi;
+        in.pix(m, b, yi, xi);
+        st.pix[i] = b * out.H * out.W;
+        st.yi[i] = yi;
+        st.xi[i] = xi;
+      } else {
+        st.pix[i] = -1;
+        st.yi[i] = st.xi[i] = 0;
+      }
+    }
+  }
+  __device__ void load(const State& st, uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
     int kc, r0;
     a_chunk(tid, kc, r0);
     const int k = kt * kBK + kc * 8;
@@ -124,24 +162,21 @@ struct ConvDgradLoader {
     const int ky = tap / 3, kx = tap - ky * 3;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int r = r0 + 16 * i, m = m0 + r;
+      const int r = r0 + 16 * i;
       const void* src = dy.p;
       uint32_t bytes = 0;
-      if (kval && m < M) {
-        int b, yi, xi;
-        in.pix(m, b, yi, xi);
-        const int ys = yi + 1 - ky, xs = xi + 1 - kx;
-        if (ys >= 0 && xs >= 0 && (ys % stride) == 0 && (xs % stride) == 0) {
-          const int yo = ys / stride, xo = xs / stride;
-          if (yo < out.H && xo < out.W) {
-            src = dy.p + ((size_t)(b * out.H + yo) * out.W + xo) * dy.cs + dy.co + co;
-            bytes = 16;
-          }
+      const int ys = st.yi[i] + 1 - ky, xs = st.xi[i] + 1 - kx;
+      if (kval && st.pix[i] >= 0 && ys >= 0 && xs >= 0) {
+        const bool div = stride == 1 || (((ys | xs) & 1) == 0);
+        const int yo = stride == 1 ? ys : (ys >> 1), xo = stride == 1 ? xs : (xs >> 1);
+        if (div && yo < out.H && xo < out.W) {
+          src = dy.p + ((size_t)st.pix[i] + (size_t)yo * out.W + xo) * dy.cs + dy.co + co;
+          bytes = 16;
         }
       }
       cp_async16(as + tile_off(r, kc, kBK), src, bytes);
     }
-    for (int c = tid; c < bn * 8; c += kThreads) {
+    for (int c = tid; c < bn * 8; c += kProducers) {
       const int r = (c & 7) + ((c >> 6) << 3), kc2 = (c >> 3) & 7;
       const int n = n0 + r, kk = kt * kBK + kc2 * 8;
       const bool v = n < N && kk < K;
@@ -185,7 +220,9 @@ struct ConvTFwdLoader {
   View x;
   const bf16* w4;   // [4 Cout][Cin]
   int Cin, N, M, bn;
-  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+  struct State {};
+  __device__ void prepare(State&, int, int, int) const {}
+  __device__ void load(const State&, uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
     int kc, r0;
     a_chunk(tid, kc, r0);
     const int k = kt * kBK + kc * 8;
@@ -196,7 +233,7 @@ struct ConvTFwdLoader {
       cp_async16(as + tile_off(r, kc, kBK), v ? (const void*)(x.p + (size_t)m * x.cs + x.co + k) : (const void*)x.p,
                  v ? 16u : 0u);
     }
-    for (int c = tid; c < bn * 8; c += kThreads) {
+    for (int c = tid; c < bn * 8; c += kProducers) {
       const int r = (c & 7) + ((c >> 6) << 3), kc2 = (c >> 3) & 7;
       const int n = n0 + r, kk = kt * kBK + kc2 * 8;
       const bool v = n < N && kk < Cin;
@@ -235,27 +272,40 @@ struct ConvTDgradLoader {
   const bf16* w4t;   // [Cin][4 Cout]
   Grid in;           // dX grid (convT input); dY is 2H x 2W
   int Cout, K, N, M, bn;
-  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+  struct State {
+    int base[8];     // per staged row: dY pixel index of (2y, 2x), -1 past M
+  };
+  __device__ void prepare(State& st, int m0, int, int tid) const {
+    int kc, r0;
+    a_chunk(tid, kc, r0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int m = m0 + r0 + 16 * i;
+      if (m < M) {
+        int b, yy, xx;
+        in.pix(m, b, yy, xx);
+        st.base[i] = (b * 2 * in.H + 2 * yy) * (2 * in.W) + 2 * xx;
+      } else {
+        st.base[i] = -1;
+      }
+    }
+  }
+  __device__ void load(const State& st, uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
     int kc, r0;
     a_chunk(tid, kc, r0);
     const int k = kt * kBK + kc * 8;
     const bool kval = k < K;
     const int d = kval ? k / Cout : 0, co = k - d * Cout;
-    const int dyy = d >> 1, dxx = d & 1;
+    const int off = (d >> 1) * (2 * in.W) + (d & 1);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int r = r0 + 16 * i, m = m0 + r;
-      const void* src = dy.p;
-      uint32_t bytes = 0;
-      if (kval && m < M) {
-        int b, yy, xx;
-        in.pix(m, b, yy, xx);
-        src = dy.p + ((size_t)(b * 2 * in.H + 2 * yy + dyy) * (2 * in.W) + 2 * xx + dxx) * dy.cs + dy.co + co;
-        bytes = 16;
-      }
-      cp_async16(as + tile_off(r, kc, kBK), src, bytes);
+      const int r = r0 + 16 * i;
+      const bool v = kval && st.base[i] >= 0;
+      cp_async16(as + tile_off(r, kc, kBK),
+                 v ? (const void*)(dy.p + ((size_t)st.base[i] + off) * dy.cs + dy.co + co) : (const void*)dy.p,
+                 v ? 16u : 0u);
     }
-    for (int c = tid; c < bn * 8; c += kThreads) {
+    for (int c = tid; c < bn * 8; c += kProducers) {
       const int r = (c & 7) + ((c >> 6) << 3), kc2 = (c >> 3) & 7;
       const int n = n0 + r, kk = kt * kBK + kc2 * 8;
       const bool v = n < N && kk < K;
@@ -323,7 +373,9 @@ struct WgradLoader {
   SrcA a;
   SrcB b;
   int P, bn;   // pixels in the reduction
-  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+  struct State {};
+  __device__ void prepare(State&, int, int, int) const {}
+  __device__ void load(const State&, uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
     const int p0 = kt * kBK;
     {   // A: 16 row groups x 8 pixel groups = 128 blocks, one per thread
       const int rg = tid >> 3, pg = tid & 7;
@@ -334,7 +386,7 @@ struct WgradLoader {
 #pragma unroll
       for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(as + tile_off(rg * 8 + c, pg, kBK)) = out[c];
     }
-    for (int blk = tid; blk < bn; blk += kThreads) {   // B: bn/8 row groups x 8 pixel groups
+    for (int blk = tid; blk < bn; blk += kProducers) {   // B: bn/8 row groups x 8 pixel groups
       const int rg = blk >> 3, pg = blk & 7;
       uint4 in[8], out[8];
 #pragma unroll

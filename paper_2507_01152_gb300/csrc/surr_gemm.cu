@@ -15,14 +15,16 @@ struct RowMajorLoader {
   const __nv_bfloat16* A;
   const __nv_bfloat16* B;
   int M, N, K, bn;
-  __device__ void load(uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
-    for (int c = tid; c < kBM * 8; c += kThreads) {
+  struct State {};
+  __device__ void prepare(State&, int, int, int) const {}
+  __device__ void load(const State&, uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
+    for (int c = tid; c < kBM * 8; c += kProducers) {
       const int r = (c & 7) + ((c >> 6) << 3), kc = (c >> 3) & 7;
       const int m = m0 + r, k = kt * kBK + kc * 8;
       const bool v = m < M && k < K;
       cp_async16(as + tile_off(r, kc, kBK), v ? (const void*)(A + (size_t)m * K + k) : (const void*)A, v ? 16u : 0u);
     }
-    for (int c = tid; c < bn * 8; c += kThreads) {
+    for (int c = tid; c < bn * 8; c += kProducers) {
       const int r = (c & 7) + ((c >> 6) << 3), kc = (c >> 3) & 7;
       const int n = n0 + r, k = kt * kBK + kc * 8;
       const bool v = n < N && k < K;

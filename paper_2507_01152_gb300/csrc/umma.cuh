@@ -66,18 +66,31 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // ------------------------------------------------------- descriptors
-// Shared-memory matrix descriptor, K-major operand without swizzle.  The
-// tile is built from 8-row x 16-byte core matrices (rows 16 B apart);
-// `lbo` = byte distance between core matrices adjacent along K, `sbo` =
-// byte distance between 8-row groups.  Bits: start address >> 4 [0,14),
-// LBO >> 4 [16,30), SBO >> 4 [32,46), descriptor version 1 [46,48),
-// layout type (0 = no swizzle) [61,64).
+// Shared-memory matrix descriptor, K-major operand.  Bits: start address
+// >> 4 [0,14), LBO >> 4 [16,30), SBO >> 4 [32,46), descriptor version 1
+// [46,48), layout type [61,64) (0 = no swizzle, 2 = 128-byte swizzle).
+// No swizzle: 8-row x 16-byte core matrices (rows 16 B apart); `lbo` =
+// distance between core matrices adjacent along K, `sbo` = between 8-row
+// groups.
 __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
+  return d;
+}
+// 128-byte swizzle, K-major: rows of 64 BF16 (128 B) stored contiguously,
+// 8-row atoms of 1024 B (SBO), the 16-byte chunk c of row r at chunk
+// position c ^ (r mod 8); atoms 1024-byte aligned.  A K step of 16
+// elements inside the atom advances the start address by 32 B.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                  // LBO (unused by this layout), encoded 1
+  d |= (uint64_t)(1024 >> 4) << 32;        // SBO = 1024 B between 8-row atoms
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
   return d;
 }
 
@@ -117,12 +130,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// byte offset of 16-byte chunk `kc` of row `r` in a K-major no-swizzle tile
-// whose rows hold `bk` elements: core matrices of 8 rows x 16 B, the bk/8
-// core matrices of an 8-row group adjacent along K (LBO = 128 B), 8-row
-// groups bk*16 B apart (SBO)
-__host__ __device__ constexpr uint32_t tile_off(int r, int kc, int bk) {
-  return (uint32_t)((r >> 3) * (bk * 16) + kc * 128 + (r & 7) * 16);
+// byte offset of 16-byte chunk `kc` (0..7) of row `r` in a K-major tile
+// of 64-element rows in the 128-byte swizzled layout
+__host__ __device__ constexpr uint32_t tile_off(int r, int kc, int /*bk*/) {
+  return (uint32_t)(r * 128 + ((kc ^ (r & 7)) << 4));
 }
 
 }  // namespace umma

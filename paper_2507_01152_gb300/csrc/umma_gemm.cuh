@@ -1,13 +1,22 @@
 // Tile GEMM on the 5th-generation tensor cores:
 //   D[m][n] = sum_k A[m][k] * B[n][k]      (BF16 in, FP32 accumulate in TMEM)
-// One CTA of 128 threads computes a 128 x BN tile.  K advances in 64-wide
-// steps through two shared-memory stages: while the tensor core works on
-// stage s (four 128 x BN x 16 MMAs issued by one thread and committed to
-// the stage's mbarrier), all threads stage the next K step into the other
-// stage with cp.async.  Operands are gathered by a Loader functor, so the
-// same kernel serves plain GEMMs and implicit-GEMM convolutions; the
-// accumulator is read back with tcgen05.ld and handed to an Epilogue
-// functor row by row (thread i of warp w owns tile row 32 w + i).
+//
+// Persistent and warp-specialised.  A CTA owns a sequence of 128 x BN
+// output tiles and runs three roles concurrently:
+//   warps 0-3  producers: gather the operands of each 64-wide K step into
+//              one of the shared-memory stages (cp.async or plain stores),
+//              up to `stages` steps ahead of the tensor core;
+//   warp 4     one thread issues the four 128 x BN x 16 MMAs of a stage and
+//              commits them to the stage's "empty" barrier;
+//   warps 5-8  epilogue: read a finished accumulator with tcgen05.ld and
+//              hand it to the Epilogue functor, while the MMAs of the next
+//              tile accumulate into the other half of a double-buffered
+//              TMEM allocation.
+// Hand-offs use mbarriers: full[s] (producers -> MMA), empty[s] (MMA
+// commit -> producers), tfull[a] (MMA commit -> epilogue), tempty[a]
+// (epilogue -> MMA).  Every wait is bounded; a wait that runs out raises a
+// shared abort flag that all roles check, so the CTA still drains its
+// copies, waits for its MMAs and frees its TMEM.
 #pragma once
 #include "umma.cuh"
 
@@ -15,111 +24,176 @@ namespace ussim {
 namespace umma {
 
 constexpr int kBM = 128, kBK = 64;
-constexpr int kThreads = 128;
+constexpr int kProducers = 128;                     // warps 0-3
+constexpr int kThreads = 288;                       // 4 producer + 1 MMA + 4 epilogue warps
 constexpr uint32_t kTileA = kBM * kBK * 2;          // bytes of one A stage
-constexpr uint32_t kSbo = kBK * 16;                 // 8-row group stride in a stage
-constexpr uint32_t kLbo = 128;                      // K-adjacent core matrices
+constexpr int kLag = 2;                             // producer steps in flight before signalling
+constexpr int kStages = 4;
 
 template <int BN>
 constexpr uint32_t stage_bytes() {
   return kTileA + (uint32_t)BN * kBK * 2;
 }
 template <int BN>
-constexpr uint32_t gemm_smem_bytes() {
-  return 2 * stage_bytes<BN>();
+constexpr uint32_t gemm_smem_bytes() {   // + slack to align the stages to 1024 B (swizzle atoms)
+  return kStages * stage_bytes<BN>() + 1024;
 }
 template <int BN>
-constexpr uint32_t tmem_cols() {
-  return BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));   // TMEM allocations: powers of 2, >= 32
+constexpr uint32_t tmem_cols() {   // one accumulator; TMEM allocations are powers of 2 >= 32
+  return BN <= 32 ? 32u : (BN <= 64 ? 64u : (BN <= 128 ? 128u : 256u));
 }
 
-// Loader:   void load(uint8_t* a_stage, uint8_t* b_stage, int m0, int n0, int kt, int tid)
-//           stages the 128 x 64 A tile rows m0.., and the BN x 64 B tile rows
-//           n0.., K step kt, into the K-major no-swizzle layout (use
-//           tile_off(r, kc, kBK) for 16-byte chunk kc of row r), with cp.async
-//           or plain shared stores; steps past the end of K must load zeros.
-//           With split K (grid.z > 1), CTA z covers steps z*k_tiles .. +k_tiles.
-// Epilogue: void store(int m, int n0, const float* v16, bool valid)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait that also gives up when another role has aborted
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                              unsigned* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicOr(err, kErrWaitTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Loader:   struct State; prepare(State&, m0, n0, tid) once per tile, then
+//           load(const State&, a_stage, b_stage, m0, n0, kt, tid) per K step:
+//           stage the 128 x 64 A tile rows m0.., and the BN x 64 B tile rows
+//           n0.., K step kt (global index), into the K-major 128-byte-swizzled
+//           layout (tile_off(r, kc, kBK) for 16-byte chunk kc of row r); steps past
+//           the end of K must load zeros.  Called by the 128 producer threads.
+// Epilogue: store(int m, int n0, const float* v16, bool valid).
+// Tiles: mt x nt x splits, M fastest; split z covers K steps z*k_tiles ...
 template <int BN, class Loader, class Epilogue>
-__global__ void __launch_bounds__(kThreads) umma_gemm_kernel(Loader ld, Epilogue ep, int M, int k_tiles,
-                                                              unsigned* err) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t bar[2];
-  __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+__global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilogue ep, int M, int mt, int nt,
+                                                                 int n_tiles, int k_tiles, unsigned* err) {
+  constexpr int S = kStages;
   constexpr uint32_t NCOL = tmem_cols<BN>();
   constexpr uint32_t IDESC = idesc_bf16_f32(kBM, BN);
-  uint8_t* stage[2] = {smem, smem + stage_bytes<BN>()};
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  __shared__ uint64_t full[S], empty[S], tfull[2], tempty[2], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
-    tmem_alloc(&tmem_base, NCOL);
+    tmem_alloc(&tmem_base, 2 * NCOL);
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], kProducers);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], kProducers);
+    }
+    mbar_init(&done, 1);
+    abort_flag = 0;
     mbar_init_fence();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-  const int kt0 = blockIdx.z * k_tiles;
 
-  ld.load(stage[0], stage[0] + kTileA, m0, n0, kt0, tid);
-  cp_async_commit();
-  bool ok = true;
-  int t = 0;
-  for (; t < k_tiles; ++t) {
-    const int s = t & 1;
-    if (t + 1 < k_tiles) {
-      // the other stage was read by the MMAs of step t-1: wait for their commit
-      if (t >= 1) ok = ok && mbar_wait(&bar[s ^ 1], ((t - 1) >> 1) & 1);
-      if (ok) ld.load(stage[s ^ 1], stage[s ^ 1] + kTileA, m0, n0, kt0 + t + 1, tid);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+  if (warp < 4) {
+    // ---------------------------------------------------------- producers
+    long long g = 0;   // global K-step counter over this CTA's tiles
+    for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x) {
+      const int z = tile / (mt * nt), rem = tile - z * mt * nt, ni = rem / mt, mi = rem - ni * mt;
+      const int m0 = mi * kBM, n0 = ni * BN, kt0 = z * k_tiles;
+      typename Loader::State st;
+      ld.prepare(st, m0, n0, tid);
+      bool ok = true;
+      for (int t = 0; t < k_tiles; ++t, ++g) {
+        const int s = (int)(g % S);
+        if (g >= S && !wait_or_abort(&empty[s], (uint32_t)((g / S - 1) & 1), &abort_flag, err)) {
+          ok = false;
+          break;
+        }
+        ld.load(st, smem + s * stage_bytes<BN>(), smem + s * stage_bytes<BN>() + kTileA, m0, n0, kt0 + t, tid);
+        cp_async_commit();
+        if (g >= kLag) {
+          cp_async_wait<kLag>();
+          fence_proxy_async();
+          mbar_arrive(&full[(g - kLag) % S]);
+        }
+      }
+      if (!ok) break;
     }
+    cp_async_wait<0>();
     fence_proxy_async();
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a = smem_u32(stage[s]), b = smem_u32(stage[s] + kTileA);
+    for (long long q = g - kLag < 0 ? 0 : g - kLag; q < g; ++q) mbar_arrive(&full[q % S]);
+  } else if (warp == 4) {
+    // ---------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      long long g = 0;
+      int j = 0;   // local tile index
+      for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x, ++j) {
+        const int a = j & 1;
+        if (j >= 2 && !wait_or_abort(&tempty[a], (uint32_t)((j / 2 - 1) & 1), &abort_flag, err)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)a * NCOL;
+        bool ok = true;
+        for (int t = 0; t < k_tiles; ++t, ++g) {
+          const int s = (int)(g % S);
+          if (!wait_or_abort(&full[s], (uint32_t)((g / S) & 1), &abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * stage_bytes<BN>()), sb = sa + kTileA;
 #pragma unroll
-      for (int j = 0; j < kBK / 16; ++j)
-        mma_bf16(tmem, smem_desc_kmajor(a + 256 * j, kLbo, kSbo), smem_desc_kmajor(b + 256 * j, kLbo, kSbo), IDESC,
-                 (t > 0 || j > 0) ? 1u : 0u);
-      mma_commit(&bar[s]);
+          for (int k = 0; k < kBK / 16; ++k)
+            mma_bf16(acc, smem_desc_sw128(sa + 32 * k), smem_desc_sw128(sb + 32 * k), IDESC, (t > 0 || k > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[a]);
+      }
+      mma_commit(&done);   // tracks every MMA this thread issued
+      if (!mbar_wait(&done, 0)) atomicOr(err, kErrWaitTimeout);
     }
-  }
-  cp_async_wait<0>();
-  const int last = (ok ? k_tiles : t) - 1;
-  bool fin = last < 0 || mbar_wait(&bar[last & 1], (last >> 1) & 1);
-  fin = __syncthreads_and(fin && ok);
-  tc_fence_after();
-  if (fin) {
-    const int row = m0 + warp * 32 + lane;
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;   // TMEM lane quarter this warp may read
+    int j = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++j) {
+      const int a = j & 1;
+      if (!wait_or_abort(&tfull[a], (uint32_t)((j / 2) & 1), &abort_flag, err)) break;
+      tc_fence_after();
+      const int z = tile / (mt * nt), rem = tile - z * mt * nt, ni = rem / mt, mi = rem - ni * mt;
+      (void)z;
+      const int row = mi * kBM + q * 32 + lane;
+      const uint32_t acc = tmem + (uint32_t)a * NCOL + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-      ep.store(row, n0 + c, v, row < M);
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(acc + (uint32_t)c, v);
+        ep.store(row, ni * BN + c, v, row < M);
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[a]);
     }
-  } else if (tid == 0) {
-    atomicOr(err, kErrWaitTimeout);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, NCOL);
+  if (warp == 0) tmem_dealloc(tmem, 2 * NCOL);
 }
 
-// splits > 1: split K into `splits` contiguous ranges (grid.z); the
-// epilogue then receives partial sums and must reduce them itself
+// splits > 1: split K into `splits` contiguous ranges; the epilogue then
+// receives partial sums and must reduce them itself
 template <int BN, class Loader, class Epilogue>
 cudaError_t launch_umma_gemm(const Loader& ld, const Epilogue& ep, int M, int N, int K, unsigned* err,
                              cudaStream_t st, int splits = 1) {
@@ -130,8 +204,15 @@ cudaError_t launch_umma_gemm(const Loader& ld, const Epilogue& ep, int M, int N,
   splits = splits < 1 ? 1 : (splits > k_total ? k_total : splits);
   const int k_tiles = (k_total + splits - 1) / splits;
   splits = (k_total + k_tiles - 1) / k_tiles;
-  const dim3 grid((M + kBM - 1) / kBM, N / BN, splits);
-  kern<<<grid, kThreads, gemm_smem_bytes<BN>(), st>>>(ld, ep, M, k_tiles, err);
+  const int mt = (M + kBM - 1) / kBM, nt = N / BN;
+  const long long n_tiles = (long long)mt * nt * splits;
+  int dev = 0, sms = 148, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, gemm_smem_bytes<BN>());
+  if (per_sm < 1) per_sm = 1;
+  const long long grid = n_tiles < (long long)sms * per_sm ? n_tiles : (long long)sms * per_sm;
+  kern<<<(unsigned)grid, kThreads, gemm_smem_bytes<BN>(), st>>>(ld, ep, M, mt, nt, (int)n_tiles, k_tiles, err);
   return cudaGetLastError();
 }
 
