@@ -46,8 +46,11 @@ struct Grid {
   }
 };
 
-// each thread stages a fixed 16-byte column chunk kc of 8 rows per A tile
-// (rows r0 + 16 i), so per-row pixel coordinates are computed once per CTA
+// each producer thread stages a fixed 16-byte column chunk kc of kRows rows
+// per A tile (rows r0 + kRowStep i), so per-row pixel coordinates are
+// computed once per tile
+constexpr int kRows = kBM * 8 / kProducers;        // 4
+constexpr int kRowStep = kBM / kRows;               // 32
 __device__ __forceinline__ void a_chunk(int tid, int& kc, int& r0) {
   kc = (tid >> 3) & 7;
   r0 = (tid & 7) + ((tid >> 6) << 3);
@@ -55,19 +58,20 @@ __device__ __forceinline__ void a_chunk(int tid, int& kc, int& r0) {
 
 // ------------------------------------------------------------ forward conv
 struct ConvFwdLoader {
+  static constexpr bool kAsync = true;
   View x;
   const bf16* w;   // [N][K]
   Grid in, out;
   int Cin, K, N, stride, M, bn;
   struct State {
-    int pix[8], y0[8], x0[8];   // per staged row: first pixel of its image (-1: row past M), yo*s-1, xo*s-1
+    int pix[kRows], y0[kRows], x0[kRows];   // per staged row: first pixel of its image (-1: row past M), yo*s-1, xo*s-1
   };
   __device__ void prepare(State& st, int m0, int, int tid) const {
     int kc, r0;
     a_chunk(tid, kc, r0);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int m = m0 + r0 + 16 * i;
+    for (int i = 0; i < kRows; ++i) {
+      const int m = m0 + r0 + kRowStep * i;
       if (m < M) {
         int b, yo, xo;
         out.pix(m, b, yo, xo);
@@ -88,8 +92,8 @@ struct ConvFwdLoader {
     const int tap = kval ? k / Cin : 0, ci = k - tap * Cin;
     const int ky = tap / 3, kx = tap - ky * 3;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int r = r0 + 16 * i;
+    for (int i = 0; i < kRows; ++i) {
+      const int r = r0 + kRowStep * i;
       const void* src = x.p;
       uint32_t bytes = 0;
       const int yi = st.y0[i] + ky, xi = st.x0[i] + kx;
@@ -128,19 +132,20 @@ struct BiasActStore {
 
 // ------------------------------------------------------------ conv dgrad
 struct ConvDgradLoader {
+  static constexpr bool kAsync = true;
   View dy;
   const bf16* wd;   // [Cin][9 Cout]: wd[ci][(ky,kx,co)] = W[co][ky][kx][ci]
   Grid in, out;     // in = dX grid (forward input), out = dY grid
   int Cout, K, N, stride, M, bn;
   struct State {
-    int pix[8], yi[8], xi[8];   // per staged row: first pixel of its dY image (-1: past M), and its dX pixel
+    int pix[kRows], yi[kRows], xi[kRows];   // per staged row: first pixel of its dY image (-1: past M), and its dX pixel
   };
   __device__ void prepare(State& st, int m0, int, int tid) const {
     int kc, r0;
     a_chunk(tid, kc, r0);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int m = m0 + r0 + 16 * i;
+    for (int i = 0; i < kRows; ++i) {
+      const int m = m0 + r0 + kRowStep * i;
       if (m < M) {
         int b, yi, xi;
         in.pix(m, b, yi, xi);
@@ -161,8 +166,8 @@ struct ConvDgradLoader {
     const int tap = kval ? k / Cout : 0, co = k - tap * Cout;
     const int ky = tap / 3, kx = tap - ky * 3;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int r = r0 + 16 * i;
+    for (int i = 0; i < kRows; ++i) {
+      const int r = r0 + kRowStep * i;
       const void* src = dy.p;
       uint32_t bytes = 0;
       const int ys = st.yi[i] + 1 - ky, xs = st.xi[i] + 1 - kx;
@@ -217,6 +222,7 @@ struct MaskedGradStore {
 
 // ------------------------------------------------------- transposed conv
 struct ConvTFwdLoader {
+  static constexpr bool kAsync = true;
   View x;
   const bf16* w4;   // [4 Cout][Cin]
   int Cin, N, M, bn;
@@ -227,8 +233,8 @@ struct ConvTFwdLoader {
     a_chunk(tid, kc, r0);
     const int k = kt * kBK + kc * 8;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int r = r0 + 16 * i, m = m0 + r;
+    for (int i = 0; i < kRows; ++i) {
+      const int r = r0 + kRowStep * i, m = m0 + r;
       const bool v = m < M && k < Cin;
       cp_async16(as + tile_off(r, kc, kBK), v ? (const void*)(x.p + (size_t)m * x.cs + x.co + k) : (const void*)x.p,
                  v ? 16u : 0u);
@@ -268,19 +274,20 @@ struct ConvTStore {
 };
 
 struct ConvTDgradLoader {
+  static constexpr bool kAsync = true;
   View dy;
   const bf16* w4t;   // [Cin][4 Cout]
   Grid in;           // dX grid (convT input); dY is 2H x 2W
   int Cout, K, N, M, bn;
   struct State {
-    int base[8];     // per staged row: dY pixel index of (2y, 2x), -1 past M
+    int base[kRows];     // per staged row: dY pixel index of (2y, 2x), -1 past M
   };
   __device__ void prepare(State& st, int m0, int, int tid) const {
     int kc, r0;
     a_chunk(tid, kc, r0);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int m = m0 + r0 + 16 * i;
+    for (int i = 0; i < kRows; ++i) {
+      const int m = m0 + r0 + kRowStep * i;
       if (m < M) {
         int b, yy, xx;
         in.pix(m, b, yy, xx);
@@ -298,8 +305,8 @@ struct ConvTDgradLoader {
     const int d = kval ? k / Cout : 0, co = k - d * Cout;
     const int off = (d >> 1) * (2 * in.W) + (d & 1);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int r = r0 + 16 * i;
+    for (int i = 0; i < kRows; ++i) {
+      const int r = r0 + kRowStep * i;
       const bool v = kval && st.base[i] >= 0;
       cp_async16(as + tile_off(r, kc, kBK),
                  v ? (const void*)(dy.p + ((size_t)st.base[i] + off) * dy.cs + dy.co + co) : (const void*)dy.p,
@@ -370,6 +377,7 @@ struct ConvTGather {  // rows (d, co) of the transposed conv's output gradient, 
 
 template <class SrcA, class SrcB>
 struct WgradLoader {
+  static constexpr bool kAsync = false;
   SrcA a;
   SrcB b;
   int P, bn;   // pixels in the reduction
@@ -377,23 +385,18 @@ struct WgradLoader {
   __device__ void prepare(State&, int, int, int) const {}
   __device__ void load(const State&, uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
     const int p0 = kt * kBK;
-    {   // A: 16 row groups x 8 pixel groups = 128 blocks, one per thread
-      const int rg = tid >> 3, pg = tid & 7;
+    // A: 16 row groups x 8 pixel groups = 128 blocks; B: bn / 8 x 8 = bn blocks
+    for (int blk = tid; blk < 128 + bn; blk += kProducers) {
+      const bool isA = blk < 128;
+      const int id = isA ? blk : blk - 128;
+      const int rg = id >> 3, pg = id & 7;
       uint4 in[8], out[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) in[q] = a.get(m0 + rg * 8, p0 + pg * 8 + q, P);
+      for (int q = 0; q < 8; ++q) in[q] = isA ? a.get(m0 + rg * 8, p0 + pg * 8 + q, P) : b.get(n0 + rg * 8, p0 + pg * 8 + q, P);
       transpose8x8(in, out);
+      uint8_t* dst = isA ? as : bs;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(as + tile_off(rg * 8 + c, pg, kBK)) = out[c];
-    }
-    for (int blk = tid; blk < bn; blk += kProducers) {   // B: bn/8 row groups x 8 pixel groups
-      const int rg = blk >> 3, pg = blk & 7;
-      uint4 in[8], out[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) in[q] = b.get(n0 + rg * 8, p0 + pg * 8 + q, P);
-      transpose8x8(in, out);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(bs + tile_off(rg * 8 + c, pg, kBK)) = out[c];
+      for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(dst + tile_off(rg * 8 + c, pg, kBK)) = out[c];
     }
   }
 };

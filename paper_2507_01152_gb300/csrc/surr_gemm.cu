@@ -12,6 +12,7 @@ namespace {
 using namespace umma;
 
 struct RowMajorLoader {
+  static constexpr bool kAsync = true;
   const __nv_bfloat16* A;
   const __nv_bfloat16* B;
   int M, N, K, bn;

@@ -3,12 +3,12 @@
 //
 // Persistent and warp-specialised.  A CTA owns a sequence of 128 x BN
 // output tiles and runs three roles concurrently:
-//   warps 0-3  producers: gather the operands of each 64-wide K step into
+//   warps 0-7  producers: gather the operands of each 64-wide K step into
 //              one of the shared-memory stages (cp.async or plain stores),
 //              up to `stages` steps ahead of the tensor core;
-//   warp 4     one thread issues the four 128 x BN x 16 MMAs of a stage and
+//   warp 8     one thread issues the four 128 x BN x 16 MMAs of a stage and
 //              commits them to the stage's "empty" barrier;
-//   warps 5-8  epilogue: read a finished accumulator with tcgen05.ld and
+//   warps 9-12 epilogue: read a finished accumulator with tcgen05.ld and
 //              hand it to the Epilogue functor, while the MMAs of the next
 //              tile accumulate into the other half of a double-buffered
 //              TMEM allocation.
@@ -24,19 +24,23 @@ namespace ussim {
 namespace umma {
 
 constexpr int kBM = 128, kBK = 64;
-constexpr int kProducers = 128;                     // warps 0-3
-constexpr int kThreads = 288;                       // 4 producer + 1 MMA + 4 epilogue warps
+constexpr int kProducers = 256;                     // warps 0-7
+constexpr int kMmaWarp = kProducers / 32;           // warp 8
+constexpr int kEpilogue = 128;                      // warps 9-12
+constexpr int kThreads = kProducers + 32 + kEpilogue;
 constexpr uint32_t kTileA = kBM * kBK * 2;          // bytes of one A stage
-constexpr int kLag = 2;                             // producer steps in flight before signalling
-constexpr int kStages = 4;
-
 template <int BN>
 constexpr uint32_t stage_bytes() {
   return kTileA + (uint32_t)BN * kBK * 2;
 }
+// stages, sized to ~192 KB of shared memory
+template <int BN>
+constexpr int gemm_stages() {
+  return BN <= 64 ? 8 : (BN <= 128 ? 6 : 4);
+}
 template <int BN>
 constexpr uint32_t gemm_smem_bytes() {   // + slack to align the stages to 1024 B (swizzle atoms)
-  return kStages * stage_bytes<BN>() + 1024;
+  return gemm_stages<BN>() * stage_bytes<BN>() + 1024;
 }
 template <int BN>
 constexpr uint32_t tmem_cols() {   // one accumulator; TMEM allocations are powers of 2 >= 32
@@ -45,6 +49,10 @@ constexpr uint32_t tmem_cols() {   // one accumulator; TMEM allocations are powe
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// arrive on `bar` once every cp.async this thread issued so far has landed
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // bounded wait that also gives up when another role has aborted
@@ -63,18 +71,19 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
   return true;
 }
 
-// Loader:   struct State; prepare(State&, m0, n0, tid) once per tile, then
+// Loader:   static constexpr bool kAsync (stages with cp.async, else with
+//           shared stores); struct State; prepare(State&, m0, n0, tid) once per tile, then
 //           load(const State&, a_stage, b_stage, m0, n0, kt, tid) per K step:
 //           stage the 128 x 64 A tile rows m0.., and the BN x 64 B tile rows
 //           n0.., K step kt (global index), into the K-major 128-byte-swizzled
 //           layout (tile_off(r, kc, kBK) for 16-byte chunk kc of row r); steps past
-//           the end of K must load zeros.  Called by the 128 producer threads.
+//           the end of K must load zeros.  Called by the kProducers producer threads.
 // Epilogue: store(int m, int n0, const float* v16, bool valid).
 // Tiles: mt x nt x splits, M fastest; split z covers K steps z*k_tiles ...
 template <int BN, class Loader, class Epilogue>
 __global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilogue ep, int M, int mt, int nt,
                                                                  int n_tiles, int k_tiles, unsigned* err) {
-  constexpr int S = kStages;
+  constexpr int S = gemm_stages<BN>();
   constexpr uint32_t NCOL = tmem_cols<BN>();
   constexpr uint32_t IDESC = idesc_bf16_f32(kBM, BN);
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -95,7 +104,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilo
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], kProducers);
+      mbar_init(&tempty[a], kEpilogue);
     }
     mbar_init(&done, 1);
     abort_flag = 0;
@@ -106,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilo
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  if (warp < 4) {
+  if (warp < kMmaWarp) {
     // ---------------------------------------------------------- producers
     long long g = 0;   // global K-step counter over this CTA's tiles
     for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x) {
@@ -122,19 +131,17 @@ __global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilo
           break;
         }
         ld.load(st, smem + s * stage_bytes<BN>(), smem + s * stage_bytes<BN>() + kTileA, m0, n0, kt0 + t, tid);
-        cp_async_commit();
-        if (g >= kLag) {
-          cp_async_wait<kLag>();
-          fence_proxy_async();
-          mbar_arrive(&full[(g - kLag) % S]);
-        }
+        // cp.async loaders: the barrier completes when the copies land; loaders
+        // that store from registers release their stores with a plain arrive
+        if (Loader::kAsync)
+          cp_async_arrive(&full[s]);
+        else
+          mbar_arrive(&full[s]);
       }
       if (!ok) break;
     }
     cp_async_wait<0>();
-    fence_proxy_async();
-    for (long long q = g - kLag < 0 ? 0 : g - kLag; q < g; ++q) mbar_arrive(&full[q % S]);
-  } else if (warp == 4) {
+  } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------- MMA issue
     if (lane == 0) {
       long long g = 0;
@@ -152,6 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilo
             break;
           }
           tc_fence_after();
+          fence_proxy_async();   // the stage was written through the generic proxy; the MMA reads it async
           const uint32_t sa = smem_u32(smem + s * stage_bytes<BN>()), sb = sa + kTileA;
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k)
@@ -206,11 +214,12 @@ cudaError_t launch_umma_gemm(const Loader& ld, const Epilogue& ep, int M, int N,
   splits = (k_total + k_tiles - 1) / k_tiles;
   const int mt = (M + kBM - 1) / kBM, nt = N / BN;
   const long long n_tiles = (long long)mt * nt * splits;
-  int dev = 0, sms = 148, per_sm = 1;
+  int dev = 0, sms = 148, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, gemm_smem_bytes<BN>());
-  if (per_sm < 1) per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, gemm_smem_bytes<BN>()) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
   const long long grid = n_tiles < (long long)sms * per_sm ? n_tiles : (long long)sms * per_sm;
   kern<<<(unsigned)grid, kThreads, gemm_smem_bytes<BN>(), st>>>(ld, ep, M, mt, nt, (int)n_tiles, k_tiles, err);
   return cudaGetLastError();
