@@ -212,6 +212,16 @@ US_API us_status us_sim_render_host(us_sim* sim, const us_env* envs, int32_t B, 
 US_API us_status us_sim_sample_slices(us_sim* sim, const us_env* envs, int32_t B, const float* poses, uint16_t* out,
                                       void* stream);
 
+/* Physics fallback for frames a learned surrogate rendered: re-render (into
+ * `frames`, same layout as us_sim_render) only the envs whose score[b]
+ * exceeds `threshold`, leaving the other frames untouched.  score: DEVICE
+ * [B] (e.g. the surrogate's predicted error); the subset is selected on the
+ * device, so nothing waits for the host.  n_rendered: DEVICE int32 (may be
+ * NULL) receives the number of frames re-rendered.  B <= 32768. */
+US_API us_status us_sim_render_gated(us_sim* sim, const us_env* envs, int32_t B, const float* poses, uint64_t seed,
+                                     uint64_t step, float* frames, const float* score, float threshold,
+                                     int32_t* n_rendered, void* stream);
+
 /* Wait for `stream` and read the sticky device error word: US_OK, or
  * US_ERR_INVALID_ARG if a pose had a non-finite entry (that frame renders
  * as water).  Clears the word. */

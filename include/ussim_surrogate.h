@@ -133,6 +133,22 @@ US_API us_status us_surr_train_step(us_surr* s, const uint16_t* x, const float* 
 /* per-frame L1 and SSIM of any prediction: out DEVICE [1 + 2B] as above */
 US_API us_status us_surr_metrics(us_surr* s, const float* pred, const float* target, int32_t B, float* out,
                                  void* stream);
+/* ---- error gate ----------------------------------------------------------
+ * The physics render is the surrogate's judge and fallback: a linear error
+ * head on the surrogate's bottleneck features (channel means of the
+ * deepest activation, 8 c values per frame) predicts each frame's L1 gap
+ * to physics; frames predicted above a threshold are re-rendered by
+ * physics (us_sim_render_gated).  The head is fitted by ridge regression
+ * on (features, true L1) pairs that physics provides. */
+US_API int32_t us_surr_num_features(const us_surr* s);
+/* features of the frames of the last us_surr_forward: DEVICE [B][8 c] */
+US_API us_status us_surr_features(us_surr* s, int32_t B, float* out, void* stream);
+/* predicted L1 gap of the frames of the last forward: DEVICE [B] */
+US_API us_status us_surr_predict_error(us_surr* s, int32_t B, float* out, void* stream);
+/* fit the head: feat HOST [n][8 c], target HOST [n] (true per-frame L1),
+ * ridge >= 0; synchronous */
+US_API us_status us_surr_fit_error_head(us_surr* s, const float* feat, const float* target, int32_t n, float ridge);
+
 /* parameters / gradients of the last train step, HOST, parameter layout (synchronous) */
 US_API us_status us_surr_get_params(const us_surr* s, float* host_out);
 US_API us_status us_surr_get_grads(us_surr* s, float* host_out);

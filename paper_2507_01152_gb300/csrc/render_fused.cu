@@ -76,12 +76,13 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_r
   DevTissue* tis = reinterpret_cast<DevTissue*>(smem + L.off_tis);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+  const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
   if (rank == 0 && tid == 0) slot[0] = (int)atomicAdd(p.work, 1u);
   cl.sync();
   int parity = 0;
   int idx = *cl.map_shared_rank(&slot[0], 0);
 
-  while (idx < p.n_items) {
+  while (idx < n_items) {
     __syncthreads();  // every thread is done with the previous item's context and tables
     if (tid == 0) {
       const EnvItem it = p.items[idx];
@@ -304,11 +305,43 @@ cudaError_t fused_max_clusters(const FusedShape& s, int* clusters) {
 cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st) {
   const void* fn = fused_fn(s.cs, s.nw);
   if (!fn) return cudaErrorInvalidValue;
-  const int clusters = std::max(1, std::min(s.clusters, p.n_items));
+  const int clusters = std::max(1, p.n_items_dev ? s.clusters : std::min(s.clusters, p.n_items));
   RenderParams pp = p;
   FusedLayout lay = s.lay;
   void* args[2] = {&pp, &lay};
   return cudaLaunchKernel(fn, dim3(clusters * s.cs), dim3(s.nw * 32), args, s.smem, st);
+}
+
+// ------------------------------------------------------------- gating
+// keep the items whose score exceeds the threshold, in batch order (one
+// block, B <= 32 * 1024): out[0 .. *count)
+__global__ void gate_compact(const EnvItem* items, int B, const float* score, float thr, EnvItem* out, int* count) {
+  __shared__ int warp_tot[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < B; c0 += blockDim.x) {
+    const int b = c0 + threadIdx.x;
+    const int keep = (b < B && score[b] > thr) ? 1 : 0;
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) warp_tot[w] = __popc(m);
+    __syncthreads();
+    int before = 0;
+    for (int i = 0; i < w; ++i) before += warp_tot[i];
+    if (keep) out[base + before + __popc(m & ((1u << lane) - 1u))] = items[b];
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) base += warp_tot[i];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
+cudaError_t launch_gate_compact(const EnvItem* items, int B, const float* score, float thr, EnvItem* out, int* count,
+                                cudaStream_t st) {
+  gate_compact<<<1, 1024, 0, st>>>(items, B, score, thr, out, count);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- checks

@@ -277,6 +277,26 @@ __global__ void relayout_convT(const float* w, bf16* wf, bf16* wt, int cin, int 
   wt[(long long)ci * cout4 + r] = v;
 }
 
+// per-frame features for the error head: channel means of the bottleneck
+// activation, feat[b][c] = mean over pixels of x[b][p][c]
+__global__ void pool_features(const bf16* x, int P, int C, float* feat) {
+  const int b = blockIdx.x;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    float s = 0.f;
+    for (int p = 0; p < P; ++p) s += __bfloat162float(x[((size_t)b * P + p) * C + c]);
+    feat[(size_t)b * C + c] = s / (float)P;
+  }
+}
+
+// predicted per-frame L1 gap: w . feat + bias
+__global__ void error_head(const float* feat, const float* w, int F, int B, float* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float s = w[F];
+  for (int f = 0; f < F; ++f) s = fmaf(w[f], feat[(size_t)b * F + f], s);
+  out[b] = s;
+}
+
 // gradient in the flat parameter layout (conv segments transposed back)
 __global__ void grads_to_param_layout(const float* g, float* out, const Seg* segs, int nseg, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -319,6 +339,7 @@ struct us_surr {
   };
   std::vector<Buf> bufs;
   float *out = nullptr, *dout = nullptr, *sh = nullptr, *smaps = nullptr, *l1s = nullptr, *sss = nullptr;
+  float *feat = nullptr, *ehead = nullptr;   // bottleneck features of the last forward, error-head weights
   unsigned* err = nullptr;
   std::string last_error;
 };
@@ -406,6 +427,8 @@ void free_surr(us_surr* s) {
   cudaFree(s->smaps);
   cudaFree(s->l1s);
   cudaFree(s->sss);
+  cudaFree(s->feat);
+  cudaFree(s->ehead);
   cudaFree(s->err);
   delete s;
 }
@@ -472,6 +495,8 @@ us_status forward_impl(us_surr* s, int B, cudaStream_t st) {
   const LayerDesc& hd = s->layers.back();
   const long long P = (long long)B * s->cfg.height * s->cfg.width;
   head_fwd<<<blocks(P), 256, 0, st>>>(s->bufs[B_X0].a, hd.cin, s->p + hd.w_off, s->p + hd.b_off, s->out, P);
+  const auto& e3 = s->bufs[B_E3];
+  pool_features<<<B, 256, 0, st>>>(e3.a, e3.H * e3.W, e3.C, s->feat);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? US_OK : cfail(s, e, "head");
 }
@@ -672,11 +697,14 @@ us_status us_surr_create(const us_surr_config* cfg, const float* init_params, us
   if ((e = cudaMalloc(&s->out, P * 4)) != cudaSuccess || (e = cudaMalloc(&s->dout, P * 4)) != cudaSuccess ||
       (e = cudaMalloc(&s->sh, (size_t)Bm * 5 * H * (W - kWin + 1) * 4)) != cudaSuccess ||
       (e = cudaMalloc(&s->smaps, (size_t)Bm * 3 * (H - kWin + 1) * (W - kWin + 1) * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&s->feat, (size_t)Bm * 8 * c * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&s->ehead, (size_t)(8 * c + 1) * 4)) != cudaSuccess ||
       (e = cudaMalloc(&s->l1s, (size_t)Bm * 4 * blocks((long long)H * W))) != cudaSuccess ||
       (e = cudaMalloc(&s->sss, (size_t)Bm * 4 * blocks((long long)(H - kWin + 1) * (W - kWin + 1)))) != cudaSuccess) {
     free_surr(s);
     return US_ERR_OOM;
   }
+  cudaMemset(s->ehead, 0, (size_t)(8 * c + 1) * 4);
   if (refresh_weights(s, 0) != US_OK || cudaDeviceSynchronize() != cudaSuccess) {
     free_surr(s);
     return US_ERR_CUDA;
@@ -729,6 +757,69 @@ us_status us_surr_metrics(us_surr* s, const float* pred, const float* target, in
   if (!s) return US_ERR_INVALID_ARG;
   if (!pred || !target || !out || B < 1 || B > s->cfg.max_batch) return fail(s, US_ERR_INVALID_ARG, "bad metrics arguments");
   return loss_impl(s, pred, target, B, out, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int32_t us_surr_num_features(const us_surr* s) { return s ? 8 * s->cfg.base_channels : -1; }
+
+us_status us_surr_features(us_surr* s, int32_t B, float* out, void* stream) {
+  if (!s || !out || B < 1 || B > s->cfg.max_batch) return US_ERR_INVALID_ARG;
+  const cudaError_t e = cudaMemcpyAsync(out, s->feat, (size_t)B * 8 * s->cfg.base_channels * 4, cudaMemcpyDeviceToDevice,
+                                        static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? US_OK : cfail(s, e, "features");
+}
+
+us_status us_surr_predict_error(us_surr* s, int32_t B, float* out, void* stream) {
+  if (!s || !out || B < 1 || B > s->cfg.max_batch) return US_ERR_INVALID_ARG;
+  error_head<<<blocks(B), 256, 0, static_cast<cudaStream_t>(stream)>>>(s->feat, s->ehead, 8 * s->cfg.base_channels, B, out);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? US_OK : cfail(s, e, "error head");
+}
+
+// Ridge least squares for the error head: minimise sum (w.f + b - y)^2 +
+// ridge |w|^2 over n (feature, true L1) pairs given on the host, by the
+// normal equations (Cholesky, FP64).
+us_status us_surr_fit_error_head(us_surr* s, const float* feat, const float* target, int32_t n, float ridge) {
+  if (!s || !feat || !target || n < 2 || !(ridge >= 0)) return US_ERR_INVALID_ARG;
+  const int F = 8 * s->cfg.base_channels, D = F + 1;
+  std::vector<double> A((size_t)D * D, 0.0), rhs(D, 0.0), w(D, 0.0);
+  std::vector<double> x(D);
+  for (int i = 0; i < n; ++i) {
+    for (int f = 0; f < F; ++f) x[f] = feat[(size_t)i * F + f];
+    x[F] = 1.0;
+    for (int a = 0; a < D; ++a) {
+      rhs[a] += x[a] * target[i];
+      for (int b = 0; b <= a; ++b) A[(size_t)a * D + b] += x[a] * x[b];
+    }
+  }
+  for (int a = 0; a < F; ++a) A[(size_t)a * D + a] += ridge;
+  A[(size_t)F * D + F] += 1e-9;
+  // Cholesky A = L L^T (lower triangle in place)
+  for (int j = 0; j < D; ++j) {
+    double d = A[(size_t)j * D + j];
+    for (int k = 0; k < j; ++k) d -= A[(size_t)j * D + k] * A[(size_t)j * D + k];
+    if (!(d > 0)) return fail(s, US_ERR_INVALID_ARG, "error-head normal equations are singular");
+    d = std::sqrt(d);
+    A[(size_t)j * D + j] = d;
+    for (int i = j + 1; i < D; ++i) {
+      double v = A[(size_t)i * D + j];
+      for (int k = 0; k < j; ++k) v -= A[(size_t)i * D + k] * A[(size_t)j * D + k];
+      A[(size_t)i * D + j] = v / d;
+    }
+  }
+  std::vector<double> y(D);
+  for (int i = 0; i < D; ++i) {
+    double v = rhs[i];
+    for (int k = 0; k < i; ++k) v -= A[(size_t)i * D + k] * y[k];
+    y[i] = v / A[(size_t)i * D + i];
+  }
+  for (int i = D - 1; i >= 0; --i) {
+    double v = y[i];
+    for (int k = i + 1; k < D; ++k) v -= A[(size_t)k * D + i] * w[k];
+    w[i] = v / A[(size_t)i * D + i];
+  }
+  std::vector<float> wf(D);
+  for (int i = 0; i < D; ++i) wf[i] = (float)w[i];
+  return cudaMemcpy(s->ehead, wf.data(), (size_t)D * 4, cudaMemcpyHostToDevice) == cudaSuccess ? US_OK : US_ERR_CUDA;
 }
 
 us_status us_surr_get_params(const us_surr* s, float* host_out) {

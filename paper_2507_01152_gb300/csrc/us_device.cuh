@@ -61,6 +61,7 @@ struct RenderParams {
   const DevPair* pairs;
   const EnvItem* items;
   int n_items;
+  const int* n_items_dev;    // if set, the item count is read here (device-built work lists)
   int n_labels;
   const float* poses;        // [B][12]
   uint2 key;                 // Philox key for this (seed, step)

@@ -318,6 +318,8 @@ void free_sim(us_sim* s) {
     drop_graph(kv.second);
     cudaFree(kv.second.d_items);
     cudaFree(kv.second.d_items_batch);
+    cudaFree(kv.second.d_items_gated);
+    cudaFree(kv.second.d_gated_count);
   }
   cudaFree(s->d_vols);
   cudaFree(s->d_probes);
@@ -625,6 +627,35 @@ us_status us_sim_render_host(us_sim* s, const us_env* envs, int32_t B, const flo
   if ((e = cudaMemcpyAsync(frames_host, s->d_host_frames, frame_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_fail(s, e, "frame copy");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e, "render");
+  return US_OK;
+}
+
+us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint64_t seed, uint64_t step,
+                              float* frames, const float* score, float threshold, int32_t* n_rendered, void* stream) {
+  us_status r = check_render_args(s, envs, B, poses, frames);
+  if (r != US_OK || B == 0) return r;
+  if (!score) return fail(s, US_ERR_INVALID_ARG, "NULL score");
+  if (B > 32 * 1024) return fail(s, US_ERR_UNSUPPORTED, "gated batches are limited to 32768 envs");
+  us_plan* pl;
+  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  cudaError_t e;
+  if (!pl->d_items_gated && ((e = cudaMalloc(&pl->d_items_gated, sizeof(EnvItem) * B)) != cudaSuccess ||
+                             (e = cudaMalloc(&pl->d_gated_count, sizeof(int))) != cudaSuccess))
+    return cuda_fail(s, e, "gated work list");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((e = launch_gate_compact(pl->d_items_batch, B, score, threshold, pl->d_items_gated, pl->d_gated_count, st)) !=
+      cudaSuccess)
+    return cuda_fail(s, e, "gate");
+  RenderParams p = base_params(s, poses, seed, step, frames);
+  p.items = pl->d_items_gated;
+  p.n_items = B;
+  p.n_items_dev = pl->d_gated_count;
+  if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess ||
+      (e = launch_fused(p, s->shape, st)) != cudaSuccess)
+    return cuda_fail(s, e, "gated render");
+  if (n_rendered && (e = cudaMemcpyAsync(n_rendered, pl->d_gated_count, sizeof(int), cudaMemcpyDeviceToDevice, st)) !=
+                        cudaSuccess)
+    return cuda_fail(s, e, "gated count");
   return US_OK;
 }
 

@@ -64,6 +64,10 @@ cudaError_t fused_prepare(const FusedShape& s);
 cudaError_t fused_max_clusters(const FusedShape& s, int* clusters);
 cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st);
 
+// items with score > thr, in batch order, and their count (device)
+cudaError_t launch_gate_compact(const EnvItem* items, int B, const float* score, float thr, EnvItem* out, int* count,
+                                cudaStream_t st);
+
 // surrogate input of a batch on the output pixel grid: [B][H][W][8] BF16
 cudaError_t launch_slice_input(const RenderParams& p, const EnvItem* items_batch, int B, int H, int W, void* out,
                                cudaStream_t st);
@@ -79,6 +83,8 @@ struct us_plan {
   std::vector<ussim::EnvItem> items_batch;   // caller order
   ussim::EnvItem* d_items = nullptr;         // device copy of items_sorted
   ussim::EnvItem* d_items_batch = nullptr;   // device copy of items_batch
+  ussim::EnvItem* d_items_gated = nullptr;   // device-built subset for gated renders
+  int* d_gated_count = nullptr;
   long long frame_floats = 0, beam_elems = 0;
   // captured [work-counter reset + fused launch], re-parameterised per call
   cudaGraph_t graph = nullptr;

@@ -23,7 +23,7 @@ HELD_OUT_SEED = 1_000_000
 class PairSource:
     """Renders (input slice, physics frame) batches on the GPU."""
 
-    def __init__(self, batch: int, spec=None, probe=None, seed: int = 0x5EED0004):
+    def __init__(self, batch: int, spec=None, probe=None, seed: int = 0x5EED0004, tuning=None):
         import torch
         from .ussim import Sim, make_envs
         self.torch = torch
@@ -50,6 +50,35 @@ class PairSource:
         return self.x, self.y
 
 
+def gate_samples(net, src: PairSource, n_batches: int, first_seed: int = HELD_OUT_SEED + 1000):
+    """(features, true per-frame L1) of the surrogate against physics on
+    ``n_batches`` batches of poses (for fitting the error head)"""
+    torch = src.torch
+    F = net.num_features()
+    feat = torch.zeros((src.B, F), device="cuda")
+    out = torch.zeros(1 + 2 * src.B, device="cuda")
+    pred = torch.zeros_like(src.y)
+    fs, ys = [], []
+    for k in range(n_batches):
+        x, y = src.batch(first_seed + k, first_seed + k)
+        net.forward(x, pred)
+        net.features(src.B, feat)
+        net.metrics(pred, y, out)
+        fs.append(feat.cpu().numpy())
+        ys.append(out[1:1 + src.B].cpu().numpy())
+    return np.concatenate(fs), np.concatenate(ys)
+
+
+def mixed_step(sim, net, poses, seed, step, x, frames, err_pred, threshold, n_rendered, stream=None, envs_c=None):
+    """One production step: surrogate frames for every env, physics
+    re-render of the frames whose predicted error exceeds ``threshold``."""
+    B = poses.shape[0]
+    sim.sample_slices(None, poses, x, stream=stream, envs_c=envs_c)
+    net.forward(x, frames, stream=stream)
+    net.predict_error(B, err_pred, stream=stream)
+    sim.render_gated(None, poses, seed, step, frames, err_pred, threshold, n_rendered, stream=stream, envs_c=envs_c)
+
+
 def make_surrogate(c: int, batch: int, lr: float, seed: int, H=256, W=256):
     from .ussim import Surrogate
     off, size, fan = Surrogate.segments(c, H, W)
@@ -73,12 +102,12 @@ def evaluate(net, src: PairSource, n_batches: int = 2):
 
 
 def train(steps: int, batch: int = 256, c: int = 32, lr: float = 2e-4, seed: int = 0, log_every: int = 50,
-          eval_batches: int = 2, log=print):
+          eval_batches: int = 2, log=print, probe=None):
     """Train for ``steps`` steps of ``batch`` fresh pairs; returns (net,
     source, history)."""
     torch = __import__("torch")
-    src = PairSource(batch)
-    net = make_surrogate(c, batch, lr, seed)
+    src = PairSource(batch, probe=probe)
+    net = make_surrogate(c, batch, lr, seed, src.probe.out_h, src.probe.out_w)
     loss = torch.zeros(1 + 2 * batch, device="cuda")
     hist = []
     t0 = time.perf_counter()

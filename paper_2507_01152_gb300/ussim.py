@@ -81,6 +81,7 @@ SIGNATURES = {
     "us_sim_render_host": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
     "us_sim_check": (C.c_int, [_P, _P]),
     "us_sim_sample_slices": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
+    "us_sim_render_gated": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, C.c_float, _P, _P]),
     "us_sim_get_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
     "us_sim_set_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
     "us_sim_autotune": (C.c_int, [_P, _P, C.c_int32, _P, _P, C.c_char_p, _P]),
@@ -101,6 +102,10 @@ SIGNATURES = {
     "us_surr_forward": (C.c_int, [_P, _P, _P, _I, _P]),
     "us_surr_train_step": (C.c_int, [_P, _P, _P, _I, _P, _I, _P]),
     "us_surr_metrics": (C.c_int, [_P, _P, _P, _I, _P, _P]),
+    "us_surr_num_features": (C.c_int32, [_P]),
+    "us_surr_features": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "us_surr_predict_error": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "us_surr_fit_error_head": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float]),
     "us_surr_get_params": (C.c_int, [_P, _P]),
     "us_surr_get_grads": (C.c_int, [_P, _P]),
     "us_surr_check": (C.c_int, [_P, _P]),
@@ -276,6 +281,13 @@ class Sim:
     def check(self, stream=None):
         self._check(self._lib.us_sim_check(self.h, _stream_handle(stream)))
 
+    def render_gated(self, envs, poses, seed, step, frames, score, threshold, n_rendered=None, stream=None,
+                     envs_c=None):
+        B = poses.shape[0]
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_render_gated(self.h, e, B, _ptr(poses), seed, step, _ptr(frames), _ptr(score),
+                                                  float(threshold), _ptr(n_rendered), _stream_handle(stream)))
+
     def sample_slices(self, envs, poses, out, stream=None, envs_c=None):
         """surrogate input [B][H][W][8] bf16 (out: torch bfloat16 CUDA tensor)"""
         B = poses.shape[0]
@@ -357,6 +369,21 @@ class Surrogate:
     def metrics(self, pred, target, out, stream=None):
         self._check(self._lib.us_surr_metrics(self.h, _ptr(pred), _ptr(target), pred.shape[0], _ptr(out),
                                               _stream_handle(stream)))
+
+    def num_features(self):
+        return self._lib.us_surr_num_features(self.h)
+
+    def features(self, B, out, stream=None):
+        self._check(self._lib.us_surr_features(self.h, B, _ptr(out), _stream_handle(stream)))
+
+    def predict_error(self, B, out, stream=None):
+        self._check(self._lib.us_surr_predict_error(self.h, B, _ptr(out), _stream_handle(stream)))
+
+    def fit_error_head(self, feat, target, ridge=1e-3):
+        feat = np.ascontiguousarray(feat, np.float32)
+        target = np.ascontiguousarray(target, np.float32)
+        self._check(self._lib.us_surr_fit_error_head(self.h, feat.ctypes.data, target.ctypes.data, len(target),
+                                                     float(ridge)))
 
     def params(self):
         out = np.zeros(self.n_params, np.float32)
