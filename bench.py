@@ -171,6 +171,130 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def surrogate_speed(sim, wl, B, stream, c=32):
+    """frames/s of surrogate inference (slices + forward) on B envs"""
+    import torch
+    from paper_2507_01152_gb300 import train as T
+    from paper_2507_01152_gb300.ussim import make_envs
+    spec = wl.volumes[0][0]
+    P = torch.from_numpy(scene.dorsal_poses(spec, B, 4242)).cuda()
+    envs = np.zeros((B, 2), np.int32)
+    ec = make_envs(envs)
+    net = T.make_surrogate(c, B, 2e-4, 0)
+    x = torch.zeros((B, 256, 256, 8), dtype=torch.bfloat16, device="cuda")
+    y = torch.zeros((B, 256, 256), device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            sim.sample_slices(None, P, x, stream=stream, envs_c=ec)
+            net.forward(x, y, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        n = 3
+        for _ in range(n):
+            sim.sample_slices(None, P, x, stream=stream, envs_c=ec)
+            net.forward(x, y, stream=stream)
+        b.record(stream)
+        b.synchronize()
+    net.check(stream)
+    ms = a.elapsed_time(b) / n
+    net.close()
+    return {"value": B / ms * 1e3, "unit": "frames/s", "envs": B, "ms_per_step": ms,
+            "tflops": 2 * 10.74e9 * B / ms / 1e9, "base_channels": c,
+            "note": "slice sampling + BF16 forward on tcgen05; speed only (weights untrained)"}
+
+
+def run_mixed(args):
+    """Mixed production step on 1024 envs over the four 512 x 512 x 256
+    volumes (curvilinear 256 x 512 probe, 256 x 256 frames): surrogate
+    frames for every env, physics re-render of the frames whose predicted
+    L1 gap exceeds the gate; compared with all-physics (fused and plain
+    per-env) on the same batch.  The surrogate is first trained here on
+    pairs the physics path renders on the 256^3 volume."""
+    import torch
+    from paper_2507_01152_gb300 import build
+    from paper_2507_01152_gb300 import train as T
+    from paper_2507_01152_gb300.ussim import Sim, make_envs
+    build.build()
+    torch.cuda.set_device(0)
+    B = 1024
+    t0 = time.perf_counter()
+    net, src, hist = T.train(args.train_steps, batch=128, c=32, lr=args.lr, log_every=0, max_batch=B)
+    train_s = time.perf_counter() - t0
+    l1_h, ss_h = T.evaluate(net, src, 4)
+    feat, true_l1 = T.gate_samples(net, src, 16)
+    net.fit_error_head(feat, true_l1, ridge=1e-2)
+    src.sim.close()
+
+    specs = scene.c3_specs()
+    vols = [(s_, *scene.make_volume(s_)) for s_ in specs]
+    probe = scene.curvilinear_probe()
+    envs = np.stack([np.arange(B) % 4, np.zeros(B)], axis=1).astype(np.int32)
+    poses = np.empty((B, 3, 4), np.float32)
+    for v in range(4):
+        idx = np.nonzero(envs[:, 0] == v)[0]
+        poses[idx] = scene.random_walk_poses(specs[v], len(idx), 1, 3000 + v)[0]
+    dv = [(torch.from_numpy(l).cuda(), torch.from_numpy(h).cuda(), s_.voxel_mm) for (s_, l, h) in vols]
+    sim = Sim(dv, scene.tissue_table(), [probe], scene.Options())
+    sim.set_tuning(8, 32, 1)
+    ec = make_envs(envs)
+    P = torch.from_numpy(poses).cuda()
+    stream = torch.cuda.Stream()
+    x = torch.zeros((B, 256, 256, 8), dtype=torch.bfloat16, device="cuda")
+    frames = torch.zeros((B, 256, 256), device="cuda")
+    phys = torch.zeros_like(frames)
+    surr = torch.zeros_like(frames)
+    pe = torch.zeros(B, device="cuda")
+    nr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    met = torch.zeros(1 + 2 * B, device="cuda")
+    seed = 0x5EED0005
+    thr = args.gate_l1
+
+    def timed(fn, k):
+        with torch.cuda.stream(stream):
+            for w in range(2):
+                fn(100 + w)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for i in range(k):
+                fn(i)
+            b.record(stream)
+            b.synchronize()
+        return a.elapsed_time(b) / k
+
+    ms_mixed = timed(lambda i: T.mixed_step(sim, net, P, seed, i, x, frames, pe, thr, nr, stream=stream, envs_c=ec),
+                     args.steps)
+    ms_phys = timed(lambda i: sim.render(None, P, seed, i, phys, stream=stream, envs_c=ec), args.steps)
+    ms_plain = timed(lambda i: sim.render_plain(None, P, seed, i, phys, stream=stream, envs_c=ec), 2)
+    ms_surr = timed(lambda i: (sim.sample_slices(None, P, x, stream=stream, envs_c=ec), net.forward(x, surr, stream=stream)),
+                    args.steps)
+    # quality of one step against the all-physics render of the same step
+    with torch.cuda.stream(stream):
+        T.mixed_step(sim, net, P, seed, 7, x, frames, pe, thr, nr, stream=stream, envs_c=ec)
+        sim.render(None, P, seed, 7, phys, stream=stream, envs_c=ec)
+        sim.sample_slices(None, P, x, stream=stream, envs_c=ec)
+        net.forward(x, surr, stream=stream)
+        net.metrics(frames, phys, met, stream=stream)
+        stream.synchronize()
+        mixed_l1, mixed_ss = float(met[1:1 + B].mean()), float(met[1 + B:].mean())
+        net.metrics(surr, phys, met, stream=stream)
+        stream.synchronize()
+        surr_l1, surr_ss = float(met[1:1 + B].mean()), float(met[1 + B:].mean())
+    net.check(stream)
+    line = {"metric": METRIC, "value": B / ms_mixed * 1e3, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 2, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": "mixed_production_1024env_curvilinear_256x512_4vol", "envs": B,
+                       "gate": f"re-render by physics where predicted L1 > {thr}"},
+            "mixed": {"frames_per_s": B / ms_mixed * 1e3, "rerendered_frac": int(nr.item()) / B,
+                      "l1_vs_physics": mixed_l1, "ssim_vs_physics": mixed_ss},
+            "surrogate_only": {"frames_per_s": B / ms_surr * 1e3, "l1_vs_physics": surr_l1, "ssim_vs_physics": surr_ss},
+            "all_physics_fused": {"frames_per_s": B / ms_phys * 1e3},
+            "all_physics_plain_per_env": {"frames_per_s": B / ms_plain * 1e3},
+            "training": {"steps": args.train_steps, "batch": 128, "pairs": 128 * args.train_steps, "seconds": train_s,
+                         "heldout_l1": l1_h, "heldout_ssim": ss_h, "loss_first_last": [hist[0][1], hist[-1][1]]}}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_2507_01152_gb300 import build
@@ -268,6 +392,12 @@ def run_ours(args):
                     "traffic": None, "peak_source": which, "kernel": "fused_render",
                     "bytes_per_launch": c2_launch_bytes(B)}
 
+    # surrogate inference throughput at 512 envs (speed only: the cost of a
+    # forward pass does not depend on the weights)
+    surrogate = None
+    if args.workload == "c2" and not args.no_surrogate:
+        surrogate = surrogate_speed(sim, wl, 512, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(wl, seconds=args.cpu_seconds)
@@ -281,7 +411,7 @@ def run_ours(args):
                            "path": "fused persistent cluster kernel, CUDA graph replay",
                            "tuning": tuning, "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "plain": plain, "clocks": clk.summary()}
+                "plain": plain, "surrogate": surrogate, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
@@ -294,15 +424,21 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "paper"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "paper", "mixed"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--gate-l1", type=float, default=0.05)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "mixed":
+        run_mixed(args)
     else:
         run_ours(args)
 

@@ -102,21 +102,24 @@ def evaluate(net, src: PairSource, n_batches: int = 2):
 
 
 def train(steps: int, batch: int = 256, c: int = 32, lr: float = 2e-4, seed: int = 0, log_every: int = 50,
-          eval_batches: int = 2, log=print, probe=None):
+          eval_batches: int = 2, log=print, probe=None, max_batch=None):
     """Train for ``steps`` steps of ``batch`` fresh pairs; returns (net,
-    source, history)."""
+    source, history).  ``max_batch`` sizes the network's buffers for later
+    inference on larger batches."""
     torch = __import__("torch")
     src = PairSource(batch, probe=probe)
-    net = make_surrogate(c, batch, lr, seed, src.probe.out_h, src.probe.out_w)
+    net = make_surrogate(c, max(batch, max_batch or 0), lr, seed, src.probe.out_h, src.probe.out_w)
     loss = torch.zeros(1 + 2 * batch, device="cuda")
     hist = []
     t0 = time.perf_counter()
     for s in range(steps):
         x, y = src.batch(s, s)
         net.train_step(x, y, loss, update=True)
-        if log_every and (s % log_every == 0 or s == steps - 1):
+        logged = log_every and s % log_every == 0
+        if logged or s == 0 or s == steps - 1:
             l = float(loss[0])
             hist.append((s, l))
-            log(f"step {s} loss {l:.4f} ({time.perf_counter() - t0:.1f} s)")
+            if log_every:
+                log(f"step {s} loss {l:.4f} ({time.perf_counter() - t0:.1f} s)")
     net.check()
     return net, src, hist
