@@ -17,8 +17,8 @@ architecture is not in the text, so the layer list below is our reading:
     head     1x1 conv (c -> 1), sigmoid
     every conv and convT is followed by ReLU (the head by the sigmoid)
 
-Loss per frame (the pix2pix L1 term, plus the structural term that
-the benchmark spec asks for): L1 + (1 - SSIM), SSIM of Wang, Bovik, Sheikh,
+Loss per frame (the pix2pix L1 term, plus a structural-similarity
+term): L1 + (1 - SSIM), SSIM of Wang, Bovik, Sheikh,
 Simoncelli 2004 (11 x 11 Gaussian window, sigma 1.5, C1 = 0.01^2,
 C2 = 0.03^2, dynamic range 1, mean over the valid region).  Batch loss =
 mean over frames.  Optimiser: Adam (Kingma & Ba 2015).
