@@ -17,7 +17,7 @@
 #include <cuda_bf16.h>
 
 #include "ussim_surrogate.h"
-#include "umma_gemm.cuh"
+#include "umma_tma.cuh"
 
 namespace ussim {
 namespace surr {
@@ -322,6 +322,62 @@ struct ConvTDgradLoader {
   }
 };
 
+// ------------------------------------------------------ TMA loaders
+// A 3x3 convolution (or the data gradient of a stride-1 one) whose operand
+// channels come in multiples of 64: every 64-wide K step lies in one tap,
+// and the tile's 128 output pixels are Yb rows x Xb columns of one image,
+// so the step's A tile is one tensor copy of the input box shifted by the
+// tap's offset (stride 2: every other pixel), the copy's zero fill
+// standing in for the padding.  B: the 64 x BN box of the weights [N][K].
+struct ConvTmaLoader {
+  static constexpr bool kTma = true;
+  CUtensorMap ta;   // activations: (C, W, H, B), traversal steps (1, s, s, 1)
+  CUtensorMap tb;   // weights: (K, N)
+  int Ho, Wo;       // grid of the GEMM rows
+  int C, stride, sign;   // channels per tap; sign +1: tap offset k - 1 (forward), -1: 1 - k (data gradient)
+  __device__ void issue(uint32_t as, uint32_t bs, int m0, int n0, int kt, uint32_t bar) const {
+    const int hw = Ho * Wo, b = m0 / hw, r = m0 - b * hw, y0 = r / Wo, x0 = r - y0 * Wo;
+    const int k = kt * kBK, tap = k / C, c0 = k - tap * C, ky = tap / 3, kx = tap - 3 * ky;
+    tma_load_4d(as, &ta, c0, x0 * stride + sign * (kx - 1), y0 * stride + sign * (ky - 1), b, bar);
+    tma_load_2d(bs, &tb, k, n0, bar);
+  }
+};
+
+// 128 pixels of one image as Yb rows x Xb columns
+inline bool conv_tma_box(int Ho, int Wo, int& Xb, int& Yb) {
+  if (Wo % kBM == 0) {
+    Xb = kBM;
+    Yb = 1;
+    return true;
+  }
+  if (kBM % Wo == 0 && Ho % (kBM / Wo) == 0) {
+    Xb = Wo;
+    Yb = kBM / Wo;
+    return true;
+  }
+  return false;
+}
+
+// activations x (C channels of a view on an Hi x Wi grid, B images) feeding
+// GEMM rows on an Ho x Wo grid; weights w [N][K]
+inline bool make_conv_tma(ConvTmaLoader& L, View x, int C, int B, int Hi, int Wi, int Ho, int Wo, int stride,
+                          int sign, const bf16* w, int K, int N, int bn) {
+  int Xb, Yb;
+  if (C % kBK || !conv_tma_box(Ho, Wo, Xb, Yb)) return false;
+  const uint64_t pitch = (uint64_t)x.cs * 2;
+  const uint64_t d[4] = {(uint64_t)C, (uint64_t)Wi, (uint64_t)Hi, (uint64_t)B};
+  const uint64_t st[3] = {pitch, pitch * Wi, pitch * Wi * Hi};
+  const uint32_t bx[4] = {(uint32_t)kBK, (uint32_t)(Xb * stride), (uint32_t)(Yb * stride), 1};
+  const uint32_t e[4] = {1, (uint32_t)stride, (uint32_t)stride, 1};
+  if (!tma::encode_bf16(&L.ta, x.p + x.co, 4, d, st, bx, e) || !rows_map(&L.tb, w, K, N, K, bn)) return false;
+  L.Ho = Ho;
+  L.Wo = Wo;
+  L.C = C;
+  L.stride = stride;
+  L.sign = sign;
+  return true;
+}
+
 // --------------------------------------------------------------- wgrad
 // Both operands of a weight gradient are stored pixel-major (channels
 // contiguous), while the GEMM reduces over pixels.  The loader reads
@@ -468,8 +524,12 @@ us_status us_conv3x3_fwd(const uint16_t* x, int32_t x_cs, int32_t x_co, const ui
   US_CHECK(y_cs % 8 == 0 && y_co % 8 == 0 && y_co + Cout <= y_cs && aligned16(x) && aligned16(y) && aligned16(w));
   const Grid in{B, H, W}, out{B, (H - 1) / stride + 1, (W - 1) / stride + 1};
   const int M = B * out.H * out.W, K = 9 * Cin, bn = pick_bn(Cout);
-  ConvFwdLoader ld{{(const bf16*)x, x_cs, x_co}, (const bf16*)w, in, out, Cin, K, Cout, stride, M, bn};
   BiasActStore ep{{(bf16*)y, y_cs, y_co}, bias, relu};
+  ConvTmaLoader tl;
+  if (make_conv_tma(tl, {(const bf16*)x, x_cs, x_co}, Cin, B, H, W, out.H, out.W, stride, 1, (const bf16*)w, K, Cout,
+                    bn))
+    return to_status(gemm_bn(bn, tl, ep, M, Cout, K, err, (cudaStream_t)stream));
+  ConvFwdLoader ld{{(const bf16*)x, x_cs, x_co}, (const bf16*)w, in, out, Cin, K, Cout, stride, M, bn};
   return to_status(gemm_bn(bn, ld, ep, M, Cout, K, err, (cudaStream_t)stream));
 }
 
@@ -482,8 +542,12 @@ us_status us_conv3x3_dgrad(const uint16_t* dy, int32_t dy_cs, int32_t dy_co, con
   US_CHECK(dx_cs % 8 == 0 && dx_co % 8 == 0 && aligned16(dy) && aligned16(wd) && aligned16(x) && aligned16(dx));
   const Grid in{B, H, W}, out{B, (H - 1) / stride + 1, (W - 1) / stride + 1};
   const int M = B * H * W, K = 9 * Cout, bn = pick_bn(Cin);
-  ConvDgradLoader ld{{(const bf16*)dy, dy_cs, dy_co}, (const bf16*)wd, in, out, Cout, K, Cin, stride, M, bn};
   MaskedGradStore ep{{(bf16*)dx, dx_cs, dx_co}, {(const bf16*)x, x_cs, x_co}, accumulate};
+  ConvTmaLoader tl;
+  if (stride == 1 &&
+      make_conv_tma(tl, {(const bf16*)dy, dy_cs, dy_co}, Cout, B, H, W, H, W, 1, -1, (const bf16*)wd, K, Cin, bn))
+    return to_status(gemm_bn(bn, tl, ep, M, Cin, K, err, (cudaStream_t)stream));
+  ConvDgradLoader ld{{(const bf16*)dy, dy_cs, dy_co}, (const bf16*)wd, in, out, Cout, K, Cin, stride, M, bn};
   return to_status(gemm_bn(bn, ld, ep, M, Cin, K, err, (cudaStream_t)stream));
 }
 
@@ -509,8 +573,11 @@ us_status us_convT2x2_fwd(const uint16_t* x, int32_t x_cs, int32_t x_co, const u
   US_CHECK(Cin % 8 == 0 && Cout % 16 == 0 && pick_bn(4 * Cout) && x_cs % 8 == 0 && x_co % 8 == 0);
   US_CHECK(y_cs % 8 == 0 && y_co % 8 == 0 && aligned16(x) && aligned16(w4) && aligned16(y));
   const int M = B * H * W, N = 4 * Cout, bn = pick_bn(N);   // 16-column chunks never straddle a (dy, dx) block
-  ConvTFwdLoader ld{{(const bf16*)x, x_cs, x_co}, (const bf16*)w4, Cin, N, M, bn};
   ConvTStore ep{{(bf16*)y, y_cs, y_co}, bias, {B, H, W}, Cout, relu};
+  RowsTmaLoader tl;
+  if (rows_map(&tl.ta, (const bf16*)x + x_co, x_cs, M, Cin, kBM) && rows_map(&tl.tb, (const bf16*)w4, Cin, N, Cin, bn))
+    return to_status(gemm_bn(bn, tl, ep, M, N, Cin, err, (cudaStream_t)stream));
+  ConvTFwdLoader ld{{(const bf16*)x, x_cs, x_co}, (const bf16*)w4, Cin, N, M, bn};
   return to_status(gemm_bn(bn, ld, ep, M, N, Cin, err, (cudaStream_t)stream));
 }
 

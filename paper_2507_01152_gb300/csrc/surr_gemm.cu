@@ -1,38 +1,16 @@
 // Plain BF16 GEMM on the tcgen05 tile kernel (C = A B^T, FP32 out): the
 // building block of the surrogate's implicit-GEMM convolutions, exposed
-// as its own op so it can be checked in isolation.
+// as its own op so it can be checked in isolation.  Operands are staged
+// with tensor copies (rows and K past the end read as zero).
 #include <cuda_bf16.h>
 
 #include "ussim_surrogate.h"
-#include "umma_gemm.cuh"
+#include "umma_tma.cuh"
 
 namespace ussim {
 namespace {
 
 using namespace umma;
-
-struct RowMajorLoader {
-  static constexpr bool kAsync = true;
-  const __nv_bfloat16* A;
-  const __nv_bfloat16* B;
-  int M, N, K, bn;
-  struct State {};
-  __device__ void prepare(State&, int, int, int) const {}
-  __device__ void load(const State&, uint8_t* as, uint8_t* bs, int m0, int n0, int kt, int tid) const {
-    for (int c = tid; c < kBM * 8; c += kProducers) {
-      const int r = (c & 7) + ((c >> 6) << 3), kc = (c >> 3) & 7;
-      const int m = m0 + r, k = kt * kBK + kc * 8;
-      const bool v = m < M && k < K;
-      cp_async16(as + tile_off(r, kc, kBK), v ? (const void*)(A + (size_t)m * K + k) : (const void*)A, v ? 16u : 0u);
-    }
-    for (int c = tid; c < bn * 8; c += kProducers) {
-      const int r = (c & 7) + ((c >> 6) << 3), kc = (c >> 3) & 7;
-      const int n = n0 + r, k = kt * kBK + kc * 8;
-      const bool v = n < N && k < K;
-      cp_async16(bs + tile_off(r, kc, kBK), v ? (const void*)(B + (size_t)n * K + k) : (const void*)B, v ? 16u : 0u);
-    }
-  }
-};
 
 struct F32Store {
   float* C;
@@ -61,7 +39,8 @@ extern "C" us_status us_gemm_bf16_nt(const uint16_t* A, const uint16_t* B, float
   const auto* b = reinterpret_cast<const __nv_bfloat16*>(B);
   cudaError_t e;
   const int bn = (N % 256 == 0) ? 256 : (N % 128 == 0) ? 128 : (N % 64 == 0) ? 64 : 32;
-  RowMajorLoader ld{a, b, M, N, K, bn};
+  umma::RowsTmaLoader ld;
+  if (!umma::rows_map(&ld.ta, a, K, M, K, umma::kBM) || !umma::rows_map(&ld.tb, b, K, N, K, bn)) return US_ERR_CUDA;
   F32Store ep{C, N};
   switch (bn) {
     case 256: e = umma::launch_umma_gemm<256>(ld, ep, M, N, K, err, st); break;

@@ -5,7 +5,9 @@
 // output tiles and runs three roles concurrently:
 //   warps 0-7  producers: gather the operands of each 64-wide K step into
 //              one of the shared-memory stages (cp.async or plain stores),
-//              up to `stages` steps ahead of the tensor core;
+//              up to `stages` steps ahead of the tensor core; loaders that
+//              describe their operands as tensor maps instead have one
+//              thread issue two tiled tensor copies (TMA) per stage;
 //   warp 8     one thread issues the four 128 x BN x 16 MMAs of a stage and
 //              commits them to the stage's "empty" barrier;
 //   warps 9-12 epilogue: read a finished accumulator with tcgen05.ld and
@@ -18,6 +20,8 @@
 // shared abort flag that all roles check, so the CTA still drains its
 // copies, waits for its MMAs and frees its TMEM.
 #pragma once
+#include <type_traits>
+
 #include "umma.cuh"
 
 namespace ussim {
@@ -55,6 +59,13 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// loaders that stage a K step with tensor copies declare kTma = true and
+// provide issue(a_smem, b_smem, m0, n0, kt, bar)
+template <class L, class = void>
+struct is_tma_loader : std::false_type {};
+template <class L>
+struct is_tma_loader<L, std::void_t<decltype(L::kTma)>> : std::integral_constant<bool, L::kTma> {};
+
 // bounded wait that also gives up when another role has aborted
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                               unsigned* err) {
@@ -78,12 +89,18 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
 //           n0.., K step kt (global index), into the K-major 128-byte-swizzled
 //           layout (tile_off(r, kc, kBK) for 16-byte chunk kc of row r); steps past
 //           the end of K must load zeros.  Called by the kProducers producer threads.
+//           TMA loaders (kTma) instead: issue(a_stage, b_stage, m0, n0, kt,
+//           full_bar), called by one thread, copying exactly stage_bytes<BN>()
+//           into the same layout (128-byte swizzled boxes; zero fill outside the
+//           tensor).
 // Epilogue: store(int m, int n0, const float* v16, bool valid).
 // Tiles: mt x nt x splits, M fastest; split z covers K steps z*k_tiles ...
 template <int BN, class Loader, class Epilogue>
-__global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilogue ep, int M, int mt, int nt,
-                                                                 int n_tiles, int k_tiles, unsigned* err) {
+__global__ void __launch_bounds__(kThreads, 1)
+    umma_gemm_kernel(const __grid_constant__ Loader ld, Epilogue ep, int M, int mt, int nt, int n_tiles, int k_tiles,
+                     unsigned* err) {
   constexpr int S = gemm_stages<BN>();
+  constexpr bool TMA = is_tma_loader<Loader>::value;
   constexpr uint32_t NCOL = tmem_cols<BN>();
   constexpr uint32_t IDESC = idesc_bf16_f32(kBM, BN);
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -99,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilo
   }
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], kProducers);
+      mbar_init(&full[s], TMA ? 1 : kProducers);
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -117,30 +134,56 @@ __global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilo
 
   if (warp < kMmaWarp) {
     // ---------------------------------------------------------- producers
-    long long g = 0;   // global K-step counter over this CTA's tiles
-    for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x) {
-      const int z = tile / (mt * nt), rem = tile - z * mt * nt, ni = rem / mt, mi = rem - ni * mt;
-      const int m0 = mi * kBM, n0 = ni * BN, kt0 = z * k_tiles;
-      typename Loader::State st;
-      ld.prepare(st, m0, n0, tid);
-      bool ok = true;
-      for (int t = 0; t < k_tiles; ++t, ++g) {
-        const int s = (int)(g % S);
-        if (g >= S && !wait_or_abort(&empty[s], (uint32_t)((g / S - 1) & 1), &abort_flag, err)) {
-          ok = false;
-          break;
+    if constexpr (TMA) {
+      if (tid == 0) {
+        long long g = 0;
+        for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x) {
+          const int z = tile / (mt * nt), rem = tile - z * mt * nt, ni = rem / mt, mi = rem - ni * mt;
+          const int m0 = mi * kBM, n0 = ni * BN, kt0 = z * k_tiles;
+          bool ok = true;
+          for (int t = 0; t < k_tiles; ++t, ++g) {
+            const int s = (int)(g % S);
+            if (g >= S && !wait_or_abort(&empty[s], (uint32_t)((g / S - 1) & 1), &abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&full[s], stage_bytes<BN>());
+            const uint32_t sa = smem_u32(smem + s * stage_bytes<BN>());
+            ld.issue(sa, sa + kTileA, m0, n0, kt0 + t, smem_u32(&full[s]));
+          }
+          if (!ok) break;
         }
-        ld.load(st, smem + s * stage_bytes<BN>(), smem + s * stage_bytes<BN>() + kTileA, m0, n0, kt0 + t, tid);
-        // cp.async loaders: the barrier completes when the copies land; loaders
-        // that store from registers release their stores with a plain arrive
-        if (Loader::kAsync)
-          cp_async_arrive(&full[s]);
-        else
-          mbar_arrive(&full[s]);
+        // every issued copy must have landed before the CTA may exit (on an
+        // abort the MMA thread may not have consumed them)
+        for (long long q = g > S ? g - S : 0; q < g; ++q)
+          if (!mbar_wait(&full[q % S], (uint32_t)((q / S) & 1))) atomicOr(err, kErrWaitTimeout);
       }
-      if (!ok) break;
+    } else {
+      long long g = 0;   // global K-step counter over this CTA's tiles
+      for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x) {
+        const int z = tile / (mt * nt), rem = tile - z * mt * nt, ni = rem / mt, mi = rem - ni * mt;
+        const int m0 = mi * kBM, n0 = ni * BN, kt0 = z * k_tiles;
+        typename Loader::State st;
+        ld.prepare(st, m0, n0, tid);
+        bool ok = true;
+        for (int t = 0; t < k_tiles; ++t, ++g) {
+          const int s = (int)(g % S);
+          if (g >= S && !wait_or_abort(&empty[s], (uint32_t)((g / S - 1) & 1), &abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          ld.load(st, smem + s * stage_bytes<BN>(), smem + s * stage_bytes<BN>() + kTileA, m0, n0, kt0 + t, tid);
+          // cp.async loaders: the barrier completes when the copies land; loaders
+          // that store from registers release their stores with a plain arrive
+          if (Loader::kAsync)
+            cp_async_arrive(&full[s]);
+          else
+            mbar_arrive(&full[s]);
+        }
+        if (!ok) break;
+      }
+      cp_async_wait<0>();
     }
-    cp_async_wait<0>();
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------- MMA issue
     if (lane == 0) {
@@ -159,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_gemm_kernel(Loader ld, Epilo
             break;
           }
           tc_fence_after();
-          fence_proxy_async();   // the stage was written through the generic proxy; the MMA reads it async
+          if (!TMA) fence_proxy_async();   // stage written through the generic proxy; the MMA reads it async
           const uint32_t sa = smem_u32(smem + s * stage_bytes<BN>()), sb = sa + kTileA;
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k)
