@@ -324,23 +324,39 @@ struct ConvTDgradLoader {
 
 // ------------------------------------------------------ TMA loaders
 // A 3x3 convolution (or the data gradient of a stride-1 one) whose operand
-// channels come in multiples of 64: every 64-wide K step lies in one tap,
-// and the tile's 128 output pixels are Yb rows x Xb columns of one image,
-// so the step's A tile is one tensor copy of the input box shifted by the
-// tap's offset (stride 2: every other pixel), the copy's zero fill
-// standing in for the padding.  B: the 64 x BN box of the weights [N][K].
+// channels C are a multiple of CB (64, 32 or 8): every CB-wide slice of a
+// 64-wide K step lies in one tap, and the tile's 128 output pixels are
+// Yb rows x Xb columns of one image, so each slice of the step's A tile
+// is one tensor copy of the input box shifted by the tap's offset
+// (stride 2: every other pixel), the copy's zero fill standing in for the
+// padding; slices past K copy a box wholly outside the image (zeros).
+// B: the 64 x BN box of the weights [N][K].
+template <int CB>
 struct ConvTmaLoader {
   static constexpr bool kTma = true;
+  static constexpr int kALayout = CB == 64 ? 0 : (CB == 32 ? 1 : 2);
+  static constexpr int kSlices = kBK / CB;
+  static constexpr uint32_t kSliceBytes = kBM * CB * 2;
   CUtensorMap ta;   // activations: (C, W, H, B), traversal steps (1, s, s, 1)
   CUtensorMap tb;   // weights: (K, N)
   int Ho, Wo;       // grid of the GEMM rows
+  int Hi;           // input rows
   int C, stride, sign;   // channels per tap; sign +1: tap offset k - 1 (forward), -1: 1 - k (data gradient)
-  __device__ void issue(uint32_t as, uint32_t bs, int m0, int n0, int kt, uint32_t bar) const {
+  // tiles past the last row (m0 >= B Ho Wo) land wholly outside the batch: zeros
+  __device__ void issue_a(uint32_t as, int m0, int kt, uint32_t bar) const {
     const int hw = Ho * Wo, b = m0 / hw, r = m0 - b * hw, y0 = r / Wo, x0 = r - y0 * Wo;
-    const int k = kt * kBK, tap = k / C, c0 = k - tap * C, ky = tap / 3, kx = tap - 3 * ky;
-    tma_load_4d(as, &ta, c0, x0 * stride + sign * (kx - 1), y0 * stride + sign * (ky - 1), b, bar);
-    tma_load_2d(bs, &tb, k, n0, bar);
+    const int k = kt * kBK;
+#pragma unroll
+    for (int j = 0; j < kSlices; ++j) {
+      const int kk = k + j * CB, tap = kk / C, c0 = kk - tap * C, ky = tap / 3, kx = tap - 3 * ky;
+      if (tap < 9)
+        tma_load_4d(as + j * kSliceBytes, &ta, c0, x0 * stride + sign * (kx - 1), y0 * stride + sign * (ky - 1), b,
+                    bar);
+      else
+        tma_load_4d(as + j * kSliceBytes, &ta, 0, 0, Hi, b, bar);
+    }
   }
+  __device__ void issue_b(uint32_t bs, int n0, int kt, uint32_t bar) const { tma_load_2d(bs, &tb, kt * kBK, n0, bar); }
 };
 
 // 128 pixels of one image as Yb rows x Xb columns
@@ -360,22 +376,51 @@ inline bool conv_tma_box(int Ho, int Wo, int& Xb, int& Yb) {
 
 // activations x (C channels of a view on an Hi x Wi grid, B images) feeding
 // GEMM rows on an Ho x Wo grid; weights w [N][K]
-inline bool make_conv_tma(ConvTmaLoader& L, View x, int C, int B, int Hi, int Wi, int Ho, int Wo, int stride,
+template <int CB>
+inline bool make_conv_tma(ConvTmaLoader<CB>& L, View x, int C, int B, int Hi, int Wi, int Ho, int Wo, int stride,
                           int sign, const bf16* w, int K, int N, int bn) {
   int Xb, Yb;
-  if (C % kBK || !conv_tma_box(Ho, Wo, Xb, Yb)) return false;
+  if (C % CB || !conv_tma_box(Ho, Wo, Xb, Yb)) return false;
   const uint64_t pitch = (uint64_t)x.cs * 2;
   const uint64_t d[4] = {(uint64_t)C, (uint64_t)Wi, (uint64_t)Hi, (uint64_t)B};
   const uint64_t st[3] = {pitch, pitch * Wi, pitch * Wi * Hi};
-  const uint32_t bx[4] = {(uint32_t)kBK, (uint32_t)(Xb * stride), (uint32_t)(Yb * stride), 1};
+  const uint32_t bx[4] = {(uint32_t)CB, (uint32_t)(Xb * stride), (uint32_t)(Yb * stride), 1};
   const uint32_t e[4] = {1, (uint32_t)stride, (uint32_t)stride, 1};
-  if (!tma::encode_bf16(&L.ta, x.p + x.co, 4, d, st, bx, e) || !rows_map(&L.tb, w, K, N, K, bn)) return false;
+  if (!tma::encode_bf16(&L.ta, x.p + x.co, 4, d, st, bx, e, CB == 8 ? 0 : 2 * CB) || !rows_map(&L.tb, w, K, N, K, bn))
+    return false;
   L.Ho = Ho;
   L.Wo = Wo;
+  L.Hi = Hi;
   L.C = C;
   L.stride = stride;
   L.sign = sign;
   return true;
+}
+
+// run a convolution GEMM through the TMA loader with the widest channel
+// slice that divides C; false if its shape does not fit one
+template <class Ep>
+bool conv_tma(cudaError_t& e, View x, int C, int B, int Hi, int Wi, int Ho, int Wo, int stride, int sign,
+              const bf16* w, int K, int N, int bn, const Ep& ep, int M, unsigned* err, cudaStream_t st) {
+  if (C % 64 == 0) {
+    ConvTmaLoader<64> L;
+    if (!make_conv_tma(L, x, C, B, Hi, Wi, Ho, Wo, stride, sign, w, K, N, bn)) return false;
+    e = gemm_bn(bn, L, ep, M, N, K, err, st);
+    return true;
+  }
+  if (C % 32 == 0) {
+    ConvTmaLoader<32> L;
+    if (!make_conv_tma(L, x, C, B, Hi, Wi, Ho, Wo, stride, sign, w, K, N, bn)) return false;
+    e = gemm_bn(bn, L, ep, M, N, K, err, st);
+    return true;
+  }
+  if (C % 8 == 0 && bn == 32) {   // only the first layer (8 input channels) takes this path
+    ConvTmaLoader<8> L;
+    if (!make_conv_tma(L, x, C, B, Hi, Wi, Ho, Wo, stride, sign, w, K, N, bn)) return false;
+    e = launch_umma_gemm<32, 4>(L, ep, M, N, K, err, st);
+    return true;
+  }
+  return false;
 }
 
 // --------------------------------------------------------------- wgrad
@@ -469,15 +514,18 @@ struct AtomicF32Store {   // G[m][n] += v (FP32), rows < M
 };
 
 // --------------------------------------------------------------- launch
+// TMA loaders run narrow tiles with several issuing warps (tiles per group):
+// 4 up to BN = 64, 2 at 128, 1 at 256
 template <class Ld, class Ep>
 cudaError_t gemm_bn(int bn, const Ld& ld, const Ep& ep, int M, int N, int K, unsigned* err, cudaStream_t st,
                     int splits = 1) {
+  constexpr bool T = is_tma_loader<Ld>::value;
   switch (bn) {
-    case 256: return launch_umma_gemm<256>(ld, ep, M, N, K, err, st, splits);
-    case 128: return launch_umma_gemm<128>(ld, ep, M, N, K, err, st, splits);
-    case 64: return launch_umma_gemm<64>(ld, ep, M, N, K, err, st, splits);
-    case 32: return launch_umma_gemm<32>(ld, ep, M, N, K, err, st, splits);
-    case 16: return launch_umma_gemm<16>(ld, ep, M, N, K, err, st, splits);
+    case 256: return launch_umma_gemm<256, 1>(ld, ep, M, N, K, err, st, splits);
+    case 128: return launch_umma_gemm<128, T ? 2 : 1>(ld, ep, M, N, K, err, st, splits);
+    case 64: return launch_umma_gemm<64, T ? 4 : 1>(ld, ep, M, N, K, err, st, splits);
+    case 32: return launch_umma_gemm<32, T ? 4 : 1>(ld, ep, M, N, K, err, st, splits);
+    case 16: return launch_umma_gemm<16, T ? 4 : 1>(ld, ep, M, N, K, err, st, splits);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -525,10 +573,10 @@ us_status us_conv3x3_fwd(const uint16_t* x, int32_t x_cs, int32_t x_co, const ui
   const Grid in{B, H, W}, out{B, (H - 1) / stride + 1, (W - 1) / stride + 1};
   const int M = B * out.H * out.W, K = 9 * Cin, bn = pick_bn(Cout);
   BiasActStore ep{{(bf16*)y, y_cs, y_co}, bias, relu};
-  ConvTmaLoader tl;
-  if (make_conv_tma(tl, {(const bf16*)x, x_cs, x_co}, Cin, B, H, W, out.H, out.W, stride, 1, (const bf16*)w, K, Cout,
-                    bn))
-    return to_status(gemm_bn(bn, tl, ep, M, Cout, K, err, (cudaStream_t)stream));
+  cudaError_t e;
+  if (conv_tma(e, {(const bf16*)x, x_cs, x_co}, Cin, B, H, W, out.H, out.W, stride, 1, (const bf16*)w, K, Cout, bn, ep,
+               M, err, (cudaStream_t)stream))
+    return to_status(e);
   ConvFwdLoader ld{{(const bf16*)x, x_cs, x_co}, (const bf16*)w, in, out, Cin, K, Cout, stride, M, bn};
   return to_status(gemm_bn(bn, ld, ep, M, Cout, K, err, (cudaStream_t)stream));
 }
@@ -543,10 +591,10 @@ us_status us_conv3x3_dgrad(const uint16_t* dy, int32_t dy_cs, int32_t dy_co, con
   const Grid in{B, H, W}, out{B, (H - 1) / stride + 1, (W - 1) / stride + 1};
   const int M = B * H * W, K = 9 * Cout, bn = pick_bn(Cin);
   MaskedGradStore ep{{(bf16*)dx, dx_cs, dx_co}, {(const bf16*)x, x_cs, x_co}, accumulate};
-  ConvTmaLoader tl;
-  if (stride == 1 &&
-      make_conv_tma(tl, {(const bf16*)dy, dy_cs, dy_co}, Cout, B, H, W, H, W, 1, -1, (const bf16*)wd, K, Cin, bn))
-    return to_status(gemm_bn(bn, tl, ep, M, Cin, K, err, (cudaStream_t)stream));
+  cudaError_t e;
+  if (stride == 1 && conv_tma(e, {(const bf16*)dy, dy_cs, dy_co}, Cout, B, H, W, H, W, 1, -1, (const bf16*)wd, K, Cin,
+                              bn, ep, M, err, (cudaStream_t)stream))
+    return to_status(e);
   ConvDgradLoader ld{{(const bf16*)dy, dy_cs, dy_co}, (const bf16*)wd, in, out, Cout, K, Cin, stride, M, bn};
   return to_status(gemm_bn(bn, ld, ep, M, Cin, K, err, (cudaStream_t)stream));
 }

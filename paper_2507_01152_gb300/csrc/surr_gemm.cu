@@ -43,10 +43,10 @@ extern "C" us_status us_gemm_bf16_nt(const uint16_t* A, const uint16_t* B, float
   if (!umma::rows_map(&ld.ta, a, K, M, K, umma::kBM) || !umma::rows_map(&ld.tb, b, K, N, K, bn)) return US_ERR_CUDA;
   F32Store ep{C, N};
   switch (bn) {
-    case 256: e = umma::launch_umma_gemm<256>(ld, ep, M, N, K, err, st); break;
-    case 128: e = umma::launch_umma_gemm<128>(ld, ep, M, N, K, err, st); break;
-    case 64: e = umma::launch_umma_gemm<64>(ld, ep, M, N, K, err, st); break;
-    default: e = umma::launch_umma_gemm<32>(ld, ep, M, N, K, err, st); break;
+    case 256: e = umma::launch_umma_gemm<256, 1>(ld, ep, M, N, K, err, st); break;
+    case 128: e = umma::launch_umma_gemm<128, 2>(ld, ep, M, N, K, err, st); break;
+    case 64: e = umma::launch_umma_gemm<64, 4>(ld, ep, M, N, K, err, st); break;
+    default: e = umma::launch_umma_gemm<32, 4>(ld, ep, M, N, K, err, st); break;
   }
   return e == cudaSuccess ? US_OK : US_ERR_CUDA;
 }

@@ -28,14 +28,16 @@ inline EncodeTiledFn encoder() {
 }
 
 // BF16 tensor of `rank` dimensions (innermost first): extents `dims`,
-// byte strides of dimensions 1.. in `strides`, copy box `box` (innermost
-// box extent 64 elements = one 128-byte swizzle row), traversal steps
-// `steps` (1 = dense).  Elements outside the tensor read as zero.
-// Returns false when the driver rejects the description.
+// byte strides of dimensions 1.. in `strides`, copy box `box`, traversal
+// steps `steps` (1 = dense).  The shared-memory image of a box has rows of
+// box[0] elements; `swizzle_bytes` (128, 64 or 0) names the swizzle of
+// those rows, which must then be exactly that long.  Elements outside the
+// tensor read as zero.  Returns false when the driver rejects the
+// description.
 inline bool encode_bf16(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
-                        const uint32_t* box, const uint32_t* steps) {
+                        const uint32_t* box, const uint32_t* steps, int swizzle_bytes = 128) {
   const EncodeTiledFn f = encoder();
-  if (!f) return false;
+  if (!f || (swizzle_bytes && (uint64_t)box[0] * 2 != (uint64_t)swizzle_bytes)) return false;
   cuuint64_t d[5], st[4];
   cuuint32_t b[5], e[5];
   for (int i = 0; i < rank; ++i) {
@@ -45,7 +47,10 @@ inline bool encode_bf16(CUtensorMap* m, const void* base, int rank, const uint64
     if (i + 1 < rank) st[i] = strides[i];
   }
   return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), d, st, b, e,
-           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_INTERLEAVE_NONE,
+           swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : (swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE),
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

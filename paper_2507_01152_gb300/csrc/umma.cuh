@@ -119,6 +119,19 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// 64-byte swizzle, K-major: rows of 32 BF16 (64 B), 8-row atoms of 512 B
+// (SBO), chunk c of row r at position c ^ ((r / 2) mod 4); a K step of 16
+// elements advances the start address by 32 B.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;                  // SWIZZLE_64B
+  return d;
+}
+
 // Instruction descriptor of kind::f16: D = F32 [4,6), A = BF16 [7,10),
 // B = BF16 [10,13), both K-major (bits 15, 16 = 0), N >> 3 at [17,23),
 // M >> 4 at [24,29).

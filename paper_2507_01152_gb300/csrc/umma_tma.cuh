@@ -16,10 +16,8 @@ namespace umma {
 struct RowsTmaLoader {
   static constexpr bool kTma = true;
   CUtensorMap ta, tb;
-  __device__ void issue(uint32_t as, uint32_t bs, int m0, int n0, int kt, uint32_t bar) const {
-    tma_load_2d(as, &ta, kt * kBK, m0, bar);
-    tma_load_2d(bs, &tb, kt * kBK, n0, bar);
-  }
+  __device__ void issue_a(uint32_t as, int m0, int kt, uint32_t bar) const { tma_load_2d(as, &ta, kt * kBK, m0, bar); }
+  __device__ void issue_b(uint32_t bs, int n0, int kt, uint32_t bar) const { tma_load_2d(bs, &tb, kt * kBK, n0, bar); }
 };
 
 // a [rows][K] BF16 matrix with row pitch `pitch` elements, copied in

@@ -44,7 +44,12 @@ def relu_input(g, shape):
 
 @pytest.mark.parametrize("B,H,W,Cin,Cout,stride,cs_in,co_in", [
     (2, 20, 20, 8, 32, 1, 8, 0), (2, 17, 23, 32, 64, 2, 64, 32), (2, 16, 16, 16, 16, 1, 32, 16), (1, 12, 12, 64, 256, 1, 64, 0),
-    (3, 9, 10, 128, 128, 2, 256, 128)])
+    (3, 9, 10, 128, 128, 2, 256, 128),
+    # shapes whose 128-pixel tiles are boxes of one image (tensor-copy loaders):
+    # 64-channel taps (4 rows x 32), 32-channel taps on 256-wide rows read
+    # from a channel slice, stride 2 with 64- and 32-channel taps, 8-channel taps
+    (2, 32, 32, 64, 64, 1, 64, 0), (2, 8, 256, 32, 32, 1, 64, 32), (2, 32, 32, 64, 128, 2, 128, 64),
+    (2, 64, 64, 32, 64, 2, 32, 0), (1, 16, 128, 8, 32, 1, 8, 0)])
 def test_conv3x3_forward_dgrad_wgrad(B, H, W, Cin, Cout, stride, cs_in, co_in):
     g = torch.Generator().manual_seed(B * 1000 + H * 31 + Cin + Cout)
     xfull = relu_input(g, (B, H, W, cs_in))
