@@ -122,10 +122,17 @@ typedef struct {
   int32_t volume_id, probe_id;
 } us_env;
 
-/* Launch shape of the fused batched render. */
+/* Launch shape of the batched render.
+ * cluster_size 4, 8 or 16: persistent cluster kernel, one thread-block
+ *   cluster per environment frame (the frame stays in distributed shared
+ *   memory); warps_per_cta 8, 16 or 32 (4-CTA clusters: 16 or 32).
+ * cluster_size 1: two-pass path without clusters, warps_per_cta (8, 16 or
+ *   32) lines per block; the axially filtered lines go through a global
+ *   buffer of the batch's beam size, allocated on first use per batch
+ *   signature.  Same frames as the cluster kernel. */
 typedef struct {
-  int32_t cluster_size;  /* CTAs per environment frame: 4, 8 or 16 */
-  int32_t warps_per_cta; /* 8, 16 or 32 (4 / 8 / 16 clusters: 16-32 / 8-32 / 8-32) */
+  int32_t cluster_size;  /* 1, 4, 8 or 16 */
+  int32_t warps_per_cta; /* 8, 16 or 32 */
   int32_t use_graph;     /* 1: replay a captured CUDA graph per batch signature
                             (not on the legacy NULL stream, nor while the
                             caller's stream is itself being captured) */
@@ -228,10 +235,13 @@ US_API us_status us_sim_render_gated(us_sim* sim, const us_env* envs, int32_t B,
 US_API us_status us_sim_check(us_sim* sim, void* stream);
 
 US_API us_status us_sim_get_tuning(const us_sim* sim, us_tuning* t);
-/* Set the fused kernel's launch shape; invalid shapes are rejected. */
+/* Set the batched render's launch shape; invalid shapes are rejected
+ * (US_ERR_INVALID_ARG), shapes whose buffers do not fit this probe set in
+ * shared memory too (US_ERR_UNSUPPORTED). */
 US_API us_status us_sim_set_tuning(us_sim* sim, const us_tuning* t);
 
-/* Time the fused render over the candidate launch shapes on this batch
+/* Time the batched render over the candidate launch shapes (cluster and
+ * two-pass) on this batch
  * (synchronous, renders into `frames`), keep the fastest, and append it to
  * the text cache at cache_path (may be NULL: no cache).  If cache_path
  * already holds an entry for this GPU, probe set and batch signature it is

@@ -1,0 +1,306 @@
+// Two-pass batched render without clusters.
+//
+// Pass A (split_lines): one block per (environment, group of G lines), one
+// warp per line.  The block takes the nearest labels of its lines and of up
+// to kThetaDMax lines on either side (the incidence stencil's reach), the
+// impedance of its own lines, runs the scanline model and the in-place
+// axial PSF, and writes the axially filtered line to a beam-layout buffer
+// in global memory (L2-resident for moderate batches).
+//
+// Pass B (split_image): one block per (environment, wedge of G lines).  The
+// block stages the filtered lines its wedge needs (its lines, one more line
+// for the bilinear step, and the lateral PSF's reach on both sides), forms
+// the lateral PSF and the log image of its lines in shared memory, and
+// scan-converts the output pixels assigned to the wedge: a host-built list,
+// per probe, of the pixels whose bilinear footprint lies on the wedge's
+// lines (pixels outside the fan go to the wedge of the preceding in-fan
+// pixel of their row), so every read is local.
+//
+// Blocks are numbered item-major over the costliest-first work list; a
+// block whose group lies past its probe's lines, or whose item lies past a
+// device-side item count, exits at once.  Per-line arithmetic, tap order and
+// bilinear formula are those of the plain and cluster paths, so all three
+// produce identical frames.
+#include <algorithm>
+#include <cstring>
+
+#include "us_internal.h"
+#include "us_scanline.cuh"
+
+namespace ussim {
+
+// axial PSF of one padded row in place (K zeros, NS samples, K zeros)
+__device__ __forceinline__ void axial_psf_row(float* prow, int NS, const float* w, int K, int lane) {
+  float prev = 0.f;
+  int prev_s = -1;
+  const int taps = 2 * K + 1;
+  for (int c = 0; c < NS; c += 32) {
+    const int s = c + lane;
+    float acc = 0.f;
+    if (s < NS) {
+      const float* q = prow + s;
+      for (int k = 0; k < taps; ++k) acc = fmaf(w[k], q[k], acc);
+    }
+    __syncwarp();
+    if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
+    __syncwarp();
+    prev = acc;
+    prev_s = s;
+  }
+  if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
+  __syncwarp();
+}
+
+struct SplitCtx {
+  EnvItem it;
+  DevProbe P;
+  DevVolume V;
+  DevPair pair;
+  Pose M;
+  int finite, valid;
+};
+
+// load the item of block `blk` (groups per item gpi) into shared memory;
+// returns false (for the whole block) if the block has no work
+__device__ __forceinline__ bool split_item(const RenderParams& p, int gpi, int G, SplitCtx& cx, int& group) {
+  const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
+  const int item = blockIdx.x / gpi;
+  group = blockIdx.x - item * gpi;
+  if (threadIdx.x == 0) {
+    cx.valid = 0;
+    if (item < n_items) {
+      const EnvItem it = p.items[item];
+      const DevProbe P = p.probes[it.probe];
+      if (group * G < P.nl) {
+        cx.it = it;
+        cx.P = P;
+        cx.V = p.vols[it.vol];
+        cx.pair = p.pairs[it.pair];
+        bool finite;
+        cx.M = load_pose(p.poses, it.b, finite);
+        cx.finite = finite;
+        cx.valid = 1;
+      }
+    }
+  }
+  __syncthreads();
+  return cx.valid != 0;
+}
+
+__global__ void __launch_bounds__(1024, 1) split_lines(RenderParams p, SplitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SplitCtx cx;
+  int group;
+  if (!split_item(p, a.gpi_lines, a.G, cx, group)) return;
+  const DevProbe& P = cx.P;
+  const int NL = P.nl, NS = P.ns, KA = P.k_ax, G = a.G;
+  const int RS = (NS + 2 * KA) | 1;
+  const int g0 = group * G, g1 = min(g0 + G, NL);
+  const int L0 = max(g0 - kThetaDMax, 0), L1 = min(g1 + kThetaDMax, NL);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NW = blockDim.x >> 5;
+  float* zbuf = reinterpret_cast<float*>(smem);                      // [G][RS]
+  float* wax = reinterpret_cast<float*>(smem + a.off_wax);
+  DevTissue* tis = reinterpret_cast<DevTissue*>(smem + a.off_tis);
+  uint8_t* lbuf = smem + a.off_lab;                                   // [L1 - L0][NS]
+  for (int t = tid; t < 2 * KA + 1; t += blockDim.x) wax[t] = __ldg(&P.w_ax[t]);
+  for (int t = tid; t < p.n_labels; t += blockDim.x) tis[t] = P.tissue[t];
+  if (!cx.finite && group == 0 && tid == 0) atomicOr(p.err, kErrNonFinitePose);
+  __syncthreads();
+
+  // labels of lines L0 .. L1-1; impedance of own lines g0 .. g1-1
+  for (int i = warp; i < L1 - L0; i += NW) {
+    const int l = L0 + i;
+    const bool own = l >= g0 && l < g1;
+    const float2 ln = P.lines[l];
+    uint8_t* lrow = lbuf + i * NS;
+    float* zrow = own ? zbuf + (l - g0) * RS + KA : nullptr;
+    for (int s = lane; s < NS; s += 32) {
+      float x, z;
+      beam_point(P, ln, s, x, z);
+      const float3 u = to_voxel(cx.M, cx.V.inv_h, x, z);
+      const int vi = nearest_voxel(cx.V, u);
+      const uint8_t lb = vi >= 0 ? __ldg(&cx.V.labels[vi]) : (uint8_t)0;
+      lrow[s] = lb;
+      if (own) {
+        zrow[s] = p.z_mode == 0 ? fmaxf(trilinear_hu(cx.V, u) + 1024.f, 1.f) : tis[lb].z;
+        if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + s] = vi;
+        if (p.label) p.label[cx.it.beam_off + (long long)l * NS + s] = lb;
+      }
+    }
+    if (own)
+      for (int q = lane; q < KA; q += 32) {
+        zrow[q - KA] = 0.f;
+        zrow[NS + q] = 0.f;
+      }
+  }
+  __syncthreads();
+
+  // scanline model and axial PSF of own lines, one warp per line
+  for (int l = g0 + warp; l < g1; l += NW) {
+    float* prow = zbuf + (l - g0) * RS;
+    float* row = prow + KA;
+    const uint8_t* lrow = lbuf + (l - L0) * NS;
+    auto labf = [&](int line, int s) -> unsigned { return lbuf[(line - L0) * NS + s]; };
+    auto own = [&](int s) -> unsigned { return lrow[s]; };
+    auto zf = [&](int s) -> float { return row[s]; };
+    scanline_model(p, P, tis, cx.pair, cx.it.b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; });
+    __syncwarp();
+    axial_psf_row(prow, NS, wax, KA, lane);
+    float* dst = a.beam + cx.it.beam_off + (long long)l * NS;
+    for (int s = lane; s < NS; s += 32) dst[s] = row[s];
+  }
+}
+
+__global__ void __launch_bounds__(1024, 1) split_image(RenderParams p, SplitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SplitCtx cx;
+  int group;
+  if (!split_item(p, a.gpi_image, a.G, cx, group)) return;
+  const DevProbe& P = cx.P;
+  const int NL = P.nl, NS = P.ns, KL = P.k_lat, G = a.G;
+  const int w0 = group * G, w1 = min(w0 + G, NL);
+  const int y1 = min(w1 + 1, NL);                                    // log rows w0 .. y1-1
+  const int a0 = max(w0 - KL, 0), a1 = min(y1 + KL, NL);             // filtered rows staged
+  const int tid = threadIdx.x;
+  float* abuf = reinterpret_cast<float*>(smem);                      // [a1 - a0][NS]
+  float* ybuf = reinterpret_cast<float*>(smem + a.off_y);            // [y1 - w0][NS]
+  float* wlat = reinterpret_cast<float*>(smem + a.off_wlat);
+  for (int t = tid; t < 2 * KL + 1; t += blockDim.x) wlat[t] = __ldg(&P.w_lat[t]);
+  {
+    const float* src = a.beam + cx.it.beam_off + (long long)a0 * NS;
+    const int n = (a1 - a0) * NS;
+    for (int t = tid; t < n; t += blockDim.x) abuf[t] = __ldcg(src + t);
+  }
+  __syncthreads();
+
+  // lateral PSF and log compression of rows w0 .. y1-1
+  {
+    const int n = (y1 - w0) * NS;
+    for (int t = tid; t < n; t += blockDim.x) {
+      const int i = t / NS, s = t - i * NS, l = w0 + i;
+      const int mlo = max(l - KL, 0), mhi = min(l + KL, NL - 1);
+      float acc = 0.f;
+      for (int m = mlo; m <= mhi; ++m) acc = fmaf(wlat[m - l + KL], abuf[(m - a0) * NS + s], acc);
+      const float y = log_compress(P, acc);
+      ybuf[t] = y;
+      if (l < w1) {
+        if (p.envelope) p.envelope[cx.it.beam_off + (long long)l * NS + s] = acc;
+        if (p.logimg) p.logimg[cx.it.beam_off + (long long)l * NS + s] = y;
+      }
+    }
+  }
+  __syncthreads();
+
+  float* out = p.frames + cx.it.frame_off;
+  if (P.kind == 0) {
+    const int n = NS * (w1 - w0), wl = w1 - w0;
+    for (int t = tid; t < n; t += blockDim.x) {
+      const int s = t / wl, j = t - s * wl;
+      __stcs(&out[(long long)s * NL + w0 + j], ybuf[j * NS + s]);
+    }
+  } else {
+    const int e0 = P.wedge_off[group], e1 = P.wedge_off[group + 1];
+    for (int e = e0 + tid; e < e1; e += blockDim.x) {
+      const float4 q = __ldg(&P.wedge[e]);
+      const int pix = __float_as_int(q.x);
+      const float fl = q.y, fs = q.z;
+      float v = 0.f;
+      if (fl >= 0.f) {
+        const int la = min((int)fl, NL - 2), sa = min((int)fs, NS - 2);
+        const float al = fl - (float)la, bb = fs - (float)sa;
+        const float* r0 = ybuf + (la - w0) * NS;
+        const float* r1 = r0 + NS;
+        const float y00 = r0[sa], y01 = r0[sa + 1];
+        const float y10 = r1[sa], y11 = r1[sa + 1];
+        const float top = fmaf(al, y10 - y00, y00), bot = fmaf(al, y11 - y01, y01);
+        v = fmaf(bb, bot - top, top);
+      }
+      __stcs(&out[pix], v);
+    }
+  }
+}
+
+bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int n_labels) {
+  const int G = sh.G;
+  if (G != 8 && G != 16 && G != 32) return false;
+  auto up = [](long long x, long long a) { return (x + a - 1) / a * a; };
+  long long zb = 0, lab = 0, ab = 0, yb = 0;
+  int gl = 0;
+  for (const ProbeHost& ph : probes) {
+    const int NL = ph.desc.n_lines, NS = ph.desc.n_samples;
+    const int rs = (NS + 2 * ph.k_ax) | 1;
+    zb = std::max(zb, (long long)G * rs * 4);
+    lab = std::max(lab, (long long)std::min(NL, G + 2 * kThetaDMax) * NS);
+    ab = std::max(ab, (long long)std::min(NL, G + 1 + 2 * ph.k_lat) * NS * 4);
+    yb = std::max(yb, (long long)std::min(NL, G + 1) * NS * 4);
+    gl = std::max(gl, (NL + G - 1) / G);
+  }
+  long long off = up(zb, 16);
+  sh.args.off_wax = (int)off;
+  off = up(off + 4 * (2 * 32 + 1), 16);
+  sh.args.off_tis = (int)off;
+  off = up(off + (long long)sizeof(DevTissue) * n_labels, 16);
+  sh.args.off_lab = (int)off;
+  off = up(off + lab, 16);
+  sh.smem_lines = (size_t)off;
+  off = up(ab, 16);
+  sh.args.off_y = (int)off;
+  off = up(off + yb, 16);
+  sh.args.off_wlat = (int)off;
+  off = up(off + 4 * (2 * kMaxHalfTaps + 1), 16);
+  sh.smem_image = (size_t)off;
+  sh.args.G = G;
+  sh.args.gpi_lines = sh.args.gpi_image = gl;
+  const size_t lim = 227 * 1024 - 1024;
+  return sh.smem_lines <= lim && sh.smem_image <= lim;
+}
+
+cudaError_t split_prepare(const SplitShape& sh) {
+  cudaError_t e = cudaFuncSetAttribute(split_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_lines);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(split_image, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_image);
+  return e;
+}
+
+cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, cudaStream_t st) {
+  SplitArgs a = sh.args;
+  a.beam = beam;
+  const int threads = sh.G * 32;
+  split_lines<<<(unsigned)(max_items * a.gpi_lines), threads, sh.smem_lines, st>>>(p, a);
+  split_image<<<(unsigned)(max_items * a.gpi_image), threads, sh.smem_image, st>>>(p, a);
+  return cudaGetLastError();
+}
+
+// Pixels of a curvilinear probe's output grid, grouped by wedge of G lines:
+// a pixel inside the fan belongs to the wedge of its bilinear base line
+// min(floor(fl), NL - 2); a pixel outside the fan to the wedge of the
+// preceding inside pixel of its row (wedge 0 if none).  Along a row the
+// base line never decreases, so the wedges' pixels form row segments.
+void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int G, std::vector<float4>& entries,
+                  std::vector<int>& off) {
+  const int nq = (NL + G - 1) / G;
+  std::vector<std::vector<float4>> per(nq);
+  for (int r = 0; r < H; ++r) {
+    int q = 0;
+    for (int c = 0; c < W; ++c) {
+      const float2 f = lut[(size_t)r * W + c];
+      if (f.x >= 0.f) q = std::min((int)f.x, NL - 2) / G;
+      const int pix = r * W + c;
+      float4 e;
+      std::memcpy(&e.x, &pix, sizeof pix);
+      e.y = f.x;
+      e.z = f.y;
+      e.w = 0.f;
+      per[q].push_back(e);
+    }
+  }
+  entries.clear();
+  off.assign(nq + 1, 0);
+  for (int q = 0; q < nq; ++q) {
+    off[q] = (int)entries.size();
+    entries.insert(entries.end(), per[q].begin(), per[q].end());
+  }
+  off[nq] = (int)entries.size();
+}
+
+}  // namespace ussim

@@ -38,6 +38,8 @@ struct DevProbe {
   const DevTissue* tissue;   // [n_labels]
   const float* px;           // curvilinear: [out_w] probe-frame x of output pixel columns
   const float* pz;           // curvilinear: [out_h] probe-frame z of output pixel rows
+  const float4* wedge;       // curvilinear, two-pass path: (pixel bits, fl, fs, 0) grouped by wedge
+  const int* wedge_off;      // [wedges + 1] start of each wedge's pixels
 };
 
 // incidence stencil extents for a (volume, probe) pair: axial half window W

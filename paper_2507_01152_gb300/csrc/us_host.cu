@@ -149,6 +149,7 @@ us_status build_probe_tables(us_sim* s, ProbeHost& ph) {
   if ((e = upload(&ph.d_wlat, wlat.data(), wlat.size())) != cudaSuccess) return cuda_fail(s, e, "upload taps");
   if ((e = upload(&ph.d_tissue, tis.data(), tis.size())) != cudaSuccess) return cuda_fail(s, e, "upload tissue");
   if (!lut.empty() && (e = upload(&ph.d_lut, lut.data(), lut.size())) != cudaSuccess) return cuda_fail(s, e, "upload lut");
+  ph.lut_host = std::move(lut);
   if (!px.empty() && ((e = upload(&ph.d_px, px.data(), px.size())) != cudaSuccess ||
                       (e = upload(&ph.d_pz, pz.data(), pz.size())) != cudaSuccess))
     return cuda_fail(s, e, "upload pixel grid");
@@ -178,6 +179,8 @@ DevProbe device_probe(const ProbeHost& ph) {
   d.tissue = ph.d_tissue;
   d.px = ph.d_px;
   d.pz = ph.d_pz;
+  d.wedge = ph.d_wedge;
+  d.wedge_off = ph.d_wedge_off;
   return d;
 }
 
@@ -288,9 +291,16 @@ us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, ui
   if (path == 0) {
     p.items = pl->d_items;
     p.n_items = B;
+    const bool two_pass = s->tuning.cluster_size == 1;
+    if (two_pass && !pl->d_beam && (e = cudaMalloc(&pl->d_beam, sizeof(float) * (size_t)pl->beam_elems)) != cudaSuccess)
+      return cuda_fail(s, e, "two-pass line buffer");
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (st && cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
     if (s->tuning.use_graph && st && cap == cudaStreamCaptureStatusNone) return graph_launch(s, pl, p, st);
+    if (two_pass) {
+      if ((e = launch_split(p, s->split, pl->d_beam, B, st)) != cudaSuccess) return cuda_fail(s, e, "two-pass render launch");
+      return US_OK;
+    }
     if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(s, e, "reset work counter");
     if ((e = launch_fused(p, s->shape, st)) != cudaSuccess) return cuda_fail(s, e, "fused render launch");
   } else {
@@ -312,6 +322,8 @@ void free_sim(us_sim* s) {
     cudaFree(ph.d_tissue);
     cudaFree(ph.d_px);
     cudaFree(ph.d_pz);
+    cudaFree(ph.d_wedge);
+    cudaFree(ph.d_wedge_off);
   }
   for (auto* d : s->d_pair_D) cudaFree(d);
   for (auto& kv : s->plans) {
@@ -320,6 +332,7 @@ void free_sim(us_sim* s) {
     cudaFree(kv.second.d_items_batch);
     cudaFree(kv.second.d_items_gated);
     cudaFree(kv.second.d_gated_count);
+    cudaFree(kv.second.d_beam);
   }
   cudaFree(s->d_vols);
   cudaFree(s->d_probes);
@@ -335,10 +348,51 @@ void free_sim(us_sim* s) {
   delete s;
 }
 
+// two-pass path with G = warps_per_cta lines per block: layouts, wedge
+// pixel lists of the curvilinear probes, device probe table
+us_status apply_split(us_sim* s, const us_tuning& t) {
+  SplitShape sh;
+  sh.G = t.warps_per_cta;
+  if (!split_shape_fits(sh, s->probes, s->n_labels))
+    return fail(s, US_ERR_UNSUPPORTED, "probe lines per block do not fit in shared memory for the two-pass path");
+  cudaError_t e;
+  bool changed = false;
+  for (ProbeHost& ph : s->probes) {
+    if (ph.desc.kind != 1 || ph.wedge_G == sh.G) continue;
+    std::vector<float4> ent;
+    std::vector<int> off;
+    build_wedges(ph.lut_host, ph.desc.out_w, ph.desc.out_h, ph.desc.n_lines, sh.G, ent, off);
+    cudaFree(ph.d_wedge);
+    cudaFree(ph.d_wedge_off);
+    ph.d_wedge = nullptr;
+    ph.d_wedge_off = nullptr;
+    ph.wedge_G = 0;
+    if ((e = upload(&ph.d_wedge, ent.data(), ent.size())) != cudaSuccess ||
+        (e = upload(&ph.d_wedge_off, off.data(), off.size())) != cudaSuccess)
+      return cuda_fail(s, e, "wedge tables");
+    ph.wedge_G = sh.G;
+    changed = true;
+  }
+  if (changed) {
+    std::vector<DevProbe> dp;
+    for (const ProbeHost& ph : s->probes) dp.push_back(device_probe(ph));
+    if ((e = cudaMemcpy(s->d_probes, dp.data(), sizeof(DevProbe) * dp.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(s, e, "probe table");
+  }
+  if ((e = split_prepare(sh)) != cudaSuccess) return cuda_fail(s, e, "kernel attributes");
+  s->split = sh;
+  s->tuning = t;
+  return US_OK;
+}
+
 us_status apply_tuning(us_sim* s, const us_tuning& t) {
   const int cs = t.cluster_size, nw = t.warps_per_cta;
-  if (!fused_shape_known(cs, nw)) return fail(s, US_ERR_INVALID_ARG, "unsupported (cluster_size, warps_per_cta)");
   if (t.use_graph & ~1) return fail(s, US_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+  if (cs == 1) {
+    if (nw != 8 && nw != 16 && nw != 32) return fail(s, US_ERR_INVALID_ARG, "two-pass path takes 8, 16 or 32 warps");
+    return apply_split(s, t);
+  }
+  if (!fused_shape_known(cs, nw)) return fail(s, US_ERR_INVALID_ARG, "unsupported (cluster_size, warps_per_cta)");
   FusedShape sh;
   sh.cs = cs;
   sh.nw = nw;
@@ -361,20 +415,35 @@ void drop_graph(us_plan& pl) {
   if (pl.graph) cudaGraphDestroy(pl.graph);
   pl.gexec = nullptr;
   pl.graph = nullptr;
-  pl.gnode = nullptr;
+  pl.gnodes.clear();
+  pl.gkps.clear();
   pl.g_cs = pl.g_nw = 0;
 }
 
-// Capture [work-counter reset + fused launch] once per batch signature and
-// launch shape; later calls only swap the kernel node's arguments.
+// Capture the render (fused: work-counter reset + kernel; two-pass: both
+// kernels) once per batch signature and launch shape; later calls only swap
+// the kernel nodes' arguments.  Both two-pass kernels take the same
+// arguments, so node order does not matter.
 us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream_t st) {
   cudaError_t e;
-  if (!pl->gexec || pl->g_cs != s->shape.cs || pl->g_nw != s->shape.nw) {
+  const bool two_pass = s->tuning.cluster_size == 1;
+  RenderParams pp = p;
+  FusedLayout lay = s->shape.lay;
+  SplitArgs sa = s->split.args;
+  sa.beam = pl->d_beam;
+  void* fargs[2] = {&pp, &lay};
+  void* sargs[2] = {&pp, &sa};
+  if (!pl->gexec || pl->g_cs != s->tuning.cluster_size || pl->g_nw != s->tuning.warps_per_cta) {
     drop_graph(*pl);
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(s, e, "graph capture");
-    cudaError_t e1 = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
-    cudaError_t e2 = launch_fused(p, s->shape, st);
+    cudaError_t e1 = cudaSuccess, e2;
+    if (two_pass) {
+      e2 = launch_split(p, s->split, pl->d_beam, p.n_items, st);
+    } else {
+      e1 = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
+      e2 = launch_fused(p, s->shape, st);
+    }
     e = cudaStreamEndCapture(st, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -384,31 +453,35 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
     cudaGraphGetNodes(g, nullptr, &n);
     std::vector<cudaGraphNode_t> nodes(n);
     if (n) cudaGraphGetNodes(g, nodes.data(), &n);
-    cudaGraphNode_t kn = nullptr;
     for (cudaGraphNode_t nd : nodes) {
       cudaGraphNodeType ty;
-      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) kn = nd;
+      cudaKernelNodeParams kp{};
+      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel &&
+          cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess) {
+        pl->gnodes.push_back(nd);
+        pl->gkps.push_back(kp);
+      }
     }
-    if (!kn || (e = cudaGraphKernelNodeGetParams(kn, &pl->gkp)) != cudaSuccess ||
-        (e = cudaGraphInstantiate(&pl->gexec, g, 0)) != cudaSuccess) {
+    if (pl->gnodes.size() != (two_pass ? 2u : 1u) || (e = cudaGraphInstantiate(&pl->gexec, g, 0)) != cudaSuccess) {
       cudaGraphDestroy(g);
       pl->gexec = nullptr;
-      return cuda_fail(s, kn ? e : cudaErrorUnknown, "graph instantiate");
+      pl->gnodes.clear();
+      pl->gkps.clear();
+      return cuda_fail(s, pl->gnodes.empty() ? cudaErrorUnknown : e, "graph instantiate");
     }
     pl->graph = g;
-    pl->gnode = kn;
-    pl->g_cs = s->shape.cs;
-    pl->g_nw = s->shape.nw;
+    pl->g_cs = s->tuning.cluster_size;
+    pl->g_nw = s->tuning.warps_per_cta;
     if ((e = cudaGraphLaunch(pl->gexec, st)) != cudaSuccess) return cuda_fail(s, e, "graph launch");
     return US_OK;
   }
-  RenderParams pp = p;
-  FusedLayout lay = s->shape.lay;
-  void* args[2] = {&pp, &lay};
-  cudaKernelNodeParams kp = pl->gkp;
-  kp.kernelParams = args;
-  kp.extra = nullptr;
-  if ((e = cudaGraphExecKernelNodeSetParams(pl->gexec, pl->gnode, &kp)) != cudaSuccess) return cuda_fail(s, e, "graph update");
+  for (size_t i = 0; i < pl->gnodes.size(); ++i) {
+    cudaKernelNodeParams kp = pl->gkps[i];
+    kp.kernelParams = two_pass ? sargs : fargs;
+    kp.extra = nullptr;
+    if ((e = cudaGraphExecKernelNodeSetParams(pl->gexec, pl->gnodes[i], &kp)) != cudaSuccess)
+      return cuda_fail(s, e, "graph update");
+  }
   if ((e = cudaGraphLaunch(pl->gexec, st)) != cudaSuccess) return cuda_fail(s, e, "graph launch");
   return US_OK;
 }
@@ -650,9 +723,14 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
   p.items = pl->d_items_gated;
   p.n_items = B;
   p.n_items_dev = pl->d_gated_count;
-  if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess ||
-      (e = launch_fused(p, s->shape, st)) != cudaSuccess)
+  if (s->tuning.cluster_size == 1) {
+    if (!pl->d_beam && (e = cudaMalloc(&pl->d_beam, sizeof(float) * (size_t)pl->beam_elems)) != cudaSuccess)
+      return cuda_fail(s, e, "two-pass line buffer");
+    if ((e = launch_split(p, s->split, pl->d_beam, B, st)) != cudaSuccess) return cuda_fail(s, e, "gated render");
+  } else if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess ||
+             (e = launch_fused(p, s->shape, st)) != cudaSuccess) {
     return cuda_fail(s, e, "gated render");
+  }
   if (n_rendered && (e = cudaMemcpyAsync(n_rendered, pl->d_gated_count, sizeof(int), cudaMemcpyDeviceToDevice, st)) !=
                         cudaSuccess)
     return cuda_fail(s, e, "gated count");
@@ -740,7 +818,8 @@ us_status us_sim_autotune(us_sim* s, const us_env* envs, int32_t B, const float*
       }
     }
   }
-  static const int cand[][2] = {{8, 32}, {8, 16}, {8, 8}, {16, 32}, {16, 16}, {16, 8}, {4, 32}, {4, 16}};
+  static const int cand[][2] = {{8, 32}, {8, 16}, {8, 8}, {16, 32}, {16, 16}, {16, 8}, {4, 32}, {4, 16},
+                                {1, 32}, {1, 16}, {1, 8}};
   float best = 1e30f;
   int best_cs = 0, best_nw = 0;
   cudaEvent_t a, b2;

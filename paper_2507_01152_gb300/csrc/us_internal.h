@@ -24,6 +24,10 @@ struct ProbeHost {
   DevTissue* d_tissue = nullptr;
   float* d_px = nullptr;
   float* d_pz = nullptr;
+  std::vector<float2> lut_host;   // scan-conversion map (curvilinear)
+  float4* d_wedge = nullptr;      // two-pass path: pixels grouped by wedge of wedge_G lines
+  int* d_wedge_off = nullptr;
+  int wedge_G = 0;
 };
 
 // global scratch of the plain path (one environment at a time)
@@ -64,6 +68,27 @@ cudaError_t fused_prepare(const FusedShape& s);
 cudaError_t fused_max_clusters(const FusedShape& s, int* clusters);
 cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st);
 
+// two-pass path: lines per block G (8, 16, 32), shared-memory layouts of
+// both passes, blocks per item of each pass
+struct SplitArgs {
+  float* beam = nullptr;   // axially filtered lines, beam layout (per item beam_off)
+  int G = 32, gpi_lines = 0, gpi_image = 0;
+  int off_wax = 0, off_tis = 0, off_lab = 0;   // pass A byte offsets
+  int off_y = 0, off_wlat = 0;                 // pass B byte offsets
+};
+struct SplitShape {
+  int G = 32;
+  SplitArgs args{};
+  size_t smem_lines = 0, smem_image = 0;
+};
+bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int n_labels);
+cudaError_t split_prepare(const SplitShape& sh);
+// both passes over the first max_items entries of p.items (fewer if
+// p.n_items_dev says so)
+cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, cudaStream_t st);
+void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int G, std::vector<float4>& entries,
+                  std::vector<int>& off);
+
 // items with score > thr, in batch order, and their count (device)
 cudaError_t launch_gate_compact(const EnvItem* items, int B, const float* score, float thr, EnvItem* out, int* count,
                                 cudaStream_t st);
@@ -86,11 +111,13 @@ struct us_plan {
   ussim::EnvItem* d_items_gated = nullptr;   // device-built subset for gated renders
   int* d_gated_count = nullptr;
   long long frame_floats = 0, beam_elems = 0;
-  // captured [work-counter reset + fused launch], re-parameterised per call
+  float* d_beam = nullptr;                   // two-pass path: filtered lines of the batch
+  // captured render (fused: work-counter reset + kernel; two-pass: both
+  // kernels), re-parameterised per call
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  cudaGraphNode_t gnode = nullptr;
-  cudaKernelNodeParams gkp{};
+  std::vector<cudaGraphNode_t> gnodes;
+  std::vector<cudaKernelNodeParams> gkps;
   int g_cs = 0, g_nw = 0;
 };
 
@@ -110,7 +137,8 @@ struct us_sim {
   unsigned* d_err = nullptr;
   unsigned* d_work = nullptr;
 
-  ussim::FusedShape shape;
+  ussim::FusedShape shape;     // cluster path (also serves gated renders when it is not tuned in)
+  ussim::SplitShape split;     // two-pass path (tuning.cluster_size == 1)
   us_tuning tuning{8, 32, 1};
 
   std::map<std::string, us_plan> plans;

@@ -48,15 +48,20 @@ def test_error_head_and_gated_fallback(trained):
     pe = pred_err.cpu().numpy()
     assert np.corrcoef(pe, l1_true)[0, 1] > 0.3            # the head ranks frames by their error
     thr = float(np.median(pe))
-    frames = torch.zeros_like(y)
-    n_rendered = torch.zeros(1, dtype=torch.int32, device="cuda")
-    T.mixed_step(src.sim, net, src.poses, src.seed, 77, x, frames, pred_err, thr, n_rendered, envs_c=src.envs_c)
-    torch.cuda.synchronize()
     gated = pe > thr
-    assert int(n_rendered.item()) == int(gated.sum())
-    f, s_, yy = frames.cpu().numpy(), surr.cpu().numpy(), y.cpu().numpy()
-    for b in range(B):
-        assert np.array_equal(f[b], yy[b] if gated[b] else s_[b]), b
+    s_, yy = surr.cpu().numpy(), y.cpu().numpy()
+    old = src.sim.get_tuning()
+    for shape in ((8, 32), (1, 16)):      # cluster kernel and two-pass path re-render the gated frames
+        src.sim.set_tuning(shape[0], shape[1], 1)
+        frames = torch.zeros_like(y)
+        n_rendered = torch.zeros(1, dtype=torch.int32, device="cuda")
+        T.mixed_step(src.sim, net, src.poses, src.seed, 77, x, frames, pred_err, thr, n_rendered, envs_c=src.envs_c)
+        torch.cuda.synchronize()
+        assert int(n_rendered.item()) == int(gated.sum())
+        f = frames.cpu().numpy()
+        for b in range(B):
+            assert np.array_equal(f[b], yy[b] if gated[b] else s_[b]), (shape, b)
+    src.sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
     net.metrics(frames, y, met)
     mixed_l1 = float(met[1:1 + B].mean())
     assert mixed_l1 <= float(l1_true.mean()) + 1e-7

@@ -1,5 +1,6 @@
-"""GPU parity of the render path (fused persistent kernel and plain
-per-environment kernels) against the CPU oracle, through the C ABI."""
+"""GPU parity of the render path (persistent cluster kernel, two-pass
+batched path and plain per-environment kernels) against the CPU oracle,
+through the C ABI."""
 import dataclasses
 import math
 
@@ -51,19 +52,40 @@ def c2():
     return wl, gpu_sim(wl)
 
 
-def test_batched_curvilinear_64env_full(c2):
+@pytest.fixture(scope="module")
+def c2_oracle(c2):
+    wl, _ = c2
+    return render_oracle(wl, wl.envs, wl.poses, wl.seed, 5, range(64))
+
+
+@pytest.mark.parametrize("shape", [(8, 32), (1, 32), (1, 16)])
+def test_batched_curvilinear_64env_full(c2, c2_oracle, shape):
     """All 64 envs of the 256^3 curvilinear batch, element by element, in the
-    launch configuration the benchmark uses."""
+    launch configurations the benchmark's autotuner chooses from (cluster
+    kernel and two-pass path)."""
     wl, sim = c2
-    g = render_gpu(sim, wl.envs, wl.poses, wl.seed, 5, path=0)
-    o = render_oracle(wl, wl.envs, wl.poses, wl.seed, 5, range(64))
-    _check_all(g, o, wl.probes, wl.envs, range(64))
+    old = sim.get_tuning()
+    try:
+        sim.set_tuning(shape[0], shape[1], 1)
+        g = render_gpu(sim, wl.envs, wl.poses, wl.seed, 5, path=0)
+    finally:
+        sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
+    _check_all(g, c2_oracle, wl.probes, wl.envs, range(64))
 
 
-def test_fused_equals_plain_bitwise(c2):
+@pytest.mark.parametrize("shape", [(8, 32), (1, 8), (1, 32)])
+def test_batched_paths_equal_plain_bitwise(c2, shape):
+    """Frames and every intermediate export (labels, voxel indices, envelope,
+    log image) of the cluster kernel and of the two-pass path equal those of
+    the plain per-environment kernels bit for bit."""
     wl, sim = c2
     envs, poses = wl.envs[:12], wl.poses[:12]
-    a = render_gpu(sim, envs, poses, 11, 2, path=0)
+    old = sim.get_tuning()
+    try:
+        sim.set_tuning(shape[0], shape[1], 0)
+        a = render_gpu(sim, envs, poses, 11, 2, path=0)
+    finally:
+        sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
     b = render_gpu(sim, envs, poses, 11, 2, path=1)
     for x, y in zip(a, b):
         for k in x:
@@ -92,7 +114,7 @@ def test_launch_shape_that_cannot_fit_is_rejected(c2):
     assert e.value.status == US_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("cs,nw", [(8, 8), (8, 16), (8, 32), (16, 8), (16, 16), (16, 32)])
+@pytest.mark.parametrize("cs,nw", [(8, 8), (8, 16), (8, 32), (16, 8), (16, 16), (16, 32), (1, 8), (1, 16), (1, 32)])
 def test_launch_shapes_agree(c2, cs, nw):
     wl, sim = c2
     envs, poses = wl.envs[:10], wl.poses[:10]
@@ -186,9 +208,11 @@ def test_tiny_random_cases_vs_oracle_and_brute_force(opt):
     poses = np.stack([_rand_pose(rng, (9.0, 8.0, 2.0)) for _ in range(B)])
     wl = scene.Workload("tiny", [(spec, lab, hu)], probes, envs, poses, options=opt, seed=99)
     sim = gpu_sim(wl)
-    for path in (0, 1):
+    o = render_oracle(wl, envs, poses, 0xABCDEF0123, 9, range(B))
+    for path, shape in ((0, (8, 32)), (0, (1, 8)), (0, (1, 32)), (1, None)):
+        if shape:
+            sim.set_tuning(shape[0], shape[1], 0)
         g = render_gpu(sim, envs, poses, 0xABCDEF0123, 9, path=path)
-        o = render_oracle(wl, envs, poses, 0xABCDEF0123, 9, range(B))
         _check_all(g, o, probes, envs, range(B))
     for b in range(3):
         br = brute.render(lab, hu, 1.0, scene.tissue_table(), probes[envs[b][1]], opt, poses[b], env=b,
@@ -213,10 +237,12 @@ def test_uneven_batch_512env_sampled():
     wl = scene.workload_c3(512, steps=2)
     sim = gpu_sim(wl)
     poses = wl.poses[1]
-    g = render_gpu(sim, wl.envs, poses, wl.seed, 1)
     which = list(range(0, 512, 23)) + [511]
     o = render_oracle(wl, wl.envs, poses, wl.seed, 1, which)
-    _check_all(g, o, wl.probes, wl.envs, which)
+    for shape in ((8, 32), (1, 32)):
+        sim.set_tuning(shape[0], shape[1], 1)
+        g = render_gpu(sim, wl.envs, poses, wl.seed, 1)
+        _check_all(g, o, wl.probes, wl.envs, which)
 
 
 def test_host_buffers_match_device(c2):
