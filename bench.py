@@ -36,6 +36,20 @@ from paper_2507_01152_gb300 import scene  # noqa: E402
 
 METRIC = "US frames/s on 1 GB300 (physics vs surrogate) at stated error; % HBM roofline"
 
+# Algorithmic ALU work of the physics path, in lane operations (one FP32 /
+# INT32 lane op per lane per cycle; an FMA and a shared-memory load count
+# once each): ~200 per beam sample (Philox ~60, transcendentals ~15,
+# gather and interpolation ~30, PSF 2 x (13 + 21) taps as FMA + load, rest
+# ~60) and ~20 per scan-converted output pixel.  Of these, the lateral PSF
+# (21 FMA + 21 loads) and the log compression (~5) per sample and the
+# per-pixel work belong to pass B of the two-pass path; the rest to pass A.
+OPS_PER_SAMPLE = 200
+OPS_PER_PIXEL = 20
+OPS_PER_SAMPLE_PASS_B = 47
+# DRAM bytes per launch of the dominant kernel from one ncu capture of the
+# current kernel source (None until captured; reset when the kernel changes)
+KERNEL_DRAM_BYTES = {}
+
 # Algorithmic bytes of one launch of the default workload: the union of
 # voxels read by the nearest / trilinear footprints of all 64 frames (label
 # 1 B + HU 2 B each), the 64 frames written (256 x 256 x 4 B) and the poses
@@ -55,6 +69,26 @@ def load_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def alu_peak(sms):
+    """lane-op/s: SMs x 128 FP32/INT32 lanes x the maximum SM clock"""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz, src = float(json.load(f)["sm_max_mhz"]), "measured clock"
+    except Exception:
+        mhz, src = 2070.0, "nominal clock"
+    return sms * 128 * mhz * 1e6, src
+
+
+def workload_units(wl):
+    """(beam samples, output pixels) of one render of the batch"""
+    samples = pixels = 0
+    for v, pr in np.asarray(wl.envs):
+        p = wl.probes[int(pr)]
+        samples += p.n_lines * p.n_samples
+        pixels += p.out_w * p.out_h
+    return samples, pixels
 
 
 class ClockSampler:
@@ -235,10 +269,11 @@ def run_mixed(args):
         poses[idx] = scene.random_walk_poses(specs[v], len(idx), 1, 3000 + v)[0]
     dv = [(torch.from_numpy(l).cuda(), torch.from_numpy(h).cuda(), s_.voxel_mm) for (s_, l, h) in vols]
     sim = Sim(dv, scene.tissue_table(), [probe], scene.Options())
-    sim.set_tuning(8, 32, 1)
     ec = make_envs(envs)
     P = torch.from_numpy(poses).cuda()
     stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim.autotune(envs, P, torch.zeros((B, 256, 256), device="cuda"), None, stream=stream)
     x = torch.zeros((B, 256, 256, 8), dtype=torch.bfloat16, device="cuda")
     frames = torch.zeros((B, 256, 256), device="cuda")
     phys = torch.zeros_like(frames)
@@ -284,6 +319,7 @@ def run_mixed(args):
             "warmup": 2, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16+f32", "data": "synthetic",
             "config": {"workload": "mixed_production_1024env_curvilinear_256x512_4vol", "envs": B,
+                       "tuning": sim.get_tuning(),
                        "gate": f"re-render by physics where predicted L1 > {thr}"},
             "mixed": {"frames_per_s": B / ms_mixed * 1e3, "rerendered_frac": int(nr.item()) / B,
                       "l1_vs_physics": mixed_l1, "ssim_vs_physics": mixed_ss},
@@ -361,7 +397,7 @@ def run_ours(args):
         total = float(t.item())
         dist.barrier()
     value = B * args.steps * world / total
-    kernel_s = total / args.steps           # one fused launch per step: the event time is the kernel's
+    kernel_s = total / args.steps           # device time of one render step (all its kernels)
 
     # plain per-environment form on the same batch (comparison)
     plain = None
@@ -384,13 +420,36 @@ def run_ours(args):
     e2e = {"value": B * e2e_steps / e2e_el * world, "unit": "frames/s", "h2d_bytes_per_step": int(host_poses.nbytes),
            "d2h_bytes_per_step": int(host_frames.nbytes)}
 
-    roofline = None
+    # per-kernel durations of the same render (events around each kernel on
+    # the launching stream, L2 flushed before every call)
+    kms = []
+    with torch.cuda.stream(stream):
+        for k in range(max(5, args.steps // 2)):
+            flush.zero_()
+            kms.append(sim.render_timed(None, poses, seed, 7000 + k, frames, stream=stream, envs_c=envs_c))
+    kavg = [sum(x[i] for x in kms) / len(kms) for i in range(len(kms[0]))]
+    names = ["split_lines", "split_image"] if tuning["cluster_size"] == 1 else ["fused_render"]
+    dom = max(range(len(kavg)), key=lambda i: kavg[i])
+    samples, pixels = workload_units(wl)
+    if len(names) == 1:
+        ops = OPS_PER_SAMPLE * samples + OPS_PER_PIXEL * pixels
+    elif dom == 0:
+        ops = (OPS_PER_SAMPLE - OPS_PER_SAMPLE_PASS_B) * samples
+    else:
+        ops = OPS_PER_SAMPLE_PASS_B * samples + OPS_PER_PIXEL * pixels
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    apeak, asrc = alu_peak(sms)
+    achieved = ops / (kavg[dom] / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": apeak / 1e12, "unit": "Tlane-op/s",
+                "frac": achieved * 1e12 / apeak,
+                "traffic": KERNEL_DRAM_BYTES.get((wl.name, names[dom], tuning["warps_per_cta"])),
+                "kernel": names[dom], "kernel_ms": kavg[dom], "kernels_ms": dict(zip(names, kavg)),
+                "lane_ops_per_launch": ops, "peak_source": f"{sms} SMs x 128 lanes x {asrc}"}
     if args.workload == "c2":
         peak, which = load_peaks()
-        achieved = c2_launch_bytes(B) / kernel_s / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "peak_source": which, "kernel": "fused_render",
-                    "bytes_per_launch": c2_launch_bytes(B)}
+        hb = c2_launch_bytes(B) / kernel_s / 1e9
+        roofline["hbm"] = {"achieved": hb, "peak": peak, "unit": "GB/s", "frac": hb / peak, "peak_source": which,
+                           "bytes_per_step": c2_launch_bytes(B), "scope": "whole render step"}
 
     # surrogate inference throughput at 512 envs (speed only: the cost of a
     # forward pass does not depend on the weights)
@@ -408,9 +467,11 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "envs_per_gpu": B, "l2": "flushed between timed steps (256 MB write)",
-                           "path": "fused persistent cluster kernel, CUDA graph replay",
+                           "path": ("two-pass batched kernels" if tuning["cluster_size"] == 1
+                                    else "persistent cluster kernel") + ", CUDA graph replay, autotuned",
                            "tuning": tuning, "parallelism": f"replicas{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * (2 if tuning["cluster_size"] == 1 else 1),
                 "plain": plain, "surrogate": surrogate, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     sim.close()

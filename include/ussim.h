@@ -129,7 +129,9 @@ typedef struct {
  * cluster_size 1: two-pass path without clusters, warps_per_cta (8, 16 or
  *   32) lines per block; the axially filtered lines go through a global
  *   buffer of the batch's beam size, allocated on first use per batch
- *   signature.  Same frames as the cluster kernel. */
+ *   signature.  Same frames as the cluster kernel.
+ * Default after us_sim_create: {1, 16, 1} (else {1, 8, 1}, else the cluster
+ * shape {8, 32, 1} or {16, 16, 1}, whichever fits the probe set first). */
 typedef struct {
   int32_t cluster_size;  /* 1, 4, 8 or 16 */
   int32_t warps_per_cta; /* 8, 16 or 32 */
@@ -248,6 +250,16 @@ US_API us_status us_sim_set_tuning(us_sim* sim, const us_tuning* t);
  * used without timing. */
 US_API us_status us_sim_autotune(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
                           float* frames, const char* cache_path, void* stream);
+
+/* The tuned batched render (as us_sim_render, without graph replay) with
+ * CUDA events recorded on `stream` around each of its kernels; waits for
+ * the render and writes each kernel's duration in ms to kernel_ms[0..n)
+ * (host, room for 2): cluster path n = 1 (the persistent kernel), two-pass
+ * path n = 2 (pass A: slice, scanline model, axial PSF; pass B: lateral PSF,
+ * log, scan conversion).  Errors as us_sim_render. */
+US_API us_status us_sim_render_timed(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                                     uint64_t seed, uint64_t step, float* frames, float* kernel_ms,
+                                     int32_t* n_kernels, void* stream);
 
 /* Message of the last error on this handle ("" if none). */
 US_API const char* us_sim_last_error(const us_sim* sim);

@@ -262,13 +262,21 @@ cudaError_t split_prepare(const SplitShape& sh) {
   return e;
 }
 
-cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, cudaStream_t st) {
+cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, int pass,
+                              cudaStream_t st) {
   SplitArgs a = sh.args;
   a.beam = beam;
   const int threads = sh.G * 32;
-  split_lines<<<(unsigned)(max_items * a.gpi_lines), threads, sh.smem_lines, st>>>(p, a);
-  split_image<<<(unsigned)(max_items * a.gpi_image), threads, sh.smem_image, st>>>(p, a);
+  if (pass == 0)
+    split_lines<<<(unsigned)(max_items * a.gpi_lines), threads, sh.smem_lines, st>>>(p, a);
+  else
+    split_image<<<(unsigned)(max_items * a.gpi_image), threads, sh.smem_image, st>>>(p, a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, cudaStream_t st) {
+  cudaError_t e = launch_split_pass(p, sh, beam, max_items, 0, st);
+  return e == cudaSuccess ? launch_split_pass(p, sh, beam, max_items, 1, st) : e;
 }
 
 // Pixels of a curvilinear probe's output grid, grouped by wedge of G lines:

@@ -609,12 +609,21 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
       return US_ERR_INVALID_ARG;
     }
   }
-  if ((r = apply_tuning(s, s->tuning)) != US_OK) {
-    // fall back to the smallest footprint that fits
-    us_tuning t{16, 16, 1};
-    if ((r = apply_tuning(s, t)) != US_OK) {
-      free_sim(s);
-      return r;
+  // the cluster shape serves gated renders too: set it first, then the
+  // default two-pass shape; fall back to smaller footprints where needed
+  {
+    us_tuning tc{8, 32, 1};
+    if ((r = apply_tuning(s, tc)) != US_OK) {
+      tc = us_tuning{16, 16, 1};
+      if ((r = apply_tuning(s, tc)) != US_OK) {
+        free_sim(s);
+        return r;
+      }
+    }
+    us_tuning t2{1, 16, 1};
+    if (apply_tuning(s, t2) != US_OK) {
+      t2 = us_tuning{1, 8, 1};
+      if (apply_tuning(s, t2) != US_OK) apply_tuning(s, tc);
     }
   }
   *out = s;
@@ -734,6 +743,46 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
   if (n_rendered && (e = cudaMemcpyAsync(n_rendered, pl->d_gated_count, sizeof(int), cudaMemcpyDeviceToDevice, st)) !=
                         cudaSuccess)
     return cuda_fail(s, e, "gated count");
+  return US_OK;
+}
+
+us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint64_t seed,
+                              uint64_t step, float* frames, float* kernel_ms, int32_t* n_kernels, void* stream) {
+  if (!kernel_ms || !n_kernels) return fail(s, US_ERR_INVALID_ARG, "NULL timing outputs");
+  *n_kernels = 0;
+  us_status r = check_render_args(s, envs, B, poses, frames);
+  if (r != US_OK || B == 0) return r;
+  us_plan* pl;
+  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  RenderParams p = base_params(s, poses, seed, step, frames);
+  p.items = pl->d_items;
+  p.n_items = B;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool two_pass = s->tuning.cluster_size == 1;
+  cudaError_t e;
+  if (two_pass && !pl->d_beam && (e = cudaMalloc(&pl->d_beam, sizeof(float) * (size_t)pl->beam_elems)) != cudaSuccess)
+    return cuda_fail(s, e, "two-pass line buffer");
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  for (auto& x : ev)
+    if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(s, e, "events");
+  const int nk = two_pass ? 2 : 1;
+  if (two_pass) {
+    cudaEventRecord(ev[0], st);
+    e = launch_split_pass(p, s->split, pl->d_beam, B, 0, st);
+    cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, B, 1, st);
+    cudaEventRecord(ev[2], st);
+  } else {
+    e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
+    cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = launch_fused(p, s->shape, st);
+    cudaEventRecord(ev[1], st);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[nk]);
+  for (int k = 0; k < nk && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&kernel_ms[k], ev[k], ev[k + 1]);
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_fail(s, e, "timed render");
+  *n_kernels = nk;
   return US_OK;
 }
 

@@ -86,6 +86,9 @@ cudaError_t split_prepare(const SplitShape& sh);
 // both passes over the first max_items entries of p.items (fewer if
 // p.n_items_dev says so)
 cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, cudaStream_t st);
+// one pass: 0 = lines (pass A), 1 = image (pass B)
+cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, int pass,
+                              cudaStream_t st);
 void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int G, std::vector<float4>& entries,
                   std::vector<int>& off);
 
@@ -139,7 +142,7 @@ struct us_sim {
 
   ussim::FusedShape shape;     // cluster path (also serves gated renders when it is not tuned in)
   ussim::SplitShape split;     // two-pass path (tuning.cluster_size == 1)
-  us_tuning tuning{8, 32, 1};
+  us_tuning tuning{1, 16, 1};
 
   std::map<std::string, us_plan> plans;
 

@@ -80,6 +80,7 @@ SIGNATURES = {
                                       C.c_int32, _P]),
     "us_sim_render_host": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
     "us_sim_check": (C.c_int, [_P, _P]),
+    "us_sim_render_timed": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, _P, _P]),
     "us_sim_sample_slices": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
     "us_sim_render_gated": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, C.c_float, _P, _P]),
     "us_sim_get_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
@@ -278,6 +279,17 @@ class Sim:
         self._check(self._lib.us_sim_render_host(self.h, e, B, _ptr(poses_host), seed, step, _ptr(frames_host),
                                                  _stream_handle(stream)))
 
+    def render_timed(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
+        """The tuned render with per-kernel CUDA-event times (ms): a list of
+        one (cluster kernel) or two (two-pass: pass A, pass B) durations."""
+        B = poses.shape[0]
+        e = envs_c if envs_c is not None else make_envs(envs)
+        ms = (C.c_float * 2)()
+        n = C.c_int32(0)
+        self._check(self._lib.us_sim_render_timed(self.h, e, B, _ptr(poses), seed, step, _ptr(frames), ms, C.byref(n),
+                                                  _stream_handle(stream)))
+        return [float(ms[i]) for i in range(n.value)]
+
     def check(self, stream=None):
         self._check(self._lib.us_sim_check(self.h, _stream_handle(stream)))
 
@@ -394,6 +406,17 @@ class Surrogate:
         out = np.zeros(self.n_params, np.float32)
         self._check(self._lib.us_surr_get_grads(self.h, out.ctypes.data))
         return out
+
+    def render_timed(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
+        """The tuned render with per-kernel CUDA-event times (ms): a list of
+        one (cluster kernel) or two (two-pass: pass A, pass B) durations."""
+        B = poses.shape[0]
+        e = envs_c if envs_c is not None else make_envs(envs)
+        ms = (C.c_float * 2)()
+        n = C.c_int32(0)
+        self._check(self._lib.us_sim_render_timed(self.h, e, B, _ptr(poses), seed, step, _ptr(frames), ms, C.byref(n),
+                                                  _stream_handle(stream)))
+        return [float(ms[i]) for i in range(n.value)]
 
     def check(self, stream=None):
         self._check(self._lib.us_surr_check(self.h, _stream_handle(stream)))
