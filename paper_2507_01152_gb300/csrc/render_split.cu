@@ -1,8 +1,9 @@
 // Two-pass batched render without clusters.
 //
 // Pass A (split_lines): one block per (environment, group of G lines), one
-// warp per line.  The block takes the nearest labels of its lines and of up
-// to kThetaDMax lines on either side (the incidence stencil's reach), the
+// warp per line.  The block takes the nearest labels of its lines and of the
+// lines the incidence stencil can reach on either side (at most kThetaDMax),
+// the
 // impedance of its own lines, runs the scanline model and the in-place
 // axial PSF, and writes the axially filtered line to a beam-layout buffer
 // in global memory (L2-resident for moderate batches).
@@ -24,6 +25,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "umma.cuh"
 #include "us_internal.h"
 #include "us_scanline.cuh"
 
@@ -87,16 +89,24 @@ __device__ __forceinline__ bool split_item(const RenderParams& p, int gpi, int G
   return cx.valid != 0;
 }
 
-__global__ void __launch_bounds__(1024, 1) split_lines(RenderParams p, SplitArgs a) {
+// minimum resident blocks per SM the register budget is cut for: pass A
+// blocks are small enough in shared memory for 3 (16 lines) or 6 (8 lines)
+template <int G>
+constexpr int lines_min_blocks() {
+  return G == 8 ? 6 : (G == 16 ? 3 : 1);
+}
+
+template <int G>
+__global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(RenderParams p, SplitArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SplitCtx cx;
   int group;
-  if (!split_item(p, a.gpi_lines, a.G, cx, group)) return;
+  if (!split_item(p, a.gpi_lines, G, cx, group)) return;
   const DevProbe& P = cx.P;
-  const int NL = P.nl, NS = P.ns, KA = P.k_ax, G = a.G;
+  const int NL = P.nl, NS = P.ns, KA = P.k_ax;
   const int RS = (NS + 2 * KA) | 1;
   const int g0 = group * G, g1 = min(g0 + G, NL);
-  const int L0 = max(g0 - kThetaDMax, 0), L1 = min(g1 + kThetaDMax, NL);
+  const int L0 = max(g0 - cx.pair.dmax, 0), L1 = min(g1 + cx.pair.dmax, NL);   // labels the stencil can reach
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NW = blockDim.x >> 5;
   float* zbuf = reinterpret_cast<float*>(smem);                      // [G][RS]
   float* wax = reinterpret_cast<float*>(smem + a.off_wax);
@@ -151,13 +161,14 @@ __global__ void __launch_bounds__(1024, 1) split_lines(RenderParams p, SplitArgs
   }
 }
 
-__global__ void __launch_bounds__(1024, 1) split_image(RenderParams p, SplitArgs a) {
+template <int G>
+__global__ void __launch_bounds__(G * 32, G == 32 ? 1 : 2) split_image(RenderParams p, SplitArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SplitCtx cx;
   int group;
-  if (!split_item(p, a.gpi_image, a.G, cx, group)) return;
+  if (!split_item(p, a.gpi_image, G, cx, group)) return;
   const DevProbe& P = cx.P;
-  const int NL = P.nl, NS = P.ns, KL = P.k_lat, G = a.G;
+  const int NL = P.nl, NS = P.ns, KL = P.k_lat;
   const int w0 = group * G, w1 = min(w0 + G, NL);
   const int y1 = min(w1 + 1, NL);                                    // log rows w0 .. y1-1
   const int a0 = max(w0 - KL, 0), a1 = min(y1 + KL, NL);             // filtered rows staged
@@ -167,9 +178,37 @@ __global__ void __launch_bounds__(1024, 1) split_image(RenderParams p, SplitArgs
   float* wlat = reinterpret_cast<float*>(smem + a.off_wlat);
   for (int t = tid; t < 2 * KL + 1; t += blockDim.x) wlat[t] = __ldg(&P.w_lat[t]);
   {
+    // the staged rows are one contiguous range of the line buffer: one bulk
+    // asynchronous copy when it is 16-byte aligned, else plain loads
     const float* src = a.beam + cx.it.beam_off + (long long)a0 * NS;
     const int n = (a1 - a0) * NS;
-    for (int t = tid; t < n; t += blockDim.x) abuf[t] = __ldcg(src + t);
+    __shared__ uint64_t bar;
+    __shared__ int landed;
+    const bool bulk = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && (n & 3) == 0;
+    if (bulk) {
+      // one thread issues the copy and waits for it (bounded); the block
+      // barrier then publishes the rows to every thread
+      if (tid == 0) {
+        umma::mbar_init(&bar, 1);
+        umma::mbar_init_fence();
+        umma::mbar_arrive_expect_tx(&bar, (uint32_t)n * 4u);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                umma::smem_u32(abuf)),
+            "l"(src), "r"((uint32_t)n * 4u), "r"(umma::smem_u32(&bar))
+            : "memory");
+        landed = umma::mbar_wait(&bar, 0) ? 1 : 0;
+        if (!landed) {
+          // report, and do not leave while the copy may still be writing
+          atomicOr(p.err, kErrStagingTimeout);
+          umma::mbar_wait(&bar, 0);
+        }
+      }
+      __syncthreads();
+      if (!landed) return;
+    } else {
+      for (int t = tid; t < n; t += blockDim.x) abuf[t] = __ldcg(src + t);
+    }
   }
   __syncthreads();
 
@@ -255,22 +294,42 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
   return sh.smem_lines <= lim && sh.smem_image <= lim;
 }
 
-cudaError_t split_prepare(const SplitShape& sh) {
-  cudaError_t e = cudaFuncSetAttribute(split_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_lines);
+template <int G>
+static cudaError_t prepare_g(const SplitShape& sh) {
+  cudaError_t e = cudaFuncSetAttribute(split_lines<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_lines);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(split_image, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_image);
+    e = cudaFuncSetAttribute(split_image<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_image);
   return e;
+}
+
+cudaError_t split_prepare(const SplitShape& sh) {
+  switch (sh.G) {
+    case 8: return prepare_g<8>(sh);
+    case 16: return prepare_g<16>(sh);
+    case 32: return prepare_g<32>(sh);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int G>
+static void launch_g(const RenderParams& p, const SplitShape& sh, const SplitArgs& a, int max_items, int pass,
+                     cudaStream_t st) {
+  if (pass == 0)
+    split_lines<G><<<(unsigned)(max_items * a.gpi_lines), G * 32, sh.smem_lines, st>>>(p, a);
+  else
+    split_image<G><<<(unsigned)(max_items * a.gpi_image), G * 32, sh.smem_image, st>>>(p, a);
 }
 
 cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, int pass,
                               cudaStream_t st) {
   SplitArgs a = sh.args;
   a.beam = beam;
-  const int threads = sh.G * 32;
-  if (pass == 0)
-    split_lines<<<(unsigned)(max_items * a.gpi_lines), threads, sh.smem_lines, st>>>(p, a);
-  else
-    split_image<<<(unsigned)(max_items * a.gpi_image), threads, sh.smem_image, st>>>(p, a);
+  switch (sh.G) {
+    case 8: launch_g<8>(p, sh, a, max_items, pass, st); break;
+    case 16: launch_g<16>(p, sh, a, max_items, pass, st); break;
+    case 32: launch_g<32>(p, sh, a, max_items, pass, st); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

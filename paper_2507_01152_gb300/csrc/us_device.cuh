@@ -12,6 +12,7 @@ constexpr int kThetaDMax = 8;      // lateral reach of the incidence stencil, li
 // error-word bits
 constexpr unsigned kErrNonFinitePose = 1u;
 constexpr unsigned kErrBadItem = 2u;
+constexpr unsigned kErrStagingTimeout = 8u;   // an asynchronous copy into shared memory did not complete
 
 struct DevVolume {
   const uint8_t* labels;
@@ -47,6 +48,7 @@ struct DevProbe {
 struct DevPair {
   int W;
   const uint8_t* D;
+  int dmax;   // max over samples of D: the stencil's lateral reach for this pair
 };
 
 // one environment of a batch, in processing order

@@ -579,7 +579,7 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
         return cuda_fail(nullptr, e, "pairs");
       }
       s->d_pair_D.push_back(dD);
-      pairs.push_back(DevPair{W, dD});
+      pairs.push_back(DevPair{W, dD, D.empty() ? 1 : (int)*std::max_element(D.begin(), D.end())});
     }
   size_t max_beam = 0;
   for (const ProbeHost& ph : s->probes) max_beam = std::max(max_beam, (size_t)ph.desc.n_lines * ph.desc.n_samples);
@@ -812,6 +812,7 @@ us_status us_sim_check(us_sim* s, void* stream) {
   if ((e = cudaMemcpy(&w, s->d_err, sizeof w, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(s, e, "error word");
   if (w) {
     cudaMemset(s->d_err, 0, sizeof w);
+    if (w & kErrStagingTimeout) return fail(s, US_ERR_TIMEOUT, "a shared-memory staging copy did not complete in time");
     if (w & kErrNonFinitePose) return fail(s, US_ERR_INVALID_ARG, "a pose had a non-finite entry (rendered as water)");
     return fail(s, US_ERR_INTERNAL, "device consistency check failed");
   }
