@@ -171,20 +171,30 @@ __global__ void __launch_bounds__(G * 32, G == 32 ? 1 : 2) split_image(RenderPar
   const int NL = P.nl, NS = P.ns, KL = P.k_lat;
   const int w0 = group * G, w1 = min(w0 + G, NL);
   const int y1 = min(w1 + 1, NL);                                    // log rows w0 .. y1-1
-  const int a0 = max(w0 - KL, 0), a1 = min(y1 + KL, NL);             // filtered rows staged
+  // staged filtered rows r0 = w0 - KL .. w0 + nrows - 1, with zero rows
+  // outside the frame and past the last needed row, so that the lateral
+  // PSF needs no edge tests (adding w * 0 leaves a sum unchanged exactly:
+  // the sums never hold -0)
+  const int r0 = w0 - KL;
+  const int nrows = (((y1 - w0) + 3) & ~3) + 2 * KL;
+  const int a0 = max(r0, 0), a1 = min(y1 + KL, NL);                  // rows present in the line buffer
   const int tid = threadIdx.x;
-  float* abuf = reinterpret_cast<float*>(smem);                      // [a1 - a0][NS]
+  float* abuf = reinterpret_cast<float*>(smem);                      // [nrows][NS]
   float* ybuf = reinterpret_cast<float*>(smem + a.off_y);            // [y1 - w0][NS]
   float* wlat = reinterpret_cast<float*>(smem + a.off_wlat);
   for (int t = tid; t < 2 * KL + 1; t += blockDim.x) wlat[t] = __ldg(&P.w_lat[t]);
+  for (int t = tid; t < (a0 - r0) * NS; t += blockDim.x) abuf[t] = 0.f;
+  for (int t = (a1 - r0) * NS + tid; t < nrows * NS; t += blockDim.x) abuf[t] = 0.f;
   {
-    // the staged rows are one contiguous range of the line buffer: one bulk
-    // asynchronous copy when it is 16-byte aligned, else plain loads
+    // the present rows are one contiguous range of the line buffer: one
+    // bulk asynchronous copy when it is 16-byte aligned, else plain loads
     const float* src = a.beam + cx.it.beam_off + (long long)a0 * NS;
+    float* dst = abuf + (a0 - r0) * NS;
     const int n = (a1 - a0) * NS;
     __shared__ uint64_t bar;
     __shared__ int landed;
-    const bool bulk = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && (n & 3) == 0;
+    const bool bulk = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) &&
+                      (n & 3) == 0;
     if (bulk) {
       // one thread issues the copy and waits for it (bounded); the block
       // barrier then publishes the rows to every thread
@@ -194,7 +204,7 @@ __global__ void __launch_bounds__(G * 32, G == 32 ? 1 : 2) split_image(RenderPar
         umma::mbar_arrive_expect_tx(&bar, (uint32_t)n * 4u);
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                umma::smem_u32(abuf)),
+                umma::smem_u32(dst)),
             "l"(src), "r"((uint32_t)n * 4u), "r"(umma::smem_u32(&bar))
             : "memory");
         landed = umma::mbar_wait(&bar, 0) ? 1 : 0;
@@ -207,24 +217,39 @@ __global__ void __launch_bounds__(G * 32, G == 32 ? 1 : 2) split_image(RenderPar
       __syncthreads();
       if (!landed) return;
     } else {
-      for (int t = tid; t < n; t += blockDim.x) abuf[t] = __ldcg(src + t);
+      for (int t = tid; t < n; t += blockDim.x) dst[t] = __ldcg(src + t);
     }
   }
   __syncthreads();
 
-  // lateral PSF and log compression of rows w0 .. y1-1
+  // lateral PSF and log compression of rows w0 .. y1-1, four lines per
+  // thread; each line's taps are summed in increasing line order
   {
-    const int n = (y1 - w0) * NS;
-    for (int t = tid; t < n; t += blockDim.x) {
-      const int i = t / NS, s = t - i * NS, l = w0 + i;
-      const int mlo = max(l - KL, 0), mhi = min(l + KL, NL - 1);
-      float acc = 0.f;
-      for (int m = mlo; m <= mhi; ++m) acc = fmaf(wlat[m - l + KL], abuf[(m - a0) * NS + s], acc);
-      const float y = log_compress(P, acc);
-      ybuf[t] = y;
-      if (l < w1) {
-        if (p.envelope) p.envelope[cx.it.beam_off + (long long)l * NS + s] = acc;
-        if (p.logimg) p.logimg[cx.it.beam_off + (long long)l * NS + s] = y;
+    const int ng = (y1 - w0 + 3) >> 2;
+    const int taps = 2 * KL + 1;
+    for (int t = tid; t < ng * NS; t += blockDim.x) {
+      const int gi = t / NS, s = t - gi * NS, i0 = 4 * gi;
+      const float* col = abuf + i0 * NS + s;     // row of line w0 + i0 + j, tap q: i0 + j + q
+      float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+      for (int q = 0; q < taps; ++q) {
+        const float w = wlat[q];
+        const float* c = col + q * NS;
+        acc0 = fmaf(w, c[0], acc0);
+        acc1 = fmaf(w, c[NS], acc1);
+        acc2 = fmaf(w, c[2 * NS], acc2);
+        acc3 = fmaf(w, c[3 * NS], acc3);
+      }
+      const float accs[4] = {acc0, acc1, acc2, acc3};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = i0 + j, l = w0 + i;
+        if (l >= y1) break;
+        const float y = log_compress(P, accs[j]);
+        ybuf[i * NS + s] = y;
+        if (l < w1) {
+          if (p.envelope) p.envelope[cx.it.beam_off + (long long)l * NS + s] = accs[j];
+          if (p.logimg) p.logimg[cx.it.beam_off + (long long)l * NS + s] = y;
+        }
       }
     }
   }
@@ -263,15 +288,15 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
   const int G = sh.G;
   if (G != 8 && G != 16 && G != 32) return false;
   auto up = [](long long x, long long a) { return (x + a - 1) / a * a; };
-  long long zb = 0, lab = 0, ab = 0, yb = 0;
+  const size_t lim = 227 * 1024 - 1024;
+  // pass A
+  long long zb = 0, lab = 0;
   int gl = 0;
   for (const ProbeHost& ph : probes) {
     const int NL = ph.desc.n_lines, NS = ph.desc.n_samples;
     const int rs = (NS + 2 * ph.k_ax) | 1;
     zb = std::max(zb, (long long)G * rs * 4);
     lab = std::max(lab, (long long)std::min(NL, G + 2 * kThetaDMax) * NS);
-    ab = std::max(ab, (long long)std::min(NL, G + 1 + 2 * ph.k_lat) * NS * 4);
-    yb = std::max(yb, (long long)std::min(NL, G + 1) * NS * 4);
     gl = std::max(gl, (NL + G - 1) / G);
   }
   long long off = up(zb, 16);
@@ -282,33 +307,56 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
   sh.args.off_lab = (int)off;
   off = up(off + lab, 16);
   sh.smem_lines = (size_t)off;
-  off = up(ab, 16);
-  sh.args.off_y = (int)off;
-  off = up(off + yb, 16);
-  sh.args.off_wlat = (int)off;
-  off = up(off + 4 * (2 * kMaxHalfTaps + 1), 16);
-  sh.smem_image = (size_t)off;
-  sh.args.G = G;
-  sh.args.gpi_lines = sh.args.gpi_image = gl;
-  const size_t lim = 227 * 1024 - 1024;
-  return sh.smem_lines <= lim && sh.smem_image <= lim;
+  if (sh.smem_lines > lim) return false;
+  // pass B: the widest wedge whose staged rows and log rows fit
+  for (int GB : {32, 16, 8}) {
+    long long ab = 0, yb = 0;
+    int gi = 0;
+    for (const ProbeHost& ph : probes) {
+      const int NL = ph.desc.n_lines, NS = ph.desc.n_samples;
+      ab = std::max(ab, (long long)(((std::min(NL, GB + 1) + 3) & ~3) + 2 * ph.k_lat) * NS * 4);
+      yb = std::max(yb, (long long)std::min(NL, GB + 1) * NS * 4);
+      gi = std::max(gi, (NL + GB - 1) / GB);
+    }
+    long long o = up(ab, 16);
+    const int off_y = (int)o;
+    o = up(o + yb, 16);
+    const int off_wlat = (int)o;
+    o = up(o + 4 * (2 * kMaxHalfTaps + 1), 16);
+    if ((size_t)o <= lim) {
+      sh.GB = GB;
+      sh.smem_image = (size_t)o;
+      sh.args.off_y = off_y;
+      sh.args.off_wlat = off_wlat;
+      sh.args.G = G;
+      sh.args.GB = GB;
+      sh.args.gpi_lines = gl;
+      sh.args.gpi_image = gi;
+      return true;
+    }
+  }
+  return false;
 }
 
+// pass 0: split_lines<G>, pass 1: split_image<G>
 template <int G>
-static cudaError_t prepare_g(const SplitShape& sh) {
-  cudaError_t e = cudaFuncSetAttribute(split_lines<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_lines);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(split_image<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_image);
-  return e;
+static cudaError_t prepare_g(int pass, size_t smem) {
+  return pass == 0 ? cudaFuncSetAttribute(split_lines<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                   : cudaFuncSetAttribute(split_image<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+static cudaError_t prepare_pass(int pass, int G, size_t smem) {
+  switch (G) {
+    case 8: return prepare_g<8>(pass, smem);
+    case 16: return prepare_g<16>(pass, smem);
+    case 32: return prepare_g<32>(pass, smem);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t split_prepare(const SplitShape& sh) {
-  switch (sh.G) {
-    case 8: return prepare_g<8>(sh);
-    case 16: return prepare_g<16>(sh);
-    case 32: return prepare_g<32>(sh);
-    default: return cudaErrorInvalidValue;
-  }
+  cudaError_t e = prepare_pass(0, sh.G, sh.smem_lines);
+  return e == cudaSuccess ? prepare_pass(1, sh.GB, sh.smem_image) : e;
 }
 
 template <int G>
@@ -324,7 +372,7 @@ cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float
                               cudaStream_t st) {
   SplitArgs a = sh.args;
   a.beam = beam;
-  switch (sh.G) {
+  switch (pass == 0 ? sh.G : sh.GB) {
     case 8: launch_g<8>(p, sh, a, max_items, pass, st); break;
     case 16: launch_g<16>(p, sh, a, max_items, pass, st); break;
     case 32: launch_g<32>(p, sh, a, max_items, pass, st); break;

@@ -32,6 +32,7 @@ struct DevProbe {
   int kind, nl, ns, out_w, out_h;
   int k_ax, k_lat;
   float dr, r0, e0, log_gain, dtheta, pitch;
+  float db_e0;               // 20 log10(e0)
   const float2* lines;       // [nl]: linear (x_l, 0), curvilinear (sin, cos)
   const float* w_ax;         // [2 k_ax + 1]
   const float* w_lat;        // [2 k_lat + 1]
@@ -210,9 +211,12 @@ __device__ __forceinline__ float lateral_spacing(const DevProbe& P, int s) {
   return P.kind == 0 ? P.pitch : fmaf((float)s, P.dr, P.r0) * P.dtheta;
 }
 
-// log compression to [0, 1] over the probe's dynamic range
+// log compression to [0, 1] over the probe's dynamic range:
+// 20 log10(I / e0) = (20 log10 2) log2(I) - 20 log10(e0), with the hardware
+// base-2 logarithm (about 2^-22 relative error, far below the image's
+// quantisation) and the e0 term precomputed on the host
 __device__ __forceinline__ float log_compress(const DevProbe& P, float I) {
-  const float db = 20.f * log10f(fmaxf(I, 1e-30f) / P.e0);
+  const float db = fmaf(6.02059991327962390f, __log2f(fmaxf(I, 1e-30f)), -P.db_e0);
   return __saturatef(fmaf(db, P.log_gain, 1.f));
 }
 

@@ -170,6 +170,7 @@ DevProbe device_probe(const ProbeHost& ph) {
   d.r0 = p.radius_mm;
   d.e0 = p.e0;
   d.log_gain = (float)(1.0 / (double)p.dyn_range_db);
+  d.db_e0 = (float)(20.0 * std::log10((double)p.e0));
   d.dtheta = (float)ph.dtheta;
   d.pitch = p.pitch_mm;
   d.lines = ph.d_lines;
@@ -358,10 +359,10 @@ us_status apply_split(us_sim* s, const us_tuning& t) {
   cudaError_t e;
   bool changed = false;
   for (ProbeHost& ph : s->probes) {
-    if (ph.desc.kind != 1 || ph.wedge_G == sh.G) continue;
+    if (ph.desc.kind != 1 || ph.wedge_G == sh.GB) continue;
     std::vector<float4> ent;
     std::vector<int> off;
-    build_wedges(ph.lut_host, ph.desc.out_w, ph.desc.out_h, ph.desc.n_lines, sh.G, ent, off);
+    build_wedges(ph.lut_host, ph.desc.out_w, ph.desc.out_h, ph.desc.n_lines, sh.GB, ent, off);
     cudaFree(ph.d_wedge);
     cudaFree(ph.d_wedge_off);
     ph.d_wedge = nullptr;
@@ -370,7 +371,7 @@ us_status apply_split(us_sim* s, const us_tuning& t) {
     if ((e = upload(&ph.d_wedge, ent.data(), ent.size())) != cudaSuccess ||
         (e = upload(&ph.d_wedge_off, off.data(), off.size())) != cudaSuccess)
       return cuda_fail(s, e, "wedge tables");
-    ph.wedge_G = sh.G;
+    ph.wedge_G = sh.GB;
     changed = true;
   }
   if (changed) {

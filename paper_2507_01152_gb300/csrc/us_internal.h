@@ -68,16 +68,17 @@ cudaError_t fused_prepare(const FusedShape& s);
 cudaError_t fused_max_clusters(const FusedShape& s, int* clusters);
 cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_t st);
 
-// two-pass path: lines per block G (8, 16, 32), shared-memory layouts of
-// both passes, blocks per item of each pass
+// two-pass path: lines per pass-A block G and per pass-B wedge GB (8, 16,
+// 32), shared-memory layouts of both passes, blocks per item of each pass
 struct SplitArgs {
   float* beam = nullptr;   // axially filtered lines, beam layout (per item beam_off)
-  int G = 32, gpi_lines = 0, gpi_image = 0;
+  int G = 32, GB = 32, gpi_lines = 0, gpi_image = 0;
   int off_wax = 0, off_tis = 0, off_lab = 0;   // pass A byte offsets
   int off_y = 0, off_wlat = 0;                 // pass B byte offsets
 };
 struct SplitShape {
-  int G = 32;
+  int G = 32;    // pass A lines per block (the tuning's warps_per_cta)
+  int GB = 32;   // pass B lines per wedge: the widest whose buffers fit
   SplitArgs args{};
   size_t smem_lines = 0, smem_image = 0;
 };
