@@ -145,18 +145,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def make_workload(name):
+def make_workload(name, copies=1):
+    """The named workload; `copies` > 1 makes a global batch of that many
+    per-rank batches (distinct poses), to be split over the ranks."""
     if name == "c2":
-        return scene.workload_c2(64)
+        return scene.workload_c2(64 * copies)
     if name == "c1":
         return scene.workload_c1()
     if name == "paper":
-        return scene.workload_paper_replica(100)
+        return scene.workload_paper_replica(100 * copies)
     if name == "c3":
-        wl = scene.workload_c3(512, steps=1)
+        wl = scene.workload_c3(512 * copies, steps=1)
         wl.poses = wl.poses[0]
         return wl
     raise ValueError(name)
+
+
+def rank_workload(wl, rank, world):
+    """This rank's contiguous, cost-balanced range of a global batch (the
+    envs and poses it renders; volumes and probes are shared)."""
+    import dataclasses
+    from paper_2507_01152_gb300 import shard
+    if world == 1:
+        return wl, (0, len(wl.envs))
+    lo, hi = shard.partition(shard.env_costs(wl.probes, wl.envs), world)[rank]
+    sub = dataclasses.replace(wl, envs=wl.envs[lo:hi], poses=wl.poses[lo:hi])
+    return sub, (lo, hi)
 
 
 def cpu_oracle_rate(wl, seconds=10.0, max_frames=None):
@@ -346,7 +360,13 @@ def run_ours(args):
         dist.init_process_group("nccl")
     build.build()
 
-    wl = make_workload(args.workload)
+    from paper_2507_01152_gb300 import shard
+    # weak scaling: a global batch of `world` per-rank batches, split into
+    # contiguous cost-balanced ranges (no collective on the data path)
+    if args.workload == "c1":      # a single environment: every rank renders its own copy
+        wl = make_workload("c1")
+    else:
+        wl, _ = rank_workload(make_workload(args.workload, world), rank, world)
     B = len(wl.envs)
     vols = [(torch.from_numpy(lab).cuda(), torch.from_numpy(hu).cuda(), spec.voxel_mm) for (spec, lab, hu) in wl.volumes]
     sim = Sim(vols, scene.tissue_table(), wl.probes, wl.options)
@@ -356,7 +376,7 @@ def run_ours(args):
     poses = torch.from_numpy(np.ascontiguousarray(wl.poses, np.float32)).cuda()
     frames = torch.empty(int(off[-1]), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    seed = wl.seed + 7919 * rank
+    seed = shard.rank_seed(wl.seed, rank)
 
     def timed(fn, steps, warmup):
         with torch.cuda.stream(stream):
@@ -391,12 +411,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     total = sum(times)
     sim.check(stream)
+    total, frames_all = shard.reduce_timing(total, B * args.steps, dist, device="cuda")
     if dist is not None:
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
         dist.barrier()
-    value = B * args.steps * world / total
+    value = frames_all / total
     kernel_s = total / args.steps           # device time of one render step (all its kernels)
 
     # plain per-environment form on the same batch (comparison)
@@ -416,8 +434,8 @@ def run_ours(args):
     e2e_steps = max(3, args.steps)
     for k in range(e2e_steps):
         sim.render_host(None, host_poses, seed, 6000 + k, host_frames, stream=stream, envs_c=envs_c)
-    e2e_el = time.perf_counter() - t0
-    e2e = {"value": B * e2e_steps / e2e_el * world, "unit": "frames/s", "h2d_bytes_per_step": int(host_poses.nbytes),
+    e2e_el, e2e_frames = shard.reduce_timing(time.perf_counter() - t0, B * e2e_steps, dist, device="cuda")
+    e2e = {"value": e2e_frames / e2e_el, "unit": "frames/s", "h2d_bytes_per_step": int(host_poses.nbytes),
            "d2h_bytes_per_step": int(host_frames.nbytes)}
 
     # per-kernel durations of the same render (events around each kernel on
@@ -469,7 +487,8 @@ def run_ours(args):
                 "config": {"workload": wl.name, "envs_per_gpu": B, "l2": "flushed between timed steps (256 MB write)",
                            "path": ("two-pass batched kernels" if tuning["cluster_size"] == 1
                                     else "persistent cluster kernel") + ", CUDA graph replay, autotuned",
-                           "tuning": tuning, "parallelism": f"replicas{world}"},
+                           "tuning": tuning,
+                           "parallelism": f"{world} ranks, contiguous cost-balanced env shards, no collective"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * (2 if tuning["cluster_size"] == 1 else 1),
                 "plain": plain, "surrogate": surrogate, "clocks": clk.summary()}
