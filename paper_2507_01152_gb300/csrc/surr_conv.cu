@@ -423,6 +423,98 @@ bool conv_tma(cudaError_t& e, View x, int C, int B, int Hi, int Wi, int Ho, int 
   return false;
 }
 
+// Weight gradient of a 3x3 convolution through tensor copies, both operands
+// MN-major (channels contiguous, as the NHWC tensors already are): for the
+// K step of 64 output pixels (a box of Yb rows x Xb columns of one image),
+// A = the input pixels under tap (ky, kx), CB (64 or 32) channels per
+// swizzled box (128 / CB boxes per tile, each inside one tap), B = the
+// output gradient of the same pixels, BN channels in boxes of up to 64.
+// Rows past the last tap copy a box wholly outside the image.
+template <int CB>
+struct WgradTmaLoader {
+  static constexpr bool kTma = true;
+  static constexpr int kALayout = CB == 64 ? 3 : 4;
+  static constexpr bool kBMajorMN = true;
+  static constexpr int kBoxes = kBM / CB;
+  static constexpr uint32_t kBoxBytes = 64u * 2u * CB;
+  CUtensorMap ta;   // X: (Cin, Wi, Hi, B), traversal steps (1, s, s, 1), box (64, Xb s, Yb s, 1)
+  CUtensorMap tb;   // dY: (Cout, Wo, Ho, B), box (bb, Xb, Yb, 1)
+  int Ho, Wo, Hi, Cin, stride, bb, nbox;   // bb channels per B box, nbox boxes per B tile
+  __device__ __forceinline__ void pix(int kt, int& b, int& y0, int& x0) const {
+    const int p0 = kt * kBK, hw = Ho * Wo;
+    b = p0 / hw;
+    const int r = p0 - b * hw;
+    y0 = r / Wo;
+    x0 = r - y0 * Wo;
+  }
+  __device__ void issue_a(uint32_t as, int m0, int kt, uint32_t bar) const {
+    int b, y0, x0;
+    pix(kt, b, y0, x0);
+#pragma unroll
+    for (int h = 0; h < kBoxes; ++h) {
+      const int r = m0 + CB * h, tap = r / Cin, c = r - tap * Cin, ky = tap / 3, kx = tap - 3 * ky;
+      if (tap < 9)
+        tma_load_4d(as + h * kBoxBytes, &ta, c, x0 * stride + kx - 1, y0 * stride + ky - 1, b, bar);
+      else
+        tma_load_4d(as + h * kBoxBytes, &ta, 0, 0, Hi, b, bar);
+    }
+  }
+  __device__ void issue_b(uint32_t bs, int n0, int kt, uint32_t bar) const {
+    int b, y0, x0;
+    pix(kt, b, y0, x0);
+    for (int j = 0; j < nbox; ++j) tma_load_4d(bs + (uint32_t)j * 64u * 2u * (uint32_t)bb, &tb, n0 + j * bb, x0, y0, b, bar);
+  }
+};
+
+// 64 pixels of one image as Yb rows x Xb columns
+inline bool pix64_box(int Ho, int Wo, int& Xb, int& Yb) {
+  if (Wo % 64 == 0) {
+    Xb = 64;
+    Yb = 1;
+    return true;
+  }
+  if (64 % Wo == 0 && Ho % (64 / Wo) == 0) {
+    Xb = Wo;
+    Yb = 64 / Wo;
+    return true;
+  }
+  return false;
+}
+
+template <int CB>
+inline bool make_wgrad_tma(WgradTmaLoader<CB>& L, View x, View dy, int Cin, int Cout, int B, int Hi, int Wi, int Ho,
+                           int Wo, int stride, int bn) {
+  int Xb, Yb;
+  // B tiles of 32 or more channels (64- and 128-byte swizzled MN-major
+  // boxes); 16-channel outputs gather with the register-transpose loader
+  if (Cin % CB || bn < 32 || !pix64_box(Ho, Wo, Xb, Yb)) return false;
+  const int bb = bn < 64 ? bn : 64;
+  {
+    const uint64_t pitch = (uint64_t)x.cs * 2;
+    const uint64_t d[4] = {(uint64_t)Cin, (uint64_t)Wi, (uint64_t)Hi, (uint64_t)B};
+    const uint64_t st[3] = {pitch, pitch * Wi, pitch * Wi * Hi};
+    const uint32_t bx[4] = {(uint32_t)CB, (uint32_t)(Xb * stride), (uint32_t)(Yb * stride), 1};
+    const uint32_t e[4] = {1, (uint32_t)stride, (uint32_t)stride, 1};
+    if (!tma::encode_bf16(&L.ta, x.p + x.co, 4, d, st, bx, e, 2 * CB)) return false;
+  }
+  {
+    const uint64_t pitch = (uint64_t)dy.cs * 2;
+    const uint64_t d[4] = {(uint64_t)Cout, (uint64_t)Wo, (uint64_t)Ho, (uint64_t)B};
+    const uint64_t st[3] = {pitch, pitch * Wo, pitch * Wo * Ho};
+    const uint32_t bx[4] = {(uint32_t)bb, (uint32_t)Xb, (uint32_t)Yb, 1};
+    const uint32_t e[4] = {1, 1, 1, 1};
+    if (!tma::encode_bf16(&L.tb, dy.p + dy.co, 4, d, st, bx, e, 2 * bb)) return false;
+  }
+  L.Ho = Ho;
+  L.Wo = Wo;
+  L.Hi = Hi;
+  L.Cin = Cin;
+  L.stride = stride;
+  L.bb = bb;
+  L.nbox = bn / bb;
+  return true;
+}
+
 // --------------------------------------------------------------- wgrad
 // Both operands of a weight gradient are stored pixel-major (channels
 // contiguous), while the GEMM reduces over pixels.  The loader reads
@@ -536,7 +628,8 @@ int pick_bn(int N) {
 
 // split the pixel reduction of a weight gradient so that the grid covers
 // about four waves of the GPU
-int wgrad_splits(int mt, int nt, long long P) {
+int wgrad_splits(int mt, int nt, long long P, int X = 1) {
+  mt = (mt + X - 1) / X;   // tile groups along M
   int sms = 152;
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -607,10 +700,21 @@ us_status us_conv3x3_wgrad(const uint16_t* x, int32_t x_cs, int32_t x_co, const 
   US_CHECK(aligned16(x) && aligned16(dy));
   const Grid in{B, H, W}, out{B, (H - 1) / stride + 1, (W - 1) / stride + 1};
   const int rows = 9 * Cin, P = B * out.H * out.W, bn = pick_bn(Cout);
-  WgradLoader<ConvIm2col, PixelRows> ld{{{(const bf16*)x, x_cs, x_co}, in, out, Cin, stride, rows},
-                                        {{(const bf16*)dy, dy_cs, dy_co}, Cout}, P, bn};
   AtomicF32Store ep{gwt, Cout, rows};
   const int mt = (rows + kBM - 1) / kBM, nt = Cout / bn;
+  const int X = bn <= 64 ? 4 : (bn <= 128 ? 2 : 1);
+  const View xv{(const bf16*)x, x_cs, x_co}, dyv{(const bf16*)dy, dy_cs, dy_co};
+  if (Cin % 64 == 0) {
+    WgradTmaLoader<64> tl;
+    if (make_wgrad_tma(tl, xv, dyv, Cin, Cout, B, H, W, out.H, out.W, stride, bn))
+      return to_status(gemm_bn(bn, tl, ep, rows, Cout, P, err, (cudaStream_t)stream, wgrad_splits(mt, nt, P, X)));
+  } else if (Cin % 32 == 0) {
+    WgradTmaLoader<32> tl;
+    if (make_wgrad_tma(tl, xv, dyv, Cin, Cout, B, H, W, out.H, out.W, stride, bn))
+      return to_status(gemm_bn(bn, tl, ep, rows, Cout, P, err, (cudaStream_t)stream, wgrad_splits(mt, nt, P, X)));
+  }
+  WgradLoader<ConvIm2col, PixelRows> ld{{{(const bf16*)x, x_cs, x_co}, in, out, Cin, stride, rows},
+                                        {{(const bf16*)dy, dy_cs, dy_co}, Cout}, P, bn};
   return to_status(gemm_bn(bn, ld, ep, rows, Cout, P, err, (cudaStream_t)stream, wgrad_splits(mt, nt, P)));
 }
 

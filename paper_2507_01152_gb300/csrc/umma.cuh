@@ -132,11 +132,26 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
   return d;
 }
 
+// MN-major operand (the M or N index contiguous): atoms of 8 K-rows, each
+// row `row_bytes` (128, 64 or 32: 64, 32 or 16 BF16 elements of M or N)
+// with the matching swizzle; SBO = the 8-row atom (8 x row_bytes), LBO =
+// distance between atoms adjacent along M / N.
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t saddr, uint32_t row_bytes, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(((8u * row_bytes) >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)(row_bytes == 128 ? 2 : (row_bytes == 64 ? 4 : 6)) << 61;   // SWIZZLE_128B / 64B / 32B
+  return d;
+}
+
 // Instruction descriptor of kind::f16: D = F32 [4,6), A = BF16 [7,10),
-// B = BF16 [10,13), both K-major (bits 15, 16 = 0), N >> 3 at [17,23),
-// M >> 4 at [24,29).
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// B = BF16 [10,13), A / B major at bits 15 / 16 (0 K-major, 1 MN-major),
+// N >> 3 at [17,23), M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, bool a_mn = false, bool b_mn = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, one M x N x 16 step, issued by one thread

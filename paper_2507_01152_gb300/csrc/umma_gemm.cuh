@@ -88,6 +88,10 @@ struct a_layout_of : std::integral_constant<int, 0> {};
 template <class L>
 struct a_layout_of<L, std::void_t<decltype(L::kALayout)>> : std::integral_constant<int, L::kALayout> {};
 
+//   3  MN-major: two 128-byte-swizzled boxes of 64 K-rows x 64 M-elements
+//      (8 KB each, the second M half 8 KB on)
+//   4  MN-major: four 64-byte-swizzled boxes of 64 K-rows x 32 M-elements
+//      (4 KB each)
 // descriptor of the 16-wide K slice k (0..3) of a stage's A tile
 template <int LAYOUT>
 __device__ __forceinline__ uint64_t a_desc(uint32_t sa, int k) {
@@ -95,8 +99,31 @@ __device__ __forceinline__ uint64_t a_desc(uint32_t sa, int k) {
     return smem_desc_sw64(sa + (uint32_t)(k >> 1) * 8192u + (uint32_t)(k & 1) * 32u);
   else if constexpr (LAYOUT == 2)
     return smem_desc_kmajor(sa + (uint32_t)k * 4096u, 2048u, 128u);
+  else if constexpr (LAYOUT == 3)
+    return smem_desc_mn(sa + (uint32_t)k * 2048u, 128u, 8192u);
+  else if constexpr (LAYOUT == 4)
+    return smem_desc_mn(sa + (uint32_t)k * 1024u, 64u, 4096u);
   else
     return smem_desc_sw128(sa + 32u * (uint32_t)k);
+}
+
+// B tile layout, declared by the loader as kBMajorMN: false = K-major
+// 128-byte swizzle (default); true = MN-major, BN / min(BN, 64) boxes of
+// 64 K-rows x min(BN, 64) N-elements, rows of 2 min(BN, 64) bytes (BN >= 32:
+// 128- or 64-byte swizzle)
+template <class L, class = void>
+struct b_mn_of : std::false_type {};
+template <class L>
+struct b_mn_of<L, std::void_t<decltype(L::kBMajorMN)>> : std::integral_constant<bool, L::kBMajorMN> {};
+
+template <bool MN, int BN>
+__device__ __forceinline__ uint64_t b_desc(uint32_t sb, int k) {
+  if constexpr (MN) {
+    constexpr uint32_t row = BN >= 64 ? 128u : (uint32_t)BN * 2u;
+    return smem_desc_mn(sb + (uint32_t)k * 16u * row, row, 64u * row);
+  } else {
+    return smem_desc_sw128(sb + 32u * (uint32_t)k);
+  }
 }
 
 // bounded wait that also gives up when another role has aborted
@@ -136,7 +163,8 @@ __global__ void __launch_bounds__(gemm_threads<X>(), 1)
   constexpr int S = gemm_stages<BN, X>();
   constexpr uint32_t SB = stage_bytes<BN, X>();
   constexpr uint32_t NCOL = tmem_cols<BN>();
-  constexpr uint32_t IDESC = idesc_bf16_f32(kBM, BN);
+  constexpr bool A_MN = a_layout_of<Loader>::value >= 3, B_MN = b_mn_of<Loader>::value;
+  constexpr uint32_t IDESC = idesc_bf16_f32(kBM, BN, A_MN, B_MN);
   constexpr bool TMA = is_tma_loader<Loader>::value;
   constexpr int kEpiWarp = kMmaWarp + X;
   static_assert(TMA || X == 1, "gather loaders stage one A tile per stage");
@@ -250,7 +278,7 @@ __global__ void __launch_bounds__(gemm_threads<X>(), 1)
           const uint32_t sa = smem_u32(smem + s * SB) + (uint32_t)w * kTileA, sb = smem_u32(smem + s * SB) + X * kTileA;
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k)
-            mma_bf16(acc, a_desc<a_layout_of<Loader>::value>(sa, k), smem_desc_sw128(sb + 32 * k), IDESC,
+            mma_bf16(acc, a_desc<a_layout_of<Loader>::value>(sa, k), b_desc<B_MN, BN>(sb, k), IDESC,
                      (t > 0 || k > 0) ? 1u : 0u);
           mma_commit(&empty[s]);
         }
