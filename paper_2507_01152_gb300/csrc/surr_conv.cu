@@ -198,6 +198,9 @@ struct MaskedGradStore {
   int accumulate;
   __device__ void store(int m, int n0, const float* v, bool valid) const {
     if (!valid) return;
+    store_pixel(m, n0, v);
+  }
+  __device__ void store_pixel(long long m, int n0, const float* v) const {
     const uint4* xp = reinterpret_cast<const uint4*>(x.p + (size_t)m * x.cs + x.co + n0);
     __align__(16) bf16 xv[16];
     reinterpret_cast<uint4*>(xv)[0] = __ldg(xp);
@@ -217,6 +220,19 @@ struct MaskedGradStore {
     }
     dst[0] = reinterpret_cast<const uint4*>(o)[0];
     dst[1] = reinterpret_cast<const uint4*>(o)[1];
+  }
+};
+
+// the same for one parity class of a stride-2 data gradient: GEMM row m is
+// pixel (y', x') of the class grid (Ho x Wo), i.e. input pixel
+// (2 y' + py, 2 x' + px) of the 2Ho x 2Wo input grid
+struct MaskedGradStoreS2 {
+  MaskedGradStore base;
+  int Ho, Wo, py, px;
+  __device__ void store(int m, int n0, const float* v, bool valid) const {
+    if (!valid) return;
+    const int hw = Ho * Wo, b = m / hw, r = m - b * hw, y = r / Wo, xx = r - y * Wo;
+    base.store_pixel(((long long)b * 2 * Ho + 2 * y + py) * (2 * Wo) + 2 * xx + px, n0, v);
   }
 };
 
@@ -422,6 +438,30 @@ bool conv_tma(cudaError_t& e, View x, int C, int B, int Hi, int Wi, int Ho, int 
   }
   return false;
 }
+
+// Data gradient of a stride-2 3x3 convolution, one output-parity class
+// (py, px) at a time: input pixel (2y' + py, 2x' + px) receives dY at
+// (y' + oy, x' + ox) through the taps ky = py + 1 - 2 oy (kx likewise) that
+// land on it - 1, 2, 2 or 4 taps instead of 9 with three quarters zero.  A
+// = tensor copies of the dY box of the tile's 128 class pixels shifted by
+// (oy, ox) per tap (64 output channels per K step); B = the columns of the
+// transposed weights [Cin][9 Cout] of the class's taps.
+struct DgradS2TmaLoader {
+  static constexpr bool kTma = true;
+  CUtensorMap ta;   // dY: (Cout, Wo, Ho, B)
+  CUtensorMap tb;   // transposed weights: (9 Cout, Cin)
+  int Ho, Wo, Cout, ntaps;
+  int tap[4], oy[4], ox[4];
+  __device__ void issue_a(uint32_t as, int m0, int kt, uint32_t bar) const {
+    const int hw = Ho * Wo, b = m0 / hw, r = m0 - b * hw, y0 = r / Wo, x0 = r - y0 * Wo;
+    const int k = kt * kBK, i = k / Cout, c0 = k - i * Cout;
+    tma_load_4d(as, &ta, c0, x0 + ox[i], y0 + oy[i], b, bar);
+  }
+  __device__ void issue_b(uint32_t bs, int n0, int kt, uint32_t bar) const {
+    const int k = kt * kBK, i = k / Cout, c0 = k - i * Cout;
+    tma_load_2d(bs, &tb, tap[i] * Cout + c0, n0, bar);
+  }
+};
 
 // Weight gradient of a 3x3 convolution through tensor copies, both operands
 // MN-major (channels contiguous, as the NHWC tensors already are): for the
@@ -688,6 +728,38 @@ us_status us_conv3x3_dgrad(const uint16_t* dy, int32_t dy_cs, int32_t dy_co, con
   if (stride == 1 && conv_tma(e, {(const bf16*)dy, dy_cs, dy_co}, Cout, B, H, W, H, W, 1, -1, (const bf16*)wd, K, Cin,
                               bn, ep, M, err, (cudaStream_t)stream))
     return to_status(e);
+  int Xb, Yb;
+  if (stride == 2 && H % 2 == 0 && W % 2 == 0 && Cout % kBK == 0 && conv_tma_box(out.H, out.W, Xb, Yb)) {
+    // four parity classes, each a dense convolution over dY with its own taps
+    DgradS2TmaLoader tl;
+    const uint64_t pitch = (uint64_t)dy_cs * 2;
+    const uint64_t d[4] = {(uint64_t)Cout, (uint64_t)out.W, (uint64_t)out.H, (uint64_t)B};
+    const uint64_t st[3] = {pitch, pitch * out.W, pitch * out.W * out.H};
+    const uint32_t bx[4] = {(uint32_t)kBK, (uint32_t)Xb, (uint32_t)Yb, 1}, es[4] = {1, 1, 1, 1};
+    if (tma::encode_bf16(&tl.ta, (const bf16*)dy + dy_co, 4, d, st, bx, es) &&
+        rows_map(&tl.tb, (const bf16*)wd, K, Cin, K, bn)) {
+      tl.Ho = out.H;
+      tl.Wo = out.W;
+      tl.Cout = Cout;
+      const int Mc = B * out.H * out.W;
+      for (int py = 0; py < 2; ++py)
+        for (int px = 0; px < 2; ++px) {
+          tl.ntaps = 0;
+          for (int ky = 0; ky < 3; ++ky)
+            for (int kx = 0; kx < 3; ++kx)
+              if (((py + 1 - ky) & 1) == 0 && ((px + 1 - kx) & 1) == 0) {
+                tl.tap[tl.ntaps] = 3 * ky + kx;
+                tl.oy[tl.ntaps] = (py + 1 - ky) / 2;
+                tl.ox[tl.ntaps] = (px + 1 - kx) / 2;
+                ++tl.ntaps;
+              }
+          MaskedGradStoreS2 eps{ep, out.H, out.W, py, px};
+          if ((e = gemm_bn(bn, tl, eps, Mc, Cin, tl.ntaps * Cout, err, (cudaStream_t)stream)) != cudaSuccess)
+            return to_status(e);
+        }
+      return US_OK;
+    }
+  }
   ConvDgradLoader ld{{(const bf16*)dy, dy_cs, dy_co}, (const bf16*)wd, in, out, Cout, K, Cin, stride, M, bn};
   return to_status(gemm_bn(bn, ld, ep, M, Cin, K, err, (cudaStream_t)stream));
 }
