@@ -368,6 +368,10 @@ def run_ours(args):
         wl = make_workload("c1")
     else:
         wl, _ = rank_workload(make_workload(args.workload, world), rank, world)
+    if args.speckle == "anchored":   # fixed two-scale scatter maps over the volume (0.25 mm cells)
+        import dataclasses
+        wl = dataclasses.replace(wl, options=dataclasses.replace(wl.options, speckle_anchor=1, speckle_levels=2,
+                                                                 speckle_cell_mm=0.25))
     B = len(wl.envs)
     vols = [(torch.from_numpy(lab).cuda(), torch.from_numpy(hu).cuda(), spec.voxel_mm) for (spec, lab, hu) in wl.volumes]
     sim = Sim(vols, scene.tissue_table(), wl.probes, wl.options)
@@ -461,7 +465,8 @@ def run_ours(args):
     achieved = ops / (kavg[dom] / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": apeak / 1e12, "unit": "Tlane-op/s",
                 "frac": achieved * 1e12 / apeak,
-                "traffic": KERNEL_DRAM_BYTES.get((wl.name, names[dom], tuning["warps_per_cta"])),
+                "traffic": KERNEL_DRAM_BYTES.get((wl.name if args.speckle == "beam" else None, names[dom],
+                                                  tuning["warps_per_cta"])),
                 "kernel": names[dom], "kernel_ms": kavg[dom], "kernels_ms": dict(zip(names, kavg)),
                 "lane_ops_per_launch": ops, "peak_source": f"{sms} SMs x 128 lanes x {asrc}"}
     if args.workload == "c2":
@@ -485,7 +490,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl.name, "envs_per_gpu": B, "l2": "flushed between timed steps (256 MB write)",
+                "config": {"workload": wl.name + ("_anchored_speckle" if args.speckle == "anchored" else ""),
+                           "envs_per_gpu": B, "l2": "flushed between timed steps (256 MB write)",
                            "path": ("two-pass batched kernels" if tuning["cluster_size"] == 1
                                     else "persistent cluster kernel") + ", CUDA graph replay, autotuned",
                            "tuning": tuning,
@@ -513,6 +519,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--gate-l1", type=float, default=0.05)
+    ap.add_argument("--speckle", default="beam", choices=["beam", "anchored"],
+                    help="scatter maps keyed by beam sample (default) or fixed over the volume")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -112,9 +112,20 @@ typedef struct {
  * z_mode 0: Z = max(HU + 1024, 1), "proportional to CT intensity" (App. B.2);
  *   1: Z from the tissue table.
  * speckle 1: N0, N1 from Philox-4x32-10 keyed by (env, line, sample, seed,
- *   step); 0: T = mu0 everywhere. */
+ *   step); 0: T = mu0 everywhere.
+ * speckle_anchor 1 (with speckle 1): N0, N1 are maps fixed over the volume
+ *   (App. B.2: sampled over 3-D space once), so the speckle moves with the
+ *   tissue: speckle_levels scales (1..3, the multi-scale maps of App. B.2) of
+ *   cubic cells of edge speckle_cell_mm * 2^k anchored at the volume origin;
+ *   a sample takes its nearest cell at each scale, whose Philox-4x32-10
+ *   words (counter = cell x, y, z, k << 16 | volume index; key = seed, no
+ *   step) give standard normals; N = sum_k a_k N_k with a_k proportional to
+ *   2^(-k/2), unit variance.  T = N0 sigma0 + mu0 where N1 <= mu1.
+ *   0: the beam-keyed maps above (speckle_levels, speckle_cell_mm unused). */
 typedef struct {
   int32_t refl_power, transmission, z_mode, speckle;
+  int32_t speckle_anchor, speckle_levels;
+  float speckle_cell_mm;
 } us_options;
 
 /* One environment of a batch: which volume and which probe it uses. */

@@ -45,7 +45,7 @@ def build(force: bool = False) -> str:
 
 class OrVolume(C.Structure):
     _fields_ = [("labels", C.c_void_p), ("hu", C.c_void_p), ("nx", C.c_int32),
-                ("ny", C.c_int32), ("nz", C.c_int32), ("voxel_mm", C.c_float)]
+                ("ny", C.c_int32), ("nz", C.c_int32), ("voxel_mm", C.c_float), ("id", C.c_int32)]
 
 
 class OrTissue(C.Structure):
@@ -63,13 +63,14 @@ class OrProbe(C.Structure):
 
 class OrOptions(C.Structure):
     _fields_ = [("refl_power", C.c_int32), ("transmission", C.c_int32),
-                ("z_mode", C.c_int32), ("speckle", C.c_int32)]
+                ("z_mode", C.c_int32), ("speckle", C.c_int32), ("speckle_anchor", C.c_int32),
+                ("speckle_levels", C.c_int32), ("speckle_cell_mm", C.c_float)]
 
 
 class OrFrameOut(C.Structure):
     _fields_ = [("frame", C.c_void_p), ("envelope", C.c_void_p), ("logimg", C.c_void_p),
                 ("S", C.c_void_p), ("E", C.c_void_p), ("cos_theta", C.c_void_p),
-                ("hu", C.c_void_p), ("nn_index", C.c_void_p), ("label", C.c_void_p)]
+                ("hu", C.c_void_p), ("nn_index", C.c_void_p), ("label", C.c_void_p), ("n1", C.c_void_p)]
 
 
 def lib():
@@ -105,6 +106,8 @@ def lib():
                                                C.c_int, C.c_void_p]
             L.oracle_sample_slice.argtypes = [C.POINTER(OrVolume), C.POINTER(OrProbe), C.c_void_p, C.c_void_p]
             L.oracle_sample_slice.restype = C.c_int
+            L.oracle_anchored_noise.argtypes = [C.c_void_p, C.c_int32, C.c_float, C.c_uint32, C.c_uint64,
+                                                C.c_void_p]
             _lib = L
     return _lib
 
@@ -129,17 +132,18 @@ def or_table(table):
 
 
 def or_options(o) -> OrOptions:
-    return OrOptions(o.refl_power, o.transmission, o.z_mode, o.speckle)
+    return OrOptions(o.refl_power, o.transmission, o.z_mode, o.speckle, getattr(o, "speckle_anchor", 0),
+                     getattr(o, "speckle_levels", 1), getattr(o, "speckle_cell_mm", 0.25))
 
 
 class _Vol:
     """Keeps the numpy arrays alive next to the ctypes descriptor."""
 
-    def __init__(self, labels, hu, voxel_mm):
+    def __init__(self, labels, hu, voxel_mm, vol_id=0):
         self.labels = np.ascontiguousarray(labels, np.uint8)
         self.hu = np.ascontiguousarray(hu, np.int16)
         nz, ny, nx = self.labels.shape
-        self.desc = OrVolume(self.labels.ctypes.data, self.hu.ctypes.data, nx, ny, nz, voxel_mm)
+        self.desc = OrVolume(self.labels.ctypes.data, self.hu.ctypes.data, nx, ny, nz, voxel_mm, vol_id)
 
 
 # --------------------------------------------------------------------- API
@@ -191,18 +195,20 @@ def scan_convert(probe, logimg):
     return out
 
 
-def render_frame(labels, hu, voxel_mm, table, probe, options, pose, env=0, seed=0, step=0):
-    """Render one frame; returns a dict of every export (numpy arrays)."""
-    vol = _Vol(labels, hu, voxel_mm)
+def render_frame(labels, hu, voxel_mm, table, probe, options, pose, env=0, seed=0, step=0, vol_id=0):
+    """Render one frame; returns a dict of every export (numpy arrays; "n1"
+    holds the anchored scatter map N1 per sample, NaN in the beam-keyed mode)."""
+    vol = _Vol(labels, hu, voxel_mm, vol_id)
     NL, NS = probe.n_lines, probe.n_samples
     res = {
         "frame": np.zeros((probe.out_h, probe.out_w)),
         "envelope": np.zeros((NL, NS)), "logimg": np.zeros((NL, NS)), "S": np.zeros((NL, NS)),
         "E": np.zeros((NL, NS)), "cos_theta": np.zeros((NL, NS)), "hu": np.zeros((NL, NS)),
         "nn_index": np.zeros((NL, NS), np.int32), "label": np.zeros((NL, NS), np.uint8),
+        "n1": np.full((NL, NS), np.nan),
     }
     o = OrFrameOut(*[res[k].ctypes.data for k in
-                     ("frame", "envelope", "logimg", "S", "E", "cos_theta", "hu", "nn_index", "label")])
+                     ("frame", "envelope", "logimg", "S", "E", "cos_theta", "hu", "nn_index", "label", "n1")])
     tab = or_table(table)
     pr = or_probe(probe)
     op = or_options(options)
@@ -217,7 +223,7 @@ def render_frame(labels, hu, voxel_mm, table, probe, options, pose, env=0, seed=
 def render_batch(volumes, table, probes, options, envs, poses, seed, step, n_threads=1):
     """Render a batch.  volumes: list of (labels, hu, voxel_mm); envs int32
     [B][2]; poses float32 [B][3][4].  Returns (frames float64 flat, offsets)."""
-    vols = [_Vol(l, h, v) for (l, h, v) in volumes]
+    vols = [_Vol(l, h, v, i) for i, (l, h, v) in enumerate(volumes)]
     vd = (OrVolume * len(vols))(*[v.desc for v in vols])
     pd = (OrProbe * len(probes))(*[or_probe(p) for p in probes])
     envs = np.ascontiguousarray(envs, np.int32)
@@ -247,6 +253,15 @@ def touched_voxels(volumes, probes, envs, poses):
     P = np.ascontiguousarray(poses, np.float32).reshape(B, 12)
     tot = lib().oracle_touched_voxels(vd, len(vols), pd, _ptr(envs), B, _ptr(P), _ptr(per))
     return int(tot), per
+
+
+def anchored_noise(pos, levels, cell_mm, vol_id, seed):
+    """(N0, N1) of the volume-anchored multi-scale scatter maps at a
+    volume-frame position (mm, float32)"""
+    p = np.ascontiguousarray(pos, np.float32)
+    out = np.zeros(2)
+    lib().oracle_anchored_noise(_ptr(p), levels, cell_mm, vol_id, seed, _ptr(out))
+    return float(out[0]), float(out[1])
 
 
 def sample_slice(labels, hu, voxel_mm, probe, pose):

@@ -37,6 +37,7 @@ typedef struct {
   const int16_t* hu;     /* same grid */
   int32_t nx, ny, nz;
   float voxel_mm;
+  int32_t id;            /* volume index: keys the volume-anchored scatter maps */
 } or_volume;
 
 typedef struct {
@@ -53,6 +54,9 @@ typedef struct {
 
 typedef struct {
   int32_t refl_power, transmission, z_mode, speckle;
+  int32_t speckle_anchor;   /* 0: maps keyed by (env, line, sample, step); 1: fixed maps over the volume */
+  int32_t speckle_levels;   /* anchored maps: number of scales (1..3) */
+  float speckle_cell_mm;    /* anchored maps: cell edge of the finest scale */
 } or_options;
 
 /* optional per-frame exports; any pointer may be NULL ([NL][NS] unless noted) */
@@ -66,6 +70,7 @@ typedef struct {
   double* hu;          /* interpolated HU */
   int32_t* nn_index;   /* nearest voxel linear index, -1 outside */
   uint8_t* label;      /* nearest label */
+  double* n1;          /* anchored scatter maps: the N1 value of each sample */
 } or_frame_out;
 
 /* ------------------------------------------------- Philox4x32-10 (SC'11) */
@@ -169,8 +174,7 @@ static void or_derive(const or_probe* p, or_derived* d) {
  *   curvilinear: rho = r0 + s * dr; x = rho * sin(theta_l); z = rho * cos(theta_l) - r0
  *   p_c = (R_c0 * x + R_c2 * z) + t_c;  u_c = p_c * (1/h)
  * Voxel (i, j, k) is centred at (i, j, k) * h. */
-static void or_sample_voxel_coords(const or_probe* p, const float* M, float inv_h, int l, int s,
-                                   float u[3]) {
+static void or_sample_position(const or_probe* p, const float* M, int l, int s, float pc[3]) {
   float x, z;
   float s_f = (float)s;
   float dr = (float)((double)p->depth_mm / (double)p->n_samples);
@@ -191,9 +195,61 @@ static void or_sample_voxel_coords(const or_probe* p, const float* M, float inv_
     float a = M[c * 4 + 0] * x;
     float b = M[c * 4 + 2] * z;
     float q = a + b;
-    float pc = q + M[c * 4 + 3];
-    u[c] = pc * inv_h;
+    pc[c] = q + M[c * 4 + 3];
   }
+}
+
+static void or_sample_voxel_coords(const or_probe* p, const float* M, float inv_h, int l, int s,
+                                   float u[3]) {
+  float pc[3];
+  or_sample_position(p, M, l, s, pc);
+  for (int c = 0; c < 3; ++c) u[c] = pc[c] * inv_h;
+}
+
+/* Volume-anchored, multi-scale scatter maps (App. B.2: N0 and N1 are sampled
+ * over 3-D space once and stay fixed; multi-scale versions of both are
+ * added).  READING: scale k < L is a lattice of cubic cells of edge
+ * c 2^k anchored at the volume origin (cell centres at n c 2^k); a sample
+ * takes the cell nearest to its volume-frame position, through the same
+ * FP32 path as the nearest voxel with 1/(c 2^k) in place of 1/h.  The cell's
+ * Philox-4x32-10 words, counter (n_x, n_y, n_z, k << 16 | volume), key =
+ * (seed_lo, seed_hi) (no step: the maps are fixed), give two standard
+ * normals by Box-Muller (cosine branch): Z0 from words 0, 1 and Z1 from
+ * words 2, 3.  N0 = sum_k a_k Z0_k, N1 = sum_k a_k Z1_k, a_k proportional
+ * to 2^(-k/2) with sum a_k^2 = 1 (unit variance; coarser scales weigh
+ * less).  T = N0 sigma0 + mu0 where N1 <= mu1, else 0. */
+static void or_anchored_noise(const float pc[3], const or_options* o, uint32_t vol_id, uint64_t seed,
+                              double* n0, double* n1) {
+  const int L = o->speckle_levels;
+  double norm = 0.0;
+  for (int k = 0; k < L; ++k) norm += pow(2.0, -k);
+  norm = sqrt(norm);
+  const float inv_c0 = (float)(1.0 / (double)o->speckle_cell_mm);
+  *n0 = 0.0;
+  *n1 = 0.0;
+  for (int k = 0; k < L; ++k) {
+    const float inv_c = inv_c0 * (float)ldexp(1.0, -k); /* exact: a power of two */
+    uint32_t ctr[4], key[2], w[4];
+    for (int c = 0; c < 3; ++c) {
+      float u = pc[c] * inv_c;
+      float f = floorf(u + 0.5f);
+      ctr[c] = (uint32_t)(int32_t)f;
+    }
+    ctr[3] = ((uint32_t)k << 16) | (vol_id & 0xFFFFu);
+    key[0] = (uint32_t)seed;
+    key[1] = (uint32_t)(seed >> 32);
+    oracle_philox4x32_10(ctr, key, w);
+    const double a = pow(2.0, -0.5 * k) / norm;
+    *n0 += a * sqrt(-2.0 * log(or_uniform(w[0]))) * cos(2.0 * M_PI * or_uniform(w[1]));
+    *n1 += a * sqrt(-2.0 * log(or_uniform(w[2]))) * cos(2.0 * M_PI * or_uniform(w[3]));
+  }
+}
+
+/* exported for the tests: the anchored maps at a volume-frame position */
+void oracle_anchored_noise(const float pos[3], int32_t levels, float cell_mm, uint32_t vol_id, uint64_t seed,
+                           double out[2]) {
+  or_options o = {1, 1, 0, 1, 1, levels, cell_mm};
+  or_anchored_noise(pos, &o, vol_id, seed, &out[0], &out[1]);
 }
 
 /* nearest voxel: i = floor(u + 0.5) per axis, outside -> -1 */
@@ -399,7 +455,14 @@ int oracle_render_frame(const or_volume* vol, const or_tissue* table, int n_labe
       }
       /* scatter pattern T and backscatter impulse E * T */
       double T;
-      if (opt->speckle) {
+      if (opt->speckle && opt->speckle_anchor) {
+        float pc[3];
+        double n0, n1;
+        or_sample_position(p, pose, l, s, pc);
+        or_anchored_noise(pc, opt, (uint32_t)vol->id, seed, &n0, &n1);
+        T = n1 <= (double)ti->mu1 ? n0 * (double)ti->sigma0 + (double)ti->mu0 : 0.0;
+        if (out && out->n1) out->n1[(int64_t)l * NS + s] = n1;
+      } else if (opt->speckle) {
         uint32_t w[4];
         oracle_speckle_words(seed, step, env, (uint32_t)l, (uint32_t)s, w);
         double n0 = oracle_n0(w, (uint32_t)s);

@@ -147,7 +147,14 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_r
       auto labf = [&](int line, int s) -> unsigned { return lab_row[line][s]; };
       auto own = [&](int s) -> unsigned { return lrow[s]; };
       auto zf = [&](int s) -> float { return row[s]; };
-      scanline_model(p, P, tis, cx.pair, b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; });
+      const float2 ln = P.lines[l];
+      auto posf = [&](int s) -> float3 {
+        float x, z;
+        beam_point(P, ln, s, x, z);
+        return sample_position(cx.M, x, z);
+      };
+      scanline_model(p, P, tis, cx.pair, b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; }, posf,
+                     cx.it.vol);
       __syncwarp();
       axial_psf_padded(sbuf + lr * RS, NS, wax, KA, lane);
     }

@@ -43,7 +43,13 @@ __global__ void plain_lines(RenderParams p, EnvItem it, const uint8_t* lab, floa
   auto own = [&](int s) -> unsigned { return lab[l * NS + s]; };
   auto zf = [&](int s) -> float { return sample_impedance(p.z_mode, P, V, M, ln, s, P.tissue, lab[l * NS + s]); };
   float* row = S + (size_t)l * NS;
-  scanline_model(p, P, P.tissue, pair, it.b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; });
+  auto posf = [&](int s) -> float3 {
+    float x, z;
+    beam_point(P, ln, s, x, z);
+    return sample_position(M, x, z);
+  };
+  scanline_model(p, P, P.tissue, pair, it.b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; }, posf,
+                 it.vol);
 }
 
 __global__ void plain_psf_axial(RenderParams p, EnvItem it, const float* S, float* A) {

@@ -96,7 +96,7 @@ constexpr int lines_min_blocks() {
   return G == 8 ? 6 : (G == 16 ? 3 : 1);
 }
 
-template <int G>
+template <int G, bool ANCHORED>
 __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(RenderParams p, SplitArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SplitCtx cx;
@@ -153,7 +153,14 @@ __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(Ren
     auto labf = [&](int line, int s) -> unsigned { return lbuf[(line - L0) * NS + s]; };
     auto own = [&](int s) -> unsigned { return lrow[s]; };
     auto zf = [&](int s) -> float { return row[s]; };
-    scanline_model(p, P, tis, cx.pair, cx.it.b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; });
+    const float2 ln = P.lines[l];
+    auto posf = [&](int s) -> float3 {
+      float x, z;
+      beam_point(P, ln, s, x, z);
+      return sample_position(cx.M, x, z);
+    };
+    scanline_model<ANCHORED>(p, P, tis, cx.pair, cx.it.b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; },
+                             posf, cx.it.vol);
     __syncwarp();
     axial_psf_row(prow, NS, wax, KA, lane);
     float* dst = a.beam + cx.it.beam_off + (long long)l * NS;
@@ -341,8 +348,11 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
 // pass 0: split_lines<G>, pass 1: split_image<G>
 template <int G>
 static cudaError_t prepare_g(int pass, size_t smem) {
-  return pass == 0 ? cudaFuncSetAttribute(split_lines<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                   : cudaFuncSetAttribute(split_image<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (pass == 1) return cudaFuncSetAttribute(split_image<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(split_lines<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e == cudaSuccess
+             ? cudaFuncSetAttribute(split_lines<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+             : e;
 }
 
 static cudaError_t prepare_pass(int pass, int G, size_t smem) {
@@ -362,8 +372,10 @@ cudaError_t split_prepare(const SplitShape& sh) {
 template <int G>
 static void launch_g(const RenderParams& p, const SplitShape& sh, const SplitArgs& a, int max_items, int pass,
                      cudaStream_t st) {
-  if (pass == 0)
-    split_lines<G><<<(unsigned)(max_items * a.gpi_lines), G * 32, sh.smem_lines, st>>>(p, a);
+  if (pass == 0 && p.speckle_anchor)
+    split_lines<G, true><<<(unsigned)(max_items * a.gpi_lines), G * 32, sh.smem_lines, st>>>(p, a);
+  else if (pass == 0)
+    split_lines<G, false><<<(unsigned)(max_items * a.gpi_lines), G * 32, sh.smem_lines, st>>>(p, a);
   else
     split_image<G><<<(unsigned)(max_items * a.gpi_image), G * 32, sh.smem_image, st>>>(p, a);
 }

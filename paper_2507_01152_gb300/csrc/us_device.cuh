@@ -8,6 +8,7 @@ namespace ussim {
 
 constexpr int kMaxHalfTaps = 48;   // PSF half-width limit (taps <= 97)
 constexpr int kThetaDMax = 8;      // lateral reach of the incidence stencil, lines
+constexpr int kMaxSpeckleLevels = 3;   // scales of the volume-anchored scatter maps
 
 // error-word bits
 constexpr unsigned kErrNonFinitePose = 1u;
@@ -26,6 +27,7 @@ struct DevVolume {
 struct DevTissue {
   float att, mu0, sigma0, z;
   unsigned long long t1;
+  float mu1;   // density threshold on N1 (anchored maps compare N1 itself)
 };
 
 struct DevProbe {
@@ -71,6 +73,10 @@ struct RenderParams {
   const float* poses;        // [B][12]
   uint2 key;                 // Philox key for this (seed, step)
   int refl_power, transmission, z_mode, speckle;
+  int speckle_anchor, speckle_levels;          // volume-anchored scatter maps
+  float inv_cell[kMaxSpeckleLevels];           // 1 / (cell edge c 2^k), FP32
+  float amp[kMaxSpeckleLevels];                // a_k, sum a_k^2 = 1
+  uint2 key_fixed;                             // Philox key of the anchored maps (seed only)
   float* frames;
   float* envelope;           // debug exports, may be null
   float* logimg;
@@ -123,12 +129,18 @@ struct Pose {
   float m[12];
 };
 
+// volume-frame position (mm) of a probe-frame point (x, 0, z)
+__device__ __forceinline__ float3 sample_position(const Pose& M, float x, float z) {
+  float3 p;
+  p.x = __fadd_rn(__fadd_rn(__fmul_rn(M.m[0], x), __fmul_rn(M.m[2], z)), M.m[3]);
+  p.y = __fadd_rn(__fadd_rn(__fmul_rn(M.m[4], x), __fmul_rn(M.m[6], z)), M.m[7]);
+  p.z = __fadd_rn(__fadd_rn(__fmul_rn(M.m[8], x), __fmul_rn(M.m[10], z)), M.m[11]);
+  return p;
+}
+
 __device__ __forceinline__ float3 to_voxel(const Pose& M, float inv_h, float x, float z) {
-  float3 u;
-  u.x = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(M.m[0], x), __fmul_rn(M.m[2], z)), M.m[3]), inv_h);
-  u.y = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(M.m[4], x), __fmul_rn(M.m[6], z)), M.m[7]), inv_h);
-  u.z = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(M.m[8], x), __fmul_rn(M.m[10], z)), M.m[11]), inv_h);
-  return u;
+  const float3 p = sample_position(M, x, z);
+  return make_float3(__fmul_rn(p.x, inv_h), __fmul_rn(p.y, inv_h), __fmul_rn(p.z, inv_h));
 }
 
 // nearest voxel: floor(u + 1/2) per axis, -1 outside the grid (NaN -> outside)
@@ -209,6 +221,30 @@ __device__ __forceinline__ float incidence_cos(LabFn lab, int l, int s, int NL, 
 
 __device__ __forceinline__ float lateral_spacing(const DevProbe& P, int s) {
   return P.kind == 0 ? P.pitch : fmaf((float)s, P.dr, P.r0) * P.dtheta;
+}
+
+// Volume-anchored multi-scale scatter maps at volume-frame position `pos`
+// of volume `vol`: (N0, N1).  Scale k: the nearest cell of edge c 2^k
+// (cell index floor(pos / (c 2^k) + 1/2), FP32 as for voxels), whose
+// Philox words (counter = cell, k << 16 | vol; key = seed) give two
+// standard normals by Box-Muller; N = sum_k a_k N_k.
+__device__ __forceinline__ float2 anchored_maps(const RenderParams& p, float3 pos, unsigned vol) {
+  float n0 = 0.f, n1 = 0.f;
+  for (int k = 0; k < p.speckle_levels; ++k) {
+    const float ic = p.inv_cell[k];
+    const int cx = (int)floorf(__fadd_rn(__fmul_rn(pos.x, ic), 0.5f));
+    const int cy = (int)floorf(__fadd_rn(__fmul_rn(pos.y, ic), 0.5f));
+    const int cz = (int)floorf(__fadd_rn(__fmul_rn(pos.z, ic), 0.5f));
+    const uint4 w = philox4x32_10(make_uint4((unsigned)cx, (unsigned)cy, (unsigned)cz, ((unsigned)k << 16) | (vol & 0xFFFFu)),
+                                  p.key_fixed);
+    float s0, c0, s1, c1;
+    // angles 2 pi u shifted into [-pi, pi): cos(t) = -cos(t - pi)
+    __sincosf(fmaf(6.28318530717958648f, u01(w.y), -3.14159265358979324f), &s0, &c0);
+    __sincosf(fmaf(6.28318530717958648f, u01(w.w), -3.14159265358979324f), &s1, &c1);
+    n0 = fmaf(p.amp[k], -sqrtf(-2.f * __logf(u01(w.x))) * c0, n0);
+    n1 = fmaf(p.amp[k], -sqrtf(-2.f * __logf(u01(w.z))) * c1, n1);
+  }
+  return make_float2(n0, n1);
 }
 
 // log compression to [0, 1] over the probe's dynamic range:

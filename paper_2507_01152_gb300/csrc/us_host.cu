@@ -116,6 +116,7 @@ us_status build_probe_tables(us_sim* s, ProbeHost& ph) {
     tis[i].sigma0 = t.sigma0;
     tis[i].z = t.z_mrayl;
     tis[i].t1 = n1_threshold((double)t.mu1);
+    tis[i].mu1 = t.mu1;
   }
   // scan-conversion map (curvilinear): fractional (line, sample) of each
   // output pixel centre over the fan's bounding box, -1 outside the fan;
@@ -260,6 +261,21 @@ RenderParams base_params(const us_sim* s, const float* poses, uint64_t seed, uin
   p.transmission = s->opt.transmission;
   p.z_mode = s->opt.z_mode;
   p.speckle = s->opt.speckle;
+  p.speckle_anchor = s->opt.speckle && s->opt.speckle_anchor;
+  if (p.speckle_anchor) {
+    // cell scales c 2^k as FP32 reciprocals (exact powers of two apart) and
+    // unit-variance weights a_k ~ 2^(-k/2), computed in FP64
+    const int L = s->opt.speckle_levels;
+    double norm = 0.0;
+    for (int k = 0; k < L; ++k) norm += std::ldexp(1.0, -k);
+    const float inv_c0 = (float)(1.0 / (double)s->opt.speckle_cell_mm);
+    p.speckle_levels = L;
+    for (int k = 0; k < L; ++k) {
+      p.inv_cell[k] = inv_c0 * (float)std::ldexp(1.0, -k);
+      p.amp[k] = (float)(std::pow(2.0, -0.5 * k) / std::sqrt(norm));
+    }
+  }
+  p.key_fixed = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   p.n_labels = s->n_labels;
   p.frames = frames;
   p.err = s->d_err;
@@ -520,9 +536,11 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
     return US_ERR_INVALID_ARG;
   us_sim* s = new (std::nothrow) us_sim();
   if (!s) return US_ERR_OOM;
-  s->opt = opt ? *opt : us_options{1, 1, 0, 1};
+  s->opt = opt ? *opt : us_options{1, 1, 0, 1, 0, 1, 0.25f};
   if (!(s->opt.refl_power == 1 || s->opt.refl_power == 2) || (s->opt.transmission & ~1) || (s->opt.z_mode & ~1) ||
-      (s->opt.speckle & ~1)) {
+      (s->opt.speckle & ~1) || (s->opt.speckle_anchor & ~1) ||
+      (s->opt.speckle_anchor && (s->opt.speckle_levels < 1 || s->opt.speckle_levels > kMaxSpeckleLevels ||
+                                 !(s->opt.speckle_cell_mm > 0.f) || !std::isfinite(s->opt.speckle_cell_mm)))) {
     delete s;
     return US_ERR_INVALID_ARG;
   }

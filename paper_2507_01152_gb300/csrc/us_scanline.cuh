@@ -27,13 +27,16 @@ __device__ __forceinline__ float warp_inclusive_scan(float v, int lane) {
 //   own(s)        -> nearest label of sample s on line l
 //   z_at(s)       -> impedance at sample s < NS of line l
 //   store(s, v)   -> receives S at sample s
+//   pos(s)        -> volume-frame position of sample s (anchored scatter maps)
 // A lane reads z_at only at its own samples (one chunk ahead) and gets the
 // next lane's value by shuffle, so store() may overwrite the storage z_at
-// reads from.
-template <class LabFn, class OwnFn, class ZFn, class StoreFn>
+// reads from.  `vol` is the environment's volume index.
+// ANCHORED = false compiles the volume-anchored branch out (kernels that are
+// instantiated per scatter-map kind).
+template <bool ANCHORED = true, class LabFn, class OwnFn, class ZFn, class StoreFn, class PosFn>
 __device__ __forceinline__ void scanline_model(const RenderParams& p, const DevProbe& P, const DevTissue* T,
                                                const DevPair& pair, int b, int l, int lane, LabFn lab,
-                                               OwnFn own, ZFn z_at_in, StoreFn store) {
+                                               OwnFn own, ZFn z_at_in, StoreFn store, PosFn pos, int vol) {
   const int NS = P.ns, NL = P.nl;
   auto z_at = [&](int s) -> float { return s < NS ? z_at_in(s) : 1.f; };
 
@@ -88,7 +91,11 @@ __device__ __forceinline__ void scanline_model(const RenderParams& p, const DevP
     }
 
     float Ta, Tb;
-    if (p.speckle) {
+    if (ANCHORED && p.speckle_anchor) {
+      const float2 na = anchored_maps(p, pos(sa), (unsigned)vol), nb = anchored_maps(p, pos(sb), (unsigned)vol);
+      Ta = na.y <= ta.mu1 ? fmaf(na.x, ta.sigma0, ta.mu0) : 0.f;
+      Tb = nb.y <= tb.mu1 ? fmaf(nb.x, tb.sigma0, tb.mu0) : 0.f;
+    } else if (p.speckle) {
       const uint4 w = philox4x32_10(make_uint4((unsigned)sa >> 1, (unsigned)l, (unsigned)b, 0u), p.key);
       const float rad = sqrtf(-2.f * __logf(u01(w.x)));
       // angle 2 pi u shifted into [-pi, pi), where the hardware sine and

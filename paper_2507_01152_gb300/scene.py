@@ -105,11 +105,17 @@ class Options:
     transmission loss ln(1 - r^2) to the energy, 0 is attenuation only
     (paper).  z_mode: 0 = impedance from HU, 1 = impedance from the tissue
     table.  speckle: 1 = random scatter pattern, 0 = scatter fixed at mu0.
+    speckle_anchor: 0 = scatter maps keyed by (env, line, sample, step);
+    1 = fixed maps over the volume (they move with the tissue), with
+    speckle_levels scales (1-3) of cells of edge speckle_cell_mm * 2^k.
     """
     refl_power: int = 1
     transmission: int = 1
     z_mode: int = 0
     speckle: int = 1
+    speckle_anchor: int = 0
+    speckle_levels: int = 1
+    speckle_cell_mm: float = 0.25
 
 
 # --------------------------------------------------------------------------

@@ -47,7 +47,8 @@ class us_probe(C.Structure):
 
 class us_options(C.Structure):
     _fields_ = [("refl_power", C.c_int32), ("transmission", C.c_int32), ("z_mode", C.c_int32),
-                ("speckle", C.c_int32)]
+                ("speckle", C.c_int32), ("speckle_anchor", C.c_int32), ("speckle_levels", C.c_int32),
+                ("speckle_cell_mm", C.c_float)]
 
 
 class us_env(C.Structure):
@@ -206,7 +207,9 @@ class Sim:
         prs = (us_probe * len(probes))(*[make_probe(p) for p in probes])
         opt = None
         if options is not None:
-            opt = us_options(options.refl_power, options.transmission, options.z_mode, options.speckle)
+            opt = us_options(options.refl_power, options.transmission, options.z_mode, options.speckle,
+                             getattr(options, "speckle_anchor", 0), getattr(options, "speckle_levels", 1),
+                             getattr(options, "speckle_cell_mm", 0.25))
         h = C.c_void_p()
         st = L.us_sim_create(vols, len(volumes), tab, len(table), prs, len(probes),
                              C.byref(opt) if opt is not None else None, C.byref(h))
