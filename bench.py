@@ -155,6 +155,8 @@ def make_workload(name, copies=1):
         return scene.workload_c1()
     if name == "paper":
         return scene.workload_paper_replica(100 * copies)
+    if name == "surgery3d":
+        return scene.workload_surgery3d(128 * copies)
     if name == "c3":
         wl = scene.workload_c3(512 * copies, steps=1)
         wl.poses = wl.poses[0]
@@ -372,6 +374,15 @@ def run_ours(args):
         import dataclasses
         wl = dataclasses.replace(wl, options=dataclasses.replace(wl.options, speckle_anchor=1, speckle_levels=2,
                                                                  speckle_cell_mm=0.25))
+    wl3 = None
+    if args.workload == "surgery3d":
+        # the timed render sweeps each probe over its elevation slices on the
+        # device (us_sim_render_3d); the other measurements use the expanded
+        # batch of 2-D slices (same kernels, host-swept poses)
+        import dataclasses
+        E, pitch = scene.SURGERY3D_SLICES, scene.SURGERY3D_PITCH_MM
+        wl3 = wl
+        wl = dataclasses.replace(wl, envs=np.repeat(wl.envs, E, axis=0), poses=scene.sweep_elevation(wl.poses, E, pitch))
     B = len(wl.envs)
     vols = [(torch.from_numpy(lab).cuda(), torch.from_numpy(hu).cuda(), spec.voxel_mm) for (spec, lab, hu) in wl.volumes]
     sim = Sim(vols, scene.tissue_table(), wl.probes, wl.options)
@@ -408,6 +419,10 @@ def run_ours(args):
     sim.set_tuning(tuning["cluster_size"], tuning["warps_per_cta"], 1)
     tuning = sim.get_tuning()
     render = lambda k: sim.render(None, poses, seed, k, frames, stream=stream, envs_c=envs_c)
+    if wl3 is not None:
+        poses3 = torch.from_numpy(np.ascontiguousarray(wl3.poses, np.float32)).cuda()
+        render = lambda k: sim.render_3d(wl3.envs, poses3, scene.SURGERY3D_SLICES, scene.SURGERY3D_PITCH_MM, seed, k,
+                                         frames, stream=stream)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -492,6 +507,9 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl.name + ("_anchored_speckle" if args.speckle == "anchored" else ""),
                            "envs_per_gpu": B, "l2": "flushed between timed steps (256 MB write)",
+                           **({"volumetric_images_per_s": value / scene.SURGERY3D_SLICES,
+                               "frame": "one 50 x 37 elevation slice (5 per volumetric image)"}
+                              if wl3 is not None else {}),
                            "path": ("two-pass batched kernels" if tuning["cluster_size"] == 1
                                     else "persistent cluster kernel") + ", CUDA graph replay, autotuned",
                            "tuning": tuning,
@@ -511,7 +529,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "paper", "mixed"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "paper", "surgery3d", "mixed"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -262,6 +262,20 @@ US_API us_status us_sim_set_tuning(us_sim* sim, const us_tuning* t);
 US_API us_status us_sim_autotune(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
                           float* frames, const char* cache_path, void* stream);
 
+/* Volumetric frames of a 3-D probe (Sec. 4, Task 3: H x W x E images; the
+ * surgery task's probe is 50 x 37 x 5 at 2 x 2 x 10 mm, App. C): every
+ * environment's probe plane is swept over n_elev (1..64) parallel planes at
+ * elevation offsets y_e = (e - (n_elev - 1) / 2) * elev_pitch_mm along the
+ * pose's own y axis (t' = t + R[:, 1] y_e, in FP32 on the device), and each
+ * plane is rendered as a 2-D frame of the expanded batch, entry b * n_elev + e
+ * (its own speckle: environment index b * n_elev + e).  frames: device, laid
+ * out as us_sim_frame_layout of the expanded env list (env b repeated
+ * n_elev times).  poses: device [B][3][4].  Errors as us_sim_render, plus
+ * US_ERR_INVALID_ARG for n_elev or the pitch out of range. */
+US_API us_status us_sim_render_3d(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                                  int32_t n_elev, float elev_pitch_mm, uint64_t seed, uint64_t step,
+                                  float* frames, void* stream);
+
 /* The tuned batched render (as us_sim_render, without graph replay) with
  * CUDA events recorded on `stream` around each of its kernels; waits for
  * the render and writes each kernel's duration in ms to kernel_ms[0..n)

@@ -362,6 +362,7 @@ void free_sim(us_sim* s) {
   cudaFree(s->d_work);
   cudaFree(s->d_host_poses);
   cudaFree(s->d_host_frames);
+  cudaFree(s->d_poses3d);
   delete s;
 }
 
@@ -763,6 +764,32 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
                         cudaSuccess)
     return cuda_fail(s, e, "gated count");
   return US_OK;
+}
+
+us_status us_sim_render_3d(us_sim* s, const us_env* envs, int32_t B, const float* poses, int32_t n_elev,
+                           float elev_pitch_mm, uint64_t seed, uint64_t step, float* frames, void* stream) {
+  us_status r = check_render_args(s, envs, B, poses, frames);
+  if (r != US_OK || B == 0) return r;
+  if (n_elev < 1 || n_elev > 64 || !std::isfinite(elev_pitch_mm) || elev_pitch_mm < 0.f)
+    return fail(s, US_ERR_INVALID_ARG, "n_elev must be 1..64 and the elevation pitch finite and >= 0");
+  if ((long long)B * n_elev > (1ll << 30)) return fail(s, US_ERR_INVALID_ARG, "batch too large");
+  const int BE = B * n_elev;
+  std::vector<us_env> ex((size_t)BE);
+  for (int b = 0; b < B; ++b)
+    for (int e = 0; e < n_elev; ++e) ex[(size_t)b * n_elev + e] = envs[b];
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  const size_t bytes = sizeof(float) * 12 * (size_t)BE;
+  if (bytes > s->poses3d_cap) {
+    cudaFree(s->d_poses3d);
+    s->d_poses3d = nullptr;
+    s->poses3d_cap = 0;
+    if ((e = cudaMalloc(&s->d_poses3d, bytes)) != cudaSuccess) return cuda_fail(s, e, "swept poses");
+    s->poses3d_cap = bytes;
+  }
+  if ((e = launch_expand_elevation(poses, B, n_elev, elev_pitch_mm, s->d_poses3d, st)) != cudaSuccess)
+    return cuda_fail(s, e, "elevation sweep");
+  return do_render(s, ex.data(), BE, s->d_poses3d, seed, step, frames, nullptr, nullptr, nullptr, nullptr, 0, st);
 }
 
 us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint64_t seed,

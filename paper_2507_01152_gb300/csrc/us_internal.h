@@ -101,6 +101,9 @@ cudaError_t launch_gate_compact(const EnvItem* items, int B, const float* score,
 cudaError_t launch_slice_input(const RenderParams& p, const EnvItem* items_batch, int B, int H, int W, void* out,
                                cudaStream_t st);
 
+// 3-D probe: B poses -> B * E poses swept along each pose's elevation axis
+cudaError_t launch_expand_elevation(const float* poses, int B, int E, float pitch, float* out, cudaStream_t st);
+
 // label check at creation: max label of a volume
 cudaError_t max_label(const uint8_t* labels, long long n, unsigned* d_out, cudaStream_t st);
 
@@ -146,6 +149,10 @@ struct us_sim {
   us_tuning tuning{1, 16, 1};
 
   std::map<std::string, us_plan> plans;
+
+  // 3-D probe: swept poses
+  float* d_poses3d = nullptr;
+  size_t poses3d_cap = 0;
 
   // staging for us_sim_render_host
   float* d_host_poses = nullptr;

@@ -417,6 +417,37 @@ def workload_paper_replica(B=100):
                     dorsal_poses(spec, B, 2001), seed=0x5EED0004)
 
 
+def surgery3d_probe() -> Probe:
+    """The surgery task's 3-D probe (App. C): 50 x 37 pixels at 2 x 2 mm per
+    elevation slice (linear, 37 lines at 2 mm, 50 samples over 100 mm); the
+    5 slices 10 mm apart come from the elevation sweep of us_sim_render_3d."""
+    return linear_probe(37, 50, 100.0, 2.0)
+
+
+SURGERY3D_SLICES, SURGERY3D_PITCH_MM = 5, 10.0
+
+
+def workload_surgery3d(B=128):
+    """B environments with the 3-D probe above the 256^3 spine volume
+    (volumetric images 50 x 37 x 5; App. C trains with 128 parallel envs)."""
+    spec = c2_spec()
+    lab, hu = make_volume(spec)
+    return Workload(f"surgery3d_50x37x5_{B}env", [(spec, lab, hu)], [surgery3d_probe()],
+                    np.zeros((B, 2), np.int32), dorsal_poses(spec, B, 2003, tilt_deg=5.0), seed=0x5EED0006)
+
+
+def sweep_elevation(poses, n_elev, pitch_mm) -> np.ndarray:
+    """Host restatement of the 3-D probe's elevation sweep, in float32 with
+    one rounding per product and sum: pose b, slice e -> entry b * n_elev + e,
+    t' = t + R[:, 1] * ((e - (n_elev - 1) / 2) * pitch)."""
+    P = np.asarray(poses, np.float32).reshape(-1, 3, 4)
+    out = np.repeat(P, n_elev, axis=0).copy()
+    for e in range(n_elev):
+        y = np.float32(np.float32(e - 0.5 * (n_elev - 1)) * np.float32(pitch_mm))
+        out[e::n_elev, :, 3] = (P[:, :, 3] + (P[:, :, 1] * y).astype(np.float32)).astype(np.float32)
+    return out
+
+
 # --------------------------------------------------------------------------
 # surrogate inputs
 # --------------------------------------------------------------------------

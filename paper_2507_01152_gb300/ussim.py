@@ -82,6 +82,7 @@ SIGNATURES = {
     "us_sim_render_host": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
     "us_sim_check": (C.c_int, [_P, _P]),
     "us_sim_render_timed": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, _P, _P]),
+    "us_sim_render_3d": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, C.c_float, C.c_uint64, C.c_uint64, _P, _P]),
     "us_sim_sample_slices": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
     "us_sim_render_gated": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, C.c_float, _P, _P]),
     "us_sim_get_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
@@ -282,6 +283,14 @@ class Sim:
         self._check(self._lib.us_sim_render_host(self.h, e, B, _ptr(poses_host), seed, step, _ptr(frames_host),
                                                  _stream_handle(stream)))
 
+    def render_3d(self, envs, poses, n_elev, elev_pitch_mm, seed, step, frames, stream=None):
+        """Volumetric frames of a 3-D probe: each env's plane swept over n_elev
+        elevation offsets; frames as frame_layout(np.repeat(envs, n_elev, 0))."""
+        B = poses.shape[0]
+        self._check(self._lib.us_sim_render_3d(self.h, make_envs(envs), B, _ptr(poses), n_elev,
+                                               float(elev_pitch_mm), seed, step, _ptr(frames),
+                                               _stream_handle(stream)))
+
     def render_timed(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
         """The tuned render with per-kernel CUDA-event times (ms): a list of
         one (cluster kernel) or two (two-pass: pass A, pass B) durations."""
@@ -409,6 +418,14 @@ class Surrogate:
         out = np.zeros(self.n_params, np.float32)
         self._check(self._lib.us_surr_get_grads(self.h, out.ctypes.data))
         return out
+
+    def render_3d(self, envs, poses, n_elev, elev_pitch_mm, seed, step, frames, stream=None):
+        """Volumetric frames of a 3-D probe: each env's plane swept over n_elev
+        elevation offsets; frames as frame_layout(np.repeat(envs, n_elev, 0))."""
+        B = poses.shape[0]
+        self._check(self._lib.us_sim_render_3d(self.h, make_envs(envs), B, _ptr(poses), n_elev,
+                                               float(elev_pitch_mm), seed, step, _ptr(frames),
+                                               _stream_handle(stream)))
 
     def render_timed(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
         """The tuned render with per-kernel CUDA-event times (ms): a list of
