@@ -108,6 +108,13 @@ def lib():
             L.oracle_sample_slice.restype = C.c_int
             L.oracle_anchored_noise.argtypes = [C.c_void_p, C.c_int32, C.c_float, C.c_uint32, C.c_uint64,
                                                 C.c_void_p]
+            L.oracle_recon_keep_threshold.argtypes = [C.c_double]
+            L.oracle_recon_keep_threshold.restype = C.c_uint32
+            L.oracle_recon_update.argtypes = [C.POINTER(OrVolume), C.POINTER(OrProbe), C.c_void_p, C.c_uint32,
+                                              C.c_uint64, C.c_uint64, C.c_int32, C.c_double, C.c_void_p,
+                                              C.c_void_p]
+            L.oracle_recon_update.restype = C.c_int64
+            L.oracle_recon_observe.argtypes = [C.POINTER(OrVolume), C.c_void_p, C.c_void_p, C.c_void_p]
             _lib = L
     return _lib
 
@@ -262,6 +269,33 @@ def anchored_noise(pos, levels, cell_mm, vol_id, seed):
     out = np.zeros(2)
     lib().oracle_anchored_noise(_ptr(p), levels, cell_mm, vol_id, seed, _ptr(out))
     return float(out[0]), float(out[1])
+
+
+def recon_update(labels, hu, voxel_mm, probe, pose, env, seed, step, bone_label, p_miss, recon):
+    """add one frame's kept bone-surface points to `recon` (uint8 volume,
+    updated in place); returns (ground-truth points, kept points)"""
+    vol = _Vol(labels, hu, voxel_mm)
+    pr = or_probe(probe)
+    M = np.ascontiguousarray(pose, np.float32).reshape(12)
+    assert recon.dtype == np.uint8 and recon.flags.c_contiguous and recon.shape == vol.labels.shape
+    kept = C.c_int64(0)
+    n = lib().oracle_recon_update(C.byref(vol.desc), C.byref(pr), _ptr(M), env, seed, step, bone_label,
+                                  float(p_miss), _ptr(recon), C.byref(kept))
+    return int(n), int(kept.value)
+
+
+def recon_observe(recon, voxel_mm, pose):
+    """the reconstruction voxelized in the probe frame: uint8 [40][40][40] (h, w, e)"""
+    nz, ny, nx = recon.shape
+    desc = OrVolume(None, None, nx, ny, nz, voxel_mm, 0)
+    M = np.ascontiguousarray(pose, np.float32).reshape(12)
+    obs = np.zeros((40, 40, 40), np.uint8)
+    lib().oracle_recon_observe(C.byref(desc), _ptr(np.ascontiguousarray(recon, np.uint8)), _ptr(M), _ptr(obs))
+    return obs
+
+
+def recon_keep_threshold(p_miss):
+    return int(lib().oracle_recon_keep_threshold(float(p_miss)))
 
 
 def sample_slice(labels, hu, voxel_mm, probe, pose):

@@ -665,3 +665,89 @@ int oracle_sample_slice(const or_volume* vol, const or_probe* p, const float* po
   }
   return 0;
 }
+
+/* ------------------------------------------- reconstruction observation */
+/*
+ * Task 2 of Sec. 4 with App. C: the bone surface segmented from each frame
+ * (simulated from the ground truth with a missing probability per point)
+ * updates a 3-D reconstruction with the probe's pose; the observation is
+ * that reconstruction transformed to the current probe frame and voxelized
+ * to H x W x E = 40 x 40 x 40 voxels of 3 mm.
+ * READING: a ground-truth surface point is a beam sample s whose nearest
+ * label is the bone label while sample s-1's is not (the boundary G of
+ * App. B.2 with bone below); it is kept unless its Philox-4x32-10 word 0,
+ * counter (s, line, env, 1), key = the render key of (seed, step), falls
+ * below floor(p_miss 2^32).  The reconstruction is the set of volume voxels
+ * (the point's nearest voxel) ever kept.  Observation voxel (h, w, e) holds
+ * 1 iff some reconstructed voxel centre v h, mapped to the probe frame by
+ * q = R^T (v h - t) (FP32: differences, then per column the three products
+ * summed in row order), has floor(q_x / 3 + 20) = w, floor(q_y / 3 + 20) = e,
+ * floor(q_z / 3) = h.
+ */
+uint32_t oracle_recon_keep_threshold(double p_miss) {
+  double t = floor(p_miss * 4294967296.0);
+  if (t < 0) t = 0;
+  if (t > 4294967295.0) t = 4294967295.0;
+  return (uint32_t)t;
+}
+
+/* add this frame's kept surface points to `recon` (one byte per voxel of the
+ * volume); returns the number of ground-truth points, *kept those kept */
+int64_t oracle_recon_update(const or_volume* vol, const or_probe* p, const float* pose, uint32_t env, uint64_t seed,
+                            uint64_t step, int32_t bone_label, double p_miss, uint8_t* recon, int64_t* kept) {
+  const int NL = p->n_lines, NS = p->n_samples;
+  const float inv_h = (float)(1.0 / (double)vol->voxel_mm);
+  const uint32_t thr = oracle_recon_keep_threshold(p_miss);
+  uint32_t key[2];
+  key[0] = (uint32_t)seed ^ (uint32_t)(step * 0x9E3779B9ull);
+  key[1] = (uint32_t)(seed >> 32);
+  int64_t n = 0, k = 0;
+  for (int l = 0; l < NL; ++l) {
+    int prev_lab = -1;
+    for (int s = 0; s < NS; ++s) {
+      float u[3];
+      or_sample_voxel_coords(p, pose, inv_h, l, s, u);
+      int64_t idx = or_nearest(vol, u);
+      int lab = idx >= 0 ? vol->labels[idx] : 0;
+      if (s > 0 && lab == bone_label && prev_lab != bone_label) {
+        ++n;
+        uint32_t ctr[4] = {(uint32_t)s, (uint32_t)l, env, 1u}, w[4];
+        oracle_philox4x32_10(ctr, key, w);
+        if (w[0] >= thr) {
+          recon[idx] = 1;
+          ++k;
+        }
+      }
+      prev_lab = lab;
+    }
+  }
+  if (kept) *kept = k;
+  return n;
+}
+
+/* voxelize the reconstruction in the probe frame of `pose`: obs [40][40][40]
+ * (h, w, e), 1 where a reconstructed voxel lands */
+void oracle_recon_observe(const or_volume* vol, const uint8_t* recon, const float* pose, uint8_t* obs) {
+  memset(obs, 0, 40 * 40 * 40);
+  const float h = vol->voxel_mm, third = (float)(1.0 / 3.0);
+  for (int64_t kz = 0; kz < vol->nz; ++kz)
+    for (int64_t jy = 0; jy < vol->ny; ++jy)
+      for (int64_t ix = 0; ix < vol->nx; ++ix) {
+        if (!recon[(kz * vol->ny + jy) * vol->nx + ix]) continue;
+        float d[3];
+        d[0] = (float)ix * h - pose[3];
+        d[1] = (float)jy * h - pose[7];
+        d[2] = (float)kz * h - pose[11];
+        float q[3];
+        for (int c = 0; c < 3; ++c) {
+          float a = pose[0 * 4 + c] * d[0];
+          float b = pose[1 * 4 + c] * d[1];
+          float e = pose[2 * 4 + c] * d[2];
+          float ab = a + b;
+          q[c] = ab + e;
+        }
+        float fw = floorf(q[0] * third + 20.0f), fe = floorf(q[1] * third + 20.0f), fh = floorf(q[2] * third);
+        if (fw >= 0 && fw < 40 && fe >= 0 && fe < 40 && fh >= 0 && fh < 40)
+          obs[((int)fh * 40 + (int)fw) * 40 + (int)fe] = 1;
+      }
+}
