@@ -348,6 +348,71 @@ def run_mixed(args):
     print(json.dumps(line), flush=True)
 
 
+def run_recon(args):
+    """Bone-surface task step (Task 2; App. C): 128 envs with the 200 x 150
+    linear probe on the 256^3 volume; every step renders the batch, adds the
+    kept bone-surface points (20% missing) to each env's reconstruction and
+    voxelizes the reconstructions to 40^3 observations at 3 mm in the probe
+    frame.  Reports env steps per second (device time, L2 flushed)."""
+    import torch
+    from paper_2507_01152_gb300 import build
+    from paper_2507_01152_gb300.ussim import Sim, make_envs
+    build.build()
+    torch.cuda.set_device(0)
+    spec = scene.c2_spec()
+    lab, hu = scene.make_volume(spec)
+    B, T = 128, args.steps + args.warmup + 1
+    probe = scene.linear_probe(150, 200, 100.0, 0.5)
+    walk = scene.random_walk_poses(spec, B, T, 2005)
+    envs = np.zeros((B, 2), np.int32)
+    sim = Sim([(torch.from_numpy(lab).cuda(), torch.from_numpy(hu).cuda(), spec.voxel_mm)], scene.tissue_table(),
+              [probe], scene.Options())
+    ec = make_envs(envs)
+    off = sim.frame_layout(envs)
+    frames = torch.empty(int(off[-1]), device="cuda")
+    words, cap = sim.recon_words(), 1 << 16
+    bm = torch.zeros((B, words), dtype=torch.int32, device="cuda")
+    pts = torch.zeros((B, cap), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(B, dtype=torch.int32, device="cuda")
+    obs = torch.zeros((B, 40, 40, 40), dtype=torch.uint8, device="cuda")
+    P = torch.from_numpy(np.ascontiguousarray(walk, np.float32)).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        sim.autotune(envs, P[0], frames, None, stream=st)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    tr = tu = to = 0.0
+    with torch.cuda.stream(st):
+        for t in range(T):
+            flush.zero_()
+            ev[0].record(st)
+            sim.render(None, P[t], 7, t, frames, stream=st, envs_c=ec)
+            ev[1].record(st)
+            sim.recon_update(envs, P[t], 7, t, 4, 0.2, bm, pts, cnt, stream=st)
+            ev[2].record(st)
+            sim.recon_observe(envs, P[t], pts, cnt, obs, stream=st)
+            ev[3].record(st)
+            ev[3].synchronize()
+            if t > args.warmup:
+                tr += ev[0].elapsed_time(ev[1])
+                tu += ev[1].elapsed_time(ev[2])
+                to += ev[2].elapsed_time(ev[3])
+    sim.check(st)
+    K = T - args.warmup - 1
+    ms = (tr + tu + to) / K
+    line = {"metric": METRIC, "value": B / ms * 1e3, "unit": "frames/s", "n_gpus": 1, "steps": K,
+            "warmup": args.warmup + 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "bone_surface_task_128env_linear_200x150_recon40", "envs": B,
+                       "frame": "one env step: render + reconstruction update + 40^3 observation",
+                       "l2": "flushed between timed steps (256 MB write)", "tuning": sim.get_tuning()},
+            "breakdown_ms": {"render": tr / K, "recon_update": tu / K, "recon_observe": to / K},
+            "reconstructed_voxels_per_env_after": float(cnt.float().mean()),
+            "occupied_obs_voxels_per_env": float(obs.float().sum()) / B}
+    print(json.dumps(line), flush=True)
+    sim.close()
+
+
 def run_ours(args):
     import torch
     from paper_2507_01152_gb300 import build
@@ -529,7 +594,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "paper", "surgery3d", "mixed"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "paper", "surgery3d", "recon", "mixed"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -546,6 +611,8 @@ def main():
         run_reference(args)
     elif args.workload == "mixed":
         run_mixed(args)
+    elif args.workload == "recon":
+        run_recon(args)
     else:
         run_ours(args)
 

@@ -276,6 +276,35 @@ US_API us_status us_sim_render_3d(us_sim* sim, const us_env* envs, int32_t B, co
                                   int32_t n_elev, float elev_pitch_mm, uint64_t seed, uint64_t step,
                                   float* frames, void* stream);
 
+/* Reconstruction observation of the bone-surface task (Sec. 4, Task 2;
+ * App. C: 40 x 40 x 40 voxels of 3 mm, 20% missing surface points).
+ * Ground-truth surface point: a beam sample s > 0 whose nearest label is
+ * bone_label while sample s - 1's is not.  It is kept unless word 0 of
+ * Philox-4x32-10 on counter (s, line, env index, 1), key = the render key
+ * of (seed, step), is below floor(p_miss 2^32).  The reconstruction of an
+ * environment is the set of volume voxels (nearest voxel of a kept point)
+ * kept so far, held by the caller as a bitmap over its volume's voxels
+ * (us_sim_recon_words() 32-bit words per environment, the largest volume's
+ * voxel count / 32 rounded up) plus the list of set voxel indices
+ * (capacity `cap` per environment) and its count; zero all three to start.
+ * us_sim_recon_update adds one frame per environment (poses device [B][3][4]);
+ * a list that reaches its capacity stops growing and is reported by
+ * us_sim_check.  us_sim_recon_observe writes obs (device uint8
+ * [B][40][40][40], index (h, w, e)): 1 where a reconstructed voxel centre
+ * v h, mapped to the probe frame by q = R^T (v h - t) (FP32), has
+ * floor(q_x / 3 + 20) = w, floor(q_y / 3 + 20) = e, floor(q_z / 3) = h.
+ * Both are asynchronous on `stream`; all buffers are caller-owned device
+ * memory.  Errors: US_ERR_INVALID_ARG (NULL buffers, cap < 1, bone label or
+ * p_miss out of range, bad ids), US_ERR_CUDA. */
+US_API int64_t us_sim_recon_words(const us_sim* sim);
+US_API us_status us_sim_recon_update(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                                     uint64_t seed, uint64_t step, int32_t bone_label, float p_miss,
+                                     uint32_t* bitmaps, int32_t* points, int32_t* counts, int32_t cap,
+                                     void* stream);
+US_API us_status us_sim_recon_observe(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                                      const int32_t* points, const int32_t* counts, int32_t cap,
+                                      uint8_t* obs, void* stream);
+
 /* The tuned batched render (as us_sim_render, without graph replay) with
  * CUDA events recorded on `stream` around each of its kernels; waits for
  * the render and writes each kernel's duration in ms to kernel_ms[0..n)

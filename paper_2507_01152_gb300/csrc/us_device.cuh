@@ -20,6 +20,7 @@ struct DevVolume {
   const int16_t* hu;
   int nx, ny, nz;
   float inv_h;
+  float h;   // voxel edge, mm (as given)
 };
 
 // per (probe, label): attenuation per sample f*alpha*dr (Np), scatter

@@ -584,7 +584,7 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
     }
   std::vector<DevVolume> dv;
   for (const us_volume& v : s->vols)
-    dv.push_back(DevVolume{v.labels, v.hu, v.nx, v.ny, v.nz, (float)(1.0 / (double)v.voxel_mm)});
+    dv.push_back(DevVolume{v.labels, v.hu, v.nx, v.ny, v.nz, (float)(1.0 / (double)v.voxel_mm), v.voxel_mm});
   std::vector<DevProbe> dp;
   for (const ProbeHost& ph : s->probes) dp.push_back(device_probe(ph));
   std::vector<DevPair> pairs;
@@ -792,6 +792,50 @@ us_status us_sim_render_3d(us_sim* s, const us_env* envs, int32_t B, const float
   return do_render(s, ex.data(), BE, s->d_poses3d, seed, step, frames, nullptr, nullptr, nullptr, nullptr, 0, st);
 }
 
+int64_t us_sim_recon_words(const us_sim* s) {
+  if (!s) return -1;
+  long long w = 0;
+  for (const us_volume& v : s->vols) w = std::max(w, ((long long)v.nx * v.ny * v.nz + 31) / 32);
+  return w;
+}
+
+us_status us_sim_recon_update(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint64_t seed,
+                              uint64_t step, int32_t bone_label, float p_miss, uint32_t* bitmaps, int32_t* points,
+                              int32_t* counts, int32_t cap, void* stream) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (B < 0 || (B > 0 && (!envs || !poses || !bitmaps || !points || !counts)) || cap < 1 || bone_label < 0 ||
+      bone_label > 255 || !(p_miss >= 0.f && p_miss <= 1.f))
+    return fail(s, US_ERR_INVALID_ARG, "bad reconstruction arguments");
+  if (B == 0) return US_OK;
+  us_plan* pl;
+  us_status r = get_plan(s, envs, B, &pl);
+  if (r != US_OK) return r;
+  RenderParams p = base_params(s, poses, seed, step, nullptr);
+  int max_lines = 1;
+  for (int b = 0; b < B; ++b) max_lines = std::max(max_lines, s->probes[envs[b].probe_id].desc.n_lines);
+  const double t = std::floor((double)p_miss * 4294967296.0);
+  const unsigned thr = (unsigned)std::min(t, 4294967295.0);
+  cudaError_t e = launch_recon_update(p, pl->d_items_batch, B, bone_label, thr, bitmaps, us_sim_recon_words(s),
+                                      points, counts, cap, max_lines, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? US_OK : cuda_fail(s, e, "reconstruction update");
+}
+
+us_status us_sim_recon_observe(us_sim* s, const us_env* envs, int32_t B, const float* poses, const int32_t* points,
+                               const int32_t* counts, int32_t cap, uint8_t* obs, void* stream) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (B < 0 || (B > 0 && (!envs || !poses || !points || !counts || !obs)) || cap < 1)
+    return fail(s, US_ERR_INVALID_ARG, "bad observation arguments");
+  if (B == 0) return US_OK;
+  us_plan* pl;
+  us_status r = get_plan(s, envs, B, &pl);
+  if (r != US_OK) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(obs, 0, (size_t)B * 64000, st);
+  if (e == cudaSuccess)
+    e = launch_recon_observe(base_params(s, poses, 0, 0, nullptr), pl->d_items_batch, B, points, counts, cap, obs, st);
+  return e == cudaSuccess ? US_OK : cuda_fail(s, e, "reconstruction observation");
+}
+
 us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint64_t seed,
                               uint64_t step, float* frames, float* kernel_ms, int32_t* n_kernels, void* stream) {
   if (!kernel_ms || !n_kernels) return fail(s, US_ERR_INVALID_ARG, "NULL timing outputs");
@@ -859,6 +903,7 @@ us_status us_sim_check(us_sim* s, void* stream) {
   if (w) {
     cudaMemset(s->d_err, 0, sizeof w);
     if (w & kErrStagingTimeout) return fail(s, US_ERR_TIMEOUT, "a shared-memory staging copy did not complete in time");
+    if (w & kErrReconOverflow) return fail(s, US_ERR_INVALID_ARG, "a reconstruction point list reached its capacity");
     if (w & kErrNonFinitePose) return fail(s, US_ERR_INVALID_ARG, "a pose had a non-finite entry (rendered as water)");
     return fail(s, US_ERR_INTERNAL, "device consistency check failed");
   }

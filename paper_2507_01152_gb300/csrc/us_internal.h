@@ -104,6 +104,14 @@ cudaError_t launch_slice_input(const RenderParams& p, const EnvItem* items_batch
 // 3-D probe: B poses -> B * E poses swept along each pose's elevation axis
 cudaError_t launch_expand_elevation(const float* poses, int B, int E, float pitch, float* out, cudaStream_t st);
 
+// reconstruction observation (recon.cu)
+constexpr unsigned kErrReconOverflow = 16u;   // a reconstruction point list reached its capacity
+cudaError_t launch_recon_update(const RenderParams& p, const EnvItem* items, int B, int bone, unsigned thr,
+                                unsigned* bitmaps, long long words, int* points, int* counts, int cap, int max_lines,
+                                cudaStream_t st);
+cudaError_t launch_recon_observe(const RenderParams& p, const EnvItem* items, int B, const int* points,
+                                 const int* counts, int cap, unsigned char* obs, cudaStream_t st);
+
 // label check at creation: max label of a volume
 cudaError_t max_label(const uint8_t* labels, long long n, unsigned* d_out, cudaStream_t st);
 

@@ -83,6 +83,10 @@ SIGNATURES = {
     "us_sim_check": (C.c_int, [_P, _P]),
     "us_sim_render_timed": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, _P, _P]),
     "us_sim_render_3d": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, C.c_float, C.c_uint64, C.c_uint64, _P, _P]),
+    "us_sim_recon_words": (C.c_int64, [_P]),
+    "us_sim_recon_update": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, C.c_int32, C.c_float, _P, _P,
+                                      _P, C.c_int32, _P]),
+    "us_sim_recon_observe": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, C.c_int32, _P, _P]),
     "us_sim_sample_slices": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
     "us_sim_render_gated": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, C.c_float, _P, _P]),
     "us_sim_get_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
@@ -291,6 +295,23 @@ class Sim:
                                                float(elev_pitch_mm), seed, step, _ptr(frames),
                                                _stream_handle(stream)))
 
+    def recon_words(self):
+        return int(self._lib.us_sim_recon_words(self.h))
+
+    def recon_update(self, envs, poses, seed, step, bone_label, p_miss, bitmaps, points, counts, stream=None):
+        """add one frame per env to the reconstructions (bitmaps uint32 [B][recon_words()],
+        points int32 [B][cap], counts int32 [B]: device tensors, zeroed to start)"""
+        B = poses.shape[0]
+        self._check(self._lib.us_sim_recon_update(self.h, make_envs(envs), B, _ptr(poses), seed, step, bone_label,
+                                                  float(p_miss), _ptr(bitmaps), _ptr(points), _ptr(counts),
+                                                  points.shape[1], _stream_handle(stream)))
+
+    def recon_observe(self, envs, poses, points, counts, obs, stream=None):
+        """the reconstructions voxelized in each env's probe frame: obs uint8 [B][40][40][40]"""
+        B = poses.shape[0]
+        self._check(self._lib.us_sim_recon_observe(self.h, make_envs(envs), B, _ptr(poses), _ptr(points),
+                                                   _ptr(counts), points.shape[1], _ptr(obs), _stream_handle(stream)))
+
     def render_timed(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
         """The tuned render with per-kernel CUDA-event times (ms): a list of
         one (cluster kernel) or two (two-pass: pass A, pass B) durations."""
@@ -426,6 +447,23 @@ class Surrogate:
         self._check(self._lib.us_sim_render_3d(self.h, make_envs(envs), B, _ptr(poses), n_elev,
                                                float(elev_pitch_mm), seed, step, _ptr(frames),
                                                _stream_handle(stream)))
+
+    def recon_words(self):
+        return int(self._lib.us_sim_recon_words(self.h))
+
+    def recon_update(self, envs, poses, seed, step, bone_label, p_miss, bitmaps, points, counts, stream=None):
+        """add one frame per env to the reconstructions (bitmaps uint32 [B][recon_words()],
+        points int32 [B][cap], counts int32 [B]: device tensors, zeroed to start)"""
+        B = poses.shape[0]
+        self._check(self._lib.us_sim_recon_update(self.h, make_envs(envs), B, _ptr(poses), seed, step, bone_label,
+                                                  float(p_miss), _ptr(bitmaps), _ptr(points), _ptr(counts),
+                                                  points.shape[1], _stream_handle(stream)))
+
+    def recon_observe(self, envs, poses, points, counts, obs, stream=None):
+        """the reconstructions voxelized in each env's probe frame: obs uint8 [B][40][40][40]"""
+        B = poses.shape[0]
+        self._check(self._lib.us_sim_recon_observe(self.h, make_envs(envs), B, _ptr(poses), _ptr(points),
+                                                   _ptr(counts), points.shape[1], _ptr(obs), _stream_handle(stream)))
 
     def render_timed(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
         """The tuned render with per-kernel CUDA-event times (ms): a list of
