@@ -141,8 +141,11 @@ typedef struct {
  *   32) lines per block; the axially filtered lines go through a global
  *   buffer of the batch's beam size, allocated on first use per batch
  *   signature.  Same frames as the cluster kernel.
- * Default after us_sim_create: {1, 16, 1} (else {1, 8, 1}, else the cluster
- * shape {8, 32, 1} or {16, 16, 1}, whichever fits the probe set first). */
+ * Default after us_sim_create: the first of {1, 16, 1}, {1, 8, 1},
+ * {1, 32, 1}, {8, 32, 1}, {16, 16, 1}, {16, 8, 1} that fits the probe set.
+ * If none fits (lines of up to 1024 samples with a wide lateral PSF), the
+ * simulator is still created: the batched entry points then return
+ * US_ERR_UNSUPPORTED and us_sim_render_plain renders. */
 typedef struct {
   int32_t cluster_size;  /* 1, 4, 8 or 16 */
   int32_t warps_per_cta; /* 8, 16 or 32 */

@@ -283,6 +283,11 @@ RenderParams base_params(const us_sim* s, const float* poses, uint64_t seed, uin
   return p;
 }
 
+us_status no_batched(us_sim* s) {
+  return fail(s, US_ERR_UNSUPPORTED,
+              "no batched launch shape fits this probe set in shared memory; use us_sim_render_plain");
+}
+
 us_status check_render_args(us_sim* s, const us_env* envs, int B, const float* poses, float* frames) {
   if (!s) return US_ERR_INVALID_ARG;
   if (B < 0) return fail(s, US_ERR_INVALID_ARG, "B must be >= 0");
@@ -306,6 +311,7 @@ us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, ui
   p.label = label;
   cudaError_t e;
   if (path == 0) {
+    if (!s->batched) return no_batched(s);
     p.items = pl->d_items;
     p.n_items = B;
     const bool two_pass = s->tuning.cluster_size == 1;
@@ -400,6 +406,7 @@ us_status apply_split(us_sim* s, const us_tuning& t) {
   if ((e = split_prepare(sh)) != cudaSuccess) return cuda_fail(s, e, "kernel attributes");
   s->split = sh;
   s->tuning = t;
+  s->batched = true;
   return US_OK;
 }
 
@@ -425,6 +432,7 @@ us_status apply_tuning(us_sim* s, const us_tuning& t) {
   sh.clusters = clusters;
   s->shape = sh;
   s->tuning = t;
+  s->batched = true;
   return US_OK;
 }
 
@@ -629,22 +637,16 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
       return US_ERR_INVALID_ARG;
     }
   }
-  // the cluster shape serves gated renders too: set it first, then the
-  // default two-pass shape; fall back to smaller footprints where needed
+  // default launch shape: the first that fits the probe set, two-pass
+  // first; when none fits (very long lines with a wide lateral PSF), the
+  // batched entry points report US_ERR_UNSUPPORTED and the plain
+  // per-environment path still renders
   {
-    us_tuning tc{8, 32, 1};
-    if ((r = apply_tuning(s, tc)) != US_OK) {
-      tc = us_tuning{16, 16, 1};
-      if ((r = apply_tuning(s, tc)) != US_OK) {
-        free_sim(s);
-        return r;
-      }
-    }
-    us_tuning t2{1, 16, 1};
-    if (apply_tuning(s, t2) != US_OK) {
-      t2 = us_tuning{1, 8, 1};
-      if (apply_tuning(s, t2) != US_OK) apply_tuning(s, tc);
-    }
+    static const us_tuning order[] = {{1, 16, 1}, {1, 8, 1}, {1, 32, 1}, {8, 32, 1}, {16, 16, 1}, {16, 8, 1}};
+    s->batched = false;
+    for (const us_tuning& t : order)
+      if (apply_tuning(s, t) == US_OK) break;
+    s->last_error.clear();
   }
   *out = s;
   return US_OK;
@@ -738,6 +740,7 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
   if (r != US_OK || B == 0) return r;
   if (!score) return fail(s, US_ERR_INVALID_ARG, "NULL score");
   if (B > 32 * 1024) return fail(s, US_ERR_UNSUPPORTED, "gated batches are limited to 32768 envs");
+  if (!s->batched) return no_batched(s);
   us_plan* pl;
   if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
   cudaError_t e;
@@ -844,6 +847,7 @@ us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const fl
   if (r != US_OK || B == 0) return r;
   us_plan* pl;
   if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  if (!s->batched) return no_batched(s);
   RenderParams p = base_params(s, poses, seed, step, frames);
   p.items = pl->d_items;
   p.n_items = B;

@@ -155,6 +155,7 @@ struct us_sim {
   ussim::FusedShape shape;     // cluster path (also serves gated renders when it is not tuned in)
   ussim::SplitShape split;     // two-pass path (tuning.cluster_size == 1)
   us_tuning tuning{1, 16, 1};
+  bool batched = true;         // a batched launch shape fits the probe set
 
   std::map<std::string, us_plan> plans;
 
