@@ -66,7 +66,12 @@ typedef struct us_sim us_sim; /* opaque */
  * volumes with label maps).  DEVICE pointers, layout [nz][ny][nx] with x
  * fastest; voxel (i, j, k) is centred at (i, j, k) * voxel_mm in the
  * volume frame (mm).  Borrowed for the life of the handle.  Samples
- * outside the grid read label 0 and HU 0 (water). */
+ * outside the grid read label 0 and HU 0 (water).  The contents are read
+ * at us_sim_create: the labels are range-checked and the HU grid is copied
+ * into a library-owned corner layout (16 bytes per cell, (nx+1)(ny+1)(nz+1)
+ * cells, unless us_options.volume_layout = 1) that the trilinear
+ * interpolation reads.  After changing a
+ * volume's contents, call us_sim_refresh_volumes before the next render. */
 typedef struct {
   const uint8_t* labels;
   const int16_t* hu;
@@ -121,11 +126,17 @@ typedef struct {
  *   words (counter = cell x, y, z, k << 16 | volume index; key = seed, no
  *   step) give standard normals; N = sum_k a_k N_k with a_k proportional to
  *   2^(-k/2), unit variance.  T = N0 sigma0 + mu0 where N1 <= mu1.
- *   0: the beam-keyed maps above (speckle_levels, speckle_cell_mm unused). */
+ *   0: the beam-keyed maps above (speckle_levels, speckle_cell_mm unused).
+ * volume_layout 0: the trilinear interpolation reads a library-owned copy
+ *   of each HU grid in corner records (the 8 corners of a cell in one 16-byte
+ *   record: one load per sample, 16 bytes of device memory per cell);
+ *   1: it reads the caller's HU grid (eight loads per sample, no copy).
+ *   Both give identical images. */
 typedef struct {
   int32_t refl_power, transmission, z_mode, speckle;
   int32_t speckle_anchor, speckle_levels;
   float speckle_cell_mm;
+  int32_t volume_layout;
 } us_options;
 
 /* One environment of a batch: which volume and which probe it uses. */
@@ -164,6 +175,16 @@ typedef struct {
 US_API us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* table,
                         int32_t n_labels, const us_probe* probes, int32_t n_probes,
                         const us_options* opt, us_sim** out);
+
+/* Re-read every volume's contents after the caller changed them: checks
+ * the labels against the tissue table and rebuilds the corner layout of
+ * the HU grid (App. B.2's image model samples the CT by trilinear
+ * interpolation; the layout holds the 8 corners of each cell together).
+ * Synchronous on `stream` (NULL = legacy default stream); no render of this
+ * handle may run meanwhile.  Errors: US_ERR_INVALID_ARG (a label outside
+ * the table; the handle keeps its previous corner layout for volumes not
+ * yet re-read), US_ERR_CUDA. */
+US_API us_status us_sim_refresh_volumes(us_sim* sim, void* stream);
 
 /* Release every resource of the handle (waits for its work to finish). */
 US_API void us_sim_destroy(us_sim* sim);

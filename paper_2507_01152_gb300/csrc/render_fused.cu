@@ -361,6 +361,31 @@ __global__ void max_label_kernel(const uint8_t* labels, long long n, unsigned* o
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
+// corner records of a volume's HU grid (layout at DevVolume::hu8)
+__global__ void pack_corners_kernel(DevVolume V, uint4* out, long long n) {
+  const int px = V.nx + 1, py = V.ny + 1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % px) - 1, j = (int)((t / px) % py) - 1, k = (int)(t / ((long long)px * py)) - 1;
+    auto at = [&](int a, int b, int c) -> unsigned {
+      const bool in = (unsigned)a < (unsigned)V.nx && (unsigned)b < (unsigned)V.ny && (unsigned)c < (unsigned)V.nz;
+      return in ? (unsigned)(uint16_t)V.hu[((long long)c * V.ny + b) * V.nx + a] : 0u;
+    };
+    unsigned w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dj = q & 1, dk = q >> 1;
+      w[q] = at(i, j + dj, k + dk) | (at(i + 1, j + dj, k + dk) << 16);
+    }
+    out[t] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+cudaError_t pack_corners(const DevVolume& V, uint4* out, cudaStream_t st) {
+  const long long n = (long long)(V.nx + 1) * (V.ny + 1) * (V.nz + 1);
+  pack_corners_kernel<<<152 * 8, 256, 0, st>>>(V, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t max_label(const uint8_t* labels, long long n, unsigned* d_out, cudaStream_t st) {
   max_label_kernel<<<1024, 256, 0, st>>>(labels, n, d_out);
   return cudaGetLastError();

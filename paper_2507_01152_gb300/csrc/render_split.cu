@@ -31,17 +31,28 @@
 
 namespace ussim {
 
-// axial PSF of one padded row in place (K zeros, NS samples, K zeros)
+// axial PSF of one padded row in place (K zeros, NS samples, K zeros).
+// KC > 0: the half-width is the compile-time KC (== K) and the taps sit in
+// registers; KC = 0: any K, taps read from shared memory.  Same tap order.
+template <int KC>
 __device__ __forceinline__ void axial_psf_row(float* prow, int NS, const float* w, int K, int lane) {
   float prev = 0.f;
   int prev_s = -1;
   const int taps = 2 * K + 1;
+  float wr[KC > 0 ? 2 * KC + 1 : 1];
+#pragma unroll
+  for (int k = 0; k < (KC > 0 ? 2 * KC + 1 : 0); ++k) wr[k] = w[k];
   for (int c = 0; c < NS; c += 32) {
     const int s = c + lane;
     float acc = 0.f;
     if (s < NS) {
       const float* q = prow + s;
-      for (int k = 0; k < taps; ++k) acc = fmaf(w[k], q[k], acc);
+      if constexpr (KC > 0) {
+#pragma unroll
+        for (int k = 0; k < 2 * KC + 1; ++k) acc = fmaf(wr[k], q[k], acc);
+      } else {
+        for (int k = 0; k < taps; ++k) acc = fmaf(w[k], q[k], acc);
+      }
     }
     __syncwarp();
     if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
@@ -51,6 +62,18 @@ __device__ __forceinline__ void axial_psf_row(float* prow, int NS, const float* 
   }
   if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
   __syncwarp();
+}
+
+__device__ __forceinline__ void axial_psf_any(float* prow, int NS, const float* w, int K, int lane) {
+  switch (K) {
+    case 3: axial_psf_row<3>(prow, NS, w, K, lane); break;
+    case 4: axial_psf_row<4>(prow, NS, w, K, lane); break;
+    case 5: axial_psf_row<5>(prow, NS, w, K, lane); break;
+    case 6: axial_psf_row<6>(prow, NS, w, K, lane); break;
+    case 7: axial_psf_row<7>(prow, NS, w, K, lane); break;
+    case 8: axial_psf_row<8>(prow, NS, w, K, lane); break;
+    default: axial_psf_row<0>(prow, NS, w, K, lane); break;
+  }
 }
 
 struct SplitCtx {
@@ -162,7 +185,7 @@ __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(Ren
     scanline_model<ANCHORED>(p, P, tis, cx.pair, cx.it.b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; },
                              posf, cx.it.vol);
     __syncwarp();
-    axial_psf_row(prow, NS, wax, KA, lane);
+    axial_psf_any(prow, NS, wax, KA, lane);
     float* dst = a.beam + cx.it.beam_off + (long long)l * NS;
     for (int s = lane; s < NS; s += 32) dst[s] = row[s];
   }

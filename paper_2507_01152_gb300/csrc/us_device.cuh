@@ -21,6 +21,12 @@ struct DevVolume {
   int nx, ny, nz;
   float inv_h;
   float h;   // voxel edge, mm (as given)
+  // Corner records of the HU grid, or null: record ((k+1)(ny+1) + j+1)(nx+1)
+  // + i+1 holds the HU of the 8 corners of the cell based at voxel (i, j, k),
+  // i in [-1, nx-1] (likewise j, k), as int16 in the order c000 c100 c010
+  // c110 c001 c101 c011 c111 (bit 0 of the corner index = x), 0 outside the
+  // grid: one 16-byte load per trilinear sample instead of eight gathers.
+  const uint4* hu8;
 };
 
 // per (probe, label): attenuation per sample f*alpha*dr (Np), scatter
@@ -169,7 +175,18 @@ __device__ __forceinline__ float trilinear_hu(const DevVolume& V, float3 u) {
   const int i = (int)fx, j = (int)fy, k = (int)fz;
   const float tx = u.x - fx, ty = u.y - fy, tz = u.z - fz;
   float c000, c100, c010, c110, c001, c101, c011, c111;
-  if ((unsigned)i < (unsigned)(V.nx - 1) && (unsigned)j < (unsigned)(V.ny - 1) && (unsigned)k < (unsigned)(V.nz - 1)) {
+  if (V.hu8) {
+    // the sign-extended halves of each word are the int16 corner values
+    const uint4 q = __ldg(&V.hu8[((k + 1) * (V.ny + 1) + (j + 1)) * (V.nx + 1) + (i + 1)]);
+    c000 = (float)((int)(q.x << 16) >> 16);
+    c100 = (float)((int)q.x >> 16);
+    c010 = (float)((int)(q.y << 16) >> 16);
+    c110 = (float)((int)q.y >> 16);
+    c001 = (float)((int)(q.z << 16) >> 16);
+    c101 = (float)((int)q.z >> 16);
+    c011 = (float)((int)(q.w << 16) >> 16);
+    c111 = (float)((int)q.w >> 16);
+  } else if ((unsigned)i < (unsigned)(V.nx - 1) && (unsigned)j < (unsigned)(V.ny - 1) && (unsigned)k < (unsigned)(V.nz - 1)) {
     const int sy = V.nx, sz = V.nx * V.ny;
     const int16_t* b = V.hu + (k * V.ny + j) * V.nx + i;
     c000 = (float)__ldg(b);

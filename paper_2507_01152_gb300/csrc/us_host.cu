@@ -349,6 +349,7 @@ void free_sim(us_sim* s) {
     cudaFree(ph.d_wedge_off);
   }
   for (auto* d : s->d_pair_D) cudaFree(d);
+  for (auto* d : s->d_hu8) cudaFree(d);
   for (auto& kv : s->plans) {
     drop_graph(kv.second);
     cudaFree(kv.second.d_items);
@@ -537,6 +538,43 @@ const char* us_status_string(us_status st) {
 
 const char* us_sim_last_error(const us_sim* s) { return s ? s->last_error.c_str() : "NULL handle"; }
 
+// Read the volumes' contents: every label must index the tissue table, and
+// the HU grid is copied into corner records (allocated once per volume; a
+// volume whose records do not fit in memory or in 31-bit indices keeps the
+// eight-gather interpolation, with identical results).  Synchronous.
+static us_status read_volumes(us_sim* s, cudaStream_t st) {
+  cudaError_t e;
+  for (size_t i = 0; i < s->vols.size(); ++i) {
+    const us_volume& v = s->vols[i];
+    unsigned mx = 0;
+    if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess ||
+        (e = max_label(v.labels, (long long)v.nx * v.ny * v.nz, s->d_work, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&mx, s->d_work, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return cuda_fail(s, e, "label check");
+    if ((int)mx >= s->n_labels) return fail(s, US_ERR_INVALID_ARG, "label outside the tissue table");
+    const long long n8 = (long long)(v.nx + 1) * (v.ny + 1) * (v.nz + 1);
+    if (!s->d_hu8[i] && s->opt.volume_layout == 0 && n8 < (1ll << 31) && cudaMalloc(&s->d_hu8[i], (size_t)n8 * sizeof(uint4)) != cudaSuccess) {
+      cudaGetLastError();
+      s->d_hu8[i] = nullptr;
+    }
+    ussim::DevVolume dv = s->dev_vols[i];
+    dv.hu8 = nullptr;
+    if (s->d_hu8[i] && (e = pack_corners(dv, s->d_hu8[i], st)) != cudaSuccess) return cuda_fail(s, e, "corner records");
+    s->dev_vols[i].hu8 = s->d_hu8[i];
+  }
+  if ((e = cudaMemcpyAsync(s->d_vols, s->dev_vols.data(), s->dev_vols.size() * sizeof(ussim::DevVolume),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_fail(s, e, "volume descriptors");
+  return US_OK;
+}
+
+us_status us_sim_refresh_volumes(us_sim* s, void* stream) {
+  if (!s) return US_ERR_INVALID_ARG;
+  return read_volumes(s, static_cast<cudaStream_t>(stream));
+}
+
 us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* table, int32_t n_labels,
                         const us_probe* probes, int32_t n_probes, const us_options* opt, us_sim** out) {
   if (!out) return US_ERR_INVALID_ARG;
@@ -545,9 +583,9 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
     return US_ERR_INVALID_ARG;
   us_sim* s = new (std::nothrow) us_sim();
   if (!s) return US_ERR_OOM;
-  s->opt = opt ? *opt : us_options{1, 1, 0, 1, 0, 1, 0.25f};
+  s->opt = opt ? *opt : us_options{1, 1, 0, 1, 0, 1, 0.25f, 0};
   if (!(s->opt.refl_power == 1 || s->opt.refl_power == 2) || (s->opt.transmission & ~1) || (s->opt.z_mode & ~1) ||
-      (s->opt.speckle & ~1) || (s->opt.speckle_anchor & ~1) ||
+      (s->opt.speckle & ~1) || (s->opt.speckle_anchor & ~1) || (s->opt.volume_layout & ~1) ||
       (s->opt.speckle_anchor && (s->opt.speckle_levels < 1 || s->opt.speckle_levels > kMaxSpeckleLevels ||
                                  !(s->opt.speckle_cell_mm > 0.f) || !std::isfinite(s->opt.speckle_cell_mm)))) {
     delete s;
@@ -592,7 +630,7 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
     }
   std::vector<DevVolume> dv;
   for (const us_volume& v : s->vols)
-    dv.push_back(DevVolume{v.labels, v.hu, v.nx, v.ny, v.nz, (float)(1.0 / (double)v.voxel_mm), v.voxel_mm});
+    dv.push_back(DevVolume{v.labels, v.hu, v.nx, v.ny, v.nz, (float)(1.0 / (double)v.voxel_mm), v.voxel_mm, nullptr});
   std::vector<DevProbe> dp;
   for (const ProbeHost& ph : s->probes) dp.push_back(device_probe(ph));
   std::vector<DevPair> pairs;
@@ -623,19 +661,11 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
     free_sim(s);
     return st;
   }
-  // every label must index the tissue table
-  for (const us_volume& v : s->vols) {
-    unsigned mx = 0;
-    if ((e = cudaMemset(s->d_work, 0, sizeof(unsigned))) != cudaSuccess ||
-        (e = max_label(v.labels, (long long)v.nx * v.ny * v.nz, s->d_work, 0)) != cudaSuccess ||
-        (e = cudaMemcpy(&mx, s->d_work, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess) {
-      free_sim(s);
-      return US_ERR_CUDA;
-    }
-    if ((int)mx >= n_labels) {
-      free_sim(s);
-      return US_ERR_INVALID_ARG;
-    }
+  s->dev_vols = dv;
+  s->d_hu8.assign(dv.size(), nullptr);
+  if ((r = read_volumes(s, nullptr)) != US_OK) {
+    free_sim(s);
+    return r;
   }
   // default launch shape: the first that fits the probe set, two-pass
   // first; when none fits (very long lines with a wide lateral PSF), the

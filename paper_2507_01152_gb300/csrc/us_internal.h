@@ -114,6 +114,8 @@ cudaError_t launch_recon_observe(const RenderParams& p, const EnvItem* items, in
 
 // label check at creation: max label of a volume
 cudaError_t max_label(const uint8_t* labels, long long n, unsigned* d_out, cudaStream_t st);
+// corner records of V's HU grid into out ((nx+1)(ny+1)(nz+1) records)
+cudaError_t pack_corners(const DevVolume& V, uint4* out, cudaStream_t st);
 
 }  // namespace ussim
 
@@ -147,6 +149,8 @@ struct us_sim {
   ussim::DevProbe* d_probes = nullptr;
   ussim::DevPair* d_pairs = nullptr;
   std::vector<uint8_t*> d_pair_D;
+  std::vector<uint4*> d_hu8;   // corner records per volume (null entries: not built)
+  std::vector<ussim::DevVolume> dev_vols;
 
   ussim::PlainScratch scratch;
   unsigned* d_err = nullptr;

@@ -108,6 +108,8 @@ class Options:
     speckle_anchor: 0 = scatter maps keyed by (env, line, sample, step);
     1 = fixed maps over the volume (they move with the tissue), with
     speckle_levels scales (1-3) of cells of edge speckle_cell_mm * 2^k.
+    volume_layout: memory layout of the HU grid on the GPU (0 = corner
+    records, 1 = the grid as given); it does not change the images.
     """
     refl_power: int = 1
     transmission: int = 1
@@ -116,6 +118,7 @@ class Options:
     speckle_anchor: int = 0
     speckle_levels: int = 1
     speckle_cell_mm: float = 0.25
+    volume_layout: int = 0
 
 
 # --------------------------------------------------------------------------

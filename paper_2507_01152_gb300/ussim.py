@@ -48,7 +48,7 @@ class us_probe(C.Structure):
 class us_options(C.Structure):
     _fields_ = [("refl_power", C.c_int32), ("transmission", C.c_int32), ("z_mode", C.c_int32),
                 ("speckle", C.c_int32), ("speckle_anchor", C.c_int32), ("speckle_levels", C.c_int32),
-                ("speckle_cell_mm", C.c_float)]
+                ("speckle_cell_mm", C.c_float), ("volume_layout", C.c_int32)]
 
 
 class us_env(C.Structure):
@@ -72,6 +72,7 @@ SIGNATURES = {
     "us_sim_create": (C.c_int, [C.POINTER(us_volume), C.c_int32, C.POINTER(us_tissue), C.c_int32,
                                 C.POINTER(us_probe), C.c_int32, C.POINTER(us_options), C.POINTER(_P)]),
     "us_sim_destroy": (None, [_P]),
+    "us_sim_refresh_volumes": (C.c_int, [_P, _P]),
     "us_sim_frame_layout": (C.c_int, [_P, _P, C.c_int32, _P]),
     "us_sim_beam_layout": (C.c_int, [_P, _P, C.c_int32, _P]),
     "us_sim_render": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
@@ -214,7 +215,7 @@ class Sim:
         if options is not None:
             opt = us_options(options.refl_power, options.transmission, options.z_mode, options.speckle,
                              getattr(options, "speckle_anchor", 0), getattr(options, "speckle_levels", 1),
-                             getattr(options, "speckle_cell_mm", 0.25))
+                             getattr(options, "speckle_cell_mm", 0.25), getattr(options, "volume_layout", 0))
         h = C.c_void_p()
         st = L.us_sim_create(vols, len(volumes), tab, len(table), prs, len(probes),
                              C.byref(opt) if opt is not None else None, C.byref(h))
@@ -325,6 +326,11 @@ class Sim:
 
     def check(self, stream=None):
         self._check(self._lib.us_sim_check(self.h, _stream_handle(stream)))
+
+    def refresh_volumes(self, stream=None):
+        """Re-read the volumes after their contents changed (label check,
+        corner layout of the HU grid); synchronous."""
+        self._check(self._lib.us_sim_refresh_volumes(self.h, _stream_handle(stream)))
 
     def render_gated(self, envs, poses, seed, step, frames, score, threshold, n_rendered=None, stream=None,
                      envs_c=None):
