@@ -140,31 +140,48 @@ __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(Ren
   if (!cx.finite && group == 0 && tid == 0) atomicOr(p.err, kErrNonFinitePose);
   __syncthreads();
 
-  // labels of lines L0 .. L1-1; impedance of own lines g0 .. g1-1
-  for (int i = warp; i < L1 - L0; i += NW) {
-    const int l = L0 + i;
-    const bool own = l >= g0 && l < g1;
-    const float2 ln = P.lines[l];
-    uint8_t* lrow = lbuf + i * NS;
-    float* zrow = own ? zbuf + (l - g0) * RS + KA : nullptr;
+  // labels and impedance of own lines g0 .. g1-1 (one line per warp), then
+  // the halo lines' labels in 32-sample chunks spread over the warps: a line
+  // d lines beyond the group is labelled only below ext[d], the stencil's
+  // reach, so the short halo lines do not load a few warps
+  auto label_of = [&](int l, int s, float3& u, int& vi) -> uint8_t {
+    float x, z;
+    beam_point(P, P.lines[l], s, x, z);
+    u = to_voxel(cx.M, cx.V.inv_h, x, z);
+    vi = nearest_voxel(cx.V, u);
+    return vi >= 0 ? __ldg(&cx.V.labels[vi]) : (uint8_t)0;
+  };
+  for (int l = g0 + warp; l < g1; l += NW) {
+    uint8_t* lrow = lbuf + (l - L0) * NS;
+    float* prow = zbuf + (l - g0) * RS;
     for (int s = lane; s < NS; s += 32) {
-      float x, z;
-      beam_point(P, ln, s, x, z);
-      const float3 u = to_voxel(cx.M, cx.V.inv_h, x, z);
-      const int vi = nearest_voxel(cx.V, u);
-      const uint8_t lb = vi >= 0 ? __ldg(&cx.V.labels[vi]) : (uint8_t)0;
+      float3 u;
+      int vi;
+      const uint8_t lb = label_of(l, s, u, vi);
       lrow[s] = lb;
-      if (own) {
-        zrow[s] = p.z_mode == 0 ? fmaxf(trilinear_hu(cx.V, u) + 1024.f, 1.f) : tis[lb].z;
-        if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + s] = vi;
-        if (p.label) p.label[cx.it.beam_off + (long long)l * NS + s] = lb;
+      prow[KA + s] = p.z_mode == 0 ? fmaxf(trilinear_hu(cx.V, u) + 1024.f, 1.f) : tis[lb].z;
+      if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + s] = vi;
+      if (p.label) p.label[cx.it.beam_off + (long long)l * NS + s] = lb;
+    }
+    for (int q = lane; q < KA; q += 32) {
+      prow[q] = 0.f;
+      prow[KA + NS + q] = 0.f;
+    }
+  }
+  {
+    const int nl_left = g0 - L0, nh = nl_left + (L1 - g1), cpl = (NS + 31) >> 5;
+    for (int t = warp; t < nh * cpl; t += NW) {
+      const int c = t / nh, h = t - c * nh;
+      const int l = h < nl_left ? L0 + h : g1 + (h - nl_left);
+      const int lim = cx.pair.ext[l < g0 ? g0 - l : l - g1 + 1];
+      if ((c << 5) >= lim) continue;   // whole warp
+      const int s = (c << 5) + lane;
+      if (s < lim) {
+        float3 u;
+        int vi;
+        lbuf[(l - L0) * NS + s] = label_of(l, s, u, vi);
       }
     }
-    if (own)
-      for (int q = lane; q < KA; q += 32) {
-        zrow[q - KA] = 0.f;
-        zrow[NS + q] = 0.f;
-      }
   }
   __syncthreads();
 

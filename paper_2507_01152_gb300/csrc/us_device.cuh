@@ -59,6 +59,10 @@ struct DevPair {
   int W;
   const uint8_t* D;
   int dmax;   // max over samples of D: the stencil's lateral reach for this pair
+  // ext[d], d = 1..dmax: the stencil reads a line d lines away from the
+  // line it serves only at samples below ext[d] (the window's end past the
+  // deepest sample s with D[s] >= d)
+  int ext[kThetaDMax + 1];
 };
 
 // one environment of a batch, in processing order

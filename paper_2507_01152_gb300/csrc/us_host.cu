@@ -645,7 +645,14 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
         return cuda_fail(nullptr, e, "pairs");
       }
       s->d_pair_D.push_back(dD);
-      pairs.push_back(DevPair{W, dD, D.empty() ? 1 : (int)*std::max_element(D.begin(), D.end())});
+      DevPair pr{W, dD, D.empty() ? 1 : (int)*std::max_element(D.begin(), D.end()), {}};
+      for (int d = 0; d <= kThetaDMax; ++d) {
+        int deepest = -1;
+        for (int q = 0; q < (int)D.size(); ++q)
+          if (D[q] >= d) deepest = q;
+        pr.ext[d] = deepest < 0 ? 0 : std::min((int)D.size(), deepest + W + 1);
+      }
+      pairs.push_back(pr);
     }
   size_t max_beam = 0;
   for (const ProbeHost& ph : s->probes) max_beam = std::max(max_beam, (size_t)ph.desc.n_lines * ph.desc.n_samples);
