@@ -225,18 +225,25 @@ __device__ __forceinline__ float impedance(int z_mode, float hu, const DevTissue
 // the label slice: M(l') counts the samples of the window s-W+1..s+W on
 // line l' that carry the label below the boundary; the shift of that count
 // between lines l-D and l+D gives the boundary's slope.  LabFn(line, s)
-// returns the nearest label of a beam sample.
+// returns the nearest label of a beam sample.  Evaluated by a whole warp
+// for one boundary (s, l, W, D, dlat the same in every lane): lane i tests
+// window positions i, i + 32, ..., and ballots add up the matches.  Every
+// lane returns the cosine.
 template <class LabFn>
-__device__ __forceinline__ float incidence_cos(LabFn lab, int l, int s, int NL, int NS, int W, int D,
-                                               float dr, float dlat) {
+__device__ __forceinline__ float incidence_cos_warp(LabFn lab, int l, int s, int NL, int NS, int W, int D,
+                                                    float dr, float dlat, int lane) {
   const unsigned below = lab(l, s + 1);
   const int lp = min(l + D, NL - 1), lm = max(l - D, 0);
-  int dM = 0;
-  for (int q = s - W + 1; q <= s + W; ++q) {
-    const int qc = min(max(q, 0), NS - 1);
-    dM += (int)(lab(lp, qc) == below) - (int)(lab(lm, qc) == below);
-  }
   if (lp <= lm) return 1.f;
+  int dM = 0;
+  for (int q0 = s - W + 1; q0 <= s + W; q0 += 32) {
+    const int q = q0 + lane;
+    const int qc = min(max(q, 0), NS - 1);
+    const bool in = q <= s + W;
+    const unsigned up = __ballot_sync(0xffffffffu, in && lab(lp, qc) == below);
+    const unsigned dn = __ballot_sync(0xffffffffu, in && lab(lm, qc) == below);
+    dM += __popc(up) - __popc(dn);
+  }
   const float t = fabsf((float)dM) * dr / ((float)(lp - lm) * dlat);
   return rsqrtf(fmaf(t, t, 1.f));
 }

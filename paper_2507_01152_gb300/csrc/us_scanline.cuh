@@ -60,9 +60,22 @@ __device__ __forceinline__ void scanline_model(const RenderParams& p, const DevP
     const float ra = sa < NS - 1 ? __fdividef(z1 - z0, z1 + z0) : 0.f;
     const float rb = sb < NS - 1 ? __fdividef(zc - z1, zc + z1) : 0.f;
 
+    // boundaries are sparse: the warp takes them one at a time, all lanes
+    // on the window of each (lane src's a sample is c + 2 src, b sample + 1)
     float cosa = 1.f, cosb = 1.f;
-    if (Ga) cosa = incidence_cos(lab, l, sa, NL, NS, pair.W, pair.D[sa], P.dr, lateral_spacing(P, sa));
-    if (Gb) cosb = incidence_cos(lab, l, sb, NL, NS, pair.W, pair.D[sb], P.dr, lateral_spacing(P, sb));
+    {
+      const unsigned ma = __ballot_sync(kFull, Ga), mb = __ballot_sync(kFull, Gb);
+      for (unsigned k = ma; k; k &= k - 1) {
+        const int src = __ffs(k) - 1, s = c + 2 * src;
+        const float v = incidence_cos_warp(lab, l, s, NL, NS, pair.W, pair.D[s], P.dr, lateral_spacing(P, s), lane);
+        if (lane == src) cosa = v;
+      }
+      for (unsigned k = mb; k; k &= k - 1) {
+        const int src = __ffs(k) - 1, s = c + 2 * src + 1;
+        const float v = incidence_cos_warp(lab, l, s, NL, NS, pair.W, pair.D[s], P.dr, lateral_spacing(P, s), lane);
+        if (lane == src) cosb = v;
+      }
+    }
 
     const DevTissue ta = T[la], tb = T[lb];
     float inc_a = sa < NS ? -ta.att : 0.f;
