@@ -66,6 +66,8 @@ __device__ __forceinline__ void axial_psf_row(float* prow, int NS, const float* 
 
 __device__ __forceinline__ void axial_psf_any(float* prow, int NS, const float* w, int K, int lane) {
   switch (K) {
+    case 1: axial_psf_row<1>(prow, NS, w, K, lane); break;
+    case 2: axial_psf_row<2>(prow, NS, w, K, lane); break;
     case 3: axial_psf_row<3>(prow, NS, w, K, lane); break;
     case 4: axial_psf_row<4>(prow, NS, w, K, lane); break;
     case 5: axial_psf_row<5>(prow, NS, w, K, lane); break;
@@ -74,6 +76,69 @@ __device__ __forceinline__ void axial_psf_any(float* prow, int NS, const float* 
     case 8: axial_psf_row<8>(prow, NS, w, K, lane); break;
     default: axial_psf_row<0>(prow, NS, w, K, lane); break;
   }
+}
+
+// Lateral PSF and log compression of rows w0 .. y1-1 of a wedge (pass B),
+// four lines per thread: abuf holds the staged filtered rows from w0 - K on
+// (zero rows outside the frame and past the last needed row), ybuf receives
+// the log image.  Each line's taps are summed in increasing line order.
+// KC > 0: K is the compile-time KC and the taps sit in registers; each
+// staged row is read once and added into the (up to) four sums it reaches,
+// in the same order.  KC = 0: any K, taps read from shared memory.
+template <int KC>
+__device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProbe& P, long long beam_off,
+                                            const float* abuf, float* ybuf, const float* wlat, int NS, int K, int w0,
+                                            int w1, int y1) {
+  const int ng = (y1 - w0 + 3) >> 2;
+  const int taps = 2 * K + 1;
+  constexpr int TC = 2 * KC + 1;
+  float wr[KC > 0 ? TC : 1];
+#pragma unroll
+  for (int q = 0; q < (KC > 0 ? TC : 0); ++q) wr[q] = wlat[q];
+  for (int t = threadIdx.x; t < ng * NS; t += blockDim.x) {
+    const int gi = t / NS, s = t - gi * NS, i0 = 4 * gi;
+    const float* col = abuf + i0 * NS + s;     // row of line w0 + i0 + j, tap q: i0 + j + q
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if constexpr (KC > 0) {
+#pragma unroll
+      for (int r = 0; r < TC + 3; ++r) {
+        const float v = col[r * NS];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (r - j >= 0 && r - j < TC) acc[j] = fmaf(wr[r - j], v, acc[j]);
+      }
+    } else {
+      for (int q = 0; q < taps; ++q) {
+        const float w = wlat[q];
+        const float* c = col + q * NS;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = fmaf(w, c[j * NS], acc[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = i0 + j, l = w0 + i;
+      if (l >= y1) break;
+      const float y = log_compress(P, acc[j]);
+      ybuf[i * NS + s] = y;
+      if (l < w1) {
+        if (p.envelope) p.envelope[beam_off + (long long)l * NS + s] = acc[j];
+        if (p.logimg) p.logimg[beam_off + (long long)l * NS + s] = y;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void lateral_psf_any(const RenderParams& p, const DevProbe& P, long long beam_off,
+                                                const float* abuf, float* ybuf, const float* wlat, int NS, int K,
+                                                int w0, int w1, int y1) {
+#define US_LAT(k) \
+  case k: lateral_psf<k>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1); break;
+  switch (K) {
+    US_LAT(2) US_LAT(3) US_LAT(4) US_LAT(5) US_LAT(6) US_LAT(7) US_LAT(8) US_LAT(9) US_LAT(10) US_LAT(11) US_LAT(12)
+    default: lateral_psf<0>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1); break;
+  }
+#undef US_LAT
 }
 
 struct SplitCtx {
@@ -269,37 +334,7 @@ __global__ void __launch_bounds__(G * 32, G == 32 ? 1 : 2) split_image(RenderPar
   }
   __syncthreads();
 
-  // lateral PSF and log compression of rows w0 .. y1-1, four lines per
-  // thread; each line's taps are summed in increasing line order
-  {
-    const int ng = (y1 - w0 + 3) >> 2;
-    const int taps = 2 * KL + 1;
-    for (int t = tid; t < ng * NS; t += blockDim.x) {
-      const int gi = t / NS, s = t - gi * NS, i0 = 4 * gi;
-      const float* col = abuf + i0 * NS + s;     // row of line w0 + i0 + j, tap q: i0 + j + q
-      float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-      for (int q = 0; q < taps; ++q) {
-        const float w = wlat[q];
-        const float* c = col + q * NS;
-        acc0 = fmaf(w, c[0], acc0);
-        acc1 = fmaf(w, c[NS], acc1);
-        acc2 = fmaf(w, c[2 * NS], acc2);
-        acc3 = fmaf(w, c[3 * NS], acc3);
-      }
-      const float accs[4] = {acc0, acc1, acc2, acc3};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int i = i0 + j, l = w0 + i;
-        if (l >= y1) break;
-        const float y = log_compress(P, accs[j]);
-        ybuf[i * NS + s] = y;
-        if (l < w1) {
-          if (p.envelope) p.envelope[cx.it.beam_off + (long long)l * NS + s] = accs[j];
-          if (p.logimg) p.logimg[cx.it.beam_off + (long long)l * NS + s] = y;
-        }
-      }
-    }
-  }
+  lateral_psf_any(p, P, cx.it.beam_off, abuf, ybuf, wlat, NS, KL, w0, w1, y1);
   __syncthreads();
 
   float* out = p.frames + cx.it.frame_off;
