@@ -78,31 +78,34 @@ __device__ __forceinline__ void axial_psf_any(float* prow, int NS, const float* 
   }
 }
 
-// Lateral PSF and log compression of rows w0 .. y1-1 of a wedge (pass B),
-// four lines per thread: abuf holds the staged filtered rows from w0 - K on
-// (zero rows outside the frame and past the last needed row), ybuf receives
-// the log image.  Each line's taps are summed in increasing line order.
+// Lateral PSF and log compression of rows w0 .. y1-1 of a pass-B tile over
+// samples s0 .. s0 + kChunk, four lines per thread: abuf holds the staged
+// filtered rows from w0 - K on (zero rows outside the frame and past the
+// last needed row), ybuf receives the log image; rows of kRowStride
+// floats, of which the first kChunk + 1 are the tile's samples and one more.  Each line's taps are summed in increasing line order.
 // KC > 0: K is the compile-time KC and the taps sit in registers; each
 // staged row is read once and added into the (up to) four sums it reaches,
 // in the same order.  KC = 0: any K, taps read from shared memory.
 template <int KC>
 __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProbe& P, long long beam_off,
                                             const float* abuf, float* ybuf, const float* wlat, int NS, int K, int w0,
-                                            int w1, int y1) {
+                                            int w1, int y1, int s0) {
+  constexpr int NC = kChunk + 1;   // columns: the tile's samples and one more
   const int ng = (y1 - w0 + 3) >> 2;
   const int taps = 2 * K + 1;
+  const int se = min(s0 + kChunk, NS);   // samples this tile exports
   constexpr int TC = 2 * KC + 1;
   float wr[KC > 0 ? TC : 1];
 #pragma unroll
   for (int q = 0; q < (KC > 0 ? TC : 0); ++q) wr[q] = wlat[q];
-  for (int t = threadIdx.x; t < ng * NS; t += blockDim.x) {
-    const int gi = t / NS, s = t - gi * NS, i0 = 4 * gi;
-    const float* col = abuf + i0 * NS + s;     // row of line w0 + i0 + j, tap q: i0 + j + q
+  for (int t = threadIdx.x; t < ng * NC; t += blockDim.x) {
+    const int gi = t / NC, c = t - gi * NC, i0 = 4 * gi;
+    const float* col = abuf + i0 * kRowStride + c;     // row of line w0 + i0 + j, tap q: i0 + j + q
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     if constexpr (KC > 0) {
 #pragma unroll
       for (int r = 0; r < TC + 3; ++r) {
-        const float v = col[r * NS];
+        const float v = col[r * kRowStride];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (r - j >= 0 && r - j < TC) acc[j] = fmaf(wr[r - j], v, acc[j]);
@@ -110,9 +113,9 @@ __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProb
     } else {
       for (int q = 0; q < taps; ++q) {
         const float w = wlat[q];
-        const float* c = col + q * NS;
+        const float* cp = col + q * kRowStride;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = fmaf(w, c[j * NS], acc[j]);
+        for (int j = 0; j < 4; ++j) acc[j] = fmaf(w, cp[j * kRowStride], acc[j]);
       }
     }
 #pragma unroll
@@ -120,8 +123,9 @@ __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProb
       const int i = i0 + j, l = w0 + i;
       if (l >= y1) break;
       const float y = log_compress(P, acc[j]);
-      ybuf[i * NS + s] = y;
-      if (l < w1) {
+      ybuf[i * kRowStride + c] = y;
+      const int s = s0 + c;
+      if (l < w1 && s < se) {
         if (p.envelope) p.envelope[beam_off + (long long)l * NS + s] = acc[j];
         if (p.logimg) p.logimg[beam_off + (long long)l * NS + s] = y;
       }
@@ -131,12 +135,12 @@ __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProb
 
 __device__ __forceinline__ void lateral_psf_any(const RenderParams& p, const DevProbe& P, long long beam_off,
                                                 const float* abuf, float* ybuf, const float* wlat, int NS, int K,
-                                                int w0, int w1, int y1) {
+                                                int w0, int w1, int y1, int s0) {
 #define US_LAT(k) \
-  case k: lateral_psf<k>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1); break;
+  case k: lateral_psf<k>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1, s0); break;
   switch (K) {
     US_LAT(2) US_LAT(3) US_LAT(4) US_LAT(5) US_LAT(6) US_LAT(7) US_LAT(8) US_LAT(9) US_LAT(10) US_LAT(11) US_LAT(12)
-    default: lateral_psf<0>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1); break;
+    default: lateral_psf<0>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1, s0); break;
   }
 #undef US_LAT
 }
@@ -273,91 +277,90 @@ __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(Ren
   }
 }
 
-template <int G>
-__global__ void __launch_bounds__(G * 32, G == 32 ? 1 : 2) split_image(RenderParams p, SplitArgs a) {
+// Pass B tile: GB lines x kChunk samples of one environment.  The block
+// stages the filtered lines of its lines (plus one for the bilinear step
+// and the lateral PSF's reach) over its samples plus one, forms the log
+// image there and writes the pixels whose bilinear base (line, sample)
+// falls in the tile.
+template <int GB>
+__global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, SplitArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ SplitCtx cx;
-  int group;
-  if (!split_item(p, a.gpi_image, G, cx, group)) return;
-  const DevProbe& P = cx.P;
+  // every thread reads its item and probe (the same addresses: broadcast
+  // loads); no block-wide set-up
+  const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
+  const int item = blockIdx.x / a.gpi_image, tile = blockIdx.x - item * a.gpi_image;
+  if (item >= n_items) return;
+  const EnvItem it = p.items[item];
+  const DevProbe& P = p.probes[it.probe];
   const int NL = P.nl, NS = P.ns, KL = P.k_lat;
-  const int w0 = group * G, w1 = min(w0 + G, NL);
+  const int nchunk = (NS + kChunk - 1) / kChunk;
+  const int q = tile / nchunk, k = tile - q * nchunk;
+  const int w0 = q * GB, w1 = min(w0 + GB, NL);
+  if (w0 >= NL) return;   // past this probe's tiles (uniform)
   const int y1 = min(w1 + 1, NL);                                    // log rows w0 .. y1-1
-  // staged filtered rows r0 = w0 - KL .. w0 + nrows - 1, with zero rows
-  // outside the frame and past the last needed row, so that the lateral
+  const int s0 = k * kChunk, sw = min(kChunk + 1, NS - s0);          // staged samples s0 .. s0+sw-1
+  // staged rows r0 = w0 - KL .. r0 + nrows - 1, zero outside the frame,
+  // past the last needed row and past the line's end, so that the lateral
   // PSF needs no edge tests (adding w * 0 leaves a sum unchanged exactly:
   // the sums never hold -0)
   const int r0 = w0 - KL;
   const int nrows = (((y1 - w0) + 3) & ~3) + 2 * KL;
   const int a0 = max(r0, 0), a1 = min(y1 + KL, NL);                  // rows present in the line buffer
   const int tid = threadIdx.x;
-  float* abuf = reinterpret_cast<float*>(smem);                      // [nrows][NS]
-  float* ybuf = reinterpret_cast<float*>(smem + a.off_y);            // [y1 - w0][NS]
+  float* abuf = reinterpret_cast<float*>(smem);                      // [nrows][kRowStride]
+  float* ybuf = reinterpret_cast<float*>(smem + a.off_y);            // [y1 - w0][kRowStride]
   float* wlat = reinterpret_cast<float*>(smem + a.off_wlat);
-  for (int t = tid; t < 2 * KL + 1; t += blockDim.x) wlat[t] = __ldg(&P.w_lat[t]);
-  for (int t = tid; t < (a0 - r0) * NS; t += blockDim.x) abuf[t] = 0.f;
-  for (int t = (a1 - r0) * NS + tid; t < nrows * NS; t += blockDim.x) abuf[t] = 0.f;
+  for (int t = tid; t < 2 * KL + 1; t += kImageThreads) wlat[t] = __ldg(&P.w_lat[t]);
   {
-    // the present rows are one contiguous range of the line buffer: one
-    // bulk asynchronous copy when it is 16-byte aligned, else plain loads
-    const float* src = a.beam + cx.it.beam_off + (long long)a0 * NS;
-    float* dst = abuf + (a0 - r0) * NS;
-    const int n = (a1 - a0) * NS;
-    __shared__ uint64_t bar;
-    __shared__ int landed;
-    const bool bulk = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) &&
-                      (n & 3) == 0;
-    if (bulk) {
-      // one thread issues the copy and waits for it (bounded); the block
-      // barrier then publishes the rows to every thread
-      if (tid == 0) {
-        umma::mbar_init(&bar, 1);
-        umma::mbar_init_fence();
-        umma::mbar_arrive_expect_tx(&bar, (uint32_t)n * 4u);
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                umma::smem_u32(dst)),
-            "l"(src), "r"((uint32_t)n * 4u), "r"(umma::smem_u32(&bar))
-            : "memory");
-        landed = umma::mbar_wait(&bar, 0) ? 1 : 0;
-        if (!landed) {
-          // report, and do not leave while the copy may still be writing
-          atomicOr(p.err, kErrStagingTimeout);
-          umma::mbar_wait(&bar, 0);
-        }
+    const float* src = a.beam + it.beam_off + s0;
+    constexpr int PPR = kRowStride / 4;                              // 16-byte pieces per row
+    if ((NS & 3) == 0 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
+      // asynchronous 16-byte copies, zero-filled past the row's end and
+      // for rows outside the frame
+      for (int t = tid; t < nrows * PPR; t += kImageThreads) {
+        const int r = t / PPR, c = (t - r * PPR) * 4;
+        const int line = r0 + r;
+        const bool present = line >= a0 && line < a1 && c < sw;
+        const float* g = present ? src + (long long)line * NS + c : a.beam;
+        umma::cp_async16(abuf + r * kRowStride + c, g, present ? 16u : 0u);
       }
-      __syncthreads();
-      if (!landed) return;
+      umma::cp_async_commit();
+      umma::cp_async_wait<0>();
     } else {
-      for (int t = tid; t < n; t += blockDim.x) dst[t] = __ldcg(src + t);
+      for (int t = tid; t < nrows * kRowStride; t += kImageThreads) {
+        const int r = t / kRowStride, c = t - r * kRowStride;
+        const int line = r0 + r;
+        abuf[t] = line >= a0 && line < a1 && c < sw ? __ldcg(src + (long long)line * NS + c) : 0.f;
+      }
     }
   }
   __syncthreads();
 
-  lateral_psf_any(p, P, cx.it.beam_off, abuf, ybuf, wlat, NS, KL, w0, w1, y1);
+  lateral_psf_any(p, P, it.beam_off, abuf, ybuf, wlat, NS, KL, w0, w1, y1, s0);
   __syncthreads();
 
-  float* out = p.frames + cx.it.frame_off;
+  float* out = p.frames + it.frame_off;
+  const int se = min(s0 + kChunk, NS);
   if (P.kind == 0) {
-    const int n = NS * (w1 - w0), wl = w1 - w0;
-    for (int t = tid; t < n; t += blockDim.x) {
+    const int wl = w1 - w0, n = (se - s0) * wl;
+    for (int t = tid; t < n; t += kImageThreads) {
       const int s = t / wl, j = t - s * wl;
-      __stcs(&out[(long long)s * NL + w0 + j], ybuf[j * NS + s]);
+      __stcs(&out[(long long)(s0 + s) * NL + w0 + j], ybuf[j * kRowStride + s]);
     }
   } else {
-    const int e0 = P.wedge_off[group], e1 = P.wedge_off[group + 1];
-    for (int e = e0 + tid; e < e1; e += blockDim.x) {
-      const float4 q = __ldg(&P.wedge[e]);
-      const int pix = __float_as_int(q.x);
-      const float fl = q.y, fs = q.z;
+    const int e0 = P.wedge_off[tile], e1 = P.wedge_off[tile + 1];
+    for (int e = e0 + tid; e < e1; e += kImageThreads) {
+      const float4 qv = __ldg(&P.wedge[e]);
+      const int pix = __float_as_int(qv.x);
+      const float fl = qv.y, fs = qv.z;
       float v = 0.f;
       if (fl >= 0.f) {
         const int la = min((int)fl, NL - 2), sa = min((int)fs, NS - 2);
         const float al = fl - (float)la, bb = fs - (float)sa;
-        const float* r0 = ybuf + (la - w0) * NS;
-        const float* r1 = r0 + NS;
-        const float y00 = r0[sa], y01 = r0[sa + 1];
-        const float y10 = r1[sa], y11 = r1[sa + 1];
+        const float* r0p = ybuf + (la - w0) * kRowStride + (sa - s0);
+        const float* r1p = r0p + kRowStride;
+        const float y00 = r0p[0], y01 = r0p[1];
+        const float y10 = r1p[0], y11 = r1p[1];
         const float top = fmaf(al, y10 - y00, y00), bot = fmaf(al, y11 - y01, y01);
         v = fmaf(bb, bot - top, top);
       }
@@ -390,22 +393,24 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
   off = up(off + lab, 16);
   sh.smem_lines = (size_t)off;
   if (sh.smem_lines > lim) return false;
-  // pass B: the widest wedge whose staged rows and log rows fit
+  // pass B: the widest wedge whose staged rows and log rows (kChunk + 1
+  // samples each) fit four blocks per SM, else two, else one
+  for (int per_sm : {4, 2, 1})
   for (int GB : {32, 16, 8}) {
     long long ab = 0, yb = 0;
     int gi = 0;
     for (const ProbeHost& ph : probes) {
       const int NL = ph.desc.n_lines, NS = ph.desc.n_samples;
-      ab = std::max(ab, (long long)(((std::min(NL, GB + 1) + 3) & ~3) + 2 * ph.k_lat) * NS * 4);
-      yb = std::max(yb, (long long)std::min(NL, GB + 1) * NS * 4);
-      gi = std::max(gi, (NL + GB - 1) / GB);
+      ab = std::max(ab, (long long)(((std::min(NL, GB + 1) + 3) & ~3) + 2 * ph.k_lat) * kRowStride * 4);
+      yb = std::max(yb, (long long)std::min(NL, GB + 1) * kRowStride * 4);
+      gi = std::max(gi, ((NL + GB - 1) / GB) * ((NS + kChunk - 1) / kChunk));
     }
     long long o = up(ab, 16);
     const int off_y = (int)o;
     o = up(o + yb, 16);
     const int off_wlat = (int)o;
     o = up(o + 4 * (2 * kMaxHalfTaps + 1), 16);
-    if ((size_t)o <= lim) {
+    if ((size_t)o <= std::min(lim, (size_t)(228 * 1024) / per_sm - 1024 - 64)) {
       sh.GB = GB;
       sh.smem_image = (size_t)o;
       sh.args.off_y = off_y;
@@ -452,7 +457,7 @@ static void launch_g(const RenderParams& p, const SplitShape& sh, const SplitArg
   else if (pass == 0)
     split_lines<G, false><<<(unsigned)(max_items * a.gpi_lines), G * 32, sh.smem_lines, st>>>(p, a);
   else
-    split_image<G><<<(unsigned)(max_items * a.gpi_image), G * 32, sh.smem_image, st>>>(p, a);
+    split_image<G><<<(unsigned)(max_items * a.gpi_image), kImageThreads, sh.smem_image, st>>>(p, a);
 }
 
 cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, int pass,
@@ -473,36 +478,38 @@ cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* bea
   return e == cudaSuccess ? launch_split_pass(p, sh, beam, max_items, 1, st) : e;
 }
 
-// Pixels of a curvilinear probe's output grid, grouped by wedge of G lines:
-// a pixel inside the fan belongs to the wedge of its bilinear base line
-// min(floor(fl), NL - 2); a pixel outside the fan to the wedge of the
-// preceding inside pixel of its row (wedge 0 if none).  Along a row the
-// base line never decreases, so the wedges' pixels form row segments.
-void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int G, std::vector<float4>& entries,
+// Pixels of a curvilinear probe's output grid, grouped by pass-B tile
+// (wedge of G lines x chunk of kChunk samples), tile = wedge * chunks +
+// chunk: a pixel inside the fan belongs to the tile of its bilinear base
+// (min(floor(fl), NL - 2), min(floor(fs), NS - 2)); a pixel outside the
+// fan to the tile of the preceding inside pixel of its row (tile 0 if
+// none).  Within a tile, pixels keep raster order.
+void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int NS, int G, std::vector<float4>& entries,
                   std::vector<int>& off) {
-  const int nq = (NL + G - 1) / G;
-  std::vector<std::vector<float4>> per(nq);
+  const int nchunk = (NS + kChunk - 1) / kChunk;
+  const int nt = ((NL + G - 1) / G) * nchunk;
+  std::vector<std::vector<float4>> per(nt);
   for (int r = 0; r < H; ++r) {
-    int q = 0;
+    int t = 0;
     for (int c = 0; c < W; ++c) {
       const float2 f = lut[(size_t)r * W + c];
-      if (f.x >= 0.f) q = std::min((int)f.x, NL - 2) / G;
+      if (f.x >= 0.f) t = (std::min((int)f.x, NL - 2) / G) * nchunk + std::min((int)f.y, NS - 2) / kChunk;
       const int pix = r * W + c;
       float4 e;
       std::memcpy(&e.x, &pix, sizeof pix);
       e.y = f.x;
       e.z = f.y;
       e.w = 0.f;
-      per[q].push_back(e);
+      per[t].push_back(e);
     }
   }
   entries.clear();
-  off.assign(nq + 1, 0);
-  for (int q = 0; q < nq; ++q) {
-    off[q] = (int)entries.size();
-    entries.insert(entries.end(), per[q].begin(), per[q].end());
+  off.assign(nt + 1, 0);
+  for (int t = 0; t < nt; ++t) {
+    off[t] = (int)entries.size();
+    entries.insert(entries.end(), per[t].begin(), per[t].end());
   }
-  off[nq] = (int)entries.size();
+  off[nt] = (int)entries.size();
 }
 
 }  // namespace ussim

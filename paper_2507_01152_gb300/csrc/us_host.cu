@@ -386,7 +386,7 @@ us_status apply_split(us_sim* s, const us_tuning& t) {
     if (ph.desc.kind != 1 || ph.wedge_G == sh.GB) continue;
     std::vector<float4> ent;
     std::vector<int> off;
-    build_wedges(ph.lut_host, ph.desc.out_w, ph.desc.out_h, ph.desc.n_lines, sh.GB, ent, off);
+    build_wedges(ph.lut_host, ph.desc.out_w, ph.desc.out_h, ph.desc.n_lines, ph.desc.n_samples, sh.GB, ent, off);
     cudaFree(ph.d_wedge);
     cudaFree(ph.d_wedge_off);
     ph.d_wedge = nullptr;

@@ -70,6 +70,10 @@ cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_
 
 // two-pass path: lines per pass-A block G and per pass-B wedge GB (8, 16,
 // 32), shared-memory layouts of both passes, blocks per item of each pass
+// pass B tiles: GB lines x kChunk samples, kImageThreads threads per block
+constexpr int kChunk = 128;
+constexpr int kImageThreads = 256;
+constexpr int kRowStride = kChunk + 4;   // shared row stride, floats (16-byte rows)
 struct SplitArgs {
   float* beam = nullptr;   // axially filtered lines, beam layout (per item beam_off)
   int G = 32, GB = 32, gpi_lines = 0, gpi_image = 0;
@@ -90,7 +94,7 @@ cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* bea
 // one pass: 0 = lines (pass A), 1 = image (pass B)
 cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, int pass,
                               cudaStream_t st);
-void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int G, std::vector<float4>& entries,
+void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int NS, int G, std::vector<float4>& entries,
                   std::vector<int>& off);
 
 // items with score > thr, in batch order, and their count (device)

@@ -368,14 +368,12 @@ def test_3d_probe_sweep_equals_2d_renders_and_oracle():
     assert np.abs(swept[1, :, 3] - swept[0, :, 3]).sum() > 9.0       # slices 10 mm apart
 
 
-def test_maximum_probe_sizes_and_shapes_that_do_not_fit():
+def test_maximum_probe_sizes_and_widest_psf():
     """Probes of the maximum size (1024 lines x 1024 samples, 1024 x 1024
     output) render through the batched path, bit-identical to the plain
-    kernels and within the parity bar of the oracle.  A probe whose lateral
-    PSF is too wide for any batched shape's shared memory still renders
-    through the plain path, while the batched entry point reports
-    US_ERR_UNSUPPORTED."""
-    from paper_2507_01152_gb300.ussim import UsError, US_ERR_UNSUPPORTED
+    kernels and within the parity bar of the oracle; so does a maximum-size
+    probe with a 48-line lateral PSF reach on either side (pass B stages
+    its rows in sample chunks, so every valid probe has a batched shape)."""
     spec = scene.c1_spec()
     lab, hu = scene.make_volume(spec)
     probes = [scene.linear_probe(1024, 1024, 100.0, 0.25),
@@ -391,14 +389,13 @@ def test_maximum_probe_sizes_and_shapes_that_do_not_fit():
             assert np.array_equal(x[k], y[k]), k
     o = render_oracle(wl, envs, poses, wl.seed, 0, [0, 1])
     _check_all(g, o, probes, envs, [0, 1])
-    # 1024 lines of 1024 samples with a 48-line lateral reach on either side:
-    # too much for the cluster kernel's per-CTA lines and for pass B's staging
     wide = [scene.linear_probe(1024, 1024, 100.0, 0.1, psf_sigma_lat_mm=1.6)]
     wl2 = scene.Workload("wide", [(spec, lab, hu)], wide, envs[:1] * 0, poses[:1], seed=12)
     sim2 = gpu_sim(wl2)
-    with pytest.raises(UsError) as e:
-        render_gpu(sim2, wl2.envs, poses[:1], 12, 0, debug=False)
-    assert e.value.status == US_ERR_UNSUPPORTED
+    assert sim2.get_tuning()["cluster_size"] == 1          # two-pass shape found
+    gw = render_gpu(sim2, wl2.envs, poses[:1], 12, 0, path=0)
     q = render_gpu(sim2, wl2.envs, poses[:1], 12, 0, path=1)
+    for k in q[0]:
+        assert np.array_equal(gw[0][k], q[0][k]), k
     o2 = render_oracle(wl2, wl2.envs, poses[:1], 12, 0, [0])
     _check_all(q, o2, wide, wl2.envs, [0])
