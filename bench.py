@@ -480,8 +480,9 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         sim.autotune(wl.envs, poses, frames, tune_cache, stream=stream)
     tuning = sim.get_tuning()
-    sim.set_tuning(tuning["cluster_size"], tuning["warps_per_cta"], 1)
+    sim.set_tuning(tuning["cluster_size"], tuning["warps_per_cta"], 1, tuning["persistent"])
     tuning = sim.get_tuning()
+    two_grids = tuning["cluster_size"] == 1 and not tuning["persistent"]
     render = lambda k: sim.render(None, poses, seed, k, frames, stream=stream, envs_c=envs_c)
     if wl3 is not None:
         poses3 = torch.from_numpy(np.ascontiguousarray(wl3.poses, np.float32)).cuda()
@@ -530,7 +531,8 @@ def run_ours(args):
             flush.zero_()
             kms.append(sim.render_timed(None, poses, seed, 7000 + k, frames, stream=stream, envs_c=envs_c))
     kavg = [sum(x[i] for x in kms) / len(kms) for i in range(len(kms[0]))]
-    names = ["split_lines", "split_image"] if tuning["cluster_size"] == 1 else ["fused_render"]
+    names = (["split_lines", "split_image"] if two_grids
+             else ["split_persist"] if tuning["cluster_size"] == 1 else ["fused_render"])
     dom = max(range(len(kavg)), key=lambda i: kavg[i])
     samples, pixels = workload_units(wl)
     if len(names) == 1:
@@ -574,12 +576,13 @@ def run_ours(args):
                            **({"volumetric_images_per_s": value / scene.SURGERY3D_SLICES,
                                "frame": "one 50 x 37 elevation slice (5 per volumetric image)"}
                               if wl3 is not None else {}),
-                           "path": ("two-pass batched kernels" if tuning["cluster_size"] == 1
+                           "path": ("two-pass batched kernels" if two_grids
+                                    else "two-pass path in one persistent grid" if tuning["cluster_size"] == 1
                                     else "persistent cluster kernel") + ", CUDA graph replay, autotuned",
                            "tuning": tuning,
                            "parallelism": f"{world} ranks, contiguous cost-balanced env shards, no collective"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps * (2 if tuning["cluster_size"] == 1 else 1),
+                "gpu_launches": args.steps * (2 if two_grids else 1),
                 "plain": plain, "surrogate": surrogate, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     sim.close()

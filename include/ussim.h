@@ -149,20 +149,27 @@ typedef struct {
  *   cluster per environment frame (the frame stays in distributed shared
  *   memory); warps_per_cta 8, 16 or 32 (4-CTA clusters: 16 or 32).
  * cluster_size 1: two-pass path without clusters, warps_per_cta (8, 16 or
- *   32) lines per block; the axially filtered lines go through a global
- *   buffer of the batch's beam size, allocated on first use per batch
- *   signature.  Same frames as the cluster kernel.
- * Default after us_sim_create: the first of {1, 16, 1}, {1, 8, 1},
- * {1, 32, 1}, {8, 32, 1}, {16, 16, 1}, {16, 8, 1} that fits the probe set.
- * If none fits (lines of up to 1024 samples with a wide lateral PSF), the
- * simulator is still created: the batched entry points then return
- * US_ERR_UNSUPPORTED and us_sim_render_plain renders. */
+ *   32) lines per pass-A block; pass B works on tiles of up to 32 lines x
+ *   128 samples.  The axially filtered lines go through a global buffer of
+ *   the batch's beam size, allocated on first use per batch signature.
+ *   persistent 0: the two passes are two grids; 1: one cooperative grid of
+ *   resident blocks takes pass-A groups, then pass-B tiles, from a counter,
+ *   and a tile starts as soon as the groups holding its lines are written
+ *   (fills the last wave of a small batch).  Same frames as the cluster
+ *   kernel either way.
+ * Default after us_sim_create: the first of {1, 16, 1, 0}, {1, 8, 1, 0},
+ * {1, 32, 1, 0}, {8, 32, 1, 0}, {16, 16, 1, 0}, {16, 8, 1, 0} that fits the
+ * probe set.  If none fits, the simulator is still created: the batched
+ * entry points then return US_ERR_UNSUPPORTED and us_sim_render_plain
+ * renders. */
 typedef struct {
   int32_t cluster_size;  /* 1, 4, 8 or 16 */
   int32_t warps_per_cta; /* 8, 16 or 32 */
   int32_t use_graph;     /* 1: replay a captured CUDA graph per batch signature
                             (not on the legacy NULL stream, nor while the
                             caller's stream is itself being captured) */
+  int32_t persistent;    /* two-pass path: 0 two grids, 1 one persistent grid;
+                            must be 0 for the cluster path */
 } us_tuning;
 
 /* Create a simulator.  Copies the descriptors, builds the derived tables
@@ -333,8 +340,9 @@ US_API us_status us_sim_recon_observe(us_sim* sim, const us_env* envs, int32_t B
  * CUDA events recorded on `stream` around each of its kernels; waits for
  * the render and writes each kernel's duration in ms to kernel_ms[0..n)
  * (host, room for 2): cluster path n = 1 (the persistent kernel), two-pass
- * path n = 2 (pass A: slice, scanline model, axial PSF; pass B: lateral PSF,
- * log, scan conversion).  Errors as us_sim_render. */
+ * path with two grids n = 2 (pass A: slice, scanline model, axial PSF; pass
+ * B: lateral PSF, log, scan conversion), with one persistent grid n = 1.
+ * Errors as us_sim_render. */
 US_API us_status us_sim_render_timed(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
                                      uint64_t seed, uint64_t step, float* frames, float* kernel_ms,
                                      int32_t* n_kernels, void* stream);

@@ -133,9 +133,14 @@ __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProb
   }
 }
 
+template <bool REG_TAPS>
 __device__ __forceinline__ void lateral_psf_any(const RenderParams& p, const DevProbe& P, long long beam_off,
                                                 const float* abuf, float* ybuf, const float* wlat, int NS, int K,
                                                 int w0, int w1, int y1, int s0) {
+  if constexpr (!REG_TAPS) {
+    lateral_psf<0>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1, s0);
+    return;
+  }
 #define US_LAT(k) \
   case k: lateral_psf<k>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1, s0); break;
   switch (K) {
@@ -154,12 +159,12 @@ struct SplitCtx {
   int finite, valid;
 };
 
-// load the item of block `blk` (groups per item gpi) into shared memory;
+// load the item of work unit `blk` (groups per item gpi) into shared memory;
 // returns false (for the whole block) if the block has no work
-__device__ __forceinline__ bool split_item(const RenderParams& p, int gpi, int G, SplitCtx& cx, int& group) {
+__device__ __forceinline__ bool split_item(const RenderParams& p, int blk, int gpi, int G, SplitCtx& cx, int& group) {
   const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
-  const int item = blockIdx.x / gpi;
-  group = blockIdx.x - item * gpi;
+  const int item = blk / gpi;
+  group = blk - item * gpi;
   if (threadIdx.x == 0) {
     cx.valid = 0;
     if (item < n_items) {
@@ -188,12 +193,15 @@ constexpr int lines_min_blocks() {
   return G == 8 ? 6 : (G == 16 ? 3 : 1);
 }
 
+// Pass A work unit `blk` = item * gpi_lines + group.  With a.done set,
+// the unit then publishes its lines: done[blk] = 1 (release, after every
+// thread's stores).
 template <int G, bool ANCHORED>
-__global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(RenderParams p, SplitArgs a) {
+__device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArgs& a, int blk) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SplitCtx cx;
   int group;
-  if (!split_item(p, a.gpi_lines, G, cx, group)) return;
+  if (!split_item(p, blk, a.gpi_lines, G, cx, group)) return;
   const DevProbe& P = cx.P;
   const int NL = P.nl, NS = P.ns, KA = P.k_ax;
   const int RS = (NS + 2 * KA) | 1;
@@ -275,6 +283,18 @@ __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(Ren
     float* dst = a.beam + cx.it.beam_off + (long long)l * NS;
     for (int s = lane; s < NS; s += 32) dst[s] = row[s];
   }
+  if (a.done) {
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a.done + blk), "r"(1u) : "memory");
+    }
+  }
+}
+
+template <int G, bool ANCHORED>
+__global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(RenderParams p, SplitArgs a) {
+  lines_body<G, ANCHORED>(p, a, blockIdx.x);
 }
 
 // Pass B tile: GB lines x kChunk samples of one environment.  The block
@@ -282,13 +302,17 @@ __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(Ren
 // and the lateral PSF's reach) over its samples plus one, forms the log
 // image there and writes the pixels whose bilinear base (line, sample)
 // falls in the tile.
-template <int GB>
-__global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, SplitArgs a) {
+// Pass B work unit `blk` = item * gpi_image + tile, run by NT threads.
+// With a.done set, the unit first waits (bounded) until the pass-A groups
+// holding its staged rows have published them.
+template <int NT, bool REG_TAPS>
+__device__ __forceinline__ void image_body(const RenderParams& p, const SplitArgs& a, int blk) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const int GB = a.GB;
   // every thread reads its item and probe (the same addresses: broadcast
   // loads); no block-wide set-up
   const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
-  const int item = blockIdx.x / a.gpi_image, tile = blockIdx.x - item * a.gpi_image;
+  const int item = blk / a.gpi_image, tile = blk - item * a.gpi_image;
   if (item >= n_items) return;
   const EnvItem it = p.items[item];
   const DevProbe& P = p.probes[it.probe];
@@ -307,17 +331,41 @@ __global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, 
   const int nrows = (((y1 - w0) + 3) & ~3) + 2 * KL;
   const int a0 = max(r0, 0), a1 = min(y1 + KL, NL);                  // rows present in the line buffer
   const int tid = threadIdx.x;
+  if (a.done) {
+    __shared__ int ready;
+    if (tid == 0) {
+      ready = 1;
+      const int G = a.G;
+      for (int g = a0 / G; g <= (a1 - 1) / G && ready; ++g) {
+        const unsigned* f = a.done + (long long)item * a.gpi_lines + g;
+        const long long t0 = clock64();
+        unsigned v;
+        for (;;) {
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+          if (v) break;
+          if (clock64() - t0 > umma::kWaitCycles) {
+            atomicOr(p.err, kErrStagingTimeout);
+            ready = 0;
+            break;
+          }
+          __nanosleep(200);
+        }
+      }
+    }
+    __syncthreads();
+    if (!ready) return;
+  }
   float* abuf = reinterpret_cast<float*>(smem);                      // [nrows][kRowStride]
   float* ybuf = reinterpret_cast<float*>(smem + a.off_y);            // [y1 - w0][kRowStride]
   float* wlat = reinterpret_cast<float*>(smem + a.off_wlat);
-  for (int t = tid; t < 2 * KL + 1; t += kImageThreads) wlat[t] = __ldg(&P.w_lat[t]);
+  for (int t = tid; t < 2 * KL + 1; t += NT) wlat[t] = __ldg(&P.w_lat[t]);
   {
     const float* src = a.beam + it.beam_off + s0;
     constexpr int PPR = kRowStride / 4;                              // 16-byte pieces per row
     if ((NS & 3) == 0 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
       // asynchronous 16-byte copies, zero-filled past the row's end and
       // for rows outside the frame
-      for (int t = tid; t < nrows * PPR; t += kImageThreads) {
+      for (int t = tid; t < nrows * PPR; t += NT) {
         const int r = t / PPR, c = (t - r * PPR) * 4;
         const int line = r0 + r;
         const bool present = line >= a0 && line < a1 && c < sw;
@@ -327,7 +375,7 @@ __global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, 
       umma::cp_async_commit();
       umma::cp_async_wait<0>();
     } else {
-      for (int t = tid; t < nrows * kRowStride; t += kImageThreads) {
+      for (int t = tid; t < nrows * kRowStride; t += NT) {
         const int r = t / kRowStride, c = t - r * kRowStride;
         const int line = r0 + r;
         abuf[t] = line >= a0 && line < a1 && c < sw ? __ldcg(src + (long long)line * NS + c) : 0.f;
@@ -336,20 +384,20 @@ __global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, 
   }
   __syncthreads();
 
-  lateral_psf_any(p, P, it.beam_off, abuf, ybuf, wlat, NS, KL, w0, w1, y1, s0);
+  lateral_psf_any<REG_TAPS>(p, P, it.beam_off, abuf, ybuf, wlat, NS, KL, w0, w1, y1, s0);
   __syncthreads();
 
   float* out = p.frames + it.frame_off;
   const int se = min(s0 + kChunk, NS);
   if (P.kind == 0) {
     const int wl = w1 - w0, n = (se - s0) * wl;
-    for (int t = tid; t < n; t += kImageThreads) {
+    for (int t = tid; t < n; t += NT) {
       const int s = t / wl, j = t - s * wl;
       __stcs(&out[(long long)(s0 + s) * NL + w0 + j], ybuf[j * kRowStride + s]);
     }
   } else {
     const int e0 = P.wedge_off[tile], e1 = P.wedge_off[tile + 1];
-    for (int e = e0 + tid; e < e1; e += kImageThreads) {
+    for (int e = e0 + tid; e < e1; e += NT) {
       const float4 qv = __ldg(&P.wedge[e]);
       const int pix = __float_as_int(qv.x);
       const float fl = qv.y, fs = qv.z;
@@ -366,6 +414,34 @@ __global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, 
       }
       __stcs(&out[pix], v);
     }
+  }
+}
+
+__global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, SplitArgs a) {
+  image_body<kImageThreads, true>(p, a, blockIdx.x);
+}
+
+// Both passes in one persistent grid (one block per resident slot): blocks
+// take work units from a counter, all pass-A groups first, then the pass-B
+// tiles in environment order; a tile waits only for the groups holding its
+// rows, all of which were taken earlier by blocks that are running and wait
+// on nothing, so every wait ends.  Pass B's tiles fill pass A's last wave.
+constexpr bool PERSIST_REG_TAPS = true;
+template <int G, bool ANCHORED>
+__global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_persist(RenderParams p, SplitArgs a) {
+  __shared__ int job;
+  const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
+  const int na = n_items * a.gpi_lines, nb = n_items * a.gpi_image;
+  for (;;) {
+    if (threadIdx.x == 0) job = (int)atomicAdd(a.work, 1u);
+    __syncthreads();
+    const int j = job;
+    if (j >= na + nb) break;
+    if (j < na)
+      lines_body<G, ANCHORED>(p, a, j);
+    else
+      image_body<G * 32, PERSIST_REG_TAPS>(p, a, j - na);
+    __syncthreads();   // shared memory and `job` are reused by the next unit
   }
 }
 
@@ -425,57 +501,97 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
   return false;
 }
 
-// pass 0: split_lines<G>, pass 1: split_image<G>
+// pass 0: split_lines<G>, pass 1: split_image; split_persist<G> takes the
+// larger of the two shared-memory sizes
 template <int G>
-static cudaError_t prepare_g(int pass, size_t smem) {
-  if (pass == 1) return cudaFuncSetAttribute(split_image<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaError_t e = cudaFuncSetAttribute(split_lines<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return e == cudaSuccess
-             ? cudaFuncSetAttribute(split_lines<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-             : e;
+static cudaError_t prepare_g(SplitShape& sh) {
+  const int sm = (int)std::max(sh.smem_lines, sh.smem_image);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(split_lines<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sh.smem_lines)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(split_lines<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sh.smem_lines)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(split_image, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem_image)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(split_persist<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(split_persist<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+          cudaSuccess)
+    return e;
+  int dev = 0, n_sm = 0, b0 = 0, b1 = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, split_persist<G, false>, G * 32, sm)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, split_persist<G, true>, G * 32, sm)) != cudaSuccess)
+    return e;
+  sh.persist_grid[0] = b0 * n_sm;
+  sh.persist_grid[1] = b1 * n_sm;
+  return (b0 > 0 && b1 > 0) ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
-static cudaError_t prepare_pass(int pass, int G, size_t smem) {
-  switch (G) {
-    case 8: return prepare_g<8>(pass, smem);
-    case 16: return prepare_g<16>(pass, smem);
-    case 32: return prepare_g<32>(pass, smem);
+cudaError_t split_prepare(SplitShape& sh) {
+  switch (sh.G) {
+    case 8: return prepare_g<8>(sh);
+    case 16: return prepare_g<16>(sh);
+    case 32: return prepare_g<32>(sh);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t split_prepare(const SplitShape& sh) {
-  cudaError_t e = prepare_pass(0, sh.G, sh.smem_lines);
-  return e == cudaSuccess ? prepare_pass(1, sh.GB, sh.smem_image) : e;
-}
-
 template <int G>
-static void launch_g(const RenderParams& p, const SplitShape& sh, const SplitArgs& a, int max_items, int pass,
-                     cudaStream_t st) {
+static cudaError_t launch_g(const RenderParams& p, const SplitShape& sh, const SplitArgs& a, int max_items, int pass,
+                            cudaStream_t st) {
   if (pass == 0 && p.speckle_anchor)
     split_lines<G, true><<<(unsigned)(max_items * a.gpi_lines), G * 32, sh.smem_lines, st>>>(p, a);
   else if (pass == 0)
     split_lines<G, false><<<(unsigned)(max_items * a.gpi_lines), G * 32, sh.smem_lines, st>>>(p, a);
-  else
-    split_image<G><<<(unsigned)(max_items * a.gpi_image), kImageThreads, sh.smem_image, st>>>(p, a);
-}
-
-cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, int pass,
-                              cudaStream_t st) {
-  SplitArgs a = sh.args;
-  a.beam = beam;
-  switch (pass == 0 ? sh.G : sh.GB) {
-    case 8: launch_g<8>(p, sh, a, max_items, pass, st); break;
-    case 16: launch_g<16>(p, sh, a, max_items, pass, st); break;
-    case 32: launch_g<32>(p, sh, a, max_items, pass, st); break;
-    default: return cudaErrorInvalidValue;
+  else if (pass == 1)
+    split_image<<<(unsigned)(max_items * a.gpi_image), kImageThreads, sh.smem_image, st>>>(p, a);
+  else {
+    // persistent: as many blocks as are resident at once (launched as a
+    // cooperative grid, so they all are), no more than there are units
+    const int units = max_items * (a.gpi_lines + a.gpi_image);
+    const int grid = std::max(1, std::min(units, sh.persist_grid[p.speckle_anchor ? 1 : 0]));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(G * 32);
+    cfg.dynamicSmemBytes = std::max(sh.smem_lines, sh.smem_image);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return p.speckle_anchor ? cudaLaunchKernelEx(&cfg, split_persist<G, true>, p, a)
+                            : cudaLaunchKernelEx(&cfg, split_persist<G, false>, p, a);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, cudaStream_t st) {
-  cudaError_t e = launch_split_pass(p, sh, beam, max_items, 0, st);
-  return e == cudaSuccess ? launch_split_pass(p, sh, beam, max_items, 1, st) : e;
+cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
+                              int pass, cudaStream_t st) {
+  SplitArgs a = sh.args;
+  a.beam = beam;
+  if (pass == 2) {
+    // sync: the unit counter, then one completion flag per pass-A group
+    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(unsigned) * (1 + (size_t)max_items * a.gpi_lines), st);
+    if (e != cudaSuccess) return e;
+    a.work = sync;
+    a.done = sync + 1;
+  }
+  switch (sh.G) {
+    case 8: return launch_g<8>(p, sh, a, max_items, pass, st);
+    case 16: return launch_g<16>(p, sh, a, max_items, pass, st);
+    case 32: return launch_g<32>(p, sh, a, max_items, pass, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
+                         cudaStream_t st) {
+  if (sh.persistent) return launch_split_pass(p, sh, beam, sync, max_items, 2, st);
+  cudaError_t e = launch_split_pass(p, sh, beam, sync, max_items, 0, st);
+  return e == cudaSuccess ? launch_split_pass(p, sh, beam, sync, max_items, 1, st) : e;
 }
 
 // Pixels of a curvilinear probe's output grid, grouped by pass-B tile

@@ -19,6 +19,7 @@ constexpr int kMaxLines = 1024, kMaxSamples = 1024;
 
 us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream_t st);
 void drop_graph(us_plan& pl);
+static cudaError_t two_pass_buffers(us_plan* pl);
 
 us_status fail(us_sim* s, us_status st, const std::string& msg) {
   if (s) s->last_error = msg;
@@ -315,13 +316,13 @@ us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, ui
     p.items = pl->d_items;
     p.n_items = B;
     const bool two_pass = s->tuning.cluster_size == 1;
-    if (two_pass && !pl->d_beam && (e = cudaMalloc(&pl->d_beam, sizeof(float) * (size_t)pl->beam_elems)) != cudaSuccess)
+    if (two_pass && (e = two_pass_buffers(pl)) != cudaSuccess)
       return cuda_fail(s, e, "two-pass line buffer");
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (st && cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
     if (s->tuning.use_graph && st && cap == cudaStreamCaptureStatusNone) return graph_launch(s, pl, p, st);
     if (two_pass) {
-      if ((e = launch_split(p, s->split, pl->d_beam, B, st)) != cudaSuccess) return cuda_fail(s, e, "two-pass render launch");
+      if ((e = launch_split(p, s->split, pl->d_beam, pl->d_sync, B, st)) != cudaSuccess) return cuda_fail(s, e, "two-pass render launch");
       return US_OK;
     }
     if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(s, e, "reset work counter");
@@ -357,6 +358,7 @@ void free_sim(us_sim* s) {
     cudaFree(kv.second.d_items_gated);
     cudaFree(kv.second.d_gated_count);
     cudaFree(kv.second.d_beam);
+    cudaFree(kv.second.d_sync);
   }
   cudaFree(s->d_vols);
   cudaFree(s->d_probes);
@@ -378,6 +380,7 @@ void free_sim(us_sim* s) {
 us_status apply_split(us_sim* s, const us_tuning& t) {
   SplitShape sh;
   sh.G = t.warps_per_cta;
+  sh.persistent = t.persistent != 0;
   if (!split_shape_fits(sh, s->probes, s->n_labels))
     return fail(s, US_ERR_UNSUPPORTED, "probe lines per block do not fit in shared memory for the two-pass path");
   cudaError_t e;
@@ -414,6 +417,8 @@ us_status apply_split(us_sim* s, const us_tuning& t) {
 us_status apply_tuning(us_sim* s, const us_tuning& t) {
   const int cs = t.cluster_size, nw = t.warps_per_cta;
   if (t.use_graph & ~1) return fail(s, US_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+  if ((t.persistent & ~1) || (t.persistent && cs != 1))
+    return fail(s, US_ERR_INVALID_ARG, "persistent must be 0 or 1, and 0 for the cluster path");
   if (cs == 1) {
     if (nw != 8 && nw != 16 && nw != 32) return fail(s, US_ERR_INVALID_ARG, "two-pass path takes 8, 16 or 32 warps");
     return apply_split(s, t);
@@ -437,6 +442,17 @@ us_status apply_tuning(us_sim* s, const us_tuning& t) {
   return US_OK;
 }
 
+// the two-pass path's per-plan buffers: filtered lines and the persistent
+// grid's synchronisation words
+static cudaError_t two_pass_buffers(us_plan* pl) {
+  cudaError_t e = cudaSuccess;
+  if (!pl->d_beam && (e = cudaMalloc(&pl->d_beam, sizeof(float) * (size_t)pl->beam_elems)) != cudaSuccess) return e;
+  if (!pl->d_sync &&
+      (e = cudaMalloc(&pl->d_sync, sizeof(unsigned) * split_sync_words((int)pl->items_batch.size()))) != cudaSuccess)
+    return e;
+  return e;
+}
+
 void drop_graph(us_plan& pl) {
   if (pl.gexec) cudaGraphExecDestroy(pl.gexec);
   if (pl.graph) cudaGraphDestroy(pl.graph);
@@ -448,9 +464,10 @@ void drop_graph(us_plan& pl) {
 }
 
 // Capture the render (fused: work-counter reset + kernel; two-pass: both
-// kernels) once per batch signature and launch shape; later calls only swap
-// the kernel nodes' arguments.  Both two-pass kernels take the same
-// arguments, so node order does not matter.
+// kernels, or the synchronisation-word reset + persistent kernel) once per
+// batch signature and launch shape; later calls only swap the kernel nodes'
+// arguments (the two-pass kernels take the same ones, so node order does
+// not matter).
 us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream_t st) {
   cudaError_t e;
   const bool two_pass = s->tuning.cluster_size == 1;
@@ -458,15 +475,18 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
   FusedLayout lay = s->shape.lay;
   SplitArgs sa = s->split.args;
   sa.beam = pl->d_beam;
+  sa.work = pl->d_sync;
+  sa.done = pl->d_sync ? pl->d_sync + 1 : nullptr;
   void* fargs[2] = {&pp, &lay};
   void* sargs[2] = {&pp, &sa};
-  if (!pl->gexec || pl->g_cs != s->tuning.cluster_size || pl->g_nw != s->tuning.warps_per_cta) {
+  if (!pl->gexec || pl->g_cs != s->tuning.cluster_size || pl->g_nw != s->tuning.warps_per_cta ||
+      pl->g_pers != s->tuning.persistent) {
     drop_graph(*pl);
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(s, e, "graph capture");
     cudaError_t e1 = cudaSuccess, e2;
     if (two_pass) {
-      e2 = launch_split(p, s->split, pl->d_beam, p.n_items, st);
+      e2 = launch_split(p, s->split, pl->d_beam, pl->d_sync, p.n_items, st);
     } else {
       e1 = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
       e2 = launch_fused(p, s->shape, st);
@@ -489,7 +509,8 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
         pl->gkps.push_back(kp);
       }
     }
-    if (pl->gnodes.size() != (two_pass ? 2u : 1u) || (e = cudaGraphInstantiate(&pl->gexec, g, 0)) != cudaSuccess) {
+    const size_t want = two_pass && !s->split.persistent ? 2u : 1u;
+    if (pl->gnodes.size() != want || (e = cudaGraphInstantiate(&pl->gexec, g, 0)) != cudaSuccess) {
       cudaGraphDestroy(g);
       pl->gexec = nullptr;
       pl->gnodes.clear();
@@ -499,6 +520,7 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
     pl->graph = g;
     pl->g_cs = s->tuning.cluster_size;
     pl->g_nw = s->tuning.warps_per_cta;
+    pl->g_pers = s->tuning.persistent;
     if ((e = cudaGraphLaunch(pl->gexec, st)) != cudaSuccess) return cuda_fail(s, e, "graph launch");
     return US_OK;
   }
@@ -675,9 +697,8 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
     return r;
   }
   // default launch shape: the first that fits the probe set, two-pass
-  // first; when none fits (very long lines with a wide lateral PSF), the
-  // batched entry points report US_ERR_UNSUPPORTED and the plain
-  // per-environment path still renders
+  // first; when none fits, the batched entry points report
+  // US_ERR_UNSUPPORTED and the plain per-environment path still renders
   {
     static const us_tuning order[] = {{1, 16, 1}, {1, 8, 1}, {1, 32, 1}, {8, 32, 1}, {16, 16, 1}, {16, 8, 1}};
     s->batched = false;
@@ -793,9 +814,9 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
   p.n_items = B;
   p.n_items_dev = pl->d_gated_count;
   if (s->tuning.cluster_size == 1) {
-    if (!pl->d_beam && (e = cudaMalloc(&pl->d_beam, sizeof(float) * (size_t)pl->beam_elems)) != cudaSuccess)
+    if ((e = two_pass_buffers(pl)) != cudaSuccess)
       return cuda_fail(s, e, "two-pass line buffer");
-    if ((e = launch_split(p, s->split, pl->d_beam, B, st)) != cudaSuccess) return cuda_fail(s, e, "gated render");
+    if ((e = launch_split(p, s->split, pl->d_beam, pl->d_sync, B, st)) != cudaSuccess) return cuda_fail(s, e, "gated render");
   } else if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess ||
              (e = launch_fused(p, s->shape, st)) != cudaSuccess) {
     return cuda_fail(s, e, "gated render");
@@ -891,17 +912,23 @@ us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const fl
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool two_pass = s->tuning.cluster_size == 1;
   cudaError_t e;
-  if (two_pass && !pl->d_beam && (e = cudaMalloc(&pl->d_beam, sizeof(float) * (size_t)pl->beam_elems)) != cudaSuccess)
+  if (two_pass && (e = two_pass_buffers(pl)) != cudaSuccess)
     return cuda_fail(s, e, "two-pass line buffer");
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   for (auto& x : ev)
     if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(s, e, "events");
-  const int nk = two_pass ? 2 : 1;
-  if (two_pass) {
+  const int nk = two_pass && !s->split.persistent ? 2 : 1;
+  if (two_pass && s->split.persistent) {
+    // the reset of the synchronisation words sits outside the timed kernel
+    e = cudaMemsetAsync(pl->d_sync, 0, sizeof(unsigned) * split_sync_words(B), st);
     cudaEventRecord(ev[0], st);
-    e = launch_split_pass(p, s->split, pl->d_beam, B, 0, st);
+    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->d_sync, B, 2, st);
     cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, B, 1, st);
+  } else if (two_pass) {
+    cudaEventRecord(ev[0], st);
+    e = launch_split_pass(p, s->split, pl->d_beam, pl->d_sync, B, 0, st);
+    cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->d_sync, B, 1, st);
     cudaEventRecord(ev[2], st);
   } else {
     e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
@@ -987,27 +1014,29 @@ us_status us_sim_autotune(us_sim* s, const us_env* envs, int32_t B, const float*
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "r")) {
       char line[768];
-      int cs = 0, nw = 0;
+      int cs = 0, nw = 0, pg = 0;
       bool found = false;
       while (std::fgets(line, sizeof line, f)) {
         const size_t n = std::strlen(sig);
-        if (std::strncmp(line, sig, n) == 0 && std::sscanf(line + n, " cs=%d nw=%d", &cs, &nw) == 2) found = true;
+        if (std::strncmp(line, sig, n) == 0 && std::sscanf(line + n, " cs=%d nw=%d pg=%d", &cs, &nw, &pg) == 3)
+          found = true;
       }
       std::fclose(f);
       if (found) {
-        us_tuning t{cs, nw, keep_graph};
+        us_tuning t{cs, nw, keep_graph, pg};
         if (apply_tuning(s, t) == US_OK) return US_OK;
       }
     }
   }
-  static const int cand[][2] = {{8, 32}, {8, 16}, {8, 8}, {16, 32}, {16, 16}, {16, 8}, {4, 32}, {4, 16},
-                                {1, 32}, {1, 16}, {1, 8}};
+  static const int cand[][3] = {{8, 32, 0}, {8, 16, 0}, {8, 8, 0}, {16, 32, 0}, {16, 16, 0}, {16, 8, 0},
+                                {4, 32, 0}, {4, 16, 0}, {1, 32, 0}, {1, 16, 0}, {1, 8, 0},
+                                {1, 32, 1}, {1, 16, 1}, {1, 8, 1}};
   float best = 1e30f;
-  int best_cs = 0, best_nw = 0;
+  int best_cs = 0, best_nw = 0, best_pg = 0;
   cudaEvent_t a, b2;
   if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b2)) != cudaSuccess) return cuda_fail(s, e, "events");
   for (const auto& c : cand) {
-    us_tuning t{c[0], c[1], 0};
+    us_tuning t{c[0], c[1], 0, c[2]};
     if (apply_tuning(s, t) != US_OK) continue;
     bool ok = true;
     for (int w = 0; w < 2 && ok; ++w)
@@ -1023,16 +1052,17 @@ us_status us_sim_autotune(us_sim* s, const us_env* envs, int32_t B, const float*
       best = ms;
       best_cs = c[0];
       best_nw = c[1];
+      best_pg = c[2];
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b2);
   if (!best_cs) return fail(s, US_ERR_UNSUPPORTED, "no launch shape fits this probe set");
-  us_tuning t{best_cs, best_nw, keep_graph};
+  us_tuning t{best_cs, best_nw, keep_graph, best_pg};
   if ((r = apply_tuning(s, t)) != US_OK) return r;
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "a")) {
-      std::fprintf(f, "%s cs=%d nw=%d ms=%.4f\n", sig, best_cs, best_nw, best / 5.0f);
+      std::fprintf(f, "%s cs=%d nw=%d pg=%d ms=%.4f\n", sig, best_cs, best_nw, best_pg, best / 5.0f);
       std::fclose(f);
     }
   }

@@ -76,6 +76,8 @@ constexpr int kImageThreads = 256;
 constexpr int kRowStride = kChunk + 4;   // shared row stride, floats (16-byte rows)
 struct SplitArgs {
   float* beam = nullptr;   // axially filtered lines, beam layout (per item beam_off)
+  unsigned* work = nullptr;   // persistent grid: unit counter
+  unsigned* done = nullptr;   // persistent grid: per pass-A group, 1 once its lines are written
   int G = 32, GB = 32, gpi_lines = 0, gpi_image = 0;
   int off_wax = 0, off_tis = 0, off_lab = 0;   // pass A byte offsets
   int off_y = 0, off_wlat = 0;                 // pass B byte offsets
@@ -85,15 +87,23 @@ struct SplitShape {
   int GB = 32;   // pass B lines per wedge: the widest whose buffers fit
   SplitArgs args{};
   size_t smem_lines = 0, smem_image = 0;
+  bool persistent = false;        // one persistent grid instead of two
+  int persist_grid[2] = {0, 0};   // resident blocks of the persistent grid (beam-keyed, anchored maps)
 };
+// words of synchronisation state the persistent two-pass grid needs for a
+// batch of B environments (unit counter + a flag per group of >= 8 lines)
+inline size_t split_sync_words(int B) { return 1 + (size_t)B * (1024 / 8); }
 bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int n_labels);
-cudaError_t split_prepare(const SplitShape& sh);
+cudaError_t split_prepare(SplitShape& sh);
 // both passes over the first max_items entries of p.items (fewer if
 // p.n_items_dev says so)
-cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, cudaStream_t st);
+cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
+                         cudaStream_t st);
 // one pass: 0 = lines (pass A), 1 = image (pass B)
-cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, int max_items, int pass,
-                              cudaStream_t st);
+// pass 0: pass A, 1: pass B (separate grids); 2: both in the persistent
+// grid (resets `sync` first)
+cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
+                              int pass, cudaStream_t st);
 void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int NS, int G, std::vector<float4>& entries,
                   std::vector<int>& off);
 
@@ -133,6 +143,8 @@ struct us_plan {
   int* d_gated_count = nullptr;
   long long frame_floats = 0, beam_elems = 0;
   float* d_beam = nullptr;                   // two-pass path: filtered lines of the batch
+  int g_pers = -1;                           // captured graph's persistent flag
+  unsigned* d_sync = nullptr;                // two-pass path: persistent grid's counter and flags
   // captured render (fused: work-counter reset + kernel; two-pass: both
   // kernels), re-parameterised per call
   cudaGraph_t graph = nullptr;

@@ -51,8 +51,9 @@ def test_error_head_and_gated_fallback(trained):
     gated = pe > thr
     s_, yy = surr.cpu().numpy(), y.cpu().numpy()
     old = src.sim.get_tuning()
-    for shape in ((8, 32), (1, 16)):      # cluster kernel and two-pass path re-render the gated frames
-        src.sim.set_tuning(shape[0], shape[1], 1)
+    # cluster kernel, two-pass path and its persistent grid re-render the gated frames
+    for shape in ((8, 32, 0), (1, 16, 0), (1, 16, 1)):
+        src.sim.set_tuning(shape[0], shape[1], 1, shape[2])
         frames = torch.zeros_like(y)
         n_rendered = torch.zeros(1, dtype=torch.int32, device="cuda")
         T.mixed_step(src.sim, net, src.poses, src.seed, 77, x, frames, pred_err, thr, n_rendered, envs_c=src.envs_c)

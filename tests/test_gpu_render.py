@@ -58,31 +58,32 @@ def c2_oracle(c2):
     return render_oracle(wl, wl.envs, wl.poses, wl.seed, 5, range(64))
 
 
-@pytest.mark.parametrize("shape", [(8, 32), (1, 32), (1, 16)])
+@pytest.mark.parametrize("shape", [(8, 32, 0), (1, 32, 0), (1, 16, 0), (1, 16, 1), (1, 8, 1)])
 def test_batched_curvilinear_64env_full(c2, c2_oracle, shape):
     """All 64 envs of the 256^3 curvilinear batch, element by element, in the
     launch configurations the benchmark's autotuner chooses from (cluster
-    kernel and two-pass path)."""
+    kernel, two-pass path in two grids and in one persistent grid)."""
     wl, sim = c2
     old = sim.get_tuning()
     try:
-        sim.set_tuning(shape[0], shape[1], 1)
+        sim.set_tuning(shape[0], shape[1], 1, shape[2])
         g = render_gpu(sim, wl.envs, wl.poses, wl.seed, 5, path=0)
     finally:
         sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
     _check_all(g, c2_oracle, wl.probes, wl.envs, range(64))
 
 
-@pytest.mark.parametrize("shape", [(8, 32), (1, 8), (1, 32)])
+@pytest.mark.parametrize("shape", [(8, 32, 0), (1, 8, 0), (1, 32, 0), (1, 16, 1), (1, 32, 1)])
 def test_batched_paths_equal_plain_bitwise(c2, shape):
     """Frames and every intermediate export (labels, voxel indices, envelope,
-    log image) of the cluster kernel and of the two-pass path equal those of
-    the plain per-environment kernels bit for bit."""
+    log image) of the cluster kernel and of the two-pass path (two grids or
+    one persistent grid) equal those of the plain per-environment kernels
+    bit for bit."""
     wl, sim = c2
     envs, poses = wl.envs[:12], wl.poses[:12]
     old = sim.get_tuning()
     try:
-        sim.set_tuning(shape[0], shape[1], 0)
+        sim.set_tuning(shape[0], shape[1], 0, shape[2])
         a = render_gpu(sim, envs, poses, 11, 2, path=0)
     finally:
         sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
@@ -112,6 +113,9 @@ def test_launch_shape_that_cannot_fit_is_rejected(c2):
     with pytest.raises(UsError) as e:
         sim.set_tuning(2, 32)          # not a compiled shape
     assert e.value.status == US_ERR_INVALID_ARG
+    with pytest.raises(UsError) as e:
+        sim.set_tuning(8, 32, 1, 1)    # the persistent grid is a two-pass form
+    assert e.value.status == US_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("cs,nw", [(8, 8), (8, 16), (8, 32), (16, 8), (16, 16), (16, 32), (1, 8), (1, 16), (1, 32)])
@@ -122,10 +126,11 @@ def test_launch_shapes_agree(c2, cs, nw):
     old = sim.get_tuning()
     try:
         for graph in (0, 1):
-            sim.set_tuning(cs, nw, graph)
-            got = render_gpu(sim, envs, poses, 21, 0, path=0, debug=False)
-            for x, y in zip(ref, got):
-                assert np.array_equal(x["frame"], y["frame"])
+            for pers in ((0, 1) if cs == 1 else (0,)):
+                sim.set_tuning(cs, nw, graph, pers)
+                got = render_gpu(sim, envs, poses, 21, 0, path=0, debug=False)
+                for x, y in zip(ref, got):
+                    assert np.array_equal(x["frame"], y["frame"])
     finally:
         sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
 
@@ -209,9 +214,9 @@ def test_tiny_random_cases_vs_oracle_and_brute_force(opt):
     wl = scene.Workload("tiny", [(spec, lab, hu)], probes, envs, poses, options=opt, seed=99)
     sim = gpu_sim(wl)
     o = render_oracle(wl, envs, poses, 0xABCDEF0123, 9, range(B))
-    for path, shape in ((0, (8, 32)), (0, (1, 8)), (0, (1, 32)), (1, None)):
+    for path, shape in ((0, (8, 32, 0)), (0, (1, 8, 0)), (0, (1, 32, 0)), (0, (1, 16, 1)), (1, None)):
         if shape:
-            sim.set_tuning(shape[0], shape[1], 0)
+            sim.set_tuning(shape[0], shape[1], 0, shape[2])
         g = render_gpu(sim, envs, poses, 0xABCDEF0123, 9, path=path)
         _check_all(g, o, probes, envs, range(B))
     for b in range(3):
@@ -239,8 +244,8 @@ def test_uneven_batch_512env_sampled():
     poses = wl.poses[1]
     which = list(range(0, 512, 23)) + [511]
     o = render_oracle(wl, wl.envs, poses, wl.seed, 1, which)
-    for shape in ((8, 32), (1, 32)):
-        sim.set_tuning(shape[0], shape[1], 1)
+    for shape in ((8, 32, 0), (1, 32, 0), (1, 16, 1)):
+        sim.set_tuning(shape[0], shape[1], 1, shape[2])
         g = render_gpu(sim, wl.envs, poses, wl.seed, 1)
         _check_all(g, o, wl.probes, wl.envs, which)
 
