@@ -273,9 +273,22 @@ US_API us_status us_sim_render_gated(us_sim* sim, const us_env* envs, int32_t B,
                                      uint64_t step, float* frames, const float* score, float threshold,
                                      int32_t* n_rendered, void* stream);
 
-/* Wait for `stream` and read the sticky device error word: US_OK, or
+/* Self-test of the persistent two-pass grid's bounded wait (not a render):
+ * launches the grid of the current tuning (which must be {1, G, *, 1})
+ * for this batch with its unit counter started past every pass-A group,
+ * so no group publishes its lines and every pass-B tile's wait runs out
+ * after wait_cycles SM clock cycles (1 .. 2e9).  The tiles then return
+ * without touching `frames` (DEVICE, the batch's frame layout) and set the
+ * error word, so the following us_sim_check returns US_ERR_TIMEOUT; the
+ * context stays usable.  Asynchronous on `stream`.  Errors: US_ERR_INVALID_ARG,
+ * US_ERR_UNSUPPORTED (another tuning), US_ERR_CUDA. */
+US_API us_status us_sim_selftest_tile_wait(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
+                                           float* frames, int64_t wait_cycles, void* stream);
+
+/* Wait for `stream` and read the sticky device error word: US_OK;
  * US_ERR_INVALID_ARG if a pose had a non-finite entry (that frame renders
- * as water).  Clears the word. */
+ * as water); US_ERR_TIMEOUT if a bounded device wait ran out (that unit's
+ * output is missing).  Clears the word. */
 US_API us_status us_sim_check(us_sim* sim, void* stream);
 
 US_API us_status us_sim_get_tuning(const us_sim* sim, us_tuning* t);

@@ -343,7 +343,7 @@ __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArg
         for (;;) {
           asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
           if (v) break;
-          if (clock64() - t0 > umma::kWaitCycles) {
+          if (clock64() - t0 > a.wait_cycles) {
             atomicOr(p.err, kErrStagingTimeout);
             ready = 0;
             break;
@@ -583,6 +583,26 @@ cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float
     case 8: return launch_g<8>(p, sh, a, max_items, pass, st);
     case 16: return launch_g<16>(p, sh, a, max_items, pass, st);
     case 32: return launch_g<32>(p, sh, a, max_items, pass, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_split_wait_selftest(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync,
+                                       int max_items, long long wait_cycles, cudaStream_t st) {
+  SplitArgs a = sh.args;
+  a.beam = beam;
+  a.work = sync;
+  a.done = sync + 1;
+  a.wait_cycles = wait_cycles;
+  const unsigned start = (unsigned)(max_items * a.gpi_lines);
+  cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(unsigned) * (1 + (size_t)max_items * a.gpi_lines), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sync, &start, sizeof start, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // `start` lives on this stack frame
+  if (e != cudaSuccess) return e;
+  switch (sh.G) {
+    case 8: return launch_g<8>(p, sh, a, max_items, 2, st);
+    case 16: return launch_g<16>(p, sh, a, max_items, 2, st);
+    case 32: return launch_g<32>(p, sh, a, max_items, 2, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -961,6 +961,26 @@ us_status us_sim_sample_slices(us_sim* s, const us_env* envs, int32_t B, const f
   return e == cudaSuccess ? US_OK : cuda_fail(s, e, "slice sampling launch");
 }
 
+us_status us_sim_selftest_tile_wait(us_sim* s, const us_env* envs, int32_t B, const float* poses, float* frames,
+                                    int64_t wait_cycles, void* stream) {
+  us_status r = check_render_args(s, envs, B, poses, frames);
+  if (r != US_OK || B == 0) return r;
+  if (wait_cycles < 1 || wait_cycles > 2000000000ll) return fail(s, US_ERR_INVALID_ARG, "wait_cycles out of range");
+  if (!s->batched || s->tuning.cluster_size != 1 || !s->tuning.persistent)
+    return fail(s, US_ERR_UNSUPPORTED, "the tuning is not the persistent two-pass grid");
+  us_plan* pl;
+  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  cudaError_t e;
+  if ((e = two_pass_buffers(pl)) != cudaSuccess) return cuda_fail(s, e, "two-pass line buffer");
+  RenderParams p = base_params(s, poses, 0, 0, frames);
+  p.items = pl->d_items;
+  p.n_items = B;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((e = launch_split_wait_selftest(p, s->split, pl->d_beam, pl->d_sync, B, wait_cycles, st)) != cudaSuccess)
+    return cuda_fail(s, e, "self-test launch");
+  return US_OK;
+}
+
 us_status us_sim_check(us_sim* s, void* stream) {
   if (!s) return US_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -970,7 +990,8 @@ us_status us_sim_check(us_sim* s, void* stream) {
   if ((e = cudaMemcpy(&w, s->d_err, sizeof w, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(s, e, "error word");
   if (w) {
     cudaMemset(s->d_err, 0, sizeof w);
-    if (w & kErrStagingTimeout) return fail(s, US_ERR_TIMEOUT, "a shared-memory staging copy did not complete in time");
+    if (w & kErrStagingTimeout)
+      return fail(s, US_ERR_TIMEOUT, "a bounded device wait ran out (staging copy or a pass-B tile's lines)");
     if (w & kErrReconOverflow) return fail(s, US_ERR_INVALID_ARG, "a reconstruction point list reached its capacity");
     if (w & kErrNonFinitePose) return fail(s, US_ERR_INVALID_ARG, "a pose had a non-finite entry (rendered as water)");
     return fail(s, US_ERR_INTERNAL, "device consistency check failed");

@@ -78,6 +78,7 @@ struct SplitArgs {
   float* beam = nullptr;   // axially filtered lines, beam layout (per item beam_off)
   unsigned* work = nullptr;   // persistent grid: unit counter
   unsigned* done = nullptr;   // persistent grid: per pass-A group, 1 once its lines are written
+  long long wait_cycles = 2000000000ll;   // persistent grid: bound of a tile's wait (SM clock cycles, ~1 s)
   int G = 32, GB = 32, gpi_lines = 0, gpi_image = 0;
   int off_wax = 0, off_tis = 0, off_lab = 0;   // pass A byte offsets
   int off_y = 0, off_wlat = 0;                 // pass B byte offsets
@@ -104,6 +105,11 @@ cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* bea
 // grid (resets `sync` first)
 cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
                               int pass, cudaStream_t st);
+// the persistent grid with its unit counter started past every pass-A group
+// and the given wait bound: no group publishes its lines, so every tile's
+// wait runs out (self-test of the bounded wait)
+cudaError_t launch_split_wait_selftest(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync,
+                                       int max_items, long long wait_cycles, cudaStream_t st);
 void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int NS, int G, std::vector<float4>& entries,
                   std::vector<int>& off);
 

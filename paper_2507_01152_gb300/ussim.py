@@ -74,6 +74,7 @@ SIGNATURES = {
                                 C.POINTER(us_probe), C.c_int32, C.POINTER(us_options), C.POINTER(_P)]),
     "us_sim_destroy": (None, [_P]),
     "us_sim_refresh_volumes": (C.c_int, [_P, _P]),
+    "us_sim_selftest_tile_wait": (C.c_int, [_P, _P, C.c_int32, _P, _P, C.c_int64, _P]),
     "us_sim_frame_layout": (C.c_int, [_P, _P, C.c_int32, _P]),
     "us_sim_beam_layout": (C.c_int, [_P, _P, C.c_int32, _P]),
     "us_sim_render": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P]),
@@ -327,6 +328,14 @@ class Sim:
 
     def check(self, stream=None):
         self._check(self._lib.us_sim_check(self.h, _stream_handle(stream)))
+
+    def selftest_tile_wait(self, envs, poses, frames, wait_cycles, stream=None):
+        """Run the persistent grid with no pass-A group published, so every
+        tile's bounded wait runs out (us_sim_check then reports
+        US_ERR_TIMEOUT)."""
+        B = poses.shape[0]
+        self._check(self._lib.us_sim_selftest_tile_wait(self.h, make_envs(envs), B, _ptr(poses), _ptr(frames),
+                                                        int(wait_cycles), _stream_handle(stream)))
 
     def refresh_volumes(self, stream=None):
         """Re-read the volumes after their contents changed (label check,

@@ -404,3 +404,33 @@ def test_maximum_probe_sizes_and_widest_psf():
         assert np.array_equal(gw[0][k], q[0][k]), k
     o2 = render_oracle(wl2, wl2.envs, poses[:1], 12, 0, [0])
     _check_all(q, o2, wide, wl2.envs, [0])
+
+
+def test_persistent_grid_wait_runs_out_and_reports(c2):
+    """The persistent grid's bounded wait, made to run out: with no pass-A
+    group published (the self-test starts the unit counter past them), every
+    pass-B tile gives up after its bound, leaves the frames untouched and
+    sets the error word; us_sim_check reports US_ERR_TIMEOUT, and the same
+    handle then renders normally."""
+    from paper_2507_01152_gb300.ussim import UsError, US_ERR_TIMEOUT
+    wl, sim = c2
+    envs, poses = wl.envs[:8], wl.poses[:8]
+    off = sim.frame_layout(envs)
+    P = torch.from_numpy(np.ascontiguousarray(poses, np.float32)).cuda()
+    frames = torch.full((int(off[-1]),), -7.0, device="cuda")
+    old = sim.get_tuning()
+    try:
+        sim.set_tuning(1, 16, 0, 1)
+        sim.selftest_tile_wait(envs, P, frames, 2_000_000)      # ~1 ms per wait
+        with pytest.raises(UsError) as e:
+            sim.check()
+        assert e.value.status == US_ERR_TIMEOUT
+        assert bool((frames == -7.0).all())
+        sim.check()                                              # the word was cleared
+        got = render_gpu(sim, envs, poses, 5, 1, debug=False)
+        sim.check()
+    finally:
+        sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
+    ref = render_gpu(sim, envs, poses, 5, 1, path=1, debug=False)
+    for x, y in zip(ref, got):
+        assert np.array_equal(x["frame"], y["frame"])
