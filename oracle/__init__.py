@@ -10,6 +10,8 @@ CPU-baseline leg of ``bench.py``; never by the product path.
   full 2-D PSF, its own Philox and Box-Muller).
 * ``surrogate_ref.py`` (O3): PyTorch CPU float64 network / loss / optimiser
   reference of the learned surrogate.
+* ``hist_match.py``: histogram matching of CT slices (the learned
+  simulator's input), exact integer decisions.
 
 Nothing here shares code with the CUDA path.  The synthetic inputs come
 from ``paper_2507_01152_gb300.scene``, which holds none of the method.
@@ -106,6 +108,8 @@ def lib():
                                                C.c_int, C.c_void_p]
             L.oracle_sample_slice.argtypes = [C.POINTER(OrVolume), C.POINTER(OrProbe), C.c_void_p, C.c_void_p]
             L.oracle_sample_slice.restype = C.c_int
+            L.oracle_sample_slice_raw.argtypes = [C.POINTER(OrVolume), C.POINTER(OrProbe), C.c_void_p, C.c_void_p]
+            L.oracle_sample_slice_raw.restype = C.c_int
             L.oracle_anchored_noise.argtypes = [C.c_void_p, C.c_int32, C.c_float, C.c_uint32, C.c_uint64,
                                                 C.c_void_p]
             L.oracle_recon_keep_threshold.argtypes = [C.c_double]
@@ -306,4 +310,15 @@ def sample_slice(labels, hu, voxel_mm, probe, pose):
     pr = or_probe(probe)
     M = np.ascontiguousarray(pose, np.float32).reshape(12)
     lib().oracle_sample_slice(C.byref(vol.desc), C.byref(pr), _ptr(M), _ptr(out))
+    return out
+
+
+def sample_slice_raw(labels, hu, voxel_mm, probe, pose):
+    """[out_h][out_w][3] = (label, trilinear HU (unscaled, FP64), inside-fan
+    flag) on one env's output pixel grid"""
+    vol = _Vol(labels, hu, voxel_mm)
+    out = np.zeros((probe.out_h, probe.out_w, 3))
+    pr = or_probe(probe)
+    M = np.ascontiguousarray(pose, np.float32).reshape(12)
+    lib().oracle_sample_slice_raw(C.byref(vol.desc), C.byref(pr), _ptr(M), _ptr(out))
     return out

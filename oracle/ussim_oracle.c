@@ -619,7 +619,9 @@ void oracle_sample_coords(const or_probe* p, const float* pose, float voxel_mm, 
  * rounded to FP32 once; linear: the beam grid (row = sample, column =
  * line).  The voxel coordinate then follows the same FP32 path as the
  * beam samples.  out: [out_h][out_w][3]. */
-int oracle_sample_slice(const or_volume* vol, const or_probe* p, const float* pose, double* out) {
+/* raw = 0: out[H][W][3] = (label / 4, clamp(HU / 1000, -1, 3), mask);
+ * raw = 1: out[H][W][3] = (label, HU, mask) (HU unscaled, unclamped) */
+static int sample_slice(const or_volume* vol, const or_probe* p, const float* pose, double* out, int raw) {
   const int W = p->out_w, H = p->out_h, NL = p->n_lines, NS = p->n_samples;
   const float inv_h = (float)(1.0 / (double)vol->voxel_mm);
   or_derived d;
@@ -654,16 +656,30 @@ int oracle_sample_slice(const or_volume* vol, const or_probe* p, const float* po
       }
       int64_t idx = or_nearest(vol, u);
       double lab = idx >= 0 ? (double)vol->labels[idx] : 0.0;
-      double hu = or_trilinear_hu(vol, u) / 1000.0;
-      if (hu < -1.0) hu = -1.0;
-      if (hu > 3.0) hu = 3.0;
+      double hu = or_trilinear_hu(vol, u);
       double* o = out + ((int64_t)r * W + c) * 3;
-      o[0] = lab / 4.0;
-      o[1] = hu;
+      if (raw) {
+        o[0] = lab;
+        o[1] = hu;
+      } else {
+        hu /= 1000.0;
+        if (hu < -1.0) hu = -1.0;
+        if (hu > 3.0) hu = 3.0;
+        o[0] = lab / 4.0;
+        o[1] = hu;
+      }
       o[2] = mask;
     }
   }
   return 0;
+}
+
+int oracle_sample_slice(const or_volume* vol, const or_probe* p, const float* pose, double* out) {
+  return sample_slice(vol, p, pose, out, 0);
+}
+
+int oracle_sample_slice_raw(const or_volume* vol, const or_probe* p, const float* pose, double* out) {
+  return sample_slice(vol, p, pose, out, 1);
 }
 
 /* ------------------------------------------- reconstruction observation */
