@@ -252,7 +252,48 @@ def surrogate_speed(sim, wl, B, stream, c=32):
     net.close()
     return {"value": B / ms * 1e3, "unit": "frames/s", "envs": B, "ms_per_step": ms,
             "tflops": 2 * 10.74e9 * B / ms / 1e9, "base_channels": c,
-            "note": "slice sampling + BF16 forward on tcgen05; speed only (weights untrained)"}
+            "note": "slice sampling + BF16 forward on tcgen05; speed only (weights untrained)",
+            "hist_match": hist_match_speed(sim, P, ec, x, stream)}
+
+
+def hist_match_speed(sim, P, ec, x, stream):
+    """CT histogram matching of the surrogate input (per env slice, 4096
+    one-HU bins, reference from another synthetic volume): slice sampling
+    with and without it, and the standalone matching of B x H x W FP32
+    values (algorithmic bytes: two reads of value + mask, one write)"""
+    import torch
+    # the caller's reference: cumulative counts of a "training CT" (another
+    # synthetic volume's integer HU, one-HU bins from -1024)
+    other = scene.make_volume(scene.VolumeSpec(96, 96, 96, 0.5, 3, 4321))[1]
+    vals = other[other > -1000].astype(np.int64) + 1024
+    ref = np.cumsum(np.bincount(np.clip(vals, 0, 4095), minlength=4096)).astype(np.int64)
+    B, H, W = x.shape[0], x.shape[1], x.shape[2]
+    hu = torch.randn((B, H * W), device="cuda") * 300.0
+    mask = torch.ones((B, H * W), dtype=torch.uint8, device="cuda")
+
+    def t(fn, n=5):
+        with torch.cuda.stream(stream):
+            fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(n):
+                fn()
+            b.record(stream)
+            b.synchronize()
+        return a.elapsed_time(b) / n
+
+    sim.set_hu_reference(None, 0, 1)
+    plain = t(lambda: sim.sample_slices(None, P, x, stream=stream, envs_c=ec))
+    sim.set_hu_reference(ref, -1024.0, 1.0)
+    matched = t(lambda: sim.sample_slices(None, P, x, stream=stream, envs_c=ec))
+    alone = t(lambda: sim.hist_match(hu, mask, hu, stream=stream))
+    sim.set_hu_reference(None, 0, 1)
+    sim.check(stream)
+    peak, which = load_peaks()
+    gbs = B * H * W * 14 / alone / 1e6
+    return {"slices_ms": plain, "slices_matched_ms": matched, "match_ms": alone, "pixels": B * H * W,
+            "match_gbs": gbs, "match_hbm_frac": gbs / peak, "peak_source": which,
+            "bytes_per_pixel": 14, "note": "reference: 4096 one-HU bins of another synthetic volume"}
 
 
 def run_mixed(args):

@@ -253,13 +253,43 @@ US_API us_status us_sim_render_debug(us_sim* sim, const us_env* envs, int32_t B,
 US_API us_status us_sim_render_host(us_sim* sim, const us_env* envs, int32_t B, const float* poses_host,
                              uint64_t seed, uint64_t step, float* frames_host, void* stream);
 
+/* Reference histogram of the CT histogram matching (Sec. 3: the learned
+ * simulator's input CT slices are matched in intensity histogram to a
+ * subset of its training CT images).  ref_cum: HOST int64 [n_bins], the
+ * reference's cumulative counts over n_bins bins of width bin_width from h0
+ * (bin k(v) = clamp(floor((v - h0) / bin_width), 0, n_bins - 1), FP32),
+ * non-decreasing with 0 < ref_cum[n_bins - 1] < 2^31; n_bins in [1, 16384].
+ * Copied (synchronous).  ref_cum NULL or n_bins 0 removes the reference.
+ * Errors: US_ERR_INVALID_ARG, US_ERR_CUDA. */
+US_API us_status us_sim_set_hu_reference(us_sim* sim, const int64_t* ref_cum, int32_t n_bins, float h0,
+                                         float bin_width);
+
+/* Histogram matching of B images of n_pix CT values to the reference
+ * (discrete histogram specification): per image, S[k] = the number of its
+ * considered pixels in bins 0..k, n = S[n_bins - 1], N = the reference
+ * total; bin k maps to the first reference bin m with ref_cum[m] * n >=
+ * S[k] * N (exact 64-bit integers), and a considered pixel becomes that
+ * bin's centre h0 + (m + 0.5) * bin_width (FP32).  hu, out: DEVICE float
+ * [B][n_pix] (out may equal hu; values finite); mask: DEVICE uint8
+ * [B][n_pix], nonzero = considered, or NULL (all).  Pixels not considered,
+ * and images without a considered pixel, are copied unchanged.
+ * n_pix in [1, 2^24].  Errors: US_ERR_INVALID_ARG (also: no reference set),
+ * US_ERR_CUDA. */
+US_API us_status us_sim_hist_match(us_sim* sim, const float* hu, const uint8_t* mask, int32_t B, int32_t n_pix,
+                                   float* out, void* stream);
+
 /* Input of the learned surrogate (ussim_surrogate.h) for a batch: the
  * label and CT slices on each env's output pixel grid (Fig. 2: the slices
  * the simulators map to images).  out: DEVICE [B][out_h][out_w][8] BF16,
  * channels (label / 4, clamp(HU / 1000, -1, 3), inside-fan flag, 0 x 5).
  * Curvilinear probes: the scan-conversion grid; linear: the beam grid
  * (row = sample, column = line).  Every env of the batch must have the
- * same output size.  Same voxel-coordinate path as the render. */
+ * same output size.  Same voxel-coordinate path as the render.  With a
+ * reference histogram set (us_sim_set_hu_reference), the HU channel of each
+ * in-fan pixel carries its histogram-matched HU instead (per env slice, see
+ * us_sim_hist_match); pixels outside the fan keep the sampled HU.  The raw
+ * slices then pass through library-owned buffers (5 bytes per pixel of the
+ * batch, allocated on first use per batch signature). */
 US_API us_status us_sim_sample_slices(us_sim* sim, const us_env* envs, int32_t B, const float* poses, uint16_t* out,
                                       void* stream);
 

@@ -9,7 +9,10 @@
 
 namespace ussim {
 
-__global__ void slice_input_kernel(RenderParams p, const EnvItem* items, int H, int W, uint4* out) {
+// hu_raw / in_fan (optional): the unscaled trilinear HU and the inside-fan
+// flag of every pixel, for the histogram matching that follows
+__global__ void slice_input_kernel(RenderParams p, const EnvItem* items, int H, int W, uint4* out, float* hu_raw,
+                                   uint8_t* in_fan) {
   const int b = blockIdx.y;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= H * W) return;
@@ -30,7 +33,12 @@ __global__ void slice_input_kernel(RenderParams p, const EnvItem* items, int H, 
   const float3 u = to_voxel(M, V.inv_h, x, z);
   const int vi = nearest_voxel(V, u);
   const float lab = vi >= 0 ? (float)__ldg(&V.labels[vi]) : 0.f;
-  const float hu = fminf(fmaxf(trilinear_hu(V, u) * 1e-3f, -1.f), 3.f);
+  const float hu_v = trilinear_hu(V, u);
+  const float hu = fminf(fmaxf(hu_v * 1e-3f, -1.f), 3.f);
+  if (hu_raw) {
+    hu_raw[(size_t)b * H * W + q] = hu_v;
+    in_fan[(size_t)b * H * W + q] = mask != 0.f;
+  }
   __align__(16) __nv_bfloat16 v[8];
   v[0] = __float2bfloat16_rn(0.25f * lab);
   v[1] = __float2bfloat16_rn(hu);
@@ -41,9 +49,9 @@ __global__ void slice_input_kernel(RenderParams p, const EnvItem* items, int H, 
 }
 
 cudaError_t launch_slice_input(const RenderParams& p, const EnvItem* items_batch, int B, int H, int W, void* out,
-                               cudaStream_t st) {
+                               float* hu_raw, uint8_t* in_fan, cudaStream_t st) {
   const dim3 grid((H * W + 255) / 256, B);
-  slice_input_kernel<<<grid, 256, 0, st>>>(p, items_batch, H, W, reinterpret_cast<uint4*>(out));
+  slice_input_kernel<<<grid, 256, 0, st>>>(p, items_batch, H, W, reinterpret_cast<uint4*>(out), hu_raw, in_fan);
   return cudaGetLastError();
 }
 

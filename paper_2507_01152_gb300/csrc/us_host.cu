@@ -16,6 +16,7 @@ namespace {
 
 constexpr int kMaxAxialHalf = 32;   // in-place axial filter in the fused kernel
 constexpr int kMaxLines = 1024, kMaxSamples = 1024;
+constexpr int kMaxMatchBins = 16384;   // histogram matching: bins of the reference (64 KB of shared memory)
 
 us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream_t st);
 void drop_graph(us_plan& pl);
@@ -351,6 +352,7 @@ void free_sim(us_sim* s) {
   }
   for (auto* d : s->d_pair_D) cudaFree(d);
   for (auto* d : s->d_hu8) cudaFree(d);
+  cudaFree(s->d_href);
   for (auto& kv : s->plans) {
     drop_graph(kv.second);
     cudaFree(kv.second.d_items);
@@ -359,6 +361,8 @@ void free_sim(us_sim* s) {
     cudaFree(kv.second.d_gated_count);
     cudaFree(kv.second.d_beam);
     cudaFree(kv.second.d_sync);
+    cudaFree(kv.second.d_slice_hu);
+    cudaFree(kv.second.d_slice_fan);
   }
   cudaFree(s->d_vols);
   cudaFree(s->d_probes);
@@ -957,8 +961,71 @@ us_status us_sim_sample_slices(us_sim* s, const us_env* envs, int32_t B, const f
       return fail(s, US_ERR_INVALID_ARG, "sample_slices needs one output size for the whole batch");
   }
   RenderParams p = base_params(s, poses, 0, 0, nullptr);
-  cudaError_t e = launch_slice_input(p, pl->d_items_batch, B, p0.out_h, p0.out_w, out, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t npx = (size_t)p0.out_h * p0.out_w;
+  cudaError_t e;
+  if (s->d_href) {
+    // raw HU and inside-fan flags of the batch, then the matching rewrites
+    // the HU channel of the in-fan pixels
+    if (pl->slice_px < (size_t)B * npx) {
+      cudaFree(pl->d_slice_hu);
+      cudaFree(pl->d_slice_fan);
+      pl->d_slice_hu = nullptr;
+      pl->d_slice_fan = nullptr;
+      pl->slice_px = 0;
+      if ((e = cudaMalloc(&pl->d_slice_hu, sizeof(float) * B * npx)) != cudaSuccess ||
+          (e = cudaMalloc(&pl->d_slice_fan, (size_t)B * npx)) != cudaSuccess)
+        return cuda_fail(s, e, "slice scratch");
+      pl->slice_px = (size_t)B * npx;
+    }
+    if ((e = launch_slice_input(p, pl->d_items_batch, B, p0.out_h, p0.out_w, out, pl->d_slice_hu, pl->d_slice_fan,
+                                st)) != cudaSuccess ||
+        (e = launch_hist_match(pl->d_slice_hu, pl->d_slice_fan, B, (int)npx, s->d_href, s->href_nb, s->href_h0,
+                               s->href_w, nullptr, out, st)) != cudaSuccess)
+      return cuda_fail(s, e, "slice sampling launch");
+    return US_OK;
+  }
+  e = launch_slice_input(p, pl->d_items_batch, B, p0.out_h, p0.out_w, out, nullptr, nullptr, st);
   return e == cudaSuccess ? US_OK : cuda_fail(s, e, "slice sampling launch");
+}
+
+us_status us_sim_set_hu_reference(us_sim* s, const int64_t* ref_cum, int32_t n_bins, float h0, float bin_width) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (!ref_cum || n_bins == 0) {
+    cudaFree(s->d_href);
+    s->d_href = nullptr;
+    s->href_nb = 0;
+    return US_OK;
+  }
+  if (n_bins < 1 || n_bins > kMaxMatchBins) return fail(s, US_ERR_INVALID_ARG, "n_bins must be in [1, 16384]");
+  if (!std::isfinite(h0) || !std::isfinite(bin_width) || !(bin_width > 0.f))
+    return fail(s, US_ERR_INVALID_ARG, "h0 and bin_width must be finite, bin_width > 0");
+  if (ref_cum[0] < 0 || ref_cum[n_bins - 1] <= 0 || ref_cum[n_bins - 1] >= (1ll << 31))
+    return fail(s, US_ERR_INVALID_ARG, "the reference total must be in [1, 2^31)");
+  for (int k = 1; k < n_bins; ++k)
+    if (ref_cum[k] < ref_cum[k - 1]) return fail(s, US_ERR_INVALID_ARG, "reference cumulative counts must not decrease");
+  long long* d = nullptr;
+  cudaError_t e;
+  if ((e = upload(&d, reinterpret_cast<const long long*>(ref_cum), (size_t)n_bins)) != cudaSuccess)
+    return cuda_fail(s, e, "reference histogram");
+  cudaFree(s->d_href);
+  s->d_href = d;
+  s->href_nb = n_bins;
+  s->href_h0 = h0;
+  s->href_w = bin_width;
+  return US_OK;
+}
+
+us_status us_sim_hist_match(us_sim* s, const float* hu, const uint8_t* mask, int32_t B, int32_t n_pix, float* out,
+                            void* stream) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (B < 0 || n_pix < 1 || n_pix > (1 << 24)) return fail(s, US_ERR_INVALID_ARG, "B >= 0 and n_pix in [1, 2^24]");
+  if (B == 0) return US_OK;
+  if (!hu || !out) return fail(s, US_ERR_INVALID_ARG, "NULL image buffer");
+  if (!s->d_href) return fail(s, US_ERR_INVALID_ARG, "no reference histogram (us_sim_set_hu_reference)");
+  cudaError_t e = launch_hist_match(hu, mask, B, n_pix, s->d_href, s->href_nb, s->href_h0, s->href_w, out, nullptr,
+                                    static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? US_OK : cuda_fail(s, e, "histogram matching launch");
 }
 
 us_status us_sim_selftest_tile_wait(us_sim* s, const us_env* envs, int32_t B, const float* poses, float* frames,

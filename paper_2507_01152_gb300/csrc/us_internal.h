@@ -119,7 +119,12 @@ cudaError_t launch_gate_compact(const EnvItem* items, int B, const float* score,
 
 // surrogate input of a batch on the output pixel grid: [B][H][W][8] BF16
 cudaError_t launch_slice_input(const RenderParams& p, const EnvItem* items_batch, int B, int H, int W, void* out,
-                               cudaStream_t st);
+                               float* hu_raw, uint8_t* in_fan, cudaStream_t st);
+// histogram matching of B images of n_pix values to the cumulative reference
+// counts R[nb] (device); out (float) and/or slice (BF16 surrogate input,
+// channel 1) receive the result
+cudaError_t launch_hist_match(const float* hu, const uint8_t* mask, int B, int n_pix, const long long* R, int nb,
+                              float h0, float w, float* out, void* slice, cudaStream_t st);
 
 // 3-D probe: B poses -> B * E poses swept along each pose's elevation axis
 cudaError_t launch_expand_elevation(const float* poses, int B, int E, float pitch, float* out, cudaStream_t st);
@@ -151,6 +156,9 @@ struct us_plan {
   float* d_beam = nullptr;                   // two-pass path: filtered lines of the batch
   int g_pers = -1;                           // captured graph's persistent flag
   unsigned* d_sync = nullptr;                // two-pass path: persistent grid's counter and flags
+  float* d_slice_hu = nullptr;               // slice sampling with histogram matching: raw HU
+  uint8_t* d_slice_fan = nullptr;            //   and inside-fan flags of the batch's pixels
+  size_t slice_px = 0;
   // captured render (fused: work-counter reset + kernel; two-pass: both
   // kernels), re-parameterised per call
   cudaGraph_t graph = nullptr;
@@ -172,6 +180,9 @@ struct us_sim {
   ussim::DevPair* d_pairs = nullptr;
   std::vector<uint8_t*> d_pair_D;
   std::vector<uint4*> d_hu8;   // corner records per volume (null entries: not built)
+  long long* d_href = nullptr;  // reference cumulative counts of the HU histogram matching (null: off)
+  int href_nb = 0;
+  float href_h0 = 0.f, href_w = 1.f;
   std::vector<ussim::DevVolume> dev_vols;
 
   ussim::PlainScratch scratch;

@@ -74,6 +74,8 @@ SIGNATURES = {
                                 C.POINTER(us_probe), C.c_int32, C.POINTER(us_options), C.POINTER(_P)]),
     "us_sim_destroy": (None, [_P]),
     "us_sim_refresh_volumes": (C.c_int, [_P, _P]),
+    "us_sim_set_hu_reference": (C.c_int, [_P, _P, C.c_int32, C.c_float, C.c_float]),
+    "us_sim_hist_match": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32, _P, _P]),
     "us_sim_selftest_tile_wait": (C.c_int, [_P, _P, C.c_int32, _P, _P, C.c_int64, _P]),
     "us_sim_frame_layout": (C.c_int, [_P, _P, C.c_int32, _P]),
     "us_sim_beam_layout": (C.c_int, [_P, _P, C.c_int32, _P]),
@@ -336,6 +338,23 @@ class Sim:
         B = poses.shape[0]
         self._check(self._lib.us_sim_selftest_tile_wait(self.h, make_envs(envs), B, _ptr(poses), _ptr(frames),
                                                         int(wait_cycles), _stream_handle(stream)))
+
+    def set_hu_reference(self, ref_cum, h0, bin_width):
+        """Reference cumulative bin counts (int64 numpy array) of the CT
+        histogram matching, or None to switch it off."""
+        if ref_cum is None:
+            self._check(self._lib.us_sim_set_hu_reference(self.h, None, 0, 0.0, 1.0))
+            return
+        import numpy as np
+        r = np.ascontiguousarray(ref_cum, np.int64)
+        self._check(self._lib.us_sim_set_hu_reference(self.h, r.ctypes.data, len(r), float(h0), float(bin_width)))
+
+    def hist_match(self, hu, mask, out, stream=None):
+        """Histogram matching of hu (float32 CUDA [B][n_pix]) into out;
+        mask uint8 CUDA [B][n_pix] or None."""
+        B, n = hu.shape
+        self._check(self._lib.us_sim_hist_match(self.h, _ptr(hu), _ptr(mask) if mask is not None else None, B, n,
+                                                _ptr(out), _stream_handle(stream)))
 
     def refresh_volumes(self, stream=None):
         """Re-read the volumes after their contents changed (label check,
