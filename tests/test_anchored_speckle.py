@@ -107,8 +107,9 @@ def test_gpu_anchored_maps_match_oracle():
     """GPU paths against the oracle with the anchored two-scale maps: the
     pre-PSF image sample by sample (an identity PSF), except where the
     oracle's N1 lies within 1e-4 of the density threshold (the FP32 and FP64
-    decisions may differ there; either is valid); and the three batched paths
-    bit-identical to each other."""
+    decisions may differ there; either is valid); and the batched paths
+    (cluster kernel, two grids, persistent grid) bit-identical to the plain
+    kernels."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -124,14 +125,15 @@ def test_gpu_anchored_maps_match_oracle():
     wl = scene.Workload("anch", [(spec, lab, hu)], probes, envs, poses, options=opt, seed=4242)
     sim = gpu_sim(wl)
     outs = {}
-    for shape in ((8, 32), (1, 16)):
-        sim.set_tuning(shape[0], shape[1], 0)
+    shapes = ((8, 32, 0), (1, 16, 0), (1, 16, 1))          # cluster, two grids, persistent grid
+    for shape in shapes:
+        sim.set_tuning(shape[0], shape[1], 0, shape[2])
         outs[shape] = render_gpu(sim, envs, poses, wl.seed, 3, path=0)
     outs["plain"] = render_gpu(sim, envs, poses, wl.seed, 3, path=1)
     for k in ("envelope", "frame"):
         for b in range(6):
-            assert np.array_equal(outs[(8, 32)][b][k], outs["plain"][b][k])
-            assert np.array_equal(outs[(1, 16)][b][k], outs["plain"][b][k])
+            for shape in shapes:
+                assert np.array_equal(outs[shape][b][k], outs["plain"][b][k]), (shape, k, b)
     tab = scene.tissue_table()
     mu1 = np.array([t.mu1 for t in tab])
     flagged = 0

@@ -349,23 +349,26 @@ extern "C" int run(const unsigned* c, const unsigned* key, unsigned* o, int n) {
 
 
 def test_3d_probe_sweep_equals_2d_renders_and_oracle():
-    """The 3-D probe (50 x 37 x 5 at 2 x 2 x 10 mm): each volumetric image
-    equals the 2-D renders of its five swept planes (host float32 sweep,
-    bit for bit), and sampled slices match the oracle."""
+    """The 3-D probe (50 x 37 x 5 at 2 x 2 x 10 mm): each volumetric image,
+    in every batched form, equals the plain 2-D renders of its five swept
+    planes (host float32 sweep, bit for bit), and sampled slices match the
+    oracle."""
     wl = scene.workload_surgery3d(12)
     sim = gpu_sim(wl)
     E, pitch = scene.SURGERY3D_SLICES, scene.SURGERY3D_PITCH_MM
     envs_x = np.repeat(wl.envs, E, axis=0)
     off = sim.frame_layout(envs_x)
     P = torch.from_numpy(np.ascontiguousarray(wl.poses, np.float32)).cuda()
-    fr3 = torch.full((int(off[-1]),), -7.0, device="cuda")
-    sim.render_3d(wl.envs, P, E, pitch, wl.seed, 2, fr3)
-    torch.cuda.synchronize()
     swept = scene.sweep_elevation(wl.poses, E, pitch)
-    ref = render_gpu(sim, envs_x, swept, wl.seed, 2, debug=False)
-    got = fr3.cpu().numpy()
-    for i in range(len(envs_x)):
-        assert np.array_equal(got[off[i]:off[i] + 37 * 50].reshape(50, 37), ref[i]["frame"]), i
+    ref = render_gpu(sim, envs_x, swept, wl.seed, 2, path=1, debug=False)
+    for shape in ((1, 16, 0), (1, 8, 1), (8, 16, 0)):     # two grids, persistent grid, cluster kernel
+        sim.set_tuning(shape[0], shape[1], 1, shape[2])
+        fr3 = torch.full((int(off[-1]),), -7.0, device="cuda")
+        sim.render_3d(wl.envs, P, E, pitch, wl.seed, 2, fr3)
+        torch.cuda.synchronize()
+        got = fr3.cpu().numpy()
+        for i in range(len(envs_x)):
+            assert np.array_equal(got[off[i]:off[i] + 37 * 50].reshape(50, 37), ref[i]["frame"]), (shape, i)
     which = [0, 7, 31, 59]
     o = render_oracle(dataclasses.replace(wl, envs=envs_x, poses=swept), envs_x, swept, wl.seed, 2, which)
     g = render_gpu(sim, envs_x, swept, wl.seed, 2)
