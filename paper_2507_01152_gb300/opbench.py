@@ -1,11 +1,18 @@
-"""Timing of single surrogate operators on the GPU (CUDA events, after
-warm-up): one 3x3 convolution pass of the tcgen05 implicit GEMM.
+"""Timing of single operators on the GPU (CUDA events, after warm-up).
 
     python -m paper_2507_01152_gb300.opbench fwd|dgrad|wgrad B H Cin Cout [stride] [reps]
+    python -m paper_2507_01152_gb300.opbench hist B H [reps]
 
-B images of H x H pixels (input grid), NHWC BF16 activations with random
-values, Cin -> Cout channels.  Prints the time per call and the rate in
-TFLOP/s (2 x 9 x Cin x Cout multiply-adds per output pixel)."""
+fwd / dgrad / wgrad: one 3x3 convolution pass of the tcgen05 implicit GEMM
+on B images of H x H pixels (input grid), NHWC BF16 activations with random
+values, Cin -> Cout channels; prints the time per call and the rate in
+TFLOP/s (2 x 9 x Cin x Cout multiply-adds per output pixel).
+
+hist: CT histogram matching (us_sim_hist_match) of B images of H x H FP32
+values (normal, 300 HU spread, every pixel considered) to a reference of
+4096 one-HU bins; prints the time per call and the rate in GB/s of
+algorithmic bytes (value and mask read twice, value written: 14 B per
+pixel)."""
 from __future__ import annotations
 
 import sys
@@ -53,7 +60,46 @@ def conv3x3(kind: str, B: int, H: int, Cin: int, Cout: int, stride: int = 1, rep
     return ms, flop / ms / 1e9
 
 
+def hist_match(B: int, H: int, reps: int = 10):
+    import numpy as np
+    import torch
+    from . import build, scene
+    from .ussim import Sim
+    build.build()
+    spec = scene.VolumeSpec(32, 32, 32, 1.0, 1, 7)
+    lab, hu = scene.make_volume(spec)
+    sim = Sim([(torch.from_numpy(lab).cuda(), torch.from_numpy(hu).cuda(), 1.0)], scene.tissue_table(),
+              [scene.linear_probe(16, 32, 30.0, 1.0)])
+    # reference: a CT-like spread of integer HU, one-HU bins from -1024
+    rng = np.random.default_rng(3)
+    vals = np.clip(np.round(rng.gamma(2.5, 150.0, 200000) - 500.0).astype(np.int64) + 1024, 0, 4095)
+    sim.set_hu_reference(np.cumsum(np.bincount(vals, minlength=4096)), -1024.0, 1.0)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn((B, H * H), device="cuda", generator=g) * 300.0
+    m = torch.ones((B, H * H), dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        sim.hist_match(x, m, y)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        sim.hist_match(x, m, y)
+    e.record()
+    e.synchronize()
+    sim.check()
+    ms = a.elapsed_time(e) / reps
+    sim.close()
+    return ms, B * H * H * 14 / ms / 1e6
+
+
 def main(argv):
+    if argv[0] == "hist":
+        B, H = int(argv[1]), int(argv[2])
+        reps = int(argv[3]) if len(argv) > 3 else 10
+        ms, gbs = hist_match(B, H, reps)
+        print(f"hist_match B={B} H={H}: {ms:.4f} ms, {gbs:.1f} GB/s", flush=True)
+        return
     kind, B, H, Cin, Cout = argv[0], *map(int, argv[1:5])
     stride = int(argv[5]) if len(argv) > 5 else 1
     reps = int(argv[6]) if len(argv) > 6 else 10
