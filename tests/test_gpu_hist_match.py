@@ -42,11 +42,12 @@ def _images(rng, B, n):
     return out
 
 
+@pytest.mark.parametrize("n", [65536 + 37, 65536 + 36])     # scalar and four-pixel vector paths
 @pytest.mark.parametrize("nb,h0,w", [(4096, -1024.0, 1.0), (16384, -1024.0, 0.25), (3, -100.0, 70.0), (1, 0.0, 1.0)])
-def test_standalone_matches_oracle_bitwise(sim, nb, h0, w):
+def test_standalone_matches_oracle_bitwise(sim, nb, h0, w, n):
     wl, s = sim
     rng = np.random.default_rng(nb)
-    B, n = 5, 65536 + 37
+    B = 5
     hu = _images(rng, B, n)
     mask = (rng.random((B, n)) < 0.8).astype(np.uint8)
     mask[3] = 0                                             # an image with no considered pixel
