@@ -430,9 +430,9 @@ def run_recon(args):
             ev[0].record(st)
             sim.render(None, P[t], 7, t, frames, stream=st, envs_c=ec)
             ev[1].record(st)
-            sim.recon_update(envs, P[t], 7, t, 4, 0.2, bm, pts, cnt, stream=st)
+            sim.recon_update(envs, P[t], 7, t, 4, 0.2, bm, pts, cnt, stream=st, envs_c=ec)
             ev[2].record(st)
-            sim.recon_observe(envs, P[t], pts, cnt, obs, stream=st)
+            sim.recon_observe(envs, P[t], pts, cnt, obs, stream=st, envs_c=ec)
             ev[3].record(st)
             ev[3].synchronize()
             if t > args.warmup:

@@ -67,11 +67,14 @@ __global__ void recon_observe(RenderParams p, const EnvItem* items, int B, const
                               int cap, unsigned char* obs) {
   const int b = blockIdx.y;
   if (b >= B) return;
+  // the grid covers the lists' capacity; blocks past this list's count
+  // leave before loading anything else
+  const int n = min(counts[b], cap);
+  if (blockIdx.x * blockDim.x >= n) return;
   const EnvItem it = items[b];
   const DevVolume V = p.vols[it.vol];
   bool finite;
   const Pose M = load_pose(p.poses, it.b, finite);
-  const int n = min(counts[b], cap);
   const float third = 0.333333343267f;   // (float)(1 / 3)
   const float vox = V.h;
   unsigned char* o = obs + (long long)b * 64000;

@@ -303,18 +303,21 @@ class Sim:
     def recon_words(self):
         return int(self._lib.us_sim_recon_words(self.h))
 
-    def recon_update(self, envs, poses, seed, step, bone_label, p_miss, bitmaps, points, counts, stream=None):
+    def recon_update(self, envs, poses, seed, step, bone_label, p_miss, bitmaps, points, counts, stream=None,
+                     envs_c=None):
         """add one frame per env to the reconstructions (bitmaps uint32 [B][recon_words()],
         points int32 [B][cap], counts int32 [B]: device tensors, zeroed to start)"""
         B = poses.shape[0]
-        self._check(self._lib.us_sim_recon_update(self.h, make_envs(envs), B, _ptr(poses), seed, step, bone_label,
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_recon_update(self.h, e, B, _ptr(poses), seed, step, bone_label,
                                                   float(p_miss), _ptr(bitmaps), _ptr(points), _ptr(counts),
                                                   points.shape[1], _stream_handle(stream)))
 
-    def recon_observe(self, envs, poses, points, counts, obs, stream=None):
+    def recon_observe(self, envs, poses, points, counts, obs, stream=None, envs_c=None):
         """the reconstructions voxelized in each env's probe frame: obs uint8 [B][40][40][40]"""
         B = poses.shape[0]
-        self._check(self._lib.us_sim_recon_observe(self.h, make_envs(envs), B, _ptr(poses), _ptr(points),
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_recon_observe(self.h, e, B, _ptr(poses), _ptr(points),
                                                    _ptr(counts), points.shape[1], _ptr(obs), _stream_handle(stream)))
 
     def render_timed(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
@@ -474,42 +477,6 @@ class Surrogate:
         out = np.zeros(self.n_params, np.float32)
         self._check(self._lib.us_surr_get_grads(self.h, out.ctypes.data))
         return out
-
-    def render_3d(self, envs, poses, n_elev, elev_pitch_mm, seed, step, frames, stream=None):
-        """Volumetric frames of a 3-D probe: each env's plane swept over n_elev
-        elevation offsets; frames as frame_layout(np.repeat(envs, n_elev, 0))."""
-        B = poses.shape[0]
-        self._check(self._lib.us_sim_render_3d(self.h, make_envs(envs), B, _ptr(poses), n_elev,
-                                               float(elev_pitch_mm), seed, step, _ptr(frames),
-                                               _stream_handle(stream)))
-
-    def recon_words(self):
-        return int(self._lib.us_sim_recon_words(self.h))
-
-    def recon_update(self, envs, poses, seed, step, bone_label, p_miss, bitmaps, points, counts, stream=None):
-        """add one frame per env to the reconstructions (bitmaps uint32 [B][recon_words()],
-        points int32 [B][cap], counts int32 [B]: device tensors, zeroed to start)"""
-        B = poses.shape[0]
-        self._check(self._lib.us_sim_recon_update(self.h, make_envs(envs), B, _ptr(poses), seed, step, bone_label,
-                                                  float(p_miss), _ptr(bitmaps), _ptr(points), _ptr(counts),
-                                                  points.shape[1], _stream_handle(stream)))
-
-    def recon_observe(self, envs, poses, points, counts, obs, stream=None):
-        """the reconstructions voxelized in each env's probe frame: obs uint8 [B][40][40][40]"""
-        B = poses.shape[0]
-        self._check(self._lib.us_sim_recon_observe(self.h, make_envs(envs), B, _ptr(poses), _ptr(points),
-                                                   _ptr(counts), points.shape[1], _ptr(obs), _stream_handle(stream)))
-
-    def render_timed(self, envs, poses, seed, step, frames, stream=None, envs_c=None):
-        """The tuned render with per-kernel CUDA-event times (ms): a list of
-        one (cluster kernel) or two (two-pass: pass A, pass B) durations."""
-        B = poses.shape[0]
-        e = envs_c if envs_c is not None else make_envs(envs)
-        ms = (C.c_float * 2)()
-        n = C.c_int32(0)
-        self._check(self._lib.us_sim_render_timed(self.h, e, B, _ptr(poses), seed, step, _ptr(frames), ms, C.byref(n),
-                                                  _stream_handle(stream)))
-        return [float(ms[i]) for i in range(n.value)]
 
     def check(self, stream=None):
         self._check(self._lib.us_surr_check(self.h, _stream_handle(stream)))
