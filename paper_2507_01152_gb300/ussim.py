@@ -192,11 +192,12 @@ def make_probe(p) -> us_probe:
 
 
 def make_envs(envs) -> C.Array:
+    """us_env array of (volume_id, probe_id) rows: one buffer copy (us_env
+    is two int32, the layout of an int32 [B][2] array)"""
     envs = np.ascontiguousarray(envs, np.int32).reshape(-1, 2)
-    arr = (us_env * max(1, len(envs)))()
-    for i, (v, p) in enumerate(envs):
-        arr[i] = us_env(int(v), int(p))
-    return arr
+    if len(envs) == 0:
+        return (us_env * 1)()
+    return (us_env * len(envs)).from_buffer_copy(envs.tobytes())
 
 
 class Sim:
