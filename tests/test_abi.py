@@ -64,3 +64,17 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(ussim, "_lib", None)
     with pytest.raises(RuntimeError):
         ussim.load()
+
+
+def test_env_array_layout():
+    """the binding's us_env array is the int32 [B][2] rows, in order (it is
+    built by one buffer copy)"""
+    import ctypes as C
+    import numpy as np
+    from paper_2507_01152_gb300.ussim import make_envs, us_env
+    assert C.sizeof(us_env) == 8
+    e = np.array([[1, 2], [3, 4], [0, 7], [5, 0]], np.int64)        # any integer dtype
+    a = make_envs(e)
+    assert [(x.volume_id, x.probe_id) for x in a] == [(1, 2), (3, 4), (0, 7), (5, 0)]
+    assert [(x.volume_id, x.probe_id) for x in make_envs(e[:, ::-1][:, ::-1])] == [(1, 2), (3, 4), (0, 7), (5, 0)]
+    assert len(make_envs(np.zeros((0, 2), np.int32))) == 1          # a valid pointer for an empty batch
