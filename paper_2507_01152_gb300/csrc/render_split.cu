@@ -221,9 +221,9 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
   // the halo lines' labels in 32-sample chunks spread over the warps: a line
   // d lines beyond the group is labelled only below ext[d], the stencil's
   // reach, so the short halo lines do not load a few warps
-  auto label_of = [&](int l, int s, float3& u, int& vi) -> uint8_t {
+  auto label_of = [&](float2 ln, int s, float3& u, int& vi) -> uint8_t {
     float x, z;
-    beam_point(P, P.lines[l], s, x, z);
+    beam_point(P, ln, s, x, z);
     u = to_voxel(cx.M, cx.V.inv_h, x, z);
     vi = nearest_voxel(cx.V, u);
     return vi >= 0 ? __ldg(&cx.V.labels[vi]) : (uint8_t)0;
@@ -231,10 +231,11 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
   for (int l = g0 + warp; l < g1; l += NW) {
     uint8_t* lrow = lbuf + (l - L0) * NS;
     float* prow = zbuf + (l - g0) * RS;
+    const float2 ln = P.lines[l];
     for (int s = lane; s < NS; s += 32) {
       float3 u;
       int vi;
-      const uint8_t lb = label_of(l, s, u, vi);
+      const uint8_t lb = label_of(ln, s, u, vi);
       lrow[s] = lb;
       prow[KA + s] = p.z_mode == 0 ? fmaxf(trilinear_hu(cx.V, u) + 1024.f, 1.f) : tis[lb].z;
       if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + s] = vi;
@@ -256,7 +257,7 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
       if (s < lim) {
         float3 u;
         int vi;
-        lbuf[(l - L0) * NS + s] = label_of(l, s, u, vi);
+        lbuf[(l - L0) * NS + s] = label_of(P.lines[l], s, u, vi);
       }
     }
   }
