@@ -437,3 +437,31 @@ def test_persistent_grid_wait_runs_out_and_reports(c2):
     ref = render_gpu(sim, envs, poses, 5, 1, path=1, debug=False)
     for x, y in zip(ref, got):
         assert np.array_equal(x["frame"], y["frame"])
+
+
+@pytest.mark.parametrize("B", [1, 2, 3])
+def test_persistent_grid_on_tiny_mixed_batches(B):
+    """The persistent grid with fewer work units than resident blocks and
+    probes of different geometry in one batch (tiles waiting on groups of
+    ragged line counts): bit-identical to the plain kernels, both tunings of
+    the group size, with and without graph replay."""
+    lab, hu = _tiny_volume(5)
+    spec = scene.VolumeSpec(18, 16, 14, 1.0, 0, 0)
+    probes = [scene.curvilinear_probe(33, 130, 12.0, 70.0, 5.0, 24, 20, psf_sigma_ax_mm=0.4, psf_sigma_lat_mm=0.5),
+              scene.linear_probe(7, 37, 9.0, 0.8, psf_sigma_ax_mm=0.5, psf_sigma_lat_mm=1.0)]
+    rng = np.random.default_rng(40 + B)
+    envs = np.stack([np.zeros(B), np.arange(B) % 2], axis=1).astype(np.int32)
+    poses = np.stack([_rand_pose(rng, (9.0, 8.0, 2.0)) for _ in range(B)])
+    wl = scene.Workload("tinyp", [(spec, lab, hu)], probes, envs, poses, seed=5)
+    sim = gpu_sim(wl)
+    ref = render_gpu(sim, envs, poses, 5, 3, path=1)
+    for nw in (8, 16, 32):
+        for graph in (0, 1):
+            sim.set_tuning(1, nw, graph, 1)
+            got = render_gpu(sim, envs, poses, 5, 3, path=0) if graph == 0 else \
+                render_gpu(sim, envs, poses, 5, 3, path=0, debug=False)
+            for x, y in zip(ref, got):
+                for k in y:
+                    assert np.array_equal(x[k], y[k]), (nw, graph, k)
+    sim.check()
+    sim.close()
