@@ -133,14 +133,9 @@ __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProb
   }
 }
 
-template <bool REG_TAPS>
 __device__ __forceinline__ void lateral_psf_any(const RenderParams& p, const DevProbe& P, long long beam_off,
                                                 const float* abuf, float* ybuf, const float* wlat, int NS, int K,
                                                 int w0, int w1, int y1, int s0) {
-  if constexpr (!REG_TAPS) {
-    lateral_psf<0>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1, s0);
-    return;
-  }
 #define US_LAT(k) \
   case k: lateral_psf<k>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1, s0); break;
   switch (K) {
@@ -306,7 +301,7 @@ __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(Ren
 // Pass B work unit `blk` = item * gpi_image + tile, run by NT threads.
 // With a.done set, the unit first waits (bounded) until the pass-A groups
 // holding its staged rows have published them.
-template <int NT, bool REG_TAPS>
+template <int NT>
 __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArgs& a, int blk) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int GB = a.GB;
@@ -385,7 +380,7 @@ __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArg
   }
   __syncthreads();
 
-  lateral_psf_any<REG_TAPS>(p, P, it.beam_off, abuf, ybuf, wlat, NS, KL, w0, w1, y1, s0);
+  lateral_psf_any(p, P, it.beam_off, abuf, ybuf, wlat, NS, KL, w0, w1, y1, s0);
   __syncthreads();
 
   float* out = p.frames + it.frame_off;
@@ -419,7 +414,7 @@ __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArg
 }
 
 __global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, SplitArgs a) {
-  image_body<kImageThreads, true>(p, a, blockIdx.x);
+  image_body<kImageThreads>(p, a, blockIdx.x);
 }
 
 // Both passes in one persistent grid (one block per resident slot): blocks
@@ -427,7 +422,6 @@ __global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, 
 // tiles in environment order; a tile waits only for the groups holding its
 // rows, all of which were taken earlier by blocks that are running and wait
 // on nothing, so every wait ends.  Pass B's tiles fill pass A's last wave.
-constexpr bool PERSIST_REG_TAPS = true;
 template <int G, bool ANCHORED>
 __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_persist(RenderParams p, SplitArgs a) {
   __shared__ int job;
@@ -441,7 +435,7 @@ __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_persist(R
     if (j < na)
       lines_body<G, ANCHORED>(p, a, j);
     else
-      image_body<G * 32, PERSIST_REG_TAPS>(p, a, j - na);
+      image_body<G * 32>(p, a, j - na);
     __syncthreads();   // shared memory and `job` are reused by the next unit
   }
 }
