@@ -214,8 +214,8 @@ static void or_sample_voxel_coords(const or_probe* p, const float* M, float inv_
  * FP32 path as the nearest voxel with 1/(c 2^k) in place of 1/h.  The cell's
  * Philox-4x32-10 words, counter (n_x, n_y, n_z, k << 16 | volume), key =
  * (seed_lo, seed_hi) (no step: the maps are fixed), give two standard
- * normals by Box-Muller (cosine branch): Z0 from words 0, 1 and Z1 from
- * words 2, 3.  N0 = sum_k a_k Z0_k, N1 = sum_k a_k Z1_k, a_k proportional
+ * normals as the Box-Muller pair of words 0 and 1: Z0 = r cos(theta),
+ * Z1 = r sin(theta), r = sqrt(-2 ln u0), theta = 2 pi u1.  N0 = sum_k a_k Z0_k, N1 = sum_k a_k Z1_k, a_k proportional
  * to 2^(-k/2) with sum a_k^2 = 1 (unit variance; coarser scales weigh
  * less).  T = N0 sigma0 + mu0 where N1 <= mu1, else 0. */
 static void or_anchored_noise(const float pc[3], const or_options* o, uint32_t vol_id, uint64_t seed,
@@ -239,9 +239,11 @@ static void or_anchored_noise(const float pc[3], const or_options* o, uint32_t v
     key[0] = (uint32_t)seed;
     key[1] = (uint32_t)(seed >> 32);
     oracle_philox4x32_10(ctr, key, w);
+    /* the Box-Muller pair of words 0 and 1: r cos(theta), r sin(theta) */
     const double a = pow(2.0, -0.5 * k) / norm;
-    *n0 += a * sqrt(-2.0 * log(or_uniform(w[0]))) * cos(2.0 * M_PI * or_uniform(w[1]));
-    *n1 += a * sqrt(-2.0 * log(or_uniform(w[2]))) * cos(2.0 * M_PI * or_uniform(w[3]));
+    const double r = sqrt(-2.0 * log(or_uniform(w[0]))), th = 2.0 * M_PI * or_uniform(w[1]);
+    *n0 += a * r * cos(th);
+    *n1 += a * r * sin(th);
   }
 }
 

@@ -256,7 +256,8 @@ __device__ __forceinline__ float lateral_spacing(const DevProbe& P, int s) {
 // of volume `vol`: (N0, N1).  Scale k: the nearest cell of edge c 2^k
 // (cell index floor(pos / (c 2^k) + 1/2), FP32 as for voxels), whose
 // Philox words (counter = cell, k << 16 | vol; key = seed) give two
-// standard normals by Box-Muller; N = sum_k a_k N_k.
+// standard normals as the Box-Muller pair of words 0 and 1 (r cos, r sin);
+// N = sum_k a_k N_k.
 __device__ __forceinline__ float2 anchored_maps(const RenderParams& p, float3 pos, unsigned vol) {
   float n0 = 0.f, n1 = 0.f;
   for (int k = 0; k < p.speckle_levels; ++k) {
@@ -266,12 +267,12 @@ __device__ __forceinline__ float2 anchored_maps(const RenderParams& p, float3 po
     const int cz = (int)floorf(__fadd_rn(__fmul_rn(pos.z, ic), 0.5f));
     const uint4 w = philox4x32_10(make_uint4((unsigned)cx, (unsigned)cy, (unsigned)cz, ((unsigned)k << 16) | (vol & 0xFFFFu)),
                                   p.key_fixed);
-    float s0, c0, s1, c1;
-    // angles 2 pi u shifted into [-pi, pi): cos(t) = -cos(t - pi)
-    __sincosf(fmaf(6.28318530717958648f, u01(w.y), -3.14159265358979324f), &s0, &c0);
-    __sincosf(fmaf(6.28318530717958648f, u01(w.w), -3.14159265358979324f), &s1, &c1);
-    n0 = fmaf(p.amp[k], -sqrtf(-2.f * __logf(u01(w.x))) * c0, n0);
-    n1 = fmaf(p.amp[k], -sqrtf(-2.f * __logf(u01(w.z))) * c1, n1);
+    float sn, cs;
+    // angle 2 pi u shifted into [-pi, pi): cos(t) = -cos(t - pi), sin(t) = -sin(t - pi)
+    __sincosf(fmaf(6.28318530717958648f, u01(w.y), -3.14159265358979324f), &sn, &cs);
+    const float r = sqrtf(-2.f * __logf(u01(w.x)));
+    n0 = fmaf(p.amp[k], -r * cs, n0);
+    n1 = fmaf(p.amp[k], -r * sn, n1);
   }
   return make_float2(n0, n1);
 }
