@@ -31,7 +31,10 @@
  *    US_ERR_INVALID_ARG with a message in us_sim_last_error().  Errors found
  *    on the device (non-finite pose entries) set a sticky error word that
  *    us_sim_check() reads.  No entry point aborts or traps.
- *  - One handle may be used from one host thread at a time.
+ *  - One handle may be used from one host thread at a time.  Its batched
+ *    renders of one batch signature (the same env list) share per-signature
+ *    workspace (line buffer, work counters): on different streams, order
+ *    them (events) or use one handle per stream.
  *  - Output is a pure function of (inputs, seed, step): two calls with the
  *    same arguments produce bit-identical frames.
  */
