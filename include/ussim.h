@@ -32,9 +32,10 @@
  *    on the device (non-finite pose entries) set a sticky error word that
  *    us_sim_check() reads.  No entry point aborts or traps.
  *  - One handle may be used from one host thread at a time.  Its batched
- *    renders of one batch signature (the same env list) share per-signature
- *    workspace (line buffer, work counters): on different streams, order
- *    them (events) or use one handle per stream.
+ *    renders share workspace (per batch signature: line buffer and the
+ *    persistent grid's counters; per handle: the cluster kernel's work
+ *    counter and the error word): on different streams, order them with
+ *    events, or use one handle per stream.
  *  - Output is a pure function of (inputs, seed, step): two calls with the
  *    same arguments produce bit-identical frames.
  */
