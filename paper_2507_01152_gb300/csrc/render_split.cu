@@ -567,12 +567,16 @@ cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float
                               int pass, cudaStream_t st) {
   SplitArgs a = sh.args;
   a.beam = beam;
-  if (pass == 2) {
+  if (pass >= 2) {
     // sync: the unit counter, then one completion flag per pass-A group
-    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(unsigned) * (1 + (size_t)max_items * a.gpi_lines), st);
-    if (e != cudaSuccess) return e;
+    // (pass 3: the caller has zeroed them)
+    if (pass == 2) {
+      cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(unsigned) * (1 + (size_t)max_items * a.gpi_lines), st);
+      if (e != cudaSuccess) return e;
+    }
     a.work = sync;
     a.done = sync + 1;
+    pass = 2;
   }
   switch (sh.G) {
     case 8: return launch_g<8>(p, sh, a, max_items, pass, st);

@@ -926,7 +926,7 @@ us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const fl
     // the reset of the synchronisation words sits outside the timed kernel
     e = cudaMemsetAsync(pl->d_sync, 0, sizeof(unsigned) * split_sync_words(B), st);
     cudaEventRecord(ev[0], st);
-    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->d_sync, B, 2, st);
+    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->d_sync, B, 3, st);
     cudaEventRecord(ev[1], st);
   } else if (two_pass) {
     cudaEventRecord(ev[0], st);

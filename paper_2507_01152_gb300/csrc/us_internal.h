@@ -102,7 +102,8 @@ cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* bea
                          cudaStream_t st);
 // one pass: 0 = lines (pass A), 1 = image (pass B)
 // pass 0: pass A, 1: pass B (separate grids); 2: both in the persistent
-// grid (resets `sync` first)
+// grid (resets `sync` first); 3: the persistent grid on a `sync` the
+// caller has zeroed
 cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
                               int pass, cudaStream_t st);
 // the persistent grid with its unit counter started past every pass-A group

@@ -465,3 +465,27 @@ def test_persistent_grid_on_tiny_mixed_batches(B):
                     assert np.array_equal(x[k], y[k]), (nw, graph, k)
     sim.check()
     sim.close()
+
+
+def test_render_timed_reports_each_form_and_renders_the_same(c2):
+    """us_sim_render_timed: two durations for the two grids, one for the
+    persistent grid and for the cluster kernel; the frames equal
+    us_sim_render's."""
+    wl, sim = c2
+    envs, poses = wl.envs[:8], wl.poses[:8]
+    off = sim.frame_layout(envs)
+    P = torch.from_numpy(np.ascontiguousarray(poses, np.float32)).cuda()
+    old = sim.get_tuning()
+    try:
+        for shape, n in (((1, 16, 0), 2), ((1, 16, 1), 1), ((8, 32, 0), 1)):
+            sim.set_tuning(shape[0], shape[1], 0, shape[2])
+            a = torch.full((int(off[-1]),), -7.0, device="cuda")
+            b = torch.full((int(off[-1]),), -7.0, device="cuda")
+            ms = sim.render_timed(envs, P, 3, 4, a)
+            sim.render(envs, P, 3, 4, b)
+            torch.cuda.synchronize()
+            assert len(ms) == n and all(t > 0 for t in ms), (shape, ms)
+            assert torch.equal(a, b), shape
+            sim.check()
+    finally:
+        sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
