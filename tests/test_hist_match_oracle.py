@@ -102,3 +102,17 @@ def test_raw_slice_agrees_with_the_scaled_slice():
     assert np.array_equal(a[..., 0], b[..., 0] / 4.0)
     assert np.array_equal(a[..., 1], np.clip(b[..., 1] / 1000.0, -1.0, 3.0))
     assert np.array_equal(a[..., 2], b[..., 2])
+
+
+def test_single_bin_references_are_closed_forms():
+    """a reference with one non-empty bin m sends every considered pixel to
+    that bin's centre; with one bin in all, to h0 + w/2"""
+    rng = np.random.default_rng(6)
+    v = _img(rng, 3000)
+    for m in (0, 700, 1500, NB - 1):
+        R = np.zeros(NB, np.int64)
+        R[m:] = 5
+        out = hm.match(v, None, R, H0, W)
+        assert np.all(out == np.float32(np.float32(m + 0.5) * np.float32(W) + np.float32(H0))), m
+    out = hm.match(v, None, np.array([7], np.int64), -20.0, 3.0)
+    assert np.all(out == np.float32(-18.5))
