@@ -56,20 +56,8 @@ using namespace ussim;
 
 extern "C" us_status us_sim_render_plain_static(us_sim* s, const us_env* envs, int32_t B, const float* poses,
                                                 uint64_t seed, uint64_t step, float* frames, void* stream) {
-  if (!s) return US_ERR_INVALID_ARG;
-  if (B < 0) {
-    s->last_error = "B must be >= 0";
-    return US_ERR_INVALID_ARG;
-  }
-  if (B == 0) return US_OK;
-  if (!envs || !poses || !frames) {
-    s->last_error = "NULL envs, poses or frames";
-    return US_ERR_INVALID_ARG;
-  }
-  if (reinterpret_cast<uintptr_t>(frames) & 15u) {
-    s->last_error = "frames must be 16-byte aligned";
-    return US_ERR_INVALID_ARG;
-  }
+  us_status r = sim_check_render_args(s, envs, B, poses, frames);
+  if (r != US_OK || B == 0) return r;
   const int n_probes = (int)s->probes.size();
   for (int b = 0; b < B; ++b) {
     const us_env& e = envs[b];
@@ -98,18 +86,9 @@ extern "C" us_status us_sim_render_plain_static(us_sim* s, const us_env* envs, i
   scr.Y = reinterpret_cast<float*>(b8 + 8 * kStaticBeamSamples);
   scr.lab = b8 + 12 * kStaticBeamSamples;
 
-  RenderParams p{};
-  p.vols = s->d_vols;
-  p.probes = s->d_probes;
-  p.pairs = s->d_pairs;
-  p.poses = poses;
-  p.key = make_uint2((uint32_t)seed ^ (uint32_t)(step * 0x9E3779B9ull), (uint32_t)(seed >> 32));
-  p.refl_power = s->opt.refl_power;
-  p.transmission = s->opt.transmission;
-  p.z_mode = s->opt.z_mode;
-  p.speckle = s->opt.speckle;
-  p.frames = frames;
-  p.err = s->d_err;
+  // the same parameters as every other render entry point (options,
+  // speckle key, volume-anchored map scales), with no debug exports
+  RenderParams p = sim_render_params(s, poses, seed, step, frames);
   p.n_items = B;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   long long frame_off = 0;

@@ -547,6 +547,15 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) 
 
 }  // namespace
 
+namespace ussim {
+RenderParams sim_render_params(const us_sim* s, const float* poses, uint64_t seed, uint64_t step, float* frames) {
+  return base_params(s, poses, seed, step, frames);
+}
+us_status sim_check_render_args(us_sim* s, const us_env* envs, int B, const float* poses, float* frames) {
+  return check_render_args(s, envs, B, poses, frames);
+}
+}  // namespace ussim
+
 extern "C" {
 
 const char* us_status_string(us_status st) {
@@ -855,6 +864,18 @@ us_status us_sim_render_3d(us_sim* s, const us_env* envs, int32_t B, const float
   if ((e = launch_expand_elevation(poses, B, n_elev, elev_pitch_mm, s->d_poses3d, st)) != cudaSuccess)
     return cuda_fail(s, e, "elevation sweep");
   return do_render(s, ex.data(), BE, s->d_poses3d, seed, step, frames, nullptr, nullptr, nullptr, nullptr, 0, st);
+}
+
+us_status us_sim_sweep_poses(const float* poses, int32_t B, int32_t n_elev, float elev_pitch_mm, float* out,
+                             void* stream) {
+  if (B < 0 || n_elev < 1 || n_elev > 64 || !std::isfinite(elev_pitch_mm) || elev_pitch_mm < 0.f)
+    return US_ERR_INVALID_ARG;
+  if (B == 0) return US_OK;
+  if (!poses || !out || (long long)B * n_elev > (1ll << 30)) return US_ERR_INVALID_ARG;
+  return launch_expand_elevation(poses, B, n_elev, elev_pitch_mm, out, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? US_OK
+             : US_ERR_CUDA;
 }
 
 int64_t us_sim_recon_words(const us_sim* s) {

@@ -138,6 +138,12 @@ cudaError_t launch_recon_update(const RenderParams& p, const EnvItem* items, int
 cudaError_t launch_recon_observe(const RenderParams& p, const EnvItem* items, int B, const int* points,
                                  const int* counts, int cap, unsigned char* obs, cudaStream_t st);
 
+// the render parameters every render entry point starts from (handle's
+// tables, options, speckle key of (seed, step), anchored-map scales), and
+// the argument checks they share (NULL buffers, 16-byte frames, 4-byte poses)
+RenderParams sim_render_params(const us_sim* s, const float* poses, uint64_t seed, uint64_t step, float* frames);
+us_status sim_check_render_args(us_sim* s, const us_env* envs, int B, const float* poses, float* frames);
+
 // label check at creation: max label of a volume
 cudaError_t max_label(const uint8_t* labels, long long n, unsigned* d_out, cudaStream_t st);
 // corner records of V's HU grid into out ((nx+1)(ny+1)(nz+1) records)
