@@ -489,7 +489,12 @@ def run_ours(args):
         import dataclasses
         E, pitch = scene.SURGERY3D_SLICES, scene.SURGERY3D_PITCH_MM
         wl3 = wl
-        wl = dataclasses.replace(wl, envs=np.repeat(wl.envs, E, axis=0), poses=scene.sweep_elevation(wl.poses, E, pitch))
+        from paper_2507_01152_gb300 import ussim
+        p3 = torch.from_numpy(np.ascontiguousarray(wl.poses, np.float32)).cuda()
+        swept = torch.empty((len(wl.poses) * E, 3, 4), dtype=torch.float32, device="cuda")
+        ussim.sweep_poses(p3, E, pitch, swept)
+        torch.cuda.synchronize()
+        wl = dataclasses.replace(wl, envs=np.repeat(wl.envs, E, axis=0), poses=swept.cpu().numpy())
     B = len(wl.envs)
     vols = [(torch.from_numpy(lab).cuda(), torch.from_numpy(hu).cuda(), spec.voxel_mm) for (spec, lab, hu) in wl.volumes]
     sim = Sim(vols, scene.tissue_table(), wl.probes, wl.options)

@@ -354,6 +354,16 @@ US_API us_status us_sim_render_3d(us_sim* sim, const us_env* envs, int32_t B, co
                                   int32_t n_elev, float elev_pitch_mm, uint64_t seed, uint64_t step,
                                   float* frames, void* stream);
 
+/* The elevation sweep of us_sim_render_3d on its own: out[b * n_elev + e] =
+ * pose b translated by y_e = (e - (n_elev - 1) / 2) * elev_pitch_mm along its
+ * own y axis (t' = t + R[:, 1] y_e; FP32, one rounding per product and sum),
+ * the rotation unchanged (Sec. 4, Task 3: H x W x E volumetric images).
+ * poses: DEVICE [B][3][4]; out: DEVICE [B * n_elev][3][4], caller-owned, not
+ * overlapping poses.  n_elev 1..64, pitch finite and >= 0, B >= 0 (0: no-op),
+ * else US_ERR_INVALID_ARG; a failed launch gives US_ERR_CUDA. */
+US_API us_status us_sim_sweep_poses(const float* poses, int32_t B, int32_t n_elev, float elev_pitch_mm,
+                                    float* out, void* stream);
+
 /* Reconstruction observation of the bone-surface task (Sec. 4, Task 2;
  * App. C: 40 x 40 x 40 voxels of 3 mm, 20% missing surface points).
  * Ground-truth surface point: a beam sample s > 0 whose nearest label is

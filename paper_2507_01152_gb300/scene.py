@@ -439,18 +439,6 @@ def workload_surgery3d(B=128):
                     np.zeros((B, 2), np.int32), dorsal_poses(spec, B, 2003, tilt_deg=5.0), seed=0x5EED0006)
 
 
-def sweep_elevation(poses, n_elev, pitch_mm) -> np.ndarray:
-    """Host restatement of the 3-D probe's elevation sweep, in float32 with
-    one rounding per product and sum: pose b, slice e -> entry b * n_elev + e,
-    t' = t + R[:, 1] * ((e - (n_elev - 1) / 2) * pitch)."""
-    P = np.asarray(poses, np.float32).reshape(-1, 3, 4)
-    out = np.repeat(P, n_elev, axis=0).copy()
-    for e in range(n_elev):
-        y = np.float32(np.float32(e - 0.5 * (n_elev - 1)) * np.float32(pitch_mm))
-        out[e::n_elev, :, 3] = (P[:, :, 3] + (P[:, :, 1] * y).astype(np.float32)).astype(np.float32)
-    return out
-
-
 # --------------------------------------------------------------------------
 # surrogate inputs
 # --------------------------------------------------------------------------

@@ -88,6 +88,7 @@ SIGNATURES = {
     "us_sim_check": (C.c_int, [_P, _P]),
     "us_sim_render_timed": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, _P, _P]),
     "us_sim_render_3d": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, C.c_float, C.c_uint64, C.c_uint64, _P, _P]),
+    "us_sim_sweep_poses": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_float, _P, _P]),
     "us_sim_recon_words": (C.c_int64, [_P]),
     "us_sim_recon_update": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, C.c_int32, C.c_float, _P, _P,
                                       _P, C.c_int32, _P]),
@@ -184,6 +185,16 @@ def op(name, *args, stream=None):
     st = getattr(L, name)(*conv, _stream_handle(stream))
     if st != US_OK:
         raise UsError(st, name)
+
+
+def sweep_poses(poses, n_elev, elev_pitch_mm, out, stream=None):
+    """The 3-D probe's elevation sweep on the device (us_sim_sweep_poses):
+    poses [B][3][4] -> out [B * n_elev][3][4], both device float32."""
+    L = load()
+    B = int(poses.shape[0])
+    st = L.us_sim_sweep_poses(_ptr(poses), B, int(n_elev), float(elev_pitch_mm), _ptr(out), _stream_handle(stream))
+    if st != US_OK:
+        raise UsError(st, "us_sim_sweep_poses")
 
 
 def make_probe(p) -> us_probe:

@@ -359,7 +359,7 @@ def test_3d_probe_sweep_equals_2d_renders_and_oracle():
     envs_x = np.repeat(wl.envs, E, axis=0)
     off = sim.frame_layout(envs_x)
     P = torch.from_numpy(np.ascontiguousarray(wl.poses, np.float32)).cuda()
-    swept = scene.sweep_elevation(wl.poses, E, pitch)
+    swept = oracle.sweep_elevation(wl.poses, E, pitch)
     ref = render_gpu(sim, envs_x, swept, wl.seed, 2, path=1, debug=False)
     for shape in ((1, 16, 0), (1, 8, 1), (8, 16, 0)):     # two grids, persistent grid, cluster kernel
         sim.set_tuning(shape[0], shape[1], 1, shape[2])
