@@ -71,7 +71,7 @@ class OrOptions(C.Structure):
 
 class OrFrameOut(C.Structure):
     _fields_ = [("frame", C.c_void_p), ("envelope", C.c_void_p), ("logimg", C.c_void_p),
-                ("S", C.c_void_p), ("E", C.c_void_p), ("cos_theta", C.c_void_p),
+                ("S", C.c_void_p), ("T", C.c_void_p), ("E", C.c_void_p), ("cos_theta", C.c_void_p),
                 ("hu", C.c_void_p), ("nn_index", C.c_void_p), ("label", C.c_void_p), ("n1", C.c_void_p)]
 
 
@@ -207,19 +207,24 @@ def scan_convert(probe, logimg):
 
 
 def render_frame(labels, hu, voxel_mm, table, probe, options, pose, env=0, seed=0, step=0, vol_id=0):
-    """Render one frame; returns a dict of every export (numpy arrays; "n1"
-    holds the anchored scatter map N1 per sample, NaN in the beam-keyed mode)."""
+    """Render one frame; returns a dict of every export (numpy arrays;
+    "envelope" is I = P (x) R_imp + E (P (x) T) before the log, "S" the image
+    under an identity PSF (R_imp + E T), "T" the scatter pattern, "E" the
+    energy; "n1" holds the anchored scatter map N1 per sample, NaN in the
+    beam-keyed mode)."""
     vol = _Vol(labels, hu, voxel_mm, vol_id)
     NL, NS = probe.n_lines, probe.n_samples
     res = {
         "frame": np.zeros((probe.out_h, probe.out_w)),
         "envelope": np.zeros((NL, NS)), "logimg": np.zeros((NL, NS)), "S": np.zeros((NL, NS)),
+        "T": np.zeros((NL, NS)),
         "E": np.zeros((NL, NS)), "cos_theta": np.zeros((NL, NS)), "hu": np.zeros((NL, NS)),
         "nn_index": np.zeros((NL, NS), np.int32), "label": np.zeros((NL, NS), np.uint8),
         "n1": np.full((NL, NS), np.nan),
     }
     o = OrFrameOut(*[res[k].ctypes.data for k in
-                     ("frame", "envelope", "logimg", "S", "E", "cos_theta", "hu", "nn_index", "label", "n1")])
+                     ("frame", "envelope", "logimg", "S", "T", "E", "cos_theta", "hu", "nn_index", "label",
+                      "n1")])
     tab = or_table(table)
     pr = or_probe(probe)
     op = or_options(options)
@@ -321,4 +326,23 @@ def sample_slice_raw(labels, hu, voxel_mm, probe, pose):
     pr = or_probe(probe)
     M = np.ascontiguousarray(pose, np.float32).reshape(12)
     lib().oracle_sample_slice_raw(C.byref(vol.desc), C.byref(pr), _ptr(M), _ptr(out))
+    return out
+
+
+def sweep_elevation(poses, n_elev, pitch_mm):
+    """Elevation sweep of the 3-D probe (Sec. 4, Task 3: volumetric images
+    H x W x E; App. C: E = 5 planes 10 mm apart).  Plane e of pose b is the
+    pose moved along its own elevation axis (the rotation's y column) by
+    y_e = (e - (E - 1) / 2) * pitch: t' = t + R[:, 1] * y_e.  FP32 with one
+    rounding per product and per sum, pose by pose and plane by plane;
+    entry b * E + e of the result."""
+    P = np.asarray(poses, np.float32).reshape(-1, 3, 4)
+    out = np.zeros((len(P) * n_elev, 3, 4), np.float32)
+    for b in range(len(P)):
+        for e in range(n_elev):
+            y = np.float32(np.float32(e - 0.5 * (n_elev - 1)) * np.float32(pitch_mm))
+            M = P[b].copy()
+            for r in range(3):
+                M[r, 3] = np.float32(P[b, r, 3] + np.float32(P[b, r, 1] * y))
+            out[b * n_elev + e] = M
     return out

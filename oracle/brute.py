@@ -6,8 +6,10 @@ definition, with no running sums and no separable filtering:
 
 * remaining energy E(u) = E0 exp(-f int_0^y alpha dv) (App. B.2) as a fresh
   sum over all samples above u, for every u;
-* the image I = P (x) (R_imp + B_imp) as the full 2-D sum over the PSF
-  support;
+* the image I = P (x) R_imp + E (P (x) T) (App. B.2: the reflection
+  impulses blurred; the backscatter B = E . P (x) T, the scatter pattern
+  blurred and then scaled by the energy at the pixel itself), each
+  convolution as the full 2-D sum over the PSF support;
 * its own Philox-4x32-10 (Salmon et al., SC 2011) on Python integers and its
   own Box-Muller transform.
 
@@ -159,6 +161,8 @@ def render(labels, hu, voxel_mm, table, probe, options, pose, env=0, seed=0, ste
     key1 = (seed >> 32) & MASK
 
     S = np.zeros((NL, NS))
+    R = np.zeros((NL, NS))
+    Tm = np.zeros((NL, NS))
     E = np.zeros((NL, NS))
     CT = np.zeros((NL, NS))
     for l in range(NL):
@@ -183,6 +187,8 @@ def render(labels, hu, voxel_mm, table, probe, options, pose, env=0, seed=0, ste
                 T = n0 * float(F32(tis.sigma0)) + float(F32(tis.mu0)) if w[2 + (s & 1)] < t1 else 0.0
             else:
                 T = float(F32(tis.mu0))
+            R[l, s] = rimp
+            Tm[l, s] = T
             S[l, s] = rimp + Es * T
 
     wax = _taps(float(F32(probe.psf_sigma_ax_mm)), dr64)
@@ -190,15 +196,18 @@ def render(labels, hu, voxel_mm, table, probe, options, pose, env=0, seed=0, ste
                 if curv else float(F32(probe.pitch_mm)))
     wlat = _taps(float(F32(probe.psf_sigma_lat_mm)), dlat_mid)
     Ka, Kl = len(wax) // 2, len(wlat) // 2
+    def blur(X, l, s):
+        acc = []
+        for j in range(-Kl, Kl + 1):
+            for k in range(-Ka, Ka + 1):
+                if 0 <= l + j < NL and 0 <= s + k < NS:
+                    acc.append(wlat[j + Kl] * wax[k + Ka] * X[l + j, s + k])
+        return math.fsum(acc)
+
     I = np.zeros((NL, NS))
     for l in range(NL):
         for s in range(NS):
-            acc = []
-            for j in range(-Kl, Kl + 1):
-                for k in range(-Ka, Ka + 1):
-                    if 0 <= l + j < NL and 0 <= s + k < NS:
-                        acc.append(wlat[j + Kl] * wax[k + Ka] * S[l + j, s + k])
-            I[l, s] = math.fsum(acc)
+            I[l, s] = blur(R, l, s) + E[l, s] * blur(Tm, l, s)
 
     dyn = float(F32(probe.dyn_range_db))
     Y = np.zeros((NL, NS))
@@ -231,5 +240,5 @@ def render(labels, hu, voxel_mm, table, probe, options, pose, env=0, seed=0, ste
                 bot = Y[l0, s0 + 1] + a * (Y[l0 + 1, s0 + 1] - Y[l0, s0 + 1])
                 frame[r, c] = top + b * (bot - top)
 
-    return {"frame": frame, "envelope": I, "logimg": Y, "S": S, "E": E, "cos_theta": CT,
+    return {"frame": frame, "envelope": I, "logimg": Y, "S": S, "T": Tm, "E": E, "cos_theta": CT,
             "hu": huv, "nn_index": nn, "label": lab}

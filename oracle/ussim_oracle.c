@@ -14,8 +14,9 @@
  *
  * Pipeline (Fig. 2 caption and Sec. 4 "Ultrasound simulation"):
  *   probe pose -> image plane -> label/HU slice on the scanline grid ->
- *   image model I = R + B (App. B.2) -> PSF -> log compression ->
- *   scan conversion.
+ *   image model I = R + B (App. B.2): R = P (x) R_imp (the blurred
+ *   reflection impulses), B = E . (P (x) T) (the scatter pattern blurred,
+ *   then scaled by the local energy) -> log compression -> scan conversion.
  * The readings taken where the paper is silent are marked READING.
  */
 #include <math.h>
@@ -62,9 +63,10 @@ typedef struct {
 /* optional per-frame exports; any pointer may be NULL ([NL][NS] unless noted) */
 typedef struct {
   double* frame;       /* [out_h][out_w] final image */
-  double* envelope;    /* I = P (x) S, before log */
+  double* envelope;    /* I = P (x) R_imp + E . (P (x) T), before log */
   double* logimg;      /* log-compressed beam image */
-  double* S;           /* R_imp + B_imp before the PSF */
+  double* S;           /* R_imp + E . T: the image under an identity PSF */
+  double* T;           /* scatter pattern T (App. B.2) */
   double* E;           /* remaining energy */
   double* cos_theta;   /* incidence cosine (1 where G = 0) */
   double* hu;          /* interpolated HU */
@@ -365,13 +367,17 @@ int oracle_render_frame(const or_volume* vol, const or_tissue* table, int n_labe
   uint8_t* lab = (uint8_t*)malloc(N);
   double* hu = (double*)malloc(N * sizeof(double));
   double* S = (double*)malloc(N * sizeof(double));
-  double* tmp = (double*)malloc(N * sizeof(double));
+  double* Rm = (double*)malloc(N * sizeof(double));
+  double* Tm = (double*)malloc(N * sizeof(double));
+  double* Em = (double*)malloc(N * sizeof(double));
+  double* tmpR = (double*)malloc(N * sizeof(double));
+  double* tmpT = (double*)malloc(N * sizeof(double));
   double* I = (double*)malloc(N * sizeof(double));
   double* Y = (double*)malloc(N * sizeof(double));
   double* wax = (double*)malloc((2 * d.k_ax + 1) * sizeof(double));
   double* wlat = (double*)malloc((2 * d.k_lat + 1) * sizeof(double));
   int rc = 0;
-  if (!lab || !hu || !S || !tmp || !I || !Y || !wax || !wlat) { rc = -3; goto done; }
+  if (!lab || !hu || !S || !Rm || !Tm || !Em || !tmpR || !tmpT || !I || !Y || !wax || !wlat) { rc = -3; goto done; }
 
   const float inv_h = (float)(1.0 / (double)vol->voxel_mm);
 
@@ -455,7 +461,7 @@ int oracle_render_frame(const or_volume* vol, const or_tissue* table, int n_labe
         double a = fabs(cth * r);
         Rimp = E * (opt->refl_power == 2 ? a * a : a);
       }
-      /* scatter pattern T and backscatter impulse E * T */
+      /* scatter pattern T (App. B.2: T~ = N0 sigma0 + mu0 where N1 <= mu1, else 0) */
       double T;
       if (opt->speckle && opt->speckle_anchor) {
         float pc[3];
@@ -474,35 +480,47 @@ int oracle_render_frame(const or_volume* vol, const or_tissue* table, int n_labe
       } else {
         T = (double)ti->mu0;
       }
-      double Bimp = E * T;
-      S[(int64_t)l * NS + s] = Rimp + Bimp;
+      Rm[(int64_t)l * NS + s] = Rimp;
+      Tm[(int64_t)l * NS + s] = T;
+      Em[(int64_t)l * NS + s] = E;
+      S[(int64_t)l * NS + s] = Rimp + E * T;
       if (out && out->E) out->E[(int64_t)l * NS + s] = E;
       if (out && out->cos_theta) out->cos_theta[(int64_t)l * NS + s] = cth;
     }
   }
 
-  /* 3. PSF: separable Gaussian on the beam grid, zero padded */
+  /* 3. PSF: separable Gaussian on the beam grid, zero padded, applied to
+   * the reflection impulses and to the scatter pattern separately.
+   * Reflection (READING): R = P (x) R_imp, the impulses G |E cos r|^p
+   * blurred, so a one-sample interface spreads over the PSF (the printed
+   * |E cos r| . P (x) G would leave it one sample thick wherever r is zero
+   * off the boundary).  Backscatter, as printed in App. B.2:
+   * B(u) = E(u) . (P (x) T)(u): the scatter pattern is blurred first, then
+   * scaled by the energy at u itself.  I = R + B. */
   oracle_psf_taps(p->psf_sigma_ax_mm, d.dr, wax, 2 * d.k_ax + 1);
   oracle_psf_taps(p->psf_sigma_lat_mm, d.dlat_mid, wlat, 2 * d.k_lat + 1);
   for (int l = 0; l < NL; ++l)
     for (int s = 0; s < NS; ++s) {
-      double acc = 0.0;
+      double accR = 0.0, accT = 0.0;
       for (int k = -d.k_ax; k <= d.k_ax; ++k) {
         int ss = s + k;
         if (ss < 0 || ss >= NS) continue;
-        acc += wax[k + d.k_ax] * S[(int64_t)l * NS + ss];
+        accR += wax[k + d.k_ax] * Rm[(int64_t)l * NS + ss];
+        accT += wax[k + d.k_ax] * Tm[(int64_t)l * NS + ss];
       }
-      tmp[(int64_t)l * NS + s] = acc;
+      tmpR[(int64_t)l * NS + s] = accR;
+      tmpT[(int64_t)l * NS + s] = accT;
     }
   for (int l = 0; l < NL; ++l)
     for (int s = 0; s < NS; ++s) {
-      double acc = 0.0;
+      double accR = 0.0, accT = 0.0;
       for (int j = -d.k_lat; j <= d.k_lat; ++j) {
         int ll = l + j;
         if (ll < 0 || ll >= NL) continue;
-        acc += wlat[j + d.k_lat] * tmp[(int64_t)ll * NS + s];
+        accR += wlat[j + d.k_lat] * tmpR[(int64_t)ll * NS + s];
+        accT += wlat[j + d.k_lat] * tmpT[(int64_t)ll * NS + s];
       }
-      I[(int64_t)l * NS + s] = acc;
+      I[(int64_t)l * NS + s] = accR + Em[(int64_t)l * NS + s] * accT;
     }
 
   /* 4. log compression, READING: 20 log10(I / E0) over a dynamic range DR
@@ -514,12 +532,14 @@ int oracle_render_frame(const or_volume* vol, const or_tissue* table, int n_labe
 
   if (out) {
     if (out->S) memcpy(out->S, S, N * sizeof(double));
+    if (out->T) memcpy(out->T, Tm, N * sizeof(double));
     if (out->envelope) memcpy(out->envelope, I, N * sizeof(double));
     if (out->logimg) memcpy(out->logimg, Y, N * sizeof(double));
     if (out->frame) oracle_scan_convert(p, Y, out->frame);
   }
 done:
-  free(lab); free(hu); free(S); free(tmp); free(I); free(Y); free(wax); free(wlat);
+  free(lab); free(hu); free(S); free(Rm); free(Tm); free(Em); free(tmpR); free(tmpT); free(I); free(Y);
+  free(wax); free(wlat);
   return rc;
 }
 

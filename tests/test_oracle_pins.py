@@ -128,6 +128,94 @@ def test_homogeneous_medium_decays_exponentially():
     np.testing.assert_allclose(res["E"][5], 2.0 * np.exp(-c * s), rtol=1e-12)
 
 
+def _partial_tap_sums(taps, n):
+    """W[i] = the sum of the taps that land inside [0, n) around index i
+    (zero padding at the borders)"""
+    K = len(taps) // 2
+    return np.array([sum(taps[k + K] for k in range(-K, K + 1) if 0 <= i + k < n) for i in range(n)])
+
+
+@pytest.mark.parametrize("probe_kind", ["linear", "curvilinear"])
+def test_homogeneous_backscatter_is_energy_times_blurred_scatter(probe_kind):
+    """App. B.2 fixes the backscatter as B = E . (P (x) T): the scatter
+    pattern is blurred, then scaled by the energy at the pixel itself.  In a
+    homogeneous attenuating medium with speckle off, T = mu0 everywhere in the
+    volume and there are no interfaces, so the whole envelope is the closed
+    form I(l, s) = E(l, s) mu0 W_lat(l) W_ax(s), W the sums of the taps that
+    fall inside the frame (1 in the interior): I = E mu0 exactly away from the
+    borders.  Blurring E . T instead (P (x) (E T)) would give
+    E_s mu0 sum_k w_k e^(-c k) in the interior, which differs by far more than
+    the tolerance here."""
+    alpha_db, mu0 = 1.1, 0.7
+    table = [scene.Tissue(0.0, 1.5, 0.0, 0.0, -math.inf), scene.Tissue(alpha_db, 1.6, mu0, 0.0, 0.0)]
+    lab, hu = _homog((160, 160, 160), 1)
+    if probe_kind == "linear":
+        probe = scene.linear_probe(32, 256, 80.0, 0.5, f_mhz=5.0, e0=2.0)
+        pose = _axis_pose([(1, 0, 0), (0, 1, 0), (0, 0, 1)], (80.0, 80.0, 4.0))
+        dlat = f32(0.5)
+    else:
+        probe = scene.curvilinear_probe(48, 200, 60.0, 50.0, 30.0, 64, 48, f_mhz=5.0, e0=2.0)
+        pose = _axis_pose([(1, 0, 0), (0, 1, 0), (0, 0, 1)], (80.0, 80.0, 4.0))
+        dlat = (f32(30.0) + 0.5 * f32(60.0)) * math.radians(f32(50.0)) / 47
+    res = oracle.render_frame(lab, hu, 1.0, table, probe, scene.Options(1, 1, 1, 0), pose)
+    NL, NS = probe.n_lines, probe.n_samples
+    dr = f32(probe.depth_mm) / NS
+    assert np.all(res["label"] == 1)                            # every sample inside the tissue
+    wax = oracle.psf_taps(f32(0.3), dr)
+    wlat = oracle.psf_taps(f32(1.0), dlat)
+    want = res["E"] * f32(mu0) * np.outer(_partial_tap_sums(wlat, NL), _partial_tap_sums(wax, NS))
+    np.testing.assert_allclose(res["envelope"], want, rtol=1e-12)
+    c = 5.0 * f32(alpha_db) * NP_PER_DB * (dr / 10.0)
+    s = np.arange(NS)
+    np.testing.assert_allclose(res["E"], np.broadcast_to(2.0 * np.exp(-c * s), (NL, NS)), rtol=1e-12)
+    Ka, Kl = len(wax) // 2, len(wlat) // 2
+    inner = (slice(Kl, NL - Kl), slice(Ka, NS - Ka))
+    np.testing.assert_allclose(res["envelope"][inner], f32(mu0) * res["E"][inner], rtol=1e-12)
+    # the other composition's interior value is distinguishable at this tolerance
+    other = f32(mu0) * res["E"][inner] * sum(w * math.exp(-c * k) for k, w in zip(range(-Ka, Ka + 1), wax))
+    assert np.min(np.abs(other / res["envelope"][inner] - 1)) > 1e-5
+
+
+def test_backscatter_blurs_the_pattern_not_the_energy_brute_force():
+    """The same composition in the pure-Python brute force (full 2-D sums),
+    with an energy that varies across the PSF support (bone-like attenuation)
+    and speckle on: I = P (x) R_imp + E (P (x) T) term by term."""
+    table = [scene.Tissue(0.0, 1.48, 0.0, 0.0, -math.inf), scene.Tissue(20.0, 1.6, 0.8, 0.3, 0.8)]
+    lab, hu = _homog((12, 12, 12), 1)
+    probe = scene.linear_probe(5, 24, 6.0, 0.5, psf_sigma_ax_mm=0.5, psf_sigma_lat_mm=0.6)
+    pose = _axis_pose([(1, 0, 0), (0, 1, 0), (0, 0, 1)], (6.0, 6.0, 2.0))
+    b = brute.render(lab, hu, 1.0, table, probe, scene.Options(1, 1, 1, 1), pose, env=2, seed=5, step=1)
+    dr = f32(6.0) / 24
+    wax = oracle.psf_taps(f32(0.5), dr)
+    wlat = oracle.psf_taps(f32(0.6), f32(0.5))
+    P2 = np.outer(wlat, wax)
+    Ka, Kl = len(wax) // 2, len(wlat) // 2
+    Tp = np.pad(b["T"], ((Kl, Kl), (Ka, Ka)))
+    blurred = np.array([[np.sum(P2 * Tp[l:l + 2 * Kl + 1, s:s + 2 * Ka + 1]) for s in range(24)] for l in range(5)])
+    np.testing.assert_allclose(b["envelope"], b["E"] * blurred, rtol=1e-12, atol=1e-300)
+    o = oracle.render_frame(lab, hu, 1.0, table, probe, scene.Options(1, 1, 1, 1), pose, env=2, seed=5, step=1)
+    np.testing.assert_allclose(o["envelope"], b["envelope"], rtol=1e-12)
+    np.testing.assert_array_equal(o["T"], b["T"])
+
+
+@pytest.mark.parametrize("mu0, want", [(1.0, 1.0), (10.0 ** -1.5, 0.5), (1e-3, 0.0), (0.0, 0.0), (-1.0, 0.0),
+                                       (10.0 ** -0.75, 0.75), (1e-4, 0.0), (3.0, 1.0)])
+def test_log_compression_closed_forms(mu0, want):
+    """Log compression y = clamp((20 log10(I / E0) + DR) / DR, 0, 1),
+    DR = 60 dB: with no attenuation, no interfaces, no speckle and no PSF the
+    envelope is I = E0 mu0 everywhere, so I = E0 gives 1, I = E0 10^(-DR/20)
+    gives 0, 30 dB below E0 gives 0.5, I <= 0 and anything below the range
+    give 0, anything above E0 gives 1."""
+    table = [scene.Tissue(0.0, 1.5, 0.0, 0.0, -math.inf), scene.Tissue(0.0, 1.6, mu0, 0.0, 0.0)]
+    lab, hu = _homog((40, 40, 40), 1)
+    probe = scene.linear_probe(8, 64, 20.0, 0.5, e0=3.0, psf_sigma_ax_mm=0.0, psf_sigma_lat_mm=0.0)
+    pose = _axis_pose([(1, 0, 0), (0, 1, 0), (0, 0, 1)], (20.0, 20.0, 4.0))
+    res = oracle.render_frame(lab, hu, 1.0, table, probe, scene.Options(1, 1, 1, 0), pose)
+    np.testing.assert_allclose(res["envelope"], 3.0 * f32(mu0), rtol=1e-15)
+    np.testing.assert_allclose(res["logimg"], want, atol=1e-6)   # mu0 crosses the ABI as float32
+    np.testing.assert_allclose(res["frame"], res["logimg"].T, atol=0)
+
+
 @pytest.mark.parametrize("p", [1, 2])
 @pytest.mark.parametrize("tau", [0, 1])
 def test_single_planar_interface(p, tau):
@@ -366,3 +454,26 @@ def test_touched_voxels_small():
                         if 0 <= q[0] < nx and 0 <= q[1] < ny and 0 <= q[2] < nz:
                             seen.add(q)
     assert tot == per[0] == len(seen)
+
+
+def test_elevation_sweep_closed_forms():
+    """The 3-D probe's elevation sweep (Sec. 4, Task 3; App. C: 5 planes
+    10 mm apart): plane e of a pose is the pose moved by
+    y_e = (e - (E - 1) / 2) * pitch along its own elevation axis (the
+    rotation's y column), the rotation unchanged.  Checked on dyadic poses
+    (exact in FP32) against hand-written translations."""
+    ident = _axis_pose([(1, 0, 0), (0, 1, 0), (0, 0, 1)], (10.0, 20.0, 30.0))
+    quarter = _axis_pose([(0, 1, 0), (0, 0, 1), (1, 0, 0)], (1.5, -2.25, 4.0))   # y axis along +z
+    out = oracle.sweep_elevation(np.stack([ident, quarter]), 5, 10.0)
+    assert out.shape == (10, 3, 4)
+    for e in range(5):
+        y = (e - 2) * 10.0
+        np.testing.assert_array_equal(out[e, :, :3], ident[:, :3])
+        np.testing.assert_array_equal(out[e, :, 3], [10.0, 20.0 + y, 30.0])
+        np.testing.assert_array_equal(out[5 + e, :, :3], quarter[:, :3])
+        np.testing.assert_array_equal(out[5 + e, :, 3], [1.5, -2.25, 4.0 + y])
+    # an even count straddles the pose: offsets -1.5, -0.5, 0.5, 1.5 pitches
+    out4 = oracle.sweep_elevation(ident[None], 4, 2.0)
+    np.testing.assert_array_equal(out4[:, 1, 3], [17.0, 19.0, 21.0, 23.0])
+    # one plane: the pose itself
+    np.testing.assert_array_equal(oracle.sweep_elevation(quarter[None], 1, 7.0)[0], quarter)
