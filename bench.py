@@ -38,19 +38,20 @@ METRIC = "US frames/s on 1 GB300 (physics vs surrogate) at stated error; % HBM r
 
 # Algorithmic ALU work of the physics path, in lane operations (one FP32 /
 # INT32 lane op per lane per cycle; an FMA and a shared-memory load count
-# once each): ~200 per beam sample (Philox ~60, transcendentals ~15,
-# gather and interpolation ~30, PSF 2 x (13 + 21) taps as FMA + load, rest
-# ~60) and ~20 per scan-converted output pixel.  Of these, the lateral PSF
-# (21 FMA + 21 loads) and the log compression (~5) per sample and the
-# per-pixel work belong to pass B of the two-pass path; the rest to pass A.
-OPS_PER_SAMPLE = 200
+# once each): ~270 per beam sample (Philox ~60, transcendentals ~15,
+# gather and interpolation ~30, the PSF on the reflection impulses and on
+# the scatter pattern, 2 x (13 + 21) taps as FMA + load each, the image
+# R + E (P (x) T) as one FMA + one load, rest ~60) and ~20 per
+# scan-converted output pixel.  Of these, the lateral PSF of both
+# (2 x 21 FMA + 2 x 21 loads), the image (2) and the log compression (~5)
+# per sample and the per-pixel work belong to pass B of the two-pass path;
+# the rest to pass A.
+OPS_PER_SAMPLE = 270
 OPS_PER_PIXEL = 20
-OPS_PER_SAMPLE_PASS_B = 47
+OPS_PER_SAMPLE_PASS_B = 91
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the
-# current kernel source (None until captured; reset when the kernel changes)
-KERNEL_DRAM_BYTES = {("c2_batched_curvilinear_64env", "split_persist", 16): 105945344 + 21466880,
-                     ("paper_replica_linear_200x150_100env", "split_lines", 8): 144545024 + 12519424,
-                     ("paper_replica_linear_200x150_100env", "split_image", 8): 12082944 + 0}
+# current kernel source (absent until captured; dropped when the kernel changes)
+KERNEL_DRAM_BYTES = {}
 
 # Algorithmic bytes of one launch of the default workload: the union of
 # voxels read by the nearest / trilinear footprints of all 64 frames (label

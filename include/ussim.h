@@ -229,7 +229,7 @@ US_API us_status us_sim_render_plain(us_sim* sim, const us_env* envs, int32_t B,
  * process whose device memory is already fully claimed by its own
  * allocator).  Same frames as us_sim_render_plain (same kernels, frame
  * layout of us_sim_frame_layout), but the per-environment scratch lives in
- * a fixed 1.625 MiB array compiled into the library, which every GPU that
+ * a fixed 2.625 MiB array compiled into the library, which every GPU that
  * loads the library holds until the process exits.  Limit: each env's
  * beam grid must have at most 256 x 512 = 131072 samples (n_lines x
  * n_samples), else US_ERR_INVALID_ARG before any launch.  The call makes

@@ -3,14 +3,16 @@
 // One thread-block cluster renders one environment's frame at a time and
 // takes the next environment from a global counter (costliest first).  The
 // frame's scanlines are split evenly over the cluster's CTAs; each CTA keeps
-// its lines' labels, pre-PSF image and log image in shared memory, and the
+// its lines' labels, scatter pattern and reflection impulses (then their
+// axially filtered forms), energy and log image in shared memory, and the
 // stages that need neighbouring lines (incidence angle, lateral PSF, scan
 // conversion) read them from the other CTAs through distributed shared
 // memory.  Nothing of a frame but the final image touches global memory.
 //
 // Per environment: (1) slice: nearest label and impedance of every sample
 // of own lines, cluster barrier; (2) scanline model + in-place axial PSF per
-// own line, cluster barrier; (3) lateral PSF + log compression, cluster
+// own line, cluster barrier; (3) lateral PSF, image
+// I = (P (x) R_imp) + E (P (x) T) (App. B.2) and log compression, cluster
 // barrier; (4) scan conversion (curvilinear) or transposed store (linear)
 // with streaming stores.  Cross-CTA rows are reached through per-item
 // tables of row pointers into the owning CTA's shared memory.
@@ -33,28 +35,40 @@ struct ItemCtx {
   int finite;
 };
 
-// In-place axial PSF of one line, one warp.  `prow` is the padded row: K
-// zeros, NS samples, K zeros, so every tap reads in bounds.  Chunk c's
-// results are written back only after chunk c+1 has been computed, so every
-// read sees unfiltered data (K <= 32).  Tap order matches the plain kernel.
-__device__ __forceinline__ void axial_psf_padded(float* prow, int NS, const float* w, int K, int lane) {
-  float prev = 0.f;
+// In-place axial PSF of one line's two padded rows (scatter pattern and
+// reflection impulses), one warp: K zeros, NS samples, K zeros, so every
+// tap reads in bounds.  Chunk c's results are written back only after chunk
+// c+1 has been computed, so every read sees unfiltered data (K <= 32).  Tap
+// order matches the plain kernel.
+__device__ __forceinline__ void axial_psf_padded(float* pt, float* pr, int NS, const float* w, int K, int lane) {
+  float prev_t = 0.f, prev_r = 0.f;
   int prev_s = -1;
   const int taps = 2 * K + 1;
   for (int c = 0; c < NS; c += 32) {
     const int s = c + lane;
-    float acc = 0.f;
+    float acc_t = 0.f, acc_r = 0.f;
     if (s < NS) {
-      const float* q = prow + s;
-      for (int k = 0; k < taps; ++k) acc = fmaf(w[k], q[k], acc);
+      const float* qt = pt + s;
+      const float* qr = pr + s;
+      for (int k = 0; k < taps; ++k) {
+        acc_t = fmaf(w[k], qt[k], acc_t);
+        acc_r = fmaf(w[k], qr[k], acc_r);
+      }
     }
     __syncwarp();
-    if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
+    if (prev_s >= 0 && prev_s < NS) {
+      pt[K + prev_s] = prev_t;
+      pr[K + prev_s] = prev_r;
+    }
     __syncwarp();
-    prev = acc;
+    prev_t = acc_t;
+    prev_r = acc_r;
     prev_s = s;
   }
-  if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
+  if (prev_s >= 0 && prev_s < NS) {
+    pt[K + prev_s] = prev_t;
+    pr[K + prev_s] = prev_r;
+  }
   __syncwarp();
 }
 
@@ -65,11 +79,13 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_r
   __shared__ int slot[2];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  float* sbuf = reinterpret_cast<float*>(smem);                   // impedance, then S, then axially filtered S
-  float* ybuf = reinterpret_cast<float*>(smem + L.off_y);         // log image of own lines
+  float* sbuf = reinterpret_cast<float*>(smem);                   // impedance, then T, then P_ax (x) T
+  float* rbuf = reinterpret_cast<float*>(smem + L.off_r);         // R_imp, then P_ax (x) R_imp
+  float* ybuf = reinterpret_cast<float*>(smem + L.off_y);         // energy, then log image of own lines
   uint8_t* lbuf = smem + L.off_lab;                               // labels of own lines
   const uint8_t** lab_row = reinterpret_cast<const uint8_t**>(smem + L.off_lrow);  // any line -> its label row
-  const float** s_row = reinterpret_cast<const float**>(smem + L.off_srow);        // any line -> its filtered row
+  const float** s_row = reinterpret_cast<const float**>(smem + L.off_srow);        // any line -> its filtered T row
+  const float** r_row = reinterpret_cast<const float**>(smem + L.off_rrow);        // any line -> its filtered R row
   const float** y_row = reinterpret_cast<const float**>(smem + L.off_yrow);        // any line -> its log row
   float* wax = reinterpret_cast<float*>(smem + L.off_wax);
   float* wlat = reinterpret_cast<float*>(smem + L.off_wlat);     // zero-padded at both ends
@@ -110,6 +126,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_r
       const int r = m / LPC, row = m - r * LPC;
       lab_row[m] = cl.map_shared_rank(lbuf, r) + row * NS;
       s_row[m] = cl.map_shared_rank(sbuf, r) + row * RS + KA;
+      r_row[m] = cl.map_shared_rank(rbuf, r) + row * RS + KA;
       y_row[m] = cl.map_shared_rank(ybuf, r) + row * RS;
     }
     if (!cx.finite && rank == 0 && tid == 0) atomicOr(p.err, kErrNonFinitePose);
@@ -135,6 +152,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_r
       for (int q = lane; q < KA; q += 32) {
         sbuf[lr * RS + q] = 0.f;
         sbuf[lr * RS + KA + NS + q] = 0.f;
+        rbuf[lr * RS + q] = 0.f;
+        rbuf[lr * RS + KA + NS + q] = 0.f;
       }
     }
     cl.sync();
@@ -143,6 +162,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_r
     for (int lr = warp; lr < n_own; lr += NW) {
       const int l = lbeg + lr;
       float* row = sbuf + lr * RS + KA;
+      float* rrow = rbuf + lr * RS + KA;
+      float* erow = ybuf + lr * RS;
       const uint8_t* lrow = lbuf + lr * NS;
       auto labf = [&](int line, int s) -> unsigned { return lab_row[line][s]; };
       auto own = [&](int s) -> unsigned { return lrow[s]; };
@@ -153,14 +174,21 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_r
         beam_point(P, ln, s, x, z);
         return sample_position(cx.M, x, z);
       };
-      scanline_model(p, P, tis, cx.pair, b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; }, posf,
-                     cx.it.vol);
+      scanline_model(p, P, tis, cx.pair, b, l, lane, labf, own, zf,
+                     [&](int s, float r, float t, float e) {
+                       row[s] = t;
+                       rrow[s] = r;
+                       erow[s] = e;
+                     },
+                     posf, cx.it.vol);
       __syncwarp();
-      axial_psf_padded(sbuf + lr * RS, NS, wax, KA, lane);
+      axial_psf_padded(sbuf + lr * RS, rbuf + lr * RS, NS, wax, KA, lane);
     }
     cl.sync();
 
-    // (3) lateral PSF (two lines per thread) and log compression
+    // (3) lateral PSF of both filtered rows (two lines per thread), the
+    // image with the line's own energy, and log compression (in place of
+    // the energy)
     {
       const int nblk = (n_own + 1) >> 1, nch = (NS + 31) >> 5;
       for (int u = warp; u < nblk * nch; u += NW) {
@@ -169,18 +197,22 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_r
         if (s >= NS) continue;
         const int lr0 = 2 * blk, l0 = lbeg + lr0;
         const int mlo = max(l0 - KL, 0), mhi = min(l0 + 1 + KL, NL - 1);
-        float acc0 = 0.f, acc1 = 0.f;
+        float t0 = 0.f, t1 = 0.f, r0 = 0.f, r1 = 0.f;
         for (int m = mlo; m <= mhi; ++m) {
-          const float v = s_row[m][s];
+          const float vt = s_row[m][s], vr = r_row[m][s];
           const int q = m - l0 + KL + 1;
-          acc0 = fmaf(wlat[q], v, acc0);
-          acc1 = fmaf(wlat[q - 1], v, acc1);
+          t0 = fmaf(wlat[q], vt, t0);
+          t1 = fmaf(wlat[q - 1], vt, t1);
+          r0 = fmaf(wlat[q], vr, r0);
+          r1 = fmaf(wlat[q - 1], vr, r1);
         }
+        const float acc0 = image_value(r0, t0, ybuf[lr0 * RS + s]);
         const float y0 = log_compress(P, acc0);
         ybuf[lr0 * RS + s] = y0;
         if (p.envelope) p.envelope[cx.it.beam_off + (long long)l0 * NS + s] = acc0;
         if (p.logimg) p.logimg[cx.it.beam_off + (long long)l0 * NS + s] = y0;
         if (lr0 + 1 < n_own) {
+          const float acc1 = image_value(r1, t1, ybuf[(lr0 + 1) * RS + s]);
           const float y1 = log_compress(P, acc1);
           ybuf[(lr0 + 1) * RS + s] = y1;
           if (p.envelope) p.envelope[cx.it.beam_off + (long long)(l0 + 1) * NS + s] = acc1;
@@ -255,6 +287,8 @@ bool fused_shape_fits(FusedShape& s, const std::vector<ProbeHost>& probes, int n
   sbuf = up(sbuf, 4);
   s.sbuf_floats = (int)sbuf;
   long long off = sbuf * 4;
+  s.lay.off_r = (int)off;
+  off += sbuf * 4;
   s.lay.off_y = (int)off;
   off += sbuf * 4;
   s.lay.off_lab = (int)off;
@@ -262,6 +296,8 @@ bool fused_shape_fits(FusedShape& s, const std::vector<ProbeHost>& probes, int n
   s.lay.off_lrow = (int)off;
   off += max_nl * 8;
   s.lay.off_srow = (int)off;
+  off += max_nl * 8;
+  s.lay.off_rrow = (int)off;
   off += max_nl * 8;
   s.lay.off_yrow = (int)off;
   off += max_nl * 8;

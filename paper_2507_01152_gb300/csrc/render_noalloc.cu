@@ -3,10 +3,11 @@
 // must not allocate device memory while they render.
 //
 // The five plain kernels need, for the environment in flight, the label
-// slice (1 byte per beam sample) and three FP32 beam planes (pre-PSF image,
-// axially filtered image, log image): 13 bytes per sample.  The array below
-// holds that for beam grids of up to kStaticBeamSamples samples (256 lines
-// x 512 samples), 1.625 MiB.  Every GPU that loads this library holds the
+// slice (1 byte per beam sample) and five FP32 beam planes (reflection
+// impulses, later the log image; scatter pattern; energy; and the two
+// axially filtered planes): 21 bytes per sample.  The array below holds that
+// for beam grids of up to kStaticBeamSamples samples (256 lines x 512
+// samples), 2.625 MiB.  Every GPU that loads this library holds the
 // array until the process exits.  All calls share it, and it keeps the
 // last call's contents; the kernels overwrite every element they read
 // before reading it, so nothing needs clearing.  Two calls whose work
@@ -21,7 +22,7 @@
 namespace ussim {
 
 constexpr long long kStaticBeamSamples = 256LL * 512LL;
-constexpr size_t kStaticScratchBytes = (size_t)kStaticBeamSamples * 13;
+constexpr size_t kStaticScratchBytes = (size_t)kStaticBeamSamples * kPlainScratchBytesPerSample;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -81,10 +82,13 @@ extern "C" us_status us_sim_render_plain_static(us_sim* s, const us_env* envs, i
   }
   PlainScratch scr;
   unsigned char* b8 = static_cast<unsigned char*>(base);
-  scr.S = reinterpret_cast<float*>(b8);
-  scr.A = reinterpret_cast<float*>(b8 + 4 * kStaticBeamSamples);
-  scr.Y = reinterpret_cast<float*>(b8 + 8 * kStaticBeamSamples);
-  scr.lab = b8 + 12 * kStaticBeamSamples;
+  scr.R = reinterpret_cast<float*>(b8);
+  scr.T = reinterpret_cast<float*>(b8 + 4 * kStaticBeamSamples);
+  scr.E = reinterpret_cast<float*>(b8 + 8 * kStaticBeamSamples);
+  scr.AR = reinterpret_cast<float*>(b8 + 12 * kStaticBeamSamples);
+  scr.AT = reinterpret_cast<float*>(b8 + 16 * kStaticBeamSamples);
+  scr.Y = scr.R;
+  scr.lab = b8 + 20 * kStaticBeamSamples;
 
   // the same parameters as every other render entry point (options,
   // speckle key, volume-anchored map scales), with no debug exports

@@ -1,6 +1,7 @@
 // Plain per-environment render: for each environment in turn, one kernel
-// per stage (label slice, scanline model, axial PSF, lateral PSF + log,
-// scan conversion) through global scratch.  This is the simple form the
+// per stage (label slice, scanline model, axial PSF, lateral PSF + image
+// I = P (x) R_imp + E (P (x) T) + log, scan conversion) through global
+// scratch.  This is the simple form the
 // fused batched kernel is measured against.
 #include "us_internal.h"
 #include "us_scanline.cuh"
@@ -27,8 +28,8 @@ __global__ void plain_slice(RenderParams p, EnvItem it, uint8_t* lab) {
   if (p.label) p.label[it.beam_off + q] = lb;
 }
 
-// scanline model, one warp per line
-__global__ void plain_lines(RenderParams p, EnvItem it, const uint8_t* lab, float* S) {
+// scanline model, one warp per line: R_imp, T and E of every sample
+__global__ void plain_lines(RenderParams p, EnvItem it, const uint8_t* lab, float* R, float* Tp, float* E) {
   const DevProbe P = p.probes[it.probe];
   const DevVolume V = p.vols[it.vol];
   const DevPair pair = p.pairs[it.pair];
@@ -42,39 +43,57 @@ __global__ void plain_lines(RenderParams p, EnvItem it, const uint8_t* lab, floa
   auto labf = [&](int line, int s) -> unsigned { return lab[line * NS + s]; };
   auto own = [&](int s) -> unsigned { return lab[l * NS + s]; };
   auto zf = [&](int s) -> float { return sample_impedance(p.z_mode, P, V, M, ln, s, P.tissue, lab[l * NS + s]); };
-  float* row = S + (size_t)l * NS;
+  const size_t row = (size_t)l * NS;
   auto posf = [&](int s) -> float3 {
     float x, z;
     beam_point(P, ln, s, x, z);
     return sample_position(M, x, z);
   };
-  scanline_model(p, P, P.tissue, pair, it.b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; }, posf,
-                 it.vol);
+  scanline_model(p, P, P.tissue, pair, it.b, l, lane, labf, own, zf,
+                 [&](int s, float r, float t, float e) {
+                   R[row + s] = r;
+                   Tp[row + s] = t;
+                   E[row + s] = e;
+                 },
+                 posf, it.vol);
 }
 
-__global__ void plain_psf_axial(RenderParams p, EnvItem it, const float* S, float* A) {
+// axial PSF of the reflection impulses and of the scatter pattern
+__global__ void plain_psf_axial(RenderParams p, EnvItem it, const float* R, const float* Tp, float* AR, float* AT) {
   const DevProbe P = p.probes[it.probe];
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= P.nl * P.ns) return;
   const int l = q / P.ns, s = q - l * P.ns;
-  float acc = 0.f;
+  float accR = 0.f, accT = 0.f;
   for (int k = -P.k_ax; k <= P.k_ax; ++k) {
     const int ss = s + k;
-    if (ss >= 0 && ss < P.ns) acc = fmaf(P.w_ax[k + P.k_ax], S[l * P.ns + ss], acc);
+    if (ss >= 0 && ss < P.ns) {
+      const float w = P.w_ax[k + P.k_ax];
+      accR = fmaf(w, R[l * P.ns + ss], accR);
+      accT = fmaf(w, Tp[l * P.ns + ss], accT);
+    }
   }
-  A[q] = acc;
+  AR[q] = accR;
+  AT[q] = accT;
 }
 
-__global__ void plain_psf_lateral_log(RenderParams p, EnvItem it, const float* A, float* Y) {
+// lateral PSF of both, the image I = (P (x) R) + E (P (x) T), log compression
+__global__ void plain_psf_lateral_log(RenderParams p, EnvItem it, const float* AR, const float* AT, const float* E,
+                                      float* Y) {
   const DevProbe P = p.probes[it.probe];
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= P.nl * P.ns) return;
   const int l = q / P.ns, s = q - l * P.ns;
-  float acc = 0.f;
+  float accR = 0.f, accT = 0.f;
   for (int j = -P.k_lat; j <= P.k_lat; ++j) {
     const int ll = l + j;
-    if (ll >= 0 && ll < P.nl) acc = fmaf(P.w_lat[j + P.k_lat], A[ll * P.ns + s], acc);
+    if (ll >= 0 && ll < P.nl) {
+      const float w = P.w_lat[j + P.k_lat];
+      accR = fmaf(w, AR[ll * P.ns + s], accR);
+      accT = fmaf(w, AT[ll * P.ns + s], accT);
+    }
   }
+  const float acc = image_value(accR, accT, E[q]);
   const float y = log_compress(P, acc);
   Y[q] = y;
   if (p.envelope) p.envelope[it.beam_off + q] = acc;
@@ -110,9 +129,9 @@ cudaError_t launch_plain_env(const RenderParams& p, const EnvItem& it, const Pro
   const int n = ph.desc.n_lines * ph.desc.n_samples;
   const int nout = ph.desc.out_w * ph.desc.out_h;
   plain_slice<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.lab);
-  plain_lines<<<(ph.desc.n_lines + 3) / 4, 128, 0, st>>>(p, it, scr.lab, scr.S);
-  plain_psf_axial<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.S, scr.A);
-  plain_psf_lateral_log<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.A, scr.Y);
+  plain_lines<<<(ph.desc.n_lines + 3) / 4, 128, 0, st>>>(p, it, scr.lab, scr.R, scr.T, scr.E);
+  plain_psf_axial<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.R, scr.T, scr.AR, scr.AT);
+  plain_psf_lateral_log<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.AR, scr.AT, scr.E, scr.Y);
   plain_scan_convert<<<(nout + 255) / 256, 256, 0, st>>>(p, it, scr.Y);
   return cudaGetLastError();
 }
@@ -125,9 +144,9 @@ cudaError_t launch_plain(const RenderParams& p, const EnvItem* items_host, int n
     const int n = ph.desc.n_lines * ph.desc.n_samples;
     const int nout = ph.desc.out_w * ph.desc.out_h;
     plain_slice<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.lab);
-    plain_lines<<<(ph.desc.n_lines + 3) / 4, 128, 0, st>>>(p, it, scr.lab, scr.S);
-    plain_psf_axial<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.S, scr.A);
-    plain_psf_lateral_log<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.A, scr.Y);
+    plain_lines<<<(ph.desc.n_lines + 3) / 4, 128, 0, st>>>(p, it, scr.lab, scr.R, scr.T, scr.E);
+    plain_psf_axial<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.R, scr.T, scr.AR, scr.AT);
+    plain_psf_lateral_log<<<(n + 255) / 256, 256, 0, st>>>(p, it, scr.AR, scr.AT, scr.E, scr.Y);
     plain_scan_convert<<<(nout + 255) / 256, 256, 0, st>>>(p, it, scr.Y);
   }
   return cudaGetLastError();

@@ -3,15 +3,16 @@
 // Pass A (split_lines): one block per (environment, group of G lines), one
 // warp per line.  The block takes the nearest labels of its lines and of the
 // lines the incidence stencil can reach on either side (at most kThetaDMax),
-// the
-// impedance of its own lines, runs the scanline model and the in-place
-// axial PSF, and writes the axially filtered line to a beam-layout buffer
-// in global memory (L2-resident for moderate batches).
+// the impedance of its own lines, runs the scanline model (reflection
+// impulses R_imp, scatter pattern T, energy E), applies the axial PSF to
+// R_imp and T in place, and writes the filtered pair (AR, AT) and E to a
+// beam-layout line buffer in global memory.
 //
 // Pass B (split_image): one block per (environment, wedge of G lines).  The
-// block stages the filtered lines its wedge needs (its lines, one more line
-// for the bilinear step, and the lateral PSF's reach on both sides), forms
-// the lateral PSF and the log image of its lines in shared memory, and
+// block stages the filtered pairs its wedge needs (its lines, one more line
+// for the bilinear step, and the lateral PSF's reach on both sides) and the
+// energy of its own lines, forms the lateral PSF of both, the image
+// I = (P (x) R_imp) + E (P (x) T) (App. B.2) and its log in shared memory, and
 // scan-converts the output pixels assigned to the wedge: a host-built list,
 // per probe, of the pixels whose bilinear footprint lies on the wedge's
 // lines (pixels outside the fan go to the wedge of the preceding in-fan
@@ -31,12 +32,15 @@
 
 namespace ussim {
 
-// axial PSF of one padded row in place (K zeros, NS samples, K zeros).
-// KC > 0: the half-width is the compile-time KC (== K) and the taps sit in
-// registers; KC = 0: any K, taps read from shared memory.  Same tap order.
+// axial PSF of two padded rows in place (K zeros, NS samples, K zeros each):
+// the scatter pattern's and the reflection impulses'.  KC > 0: the
+// half-width is the compile-time KC (== K) and the taps sit in registers;
+// KC = 0: any K, taps read from shared memory.  Same tap order as the plain
+// kernel.  Chunk c's results are written back only after chunk c + 1 has
+// been computed, so every read sees unfiltered data (K <= 32).
 template <int KC>
-__device__ __forceinline__ void axial_psf_row(float* prow, int NS, const float* w, int K, int lane) {
-  float prev = 0.f;
+__device__ __forceinline__ void axial_psf_rows(float* pt, float* pr, int NS, const float* w, int K, int lane) {
+  float prev_t = 0.f, prev_r = 0.f;
   int prev_s = -1;
   const int taps = 2 * K + 1;
   float wr[KC > 0 ? 2 * KC + 1 : 1];
@@ -44,54 +48,73 @@ __device__ __forceinline__ void axial_psf_row(float* prow, int NS, const float* 
   for (int k = 0; k < (KC > 0 ? 2 * KC + 1 : 0); ++k) wr[k] = w[k];
   for (int c = 0; c < NS; c += 32) {
     const int s = c + lane;
-    float acc = 0.f;
+    float acc_t = 0.f, acc_r = 0.f;
     if (s < NS) {
-      const float* q = prow + s;
+      const float* qt = pt + s;
+      const float* qr = pr + s;
       if constexpr (KC > 0) {
 #pragma unroll
-        for (int k = 0; k < 2 * KC + 1; ++k) acc = fmaf(wr[k], q[k], acc);
+        for (int k = 0; k < 2 * KC + 1; ++k) {
+          acc_t = fmaf(wr[k], qt[k], acc_t);
+          acc_r = fmaf(wr[k], qr[k], acc_r);
+        }
       } else {
-        for (int k = 0; k < taps; ++k) acc = fmaf(w[k], q[k], acc);
+        for (int k = 0; k < taps; ++k) {
+          acc_t = fmaf(w[k], qt[k], acc_t);
+          acc_r = fmaf(w[k], qr[k], acc_r);
+        }
       }
     }
     __syncwarp();
-    if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
+    if (prev_s >= 0 && prev_s < NS) {
+      pt[K + prev_s] = prev_t;
+      pr[K + prev_s] = prev_r;
+    }
     __syncwarp();
-    prev = acc;
+    prev_t = acc_t;
+    prev_r = acc_r;
     prev_s = s;
   }
-  if (prev_s >= 0 && prev_s < NS) prow[K + prev_s] = prev;
+  if (prev_s >= 0 && prev_s < NS) {
+    pt[K + prev_s] = prev_t;
+    pr[K + prev_s] = prev_r;
+  }
   __syncwarp();
 }
 
-__device__ __forceinline__ void axial_psf_any(float* prow, int NS, const float* w, int K, int lane) {
+__device__ __forceinline__ void axial_psf_any(float* pt, float* pr, int NS, const float* w, int K, int lane) {
   switch (K) {
-    case 1: axial_psf_row<1>(prow, NS, w, K, lane); break;
-    case 2: axial_psf_row<2>(prow, NS, w, K, lane); break;
-    case 3: axial_psf_row<3>(prow, NS, w, K, lane); break;
-    case 4: axial_psf_row<4>(prow, NS, w, K, lane); break;
-    case 5: axial_psf_row<5>(prow, NS, w, K, lane); break;
-    case 6: axial_psf_row<6>(prow, NS, w, K, lane); break;
-    case 7: axial_psf_row<7>(prow, NS, w, K, lane); break;
-    case 8: axial_psf_row<8>(prow, NS, w, K, lane); break;
-    default: axial_psf_row<0>(prow, NS, w, K, lane); break;
+    case 1: axial_psf_rows<1>(pt, pr, NS, w, K, lane); break;
+    case 2: axial_psf_rows<2>(pt, pr, NS, w, K, lane); break;
+    case 3: axial_psf_rows<3>(pt, pr, NS, w, K, lane); break;
+    case 4: axial_psf_rows<4>(pt, pr, NS, w, K, lane); break;
+    case 5: axial_psf_rows<5>(pt, pr, NS, w, K, lane); break;
+    case 6: axial_psf_rows<6>(pt, pr, NS, w, K, lane); break;
+    case 7: axial_psf_rows<7>(pt, pr, NS, w, K, lane); break;
+    case 8: axial_psf_rows<8>(pt, pr, NS, w, K, lane); break;
+    default: axial_psf_rows<0>(pt, pr, NS, w, K, lane); break;
   }
 }
 
-// Lateral PSF and log compression of rows w0 .. y1-1 of a pass-B tile over
-// samples s0 .. s0 + kChunk, four lines per thread: abuf holds the staged
-// filtered rows from w0 - K on (zero rows outside the frame and past the
-// last needed row), ybuf receives the log image; rows of kRowStride
-// floats, of which the first kChunk + 1 are the tile's samples and one more.  Each line's taps are summed in increasing line order.
+// Lateral PSF, image and log compression of rows w0 .. y1-1 of a pass-B
+// tile over samples s0 .. s0 + kChunk, kLatLines lines per thread: abuf holds
+// the staged filtered pairs (AR, AT) from w0 - K on (zero rows outside the
+// frame and past the last needed row), ybuf the energy of rows w0 .. y1-1 and
+// receives their log image in place; rows of kRowStride elements, of which
+// the first kChunk + 1 are the tile's samples and one more.  Each line's taps
+// are summed in increasing line order, for AR and AT alike; then
+// I = image_value(P (x) AR, P (x) AT, E).
 // KC > 0: K is the compile-time KC and the taps sit in registers; each
-// staged row is read once and added into the (up to) four sums it reaches,
-// in the same order.  KC = 0: any K, taps read from shared memory.
+// staged row is read once and added into the (up to kLatLines) sums it
+// reaches, in the same order.  KC = 0: any K, taps read from shared memory.
+constexpr int kLatLines = 2;
 template <int KC>
 __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProbe& P, long long beam_off,
-                                            const float* abuf, float* ybuf, const float* wlat, int NS, int K, int w0,
+                                            const float2* abuf, float* ybuf, const float* wlat, int NS, int K, int w0,
                                             int w1, int y1, int s0) {
   constexpr int NC = kChunk + 1;   // columns: the tile's samples and one more
-  const int ng = (y1 - w0 + 3) >> 2;
+  constexpr int LL = kLatLines;
+  const int ng = (y1 - w0 + LL - 1) / LL;
   const int taps = 2 * K + 1;
   const int se = min(s0 + kChunk, NS);   // samples this tile exports
   constexpr int TC = 2 * KC + 1;
@@ -99,34 +122,45 @@ __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProb
 #pragma unroll
   for (int q = 0; q < (KC > 0 ? TC : 0); ++q) wr[q] = wlat[q];
   for (int t = threadIdx.x; t < ng * NC; t += blockDim.x) {
-    const int gi = t / NC, c = t - gi * NC, i0 = 4 * gi;
-    const float* col = abuf + i0 * kRowStride + c;     // row of line w0 + i0 + j, tap q: i0 + j + q
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int gi = t / NC, c = t - gi * NC, i0 = LL * gi;
+    const float2* col = abuf + i0 * kRowStride + c;    // row of line w0 + i0 + j, tap q: i0 + j + q
+    float accR[LL], accT[LL];
+#pragma unroll
+    for (int j = 0; j < LL; ++j) accR[j] = accT[j] = 0.f;
     if constexpr (KC > 0) {
 #pragma unroll
-      for (int r = 0; r < TC + 3; ++r) {
-        const float v = col[r * kRowStride];
+      for (int r = 0; r < TC + LL - 1; ++r) {
+        const float2 v = col[r * kRowStride];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (r - j >= 0 && r - j < TC) acc[j] = fmaf(wr[r - j], v, acc[j]);
+        for (int j = 0; j < LL; ++j)
+          if (r - j >= 0 && r - j < TC) {
+            accR[j] = fmaf(wr[r - j], v.x, accR[j]);
+            accT[j] = fmaf(wr[r - j], v.y, accT[j]);
+          }
       }
     } else {
       for (int q = 0; q < taps; ++q) {
         const float w = wlat[q];
-        const float* cp = col + q * kRowStride;
+        const float2* cp = col + q * kRowStride;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = fmaf(w, cp[j * kRowStride], acc[j]);
+        for (int j = 0; j < LL; ++j) {
+          const float2 v = cp[j * kRowStride];
+          accR[j] = fmaf(w, v.x, accR[j]);
+          accT[j] = fmaf(w, v.y, accT[j]);
+        }
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < LL; ++j) {
       const int i = i0 + j, l = w0 + i;
       if (l >= y1) break;
-      const float y = log_compress(P, acc[j]);
-      ybuf[i * kRowStride + c] = y;
+      float* yp = ybuf + i * kRowStride + c;
+      const float I = image_value(accR[j], accT[j], *yp);
+      const float y = log_compress(P, I);
+      *yp = y;
       const int s = s0 + c;
       if (l < w1 && s < se) {
-        if (p.envelope) p.envelope[beam_off + (long long)l * NS + s] = acc[j];
+        if (p.envelope) p.envelope[beam_off + (long long)l * NS + s] = I;
         if (p.logimg) p.logimg[beam_off + (long long)l * NS + s] = y;
       }
     }
@@ -134,7 +168,7 @@ __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProb
 }
 
 __device__ __forceinline__ void lateral_psf_any(const RenderParams& p, const DevProbe& P, long long beam_off,
-                                                const float* abuf, float* ybuf, const float* wlat, int NS, int K,
+                                                const float2* abuf, float* ybuf, const float* wlat, int NS, int K,
                                                 int w0, int w1, int y1, int s0) {
 #define US_LAT(k) \
   case k: lateral_psf<k>(p, P, beam_off, abuf, ybuf, wlat, NS, K, w0, w1, y1, s0); break;
@@ -181,11 +215,12 @@ __device__ __forceinline__ bool split_item(const RenderParams& p, int blk, int g
   return cx.valid != 0;
 }
 
-// minimum resident blocks per SM the register budget is cut for: pass A
-// blocks are small enough in shared memory for 3 (16 lines) or 6 (8 lines)
+// minimum resident blocks per SM the register budget is cut for (64
+// registers a thread): pass A holds two padded rows per line, so its blocks
+// fit 4 (8 lines) or 2 (16 lines) to an SM on 512-sample probes
 template <int G>
 constexpr int lines_min_blocks() {
-  return G == 8 ? 6 : (G == 16 ? 3 : 1);
+  return G == 8 ? 4 : (G == 16 ? 2 : 1);
 }
 
 // Pass A work unit `blk` = item * gpi_lines + group.  With a.done set,
@@ -203,7 +238,8 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
   const int g0 = group * G, g1 = min(g0 + G, NL);
   const int L0 = max(g0 - cx.pair.dmax, 0), L1 = min(g1 + cx.pair.dmax, NL);   // labels the stencil can reach
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NW = blockDim.x >> 5;
-  float* zbuf = reinterpret_cast<float*>(smem);                      // [G][RS]
+  float* zbuf = reinterpret_cast<float*>(smem);                      // [G][RS]: impedance, T, then P_ax (x) T
+  float* rbuf = reinterpret_cast<float*>(smem + a.off_r);            // [G][RS]: R_imp, then P_ax (x) R_imp
   float* wax = reinterpret_cast<float*>(smem + a.off_wax);
   DevTissue* tis = reinterpret_cast<DevTissue*>(smem + a.off_tis);
   uint8_t* lbuf = smem + a.off_lab;                                   // [L1 - L0][NS]
@@ -236,9 +272,12 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
       if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + s] = vi;
       if (p.label) p.label[cx.it.beam_off + (long long)l * NS + s] = lb;
     }
+    float* rrow = rbuf + (l - g0) * RS;
     for (int q = lane; q < KA; q += 32) {
       prow[q] = 0.f;
       prow[KA + NS + q] = 0.f;
+      rrow[q] = 0.f;
+      rrow[KA + NS + q] = 0.f;
     }
   }
   {
@@ -258,10 +297,13 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
   }
   __syncthreads();
 
-  // scanline model and axial PSF of own lines, one warp per line
+  // scanline model and axial PSF of own lines, one warp per line; the
+  // energy goes straight to the line buffer's E plane
   for (int l = g0 + warp; l < g1; l += NW) {
     float* prow = zbuf + (l - g0) * RS;
     float* row = prow + KA;
+    float* rrow = rbuf + (l - g0) * RS;
+    float* erow = a.ebeam + cx.it.beam_off + (long long)l * NS;
     const uint8_t* lrow = lbuf + (l - L0) * NS;
     auto labf = [&](int line, int s) -> unsigned { return lbuf[(line - L0) * NS + s]; };
     auto own = [&](int s) -> unsigned { return lrow[s]; };
@@ -272,12 +314,17 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
       beam_point(P, ln, s, x, z);
       return sample_position(cx.M, x, z);
     };
-    scanline_model<ANCHORED>(p, P, tis, cx.pair, cx.it.b, l, lane, labf, own, zf, [&](int s, float v) { row[s] = v; },
+    scanline_model<ANCHORED>(p, P, tis, cx.pair, cx.it.b, l, lane, labf, own, zf,
+                             [&](int s, float r, float t, float e) {
+                               row[s] = t;
+                               rrow[KA + s] = r;
+                               erow[s] = e;
+                             },
                              posf, cx.it.vol);
     __syncwarp();
-    axial_psf_any(prow, NS, wax, KA, lane);
-    float* dst = a.beam + cx.it.beam_off + (long long)l * NS;
-    for (int s = lane; s < NS; s += 32) dst[s] = row[s];
+    axial_psf_any(prow, rrow, NS, wax, KA, lane);
+    float2* dst = a.beam + cx.it.beam_off + (long long)l * NS;
+    for (int s = lane; s < NS; s += 32) dst[s] = make_float2(rrow[KA + s], row[s]);
   }
   if (a.done) {
     __syncthreads();
@@ -324,7 +371,7 @@ __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArg
   // PSF needs no edge tests (adding w * 0 leaves a sum unchanged exactly:
   // the sums never hold -0)
   const int r0 = w0 - KL;
-  const int nrows = (((y1 - w0) + 3) & ~3) + 2 * KL;
+  const int nrows = (((y1 - w0) + kLatLines - 1) / kLatLines) * kLatLines + 2 * KL;
   const int a0 = max(r0, 0), a1 = min(y1 + KL, NL);                  // rows present in the line buffer
   const int tid = threadIdx.x;
   if (a.done) {
@@ -351,22 +398,32 @@ __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArg
     __syncthreads();
     if (!ready) return;
   }
-  float* abuf = reinterpret_cast<float*>(smem);                      // [nrows][kRowStride]
-  float* ybuf = reinterpret_cast<float*>(smem + a.off_y);            // [y1 - w0][kRowStride]
+  float2* abuf = reinterpret_cast<float2*>(smem);                    // [nrows][kRowStride] (AR, AT)
+  float* ybuf = reinterpret_cast<float*>(smem + a.off_y);            // [y1 - w0][kRowStride]: E, then the log image
   float* wlat = reinterpret_cast<float*>(smem + a.off_wlat);
   for (int t = tid; t < 2 * KL + 1; t += NT) wlat[t] = __ldg(&P.w_lat[t]);
   {
-    const float* src = a.beam + it.beam_off + s0;
-    constexpr int PPR = kRowStride / 4;                              // 16-byte pieces per row
-    if ((NS & 3) == 0 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
-      // asynchronous 16-byte copies, zero-filled past the row's end and
-      // for rows outside the frame
-      for (int t = tid; t < nrows * PPR; t += NT) {
-        const int r = t / PPR, c = (t - r * PPR) * 4;
+    const float2* src = a.beam + it.beam_off + s0;
+    const float* esrc = a.ebeam + it.beam_off + s0;
+    const int ne = y1 - w0;
+    if ((NS & 3) == 0 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) &&
+        ((reinterpret_cast<uintptr_t>(esrc) & 15u) == 0)) {
+      // asynchronous 16-byte copies (two pairs, four energies), zero-filled
+      // past the row's end and for rows outside the frame
+      constexpr int PPA = kRowStride / 2;                            // 16-byte pieces per pair row
+      for (int t = tid; t < nrows * PPA; t += NT) {
+        const int r = t / PPA, c = (t - r * PPA) * 2;
         const int line = r0 + r;
         const bool present = line >= a0 && line < a1 && c < sw;
-        const float* g = present ? src + (long long)line * NS + c : a.beam;
+        const float2* g = present ? src + (long long)line * NS + c : a.beam;
         umma::cp_async16(abuf + r * kRowStride + c, g, present ? 16u : 0u);
+      }
+      constexpr int PPE = kRowStride / 4;                            // 16-byte pieces per energy row
+      for (int t = tid; t < ne * PPE; t += NT) {
+        const int r = t / PPE, c = (t - r * PPE) * 4;
+        const bool present = c < sw;
+        const float* g = present ? esrc + (long long)(w0 + r) * NS + c : a.ebeam;
+        umma::cp_async16(ybuf + r * kRowStride + c, g, present ? 16u : 0u);
       }
       umma::cp_async_commit();
       umma::cp_async_wait<0>();
@@ -374,7 +431,11 @@ __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArg
       for (int t = tid; t < nrows * kRowStride; t += NT) {
         const int r = t / kRowStride, c = t - r * kRowStride;
         const int line = r0 + r;
-        abuf[t] = line >= a0 && line < a1 && c < sw ? __ldcg(src + (long long)line * NS + c) : 0.f;
+        abuf[t] = line >= a0 && line < a1 && c < sw ? __ldcg(src + (long long)line * NS + c) : make_float2(0.f, 0.f);
+      }
+      for (int t = tid; t < ne * kRowStride; t += NT) {
+        const int r = t / kRowStride, c = t - r * kRowStride;
+        ybuf[t] = c < sw ? __ldcg(esrc + (long long)(w0 + r) * NS + c) : 0.f;
       }
     }
   }
@@ -456,6 +517,8 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
     gl = std::max(gl, (NL + G - 1) / G);
   }
   long long off = up(zb, 16);
+  sh.args.off_r = (int)off;
+  off = up(off + zb, 16);
   sh.args.off_wax = (int)off;
   off = up(off + 4 * (2 * 32 + 1), 16);
   sh.args.off_tis = (int)off;
@@ -464,15 +527,17 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
   off = up(off + lab, 16);
   sh.smem_lines = (size_t)off;
   if (sh.smem_lines > lim) return false;
-  // pass B: the widest wedge whose staged rows and log rows (kChunk + 1
-  // samples each) fit four blocks per SM, else two, else one
-  for (int per_sm : {4, 2, 1})
+  // pass B: the widest wedge whose staged pair rows (8 bytes a sample) and
+  // energy / log rows (kChunk + 1 samples each) fit four blocks per SM,
+  // else three, two, one
+  for (int per_sm : {4, 3, 2, 1})
   for (int GB : {32, 16, 8}) {
     long long ab = 0, yb = 0;
     int gi = 0;
     for (const ProbeHost& ph : probes) {
       const int NL = ph.desc.n_lines, NS = ph.desc.n_samples;
-      ab = std::max(ab, (long long)(((std::min(NL, GB + 1) + 3) & ~3) + 2 * ph.k_lat) * kRowStride * 4);
+      const int rows = ((std::min(NL, GB + 1) + kLatLines - 1) / kLatLines) * kLatLines + 2 * ph.k_lat;
+      ab = std::max(ab, (long long)rows * kRowStride * 8);
       yb = std::max(yb, (long long)std::min(NL, GB + 1) * kRowStride * 4);
       gi = std::max(gi, ((NL + GB - 1) / GB) * ((NS + kChunk - 1) / kChunk));
     }
@@ -563,10 +628,10 @@ static cudaError_t launch_g(const RenderParams& p, const SplitShape& sh, const S
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
-                              int pass, cudaStream_t st) {
+cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems,
+                              unsigned* sync, int max_items, int pass, cudaStream_t st) {
   SplitArgs a = sh.args;
-  a.beam = beam;
+  set_line_buffer(a, beam, beam_elems);
   if (pass >= 2) {
     // sync: the unit counter, then one completion flag per pass-A group
     // (pass 3: the caller has zeroed them)
@@ -586,10 +651,10 @@ cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float
   }
 }
 
-cudaError_t launch_split_wait_selftest(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync,
-                                       int max_items, long long wait_cycles, cudaStream_t st) {
+cudaError_t launch_split_wait_selftest(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems,
+                                       unsigned* sync, int max_items, long long wait_cycles, cudaStream_t st) {
   SplitArgs a = sh.args;
-  a.beam = beam;
+  set_line_buffer(a, beam, beam_elems);
   a.work = sync;
   a.done = sync + 1;
   a.wait_cycles = wait_cycles;
@@ -606,11 +671,11 @@ cudaError_t launch_split_wait_selftest(const RenderParams& p, const SplitShape& 
   }
 }
 
-cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
-                         cudaStream_t st) {
-  if (sh.persistent) return launch_split_pass(p, sh, beam, sync, max_items, 2, st);
-  cudaError_t e = launch_split_pass(p, sh, beam, sync, max_items, 0, st);
-  return e == cudaSuccess ? launch_split_pass(p, sh, beam, sync, max_items, 1, st) : e;
+cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems, unsigned* sync,
+                         int max_items, cudaStream_t st) {
+  if (sh.persistent) return launch_split_pass(p, sh, beam, beam_elems, sync, max_items, 2, st);
+  cudaError_t e = launch_split_pass(p, sh, beam, beam_elems, sync, max_items, 0, st);
+  return e == cudaSuccess ? launch_split_pass(p, sh, beam, beam_elems, sync, max_items, 1, st) : e;
 }
 
 // Pixels of a curvilinear probe's output grid, grouped by pass-B tile

@@ -277,6 +277,12 @@ __device__ __forceinline__ float2 anchored_maps(const RenderParams& p, float3 po
   return make_float2(n0, n1);
 }
 
+// the image at a beam sample from its blurred reflection impulses
+// pr = (P (x) R_imp), its blurred scatter pattern pt = (P (x) T) and its own
+// energy e: I = R + B with the backscatter B = E . (P (x) T) (App. B.2).
+// Every path forms it here, so they agree bit for bit.
+__device__ __forceinline__ float image_value(float pr, float pt, float e) { return fmaf(e, pt, pr); }
+
 // log compression to [0, 1] over the probe's dynamic range:
 // 20 log10(I / e0) = (20 log10 2) log2(I) - 20 log10(e0), with the hardware
 // base-2 logarithm (about 2^-22 relative error, far below the image's

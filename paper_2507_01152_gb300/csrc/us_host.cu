@@ -323,7 +323,7 @@ us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, ui
     if (st && cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
     if (s->tuning.use_graph && st && cap == cudaStreamCaptureStatusNone) return graph_launch(s, pl, p, st);
     if (two_pass) {
-      if ((e = launch_split(p, s->split, pl->d_beam, pl->d_sync, B, st)) != cudaSuccess) return cuda_fail(s, e, "two-pass render launch");
+      if ((e = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, st)) != cudaSuccess) return cuda_fail(s, e, "two-pass render launch");
       return US_OK;
     }
     if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(s, e, "reset work counter");
@@ -368,9 +368,11 @@ void free_sim(us_sim* s) {
   cudaFree(s->d_probes);
   cudaFree(s->d_pairs);
   cudaFree(s->scratch.lab);
-  cudaFree(s->scratch.S);
-  cudaFree(s->scratch.A);
-  cudaFree(s->scratch.Y);
+  cudaFree(s->scratch.R);
+  cudaFree(s->scratch.T);
+  cudaFree(s->scratch.E);
+  cudaFree(s->scratch.AR);
+  cudaFree(s->scratch.AT);
   cudaFree(s->d_err);
   cudaFree(s->d_work);
   cudaFree(s->d_host_poses);
@@ -450,7 +452,8 @@ us_status apply_tuning(us_sim* s, const us_tuning& t) {
 // grid's synchronisation words
 static cudaError_t two_pass_buffers(us_plan* pl) {
   cudaError_t e = cudaSuccess;
-  if (!pl->d_beam && (e = cudaMalloc(&pl->d_beam, sizeof(float) * (size_t)pl->beam_elems)) != cudaSuccess) return e;
+  if (!pl->d_beam && (e = cudaMalloc(&pl->d_beam, kLineBufferBytesPerSample * (size_t)pl->beam_elems)) != cudaSuccess)
+    return e;
   if (!pl->d_sync &&
       (e = cudaMalloc(&pl->d_sync, sizeof(unsigned) * split_sync_words((int)pl->items_batch.size()))) != cudaSuccess)
     return e;
@@ -478,7 +481,7 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
   RenderParams pp = p;
   FusedLayout lay = s->shape.lay;
   SplitArgs sa = s->split.args;
-  sa.beam = pl->d_beam;
+  set_line_buffer(sa, pl->d_beam, pl->beam_elems);
   sa.work = pl->d_sync;
   sa.done = pl->d_sync ? pl->d_sync + 1 : nullptr;
   void* fargs[2] = {&pp, &lay};
@@ -490,7 +493,7 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(s, e, "graph capture");
     cudaError_t e1 = cudaSuccess, e2;
     if (two_pass) {
-      e2 = launch_split(p, s->split, pl->d_beam, pl->d_sync, p.n_items, st);
+      e2 = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, p.n_items, st);
     } else {
       e1 = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
       e2 = launch_fused(p, s->shape, st);
@@ -694,15 +697,18 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
   if ((e = upload(&s->d_vols, dv.data(), dv.size())) != cudaSuccess || (e = upload(&s->d_probes, dp.data(), dp.size())) != cudaSuccess ||
       (e = upload(&s->d_pairs, pairs.data(), pairs.size())) != cudaSuccess ||
       (e = cudaMalloc(&s->scratch.lab, max_beam)) != cudaSuccess ||
-      (e = cudaMalloc(&s->scratch.S, max_beam * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&s->scratch.A, max_beam * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&s->scratch.Y, max_beam * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->scratch.R, max_beam * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->scratch.T, max_beam * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->scratch.E, max_beam * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->scratch.AR, max_beam * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->scratch.AT, max_beam * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->d_err, sizeof(unsigned))) != cudaSuccess || (e = cudaMalloc(&s->d_work, sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMemset(s->d_err, 0, sizeof(unsigned))) != cudaSuccess) {
     us_status st = e == cudaErrorMemoryAllocation ? US_ERR_OOM : US_ERR_CUDA;
     free_sim(s);
     return st;
   }
+  s->scratch.Y = s->scratch.R;   // the log image reuses R's storage (R is dead once AR is formed)
   s->dev_vols = dv;
   s->d_hu8.assign(dv.size(), nullptr);
   if ((r = read_volumes(s, nullptr)) != US_OK) {
@@ -829,7 +835,7 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
   if (s->tuning.cluster_size == 1) {
     if ((e = two_pass_buffers(pl)) != cudaSuccess)
       return cuda_fail(s, e, "two-pass line buffer");
-    if ((e = launch_split(p, s->split, pl->d_beam, pl->d_sync, B, st)) != cudaSuccess) return cuda_fail(s, e, "gated render");
+    if ((e = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, st)) != cudaSuccess) return cuda_fail(s, e, "gated render");
   } else if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess ||
              (e = launch_fused(p, s->shape, st)) != cudaSuccess) {
     return cuda_fail(s, e, "gated render");
@@ -947,13 +953,13 @@ us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const fl
     // the reset of the synchronisation words sits outside the timed kernel
     e = cudaMemsetAsync(pl->d_sync, 0, sizeof(unsigned) * split_sync_words(B), st);
     cudaEventRecord(ev[0], st);
-    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->d_sync, B, 3, st);
+    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, 3, st);
     cudaEventRecord(ev[1], st);
   } else if (two_pass) {
     cudaEventRecord(ev[0], st);
-    e = launch_split_pass(p, s->split, pl->d_beam, pl->d_sync, B, 0, st);
+    e = launch_split_pass(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, 0, st);
     cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->d_sync, B, 1, st);
+    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, 1, st);
     cudaEventRecord(ev[2], st);
   } else {
     e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
@@ -1064,7 +1070,7 @@ us_status us_sim_selftest_tile_wait(us_sim* s, const us_env* envs, int32_t B, co
   p.items = pl->d_items;
   p.n_items = B;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if ((e = launch_split_wait_selftest(p, s->split, pl->d_beam, pl->d_sync, B, wait_cycles, st)) != cudaSuccess)
+  if ((e = launch_split_wait_selftest(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, wait_cycles, st)) != cudaSuccess)
     return cuda_fail(s, e, "self-test launch");
   return US_OK;
 }

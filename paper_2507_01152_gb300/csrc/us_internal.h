@@ -30,13 +30,21 @@ struct ProbeHost {
   int wedge_G = 0;
 };
 
-// global scratch of the plain path (one environment at a time)
+// global scratch of the plain path (one environment at a time): labels,
+// the model's reflection impulses R, scatter pattern T and energy E, their
+// axially filtered AR, AT, and the log image Y (Y may share R's storage:
+// R is dead once AR is formed)
 struct PlainScratch {
   uint8_t* lab = nullptr;
-  float* S = nullptr;
-  float* A = nullptr;
+  float* R = nullptr;
+  float* T = nullptr;
+  float* E = nullptr;
+  float* AR = nullptr;
+  float* AT = nullptr;
   float* Y = nullptr;
 };
+// bytes of plain-path scratch per beam sample (lab 1, R/Y, T, E, AR, AT)
+constexpr int kPlainScratchBytesPerSample = 1 + 5 * 4;
 
 cudaError_t launch_plain(const RenderParams& p, const EnvItem* items_host, int n_items,
                          const ProbeHost* probes, PlainScratch& scr, cudaStream_t st);
@@ -46,7 +54,7 @@ cudaError_t launch_plain_env(const RenderParams& p, const EnvItem& it, const Pro
 
 // launch shape of the fused kernel and its dynamic shared-memory layout
 struct FusedLayout {
-  int off_y, off_lab, off_lrow, off_srow, off_yrow, off_wax, off_wlat, off_tis;  // byte offsets
+  int off_r, off_y, off_lab, off_lrow, off_srow, off_rrow, off_yrow, off_wax, off_wlat, off_tis;  // byte offsets
 };
 
 struct FusedShape {
@@ -75,12 +83,13 @@ constexpr int kChunk = 128;
 constexpr int kImageThreads = 256;
 constexpr int kRowStride = kChunk + 4;   // shared row stride, floats (16-byte rows)
 struct SplitArgs {
-  float* beam = nullptr;   // axially filtered lines, beam layout (per item beam_off)
+  float2* beam = nullptr;   // axially filtered (AR, AT) pairs, beam layout (per item beam_off)
+  float* ebeam = nullptr;   // energy E of every beam sample, same layout
   unsigned* work = nullptr;   // persistent grid: unit counter
   unsigned* done = nullptr;   // persistent grid: per pass-A group, 1 once its lines are written
   long long wait_cycles = 2000000000ll;   // persistent grid: bound of a tile's wait (SM clock cycles, ~1 s)
   int G = 32, GB = 32, gpi_lines = 0, gpi_image = 0;
-  int off_wax = 0, off_tis = 0, off_lab = 0;   // pass A byte offsets
+  int off_r = 0, off_wax = 0, off_tis = 0, off_lab = 0;   // pass A byte offsets
   int off_y = 0, off_wlat = 0;                 // pass B byte offsets
 };
 struct SplitShape {
@@ -91,6 +100,13 @@ struct SplitShape {
   bool persistent = false;        // one persistent grid instead of two
   int persist_grid[2] = {0, 0};   // resident blocks of the persistent grid (beam-keyed, anchored maps)
 };
+// the line buffer of a batch of beam_elems samples: (AR, AT) pairs, then
+// the energy plane, 12 bytes a sample
+constexpr size_t kLineBufferBytesPerSample = 12;
+inline void set_line_buffer(SplitArgs& a, float* base, long long beam_elems) {
+  a.beam = reinterpret_cast<float2*>(base);
+  a.ebeam = base + 2 * beam_elems;
+}
 // words of synchronisation state the persistent two-pass grid needs for a
 // batch of B environments (unit counter + a flag per group of >= 8 lines)
 inline size_t split_sync_words(int B) { return 1 + (size_t)B * (1024 / 8); }
@@ -98,19 +114,19 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
 cudaError_t split_prepare(SplitShape& sh);
 // both passes over the first max_items entries of p.items (fewer if
 // p.n_items_dev says so)
-cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
-                         cudaStream_t st);
+cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems, unsigned* sync,
+                         int max_items, cudaStream_t st);
 // one pass: 0 = lines (pass A), 1 = image (pass B)
 // pass 0: pass A, 1: pass B (separate grids); 2: both in the persistent
 // grid (resets `sync` first); 3: the persistent grid on a `sync` the
 // caller has zeroed
-cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync, int max_items,
-                              int pass, cudaStream_t st);
+cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems,
+                              unsigned* sync, int max_items, int pass, cudaStream_t st);
 // the persistent grid with its unit counter started past every pass-A group
 // and the given wait bound: no group publishes its lines, so every tile's
 // wait runs out (self-test of the bounded wait)
-cudaError_t launch_split_wait_selftest(const RenderParams& p, const SplitShape& sh, float* beam, unsigned* sync,
-                                       int max_items, long long wait_cycles, cudaStream_t st);
+cudaError_t launch_split_wait_selftest(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems,
+                                       unsigned* sync, int max_items, long long wait_cycles, cudaStream_t st);
 void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int NS, int G, std::vector<float4>& entries,
                   std::vector<int>& off);
 

@@ -1,6 +1,9 @@
 // The image model along one scanline (SonoGym App. B.2), evaluated by one
-// warp: reflection R, remaining energy E, scatter pattern T, backscatter B,
-// and the pre-PSF image S = R + B for every sample of the line.
+// warp: for every sample of the line, the reflection impulse
+// R_imp = G |E cos(theta) r|^p, the scatter pattern T and the remaining
+// energy E.  The image is I = P (x) R_imp + E . (P (x) T): the PSF blurs the
+// impulses and the scatter pattern, and the backscatter B = E . (P (x) T)
+// takes the energy at the pixel itself (App. B.2).
 #pragma once
 #include "us_device.cuh"
 
@@ -26,7 +29,7 @@ __device__ __forceinline__ float warp_inclusive_scan(float v, int lane) {
 //   lab(line, s)  -> nearest label of a beam sample (any line of the env)
 //   own(s)        -> nearest label of sample s on line l
 //   z_at(s)       -> impedance at sample s < NS of line l
-//   store(s, v)   -> receives S at sample s
+//   store(s, r, t, e) -> receives R_imp, T and E at sample s
 //   pos(s)        -> volume-frame position of sample s (anchored scatter maps)
 // A lane reads z_at only at its own samples (one chunk ahead) and gets the
 // next lane's value by shuffle, so store() may overwrite the storage z_at
@@ -123,8 +126,8 @@ __device__ __forceinline__ void scanline_model(const RenderParams& p, const DevP
       Ta = ta.mu0;
       Tb = tb.mu0;
     }
-    if (sa < NS) store(sa, fmaf(Ea, Ta, Ra));
-    if (sb < NS) store(sb, fmaf(Eb, Tb, Rb));
+    if (sa < NS) store(sa, Ra, Ta, Ea);
+    if (sb < NS) store(sb, Rb, Tb, Eb);
     z0 = nz0;
     z1 = nz1;
   }
