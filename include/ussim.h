@@ -9,9 +9,11 @@
  * (Fig. 2 caption; Sec. 4 "Ultrasound simulation"):
  *
  *   E(u) = E0 exp(-f * int_0^y alpha)            remaining energy   (App. B.2)
- *   R(u) = |E cos(theta) (Z(y+dy)-Z(y))/(Z(y+dy)+Z(y))| at boundaries G
- *   B(u) = E T,  T = N0 sigma0 + mu0 if N1 <= mu1 else 0   (App. B.2)
- *   I    = P (x) (R + B),  P a 2-D Gaussian PSF             (App. B.2)
+ *   R_imp(u) = |E cos(theta) (Z(y+dy)-Z(y))/(Z(y+dy)+Z(y))| at boundaries G
+ *   T(u) = N0 sigma0 + mu0 if N1 <= mu1 else 0       scatter pattern (App. B.2)
+ *   I    = P (x) R_imp + E . (P (x) T),  P a 2-D Gaussian PSF      (App. B.2)
+ *          (the backscatter B = E . P (x) T as printed: the pattern is
+ *          blurred, then scaled by the energy at the pixel)
  *
  * followed by log compression and, for curvilinear probes, scan conversion
  * to a Cartesian image.  Readings taken where the paper is silent (noise
@@ -176,7 +178,9 @@ typedef struct {
                             must be 0 for the cluster path */
 } us_tuning;
 
-/* Create a simulator.  Copies the descriptors, builds the derived tables
+/* Create a simulator (the per-environment assets of Sec. 4 "Ultrasound
+ * simulation" and App. B.2: CT volume and label map, tissue acoustic
+ * settings, probe geometry).  Copies the descriptors, builds the derived tables
  * (per-line geometry, PSF taps, scan-conversion maps, tissue constants,
  * N1 thresholds) and checks on the device that every label is below
  * n_labels (synchronous).  vols/labels/hu stay borrowed.  opt may be NULL
@@ -200,26 +204,45 @@ US_API us_status us_sim_refresh_volumes(us_sim* sim, void* stream);
 /* Release every resource of the handle (waits for its work to finish). */
 US_API void us_sim_destroy(us_sim* sim);
 
-/* Frame layout for a batch: offsets[b] is the first float of frame b in
- * the frame buffer (row-major out_h x out_w), offsets[B] the total size in
- * floats.  Each frame starts on a 256-byte boundary.  offsets: HOST, B+1. */
+/* Frame layout for a batch (one H x W image per environment, App. B.2's
+ * I in R^(H x W); Sec. 4: the batch of parallel environments): offsets[b] is
+ * the first float of frame b in the frame buffer (row-major out_h x out_w),
+ * offsets[B] the total size in floats.  Each frame starts on a 256-byte
+ * boundary.  offsets: HOST, B+1.  Errors: US_ERR_INVALID_ARG (NULL handle,
+ * envs or offsets; B < 0; an id out of range). */
 US_API us_status us_sim_frame_layout(const us_sim* sim, const us_env* envs, int32_t B, int64_t* offsets);
 
 /* Beam-grid layout for the debug exports: offsets[b] = first element of
  * env b's [NL][NS] grid.  offsets: HOST, B+1. */
 US_API us_status us_sim_beam_layout(const us_sim* sim, const us_env* envs, int32_t B, int64_t* offsets);
 
-/* Render one frame per environment with the fused, persistent, batched
- * kernel (one thread-block cluster per frame, work taken from a counter).
+/* Render one frame per environment (Fig. 2 caption and Sec. 4 "Ultrasound
+ * simulation": probe pose -> image plane -> label / CT slice -> image;
+ * App. B.2: the image model above), all environments of the batch in the
+ * batched launch shape the handle is tuned to (us_sim_get_tuning): by
+ * default the two-pass path (pass A per group of lines: slice, scanline
+ * model, axial PSF; pass B per tile: lateral PSF, image, log, scan
+ * conversion), in two grids or one persistent grid; or the cluster kernel
+ * (one thread-block cluster per frame).  All shapes give the same bits.
+ * Replays a captured CUDA graph per batch signature when use_graph is set.
  * envs: HOST [B]; poses: DEVICE float [B][3][4], probe frame (x lateral,
- * y elevation, z along the beam, mm) -> volume frame (mm); frames: DEVICE,
- * laid out by us_sim_frame_layout, 16-byte aligned.  B = 0 is a no-op. */
+ * y elevation, z along the beam, mm) -> volume frame (mm), 4-byte aligned;
+ * frames: DEVICE, laid out by us_sim_frame_layout, 16-byte aligned,
+ * caller-owned.  B = 0 is a no-op.  Errors: US_ERR_INVALID_ARG (NULL or
+ * misaligned buffers, B < 0, ids out of range), US_ERR_UNSUPPORTED (no
+ * batched shape fits the probe set: use us_sim_render_plain), US_ERR_OOM
+ * (first use of a batch signature allocates its work list and line
+ * buffer), US_ERR_CUDA; non-finite poses render as water and set the error
+ * word that us_sim_check reads. */
 US_API us_status us_sim_render(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
                         uint64_t seed, uint64_t step, float* frames, void* stream);
 
-/* Same result through the plain per-environment form: for each environment
- * in turn, separate kernels for slicing, the scanline model, the two PSF
- * passes and scan conversion (the comparison baseline). */
+/* Same result through the plain per-environment form (the same App. B.2
+ * model, Sec. 4's batch rendered one environment at a time): for each
+ * environment in turn, separate kernels for slicing, the scanline model,
+ * the two PSF passes and scan conversion, through per-handle scratch (the
+ * comparison baseline).  Arguments and errors as us_sim_render, without
+ * US_ERR_UNSUPPORTED. */
 US_API us_status us_sim_render_plain(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
                               uint64_t seed, uint64_t step, float* frames, void* stream);
 
@@ -242,10 +265,13 @@ US_API us_status us_sim_render_plain(us_sim* sim, const us_env* envs, int32_t B,
 US_API us_status us_sim_render_plain_static(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
                                             uint64_t seed, uint64_t step, float* frames, void* stream);
 
-/* Render with intermediate exports for testing.  path 0 = fused, 1 = plain.
- * envelope (float), logimg (float), nn_index (int32, -1 outside the
- * volume), label (uint8): DEVICE, laid out by us_sim_beam_layout, [NL][NS]
- * per env; any may be NULL.  envelope is I before log compression. */
+/* Render with intermediate exports for testing (the stages of Fig. 2 and
+ * App. B.2: the label slice, the image I before and after log compression).
+ * path 0 = the tuned batched shape, 1 = plain.  envelope (float), logimg
+ * (float), nn_index (int32, -1 outside the volume), label (uint8): DEVICE,
+ * laid out by us_sim_beam_layout, [NL][NS] per env; any may be NULL.
+ * envelope is I = P (x) R_imp + E (P (x) T) before log compression.
+ * Errors as us_sim_render. */
 US_API us_status us_sim_render_debug(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
                               uint64_t seed, uint64_t step, float* frames, float* envelope,
                               float* logimg, int32_t* nn_index, uint8_t* label, int32_t path,
@@ -297,7 +323,9 @@ US_API us_status us_sim_hist_match(us_sim* sim, const float* hu, const uint8_t* 
 US_API us_status us_sim_sample_slices(us_sim* sim, const us_env* envs, int32_t B, const float* poses, uint16_t* out,
                                       void* stream);
 
-/* Physics fallback for frames a learned surrogate rendered: re-render (into
+/* Physics fallback for frames a learned surrogate rendered (App. B.2 has a
+ * model-based and a learning-based simulator; here the model-based one
+ * judges and replaces the learned one's frames): re-render (into
  * `frames`, same layout as us_sim_render) only the envs whose score[b]
  * exceeds `threshold`, leaving the other frames untouched.  score: DEVICE
  * [B] (e.g. the surrogate's predicted error); the subset is selected on the
@@ -325,18 +353,22 @@ US_API us_status us_sim_selftest_tile_wait(us_sim* sim, const us_env* envs, int3
  * output is missing).  Clears the word. */
 US_API us_status us_sim_check(us_sim* sim, void* stream);
 
+/* Read the batched render's launch shape (a property of this build's
+ * kernels; the paper batches environments, Sec. 4, without a stated
+ * kernel design).  Errors: US_ERR_INVALID_ARG (NULL). */
 US_API us_status us_sim_get_tuning(const us_sim* sim, us_tuning* t);
 /* Set the batched render's launch shape; invalid shapes are rejected
  * (US_ERR_INVALID_ARG), shapes whose buffers do not fit this probe set in
  * shared memory too (US_ERR_UNSUPPORTED). */
 US_API us_status us_sim_set_tuning(us_sim* sim, const us_tuning* t);
 
-/* Time the batched render over the candidate launch shapes (cluster and
- * two-pass) on this batch
- * (synchronous, renders into `frames`), keep the fastest, and append it to
- * the text cache at cache_path (may be NULL: no cache).  If cache_path
- * already holds an entry for this GPU, probe set and batch signature it is
- * used without timing. */
+/* Time the batched render (the App. B.2 model over Sec. 4's batch of
+ * environments) over the candidate launch shapes (cluster and two-pass) on
+ * this batch (synchronous, renders into `frames`), keep the fastest, and
+ * append it to the text cache at cache_path (may be NULL: no cache).  If
+ * cache_path already holds an entry for this GPU, probe set and batch
+ * signature it is used without timing.  Arguments as us_sim_render.
+ * Errors: as us_sim_render; US_ERR_UNSUPPORTED if no shape fits. */
 US_API us_status us_sim_autotune(us_sim* sim, const us_env* envs, int32_t B, const float* poses,
                           float* frames, const char* cache_path, void* stream);
 

@@ -119,18 +119,32 @@ US_API int32_t us_surr_param_segments(const us_surr_config* cfg, int32_t max_seg
                                       int64_t* sizes, int32_t* fan_in);
 /* number of FP32 parameters of the network, or -1 for a bad config */
 US_API int64_t us_surr_num_params(const us_surr_config* cfg);
-/* init_params: HOST, us_surr_num_params floats (copied). */
+/* Create the network of the layer list above (App. B.2, learning-based
+ * approach: the U-Net the paper trains on CT-US pairs).  init_params: HOST,
+ * us_surr_num_params floats (copied); the handle owns its weights, Adam
+ * moments and activations for max_batch frames.  Errors: US_ERR_INVALID_ARG
+ * (bad config, NULL), US_ERR_OOM, US_ERR_CUDA. */
 US_API us_status us_surr_create(const us_surr_config* cfg, const float* init_params, us_surr** out);
 US_API void us_surr_destroy(us_surr* s);
 US_API const char* us_surr_last_error(const us_surr* s);
-/* y[B][H][W] = net(x); x, y DEVICE. */
+/* Forward pass (App. B.2: the learned simulator maps the CT / label slice
+ * to the ultrasound image): y[B][H][W] = net(x); x [B][H][W][8] BF16, y FP32,
+ * DEVICE, caller-owned; 1 <= B <= max_batch.  Keeps the activations of this
+ * call for us_surr_features / us_surr_predict_error.  Errors:
+ * US_ERR_INVALID_ARG, US_ERR_CUDA; a bounded tensor-core wait that runs out
+ * is reported by us_surr_check. */
 US_API us_status us_surr_forward(us_surr* s, const uint16_t* x, float* y, int32_t B, void* stream);
-/* One training step on (x, target): forward, loss, backward, and (update =
- * 1) an Adam update.  loss_out: DEVICE [1 + 2B]: batch loss, per-frame L1,
- * per-frame SSIM (before the update). */
+/* One training step on (x, target) (App. B.2: the network is trained on
+ * paired slices and images with an L1 term; here the images are the
+ * physics renders): forward, loss, backward, and (update = 1) an Adam
+ * update.  x as us_surr_forward; target DEVICE [B][H][W] FP32.  loss_out:
+ * DEVICE [1 + 2B]: batch loss, per-frame L1, per-frame SSIM (before the
+ * update).  Errors as us_surr_forward. */
 US_API us_status us_surr_train_step(us_surr* s, const uint16_t* x, const float* target, int32_t B, float* loss_out,
                                     int32_t update, void* stream);
-/* per-frame L1 and SSIM of any prediction: out DEVICE [1 + 2B] as above */
+/* per-frame L1 and SSIM of any prediction (the quality the paper reports
+ * for its learned simulator includes SSIM, Sec. 5): pred, target DEVICE
+ * [B][H][W]; out DEVICE [1 + 2B] as above.  Errors: US_ERR_INVALID_ARG. */
 US_API us_status us_surr_metrics(us_surr* s, const float* pred, const float* target, int32_t B, float* out,
                                  void* stream);
 /* ---- error gate ----------------------------------------------------------
@@ -146,7 +160,11 @@ US_API us_status us_surr_features(us_surr* s, int32_t B, float* out, void* strea
 /* predicted L1 gap of the frames of the last forward: DEVICE [B] */
 US_API us_status us_surr_predict_error(us_surr* s, int32_t B, float* out, void* stream);
 /* fit the head: feat HOST [n][8 c], target HOST [n] (true per-frame L1),
- * ridge >= 0; synchronous */
+ * ridge >= 0; minimises sum_i (w . feat_i + w0 - target_i)^2 + ridge |w|^2
+ * (intercept w0 not penalised) through the FP64 normal equations and a
+ * Cholesky solve; synchronous.  The paper has no counterpart (its learned
+ * simulator has no error gate).  Errors: US_ERR_INVALID_ARG (n < 2, NULL,
+ * ridge < 0, singular system), US_ERR_CUDA. */
 US_API us_status us_surr_fit_error_head(us_surr* s, const float* feat, const float* target, int32_t n, float ridge);
 
 /* parameters / gradients of the last train step, HOST, parameter layout (synchronous) */
@@ -155,7 +173,9 @@ US_API us_status us_surr_get_grads(us_surr* s, float* host_out);
 /* wait for `stream`; US_ERR_TIMEOUT if a bounded tensor-core wait ran out */
 US_API us_status us_surr_check(us_surr* s, void* stream);
 /* checkpoint: config, step, parameters, Adam moments, CRC32; resuming
- * reproduces the next step exactly */
+ * reproduces the next step exactly (the paper trains its networks for
+ * 15-25 epochs, App. B.2; long runs need resumable state).  Errors:
+ * US_ERR_INVALID_ARG (bad path, config mismatch, CRC mismatch), US_ERR_CUDA. */
 US_API us_status us_surr_save(const us_surr* s, const char* path);
 US_API us_status us_surr_load(us_surr* s, const char* path);
 
