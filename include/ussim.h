@@ -335,6 +335,50 @@ US_API us_status us_sim_render_gated(us_sim* sim, const us_env* envs, int32_t B,
                                      uint64_t step, float* frames, const float* score, float threshold,
                                      int32_t* n_rendered, void* stream);
 
+/* The physics audit of the surrogate's error gate (App. B.2's model-based
+ * simulator checking its learning-based one; the paper has no gate, this
+ * is the library's reading): among the envs the gate keeps (score[b] <=
+ * threshold, as us_sim_render_gated), env b is audited when word 0 of
+ * Philox-4x32-10 on counter (0, 0, b, 2), key = the render key of
+ * (seed, step), is below floor(fraction 2^32): a seeded subset of about
+ * that fraction, fresh every step.  The audited envs are rendered by
+ * physics into audit_frames (DEVICE, the batch's frame layout; the other
+ * frames are left untouched), so that the surrogate frame in the caller's
+ * own buffer can be compared with its physics twin.  flags: DEVICE uint8
+ * [B] (may be NULL), 1 where audited; n_audited: DEVICE int32 (may be
+ * NULL).  fraction in [0, 1]; B <= 32768.  Errors as us_sim_render_gated.
+ * Uses its own work list, but the line buffer of the batch signature like
+ * every batched render (order it with other renders of the same batch). */
+US_API us_status us_sim_render_audit(us_sim* sim, const us_env* envs, int32_t B, const float* poses, uint64_t seed,
+                                     uint64_t step, float* audit_frames, const float* score, float threshold,
+                                     float fraction, uint8_t* flags, int32_t* n_audited, void* stream);
+
+/* Surrogate input on a common grid for a batch of mixed probes (App. B.2's
+ * learned simulator maps the slices to images; one network size serves
+ * every probe): each env's label / CT slice sampled on an H x W grid of
+ * pixel centres spanning that env's output field, channels as in
+ * us_sim_sample_slices.  Curvilinear: the fan's bounding box (the
+ * scan-conversion field) at H x W, inside-fan flag from the same test;
+ * linear: x = ((c + 1/2) NL / W - 1/2 - (NL - 1) / 2) pitch,
+ * z = ((r + 1/2) NS / H - 1/2) depth / NS, flag 1.  Pixel positions are
+ * computed in FP64 on the host and rounded once to FP32; the voxel path is
+ * the render's.  Probes of any output size may share the batch.  out:
+ * DEVICE [B][H][W][8] BF16, 16-byte aligned.  H, W in [2, 4096].  The first
+ * call for a grid size builds its tables (synchronous, library-owned).
+ * Errors: US_ERR_INVALID_ARG, US_ERR_OOM, US_ERR_CUDA. */
+US_API us_status us_sim_sample_slices_grid(us_sim* sim, const us_env* envs, int32_t B, const float* poses, int32_t H,
+                                           int32_t W, uint16_t* out, void* stream);
+
+/* Surrogate frames on the common grid back to each env's own output grid:
+ * output pixel (r, c) of env b's out_h x out_w frame reads src[b] (DEVICE
+ * FP32 [B][H][W], the same field) at fy = (r + 1/2) H / out_h - 1/2,
+ * fx = (c + 1/2) W / out_w - 1/2, clamped to the grid, bilinearly;
+ * curvilinear pixels outside the fan are 0, as in the physics frame.
+ * frames: DEVICE, laid out by us_sim_frame_layout, 16-byte aligned.  H, W
+ * in [2, 4096].  Errors: US_ERR_INVALID_ARG, US_ERR_CUDA. */
+US_API us_status us_sim_resize_frames(us_sim* sim, const us_env* envs, int32_t B, const float* src, int32_t H,
+                                      int32_t W, float* frames, void* stream);
+
 /* Self-test of the persistent two-pass grid's bounded wait (not a render):
  * launches the grid of the current tuning (which must be {1, G, *, 1})
  * for this batch with its unit counter started past every pass-A group,

@@ -147,6 +147,12 @@ US_API us_status us_surr_train_step(us_surr* s, const uint16_t* x, const float* 
  * [B][H][W]; out DEVICE [1 + 2B] as above.  Errors: US_ERR_INVALID_ARG. */
 US_API us_status us_surr_metrics(us_surr* s, const float* pred, const float* target, int32_t B, float* out,
                                  void* stream);
+/* The same per-frame L1 and SSIM for B frames of an explicit H x W
+ * (11 <= H <= height, 11 <= W <= width of the network's config, B <=
+ * max_batch): quality of frames of other probe sizes against physics.
+ * Errors: US_ERR_INVALID_ARG. */
+US_API us_status us_surr_metrics_hw(us_surr* s, const float* pred, const float* target, int32_t B, int32_t H,
+                                    int32_t W, float* out, void* stream);
 /* ---- error gate ----------------------------------------------------------
  * The physics render is the surrogate's judge and fallback: a linear error
  * head on the surrogate's bottleneck features (channel means of the

@@ -110,6 +110,9 @@ def lib():
             L.oracle_sample_slice.restype = C.c_int
             L.oracle_sample_slice_raw.argtypes = [C.POINTER(OrVolume), C.POINTER(OrProbe), C.c_void_p, C.c_void_p]
             L.oracle_sample_slice_raw.restype = C.c_int
+            L.oracle_sample_slice_grid.argtypes = [C.POINTER(OrVolume), C.POINTER(OrProbe), C.c_void_p, C.c_int,
+                                                   C.c_int, C.c_void_p]
+            L.oracle_sample_slice_grid.restype = C.c_int
             L.oracle_anchored_noise.argtypes = [C.c_void_p, C.c_int32, C.c_float, C.c_uint32, C.c_uint64,
                                                 C.c_void_p]
             L.oracle_recon_keep_threshold.argtypes = [C.c_double]
@@ -345,4 +348,83 @@ def sweep_elevation(poses, n_elev, pitch_mm):
             for r in range(3):
                 M[r, 3] = np.float32(P[b, r, 3] + np.float32(P[b, r, 1] * y))
             out[b * n_elev + e] = M
+    return out
+
+
+def sample_slice_grid(labels, hu, voxel_mm, probe, pose, H, W):
+    """surrogate input of one env on an H x W grid over its output field:
+    [H][W][3] = (label / 4, clamp(HU / 1000, -1, 3), inside-field flag)"""
+    vol = _Vol(labels, hu, voxel_mm)
+    out = np.zeros((H, W, 3))
+    pr = or_probe(probe)
+    M = np.ascontiguousarray(pose, np.float32).reshape(12)
+    lib().oracle_sample_slice_grid(C.byref(vol.desc), C.byref(pr), _ptr(M), H, W, _ptr(out))
+    return out
+
+
+def fan_mask(probe):
+    """[out_h][out_w] 1 where an output pixel centre lies inside the fan (the
+    scan conversion's test, FP64); all ones for a linear probe"""
+    H, W = probe.out_h, probe.out_w
+    if probe.kind == 0:
+        return np.ones((H, W), bool)
+    NL, NS = probe.n_lines, probe.n_samples
+    f32 = lambda v: float(np.float32(v))
+    r0, D = f32(probe.radius_mm), f32(probe.depth_mm)
+    half = 0.5 * f32(probe.fan_deg) * np.pi / 180.0
+    dth = f32(probe.fan_deg) * np.pi / 180.0 / (NL - 1)
+    dr = D / NS
+    xmax = (r0 + D) * np.sin(half)
+    zmin, zmax = r0 * np.cos(half), r0 + D
+    m = np.zeros((H, W), bool)
+    for r in range(H):
+        z = zmin + (r + 0.5) * (zmax - zmin) / H
+        for c in range(W):
+            x = -xmax + (c + 0.5) * 2 * xmax / W
+            fl = np.arctan2(x, z) / dth + 0.5 * (NL - 1)
+            fs = (np.hypot(x, z) - r0) / dr
+            m[r, c] = 0 <= fl <= NL - 1 and 0 <= fs <= NS - 1
+    return m
+
+
+def resize_frame(src, probe, mask=None):
+    """An H x W frame over a probe's output field onto the probe's own
+    out_h x out_w grid: output pixel (r, c) reads src at
+    fy = (r + 1/2) H / out_h - 1/2, fx = (c + 1/2) W / out_w - 1/2 (pixel
+    centres of the same field), clamped to the source, bilinearly; 0 outside
+    a curvilinear fan (mask = fan_mask(probe), computed if not given)."""
+    src = np.asarray(src, np.float64)
+    H, W = src.shape
+    OH, OW = probe.out_h, probe.out_w
+    if mask is None:
+        mask = fan_mask(probe)
+    out = np.zeros((OH, OW))
+    for r in range(OH):
+        fy = min(max((r + 0.5) * H / OH - 0.5, 0.0), H - 1.0)
+        y0 = min(int(np.floor(fy)), H - 2)
+        a = fy - y0
+        for c in range(OW):
+            if not mask[r, c]:
+                continue
+            fx = min(max((c + 0.5) * W / OW - 0.5, 0.0), W - 1.0)
+            x0 = min(int(np.floor(fx)), W - 2)
+            b = fx - x0
+            top = src[y0, x0] + b * (src[y0, x0 + 1] - src[y0, x0])
+            bot = src[y0 + 1, x0] + b * (src[y0 + 1, x0 + 1] - src[y0 + 1, x0])
+            out[r, c] = top + a * (bot - top)
+    return out
+
+
+def audit_selected(B, seed, step, fraction, score, threshold):
+    """The gate's physics audit: env b is audited when the gate keeps it
+    (not score[b] > threshold) and word 0 of Philox-4x32-10 on counter
+    (0, 0, b, 2), key (seed_lo ^ (uint32)(step * 0x9E3779B9), seed_hi), is
+    below floor(fraction 2^32).  Returns a bool array [B]."""
+    t = int(np.floor(fraction * 4294967296.0))
+    key = [(seed & 0xFFFFFFFF) ^ ((step * 0x9E3779B9) & 0xFFFFFFFF), (seed >> 32) & 0xFFFFFFFF]
+    out = np.zeros(B, bool)
+    for b in range(B):
+        if score[b] > threshold:
+            continue
+        out[b] = int(philox4x32_10([0, 0, b, 2], key)[0]) < t
     return out

@@ -98,22 +98,35 @@ def convT2x2(x, w4, b, relu=True):
     return torch.relu(y) if relu else y
 
 
-def forward(P, x, c: int, levels: int = 4, keep=None):
-    """x [B][H][W][8] -> frame [B][H][W] in (0, 1)."""
-    h = conv3x3(x, P["enc0a.w"], P["enc0a.b"], 1)
-    skips = [conv3x3(h, P["enc0b.w"], P["enc0b.b"], 1)]
+def bf16_round(t):
+    """round to the nearest bfloat16 (ties to even), back to float64"""
+    return t.to(torch.bfloat16).to(DT)
+
+
+def forward(P, x, c: int, levels: int = 4, keep=None, act=None):
+    """x [B][H][W][8] -> frame [B][H][W] in (0, 1).
+
+    act, if given, is applied to the output of every conv and convT (after
+    its ReLU): the surrogate's stated precision keeps activations in BF16
+    between layers (BF16 weights / activations, FP32 accumulation), which
+    ``act=bf16_round`` restates; the default keeps float64 throughout."""
+    A = act if act is not None else (lambda t: t)
+    h = A(conv3x3(x, P["enc0a.w"], P["enc0a.b"], 1))
+    skips = [A(conv3x3(h, P["enc0b.w"], P["enc0b.b"], 1))]
     h = skips[0]
     for l in range(1, levels):
-        h = conv3x3(h, P[f"down{l}.w"], P[f"down{l}.b"], 2)
-        h = conv3x3(h, P[f"enc{l}a.w"], P[f"enc{l}a.b"], 1)
-        h = conv3x3(h, P[f"enc{l}b.w"], P[f"enc{l}b.b"], 1)
+        h = A(conv3x3(h, P[f"down{l}.w"], P[f"down{l}.b"], 2))
+        h = A(conv3x3(h, P[f"enc{l}a.w"], P[f"enc{l}a.b"], 1))
+        h = A(conv3x3(h, P[f"enc{l}b.w"], P[f"enc{l}b.b"], 1))
         skips.append(h)
+    if keep is not None:
+        keep["bottleneck"] = skips[-1]
     h = skips[-1]
     for l in range(levels - 2, -1, -1):
-        u = convT2x2(h, P[f"up{l}.w"], P[f"up{l}.b"])
+        u = A(convT2x2(h, P[f"up{l}.w"], P[f"up{l}.b"]))
         h = torch.cat([u, skips[l]], dim=-1)
-        h = conv3x3(h, P[f"dec{l}a.w"], P[f"dec{l}a.b"], 1)
-        h = conv3x3(h, P[f"dec{l}b.w"], P[f"dec{l}b.b"], 1)
+        h = A(conv3x3(h, P[f"dec{l}a.w"], P[f"dec{l}a.b"], 1))
+        h = A(conv3x3(h, P[f"dec{l}b.w"], P[f"dec{l}b.b"], 1))
         if keep is not None:
             keep[f"dec{l}"] = h
     z = (h * P["head.w"]).sum(-1) + P["head.b"]
@@ -169,3 +182,39 @@ def adam_step(p, g, m, v, t, lr=2e-4, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
     return p - lr * mh / (torch.sqrt(vh) + eps), m, v
+
+
+# ---------------------------------------------------------------- error gate
+# The physics render judges the surrogate (the learned and the model-based
+# simulators of App. B.2 side by side): a linear head on the network's
+# bottleneck features predicts each frame's L1 gap to physics, and frames
+# predicted over a threshold are re-rendered by physics.  READING (the
+# paper has no gate): features = the channel means of the deepest encoder
+# activation; the head is fitted by ridge regression with an unpenalised
+# intercept.
+
+
+def features(bottleneck):
+    """[B][h][w][C] deepest activation -> [B][C] channel means"""
+    return bottleneck.mean(dim=(1, 2))
+
+
+def fit_error_head(feat, target, ridge):
+    """argmin_(w, w0) sum_i (w . f_i + w0 - t_i)^2 + ridge |w|^2, by its
+    normal equations [X^T X + diag(ridge, .., ridge, 0)] (w, w0) = X^T t with
+    X = [f, 1], solved by a library linear solve in float64.  Returns the
+    F + 1 coefficients (w, w0)."""
+    import numpy as np
+    f = np.asarray(feat, np.float64)
+    t = np.asarray(target, np.float64)
+    X = np.concatenate([f, np.ones((len(f), 1))], axis=1)
+    A = X.T @ X
+    A[np.arange(f.shape[1]), np.arange(f.shape[1])] += ridge
+    return np.linalg.solve(A, X.T @ t)
+
+
+def predict_error(coef, feat):
+    """w . f + w0 per frame"""
+    import numpy as np
+    f = np.asarray(feat, np.float64)
+    return f @ coef[:-1] + coef[-1]

@@ -704,6 +704,61 @@ int oracle_sample_slice_raw(const or_volume* vol, const or_probe* p, const float
   return sample_slice(vol, p, pose, out, 1);
 }
 
+/* Surrogate input on a common H x W grid over a probe's output field (the
+ * learned simulator of App. B.2 run at one size for every probe).  READING:
+ * pixel centres of an H x W grid spanning the field, in FP64, rounded once
+ * to FP32: curvilinear, the fan's bounding box in apex coordinates (as the
+ * scan conversion, at H x W), shifted by -r0 into the probe frame, flag =
+ * inside the fan; linear, x = ((c + 1/2) NL / W - 1/2 - (NL - 1) / 2) pitch,
+ * z = ((r + 1/2) NS / H - 1/2) dr, flag 1.  The voxel coordinate then
+ * follows the render's FP32 path.  out: [H][W][3] = (label / 4,
+ * clamp(HU / 1000, -1, 3), flag). */
+int oracle_sample_slice_grid(const or_volume* vol, const or_probe* p, const float* pose, int H, int W, double* out) {
+  const int NL = p->n_lines, NS = p->n_samples;
+  const float inv_h = (float)(1.0 / (double)vol->voxel_mm);
+  or_derived d;
+  or_derive(p, &d);
+  for (int r = 0; r < H; ++r) {
+    for (int c = 0; c < W; ++c) {
+      float x, z;
+      double flag = 1.0;
+      if (p->kind == 0) {
+        x = (float)(((c + 0.5) * NL / W - 0.5 - 0.5 * (NL - 1)) * (double)p->pitch_mm);
+        z = (float)(((r + 0.5) * NS / H - 0.5) * d.dr);
+      } else {
+        double r0 = p->radius_mm, D = p->depth_mm;
+        double half = 0.5 * (double)p->fan_deg * M_PI / 180.0;
+        double xmax = (r0 + D) * sin(half), xmin = -xmax;
+        double zmin = r0 * cos(half), zmax = r0 + D;
+        double xa = xmin + (c + 0.5) * (xmax - xmin) / W;
+        double za = zmin + (r + 0.5) * (zmax - zmin) / H;
+        double fl = atan2(xa, za) / d.dtheta + 0.5 * (NL - 1);
+        double fs = (hypot(xa, za) - r0) / d.dr;
+        flag = (fl >= 0 && fl <= NL - 1 && fs >= 0 && fs <= NS - 1) ? 1.0 : 0.0;
+        x = (float)xa;
+        z = (float)(za - r0);
+      }
+      float u[3];
+      for (int k = 0; k < 3; ++k) {
+        float a = pose[k * 4 + 0] * x;
+        float b = pose[k * 4 + 2] * z;
+        float q = a + b;
+        float pc = q + pose[k * 4 + 3];
+        u[k] = pc * inv_h;
+      }
+      int64_t idx = or_nearest(vol, u);
+      double hu = or_trilinear_hu(vol, u) / 1000.0;
+      if (hu < -1.0) hu = -1.0;
+      if (hu > 3.0) hu = 3.0;
+      double* o = out + ((int64_t)r * W + c) * 3;
+      o[0] = (idx >= 0 ? (double)vol->labels[idx] : 0.0) / 4.0;
+      o[1] = hu;
+      o[2] = flag;
+    }
+  }
+  return 0;
+}
+
 /* ------------------------------------------- reconstruction observation */
 /*
  * Task 2 of Sec. 4 with App. C: the bone surface segmented from each frame

@@ -547,8 +547,9 @@ us_status backward_impl(us_surr* s, int B, cudaStream_t st) {
 }
 
 us_status loss_impl(us_surr* s, const float* pred, const float* target, int B, float* loss_out, float* dpred,
-                    cudaStream_t st) {
-  const int H = s->cfg.height, W = s->cfg.width;
+                    cudaStream_t st, int H = 0, int W = 0) {
+  if (H == 0) H = s->cfg.height;
+  if (W == 0) W = s->cfg.width;
   const int n_ss = (int)blocks((long long)(H - kWin + 1) * (W - kWin + 1), kRedThreads);
   const int n_l1 = (int)blocks((long long)H * W, kRedThreads);
   ssim_hpass<<<blocks((long long)B * H * (W - kWin + 1)), 256, 0, st>>>(pred, target, s->sh, B, H, W);
@@ -757,6 +758,15 @@ us_status us_surr_metrics(us_surr* s, const float* pred, const float* target, in
   if (!s) return US_ERR_INVALID_ARG;
   if (!pred || !target || !out || B < 1 || B > s->cfg.max_batch) return fail(s, US_ERR_INVALID_ARG, "bad metrics arguments");
   return loss_impl(s, pred, target, B, out, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+us_status us_surr_metrics_hw(us_surr* s, const float* pred, const float* target, int32_t B, int32_t H, int32_t W,
+                             float* out, void* stream) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (!pred || !target || !out || B < 1 || B > s->cfg.max_batch || H < kWin || W < kWin || H > s->cfg.height ||
+      W > s->cfg.width)
+    return fail(s, US_ERR_INVALID_ARG, "bad metrics arguments");
+  return loss_impl(s, pred, target, B, out, nullptr, static_cast<cudaStream_t>(stream), H, W);
 }
 
 int32_t us_surr_num_features(const us_surr* s) { return s ? 8 * s->cfg.base_channels : -1; }

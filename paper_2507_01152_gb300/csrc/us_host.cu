@@ -359,10 +359,16 @@ void free_sim(us_sim* s) {
     cudaFree(kv.second.d_items_batch);
     cudaFree(kv.second.d_items_gated);
     cudaFree(kv.second.d_gated_count);
+    cudaFree(kv.second.d_items_audit);
+    cudaFree(kv.second.d_audit_count);
     cudaFree(kv.second.d_beam);
     cudaFree(kv.second.d_sync);
     cudaFree(kv.second.d_slice_hu);
     cudaFree(kv.second.d_slice_fan);
+  }
+  for (auto& g : s->grids) {
+    cudaFree(g.second.d_tabs);
+    for (void* b : g.second.bufs) cudaFree(b);
   }
   cudaFree(s->d_vols);
   cudaFree(s->d_probes);
@@ -844,6 +850,129 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
                         cudaSuccess)
     return cuda_fail(s, e, "gated count");
   return US_OK;
+}
+
+us_status us_sim_render_audit(us_sim* s, const us_env* envs, int32_t B, const float* poses, uint64_t seed,
+                              uint64_t step, float* audit_frames, const float* score, float threshold, float fraction,
+                              uint8_t* flags, int32_t* n_audited, void* stream) {
+  us_status r = check_render_args(s, envs, B, poses, audit_frames);
+  if (r != US_OK || B == 0) return r;
+  if (!score) return fail(s, US_ERR_INVALID_ARG, "NULL score");
+  if (!(fraction >= 0.f && fraction <= 1.f)) return fail(s, US_ERR_INVALID_ARG, "audit fraction must be in [0, 1]");
+  if (B > 32 * 1024) return fail(s, US_ERR_UNSUPPORTED, "audited batches are limited to 32768 envs");
+  if (!s->batched) return no_batched(s);
+  us_plan* pl;
+  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  cudaError_t e;
+  if (!pl->d_items_audit && ((e = cudaMalloc(&pl->d_items_audit, sizeof(EnvItem) * B)) != cudaSuccess ||
+                             (e = cudaMalloc(&pl->d_audit_count, sizeof(int))) != cudaSuccess))
+    return cuda_fail(s, e, "audit work list");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  RenderParams p = base_params(s, poses, seed, step, audit_frames);
+  const double t = std::floor((double)fraction * 4294967296.0);
+  if ((e = launch_audit_compact(pl->d_items_batch, B, score, threshold, p.key, (unsigned long long)t,
+                                pl->d_items_audit, pl->d_audit_count, flags, st)) != cudaSuccess)
+    return cuda_fail(s, e, "audit selection");
+  p.items = pl->d_items_audit;
+  p.n_items = B;
+  p.n_items_dev = pl->d_audit_count;
+  if (s->tuning.cluster_size == 1) {
+    if ((e = two_pass_buffers(pl)) != cudaSuccess) return cuda_fail(s, e, "two-pass line buffer");
+    if ((e = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, st)) != cudaSuccess)
+      return cuda_fail(s, e, "audit render");
+  } else if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess ||
+             (e = launch_fused(p, s->shape, st)) != cudaSuccess) {
+    return cuda_fail(s, e, "audit render");
+  }
+  if (n_audited && (e = cudaMemcpyAsync(n_audited, pl->d_audit_count, sizeof(int), cudaMemcpyDeviceToDevice, st)) !=
+                       cudaSuccess)
+    return cuda_fail(s, e, "audit count");
+  return US_OK;
+}
+
+us_status us_sim_sample_slices_grid(us_sim* s, const us_env* envs, int32_t B, const float* poses, int32_t H,
+                                    int32_t W, uint16_t* out, void* stream) {
+  us_status r = check_render_args(s, envs, B, poses, reinterpret_cast<float*>(out));
+  if (r != US_OK || B == 0) return r;
+  if (H < 2 || W < 2 || H > 4096 || W > 4096) return fail(s, US_ERR_INVALID_ARG, "grid size must be in [2, 4096]");
+  us_plan* pl;
+  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  auto key = std::make_pair((int)H, (int)W);
+  auto it = s->grids.find(key);
+  cudaError_t e;
+  if (it == s->grids.end()) {
+    // per probe: pixel centres of an H x W grid over its output field, in
+    // FP64, rounded once to FP32 (curvilinear: the fan's bounding box in apex
+    // coordinates, shifted by -r0 into the probe frame, and the inside-fan
+    // test of the scan conversion; linear: the rectangle of lines 0 .. NL-1
+    // and samples 0 .. NS-1, all inside)
+    us_sim::GridTabs g;
+    std::vector<DevGridTab> tabs;
+    for (const ProbeHost& ph : s->probes) {
+      const us_probe& p = ph.desc;
+      const int NL = p.n_lines, NS = p.n_samples;
+      std::vector<float> px(W), pz(H);
+      std::vector<uint8_t> mask((size_t)H * W, 1);
+      if (p.kind == 1) {
+        const double r0 = p.radius_mm, D = p.depth_mm;
+        const double half = 0.5 * (double)p.fan_deg * M_PI / 180.0;
+        const double xmax = (r0 + D) * std::sin(half), xmin = -xmax;
+        const double zmin = r0 * std::cos(half), zmax = r0 + D;
+        for (int c = 0; c < W; ++c) px[c] = (float)(xmin + (c + 0.5) * (xmax - xmin) / W);
+        for (int q = 0; q < H; ++q) pz[q] = (float)(zmin + (q + 0.5) * (zmax - zmin) / H - r0);
+        for (int q = 0; q < H; ++q)
+          for (int c = 0; c < W; ++c) {
+            const double x = xmin + (c + 0.5) * (xmax - xmin) / W;
+            const double z = zmin + (q + 0.5) * (zmax - zmin) / H;
+            const double fl = std::atan2(x, z) / ph.dtheta + 0.5 * (NL - 1);
+            const double fs = (std::hypot(x, z) - r0) / ph.dr;
+            mask[(size_t)q * W + c] = fl >= 0 && fl <= NL - 1 && fs >= 0 && fs <= NS - 1;
+          }
+      } else {
+        for (int c = 0; c < W; ++c)
+          px[c] = (float)(((c + 0.5) * NL / W - 0.5 - 0.5 * (NL - 1)) * (double)p.pitch_mm);
+        for (int q = 0; q < H; ++q) pz[q] = (float)(((q + 0.5) * NS / H - 0.5) * ph.dr);
+      }
+      float *dpx = nullptr, *dpz = nullptr;
+      uint8_t* dm = nullptr;
+      if ((e = upload(&dpx, px.data(), px.size())) == cudaSuccess) g.bufs.push_back(dpx);
+      if (e == cudaSuccess && (e = upload(&dpz, pz.data(), pz.size())) == cudaSuccess) g.bufs.push_back(dpz);
+      if (e == cudaSuccess && (e = upload(&dm, mask.data(), mask.size())) == cudaSuccess) g.bufs.push_back(dm);
+      if (e != cudaSuccess) {
+        for (void* b : g.bufs) cudaFree(b);
+        return cuda_fail(s, e, "surrogate grid tables");
+      }
+      tabs.push_back(DevGridTab{dpx, dpz, dm});
+    }
+    if ((e = upload(&g.d_tabs, tabs.data(), tabs.size())) != cudaSuccess) {
+      for (void* b : g.bufs) cudaFree(b);
+      return cuda_fail(s, e, "surrogate grid tables");
+    }
+    it = s->grids.emplace(key, std::move(g)).first;
+  }
+  RenderParams p = base_params(s, poses, 0, 0, nullptr);
+  if ((e = launch_grid_slices(p, pl->d_items_batch, B, H, W, it->second.d_tabs, out,
+                              static_cast<cudaStream_t>(stream))) != cudaSuccess)
+    return cuda_fail(s, e, "grid slice sampling launch");
+  return US_OK;
+}
+
+us_status us_sim_resize_frames(us_sim* s, const us_env* envs, int32_t B, const float* src, int32_t H, int32_t W,
+                               float* frames, void* stream) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (B < 0) return fail(s, US_ERR_INVALID_ARG, "B must be >= 0");
+  if (B == 0) return US_OK;
+  if (!envs || !src || !frames) return fail(s, US_ERR_INVALID_ARG, "NULL envs, src or frames");
+  if (!aligned16(frames)) return fail(s, US_ERR_INVALID_ARG, "frames must be 16-byte aligned");
+  if (H < 2 || W < 2 || H > 4096 || W > 4096) return fail(s, US_ERR_INVALID_ARG, "grid size must be in [2, 4096]");
+  us_plan* pl;
+  us_status r;
+  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  int max_out = 0;
+  for (const ProbeHost& ph : s->probes) max_out = std::max(max_out, ph.desc.out_w * ph.desc.out_h);
+  RenderParams p = base_params(s, nullptr, 0, 0, frames);
+  cudaError_t e = launch_resize(p, pl->d_items_batch, B, src, H, W, max_out, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? US_OK : cuda_fail(s, e, "resize launch");
 }
 
 us_status us_sim_render_3d(us_sim* s, const us_env* envs, int32_t B, const float* poses, int32_t n_elev,

@@ -133,6 +133,25 @@ void build_wedges(const std::vector<float2>& lut, int W, int H, int NL, int NS, 
 // items with score > thr, in batch order, and their count (device)
 cudaError_t launch_gate_compact(const EnvItem* items, int B, const float* score, float thr, EnvItem* out, int* count,
                                 cudaStream_t st);
+// items the gate keeps (score <= thr) that the seeded audit selects (Philox
+// word below t_audit), in batch order, their count and per-env flags
+cudaError_t launch_audit_compact(const EnvItem* items, int B, const float* score, float thr, uint2 key,
+                                 unsigned long long t_audit, EnvItem* out, int* count, uint8_t* flags,
+                                 cudaStream_t st);
+
+// a probe's H x W surrogate grid over its output field: probe-frame x of
+// each column, z of each row (FP64 on the host, rounded once), and the
+// inside-fan flag of each pixel
+struct DevGridTab {
+  const float* px;
+  const float* pz;
+  const uint8_t* mask;
+};
+cudaError_t launch_grid_slices(const RenderParams& p, const EnvItem* items_batch, int B, int H, int W,
+                               const DevGridTab* tabs, void* out, cudaStream_t st);
+// H x W frames -> each env's own output grid (p.frames, frame layout)
+cudaError_t launch_resize(const RenderParams& p, const EnvItem* items_batch, int B, const float* src, int H, int W,
+                          int max_out, cudaStream_t st);
 
 // surrogate input of a batch on the output pixel grid: [B][H][W][8] BF16
 cudaError_t launch_slice_input(const RenderParams& p, const EnvItem* items_batch, int B, int H, int W, void* out,
@@ -175,6 +194,8 @@ struct us_plan {
   ussim::EnvItem* d_items_batch = nullptr;   // device copy of items_batch
   ussim::EnvItem* d_items_gated = nullptr;   // device-built subset for gated renders
   int* d_gated_count = nullptr;
+  ussim::EnvItem* d_items_audit = nullptr;   // device-built subset for the gate's physics audit
+  int* d_audit_count = nullptr;
   long long frame_floats = 0, beam_elems = 0;
   float* d_beam = nullptr;                   // two-pass path: filtered lines of the batch
   int g_pers = -1;                           // captured graph's persistent flag
@@ -218,6 +239,14 @@ struct us_sim {
   bool batched = true;         // a batched launch shape fits the probe set
 
   std::map<std::string, us_plan> plans;
+
+  // surrogate grids of every probe, per grid size (H, W): device tables and
+  // the allocations behind them
+  struct GridTabs {
+    ussim::DevGridTab* d_tabs = nullptr;
+    std::vector<void*> bufs;
+  };
+  std::map<std::pair<int, int>, GridTabs> grids;
 
   // 3-D probe: swept poses
   float* d_poses3d = nullptr;

@@ -94,6 +94,10 @@ SIGNATURES = {
                                       _P, C.c_int32, _P]),
     "us_sim_recon_observe": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, C.c_int32, _P, _P]),
     "us_sim_sample_slices": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
+    "us_sim_sample_slices_grid": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P]),
+    "us_sim_resize_frames": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P]),
+    "us_sim_render_audit": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, C.c_float, C.c_float,
+                                      _P, _P, _P]),
     "us_sim_render_gated": (C.c_int, [_P, _P, C.c_int32, _P, C.c_uint64, C.c_uint64, _P, _P, C.c_float, _P, _P]),
     "us_sim_get_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
     "us_sim_set_tuning": (C.c_int, [_P, C.POINTER(us_tuning)]),
@@ -115,6 +119,7 @@ SIGNATURES = {
     "us_surr_forward": (C.c_int, [_P, _P, _P, _I, _P]),
     "us_surr_train_step": (C.c_int, [_P, _P, _P, _I, _P, _I, _P]),
     "us_surr_metrics": (C.c_int, [_P, _P, _P, _I, _P, _P]),
+    "us_surr_metrics_hw": (C.c_int, [_P, _P, _P, _I, _I, _I, _P, _P]),
     "us_surr_num_features": (C.c_int32, [_P]),
     "us_surr_features": (C.c_int, [_P, C.c_int32, _P, _P]),
     "us_surr_predict_error": (C.c_int, [_P, C.c_int32, _P, _P]),
@@ -383,6 +388,29 @@ class Sim:
         self._check(self._lib.us_sim_render_gated(self.h, e, B, _ptr(poses), seed, step, _ptr(frames), _ptr(score),
                                                   float(threshold), _ptr(n_rendered), _stream_handle(stream)))
 
+    def render_audit(self, envs, poses, seed, step, audit_frames, score, threshold, fraction, flags=None,
+                     n_audited=None, stream=None, envs_c=None):
+        """physics render of the seeded audit subset of the frames the gate keeps"""
+        B = poses.shape[0]
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_render_audit(self.h, e, B, _ptr(poses), seed, step, _ptr(audit_frames),
+                                                  _ptr(score), float(threshold), float(fraction), _ptr(flags),
+                                                  _ptr(n_audited), _stream_handle(stream)))
+
+    def sample_slices_grid(self, envs, poses, H, W, out, stream=None, envs_c=None):
+        """surrogate input [B][H][W][8] bf16 on an H x W grid over each env's field"""
+        B = poses.shape[0]
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_sample_slices_grid(self.h, e, B, _ptr(poses), int(H), int(W), _ptr(out),
+                                                        _stream_handle(stream)))
+
+    def resize_frames(self, envs, src, frames, stream=None, envs_c=None):
+        """src [B][H][W] float32 -> frames in the batch's frame layout"""
+        B, H, W = src.shape
+        e = envs_c if envs_c is not None else make_envs(envs)
+        self._check(self._lib.us_sim_resize_frames(self.h, e, B, _ptr(src), H, W, _ptr(frames),
+                                                   _stream_handle(stream)))
+
     def sample_slices(self, envs, poses, out, stream=None, envs_c=None):
         """surrogate input [B][H][W][8] bf16 (out: torch bfloat16 CUDA tensor)"""
         B = poses.shape[0]
@@ -464,6 +492,12 @@ class Surrogate:
     def metrics(self, pred, target, out, stream=None):
         self._check(self._lib.us_surr_metrics(self.h, _ptr(pred), _ptr(target), pred.shape[0], _ptr(out),
                                               _stream_handle(stream)))
+
+    def metrics_hw(self, pred, target, out, stream=None):
+        """per-frame L1 / SSIM of [B][H][W] frames of any size up to the network's"""
+        B, H, W = pred.shape
+        self._check(self._lib.us_surr_metrics_hw(self.h, _ptr(pred), _ptr(target), B, H, W, _ptr(out),
+                                                 _stream_handle(stream)))
 
     def num_features(self):
         return self._lib.us_surr_num_features(self.h)

@@ -131,3 +131,55 @@ def test_adam_matches_torch_optimizer():
     # first step moves every coordinate by about lr against the gradient's sign
     p1, _, _ = S.adam_step(p0, grads[0], torch.zeros(50, dtype=S.DT), torch.zeros(50, dtype=S.DT), 1)
     assert torch.allclose(p1 - p0, -2e-4 * torch.sign(grads[0]), atol=1e-9)
+
+
+def test_bf16_round_is_round_to_nearest_even():
+    """the BF16 activation rounding the parity tests restate: 8 significant
+    bits, ties to even (values chosen by hand)"""
+    v = torch.tensor([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -9, 3.0 + 2 ** -7, -2.5, 0.0],
+                     dtype=torch.float64)
+    want = [1.0, 1.0, 1.0 + 2 ** -6, 1.0, 3.0, -2.5, 0.0]
+    assert S.bf16_round(v).tolist() == want
+    x = torch.randn(1000, dtype=torch.float64, generator=torch.Generator().manual_seed(2))
+    r = S.bf16_round(x)
+    assert torch.all((r - x).abs() <= 2.0 ** -8 * x.abs())          # half an ulp: at most 2^-8 relative
+
+
+def test_bf16_forward_is_the_float64_forward_rounded_per_layer():
+    """with act = identity the BF16 option changes nothing; with BF16
+    rounding every activation the network output moves by no more than the
+    per-layer rounding lets it"""
+    c = 4
+    P = S.unflatten(torch.randn(S.n_params(c), dtype=torch.float64, generator=torch.Generator().manual_seed(1)) * 0.3,
+                    c)
+    x = torch.rand((1, 16, 16, 8), dtype=torch.float64, generator=torch.Generator().manual_seed(2))
+    a = S.forward(P, x, c)
+    b = S.forward(P, x, c, act=lambda t: t)
+    assert torch.equal(a, b)
+    keep = {}
+    q = S.forward(P, x, c, keep=keep, act=S.bf16_round)
+    assert torch.equal(keep["bottleneck"], S.bf16_round(keep["bottleneck"]))
+    assert 0 < float((q - a).abs().max()) < 0.05
+
+
+def test_error_head_ridge_closed_forms():
+    """The error head's ridge regression (unpenalised intercept):
+    * ridge 0 on an exactly linear target recovers its coefficients;
+    * one feature: w = sum (f - fbar)(t - tbar) / (sum (f - fbar)^2 + ridge),
+      w0 = tbar - w fbar (the textbook closed form);
+    * a huge ridge drives w to 0 and w0 to the mean target."""
+    r = _rng(8)
+    f = r.normal(size=(50, 3))
+    coef = np.array([0.5, -2.0, 0.25, 1.5])
+    t = f @ coef[:3] + coef[3]
+    np.testing.assert_allclose(S.fit_error_head(f, t, 0.0), coef, rtol=1e-10, atol=1e-12)
+    f1 = r.normal(size=(40, 1))
+    t1 = r.normal(size=40)
+    for lam in (0.0, 0.3, 7.0):
+        fc, tc = f1[:, 0] - f1[:, 0].mean(), t1 - t1.mean()
+        w = (fc @ tc) / (fc @ fc + lam)
+        got = S.fit_error_head(f1, t1, lam)
+        np.testing.assert_allclose(got, [w, t1.mean() - w * f1[:, 0].mean()], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(S.predict_error(got, f1), w * f1[:, 0] + got[1], rtol=1e-12)
+    big = S.fit_error_head(f, t, 1e12)
+    assert np.all(np.abs(big[:3]) < 1e-8) and abs(big[3] - t.mean()) < 1e-6
