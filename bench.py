@@ -59,10 +59,18 @@ KERNEL_DRAM_BYTES = {}
 # read (64 x 48 B).  The voxel count comes from the oracle's exact count for
 # these poses; the CPU test suite re-derives it.
 C2_TOUCHED_VOXELS_VALUE = 3075431
+# The same for the 512-env batch of four 512 x 512 x 256 volumes and three
+# probes (first step of its random walks), counted per volume and summed.
+C3_TOUCHED_VOXELS_VALUE = 18472899
 
 
 def c2_launch_bytes(B=64):
     return 3 * C2_TOUCHED_VOXELS_VALUE + B * 256 * 256 * 4 + B * 48
+
+
+def c3_launch_bytes(wl):
+    pixels = sum(wl.probes[int(p)].out_w * wl.probes[int(p)].out_h for p in np.asarray(wl.envs)[:, 1])
+    return 3 * C3_TOUCHED_VOXELS_VALUE + 4 * pixels + len(wl.envs) * 48
 
 
 def load_peaks():
@@ -297,52 +305,105 @@ def hist_match_speed(sim, P, ec, x, stream):
             "bytes_per_pixel": 14, "note": "reference: 4096 one-HU bins of another synthetic volume"}
 
 
-def run_mixed(args):
-    """Mixed production step on 1024 envs over the four 512 x 512 x 256
-    volumes (curvilinear 256 x 512 probe, 256 x 256 frames): surrogate
-    frames for every env, physics re-render of the frames whose predicted
-    L1 gap exceeds the gate; compared with all-physics (fused and plain
-    per-env) on the same batch.  The surrogate is first trained here on
-    pairs the physics path renders on the 256^3 volume."""
+def c5_surrogate_block(args, volumes=None, log=lambda *a: None):
+    """The learned surrogate in production (C5), after its training (C4).
+
+    Training: ``args.train_pairs`` fresh physics pairs (curvilinear 256 x 512
+    probe on the 256^3 volume, 256 x 256 frames) in batches of
+    ``args.train_batch``, every pair rendered on the device in the loop;
+    held-out L1 / SSIM on 2048 poses from seeds 1,000,000 on.
+
+    Production step on 1024 envs over the four C3 volumes and the three C3
+    probes (a third each): the label / CT slices of every env on one
+    256 x 256 grid over its own output field, the surrogate forward, the
+    error head, the resize back to each env's frame, then the physics
+    fallback for the frames whose predicted L1 gap exceeds the gate and the
+    physics audit of a seeded 5% of the frames the gate kept.  The error
+    head is fitted on two calibration steps of the same batch (surrogate
+    against all-physics, per-frame L1).  Compared with all-physics batched
+    and plain per-env renders of the same batch on the same GPU; L1 / SSIM
+    of the mixed and surrogate-only frames against the all-physics frames of
+    the same step, per probe type."""
+    import math as _m
     import torch
-    from paper_2507_01152_gb300 import build
     from paper_2507_01152_gb300 import train as T
     from paper_2507_01152_gb300.ussim import Sim, make_envs
-    build.build()
-    torch.cuda.set_device(0)
-    B = 1024
+    B, G = 1024, 256
+    tb = args.train_batch
+    steps = max(1, _m.ceil(args.train_pairs / tb))
     t0 = time.perf_counter()
-    net, src, hist = T.train(args.train_steps, batch=128, c=32, lr=args.lr, log_every=0, max_batch=B)
+    net, src, hist = T.train(steps, batch=tb, c=32, lr=args.lr, log_every=0, max_batch=B)
+    torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    l1_h, ss_h = T.evaluate(net, src, 4)
-    feat, true_l1 = T.gate_samples(net, src, 16)
-    net.fit_error_head(feat, true_l1, ridge=1e-2)
+    l1_h, ss_h = T.evaluate(net, src, max(1, _m.ceil(2048 / tb)))
     src.sim.close()
+    log(f"trained {steps} x {tb} pairs in {train_s:.1f} s; held-out L1 {l1_h:.4f} SSIM {ss_h:.4f}")
 
-    specs = scene.c3_specs()
-    vols = [(s_, *scene.make_volume(s_)) for s_ in specs]
-    probe = scene.curvilinear_probe()
-    envs = np.stack([np.arange(B) % 4, np.zeros(B)], axis=1).astype(np.int32)
-    poses = np.empty((B, 3, 4), np.float32)
-    for v in range(4):
-        idx = np.nonzero(envs[:, 0] == v)[0]
-        poses[idx] = scene.random_walk_poses(specs[v], len(idx), 1, 3000 + v)[0]
-    dv = [(torch.from_numpy(l).cuda(), torch.from_numpy(h).cuda(), s_.voxel_mm) for (s_, l, h) in vols]
-    sim = Sim(dv, scene.tissue_table(), [probe], scene.Options())
-    ec = make_envs(envs)
-    P = torch.from_numpy(poses).cuda()
+    wl = scene.workload_c5(B, steps=3, volumes=volumes)
+    dv = [(torch.from_numpy(l).cuda(), torch.from_numpy(h).cuda(), s_.voxel_mm) for (s_, l, h) in wl.volumes]
+    sim = Sim(dv, scene.tissue_table(), wl.probes, wl.options)
+    envs, ec = wl.envs, make_envs(wl.envs)
+    off = sim.frame_layout(envs)
+    groups = []                    # (probe, first env, count): contiguous frames of one size
+    for p_ in range(3):
+        idx = np.nonzero(envs[:, 1] == p_)[0]
+        groups.append((p_, int(idx[0]), len(idx)))
+    Pw = [torch.from_numpy(np.ascontiguousarray(wl.poses[k])).cuda() for k in range(3)]
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        sim.autotune(envs, P, torch.zeros((B, 256, 256), device="cuda"), None, stream=stream)
-    x = torch.zeros((B, 256, 256, 8), dtype=torch.bfloat16, device="cuda")
-    frames = torch.zeros((B, 256, 256), device="cuda")
-    phys = torch.zeros_like(frames)
-    surr = torch.zeros_like(frames)
+    nf = int(off[-1])
+    frames = torch.zeros(nf, device="cuda")
+    phys = torch.zeros(nf, device="cuda")
+    audit = torch.zeros(nf, device="cuda")
+    x = torch.zeros((B, G, G, 8), dtype=torch.bfloat16, device="cuda")
+    s256 = torch.zeros((B, G, G), device="cuda")
     pe = torch.zeros(B, device="cuda")
+    feat = torch.zeros((B, net.num_features()), device="cuda")
     nr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    na = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flags = torch.zeros(B, dtype=torch.uint8, device="cuda")
     met = torch.zeros(1 + 2 * B, device="cuda")
-    seed = 0x5EED0005
-    thr = args.gate_l1
+    seed = wl.seed
+    thr, frac = args.gate_l1, 0.05
+    with torch.cuda.stream(stream):
+        sim.autotune(envs, Pw[0], phys, None, stream=stream)
+
+    def view(buf, g):
+        p_, first, n = g
+        pr = wl.probes[p_]
+        return buf[int(off[first]):int(off[first]) + n * pr.out_h * pr.out_w].view(n, pr.out_h, pr.out_w)
+
+    def per_frame(a, b):
+        """per-frame (L1, SSIM) of frames a against b, env order"""
+        l1, ss = np.zeros(B), np.zeros(B)
+        for g in groups:
+            p_, first, n = g
+            net.metrics_hw(view(a, g), view(b, g), met[:1 + 2 * n], stream=stream)
+            m = met[:1 + 2 * n].cpu().numpy()
+            l1[first:first + n], ss[first:first + n] = m[1:1 + n], m[1 + n:1 + 2 * n]
+        return l1, ss
+
+    def surrogate(P):
+        sim.sample_slices_grid(None, P, G, G, x, stream=stream, envs_c=ec)
+        net.forward(x, s256, stream=stream)
+        net.predict_error(B, pe, stream=stream)
+        sim.resize_frames(None, s256, frames, stream=stream, envs_c=ec)
+
+    def mixed(P, step):
+        surrogate(P)
+        sim.render_gated(None, P, seed, step, frames, pe, thr, nr, stream=stream, envs_c=ec)
+        sim.render_audit(None, P, seed, step, audit, pe, thr, frac, flags, na, stream=stream, envs_c=ec)
+
+    # error head on two calibration steps (poses of walk steps 1 and 2)
+    fs, ys = [], []
+    with torch.cuda.stream(stream):
+        for k in (1, 2):
+            surrogate(Pw[k])
+            net.features(B, feat, stream=stream)
+            sim.render(None, Pw[k], seed, 900 + k, phys, stream=stream, envs_c=ec)
+            l1, _ = per_frame(frames, phys)
+            fs.append(feat.cpu().numpy())
+            ys.append(l1)
+    net.fit_error_head(np.concatenate(fs), np.concatenate(ys), ridge=1e-2)
 
     def timed(fn, k):
         with torch.cuda.stream(stream):
@@ -356,38 +417,67 @@ def run_mixed(args):
             b.synchronize()
         return a.elapsed_time(b) / k
 
-    ms_mixed = timed(lambda i: T.mixed_step(sim, net, P, seed, i, x, frames, pe, thr, nr, stream=stream, envs_c=ec),
-                     args.steps)
-    ms_phys = timed(lambda i: sim.render(None, P, seed, i, phys, stream=stream, envs_c=ec), args.steps)
-    ms_plain = timed(lambda i: sim.render_plain(None, P, seed, i, phys, stream=stream, envs_c=ec), 2)
-    ms_surr = timed(lambda i: (sim.sample_slices(None, P, x, stream=stream, envs_c=ec), net.forward(x, surr, stream=stream)),
-                    args.steps)
+    P0 = Pw[0]
+    ms_mixed = timed(lambda i: mixed(P0, i), args.c5_steps)
+    ms_surr = timed(lambda i: surrogate(P0), args.c5_steps)
+    ms_phys = timed(lambda i: sim.render(None, P0, seed, i, phys, stream=stream, envs_c=ec), args.c5_steps)
+    ms_plain = timed(lambda i: sim.render_plain(None, P0, seed, i, phys, stream=stream, envs_c=ec), 2)
     # quality of one step against the all-physics render of the same step
     with torch.cuda.stream(stream):
-        T.mixed_step(sim, net, P, seed, 7, x, frames, pe, thr, nr, stream=stream, envs_c=ec)
-        sim.render(None, P, seed, 7, phys, stream=stream, envs_c=ec)
-        sim.sample_slices(None, P, x, stream=stream, envs_c=ec)
-        net.forward(x, surr, stream=stream)
-        net.metrics(frames, phys, met, stream=stream)
+        mixed(P0, 7)
+        pe_h = pe.cpu().numpy()
+        fl = flags.cpu().numpy().astype(bool)
+        n_re = int(nr.item())
+        sim.render(None, P0, seed, 7, phys, stream=stream, envs_c=ec)
+        mix_l1, mix_ss = per_frame(frames, phys)
+        surrogate(P0)
+        sur_l1, sur_ss = per_frame(frames, phys)
+        aud_l1, _ = per_frame(frames, audit)         # surrogate frames against their audit renders
         stream.synchronize()
-        mixed_l1, mixed_ss = float(met[1:1 + B].mean()), float(met[1 + B:].mean())
-        net.metrics(surr, phys, met, stream=stream)
-        stream.synchronize()
-        surr_l1, surr_ss = float(met[1:1 + B].mean()), float(met[1 + B:].mean())
     net.check(stream)
-    line = {"metric": METRIC, "value": B / ms_mixed * 1e3, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": 2, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16+f32", "data": "synthetic",
-            "config": {"workload": "mixed_production_1024env_curvilinear_256x512_4vol", "envs": B,
-                       "tuning": sim.get_tuning(),
-                       "gate": f"re-render by physics where predicted L1 > {thr}"},
-            "mixed": {"frames_per_s": B / ms_mixed * 1e3, "rerendered_frac": int(nr.item()) / B,
-                      "l1_vs_physics": mixed_l1, "ssim_vs_physics": mixed_ss},
-            "surrogate_only": {"frames_per_s": B / ms_surr * 1e3, "l1_vs_physics": surr_l1, "ssim_vs_physics": surr_ss},
-            "all_physics_fused": {"frames_per_s": B / ms_phys * 1e3},
-            "all_physics_plain_per_env": {"frames_per_s": B / ms_plain * 1e3},
-            "training": {"steps": args.train_steps, "batch": 128, "pairs": 128 * args.train_steps, "seconds": train_s,
-                         "heldout_l1": l1_h, "heldout_ssim": ss_h, "loss_first_last": [hist[0][1], hist[-1][1]]}}
+    sim.check(stream)
+    gated = pe_h > thr
+    names = ["linear_128x256", "curvilinear_192x384", "curvilinear_256x512"]
+    per_probe = {}
+    for (p_, first, n) in groups:
+        sl = slice(first, first + n)
+        per_probe[names[p_]] = {"envs": n, "rerendered_frac": float(gated[sl].mean()),
+                                "mixed_l1": float(mix_l1[sl].mean()), "mixed_ssim": float(mix_ss[sl].mean()),
+                                "surrogate_l1": float(sur_l1[sl].mean()), "surrogate_ssim": float(sur_ss[sl].mean())}
+    audit_rep = {"fraction": frac, "audited": int(fl.sum()),
+                 "pred_abs_err": float(np.abs(pe_h[fl] - aud_l1[fl]).mean()) if fl.any() else None,
+                 "true_l1_mean": float(aud_l1[fl].mean()) if fl.any() else None,
+                 "missed_over_gate": float((aud_l1[fl] > thr).mean()) if fl.any() else None}
+    sim.close()
+    net.close()
+    return {"workload": wl.name, "envs": B, "grid": f"{G}x{G}", "gate_l1": thr,
+            "mixed": {"frames_per_s": B / ms_mixed * 1e3, "ms_per_step": ms_mixed, "rerendered_frac": n_re / B,
+                      "l1_vs_physics": float(mix_l1.mean()), "ssim_vs_physics": float(mix_ss.mean()),
+                      "meets_gate": bool(mix_l1.mean() <= thr and mix_ss.mean() >= 0.80)},
+            "surrogate_only": {"frames_per_s": B / ms_surr * 1e3, "ms_per_step": ms_surr,
+                               "l1_vs_physics": float(sur_l1.mean()), "ssim_vs_physics": float(sur_ss.mean()),
+                               "tflops": 2 * 10.74e9 * B / ms_surr / 1e9},
+            "all_physics_batched": {"frames_per_s": B / ms_phys * 1e3, "ms_per_step": ms_phys},
+            "all_physics_plain_per_env": {"frames_per_s": B / ms_plain * 1e3, "ms_per_step": ms_plain},
+            "per_probe": per_probe, "audit": audit_rep,
+            "training": {"pairs": steps * tb, "batch": tb, "steps": steps, "seconds": train_s,
+                         "heldout_poses": max(1, _m.ceil(2048 / tb)) * tb, "heldout_l1": l1_h, "heldout_ssim": ss_h,
+                         "loss_first_last": [hist[0][1], hist[-1][1]]}}
+
+
+def run_mixed(args):
+    """The C4 training and C5 production step alone, as one JSON line."""
+    import torch
+    from paper_2507_01152_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    blk = c5_surrogate_block(args, log=lambda m: print(m, file=sys.stderr, flush=True))
+    line = {"metric": METRIC, "value": blk["mixed"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1,
+            "steps": args.c5_steps, "warmup": 2, "ms_per_step": blk["mixed"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": blk["workload"], "envs": blk["envs"],
+                       "gate": f"physics re-render where predicted L1 > {blk['gate_l1']}; 5% physics audit"},
+            "surrogate": blk}
     print(json.dumps(line), flush=True)
 
 
@@ -599,17 +689,31 @@ def run_ours(args):
                                                   tuning["warps_per_cta"])),
                 "kernel": names[dom], "kernel_ms": kavg[dom], "kernels_ms": dict(zip(names, kavg)),
                 "lane_ops_per_launch": ops, "peak_source": f"{sms} SMs x 128 lanes x {asrc}"}
-    if args.workload == "c2":
+    alg_bytes = None
+    if world == 1 and args.workload == "c2":
+        alg_bytes = c2_launch_bytes(B)
+    elif world == 1 and args.workload == "c3":
+        alg_bytes = c3_launch_bytes(wl)
+    if alg_bytes is not None:
         peak, which = load_peaks()
-        hb = c2_launch_bytes(B) / kernel_s / 1e9
+        hb = alg_bytes / kernel_s / 1e9
         roofline["hbm"] = {"achieved": hb, "peak": peak, "unit": "GB/s", "frac": hb / peak, "peak_source": which,
-                           "bytes_per_step": c2_launch_bytes(B), "scope": "whole render step"}
+                           "bytes_per_step": alg_bytes, "scope": "whole render step",
+                           "bytes": "union of touched voxels (label 1 B + HU 2 B, the oracle's exact count) + "
+                                    "frames written + poses"}
 
-    # surrogate inference throughput at 512 envs (speed only: the cost of a
-    # forward pass does not depend on the weights)
+    # the learned surrogate: trained at the C4 size, then the C5 production
+    # step (surrogate + error gate + physics fallback + audit) beside
+    # all-physics on the same GPU
     surrogate = None
     if args.workload == "c2" and not args.no_surrogate:
+        # surrogate inference throughput at 512 envs (speed only: the cost
+        # of a forward pass does not depend on the weights)
         surrogate = surrogate_speed(sim, wl, 512, stream)
+    if args.workload == "c3" and world == 1 and not args.no_surrogate:
+        sim.close()
+        sim = None
+        surrogate = c5_surrogate_block(args, volumes=wl.volumes)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -634,7 +738,8 @@ def run_ours(args):
                 "gpu_launches": args.steps * (2 if two_grids else 1),
                 "plain": plain, "surrogate": surrogate, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -645,12 +750,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "paper", "surgery3d", "recon", "mixed"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "paper", "surgery3d", "recon", "mixed"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--train-pairs", type=int, default=200_000, help="surrogate training pairs (C4: 200k)")
+    ap.add_argument("--train-batch", type=int, default=256, help="surrogate training batch (C4: 256)")
+    ap.add_argument("--c5-steps", type=int, default=10, help="timed steps of the C5 production step")
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--gate-l1", type=float, default=0.05)
     ap.add_argument("--speckle", default="beam", choices=["beam", "anchored"],

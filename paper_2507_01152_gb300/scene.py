@@ -410,6 +410,24 @@ def workload_c3(B=512, steps=100, volumes=None):
     return Workload(f"c3_uneven_{B}env", volumes, c3_probes(), envs, poses, seed=0x5EED0003)
 
 
+def workload_c5(B=1024, steps=3, volumes=None):
+    """B envs over the four 512 x 512 x 256 volumes and three probes of C3,
+    grouped by probe (the first third linear 128 x 256, the next
+    curvilinear 192 x 384, the last curvilinear 256 x 512, so that the frames
+    of one probe type are contiguous in the frame layout); env b uses volume
+    b % 4; seeded random-walk poses over ``steps`` steps."""
+    specs = c3_specs()
+    if volumes is None:
+        volumes = [(s, *make_volume(s)) for s in specs]
+    probe_of = np.minimum(np.arange(B) * 3 // B, 2)
+    envs = np.stack([np.arange(B) % 4, probe_of], axis=1).astype(np.int32)
+    poses = np.empty((steps, B, 3, 4), np.float32)
+    for v in range(4):
+        idx = np.nonzero(envs[:, 0] == v)[0]
+        poses[:, idx] = random_walk_poses(specs[v], len(idx), steps, 3100 + v)
+    return Workload(f"c5_mixed_{B}env", volumes, c3_probes(), envs, poses, seed=0x5EED0005)
+
+
 def workload_paper_replica(B=100):
     """100 envs, linear 150 lines x 200 samples at 0.5 mm (200 x 150 image,
     App. C.1), on the 256^3 volume."""
