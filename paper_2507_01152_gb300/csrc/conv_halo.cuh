@@ -1,0 +1,212 @@
+// Stride-1 3x3 convolution forward for the surrogate's narrow layers, with
+// each tile's input staged once as a haloed box:
+//
+//   y[b,y,x,co] = act(bias[co] + sum_(ky,kx,ci) x[b, y+ky-1, x+kx-1, ci] w[co][ky][kx][ci])
+//
+// An output tile is 16 rows x 8 columns of one image (the 128 rows M of a
+// tcgen05 MMA).  Its input box, 18 x 10 pixels with the one-pixel halo, is
+// copied by tensor copies (TMA) once, as CIN / 8 planes of 16-byte pixels
+// (the copies' zero fill is the padding); the nine taps are then nine
+// shifted windows of that box, read by the MMAs through unswizzled K-major
+// descriptors: 8-row core matrices are the 8 pixels of one box row
+// (16 bytes apart), consecutive output rows one box row (160 bytes) apart,
+// channel planes one plane (2944 bytes, 128-byte aligned) apart.  The
+// tap-by-tap forms stage the box nine times over; this one moves it once,
+// so the narrow layers (32 or 64 output channels on the full- and
+// half-resolution grids) are no longer bound by the L2 -> shared-memory
+// traffic of the re-reads.
+//
+// The weights [9 taps][CIN / 8 planes][COUT rows][16 B] stay resident in
+// shared memory for the whole persistent CTA.  Roles: warp 0 (one thread)
+// issues the box copies of up to S tiles ahead; X issuing warps each own
+// every X-th tile of the CTA (one elected thread issues its 9 CIN / 16 MMAs
+// of 128 x COUT x 16 into one half of its double-buffered TMEM
+// accumulator); four epilogue warps add the bias, apply the ReLU and store
+// BF16 pixels.  Every wait is bounded; a wait that runs out raises the
+// shared abort flag, the CTA drains its copies and MMAs, frees its TMEM and
+// reports kErrWaitTimeout.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "umma_gemm.cuh"
+
+namespace ussim {
+namespace umma {
+
+template <int CIN, int COUT>
+struct HaloCfg {
+  static constexpr int TY = 16, TX = 8;                        // output tile: 16 rows x 8 columns
+  static constexpr int BY = TY + 2, BX = TX + 2;               // staged box with the halo
+  static constexpr int NCH = CIN / 8;                          // 16-byte channel planes
+  static constexpr uint32_t BOX = (uint32_t)BY * BX * 16;      // bytes of one plane's copy: 2880
+  static constexpr uint32_t PLANE = (BOX + 127u) / 128u * 128u;   // plane stride, 128-byte aligned copies
+  static constexpr uint32_t STAGE = NCH * PLANE;
+  static constexpr uint32_t WBYTES = 9u * NCH * COUT * 16;
+  static constexpr int X = COUT <= 32 ? 8 : 4;                 // issuing warps: 2 X COUT TMEM columns = 512
+  // stages: a multiple of X, so that stage s always serves issuer s mod X
+  // and each issuer sees every phase of its stages' barriers in order
+  static constexpr int S0 = (int)((225u * 1024u - WBYTES) / STAGE);
+  static constexpr int S = (S0 > 8 ? 8 : S0) / X * X;
+  static constexpr int kEpi = 4;
+  static constexpr int THREADS = 32 * (1 + X + kEpi);
+  static constexpr uint32_t SMEM = WBYTES + S * STAGE + 128;   // + alignment slack
+  static_assert(CIN % 16 == 0 && (COUT == 32 || COUT == 64), "halo conv shapes");
+  static_assert(S >= X, "stages do not fit");
+  static_assert(2 * X * COUT <= 512, "accumulators exceed TMEM");
+};
+
+struct HaloArgs {
+  const __nv_bfloat16* w;   // [COUT][3][3][CIN]
+  const float* bias;        // [COUT]
+  __nv_bfloat16* y;         // output view: pixel p at y + p * y_cs + y_co
+  int y_cs, y_co, relu;
+  int B, H, W, tiles_y, tiles_x, n_tiles;
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
+    conv3x3_halo_kernel(const __grid_constant__ CUtensorMap tx, const HaloArgs a, unsigned* err) {
+  using C = HaloCfg<CIN, COUT>;
+  constexpr int X = C::X, S = C::S, NCH = C::NCH;
+  constexpr uint32_t IDESC = idesc_bf16_f32(kBM, COUT);
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  uint8_t* wsm = smem;                          // resident weights
+  uint8_t* box = smem + C::WBYTES;              // S staged boxes
+  __shared__ uint64_t full[S], empty[S], tfull[X][2], tempty[X][2], done[X];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int w = 0; w < X; ++w) {
+      for (int q = 0; q < 2; ++q) {
+        mbar_init(&tfull[w][q], 1);
+        mbar_init(&tempty[w][q], 32 * C::kEpi);
+      }
+      mbar_init(&done[w], 1);
+    }
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  // weights: w[co][tap][ci] -> plane-major [tap][ci / 8][co][16 B]
+  for (int i = tid; i < 9 * NCH * COUT; i += blockDim.x) {
+    const int co = i % COUT, r = i / COUT, ch = r % NCH, tap = r / NCH;
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w + ((size_t)co * 9 + tap) * CIN + ch * 8));
+    *reinterpret_cast<uint4*>(wsm + ((size_t)(tap * NCH + ch) * COUT + co) * 16) = v;
+  }
+  fence_proxy_async();   // generic-proxy stores, read by the tensor core
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const int n_local = a.n_tiles > (int)blockIdx.x ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  auto tile_of = [&](int g, int& b, int& y0, int& x0) {
+    const int t = (int)blockIdx.x + g * (int)gridDim.x;
+    const int per = a.tiles_y * a.tiles_x;
+    b = t / per;
+    const int r = t - b * per, ty = r / a.tiles_x;
+    y0 = ty * C::TY;
+    x0 = (r - ty * a.tiles_x) * C::TX;
+  };
+
+  if (warp == 0) {
+    // ----------------------------------------------------------- producer
+    if (lane == 0) {
+      int g = 0;
+      for (; g < n_local && !abort_flag; ++g) {
+        const int s = g % S;
+        if (g >= S && !wait_or_abort(&empty[s], (uint32_t)((g / S - 1) & 1), &abort_flag, err)) break;
+        int b, y0, x0;
+        tile_of(g, b, y0, x0);
+        mbar_arrive_expect_tx(&full[s], NCH * C::BOX);
+        const uint32_t dst = smem_u32(box + (size_t)s * C::STAGE), bar = smem_u32(&full[s]);
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) tma_load_4d(dst + ch * C::PLANE, &tx, ch * 8, x0 - 1, y0 - 1, b, bar);
+      }
+      // every issued copy must land before the CTA may exit
+      for (int q = g > S ? g - S : 0; q < g; ++q)
+        if (!mbar_wait(&full[q % S], (uint32_t)((q / S) & 1))) atomicOr(err, kErrWaitTimeout);
+    }
+    __syncwarp();
+  } else if (warp <= X) {
+    // ---------------------------------------------------------- MMA issue
+    const int w = warp - 1;
+    if (lane == 0) {
+      const uint32_t wbase = smem_u32(wsm);
+      for (int g = w, j = 0; g < n_local && !abort_flag; g += X, ++j) {
+        const int s = g % S, q = j & 1;
+        if (j >= 2 && !wait_or_abort(&tempty[w][q], (uint32_t)((j / 2 - 1) & 1), &abort_flag, err)) break;
+        if (!wait_or_abort(&full[s], (uint32_t)((g / S) & 1), &abort_flag, err)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(w * 2 + q) * COUT;
+        const uint32_t sbox = smem_u32(box + (size_t)s * C::STAGE);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap - 3 * ky;
+#pragma unroll
+          for (int kk = 0; kk < NCH / 2; ++kk) {
+            const uint64_t ad = smem_desc_kmajor(sbox + (uint32_t)(2 * kk) * C::PLANE + (uint32_t)(ky * C::BX + kx) * 16u,
+                                                 C::PLANE, (uint32_t)C::BX * 16u);
+            const uint64_t bd = smem_desc_kmajor(wbase + (uint32_t)((tap * NCH + 2 * kk) * COUT) * 16u,
+                                                 (uint32_t)COUT * 16u, 128u);
+            mma_bf16(acc, ad, bd, IDESC, (tap > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(&empty[s]);
+        mma_commit(&tfull[w][q]);
+      }
+      mma_commit(&done[w]);
+      if (!mbar_wait(&done[w], 0)) atomicOr(err, kErrWaitTimeout);
+    }
+    __syncwarp();
+  } else {
+    // ----------------------------------------------------------- epilogue
+    const int qd = warp & 3;               // TMEM lane quarter this warp may read
+    const int m = qd * 32 + lane;          // tile row: pixel (m / 8, m % 8)
+    for (int g = 0, ok = 1; g < n_local && ok; ++g) {
+      const int w = g % X, j = g / X, q = j & 1;
+      if (!wait_or_abort(&tfull[w][q], (uint32_t)((j / 2) & 1), &abort_flag, err)) break;
+      tc_fence_after();
+      int b, y0, x0;
+      tile_of(g, b, y0, x0);
+      const int yy = y0 + (m >> 3), xx = x0 + (m & 7);
+      const bool valid = yy < a.H && xx < a.W;
+      __nv_bfloat16* dst = a.y + ((size_t)((size_t)b * a.H + yy) * a.W + xx) * a.y_cs + a.y_co;
+      const uint32_t acc = tmem + (uint32_t)(w * 2 + q) * COUT + ((uint32_t)(qd * 32) << 16);
+#pragma unroll
+      for (int c = 0; c < COUT; c += 16) {
+        float v[16];
+        tmem_ld16(acc + (uint32_t)c, v);
+        __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float t = v[i] + __ldg(&a.bias[c + i]);
+          o[i] = __float2bfloat16_rn(a.relu ? fmaxf(t, 0.f) : t);
+        }
+        if (valid) {
+          uint4* d4 = reinterpret_cast<uint4*>(dst + c);
+          d4[0] = reinterpret_cast<const uint4*>(o)[0];
+          d4[1] = reinterpret_cast<const uint4*>(o)[1];
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[w][q]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+}  // namespace umma
+}  // namespace ussim

@@ -16,6 +16,7 @@
 // reduction of split-K partial sums (wgrad).
 #include <cuda_bf16.h>
 
+#include "conv_halo.cuh"
 #include "ussim_surrogate.h"
 #include "umma_tma.cuh"
 
@@ -662,6 +663,55 @@ cudaError_t gemm_bn(int bn, const Ld& ld, const Ep& ep, int M, int N, int K, uns
   }
 }
 
+// Stride-1 forward of the narrow layers through the haloed-box kernel
+// (conv_halo.cuh): CIN, COUT in {32, 64}.  False (e untouched) if the shape
+// has no instantiation or the tensor map cannot describe the input.
+template <int CIN, int COUT>
+bool halo_fwd(cudaError_t& e, View x, const bf16* w, const float* bias, OutView y, int relu, int B, int H, int W,
+              unsigned* err, cudaStream_t st) {
+  using Cf = HaloCfg<CIN, COUT>;
+  CUtensorMap m;
+  const uint64_t pitch = (uint64_t)x.cs * 2;
+  const uint64_t d[4] = {(uint64_t)CIN, (uint64_t)W, (uint64_t)H, (uint64_t)B};
+  const uint64_t strd[3] = {pitch, pitch * W, pitch * W * H};
+  const uint32_t bx[4] = {8, (uint32_t)Cf::BX, (uint32_t)Cf::BY, 1}, es[4] = {1, 1, 1, 1};
+  if (!tma::encode_bf16(&m, x.p + x.co, 4, d, strd, bx, es, 0)) return false;
+  HaloArgs a;
+  a.w = w;
+  a.bias = bias;
+  a.y = y.p;
+  a.y_cs = y.cs;
+  a.y_co = y.co;
+  a.relu = relu;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.tiles_y = (H + Cf::TY - 1) / Cf::TY;
+  a.tiles_x = (W + Cf::TX - 1) / Cf::TX;
+  const long long nt = (long long)B * a.tiles_y * a.tiles_x;
+  if (nt > (1ll << 30)) return false;
+  a.n_tiles = (int)nt;
+  auto kern = conv3x3_halo_kernel<CIN, COUT>;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM)) != cudaSuccess)
+    return true;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<long long>(nt, sms);
+  kern<<<grid, Cf::THREADS, Cf::SMEM, st>>>(m, a, err);
+  e = cudaGetLastError();
+  return true;
+}
+
+bool halo_fwd_any(cudaError_t& e, View x, int Cin, int Cout, const bf16* w, const float* bias, OutView y, int relu,
+                  int B, int H, int W, unsigned* err, cudaStream_t st) {
+  if (Cin == 32 && Cout == 32) return halo_fwd<32, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
+  if (Cin == 64 && Cout == 32) return halo_fwd<64, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
+  if (Cin == 32 && Cout == 64) return halo_fwd<32, 64>(e, x, w, bias, y, relu, B, H, W, err, st);
+  if (Cin == 64 && Cout == 64) return halo_fwd<64, 64>(e, x, w, bias, y, relu, B, H, W, err, st);
+  return false;
+}
+
 int pick_bn(int N) {
   return (N % 256 == 0) ? 256 : (N % 128 == 0) ? 128 : (N % 64 == 0) ? 64 : (N % 32 == 0) ? 32 : (N % 16 == 0) ? 16 : 0;
 }
@@ -707,6 +757,9 @@ us_status us_conv3x3_fwd(const uint16_t* x, int32_t x_cs, int32_t x_co, const ui
   const int M = B * out.H * out.W, K = 9 * Cin, bn = pick_bn(Cout);
   BiasActStore ep{{(bf16*)y, y_cs, y_co}, bias, relu};
   cudaError_t e;
+  if (stride == 1 && halo_fwd_any(e, {(const bf16*)x, x_cs, x_co}, Cin, Cout, (const bf16*)w, bias,
+                                  {(bf16*)y, y_cs, y_co}, relu, B, H, W, err, (cudaStream_t)stream))
+    return to_status(e);
   if (conv_tma(e, {(const bf16*)x, x_cs, x_co}, Cin, B, H, W, out.H, out.W, stride, 1, (const bf16*)w, K, Cout, bn, ep,
                M, err, (cudaStream_t)stream))
     return to_status(e);
