@@ -173,6 +173,40 @@ US_API us_status us_surr_predict_error(us_surr* s, int32_t B, float* out, void* 
  * ridge < 0, singular system), US_ERR_CUDA. */
 US_API us_status us_surr_fit_error_head(us_surr* s, const float* feat, const float* target, int32_t n, float ridge);
 
+/* ---- GAN term -----------------------------------------------------------
+ * App. B.2 trains the learned simulator with an L1 term and a GAN term,
+ * weights 1 and 0.01.  The discriminator (the library's reading of
+ * pix2pix's patch classifier) sees the input slice and a frame as 16
+ * channels (the 8 slice channels, the frame, 7 zeros) through three 3x3
+ * stride-2 convolutions with ReLU (16 -> cd -> 2 cd -> 2 cd) and a 1x1 head
+ * to one logit per 8 x 8 patch; BCE on logits averaged over every patch.
+ * Parameters (FP32, this order): d1 w [cd][3][3][16], d1 b [cd], d2 w
+ * [2cd][3][3][cd], d2 b, d3 w [2cd][3][3][2cd], d3 b, head w [2cd], head b [1].
+ * With the term enabled, us_surr_train_step minimises
+ *   L1 + (1 - SSIM) + gan_weight * BCE(D(x, G(x)), 1)
+ * over the generator (the discriminator held fixed; loss_out[0] includes
+ * the term), and us_surr_gan_disc_step minimises
+ *   (BCE(D(x, real), 1) + BCE(D(x, G(x)), 0)) / 2
+ * over the discriminator, the fake frames being those of the last forward
+ * pass (call it after the train step of the same x).  Requires height and
+ * width multiples of 8. */
+/* parameter count of a discriminator of width cd (16 .. 128, multiple of 16), -1 otherwise */
+US_API int64_t us_surr_gan_num_params(int32_t cd);
+/* enable the GAN term: init HOST [us_surr_gan_num_params(cd)] (copied),
+ * gan_weight >= 0 (the paper's 0.01), lr > 0 (the discriminator's Adam step;
+ * its betas and eps are the network's).  Allocates the discriminator's
+ * buffers for max_batch frames (synchronous).  Errors: US_ERR_INVALID_ARG
+ * (bad arguments, already enabled), US_ERR_OOM, US_ERR_CUDA. */
+US_API us_status us_surr_gan_enable(us_surr* s, int32_t cd, const float* init, float gan_weight, float lr);
+/* one discriminator step on (x, real) and the last forward's frames: loss_out
+ * DEVICE [3] = (loss, real term, fake term); update = 1 applies Adam.
+ * Errors: US_ERR_INVALID_ARG (not enabled, bad arguments), US_ERR_CUDA. */
+US_API us_status us_surr_gan_disc_step(us_surr* s, const uint16_t* x, const float* real, int32_t B, float* loss_out,
+                                       int32_t update, void* stream);
+/* discriminator parameters and the gradients of its last step, HOST
+ * [us_surr_gan_num_params(cd)], parameter layout; either may be NULL (synchronous) */
+US_API us_status us_surr_gan_get(us_surr* s, float* params, float* grads);
+
 /* parameters / gradients of the last train step, HOST, parameter layout (synchronous) */
 US_API us_status us_surr_get_params(const us_surr* s, float* host_out);
 US_API us_status us_surr_get_grads(us_surr* s, float* host_out);

@@ -218,3 +218,99 @@ def predict_error(coef, feat):
     import numpy as np
     f = np.asarray(feat, np.float64)
     return f @ coef[:-1] + coef[-1]
+
+
+# ------------------------------------------------------------- GAN term
+# App. B.2 (learning-based approach) trains its pix2pix network with an L1
+# term and a GAN term, weights 1 and 0.01.  READING (the discriminator is
+# not described; pix2pix's is a conditional patch classifier): the
+# discriminator sees the input slice and a frame, as 16 channels (the 8
+# input channels, the frame, 7 zeros), through three 3x3 stride-2
+# convolutions with ReLU (16 -> cd -> 2 cd -> 2 cd channels; ReLU where
+# pix2pix has a leaky one, the activation the operators provide) and a 1x1
+# head to one logit per patch of 8 x 8 pixels.  Losses, with BCE on logits
+# averaged over every patch of every frame:
+#   generator:     L1 + (1 - SSIM) + gan_weight * BCE(D(x, G(x)), 1)
+#   discriminator: (BCE(D(x, y), 1) + BCE(D(x, G(x)), 0)) / 2
+GAN_WEIGHT = 0.01
+D_IN = 16
+
+
+def disc_layer_specs(cd: int):
+    return [("d1", "conv", D_IN, cd, 2), ("d2", "conv", cd, 2 * cd, 2), ("d3", "conv", 2 * cd, 2 * cd, 2),
+            ("dhead", "head", 2 * cd, 1, 1)]
+
+
+def disc_param_shapes(cd: int):
+    out = []
+    for name, kind, cin, cout, s in disc_layer_specs(cd):
+        if kind == "conv":
+            out += [(name + ".w", (cout, 3, 3, cin)), (name + ".b", (cout,))]
+        else:
+            out += [(name + ".w", (cin,)), (name + ".b", (1,))]
+    return out
+
+
+def disc_n_params(cd: int) -> int:
+    return sum(math.prod(s) for _, s in disc_param_shapes(cd))
+
+
+def disc_unflatten(flat, cd: int):
+    flat = torch.as_tensor(flat, dtype=DT)
+    P, o = {}, 0
+    for name, shp in disc_param_shapes(cd):
+        n = math.prod(shp)
+        P[name] = flat[o:o + n].reshape(shp)
+        o += n
+    assert o == flat.numel()
+    return P
+
+
+def disc_input(x, y):
+    """[B][H][W][16]: the 8 input channels, the frame, 7 zeros"""
+    B, H, W, _ = x.shape
+    z = torch.zeros((B, H, W, D_IN - IN_CH - 1), dtype=x.dtype)
+    return torch.cat([x[..., :IN_CH], y[..., None], z], dim=-1)
+
+
+def disc_forward(Pd, x, y, act=None):
+    """patch logits [B][H/8][W/8] of the discriminator on (slice x, frame y)"""
+    A = act if act is not None else (lambda t: t)
+    h = A(disc_input(x, y))
+    for name in ("d1", "d2", "d3"):
+        h = A(conv3x3(h, Pd[name + ".w"], Pd[name + ".b"], 2))
+    return (h * Pd["dhead.w"]).sum(-1) + Pd["dhead.b"]
+
+
+def bce_logits(z, t):
+    """mean over every element of the binary cross-entropy of logits z
+    against target t in {0, 1}: log(1 + e^z) - t z"""
+    return (F.softplus(z) - t * z).mean()
+
+
+def gan_generator_loss(P, Pd, x, target, c: int, cd: int, gan_weight=GAN_WEIGHT):
+    pred = forward(P, x, c)
+    return loss(pred, target) + gan_weight * bce_logits(disc_forward(Pd, x, pred), 1.0), pred
+
+
+def gan_generator_grads(flat, dflat, x, target, c: int, cd: int, gan_weight=GAN_WEIGHT):
+    """(loss, d loss / d generator params) of the generator's combined loss,
+    the discriminator held fixed"""
+    p = torch.as_tensor(flat, dtype=DT).clone().requires_grad_(True)
+    Pd = disc_unflatten(torch.as_tensor(dflat, dtype=DT), cd)
+    L, _ = gan_generator_loss(unflatten(p, c), Pd, torch.as_tensor(x, dtype=DT), torch.as_tensor(target, dtype=DT),
+                              c, cd, gan_weight)
+    L.backward()
+    return float(L.detach()), p.grad.detach().clone()
+
+
+def disc_loss_and_grads(dflat, x, real, fake, cd: int):
+    """(loss, d loss / d discriminator params) of
+    (BCE(D(x, real), 1) + BCE(D(x, fake), 0)) / 2"""
+    q = torch.as_tensor(dflat, dtype=DT).clone().requires_grad_(True)
+    Pd = disc_unflatten(q, cd)
+    x = torch.as_tensor(x, dtype=DT)
+    L = 0.5 * (bce_logits(disc_forward(Pd, x, torch.as_tensor(real, dtype=DT)), 1.0) +
+               bce_logits(disc_forward(Pd, x, torch.as_tensor(fake, dtype=DT)), 0.0))
+    L.backward()
+    return float(L.detach()), q.grad.detach().clone()

@@ -21,8 +21,8 @@
 // issues the box copies of up to S tiles ahead; X issuing warps each own
 // every X-th tile of the CTA (one elected thread issues its 9 CIN / 16 MMAs
 // of 128 x COUT x 16 into one half of its double-buffered TMEM
-// accumulator); four epilogue warps add the bias, apply the ReLU and store
-// BF16 pixels.  Every wait is bounded; a wait that runs out raises the
+// accumulator); two groups of four epilogue warps, taking alternate tiles,
+// add the bias, apply the ReLU and store BF16 pixels.  Every wait is bounded; a wait that runs out raises the
 // shared abort flag, the CTA drains its copies and MMAs, frees its TMEM and
 // reports kErrWaitTimeout.
 #pragma once
@@ -39,19 +39,24 @@ struct HaloCfg {
   static constexpr int TY = 16, TX = 8;                        // output tile: 16 rows x 8 columns
   static constexpr int BY = TY + 2, BX = TX + 2;               // staged box with the halo
   static constexpr int NCH = CIN / 8;                          // 16-byte channel planes
+  // 8 input channels: one MMA of K = 16 takes two taps of 8 channels (the
+  // tap pair's pixel offset is the descriptor's K stride); a tenth, zero
+  // tap completes the last pair
+  static constexpr bool PAIRED = CIN == 8;
+  static constexpr int NTAPW = PAIRED ? 10 : 9;                // taps in the weight layout
   static constexpr uint32_t BOX = (uint32_t)BY * BX * 16;      // bytes of one plane's copy: 2880
   static constexpr uint32_t PLANE = (BOX + 127u) / 128u * 128u;   // plane stride, 128-byte aligned copies
   static constexpr uint32_t STAGE = NCH * PLANE;
-  static constexpr uint32_t WBYTES = 9u * NCH * COUT * 16;
+  static constexpr uint32_t WBYTES = (uint32_t)NTAPW * NCH * COUT * 16;
   static constexpr int X = COUT <= 32 ? 8 : 4;                 // issuing warps: 2 X COUT TMEM columns = 512
   // stages: a multiple of X, so that stage s always serves issuer s mod X
   // and each issuer sees every phase of its stages' barriers in order
   static constexpr int S0 = (int)((225u * 1024u - WBYTES) / STAGE);
   static constexpr int S = (S0 > 8 ? 8 : S0) / X * X;
-  static constexpr int kEpi = 4;
-  static constexpr int THREADS = 32 * (1 + X + kEpi);
+  static constexpr int kEpiGroups = 2;                          // epilogue groups of 4 warps, alternate tiles
+  static constexpr int THREADS = 32 * (1 + X + 4 * kEpiGroups);
   static constexpr uint32_t SMEM = WBYTES + S * STAGE + 128;   // + alignment slack
-  static_assert(CIN % 16 == 0 && (COUT == 32 || COUT == 64), "halo conv shapes");
+  static_assert((CIN == 8 || CIN % 16 == 0) && (COUT == 32 || COUT == 64), "halo conv shapes");
   static_assert(S >= X, "stages do not fit");
   static_assert(2 * X * COUT <= 512, "accumulators exceed TMEM");
 };
@@ -91,18 +96,27 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
     for (int w = 0; w < X; ++w) {
       for (int q = 0; q < 2; ++q) {
         mbar_init(&tfull[w][q], 1);
-        mbar_init(&tempty[w][q], 32 * C::kEpi);
+        mbar_init(&tempty[w][q], 128);   // the four warps of the epilogue group that takes the tile
       }
       mbar_init(&done[w], 1);
     }
     abort_flag = 0;
     mbar_init_fence();
   }
-  // weights: w[co][tap][ci] -> plane-major [tap][ci / 8][co][16 B]
-  for (int i = tid; i < 9 * NCH * COUT; i += blockDim.x) {
+  // weights: w[co][tap][ci] -> plane-major [tap][ci / 8][co][16 B] (the
+  // paired layout's tenth tap zero)
+  for (int i = tid; i < C::NTAPW * NCH * COUT; i += blockDim.x) {
     const int co = i % COUT, r = i / COUT, ch = r % NCH, tap = r / NCH;
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w + ((size_t)co * 9 + tap) * CIN + ch * 8));
+    const uint4 v = tap < 9 ? __ldg(reinterpret_cast<const uint4*>(a.w + ((size_t)co * 9 + tap) * CIN + ch * 8))
+                            : make_uint4(0u, 0u, 0u, 0u);
     *reinterpret_cast<uint4*>(wsm + ((size_t)(tap * NCH + ch) * COUT + co) * 16) = v;
+  }
+  // the pad after each plane's copy reads as zero (the paired layout's last
+  // pair reaches one pixel into it, against zero weights)
+  constexpr int PADV = (int)(C::PLANE - C::BOX) / 16;
+  for (int i = tid; i < S * NCH * PADV; i += blockDim.x) {
+    const int pl = i / PADV, k = i - pl * PADV;
+    *reinterpret_cast<uint4*>(box + (size_t)pl * C::PLANE + C::BOX + (size_t)k * 16) = make_uint4(0u, 0u, 0u, 0u);
   }
   fence_proxy_async();   // generic-proxy stores, read by the tensor core
   tc_fence_before();
@@ -150,8 +164,19 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
         tc_fence_after();
         const uint32_t acc = tmem + (uint32_t)(w * 2 + q) * COUT;
         const uint32_t sbox = smem_u32(box + (size_t)s * C::STAGE);
+        if constexpr (C::PAIRED) {
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
+          for (int j = 0; j < 5; ++j) {
+            const int t0 = 2 * j, t1 = 2 * j + 1;
+            const int o0 = (t0 / 3) * C::BX + t0 % 3, o1 = t1 < 9 ? (t1 / 3) * C::BX + t1 % 3 : o0 + 1;
+            const uint64_t ad = smem_desc_kmajor(sbox + (uint32_t)o0 * 16u, (uint32_t)(o1 - o0) * 16u,
+                                                 (uint32_t)C::BX * 16u);
+            const uint64_t bd = smem_desc_kmajor(wbase + (uint32_t)(t0 * COUT) * 16u, (uint32_t)COUT * 16u, 128u);
+            mma_bf16(acc, ad, bd, IDESC, j > 0 ? 1u : 0u);
+          }
+        }
+#pragma unroll
+        for (int tap = 0; tap < (C::PAIRED ? 0 : 9); ++tap) {
           const int ky = tap / 3, kx = tap - 3 * ky;
 #pragma unroll
           for (int kk = 0; kk < NCH / 2; ++kk) {
@@ -171,9 +196,13 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
     __syncwarp();
   } else {
     // ----------------------------------------------------------- epilogue
+    // two groups of four warps take alternate tiles; within a group, warp
+    // (index mod 4) reads its TMEM lane quarter, all of a tile's columns in
+    // flight before one wait
+    const int grp = (warp - 1 - X) >> 2;
     const int qd = warp & 3;               // TMEM lane quarter this warp may read
     const int m = qd * 32 + lane;          // tile row: pixel (m / 8, m % 8)
-    for (int g = 0, ok = 1; g < n_local && ok; ++g) {
+    for (int g = grp; g < n_local; g += C::kEpiGroups) {
       const int w = g % X, j = g / X, q = j & 1;
       if (!wait_or_abort(&tfull[w][q], (uint32_t)((j / 2) & 1), &abort_flag, err)) break;
       tc_fence_after();
@@ -183,24 +212,28 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
       const bool valid = yy < a.H && xx < a.W;
       __nv_bfloat16* dst = a.y + ((size_t)((size_t)b * a.H + yy) * a.W + xx) * a.y_cs + a.y_co;
       const uint32_t acc = tmem + (uint32_t)(w * 2 + q) * COUT + ((uint32_t)(qd * 32) << 16);
+      // 32 columns in flight per wait
 #pragma unroll
-      for (int c = 0; c < COUT; c += 16) {
-        float v[16];
-        tmem_ld16(acc + (uint32_t)c, v);
-        __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float t = v[i] + __ldg(&a.bias[c + i]);
-          o[i] = __float2bfloat16_rn(a.relu ? fmaxf(t, 0.f) : t);
+      for (int c0 = 0; c0 < COUT; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld16_nowait(acc + (uint32_t)c0, r);
+        tmem_ld16_nowait(acc + (uint32_t)c0 + 16u, r + 16);
+        tmem_wait_ld();
+        if (c0 + 32 >= COUT) {
+          tc_fence_before();
+          mbar_arrive(&tempty[w][q]);      // the accumulator is free once it is in registers
         }
-        if (valid) {
-          uint4* d4 = reinterpret_cast<uint4*>(dst + c);
-          d4[0] = reinterpret_cast<const uint4*>(o)[0];
-          d4[1] = reinterpret_cast<const uint4*>(o)[1];
+#pragma unroll
+        for (int c = 0; c < 32; c += 8) {
+          __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float t = __uint_as_float(r[c + i]) + __ldg(&a.bias[c0 + c + i]);
+            o[i] = __float2bfloat16_rn(a.relu ? fmaxf(t, 0.f) : t);
+          }
+          if (valid) *reinterpret_cast<uint4*>(dst + c0 + c) = *reinterpret_cast<const uint4*>(o);
         }
       }
-      tc_fence_before();
-      mbar_arrive(&tempty[w][q]);
     }
   }
   tc_fence_before();

@@ -38,8 +38,13 @@ namespace ussim {
 // KC = 0: any K, taps read from shared memory.  Same tap order as the plain
 // kernel.  Chunk c's results are written back only after chunk c + 1 has
 // been computed, so every read sees unfiltered data (K <= 32).
+// rmask bit i: some reflection impulse of samples 32 i .. 32 i + 31 is not
+// zero.  The impulses are >= 0, so an output chunk whose window (chunks
+// i - 1 .. i + 1, K <= 32) holds none is exactly +0, as the full sum of
+// zero taps would be: the warp skips its reflection taps there.
 template <int KC>
-__device__ __forceinline__ void axial_psf_rows(float* pt, float* pr, int NS, const float* w, int K, int lane) {
+__device__ __forceinline__ void axial_psf_rows(float* pt, float* pr, int NS, const float* w, int K, int lane,
+                                               unsigned rmask) {
   float prev_t = 0.f, prev_r = 0.f;
   int prev_s = -1;
   const int taps = 2 * K + 1;
@@ -47,22 +52,27 @@ __device__ __forceinline__ void axial_psf_rows(float* pt, float* pr, int NS, con
 #pragma unroll
   for (int k = 0; k < (KC > 0 ? 2 * KC + 1 : 0); ++k) wr[k] = w[k];
   for (int c = 0; c < NS; c += 32) {
-    const int s = c + lane;
+    const int s = c + lane, ci = c >> 5;
+    const bool refl = ((ci == 0 ? rmask << 1 : rmask >> (ci - 1)) & 7u) != 0;   // warp-uniform
     float acc_t = 0.f, acc_r = 0.f;
     if (s < NS) {
       const float* qt = pt + s;
       const float* qr = pr + s;
       if constexpr (KC > 0) {
+        if (refl) {
 #pragma unroll
-        for (int k = 0; k < 2 * KC + 1; ++k) {
-          acc_t = fmaf(wr[k], qt[k], acc_t);
-          acc_r = fmaf(wr[k], qr[k], acc_r);
+          for (int k = 0; k < 2 * KC + 1; ++k) {
+            acc_t = fmaf(wr[k], qt[k], acc_t);
+            acc_r = fmaf(wr[k], qr[k], acc_r);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 2 * KC + 1; ++k) acc_t = fmaf(wr[k], qt[k], acc_t);
         }
       } else {
-        for (int k = 0; k < taps; ++k) {
-          acc_t = fmaf(w[k], qt[k], acc_t);
-          acc_r = fmaf(w[k], qr[k], acc_r);
-        }
+        for (int k = 0; k < taps; ++k) acc_t = fmaf(w[k], qt[k], acc_t);
+        if (refl)
+          for (int k = 0; k < taps; ++k) acc_r = fmaf(w[k], qr[k], acc_r);
       }
     }
     __syncwarp();
@@ -82,17 +92,18 @@ __device__ __forceinline__ void axial_psf_rows(float* pt, float* pr, int NS, con
   __syncwarp();
 }
 
-__device__ __forceinline__ void axial_psf_any(float* pt, float* pr, int NS, const float* w, int K, int lane) {
+__device__ __forceinline__ void axial_psf_any(float* pt, float* pr, int NS, const float* w, int K, int lane,
+                                              unsigned rmask) {
   switch (K) {
-    case 1: axial_psf_rows<1>(pt, pr, NS, w, K, lane); break;
-    case 2: axial_psf_rows<2>(pt, pr, NS, w, K, lane); break;
-    case 3: axial_psf_rows<3>(pt, pr, NS, w, K, lane); break;
-    case 4: axial_psf_rows<4>(pt, pr, NS, w, K, lane); break;
-    case 5: axial_psf_rows<5>(pt, pr, NS, w, K, lane); break;
-    case 6: axial_psf_rows<6>(pt, pr, NS, w, K, lane); break;
-    case 7: axial_psf_rows<7>(pt, pr, NS, w, K, lane); break;
-    case 8: axial_psf_rows<8>(pt, pr, NS, w, K, lane); break;
-    default: axial_psf_rows<0>(pt, pr, NS, w, K, lane); break;
+    case 1: axial_psf_rows<1>(pt, pr, NS, w, K, lane, rmask); break;
+    case 2: axial_psf_rows<2>(pt, pr, NS, w, K, lane, rmask); break;
+    case 3: axial_psf_rows<3>(pt, pr, NS, w, K, lane, rmask); break;
+    case 4: axial_psf_rows<4>(pt, pr, NS, w, K, lane, rmask); break;
+    case 5: axial_psf_rows<5>(pt, pr, NS, w, K, lane, rmask); break;
+    case 6: axial_psf_rows<6>(pt, pr, NS, w, K, lane, rmask); break;
+    case 7: axial_psf_rows<7>(pt, pr, NS, w, K, lane, rmask); break;
+    case 8: axial_psf_rows<8>(pt, pr, NS, w, K, lane, rmask); break;
+    default: axial_psf_rows<0>(pt, pr, NS, w, K, lane, rmask); break;
   }
 }
 
@@ -314,15 +325,18 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
       beam_point(P, ln, s, x, z);
       return sample_position(cx.M, x, z);
     };
+    unsigned rmask = 0;   // this lane's 32-sample chunks with a non-zero reflection impulse
     scanline_model<ANCHORED>(p, P, tis, cx.pair, cx.it.b, l, lane, labf, own, zf,
                              [&](int s, float r, float t, float e) {
                                row[s] = t;
                                rrow[KA + s] = r;
                                erow[s] = e;
+                               if (r != 0.f) rmask |= 1u << (s >> 5);
                              },
                              posf, cx.it.vol);
+    rmask = __reduce_or_sync(kFull, rmask);
     __syncwarp();
-    axial_psf_any(prow, rrow, NS, wax, KA, lane);
+    axial_psf_any(prow, rrow, NS, wax, KA, lane, rmask);
     float2* dst = a.beam + cx.it.beam_off + (long long)l * NS;
     for (int s = lane; s < NS; s += 32) dst[s] = make_float2(rrow[KA + s], row[s]);
   }

@@ -664,7 +664,7 @@ cudaError_t gemm_bn(int bn, const Ld& ld, const Ep& ep, int M, int N, int K, uns
 }
 
 // Stride-1 forward of the narrow layers through the haloed-box kernel
-// (conv_halo.cuh): CIN, COUT in {32, 64}.  False (e untouched) if the shape
+// (conv_halo.cuh): CIN, COUT in {32, 64}, and the first layer's 8 -> 32.  False (e untouched) if the shape
 // has no instantiation or the tensor map cannot describe the input.
 template <int CIN, int COUT>
 bool halo_fwd(cudaError_t& e, View x, const bf16* w, const float* bias, OutView y, int relu, int B, int H, int W,
@@ -705,6 +705,7 @@ bool halo_fwd(cudaError_t& e, View x, const bf16* w, const float* bias, OutView 
 
 bool halo_fwd_any(cudaError_t& e, View x, int Cin, int Cout, const bf16* w, const float* bias, OutView y, int relu,
                   int B, int H, int W, unsigned* err, cudaStream_t st) {
+  if (Cin == 8 && Cout == 32) return halo_fwd<8, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 32 && Cout == 32) return halo_fwd<32, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 64 && Cout == 32) return halo_fwd<64, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 32 && Cout == 64) return halo_fwd<32, 64>(e, x, w, bias, y, relu, B, H, W, err, st);

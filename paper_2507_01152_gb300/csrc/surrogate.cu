@@ -41,13 +41,23 @@ struct LayerDesc {
 
 // ------------------------------------------------------------------ kernels
 
-// out[p] = sigmoid(sum_c f[p][c] w[c] + b)
+// out[p] = sigmoid(sum_c f[p][c] w[c] + b); a pixel's channels are read
+// as 16-byte vectors (C a multiple of 8, rows 16-byte aligned), summed in
+// channel order
 __global__ void head_fwd(const bf16* f, int C, const float* w, const float* b, float* out, long long P) {
+  __shared__ float sw[256];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sw[i] = w[i];
+  __syncthreads();
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const bf16* fp = f + p * C;
+  const uint4* fp = reinterpret_cast<const uint4*>(f + p * C);
   float z = b[0];
-  for (int c = 0; c < C; ++c) z = fmaf(__bfloat162float(fp[c]), w[c], z);
+  for (int c8 = 0; c8 < C / 8; ++c8) {
+    const uint4 q = __ldg(fp + c8);
+    const bf16* h = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) z = fmaf(__bfloat162float(h[i]), sw[c8 * 8 + i], z);
+  }
   out[p] = 1.f / (1.f + expf(-z));
 }
 
@@ -278,12 +288,31 @@ __global__ void relayout_convT(const float* w, bf16* wf, bf16* wt, int cin, int 
 }
 
 // per-frame features for the error head: channel means of the bottleneck
-// activation, feat[b][c] = mean over pixels of x[b][p][c]
-__global__ void pool_features(const bf16* x, int P, int C, float* feat) {
-  const int b = blockIdx.x;
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+// activation, feat[b][c] = mean over pixels of x[b][p][c].  One block of
+// 1024 threads per frame: thread t sums channel t mod C over the pixels
+// p = t / C (mod 1024 / C) with four accumulators, then the groups'
+// partial sums are added in a fixed order (deterministic).  C <= 1024;
+// threads past the last whole group of C only join the barrier.
+__global__ void __launch_bounds__(1024) pool_features(const bf16* x, int P, int C, float* feat) {
+  __shared__ float part[1024];
+  const int b = blockIdx.x, t = threadIdx.x, c = t % C, grp = t / C, ngrp = 1024 / C;
+  if (grp < ngrp) {
+    const bf16* xb = x + (size_t)b * P * C + c;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int p = grp;
+    for (; p + 3 * ngrp < P; p += 4 * ngrp) {
+      s0 += __bfloat162float(xb[(size_t)p * C]);
+      s1 += __bfloat162float(xb[(size_t)(p + ngrp) * C]);
+      s2 += __bfloat162float(xb[(size_t)(p + 2 * ngrp) * C]);
+      s3 += __bfloat162float(xb[(size_t)(p + 3 * ngrp) * C]);
+    }
+    for (; p < P; p += ngrp) s0 += __bfloat162float(xb[(size_t)p * C]);
+    part[t] = (s0 + s1) + (s2 + s3);
+  }
+  __syncthreads();
+  if (grp == 0) {
     float s = 0.f;
-    for (int p = 0; p < P; ++p) s += __bfloat162float(x[((size_t)b * P + p) * C + c]);
+    for (int g = 0; g < ngrp; ++g) s += part[g * C + c];
     feat[(size_t)b * C + c] = s / (float)P;
   }
 }
@@ -314,6 +343,89 @@ __global__ void grads_to_param_layout(const float* g, float* out, const Seg* seg
 
 inline unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// ------------------------------------------------------------ GAN term
+// discriminator input: the 8 channels of the slice, the frame (BF16), 7 zeros
+__global__ void disc_input(const bf16* x, const float* y, bf16* out, long long P) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const uint4 xv = reinterpret_cast<const uint4*>(x)[p];
+  __align__(16) bf16 o[8];
+  o[0] = __float2bfloat16_rn(y[p]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) o[k] = __float2bfloat16_rn(0.f);
+  reinterpret_cast<uint4*>(out)[2 * p] = xv;
+  reinterpret_cast<uint4*>(out)[2 * p + 1] = *reinterpret_cast<const uint4*>(o);
+}
+
+// patch logits z[p] = sum_c f[p][c] w[c] + b
+__global__ void disc_head_fwd(const bf16* f, int C, const float* w, const float* b, float* z, long long P) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const bf16* fp = f + p * C;
+  float acc = b[0];
+  for (int c = 0; c < C; ++c) acc = fmaf(__bfloat162float(fp[c]), w[c], acc);
+  z[p] = acc;
+}
+
+// BCE of logits against a constant target t: per block, the fixed-order sum
+// of log(1 + e^z) - t z into partial[block]; dz[p] = scale (s(z) - t)
+__global__ void bce_logits_kernel(const float* z, float t, float scale, float* dz, float* partial, long long P) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (p < P) {
+    const float v = z[p];
+    // log(1 + e^v) without overflow: max(v, 0) + log1p(e^-|v|)
+    l = fmaxf(v, 0.f) + log1pf(expf(-fabsf(v))) - t * v;
+    dz[p] = scale * (1.f / (1.f + expf(-v)) - t);
+  }
+  block_sum_to(partial, l);
+}
+
+// out[0] (+)= weight * (sum of the partials) / P, in order
+__global__ void bce_finish(const float* partial, int n, long long P, float weight, int accumulate, float* out) {
+  float s = 0.f;
+  for (int k = 0; k < n; ++k) s += partial[k];
+  const float v = weight * s / (float)P;
+  out[0] = accumulate ? out[0] + v : v;
+}
+
+// through the head: df = dz w [f > 0]; gw[c] += sum dz f[c], gb += sum dz
+// (gw, gb may be null: no parameter gradients)
+__global__ void disc_head_bwd(const bf16* f, int C, const float* w, const float* dz, bf16* df, float* gw, float* gb,
+                              long long P) {
+  __shared__ float sw[256 + 1];
+  for (int i = threadIdx.x; i <= C; i += blockDim.x) sw[i] = 0.f;
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p < P) {
+    const float d = dz[p];
+    const bf16* fp = f + p * C;
+    bf16* dp = df + p * C;
+    for (int c = 0; c < C; ++c) {
+      const float fv = __bfloat162float(fp[c]);
+      dp[c] = __float2bfloat16_rn(fv > 0.f ? d * w[c] : 0.f);
+      if (gw) atomicAdd(&sw[c], d * fv);
+    }
+    if (gb) atomicAdd(&sw[C], d);
+  }
+  __syncthreads();
+  if (gw)
+    for (int i = threadIdx.x; i < C; i += blockDim.x) atomicAdd(&gw[i], sw[i]);
+  if (gb && threadIdx.x == 0) atomicAdd(gb, sw[C]);
+}
+
+// dout[p] += g[p * cs + ch]: the frame channel of the discriminator's input
+// gradient, added to the generator's output gradient
+__global__ void add_channel(const bf16* g, int cs, int ch, float* dout, long long P) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p < P) dout[p] += __bfloat162float(g[p * cs + ch]);
+}
+
+__global__ void fill_bf16(bf16* p, float v, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = __float2bfloat16_rn(v);
+}
+
 }  // namespace surr
 }  // namespace ussim
 
@@ -342,6 +454,20 @@ struct us_surr {
   float *feat = nullptr, *ehead = nullptr;   // bottleneck features of the last forward, error-head weights
   unsigned* err = nullptr;
   std::string last_error;
+  // GAN term (App. B.2: L1 and GAN terms, weights 1 and 0.01): the patch
+  // discriminator's parameters, optimiser state, BF16 weights and buffers
+  int gan_cd = 0;
+  float gan_weight = 0.f, gan_lr = 0.f;
+  int gan_step = 0;
+  std::vector<LayerDesc> dlayers;   // d1, d2, d3 (conv3x3 stride 2), head
+  std::vector<Seg> dsegs;
+  long long dn = 0;
+  float *dp = nullptr, *dm = nullptr, *dv = nullptr, *dg = nullptr, *dg_host = nullptr;
+  Seg* d_dsegs = nullptr;
+  bf16 *dwf[3] = {}, *dwd[3] = {};
+  bf16 *din = nullptr, *din_g = nullptr, *dones = nullptr;
+  bf16 *dact[3] = {}, *dgr[3] = {};
+  float *dlogit = nullptr, *ddz = nullptr, *dpart = nullptr;
 };
 
 namespace {
@@ -430,6 +556,24 @@ void free_surr(us_surr* s) {
   cudaFree(s->feat);
   cudaFree(s->ehead);
   cudaFree(s->err);
+  cudaFree(s->dp);
+  cudaFree(s->dm);
+  cudaFree(s->dv);
+  cudaFree(s->dg);
+  cudaFree(s->dg_host);
+  cudaFree(s->d_dsegs);
+  for (int i = 0; i < 3; ++i) {
+    cudaFree(s->dwf[i]);
+    cudaFree(s->dwd[i]);
+    cudaFree(s->dact[i]);
+    cudaFree(s->dgr[i]);
+  }
+  cudaFree(s->din);
+  cudaFree(s->din_g);
+  cudaFree(s->dones);
+  cudaFree(s->dlogit);
+  cudaFree(s->ddz);
+  cudaFree(s->dpart);
   delete s;
 }
 
@@ -496,7 +640,7 @@ us_status forward_impl(us_surr* s, int B, cudaStream_t st) {
   const long long P = (long long)B * s->cfg.height * s->cfg.width;
   head_fwd<<<blocks(P), 256, 0, st>>>(s->bufs[B_X0].a, hd.cin, s->p + hd.w_off, s->p + hd.b_off, s->out, P);
   const auto& e3 = s->bufs[B_E3];
-  pool_features<<<B, 256, 0, st>>>(e3.a, e3.H * e3.W, e3.C, s->feat);
+  pool_features<<<B, 1024, 0, st>>>(e3.a, e3.H * e3.W, e3.C, s->feat);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? US_OK : cfail(s, e, "head");
 }
@@ -544,6 +688,126 @@ us_status backward_impl(us_surr* s, int B, cudaStream_t st) {
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? US_OK : cfail(s, e, "backward");
+}
+
+// ---------------------------------------------------------- GAN term
+constexpr int kDiscIn = 16;   // discriminator input channels: slice 8, frame 1, zeros 7
+
+void build_disc(us_surr* s, int cd) {
+  s->dlayers.clear();
+  s->dsegs.clear();
+  s->dn = 0;
+  const int H = s->cfg.height, W = s->cfg.width;
+  const int cin[3] = {kDiscIn, cd, 2 * cd}, cout[3] = {cd, 2 * cd, 2 * cd};
+  for (int i = 0; i < 4; ++i) {
+    LayerDesc d{};
+    d.kind = i < 3 ? 0 : 2;
+    d.cin = i < 3 ? cin[i] : 2 * cd;
+    d.cout = i < 3 ? cout[i] : 1;
+    d.stride = i < 3 ? 2 : 1;
+    d.hin = H >> i;
+    d.win = W >> i;
+    d.w_size = d.kind == 0 ? 9LL * d.cin * d.cout : d.cin;
+    d.w_off = s->dn;
+    d.b_off = d.w_off + d.w_size;
+    s->dn = d.b_off + d.cout;
+    s->dlayers.push_back(d);
+    s->dsegs.push_back(Seg{d.w_off, d.w_size, d.kind == 0 ? 1 : 0, d.cin, d.cout});
+    s->dsegs.push_back(Seg{d.b_off, d.cout, 0, 0, 0});
+  }
+}
+
+us_status refresh_disc_weights(us_surr* s, cudaStream_t st) {
+  for (int i = 0; i < 3; ++i) {
+    const LayerDesc& d = s->dlayers[i];
+    relayout_conv<<<blocks(d.w_size), 256, 0, st>>>(s->dp + d.w_off, s->dwf[i], s->dwd[i], d.cin, d.cout);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? US_OK : cfail(s, e, "discriminator weight relayout");
+}
+
+// discriminator forward on (slice x, frame y): logits of the B frames' patches
+us_status disc_forward(us_surr* s, const bf16* x, const float* y, int B, cudaStream_t st) {
+  const int H = s->cfg.height, W = s->cfg.width;
+  const long long P = (long long)B * H * W;
+  disc_input<<<blocks(P), 256, 0, st>>>(x, y, s->din, P);
+  const bf16* in = s->din;
+  int in_c = kDiscIn;
+  for (int i = 0; i < 3; ++i) {
+    const LayerDesc& d = s->dlayers[i];
+    const us_status r = us_conv3x3_fwd(reinterpret_cast<const uint16_t*>(in), in_c, 0,
+                                       reinterpret_cast<const uint16_t*>(s->dwf[i]), s->dp + d.b_off,
+                                       reinterpret_cast<uint16_t*>(s->dact[i]), d.cout, 0, B, d.hin, d.win, d.cin,
+                                       d.cout, 2, 1, s->err, st);
+    if (r != US_OK) return fail(s, r, "discriminator layer " + std::to_string(i));
+    in = s->dact[i];
+    in_c = d.cout;
+  }
+  const LayerDesc& hd = s->dlayers[3];
+  const long long Pd = (long long)B * (H >> 3) * (W >> 3);
+  disc_head_fwd<<<blocks(Pd), 256, 0, st>>>(s->dact[2], hd.cin, s->dp + hd.w_off, s->dp + hd.b_off, s->dlogit, Pd);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? US_OK : cfail(s, e, "discriminator forward");
+}
+
+// BCE of the last logits against t: out[0] (+)= weight * mean; dz = scale (s(z) - t)
+us_status disc_bce(us_surr* s, int B, float t, float weight, float scale, int accumulate, float* out,
+                   cudaStream_t st) {
+  const long long Pd = (long long)B * (s->cfg.height >> 3) * (s->cfg.width >> 3);
+  const unsigned nb = blocks(Pd, kRedThreads);
+  bce_logits_kernel<<<nb, kRedThreads, 0, st>>>(s->dlogit, t, scale, s->ddz, s->dpart, Pd);
+  bce_finish<<<1, 1, 0, st>>>(s->dpart, (int)nb, Pd, weight, accumulate, out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? US_OK : cfail(s, e, "discriminator loss");
+}
+
+// from dz back through the discriminator: with_params adds the parameter
+// gradients to dg; with_input leaves the gradient of its input in din_g
+us_status disc_backward(us_surr* s, int B, bool with_params, bool with_input, cudaStream_t st) {
+  const int H = s->cfg.height, W = s->cfg.width;
+  const LayerDesc& hd = s->dlayers[3];
+  const long long Pd = (long long)B * (H >> 3) * (W >> 3);
+  disc_head_bwd<<<blocks(Pd), 256, 0, st>>>(s->dact[2], hd.cin, s->dp + hd.w_off, s->ddz, s->dgr[2],
+                                            with_params ? s->dg + hd.w_off : nullptr,
+                                            with_params ? s->dg + hd.b_off : nullptr, Pd);
+  for (int i = 2; i >= 0; --i) {
+    const LayerDesc& d = s->dlayers[i];
+    const long long Pout = (long long)B * (d.hin / 2) * (d.win / 2);
+    const uint16_t* dy = reinterpret_cast<const uint16_t*>(s->dgr[i]);
+    const bf16* xin = i > 0 ? s->dact[i - 1] : s->din;
+    us_status r = US_OK;
+    if (with_params) {
+      bias_grad<<<blocks(Pout, 4096), 256, 0, st>>>(s->dgr[i], d.cout, 0, d.cout, Pout, 4096, s->dg + d.b_off);
+      r = us_conv3x3_wgrad(reinterpret_cast<const uint16_t*>(xin), d.cin, 0, dy, d.cout, 0, s->dg + d.w_off, B, d.hin,
+                           d.win, d.cin, d.cout, 2, s->err, st);
+    }
+    if (r == US_OK && (i > 0 || with_input)) {
+      // inner layers: the input is a post-ReLU activation (its mask applies);
+      // the first layer's input is not, so its gradient is taken through an
+      // all-ones mask
+      const bf16* mask = i > 0 ? xin : s->dones;
+      bf16* dx = i > 0 ? s->dgr[i - 1] : s->din_g;
+      r = us_conv3x3_dgrad(dy, d.cout, 0, reinterpret_cast<const uint16_t*>(s->dwd[i]),
+                           reinterpret_cast<const uint16_t*>(mask), d.cin, 0, reinterpret_cast<uint16_t*>(dx), d.cin,
+                           0, 0, B, d.hin, d.win, d.cin, d.cout, 2, s->err, st);
+    }
+    if (r != US_OK) return fail(s, r, "discriminator backward layer " + std::to_string(i));
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? US_OK : cfail(s, e, "discriminator backward");
+}
+
+// the generator's GAN term: loss_out[0] += w BCE(D(x, pred), 1) and
+// dout += d/dpred of it (the discriminator held fixed)
+us_status gan_generator_term(us_surr* s, const bf16* x, int B, float* loss_out, cudaStream_t st) {
+  const long long Pd = (long long)B * (s->cfg.height >> 3) * (s->cfg.width >> 3);
+  TRY(disc_forward(s, x, s->out, B, st));
+  TRY(disc_bce(s, B, 1.f, s->gan_weight, s->gan_weight / (float)Pd, 1, loss_out, st));
+  TRY(disc_backward(s, B, false, true, st));
+  const long long P = (long long)B * s->cfg.height * s->cfg.width;
+  add_channel<<<blocks(P), 256, 0, st>>>(s->din_g, kDiscIn, kInCh, s->dout, P);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? US_OK : cfail(s, e, "GAN term");
 }
 
 us_status loss_impl(us_surr* s, const float* pred, const float* target, int B, float* loss_out, float* dpred,
@@ -739,6 +1003,7 @@ us_status us_surr_train_step(us_surr* s, const uint16_t* x, const float* target,
   s->bufs[B_IN].a = const_cast<bf16*>(reinterpret_cast<const bf16*>(x));
   us_status r = forward_impl(s, B, st);
   if (r == US_OK) r = loss_impl(s, s->out, target, B, loss_out, s->dout, st);
+  if (r == US_OK && s->gan_weight > 0.f) r = gan_generator_term(s, reinterpret_cast<const bf16*>(x), B, loss_out, st);
   if (r == US_OK) r = backward_impl(s, B, st);
   s->bufs[B_IN].a = nullptr;
   if (r != US_OK) return r;
@@ -836,6 +1101,109 @@ us_status us_surr_get_params(const us_surr* s, float* host_out) {
   if (!s || !host_out) return US_ERR_INVALID_ARG;
   return cudaMemcpy(host_out, s->p, sizeof(float) * s->n_params, cudaMemcpyDeviceToHost) == cudaSuccess ? US_OK
                                                                                                           : US_ERR_CUDA;
+}
+
+int64_t us_surr_gan_num_params(int32_t cd) {
+  if (cd < 16 || cd > 128 || cd % 16) return -1;
+  us_surr tmp;
+  tmp.cfg.height = tmp.cfg.width = 64;
+  build_disc(&tmp, cd);
+  return tmp.dn;
+}
+
+us_status us_surr_gan_enable(us_surr* s, int32_t cd, const float* init, float gan_weight, float lr) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (!init || cd < 16 || cd > 128 || cd % 16 || !(gan_weight >= 0.f) || !(lr > 0.f) || s->gan_cd)
+    return fail(s, US_ERR_INVALID_ARG, "bad GAN arguments (or the GAN term is already enabled)");
+  build_disc(s, cd);
+  const int H = s->cfg.height, W = s->cfg.width, Bm = s->cfg.max_batch;
+  const long long P = (long long)Bm * H * W;
+  cudaError_t e = cudaSuccess;
+  auto fa = [&](float** p, long long n) {
+    if (e == cudaSuccess) e = cudaMalloc(p, sizeof(float) * (size_t)std::max(1LL, n));
+  };
+  auto ba = [&](bf16** p, long long n) {
+    if (e == cudaSuccess) e = cudaMalloc(p, sizeof(bf16) * (size_t)std::max(1LL, n));
+  };
+  fa(&s->dp, s->dn);
+  fa(&s->dm, s->dn);
+  fa(&s->dv, s->dn);
+  fa(&s->dg, s->dn);
+  fa(&s->dg_host, s->dn);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_dsegs, sizeof(Seg) * s->dsegs.size());
+  for (int i = 0; i < 3; ++i) {
+    const LayerDesc& d = s->dlayers[i];
+    ba(&s->dwf[i], d.w_size);
+    ba(&s->dwd[i], d.w_size);
+    ba(&s->dact[i], (long long)Bm * (d.hin / 2) * (d.win / 2) * d.cout);
+    ba(&s->dgr[i], (long long)Bm * (d.hin / 2) * (d.win / 2) * d.cout);
+  }
+  ba(&s->din, P * kDiscIn);
+  ba(&s->din_g, P * kDiscIn);
+  ba(&s->dones, P * kDiscIn);
+  const long long Pd = (long long)Bm * (H >> 3) * (W >> 3);
+  fa(&s->dlogit, Pd);
+  fa(&s->ddz, Pd);
+  fa(&s->dpart, (long long)blocks(Pd, kRedThreads));
+  if (e == cudaSuccess) e = cudaMemcpy(s->dp, init, sizeof(float) * s->dn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->dm, 0, sizeof(float) * s->dn);
+  if (e == cudaSuccess) e = cudaMemset(s->dv, 0, sizeof(float) * s->dn);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->d_dsegs, s->dsegs.data(), sizeof(Seg) * s->dsegs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    fill_bf16<<<blocks(P * kDiscIn), 256>>>(s->dones, 1.f, P * kDiscIn);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cfail(s, e, "GAN buffers");
+  s->gan_cd = cd;
+  s->gan_weight = gan_weight;
+  s->gan_lr = lr;
+  TRY(refresh_disc_weights(s, nullptr));
+  e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? US_OK : cfail(s, e, "GAN set-up");
+}
+
+us_status us_surr_gan_disc_step(us_surr* s, const uint16_t* x, const float* real, int32_t B, float* loss_out,
+                                int32_t update, void* stream) {
+  if (!s) return US_ERR_INVALID_ARG;
+  if (!s->gan_cd) return fail(s, US_ERR_INVALID_ARG, "the GAN term is not enabled");
+  if (!x || !real || !loss_out || B < 1 || B > s->cfg.max_batch || !aligned16(x))
+    return fail(s, US_ERR_INVALID_ARG, "bad discriminator-step arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long Pd = (long long)B * (s->cfg.height >> 3) * (s->cfg.width >> 3);
+  const bf16* xb = reinterpret_cast<const bf16*>(x);
+  cudaError_t e = cudaMemsetAsync(s->dg, 0, sizeof(float) * s->dn, st);
+  if (e != cudaSuccess) return cfail(s, e, "zero discriminator grads");
+  // (BCE(D(x, real), 1) + BCE(D(x, fake), 0)) / 2, the fake frames being the
+  // last forward's output; loss_out [3]: the loss, its real and fake terms
+  TRY(disc_forward(s, xb, real, B, st));
+  TRY(disc_bce(s, B, 1.f, 1.f, 0.5f / (float)Pd, 0, loss_out + 1, st));
+  TRY(disc_backward(s, B, true, false, st));
+  TRY(disc_forward(s, xb, s->out, B, st));
+  TRY(disc_bce(s, B, 0.f, 1.f, 0.5f / (float)Pd, 0, loss_out + 2, st));
+  TRY(disc_backward(s, B, true, false, st));
+  bce_finish<<<1, 1, 0, st>>>(loss_out + 1, 2, 2, 1.f, 0, loss_out);
+  if (update) {
+    s->gan_step += 1;
+    const float c1 = 1.f - std::pow(s->cfg.beta1, (float)s->gan_step), c2 = 1.f - std::pow(s->cfg.beta2, (float)s->gan_step);
+    adam_kernel<<<blocks(s->dn), 256, 0, st>>>(s->dp, s->dm, s->dv, s->dg, s->d_dsegs, (int)s->dsegs.size(), s->dn,
+                                               s->gan_lr, s->cfg.beta1, s->cfg.beta2, s->cfg.eps, c1, c2);
+    TRY(refresh_disc_weights(s, st));
+  }
+  e = cudaGetLastError();
+  return e == cudaSuccess ? US_OK : cfail(s, e, "discriminator step");
+}
+
+us_status us_surr_gan_get(us_surr* s, float* params_host, float* grads_host) {
+  if (!s || !s->gan_cd) return US_ERR_INVALID_ARG;
+  if (params_host && cudaMemcpy(params_host, s->dp, sizeof(float) * s->dn, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return US_ERR_CUDA;
+  if (grads_host) {
+    grads_to_param_layout<<<blocks(s->dn), 256>>>(s->dg, s->dg_host, s->d_dsegs, (int)s->dsegs.size(), s->dn);
+    if (cudaMemcpy(grads_host, s->dg_host, sizeof(float) * s->dn, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return US_ERR_CUDA;
+  }
+  return US_OK;
 }
 
 us_status us_surr_get_grads(us_surr* s, float* host_out) {

@@ -2,11 +2,16 @@
 
     python -m paper_2507_01152_gb300.opbench fwd|dgrad|wgrad B H Cin Cout [stride] [reps]
     python -m paper_2507_01152_gb300.opbench hist B H [reps]
+    python -m paper_2507_01152_gb300.opbench surrogate B [reps]
 
 fwd / dgrad / wgrad: one 3x3 convolution pass of the tcgen05 implicit GEMM
 on B images of H x H pixels (input grid), NHWC BF16 activations with random
 values, Cin -> Cout channels; prints the time per call and the rate in
 TFLOP/s (2 x 9 x Cin x Cout multiply-adds per output pixel).
+
+surrogate: the whole surrogate forward (base 32 channels, 256 x 256
+frames) on B random input slices; prints the time per call, frames/s and
+TFLOP/s (2 x 10.74 G multiply-adds per frame).
 
 hist: CT histogram matching (us_sim_hist_match) of B images of H x H FP32
 values (normal, 300 HU spread, every pixel considered) to a reference of
@@ -93,7 +98,43 @@ def hist_match(B: int, H: int, reps: int = 10):
     return ms, B * H * H * 14 / ms / 1e6
 
 
+def surrogate_forward(B: int, reps: int = 5, c: int = 32, H: int = 256):
+    """the whole surrogate forward (c base channels, H x H frames) on B
+    random BF16 input slices: ms per call, frames/s, TFLOP/s (2 x the
+    network's multiply-adds)"""
+    import numpy as np
+    import torch
+    from . import build, scene
+    from .ussim import Surrogate
+    build.build()
+    off, size, fan = Surrogate.segments(c, H, H)
+    net = Surrogate(c, H, H, B, scene.surrogate_init(size, fan, 0))
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.rand((B, H, H, 8), device="cuda", generator=g).to(torch.bfloat16)
+    y = torch.empty((B, H, H), device="cuda")
+    for _ in range(2):
+        net.forward(x, y)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        net.forward(x, y)
+    e.record()
+    e.synchronize()
+    net.check()
+    ms = a.elapsed_time(e) / reps
+    macs = 10.74e9 * (c / 32) ** 2 * (H / 256) ** 2
+    net.close()
+    return ms, B / ms * 1e3, 2 * macs * B / ms / 1e9
+
+
 def main(argv):
+    if argv[0] == "surrogate":
+        B = int(argv[1])
+        reps = int(argv[2]) if len(argv) > 2 else 5
+        ms, fps, tf = surrogate_forward(B, reps)
+        print(f"surrogate forward B={B} c=32 256x256: {ms:.4f} ms, {fps:.0f} frames/s, {tf:.1f} TFLOP/s", flush=True)
+        return
     if argv[0] == "hist":
         B, H = int(argv[1]), int(argv[2])
         reps = int(argv[3]) if len(argv) > 3 else 10

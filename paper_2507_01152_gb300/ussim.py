@@ -120,6 +120,10 @@ SIGNATURES = {
     "us_surr_train_step": (C.c_int, [_P, _P, _P, _I, _P, _I, _P]),
     "us_surr_metrics": (C.c_int, [_P, _P, _P, _I, _P, _P]),
     "us_surr_metrics_hw": (C.c_int, [_P, _P, _P, _I, _I, _I, _P, _P]),
+    "us_surr_gan_num_params": (C.c_int64, [C.c_int32]),
+    "us_surr_gan_enable": (C.c_int, [_P, C.c_int32, _P, C.c_float, C.c_float]),
+    "us_surr_gan_disc_step": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.c_int32, _P]),
+    "us_surr_gan_get": (C.c_int, [_P, _P, _P]),
     "us_surr_num_features": (C.c_int32, [_P]),
     "us_surr_features": (C.c_int, [_P, C.c_int32, _P, _P]),
     "us_surr_predict_error": (C.c_int, [_P, C.c_int32, _P, _P]),
@@ -492,6 +496,25 @@ class Surrogate:
     def metrics(self, pred, target, out, stream=None):
         self._check(self._lib.us_surr_metrics(self.h, _ptr(pred), _ptr(target), pred.shape[0], _ptr(out),
                                               _stream_handle(stream)))
+
+    def gan_enable(self, cd, init, gan_weight=0.01, lr=2e-4):
+        """enable the GAN term with a discriminator of width cd (init: host float32 parameters)"""
+        init = np.ascontiguousarray(init, np.float32)
+        n = int(self._lib.us_surr_gan_num_params(int(cd)))
+        if init.size != n:
+            raise ValueError(f"discriminator of width {cd} has {n} parameters, got {init.size}")
+        self._gan_n = n
+        self._check(self._lib.us_surr_gan_enable(self.h, int(cd), _ptr(init), float(gan_weight), float(lr)))
+
+    def gan_disc_step(self, x, real, loss_out, update=True, stream=None):
+        self._check(self._lib.us_surr_gan_disc_step(self.h, _ptr(x), _ptr(real), x.shape[0], _ptr(loss_out),
+                                                    1 if update else 0, _stream_handle(stream)))
+
+    def gan_params_grads(self):
+        p = np.zeros(self._gan_n, np.float32)
+        g = np.zeros(self._gan_n, np.float32)
+        self._check(self._lib.us_surr_gan_get(self.h, _ptr(p), _ptr(g)))
+        return p, g
 
     def metrics_hw(self, pred, target, out, stream=None):
         """per-frame L1 / SSIM of [B][H][W] frames of any size up to the network's"""

@@ -183,3 +183,54 @@ def test_error_head_ridge_closed_forms():
         np.testing.assert_allclose(S.predict_error(got, f1), w * f1[:, 0] + got[1], rtol=1e-12)
     big = S.fit_error_head(f, t, 1e12)
     assert np.all(np.abs(big[:3]) < 1e-8) and abs(big[3] - t.mean()) < 1e-6
+
+
+def test_bce_on_logits_closed_form_and_gradient():
+    """BCE of logits, the textbook -[t log s(z) + (1 - t) log(1 - s(z))]
+    with s the logistic function, and its gradient (s(z) - t) / n"""
+    z = torch.tensor([-3.0, -0.5, 0.0, 0.7, 4.0], dtype=torch.float64, requires_grad=True)
+    for t in (0.0, 1.0):
+        s = 1.0 / (1.0 + torch.exp(-z.detach()))
+        want = -(t * torch.log(s) + (1 - t) * torch.log(1 - s)).mean()
+        L = S.bce_logits(z, t)
+        assert abs(float(L.detach()) - float(want)) < 1e-14
+        g, = torch.autograd.grad(L, z)
+        assert torch.allclose(g, (s - t) / 5, rtol=1e-13, atol=1e-15)
+    assert abs(float(S.bce_logits(torch.zeros(4, dtype=torch.float64), 1.0)) - math.log(2)) < 1e-15
+
+
+def test_discriminator_shapes_input_and_parameter_count():
+    cd = 8
+    n = 9 * 16 * cd + cd + 9 * cd * 2 * cd + 2 * cd + 9 * 2 * cd * 2 * cd + 2 * cd + 2 * cd + 1
+    assert S.disc_n_params(cd) == n
+    g = torch.Generator().manual_seed(3)
+    x = torch.rand((2, 32, 24, 8), dtype=torch.float64, generator=g)
+    y = torch.rand((2, 32, 24), dtype=torch.float64, generator=g)
+    d = S.disc_input(x, y)
+    assert d.shape == (2, 32, 24, 16)
+    assert torch.equal(d[..., :8], x) and torch.equal(d[..., 8], y) and torch.all(d[..., 9:] == 0)
+    Pd = S.disc_unflatten(torch.randn(n, dtype=torch.float64, generator=g) * 0.2, cd)
+    z = S.disc_forward(Pd, x, y)
+    assert z.shape == (2, 4, 3)                       # one logit per 8 x 8 patch
+
+
+def test_gan_generator_gradient_matches_finite_differences():
+    """the combined generator loss L1 + (1 - SSIM) + 0.01 BCE(D(x, G(x)), 1)
+    differentiated by autograd against central differences, on a tiny net"""
+    c, cd = 4, 4
+    g = torch.Generator().manual_seed(5)
+    flat = torch.randn(S.n_params(c), dtype=torch.float64, generator=g) * 0.3
+    dflat = torch.randn(S.disc_n_params(cd), dtype=torch.float64, generator=g) * 0.3
+    x = torch.rand((1, 16, 16, 8), dtype=torch.float64, generator=g)
+    t = torch.rand((1, 16, 16), dtype=torch.float64, generator=g)
+    L, grad = S.gan_generator_grads(flat, dflat, x, t, c, cd, gan_weight=5.0)   # a large weight exposes the term
+    idx = torch.randperm(flat.numel(), generator=g)[:6]
+    for i in idx.tolist():
+        e = torch.zeros_like(flat)
+        e[i] = 1e-6
+        Lp, _ = S.gan_generator_grads(flat + e, dflat, x, t, c, cd, gan_weight=5.0)
+        Lm, _ = S.gan_generator_grads(flat - e, dflat, x, t, c, cd, gan_weight=5.0)
+        fd = (Lp - Lm) / 2e-6
+        assert abs(fd - float(grad[i])) <= 1e-6 * max(1.0, abs(fd)), (i, fd, float(grad[i]))
+    L0, g0 = S.gan_generator_grads(flat, dflat, x, t, c, cd, gan_weight=0.0)
+    assert abs(L0 - S.loss_and_grads(flat, x, t, c)[0]) < 1e-12      # weight 0: the plain loss
