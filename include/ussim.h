@@ -34,10 +34,17 @@
  *    on the device (non-finite pose entries) set a sticky error word that
  *    us_sim_check() reads.  No entry point aborts or traps.
  *  - One handle may be used from one host thread at a time.  Its batched
- *    renders share workspace (per batch signature: line buffer and the
- *    persistent grid's counters; per handle: the cluster kernel's work
- *    counter and the error word): on different streams, order them with
- *    events, or use one handle per stream.
+ *    renders keep their workspace (work lists, line buffer, the persistent
+ *    grid's counters, the cluster kernel's work counter, the captured graph)
+ *    per batch signature and stream, allocated on first use: renders on
+ *    different streams may overlap; two renders of one signature on one
+ *    stream are ordered by the stream.  The error word is per handle (its
+ *    bits are sticky, so concurrent renders only add to it).
+ *    A plan is kept for every (signature, stream) pair seen, until
+ *    us_sim_destroy.  us_sim_render_plain and us_sim_render_debug's plain path
+ *    share one per-handle scratch, and us_sim_render_host its per-handle staging
+ *    buffers: order those calls.  us_sim_render_plain_static shares one
+ *    scratch array per process.
  *  - Output is a pure function of (inputs, seed, step): two calls with the
  *    same arguments produce bit-identical frames.
  */

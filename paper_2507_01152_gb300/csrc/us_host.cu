@@ -203,12 +203,17 @@ void pair_tables(const us_volume& v, const ProbeHost& ph, int& W, std::vector<ui
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-std::string plan_key(const us_env* envs, int B) {
-  return std::string(reinterpret_cast<const char*>(envs), (size_t)B * sizeof(us_env));
+// a batch signature's plan is per stream: renders of the same signature on
+// different streams get their own line buffer, synchronisation words, work
+// counter and graph, so they may overlap
+std::string plan_key(const us_env* envs, int B, cudaStream_t st) {
+  std::string k(reinterpret_cast<const char*>(envs), (size_t)B * sizeof(us_env));
+  k.append(reinterpret_cast<const char*>(&st), sizeof st);
+  return k;
 }
 
-us_status get_plan(us_sim* s, const us_env* envs, int B, us_plan** out) {
-  std::string key = plan_key(envs, B);
+us_status get_plan(us_sim* s, const us_env* envs, int B, us_plan** out, cudaStream_t st) {
+  std::string key = plan_key(envs, B, st);
   auto it = s->plans.find(key);
   if (it != s->plans.end()) {
     *out = &it->second;
@@ -245,7 +250,12 @@ us_status get_plan(us_sim* s, const us_env* envs, int B, us_plan** out) {
   if (B > 0) {
     cudaError_t e = upload(&pl.d_items, pl.items_sorted.data(), pl.items_sorted.size());
     if (e == cudaSuccess) e = upload(&pl.d_items_batch, pl.items_batch.data(), pl.items_batch.size());
-    if (e != cudaSuccess) return cuda_fail(s, e, "upload work list");
+    if (e == cudaSuccess) e = cudaMalloc(&pl.d_work, sizeof(unsigned));
+    if (e != cudaSuccess) {
+      cudaFree(pl.d_items);
+      cudaFree(pl.d_items_batch);
+      return cuda_fail(s, e, "upload work list");
+    }
   }
   auto ins = s->plans.emplace(std::move(key), std::move(pl));
   *out = &ins.first->second;
@@ -305,8 +315,9 @@ us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, ui
   us_status r = check_render_args(s, envs, B, poses, frames);
   if (r != US_OK || B == 0) return r;
   us_plan* pl;
-  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  if ((r = get_plan(s, envs, B, &pl, st)) != US_OK) return r;
   RenderParams p = base_params(s, poses, seed, step, frames);
+  p.work = pl->d_work;
   p.envelope = envelope;
   p.logimg = logimg;
   p.nn_index = nn;
@@ -326,7 +337,7 @@ us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, ui
       if ((e = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, st)) != cudaSuccess) return cuda_fail(s, e, "two-pass render launch");
       return US_OK;
     }
-    if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(s, e, "reset work counter");
+    if ((e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(s, e, "reset work counter");
     if ((e = launch_fused(p, s->shape, st)) != cudaSuccess) return cuda_fail(s, e, "fused render launch");
   } else {
     p.n_items = B;
@@ -361,6 +372,7 @@ void free_sim(us_sim* s) {
     cudaFree(kv.second.d_gated_count);
     cudaFree(kv.second.d_items_audit);
     cudaFree(kv.second.d_audit_count);
+    cudaFree(kv.second.d_work);
     cudaFree(kv.second.d_beam);
     cudaFree(kv.second.d_sync);
     cudaFree(kv.second.d_slice_hu);
@@ -501,7 +513,7 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
     if (two_pass) {
       e2 = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, p.n_items, st);
     } else {
-      e1 = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
+      e1 = cudaMemsetAsync(p.work, 0, sizeof(unsigned), st);
       e2 = launch_fused(p, s->shape, st);
     }
     e = cudaStreamEndCapture(st, &g);
@@ -788,7 +800,7 @@ us_status us_sim_render_host(us_sim* s, const us_env* envs, int32_t B, const flo
   if (B == 0) return US_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   us_plan* pl;
-  us_status r = get_plan(s, envs, B, &pl);
+  us_status r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream));
   if (r != US_OK) return r;
   for (int i = 0; i < 12 * B; ++i)
     if (!std::isfinite(poses_host[i])) return fail(s, US_ERR_INVALID_ARG, "non-finite pose entry");
@@ -825,7 +837,7 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
   if (B > 32 * 1024) return fail(s, US_ERR_UNSUPPORTED, "gated batches are limited to 32768 envs");
   if (!s->batched) return no_batched(s);
   us_plan* pl;
-  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  if ((r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream))) != US_OK) return r;
   cudaError_t e;
   if (!pl->d_items_gated && ((e = cudaMalloc(&pl->d_items_gated, sizeof(EnvItem) * B)) != cudaSuccess ||
                              (e = cudaMalloc(&pl->d_gated_count, sizeof(int))) != cudaSuccess))
@@ -835,6 +847,7 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
       cudaSuccess)
     return cuda_fail(s, e, "gate");
   RenderParams p = base_params(s, poses, seed, step, frames);
+  p.work = pl->d_work;
   p.items = pl->d_items_gated;
   p.n_items = B;
   p.n_items_dev = pl->d_gated_count;
@@ -842,7 +855,7 @@ us_status us_sim_render_gated(us_sim* s, const us_env* envs, int32_t B, const fl
     if ((e = two_pass_buffers(pl)) != cudaSuccess)
       return cuda_fail(s, e, "two-pass line buffer");
     if ((e = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, st)) != cudaSuccess) return cuda_fail(s, e, "gated render");
-  } else if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess ||
+  } else if ((e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), st)) != cudaSuccess ||
              (e = launch_fused(p, s->shape, st)) != cudaSuccess) {
     return cuda_fail(s, e, "gated render");
   }
@@ -862,13 +875,14 @@ us_status us_sim_render_audit(us_sim* s, const us_env* envs, int32_t B, const fl
   if (B > 32 * 1024) return fail(s, US_ERR_UNSUPPORTED, "audited batches are limited to 32768 envs");
   if (!s->batched) return no_batched(s);
   us_plan* pl;
-  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  if ((r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream))) != US_OK) return r;
   cudaError_t e;
   if (!pl->d_items_audit && ((e = cudaMalloc(&pl->d_items_audit, sizeof(EnvItem) * B)) != cudaSuccess ||
                              (e = cudaMalloc(&pl->d_audit_count, sizeof(int))) != cudaSuccess))
     return cuda_fail(s, e, "audit work list");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   RenderParams p = base_params(s, poses, seed, step, audit_frames);
+  p.work = pl->d_work;
   const double t = std::floor((double)fraction * 4294967296.0);
   if ((e = launch_audit_compact(pl->d_items_batch, B, score, threshold, p.key, (unsigned long long)t,
                                 pl->d_items_audit, pl->d_audit_count, flags, st)) != cudaSuccess)
@@ -880,7 +894,7 @@ us_status us_sim_render_audit(us_sim* s, const us_env* envs, int32_t B, const fl
     if ((e = two_pass_buffers(pl)) != cudaSuccess) return cuda_fail(s, e, "two-pass line buffer");
     if ((e = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, st)) != cudaSuccess)
       return cuda_fail(s, e, "audit render");
-  } else if ((e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st)) != cudaSuccess ||
+  } else if ((e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), st)) != cudaSuccess ||
              (e = launch_fused(p, s->shape, st)) != cudaSuccess) {
     return cuda_fail(s, e, "audit render");
   }
@@ -896,7 +910,7 @@ us_status us_sim_sample_slices_grid(us_sim* s, const us_env* envs, int32_t B, co
   if (r != US_OK || B == 0) return r;
   if (H < 2 || W < 2 || H > 4096 || W > 4096) return fail(s, US_ERR_INVALID_ARG, "grid size must be in [2, 4096]");
   us_plan* pl;
-  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  if ((r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream))) != US_OK) return r;
   auto key = std::make_pair((int)H, (int)W);
   auto it = s->grids.find(key);
   cudaError_t e;
@@ -967,7 +981,7 @@ us_status us_sim_resize_frames(us_sim* s, const us_env* envs, int32_t B, const f
   if (H < 2 || W < 2 || H > 4096 || W > 4096) return fail(s, US_ERR_INVALID_ARG, "grid size must be in [2, 4096]");
   us_plan* pl;
   us_status r;
-  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  if ((r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream))) != US_OK) return r;
   int max_out = 0;
   for (const ProbeHost& ph : s->probes) max_out = std::max(max_out, ph.desc.out_w * ph.desc.out_h);
   RenderParams p = base_params(s, nullptr, 0, 0, frames);
@@ -1029,7 +1043,7 @@ us_status us_sim_recon_update(us_sim* s, const us_env* envs, int32_t B, const fl
     return fail(s, US_ERR_INVALID_ARG, "bad reconstruction arguments");
   if (B == 0) return US_OK;
   us_plan* pl;
-  us_status r = get_plan(s, envs, B, &pl);
+  us_status r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream));
   if (r != US_OK) return r;
   RenderParams p = base_params(s, poses, seed, step, nullptr);
   int max_lines = 1;
@@ -1048,7 +1062,7 @@ us_status us_sim_recon_observe(us_sim* s, const us_env* envs, int32_t B, const f
     return fail(s, US_ERR_INVALID_ARG, "bad observation arguments");
   if (B == 0) return US_OK;
   us_plan* pl;
-  us_status r = get_plan(s, envs, B, &pl);
+  us_status r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream));
   if (r != US_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(obs, 0, (size_t)B * 64000, st);
@@ -1064,9 +1078,10 @@ us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const fl
   us_status r = check_render_args(s, envs, B, poses, frames);
   if (r != US_OK || B == 0) return r;
   us_plan* pl;
-  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  if ((r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream))) != US_OK) return r;
   if (!s->batched) return no_batched(s);
   RenderParams p = base_params(s, poses, seed, step, frames);
+  p.work = pl->d_work;
   p.items = pl->d_items;
   p.n_items = B;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1091,7 +1106,7 @@ us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const fl
     if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, 1, st);
     cudaEventRecord(ev[2], st);
   } else {
-    e = cudaMemsetAsync(s->d_work, 0, sizeof(unsigned), st);
+    e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), st);
     cudaEventRecord(ev[0], st);
     if (e == cudaSuccess) e = launch_fused(p, s->shape, st);
     cudaEventRecord(ev[1], st);
@@ -1109,7 +1124,7 @@ us_status us_sim_sample_slices(us_sim* s, const us_env* envs, int32_t B, const f
   us_status r = check_render_args(s, envs, B, poses, reinterpret_cast<float*>(out));
   if (r != US_OK || B == 0) return r;
   us_plan* pl;
-  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  if ((r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream))) != US_OK) return r;
   const us_probe& p0 = s->probes[envs[0].probe_id].desc;
   for (int b = 1; b < B; ++b) {
     const us_probe& pb = s->probes[envs[b].probe_id].desc;
@@ -1192,7 +1207,7 @@ us_status us_sim_selftest_tile_wait(us_sim* s, const us_env* envs, int32_t B, co
   if (!s->batched || s->tuning.cluster_size != 1 || !s->tuning.persistent)
     return fail(s, US_ERR_UNSUPPORTED, "the tuning is not the persistent two-pass grid");
   us_plan* pl;
-  if ((r = get_plan(s, envs, B, &pl)) != US_OK) return r;
+  if ((r = get_plan(s, envs, B, &pl, static_cast<cudaStream_t>(stream))) != US_OK) return r;
   cudaError_t e;
   if ((e = two_pass_buffers(pl)) != cudaSuccess) return cuda_fail(s, e, "two-pass line buffer");
   RenderParams p = base_params(s, poses, 0, 0, frames);

@@ -186,7 +186,8 @@ cudaError_t pack_corners(const DevVolume& V, uint4* out, cudaStream_t st);
 
 }  // namespace ussim
 
-// a batch signature's precomputed work list
+// a batch signature's precomputed work list and workspace, one per
+// (signature, stream)
 struct us_plan {
   std::vector<ussim::EnvItem> items_sorted;  // fused order: costliest first
   std::vector<ussim::EnvItem> items_batch;   // caller order
@@ -194,6 +195,7 @@ struct us_plan {
   ussim::EnvItem* d_items_batch = nullptr;   // device copy of items_batch
   ussim::EnvItem* d_items_gated = nullptr;   // device-built subset for gated renders
   int* d_gated_count = nullptr;
+  unsigned* d_work = nullptr;                // cluster path: this plan's work counter
   ussim::EnvItem* d_items_audit = nullptr;   // device-built subset for the gate's physics audit
   int* d_audit_count = nullptr;
   long long frame_floats = 0, beam_elems = 0;

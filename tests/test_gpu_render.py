@@ -489,3 +489,36 @@ def test_render_timed_reports_each_form_and_renders_the_same(c2):
             sim.check()
     finally:
         sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"])
+
+
+@pytest.mark.parametrize("shape", [(8, 32, 1, 0), (1, 16, 1, 0), (1, 16, 0, 1), (1, 32, 1, 1)])
+def test_same_signature_on_two_streams_overlaps_safely(c2, shape):
+    """A batch signature's workspace (work lists, line buffer, persistent
+    grid counters, cluster work counter, captured graph) is kept per stream:
+    renders of one signature queued on two streams with no ordering between
+    them give the frames each gives alone."""
+    wl, sim = c2
+    envs = wl.envs[:16]
+    off = sim.frame_layout(envs)
+    n = int(off[-1])
+    old = sim.get_tuning()
+    try:
+        sim.set_tuning(*shape)
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        P = [torch.from_numpy(wl.poses[16 * k:16 * k + 16]).cuda() for k in range(2)]
+        alone = []
+        for k in range(2):
+            fr = torch.empty(n, device="cuda")
+            sim.render(envs, P[k], 40 + k, k, fr, stream=streams[k])
+            streams[k].synchronize()
+            alone.append(fr.cpu().numpy())
+        for _ in range(3):
+            outs = [torch.full((n,), -1.0, device="cuda") for _ in range(2)]
+            torch.cuda.synchronize()
+            for k in range(2):
+                sim.render(envs, P[k], 40 + k, k, outs[k], stream=streams[k])
+            torch.cuda.synchronize()
+            for k in range(2):
+                assert np.array_equal(outs[k].cpu().numpy(), alone[k])
+    finally:
+        sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"], old.get("persistent", 0))
