@@ -51,7 +51,11 @@ OPS_PER_PIXEL = 20
 OPS_PER_SAMPLE_PASS_B = 91
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the
 # current kernel source (absent until captured; dropped when the kernel changes)
-KERNEL_DRAM_BYTES = {}
+KERNEL_DRAM_BYTES = {
+    # C3, 512 envs, pass A (16-line groups): 476.95 MB read + 454.01 MB
+    # written, one 1-pass capture of the full-size launch
+    ("c3_uneven_512env", "split_lines", 16): 930_960_000,
+}
 
 # Algorithmic bytes of one launch of the default workload: the union of
 # voxels read by the nearest / trilinear footprints of all 64 frames (label

@@ -39,8 +39,7 @@ __global__ void recon_update(RenderParams p, const EnvItem* items, int B, int bo
       if (s < P.ns) {
         float x, z;
         beam_point(P, ln, s, x, z);
-        vi = nearest_voxel(V, to_voxel(M, V.inv_h, x, z));
-        lab = vi >= 0 ? (int)__ldg(&V.labels[vi]) : 0;
+        lab = (int)nearest_label(V, to_voxel(M, V.inv_h, x, z), vi);
       }
       int prev = __shfl_up_sync(0xffffffffu, lab, 1);
       if (lane == 0) prev = carry;

@@ -142,8 +142,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(NW * 32, 1) fused_r
         float x, z;
         beam_point(P, ln, s, x, z);
         const float3 u = to_voxel(cx.M, cx.V.inv_h, x, z);
-        const int vi = nearest_voxel(cx.V, u);
-        const uint8_t lb = vi >= 0 ? __ldg(&cx.V.labels[vi]) : (uint8_t)0;
+        int vi;
+        const uint8_t lb = nearest_label(cx.V, u, vi);
         lrow[s] = lb;
         zrow[s] = p.z_mode == 0 ? fmaxf(trilinear_hu(cx.V, u) + 1024.f, 1.f) : tis[lb].z;
         if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + s] = vi;
@@ -397,11 +397,14 @@ __global__ void max_label_kernel(const uint8_t* labels, long long n, unsigned* o
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-// corner records of a volume's HU grid (layout at DevVolume::hu8)
+// corner records of a volume's HU grid (layout at DevVolume::hu8; the
+// records of the y padding, never read, hold the zeros of cells outside)
 __global__ void pack_corners_kernel(DevVolume V, uint4* out, long long n) {
-  const int px = V.nx + 1, py = V.ny + 1;
+  const int px = V.nx + 1;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % px) - 1, j = (int)((t / px) % py) - 1, k = (int)(t / ((long long)px * py)) - 1;
+    const long long c = t >> 2;
+    const int i = (int)(c % px) - 1, jq = (int)((c / px) % V.qy), k = (int)(c / ((long long)px * V.qy)) - 1;
+    const int j = jq * 4 + (int)(t & 3) - 1;
     auto at = [&](int a, int b, int c) -> unsigned {
       const bool in = (unsigned)a < (unsigned)V.nx && (unsigned)b < (unsigned)V.ny && (unsigned)c < (unsigned)V.nz;
       return in ? (unsigned)(uint16_t)V.hu[((long long)c * V.ny + b) * V.nx + a] : 0u;
@@ -417,8 +420,33 @@ __global__ void pack_corners_kernel(DevVolume V, uint4* out, long long n) {
 }
 
 cudaError_t pack_corners(const DevVolume& V, uint4* out, cudaStream_t st) {
-  const long long n = (long long)(V.nx + 1) * (V.ny + 1) * (V.nz + 1);
-  pack_corners_kernel<<<152 * 8, 256, 0, st>>>(V, out, n);
+  pack_corners_kernel<<<152 * 8, 256, 0, st>>>(V, out, corner_records(V.nx, V.ny, V.nz));
+  return cudaGetLastError();
+}
+
+// labels in 4 x 4 x 4 bricks (layout at DevVolume::lab4): one thread per
+// 4-voxel row of a brick
+__global__ void pack_labels_kernel(DevVolume V, uint32_t* out, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t >> 4;
+    const int r = (int)(t & 15);
+    const int bi = (int)(b % V.bx), bj = (int)((b / V.bx) % V.by), bk = (int)(b / ((long long)V.bx * V.by));
+    const int j = bj * 4 + (r & 3), k = bk * 4 + (r >> 2);
+    uint32_t w = 0;
+    if (j < V.ny && k < V.nz) {
+      const uint8_t* row = V.labels + ((long long)k * V.ny + j) * V.nx;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = bi * 4 + q;
+        if (i < V.nx) w |= (uint32_t)row[i] << (8 * q);
+      }
+    }
+    out[t] = w;
+  }
+}
+
+cudaError_t pack_labels(const DevVolume& V, uint8_t* out, cudaStream_t st) {
+  pack_labels_kernel<<<152 * 8, 256, 0, st>>>(V, reinterpret_cast<uint32_t*>(out), label_bricks_bytes(V.nx, V.ny, V.nz) / 4);
   return cudaGetLastError();
 }
 

@@ -21,8 +21,8 @@ __global__ void plain_slice(RenderParams p, EnvItem it, uint8_t* lab) {
   const int l = q / P.ns, s = q - l * P.ns;
   float x, z;
   beam_point(P, P.lines[l], s, x, z);
-  const int idx = nearest_voxel(V, to_voxel(M, V.inv_h, x, z));
-  const uint8_t lb = idx >= 0 ? __ldg(&V.labels[idx]) : (uint8_t)0;
+  int idx;
+  const uint8_t lb = nearest_label(V, to_voxel(M, V.inv_h, x, z), idx);
   lab[q] = lb;
   if (p.nn_index) p.nn_index[it.beam_off + q] = idx;
   if (p.label) p.label[it.beam_off + q] = lb;

@@ -267,8 +267,7 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
     float x, z;
     beam_point(P, ln, s, x, z);
     u = to_voxel(cx.M, cx.V.inv_h, x, z);
-    vi = nearest_voxel(cx.V, u);
-    return vi >= 0 ? __ldg(&cx.V.labels[vi]) : (uint8_t)0;
+    return nearest_label(cx.V, u, vi);
   };
   for (int l = g0 + warp; l < g1; l += NW) {
     uint8_t* lrow = lbuf + (l - L0) * NS;

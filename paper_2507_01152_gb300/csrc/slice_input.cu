@@ -31,8 +31,8 @@ __global__ void slice_input_kernel(RenderParams p, const EnvItem* items, int H, 
     beam_point(P, P.lines[c], r, x, z);
   }
   const float3 u = to_voxel(M, V.inv_h, x, z);
-  const int vi = nearest_voxel(V, u);
-  const float lab = vi >= 0 ? (float)__ldg(&V.labels[vi]) : 0.f;
+  int vi;
+  const float lab = (float)nearest_label(V, u, vi);
   const float hu_v = trilinear_hu(V, u);
   const float hu = fminf(fmaxf(hu_v * 1e-3f, -1.f), 3.f);
   if (hu_raw) {

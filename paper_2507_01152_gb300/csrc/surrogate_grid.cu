@@ -30,8 +30,8 @@ __global__ void grid_slice_kernel(RenderParams p, const EnvItem* items, int H, i
   const Pose M = load_pose(p.poses, it.b, finite);
   const int r = q / W, c = q - r * W;
   const float3 u = to_voxel(M, V.inv_h, __ldg(&t.px[c]), __ldg(&t.pz[r]));
-  const int vi = nearest_voxel(V, u);
-  const float lab = vi >= 0 ? (float)__ldg(&V.labels[vi]) : 0.f;
+  int vi;
+  const float lab = (float)nearest_label(V, u, vi);
   const float hu = fminf(fmaxf(trilinear_hu(V, u) * 1e-3f, -1.f), 3.f);
   __align__(16) __nv_bfloat16 v[8];
   v[0] = __float2bfloat16_rn(0.25f * lab);

@@ -21,12 +21,24 @@ struct DevVolume {
   int nx, ny, nz;
   float inv_h;
   float h;   // voxel edge, mm (as given)
-  // Corner records of the HU grid, or null: record ((k+1)(ny+1) + j+1)(nx+1)
-  // + i+1 holds the HU of the 8 corners of the cell based at voxel (i, j, k),
-  // i in [-1, nx-1] (likewise j, k), as int16 in the order c000 c100 c010
-  // c110 c001 c101 c011 c111 (bit 0 of the corner index = x), 0 outside the
-  // grid: one 16-byte load per trilinear sample instead of eight gathers.
+  // Corner records of the HU grid, or null: one 16-byte record per cell
+  // (i, j, k), the cell based at voxel (i, j, k) for i in [-1, nx-1]
+  // (likewise j, k), holding the HU of its 8 corners as int16 in the order
+  // c000 c100 c010 c110 c001 c101 c011 c111 (bit 0 of the corner index = x),
+  // 0 outside the grid: one 16-byte load per trilinear sample instead of
+  // eight gathers.  Records go in quads along y (with J = j + 1, I = i + 1,
+  // K = k + 1: record ((K qy + J/4)(nx + 1) + I) 4 + J%4, qy = ceil((ny+1)/4)),
+  // so that one 64-byte DRAM fetch holds four cells in y: an image plane
+  // whose depth runs along y reads most of them.
   const uint4* hu8;
+  int qy;
+  // Labels in 4 x 4 x 4 bricks of 64 bytes, or null: voxel (i, j, k) at byte
+  // ((k/4 by + j/4) bx + i/4) 64 + (k%4) 16 + (j%4) 4 + i%4, bx = ceil(nx/4),
+  // by = ceil(ny/4), 0 in the padding.  A 64-byte fetch then holds a
+  // 4 x 4 x 4 neighbourhood that an oblique plane crosses, where a row-major
+  // fetch holds 64 voxels of one row.
+  const uint8_t* lab4;
+  int bx, by;
 };
 
 // per (probe, label): attenuation per sample f*alpha*dr (Np), scatter
@@ -154,14 +166,43 @@ __device__ __forceinline__ float3 to_voxel(const Pose& M, float inv_h, float x, 
   return make_float3(__fmul_rn(p.x, inv_h), __fmul_rn(p.y, inv_h), __fmul_rn(p.z, inv_h));
 }
 
-// nearest voxel: floor(u + 1/2) per axis, -1 outside the grid (NaN -> outside)
-__device__ __forceinline__ int nearest_voxel(const DevVolume& V, float3 u) {
+// nearest voxel: floor(u + 1/2) per axis; false outside the grid (NaN -> outside)
+__device__ __forceinline__ bool nearest_ijk(const DevVolume& V, float3 u, int& i, int& j, int& k) {
   const float fx = floorf(__fadd_rn(u.x, 0.5f));
   const float fy = floorf(__fadd_rn(u.y, 0.5f));
   const float fz = floorf(__fadd_rn(u.z, 0.5f));
   if (!(fx >= 0.f && fx < (float)V.nx && fy >= 0.f && fy < (float)V.ny && fz >= 0.f && fz < (float)V.nz))
-    return -1;
-  return ((int)fz * V.ny + (int)fy) * V.nx + (int)fx;
+    return false;
+  i = (int)fx;
+  j = (int)fy;
+  k = (int)fz;
+  return true;
+}
+
+// linear index of the nearest voxel, -1 outside the grid
+__device__ __forceinline__ int nearest_voxel(const DevVolume& V, float3 u) {
+  int i, j, k;
+  return nearest_ijk(V, u, i, j, k) ? (k * V.ny + j) * V.nx + i : -1;
+}
+
+// label of voxel (i, j, k) inside the grid
+__device__ __forceinline__ uint8_t label_at(const DevVolume& V, int i, int j, int k) {
+  if (V.lab4)
+    return __ldg(&V.lab4[((((k >> 2) * V.by + (j >> 2)) * V.bx + (i >> 2)) << 6) | ((k & 3) << 4) | ((j & 3) << 2) |
+                         (i & 3)]);
+  return __ldg(&V.labels[(k * V.ny + j) * V.nx + i]);
+}
+
+// label of the nearest voxel (0 outside the grid) and its linear index vi
+// (-1 outside)
+__device__ __forceinline__ uint8_t nearest_label(const DevVolume& V, float3 u, int& vi) {
+  int i, j, k;
+  if (!nearest_ijk(V, u, i, j, k)) {
+    vi = -1;
+    return 0;
+  }
+  vi = (k * V.ny + j) * V.nx + i;
+  return label_at(V, i, j, k);
 }
 
 __device__ __forceinline__ float hu_at(const DevVolume& V, int i, int j, int k) {
@@ -181,7 +222,7 @@ __device__ __forceinline__ float trilinear_hu(const DevVolume& V, float3 u) {
   float c000, c100, c010, c110, c001, c101, c011, c111;
   if (V.hu8) {
     // the sign-extended halves of each word are the int16 corner values
-    const uint4 q = __ldg(&V.hu8[((k + 1) * (V.ny + 1) + (j + 1)) * (V.nx + 1) + (i + 1)]);
+    const uint4 q = __ldg(&V.hu8[((((k + 1) * V.qy + ((j + 1) >> 2)) * (V.nx + 1) + (i + 1)) << 2) | ((j + 1) & 3)]);
     c000 = (float)((int)(q.x << 16) >> 16);
     c100 = (float)((int)q.x >> 16);
     c010 = (float)((int)(q.y << 16) >> 16);

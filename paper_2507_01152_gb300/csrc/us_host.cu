@@ -363,6 +363,7 @@ void free_sim(us_sim* s) {
   }
   for (auto* d : s->d_pair_D) cudaFree(d);
   for (auto* d : s->d_hu8) cudaFree(d);
+  for (auto* d : s->d_lab4) cudaFree(d);
   cudaFree(s->d_href);
   for (auto& kv : s->plans) {
     drop_graph(kv.second);
@@ -594,10 +595,11 @@ const char* us_status_string(us_status st) {
 
 const char* us_sim_last_error(const us_sim* s) { return s ? s->last_error.c_str() : "NULL handle"; }
 
-// Read the volumes' contents: every label must index the tissue table, and
-// the HU grid is copied into corner records (allocated once per volume; a
-// volume whose records do not fit in memory or in 31-bit indices keeps the
-// eight-gather interpolation, with identical results).  Synchronous.
+// Read the volumes' contents: every label must index the tissue table, the
+// HU grid is copied into corner records and the labels into 4 x 4 x 4
+// bricks (each allocated once per volume; a volume whose copy does not fit
+// in memory or in 31-bit indices keeps reading the caller's grid, with
+// identical results).  Synchronous.
 static us_status read_volumes(us_sim* s, cudaStream_t st) {
   cudaError_t e;
   for (size_t i = 0; i < s->vols.size(); ++i) {
@@ -609,15 +611,28 @@ static us_status read_volumes(us_sim* s, cudaStream_t st) {
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
       return cuda_fail(s, e, "label check");
     if ((int)mx >= s->n_labels) return fail(s, US_ERR_INVALID_ARG, "label outside the tissue table");
-    const long long n8 = (long long)(v.nx + 1) * (v.ny + 1) * (v.nz + 1);
+    const long long n8 = corner_records(v.nx, v.ny, v.nz), n4 = label_bricks_bytes(v.nx, v.ny, v.nz);
     if (!s->d_hu8[i] && s->opt.volume_layout == 0 && n8 < (1ll << 31) && cudaMalloc(&s->d_hu8[i], (size_t)n8 * sizeof(uint4)) != cudaSuccess) {
       cudaGetLastError();
       s->d_hu8[i] = nullptr;
     }
+    if (!s->d_lab4[i] && s->opt.volume_layout == 0 && n4 < (1ll << 31) && cudaMalloc(&s->d_lab4[i], (size_t)n4) != cudaSuccess) {
+      cudaGetLastError();
+      s->d_lab4[i] = nullptr;
+    }
     ussim::DevVolume dv = s->dev_vols[i];
     dv.hu8 = nullptr;
+    dv.lab4 = nullptr;
+    dv.qy = corner_quads_y(v.ny);
+    dv.bx = (v.nx + 3) / 4;
+    dv.by = (v.ny + 3) / 4;
     if (s->d_hu8[i] && (e = pack_corners(dv, s->d_hu8[i], st)) != cudaSuccess) return cuda_fail(s, e, "corner records");
+    if (s->d_lab4[i] && (e = pack_labels(dv, s->d_lab4[i], st)) != cudaSuccess) return cuda_fail(s, e, "label bricks");
     s->dev_vols[i].hu8 = s->d_hu8[i];
+    s->dev_vols[i].lab4 = s->d_lab4[i];
+    s->dev_vols[i].qy = dv.qy;
+    s->dev_vols[i].bx = dv.bx;
+    s->dev_vols[i].by = dv.by;
   }
   if ((e = cudaMemcpyAsync(s->d_vols, s->dev_vols.data(), s->dev_vols.size() * sizeof(ussim::DevVolume),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
@@ -686,7 +701,8 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
     }
   std::vector<DevVolume> dv;
   for (const us_volume& v : s->vols)
-    dv.push_back(DevVolume{v.labels, v.hu, v.nx, v.ny, v.nz, (float)(1.0 / (double)v.voxel_mm), v.voxel_mm, nullptr});
+    dv.push_back(DevVolume{v.labels, v.hu, v.nx, v.ny, v.nz, (float)(1.0 / (double)v.voxel_mm), v.voxel_mm, nullptr,
+                                0, nullptr, 0, 0});
   std::vector<DevProbe> dp;
   for (const ProbeHost& ph : s->probes) dp.push_back(device_probe(ph));
   std::vector<DevPair> pairs;
@@ -729,6 +745,7 @@ us_status us_sim_create(const us_volume* vols, int32_t n_vols, const us_tissue* 
   s->scratch.Y = s->scratch.R;   // the log image reuses R's storage (R is dead once AR is formed)
   s->dev_vols = dv;
   s->d_hu8.assign(dv.size(), nullptr);
+  s->d_lab4.assign(dv.size(), nullptr);
   if ((r = read_volumes(s, nullptr)) != US_OK) {
     free_sim(s);
     return r;

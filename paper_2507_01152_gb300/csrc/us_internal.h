@@ -181,8 +181,19 @@ us_status sim_check_render_args(us_sim* s, const us_env* envs, int B, const floa
 
 // label check at creation: max label of a volume
 cudaError_t max_label(const uint8_t* labels, long long n, unsigned* d_out, cudaStream_t st);
-// corner records of V's HU grid into out ((nx+1)(ny+1)(nz+1) records)
+// corner records of V's HU grid into out (corner_records(nx, ny, nz)
+// records; V.qy set)
+inline int corner_quads_y(int ny) { return (ny + 4) / 4; }
+inline long long corner_records(int nx, int ny, int nz) {
+  return (long long)(nx + 1) * corner_quads_y(ny) * 4 * (nz + 1);
+}
 cudaError_t pack_corners(const DevVolume& V, uint4* out, cudaStream_t st);
+// V's labels in 4 x 4 x 4 bricks into out (label_bricks_bytes(nx, ny, nz)
+// bytes; V.bx, V.by set)
+inline long long label_bricks_bytes(int nx, int ny, int nz) {
+  return (long long)((nx + 3) / 4) * ((ny + 3) / 4) * ((nz + 3) / 4) * 64;
+}
+cudaError_t pack_labels(const DevVolume& V, uint8_t* out, cudaStream_t st);
 
 }  // namespace ussim
 
@@ -226,6 +237,7 @@ struct us_sim {
   ussim::DevPair* d_pairs = nullptr;
   std::vector<uint8_t*> d_pair_D;
   std::vector<uint4*> d_hu8;   // corner records per volume (null entries: not built)
+  std::vector<uint8_t*> d_lab4;   // bricked labels per volume (null entries: not built)
   long long* d_href = nullptr;  // reference cumulative counts of the HU histogram matching (null: off)
   int href_nb = 0;
   float href_h0 = 0.f, href_w = 1.f;

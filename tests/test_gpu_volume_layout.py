@@ -91,3 +91,57 @@ def test_refresh_volumes_after_the_hu_grid_changes():
     sim.refresh_volumes()
     sim.close()
     fresh.close()
+
+
+def test_bricked_labels_and_corner_quads_on_a_ragged_grid():
+    """A grid whose sides are not multiples of 4 (the label bricks and the
+    corner records' y quads then end in padding): every render path, the
+    surrogate's slice sampling on the beam grid and on a square grid, and
+    the exported labels and voxel indices equal those read from the caller's
+    grid, with poses that run past every face."""
+    spec = scene.VolumeSpec(126, 130, 122, 1.0, 2, 4321)
+    lab_np, hu_np = scene.make_volume(spec)
+    wl = scene.Workload("ragged", [(spec, lab_np, hu_np)], [scene.curvilinear_probe(96, 192, 80.0, 60.0, 40.0, 96, 96),
+                                                           scene.linear_probe(64, 128, 80.0, 0.5)],
+                        np.array([[0, b % 2] for b in range(8)], np.int32), _edge_poses(spec, 8), seed=5)
+    lab, hu = torch.from_numpy(lab_np).cuda(), torch.from_numpy(hu_np).cuda()
+    a, b = _sim(wl, lab, hu, 0), _sim(wl, lab, hu, 1)
+    for kw in (dict(shape=(1, 16)), dict(shape=(1, 8)), dict(shape=(8, 32)), dict(plain=True)):
+        ga, gb = _render(a, wl.envs, wl.poses, 4, **kw), _render(b, wl.envs, wl.poses, 4, **kw)
+        for e in range(8):
+            for k in ("frame", "envelope", "logimg", "nn_index", "label"):
+                assert np.array_equal(ga[e][k], gb[e][k]), (kw, e, k)
+    assert any((g["nn_index"] < 0).mean() > 0.05 for g in ga)
+    P = torch.from_numpy(np.ascontiguousarray(wl.poses, np.float32)).cuda()
+    for H, W in ((64, 64), (37, 53)):
+        sa = torch.empty((8, H, W, 8), dtype=torch.bfloat16, device="cuda")
+        sb = torch.empty_like(sa)
+        a.sample_slices_grid(wl.envs, P, H, W, sa)
+        b.sample_slices_grid(wl.envs, P, H, W, sb)
+        torch.cuda.synchronize()
+        assert torch.equal(sa.view(torch.int16), sb.view(torch.int16))
+        assert float(sa[..., 0].float().max()) > 0      # labels were read
+    a.close()
+    b.close()
+
+
+def test_refresh_volumes_after_the_labels_change():
+    """us_sim_refresh_volumes rebuilds the bricked labels: a relabelled block
+    renders as a fresh handle reading the caller's grid renders it."""
+    wl = scene.workload_c2(4)
+    spec, lab_np, hu_np = wl.volumes[0]
+    lab, hu = torch.from_numpy(lab_np.copy()).cuda(), torch.from_numpy(hu_np).cuda()
+    envs, poses = wl.envs[:4], wl.poses[:4]
+    sim = _sim(wl, lab, hu, 0)
+    before = _render(sim, envs, poses, 2, shape=(1, 16))
+    lab[:, 60:200, 40:90] = 4           # a block of bone
+    sim.refresh_volumes()
+    after = _render(sim, envs, poses, 2, shape=(1, 16))
+    fresh = _sim(wl, lab, hu, 1)
+    want = _render(fresh, envs, poses, 2, shape=(1, 16))
+    for e in range(4):
+        for k in ("label", "envelope", "frame"):
+            assert np.array_equal(after[e][k], want[e][k]), (e, k)
+    assert any(not np.array_equal(before[e]["label"], after[e]["label"]) for e in range(4))
+    sim.close()
+    fresh.close()
