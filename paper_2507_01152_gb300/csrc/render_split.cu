@@ -269,18 +269,41 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
     u = to_voxel(cx.M, cx.V.inv_h, x, z);
     return nearest_label(cx.V, u, vi);
   };
+  // Own lines take kLabU samples a lane per step (s, s + 32, ...): every
+  // sample's label and corner-record loads are issued before any is used.
+  constexpr int kLabU = 4;
+  const bool cells = p.z_mode == 0 && cx.V.hu8 != nullptr;
   for (int l = g0 + warp; l < g1; l += NW) {
     uint8_t* lrow = lbuf + (l - L0) * NS;
     float* prow = zbuf + (l - g0) * RS;
     const float2 ln = P.lines[l];
-    for (int s = lane; s < NS; s += 32) {
-      float3 u;
-      int vi;
-      const uint8_t lb = label_of(ln, s, u, vi);
-      lrow[s] = lb;
-      prow[KA + s] = p.z_mode == 0 ? fmaxf(trilinear_hu(cx.V, u) + 1024.f, 1.f) : tis[lb].z;
-      if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + s] = vi;
-      if (p.label) p.label[cx.it.beam_off + (long long)l * NS + s] = lb;
+    for (int s = lane; s < NS; s += 32 * kLabU) {
+      float3 u[kLabU];
+      int vi[kLabU];
+      uint8_t lb[kLabU];
+      float zv[kLabU];
+#pragma unroll
+      for (int j = 0; j < kLabU; ++j) lb[j] = label_of(ln, s + 32 * j < NS ? s + 32 * j : s, u[j], vi[j]);
+      if (cells) {
+        HuCell c[kLabU];
+#pragma unroll
+        for (int j = 0; j < kLabU; ++j) c[j] = hu_cell_fetch(cx.V, u[j]);
+#pragma unroll
+        for (int j = 0; j < kLabU; ++j) zv[j] = fmaxf(hu_cell_value(c[j]) + 1024.f, 1.f);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kLabU; ++j) zv[j] = p.z_mode == 0 ? fmaxf(trilinear_hu(cx.V, u[j]) + 1024.f, 1.f) : tis[lb[j]].z;
+      }
+#pragma unroll
+      for (int j = 0; j < kLabU; ++j) {
+        const int sj = s + 32 * j;
+        if (sj < NS) {
+          lrow[sj] = lb[j];
+          prow[KA + sj] = zv[j];
+          if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + sj] = vi[j];
+          if (p.label) p.label[cx.it.beam_off + (long long)l * NS + sj] = lb[j];
+        }
+      }
     }
     float* rrow = rbuf + (l - g0) * RS;
     for (int q = lane; q < KA; q += 32) {
@@ -291,18 +314,32 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
     }
   }
   {
-    const int nl_left = g0 - L0, nh = nl_left + (L1 - g1), cpl = (NS + 31) >> 5;
-    for (int t = warp; t < nh * cpl; t += NW) {
-      const int c = t / nh, h = t - c * nh;
-      const int l = h < nl_left ? L0 + h : g1 + (h - nl_left);
-      const int lim = cx.pair.ext[l < g0 ? g0 - l : l - g1 + 1];
-      if ((c << 5) >= lim) continue;   // whole warp
-      const int s = (c << 5) + lane;
-      if (s < lim) {
-        float3 u;
-        int vi;
-        lbuf[(l - L0) * NS + s] = label_of(P.lines[l], s, u, vi);
+    // two 32-sample units a warp per step, both loads issued first
+    const int nl_left = g0 - L0, nh = nl_left + (L1 - g1), cpl = (NS + 31) >> 5, nu = nh * cpl;
+    for (int t0 = warp; t0 < nu; t0 += 2 * NW) {
+      int at[2];
+      uint8_t lv[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int t = t0 + j * NW;
+        at[j] = -1;
+        lv[j] = 0;
+        if (t < nu) {
+          const int c = t / nh, h = t - c * nh;
+          const int l = h < nl_left ? L0 + h : g1 + (h - nl_left);
+          const int lim = cx.pair.ext[l < g0 ? g0 - l : l - g1 + 1];
+          const int s = (c << 5) + lane;
+          if (s < lim) {
+            float3 u;
+            int vi;
+            at[j] = (l - L0) * NS + s;
+            lv[j] = label_of(P.lines[l], s, u, vi);
+          }
+        }
       }
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (at[j] >= 0) lbuf[at[j]] = lv[j];
     }
   }
   __syncthreads();

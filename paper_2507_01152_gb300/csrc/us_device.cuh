@@ -211,27 +211,59 @@ __device__ __forceinline__ float hu_at(const DevVolume& V, int i, int j, int k) 
              : 0.f;
 }
 
+// the trilinear blend of a cell's 8 corner values at fractions (tx, ty, tz),
+// in one fixed order
+__device__ __forceinline__ float trilinear_blend(float tx, float ty, float tz, float c000, float c100, float c010,
+                                                 float c110, float c001, float c101, float c011, float c111) {
+  const float a00 = fmaf(tx, c100 - c000, c000), a10 = fmaf(tx, c110 - c010, c010);
+  const float a01 = fmaf(tx, c101 - c001, c001), a11 = fmaf(tx, c111 - c011, c011);
+  const float b0 = fmaf(ty, a10 - a00, a00), b1 = fmaf(ty, a11 - a01, a01);
+  return fmaf(tz, b1 - b0, b0);
+}
+
+// Trilinear HU from the corner records in two steps, so that a caller can
+// issue the loads of several samples before it blends any: hu_cell_fetch
+// loads the sample's record (V.hu8 must be set), hu_cell_value blends it.
+// Together they compute exactly what trilinear_hu computes.
+struct HuCell {
+  uint4 q;
+  float tx, ty, tz;
+  bool in;   // false: the cell lies outside the grid, the value is 0
+};
+__device__ __forceinline__ HuCell hu_cell_fetch(const DevVolume& V, float3 u) {
+  const float fx = floorf(u.x), fy = floorf(u.y), fz = floorf(u.z);
+  HuCell c;
+  c.in = fx >= -1.f && fx < (float)V.nx && fy >= -1.f && fy < (float)V.ny && fz >= -1.f && fz < (float)V.nz;
+  c.tx = u.x - fx;
+  c.ty = u.y - fy;
+  c.tz = u.z - fz;
+  c.q = make_uint4(0u, 0u, 0u, 0u);
+  if (c.in) {
+    const int i = (int)fx, j = (int)fy, k = (int)fz;
+    c.q = __ldg(&V.hu8[((((k + 1) * V.qy + ((j + 1) >> 2)) * (V.nx + 1) + (i + 1)) << 2) | ((j + 1) & 3)]);
+  }
+  return c;
+}
+__device__ __forceinline__ float hu_cell_value(const HuCell& c) {
+  if (!c.in) return 0.f;
+  // the sign-extended halves of each word are the int16 corner values
+  const uint4 q = c.q;
+  return trilinear_blend(c.tx, c.ty, c.tz, (float)((int)(q.x << 16) >> 16), (float)((int)q.x >> 16),
+                         (float)((int)(q.y << 16) >> 16), (float)((int)q.y >> 16), (float)((int)(q.z << 16) >> 16),
+                         (float)((int)q.z >> 16), (float)((int)(q.w << 16) >> 16), (float)((int)q.w >> 16));
+}
+
 // trilinear HU; corners outside the grid read 0 (water).  Interior
 // footprints (the common case) skip the per-corner bounds checks.
 __device__ __forceinline__ float trilinear_hu(const DevVolume& V, float3 u) {
+  if (V.hu8) return hu_cell_value(hu_cell_fetch(V, u));
   const float fx = floorf(u.x), fy = floorf(u.y), fz = floorf(u.z);
   if (!(fx >= -1.f && fx < (float)V.nx && fy >= -1.f && fy < (float)V.ny && fz >= -1.f && fz < (float)V.nz))
     return 0.f;
   const int i = (int)fx, j = (int)fy, k = (int)fz;
   const float tx = u.x - fx, ty = u.y - fy, tz = u.z - fz;
   float c000, c100, c010, c110, c001, c101, c011, c111;
-  if (V.hu8) {
-    // the sign-extended halves of each word are the int16 corner values
-    const uint4 q = __ldg(&V.hu8[((((k + 1) * V.qy + ((j + 1) >> 2)) * (V.nx + 1) + (i + 1)) << 2) | ((j + 1) & 3)]);
-    c000 = (float)((int)(q.x << 16) >> 16);
-    c100 = (float)((int)q.x >> 16);
-    c010 = (float)((int)(q.y << 16) >> 16);
-    c110 = (float)((int)q.y >> 16);
-    c001 = (float)((int)(q.z << 16) >> 16);
-    c101 = (float)((int)q.z >> 16);
-    c011 = (float)((int)(q.w << 16) >> 16);
-    c111 = (float)((int)q.w >> 16);
-  } else if ((unsigned)i < (unsigned)(V.nx - 1) && (unsigned)j < (unsigned)(V.ny - 1) && (unsigned)k < (unsigned)(V.nz - 1)) {
+  if ((unsigned)i < (unsigned)(V.nx - 1) && (unsigned)j < (unsigned)(V.ny - 1) && (unsigned)k < (unsigned)(V.nz - 1)) {
     const int sy = V.nx, sz = V.nx * V.ny;
     const int16_t* b = V.hu + (k * V.ny + j) * V.nx + i;
     c000 = (float)__ldg(b);
@@ -252,10 +284,7 @@ __device__ __forceinline__ float trilinear_hu(const DevVolume& V, float3 u) {
     c011 = hu_at(V, i, j + 1, k + 1);
     c111 = hu_at(V, i + 1, j + 1, k + 1);
   }
-  const float a00 = fmaf(tx, c100 - c000, c000), a10 = fmaf(tx, c110 - c010, c010);
-  const float a01 = fmaf(tx, c101 - c001, c001), a11 = fmaf(tx, c111 - c011, c011);
-  const float b0 = fmaf(ty, a10 - a00, a00), b1 = fmaf(ty, a11 - a01, a01);
-  return fmaf(tz, b1 - b0, b0);
+  return trilinear_blend(tx, ty, tz, c000, c100, c010, c110, c001, c101, c011, c111);
 }
 
 __device__ __forceinline__ float impedance(int z_mode, float hu, const DevTissue& t) {
