@@ -32,21 +32,18 @@
 
 namespace ussim {
 
-// axial PSF of two padded rows in place (K zeros, NS samples, K zeros each):
-// the scatter pattern's and the reflection impulses'.  KC > 0: the
+// axial PSF of two padded rows (K zeros, NS samples, K zeros each): the
+// scatter pattern's and the reflection impulses', written as (P (x) R_imp,
+// P (x) T) pairs to dst[0 .. NS-1] (the line buffer).  KC > 0: the
 // half-width is the compile-time KC (== K) and the taps sit in registers;
 // KC = 0: any K, taps read from shared memory.  Same tap order as the plain
-// kernel.  Chunk c's results are written back only after chunk c + 1 has
-// been computed, so every read sees unfiltered data (K <= 32).
-// rmask bit i: some reflection impulse of samples 32 i .. 32 i + 31 is not
-// zero.  The impulses are >= 0, so an output chunk whose window (chunks
-// i - 1 .. i + 1, K <= 32) holds none is exactly +0, as the full sum of
-// zero taps would be: the warp skips its reflection taps there.
+// kernel.  rmask bit i: some reflection impulse of samples 32 i .. 32 i + 31
+// is not zero.  The impulses are >= 0, so an output chunk whose window
+// (chunks i - 1 .. i + 1, K <= 32) holds none is exactly +0, as the full
+// sum of zero taps would be: the warp skips its reflection taps there.
 template <int KC>
-__device__ __forceinline__ void axial_psf_rows(float* pt, float* pr, int NS, const float* w, int K, int lane,
-                                               unsigned rmask) {
-  float prev_t = 0.f, prev_r = 0.f;
-  int prev_s = -1;
+__device__ __forceinline__ void axial_psf_rows(const float* pt, const float* pr, int NS, const float* w, int K,
+                                               int lane, unsigned rmask, float2* dst) {
   const int taps = 2 * K + 1;
   float wr[KC > 0 ? 2 * KC + 1 : 1];
 #pragma unroll
@@ -54,8 +51,8 @@ __device__ __forceinline__ void axial_psf_rows(float* pt, float* pr, int NS, con
   for (int c = 0; c < NS; c += 32) {
     const int s = c + lane, ci = c >> 5;
     const bool refl = ((ci == 0 ? rmask << 1 : rmask >> (ci - 1)) & 7u) != 0;   // warp-uniform
-    float acc_t = 0.f, acc_r = 0.f;
     if (s < NS) {
+      float acc_t = 0.f, acc_r = 0.f;
       const float* qt = pt + s;
       const float* qr = pr + s;
       if constexpr (KC > 0) {
@@ -74,36 +71,23 @@ __device__ __forceinline__ void axial_psf_rows(float* pt, float* pr, int NS, con
         if (refl)
           for (int k = 0; k < taps; ++k) acc_r = fmaf(w[k], qr[k], acc_r);
       }
+      dst[s] = make_float2(acc_r, acc_t);
     }
-    __syncwarp();
-    if (prev_s >= 0 && prev_s < NS) {
-      pt[K + prev_s] = prev_t;
-      pr[K + prev_s] = prev_r;
-    }
-    __syncwarp();
-    prev_t = acc_t;
-    prev_r = acc_r;
-    prev_s = s;
   }
-  if (prev_s >= 0 && prev_s < NS) {
-    pt[K + prev_s] = prev_t;
-    pr[K + prev_s] = prev_r;
-  }
-  __syncwarp();
 }
 
-__device__ __forceinline__ void axial_psf_any(float* pt, float* pr, int NS, const float* w, int K, int lane,
-                                              unsigned rmask) {
+__device__ __forceinline__ void axial_psf_any(const float* pt, const float* pr, int NS, const float* w, int K,
+                                              int lane, unsigned rmask, float2* dst) {
   switch (K) {
-    case 1: axial_psf_rows<1>(pt, pr, NS, w, K, lane, rmask); break;
-    case 2: axial_psf_rows<2>(pt, pr, NS, w, K, lane, rmask); break;
-    case 3: axial_psf_rows<3>(pt, pr, NS, w, K, lane, rmask); break;
-    case 4: axial_psf_rows<4>(pt, pr, NS, w, K, lane, rmask); break;
-    case 5: axial_psf_rows<5>(pt, pr, NS, w, K, lane, rmask); break;
-    case 6: axial_psf_rows<6>(pt, pr, NS, w, K, lane, rmask); break;
-    case 7: axial_psf_rows<7>(pt, pr, NS, w, K, lane, rmask); break;
-    case 8: axial_psf_rows<8>(pt, pr, NS, w, K, lane, rmask); break;
-    default: axial_psf_rows<0>(pt, pr, NS, w, K, lane, rmask); break;
+    case 1: axial_psf_rows<1>(pt, pr, NS, w, K, lane, rmask, dst); break;
+    case 2: axial_psf_rows<2>(pt, pr, NS, w, K, lane, rmask, dst); break;
+    case 3: axial_psf_rows<3>(pt, pr, NS, w, K, lane, rmask, dst); break;
+    case 4: axial_psf_rows<4>(pt, pr, NS, w, K, lane, rmask, dst); break;
+    case 5: axial_psf_rows<5>(pt, pr, NS, w, K, lane, rmask, dst); break;
+    case 6: axial_psf_rows<6>(pt, pr, NS, w, K, lane, rmask, dst); break;
+    case 7: axial_psf_rows<7>(pt, pr, NS, w, K, lane, rmask, dst); break;
+    case 8: axial_psf_rows<8>(pt, pr, NS, w, K, lane, rmask, dst); break;
+    default: axial_psf_rows<0>(pt, pr, NS, w, K, lane, rmask, dst); break;
   }
 }
 
@@ -273,6 +257,7 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
   // sample's label and corner-record loads are issued before any is used.
   constexpr int kLabU = 4;
   const bool cells = p.z_mode == 0 && cx.V.hu8 != nullptr;
+  const bool exports = p.nn_index != nullptr || p.label != nullptr;   // debug exports
   for (int l = g0 + warp; l < g1; l += NW) {
     uint8_t* lrow = lbuf + (l - L0) * NS;
     float* prow = zbuf + (l - g0) * RS;
@@ -300,8 +285,14 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
         if (sj < NS) {
           lrow[sj] = lb[j];
           prow[KA + sj] = zv[j];
-          if (p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + sj] = vi[j];
-          if (p.label) p.label[cx.it.beam_off + (long long)l * NS + sj] = lb[j];
+        }
+      }
+      if (exports) {
+#pragma unroll
+        for (int j = 0; j < kLabU; ++j) {
+          const int sj = s + 32 * j;
+          if (sj < NS && p.nn_index) p.nn_index[cx.it.beam_off + (long long)l * NS + sj] = vi[j];
+          if (sj < NS && p.label) p.label[cx.it.beam_off + (long long)l * NS + sj] = lb[j];
         }
       }
     }
@@ -372,9 +363,7 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
                              posf, cx.it.vol);
     rmask = __reduce_or_sync(kFull, rmask);
     __syncwarp();
-    axial_psf_any(prow, rrow, NS, wax, KA, lane, rmask);
-    float2* dst = a.beam + cx.it.beam_off + (long long)l * NS;
-    for (int s = lane; s < NS; s += 32) dst[s] = make_float2(rrow[KA + s], row[s]);
+    axial_psf_any(prow, rrow, NS, wax, KA, lane, rmask, a.beam + cx.it.beam_off + (long long)l * NS);
   }
   if (a.done) {
     __syncthreads();
