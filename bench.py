@@ -623,7 +623,7 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         sim.autotune(wl.envs, poses, frames, tune_cache, stream=stream)
     tuning = sim.get_tuning()
-    sim.set_tuning(tuning["cluster_size"], tuning["warps_per_cta"], 1, tuning["persistent"])
+    sim.set_tuning(tuning["cluster_size"], tuning["warps_per_cta"], 1, tuning["persistent"], tuning["wedge_lines"])
     tuning = sim.get_tuning()
     two_grids = tuning["cluster_size"] == 1 and not tuning["persistent"]
     render = lambda k: sim.render(None, poses, seed, k, frames, stream=stream, envs_c=envs_c)

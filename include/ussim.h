@@ -162,16 +162,17 @@ typedef struct {
  *   cluster per environment frame (the frame stays in distributed shared
  *   memory); warps_per_cta 8, 16 or 32 (4-CTA clusters: 16 or 32).
  * cluster_size 1: two-pass path without clusters, warps_per_cta (8, 16 or
- *   32) lines per pass-A block; pass B works on tiles of up to 32 lines x
- *   128 samples.  The axially filtered lines go through a global buffer of
+ *   32) lines per pass-A block; pass B works on tiles of wedge_lines (8, 16
+ *   or 32; 0: the widest whose buffers fit four blocks per SM, else three,
+ *   two, one) lines x 128 samples.  The axially filtered lines go through a global buffer of
  *   the batch's beam size, allocated on first use per batch signature.
  *   persistent 0: the two passes are two grids; 1: one cooperative grid of
  *   resident blocks takes pass-A groups, then pass-B tiles, from a counter,
  *   and a tile starts as soon as the groups holding its lines are written
  *   (fills the last wave of a small batch).  Same frames as the cluster
  *   kernel either way.
- * Default after us_sim_create: the first of {1, 16, 1, 0}, {1, 8, 1, 0},
- * {1, 32, 1, 0}, {8, 32, 1, 0}, {16, 16, 1, 0}, {16, 8, 1, 0} that fits the
+ * Default after us_sim_create: the first of {1, 16, 1, 0, 0}, {1, 8, 1, 0, 0},
+ * {1, 32, 1, 0, 0}, {8, 32, 1, 0, 0}, {16, 16, 1, 0, 0}, {16, 8, 1, 0, 0} that fits the
  * probe set.  If none fits, the simulator is still created: the batched
  * entry points then return US_ERR_UNSUPPORTED and us_sim_render_plain
  * renders. */
@@ -183,6 +184,8 @@ typedef struct {
                             caller's stream is itself being captured) */
   int32_t persistent;    /* two-pass path: 0 two grids, 1 one persistent grid;
                             must be 0 for the cluster path */
+  int32_t wedge_lines;   /* two-pass path: pass-B tile lines, 0 (widest that
+                            fits), 8, 16 or 32; must be 0 for the cluster path */
 } us_tuning;
 
 /* Create a simulator (the per-environment assets of Sec. 4 "Ultrasound

@@ -571,6 +571,7 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
   // else three, two, one
   for (int per_sm : {4, 3, 2, 1})
   for (int GB : {32, 16, 8}) {
+    if (sh.GB_req && GB != sh.GB_req) continue;
     long long ab = 0, yb = 0;
     int gi = 0;
     for (const ProbeHost& ph : probes) {

@@ -405,6 +405,7 @@ void free_sim(us_sim* s) {
 us_status apply_split(us_sim* s, const us_tuning& t) {
   SplitShape sh;
   sh.G = t.warps_per_cta;
+  sh.GB_req = t.wedge_lines;
   sh.persistent = t.persistent != 0;
   if (!split_shape_fits(sh, s->probes, s->n_labels))
     return fail(s, US_ERR_UNSUPPORTED, "probe lines per block do not fit in shared memory for the two-pass path");
@@ -444,6 +445,9 @@ us_status apply_tuning(us_sim* s, const us_tuning& t) {
   if (t.use_graph & ~1) return fail(s, US_ERR_INVALID_ARG, "use_graph must be 0 or 1");
   if ((t.persistent & ~1) || (t.persistent && cs != 1))
     return fail(s, US_ERR_INVALID_ARG, "persistent must be 0 or 1, and 0 for the cluster path");
+  if ((t.wedge_lines != 0 && t.wedge_lines != 8 && t.wedge_lines != 16 && t.wedge_lines != 32) ||
+      (t.wedge_lines && cs != 1))
+    return fail(s, US_ERR_INVALID_ARG, "wedge_lines must be 0, 8, 16 or 32, and 0 for the cluster path");
   if (cs == 1) {
     if (nw != 8 && nw != 16 && nw != 32) return fail(s, US_ERR_INVALID_ARG, "two-pass path takes 8, 16 or 32 warps");
     return apply_split(s, t);
@@ -506,7 +510,7 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
   void* fargs[2] = {&pp, &lay};
   void* sargs[2] = {&pp, &sa};
   if (!pl->gexec || pl->g_cs != s->tuning.cluster_size || pl->g_nw != s->tuning.warps_per_cta ||
-      pl->g_pers != s->tuning.persistent) {
+      pl->g_pers != s->tuning.persistent || pl->g_gb != s->split.GB) {
     drop_graph(*pl);
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(s, e, "graph capture");
@@ -547,6 +551,7 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
     pl->g_cs = s->tuning.cluster_size;
     pl->g_nw = s->tuning.warps_per_cta;
     pl->g_pers = s->tuning.persistent;
+    pl->g_gb = s->split.GB;
     if ((e = cudaGraphLaunch(pl->gexec, st)) != cudaSuccess) return cuda_fail(s, e, "graph launch");
     return US_OK;
   }
@@ -1290,29 +1295,38 @@ us_status us_sim_autotune(us_sim* s, const us_env* envs, int32_t B, const float*
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "r")) {
       char line[768];
-      int cs = 0, nw = 0, pg = 0;
+      int cs = 0, nw = 0, pg = 0, wl = 0;
       bool found = false;
       while (std::fgets(line, sizeof line, f)) {
         const size_t n = std::strlen(sig);
-        if (std::strncmp(line, sig, n) == 0 && std::sscanf(line + n, " cs=%d nw=%d pg=%d", &cs, &nw, &pg) == 3)
+        int c0 = 0, n0 = 0, p0 = 0, w0 = 0;
+        const int got = std::strncmp(line, sig, n) == 0
+                            ? std::sscanf(line + n, " cs=%d nw=%d pg=%d wl=%d", &c0, &n0, &p0, &w0)
+                            : 0;
+        if (got >= 3) {   // lines written before the wedge choice have no wl: the widest wedge
+          cs = c0, nw = n0, pg = p0, wl = got == 4 ? w0 : 0;
           found = true;
+        }
       }
       std::fclose(f);
       if (found) {
-        us_tuning t{cs, nw, keep_graph, pg};
+        us_tuning t{cs, nw, keep_graph, pg, wl};
         if (apply_tuning(s, t) == US_OK) return US_OK;
       }
     }
   }
-  static const int cand[][3] = {{8, 32, 0}, {8, 16, 0}, {8, 8, 0}, {16, 32, 0}, {16, 16, 0}, {16, 8, 0},
-                                {4, 32, 0}, {4, 16, 0}, {1, 32, 0}, {1, 16, 0}, {1, 8, 0},
-                                {1, 32, 1}, {1, 16, 1}, {1, 8, 1}};
+  // (cluster size, warps, persistent, pass-B wedge lines)
+  static const int cand[][4] = {
+      {8, 32, 0, 0},  {8, 16, 0, 0},  {8, 8, 0, 0},   {16, 32, 0, 0}, {16, 16, 0, 0}, {16, 8, 0, 0},
+      {4, 32, 0, 0},  {4, 16, 0, 0},  {1, 32, 0, 32}, {1, 32, 0, 16}, {1, 32, 0, 8},  {1, 16, 0, 32},
+      {1, 16, 0, 16}, {1, 16, 0, 8},  {1, 8, 0, 32},  {1, 8, 0, 16},  {1, 8, 0, 8},   {1, 32, 1, 32},
+      {1, 32, 1, 16}, {1, 16, 1, 32}, {1, 16, 1, 16}, {1, 8, 1, 32},  {1, 8, 1, 16},  {1, 8, 1, 8}};
   float best = 1e30f;
-  int best_cs = 0, best_nw = 0, best_pg = 0;
+  int best_cs = 0, best_nw = 0, best_pg = 0, best_wl = 0;
   cudaEvent_t a, b2;
   if ((e = cudaEventCreate(&a)) != cudaSuccess || (e = cudaEventCreate(&b2)) != cudaSuccess) return cuda_fail(s, e, "events");
   for (const auto& c : cand) {
-    us_tuning t{c[0], c[1], 0, c[2]};
+    us_tuning t{c[0], c[1], 0, c[2], c[3]};
     if (apply_tuning(s, t) != US_OK) continue;
     bool ok = true;
     for (int w = 0; w < 2 && ok; ++w)
@@ -1329,16 +1343,17 @@ us_status us_sim_autotune(us_sim* s, const us_env* envs, int32_t B, const float*
       best_cs = c[0];
       best_nw = c[1];
       best_pg = c[2];
+      best_wl = c[3];
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b2);
   if (!best_cs) return fail(s, US_ERR_UNSUPPORTED, "no launch shape fits this probe set");
-  us_tuning t{best_cs, best_nw, keep_graph, best_pg};
+  us_tuning t{best_cs, best_nw, keep_graph, best_pg, best_wl};
   if ((r = apply_tuning(s, t)) != US_OK) return r;
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "a")) {
-      std::fprintf(f, "%s cs=%d nw=%d pg=%d ms=%.4f\n", sig, best_cs, best_nw, best_pg, best / 5.0f);
+      std::fprintf(f, "%s cs=%d nw=%d pg=%d wl=%d ms=%.4f\n", sig, best_cs, best_nw, best_pg, best_wl, best / 5.0f);
       std::fclose(f);
     }
   }

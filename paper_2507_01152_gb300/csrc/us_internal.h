@@ -95,6 +95,7 @@ struct SplitArgs {
 struct SplitShape {
   int G = 32;    // pass A lines per block (the tuning's warps_per_cta)
   int GB = 32;   // pass B lines per wedge: the widest whose buffers fit
+  int GB_req = 0;   // requested pass B lines per wedge (0: the widest that fits)
   SplitArgs args{};
   size_t smem_lines = 0, smem_image = 0;
   bool persistent = false;        // one persistent grid instead of two
@@ -222,7 +223,7 @@ struct us_plan {
   cudaGraphExec_t gexec = nullptr;
   std::vector<cudaGraphNode_t> gnodes;
   std::vector<cudaKernelNodeParams> gkps;
-  int g_cs = 0, g_nw = 0;
+  int g_cs = 0, g_nw = 0, g_gb = 0;   // captured graph's shape (pass B wedge lines)
 };
 
 struct us_sim {

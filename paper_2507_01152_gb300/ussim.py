@@ -57,7 +57,7 @@ class us_env(C.Structure):
 
 class us_tuning(C.Structure):
     _fields_ = [("cluster_size", C.c_int32), ("warps_per_cta", C.c_int32), ("use_graph", C.c_int32),
-                ("persistent", C.c_int32)]
+                ("persistent", C.c_int32), ("wedge_lines", C.c_int32)]
 
 
 class us_surr_config(C.Structure):
@@ -426,10 +426,10 @@ class Sim:
         self._check(self._lib.us_sim_get_tuning(self.h, C.byref(t)))
         return {k: getattr(t, k) for k, _ in us_tuning._fields_}
 
-    def set_tuning(self, cluster_size, warps_per_cta, use_graph=None, persistent=0):
+    def set_tuning(self, cluster_size, warps_per_cta, use_graph=None, persistent=0, wedge_lines=0):
         if use_graph is None:
             use_graph = self.get_tuning()["use_graph"]
-        t = us_tuning(cluster_size, warps_per_cta, use_graph, persistent)
+        t = us_tuning(cluster_size, warps_per_cta, use_graph, persistent, wedge_lines)
         self._check(self._lib.us_sim_set_tuning(self.h, C.byref(t)))
 
     def autotune(self, envs, poses, frames, cache_path=None, stream=None):

@@ -522,3 +522,32 @@ def test_same_signature_on_two_streams_overlaps_safely(c2, shape):
                 assert np.array_equal(outs[k].cpu().numpy(), alone[k])
     finally:
         sim.set_tuning(old["cluster_size"], old["warps_per_cta"], old["use_graph"], old.get("persistent", 0))
+
+
+@pytest.mark.parametrize("nw,pers", [(16, 0), (8, 0), (16, 1)])
+def test_pass_b_wedge_widths_agree(nw, pers):
+    """Pass-B tiles of 8, 16 or 32 lines (us_tuning.wedge_lines) give the
+    frames of the plain per-environment kernels bit for bit, on a batch that
+    mixes a linear and two curvilinear probes; a width outside {0, 8, 16,
+    32}, or one given to the cluster path, is refused."""
+    from paper_2507_01152_gb300.ussim import UsError, US_ERR_INVALID_ARG
+    spec = scene.VolumeSpec(128, 128, 128, 1.0, 2, 77)
+    lab, hu = scene.make_volume(spec)
+    probes = [scene.linear_probe(64, 128, 80.0, 0.5), scene.curvilinear_probe(96, 192, 80.0, 60.0, 40.0, 96, 96),
+              scene.curvilinear_probe(128, 256, 80.0, 60.0, 40.0, 128, 128)]
+    envs = np.array([[0, b % 3] for b in range(9)], np.int32)
+    wl = scene.Workload("mix", [(spec, lab, hu)], probes, envs, scene.dorsal_poses(spec, 9, 12), seed=3)
+    sim = gpu_sim(wl)
+    ref = render_gpu(sim, wl.envs, wl.poses, 8, 1, path=1, debug=False)
+    for wedge in (8, 16, 32, 0):
+        sim.set_tuning(1, nw, 1, pers, wedge)
+        assert sim.get_tuning()["wedge_lines"] == wedge
+        for step in range(2):      # the second call replays the graph captured for this width
+            got = render_gpu(sim, wl.envs, wl.poses, 8, 1, path=0, debug=False)
+            for x, y in zip(ref, got):
+                assert np.array_equal(x["frame"], y["frame"]), (wedge, step)
+    for bad in ((1, 16, 1, 0, 12), (8, 32, 1, 0, 16)):
+        with pytest.raises(UsError) as e:
+            sim.set_tuning(*bad)
+        assert e.value.status == US_ERR_INVALID_ARG
+    sim.close()
