@@ -102,7 +102,7 @@ __device__ __forceinline__ void axial_psf_any(const float* pt, const float* pr, 
 // KC > 0: K is the compile-time KC and the taps sit in registers; each
 // staged row is read once and added into the (up to kLatLines) sums it
 // reaches, in the same order.  KC = 0: any K, taps read from shared memory.
-constexpr int kLatLines = 2;
+constexpr int kLatLines = 3;
 template <int KC>
 __device__ __forceinline__ void lateral_psf(const RenderParams& p, const DevProbe& P, long long beam_off,
                                             const float2* abuf, float* ybuf, const float* wlat, int NS, int K, int w0,
