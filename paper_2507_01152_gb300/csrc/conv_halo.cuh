@@ -64,9 +64,16 @@ struct HaloCfg {
 struct HaloArgs {
   const __nv_bfloat16* w;   // [COUT][3][3][CIN]
   const float* bias;        // [COUT]
-  __nv_bfloat16* y;         // output view: pixel p at y + p * y_cs + y_co
+  __nv_bfloat16* y;         // output view: pixel p at y + p * y_cs + y_co (null: not stored)
   int y_cs, y_co, relu;
   int B, H, W, tiles_y, tiles_x, n_tiles;
+  // optional fused 1 x 1 head (COUT = 32): head_out[p] = sigmoid(head_b[0] +
+  // sum_c y[p][c] head_w[c]) over the BF16 outputs; each group of 8
+  // channels summed in channel order, then head_b and the group sums in
+  // group order
+  const float* head_w = nullptr;
+  const float* head_b = nullptr;
+  float* head_out = nullptr;
 };
 
 template <int CIN, int COUT>
@@ -210,7 +217,9 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
       tile_of(g, b, y0, x0);
       const int yy = y0 + (m >> 3), xx = x0 + (m & 7);
       const bool valid = yy < a.H && xx < a.W;
-      __nv_bfloat16* dst = a.y + ((size_t)((size_t)b * a.H + yy) * a.W + xx) * a.y_cs + a.y_co;
+      const size_t pix = (size_t)((size_t)b * a.H + yy) * a.W + xx;
+      __nv_bfloat16* dst = a.y ? a.y + pix * a.y_cs + a.y_co : nullptr;
+      float zg[COUT / 8];   // the fused head's group sums
       const uint32_t acc = tmem + (uint32_t)(w * 2 + q) * COUT + ((uint32_t)(qd * 32) << 16);
       // 32 columns in flight per wait
 #pragma unroll
@@ -231,7 +240,23 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
             const float t = __uint_as_float(r[c + i]) + __ldg(&a.bias[c0 + c + i]);
             o[i] = __float2bfloat16_rn(a.relu ? fmaxf(t, 0.f) : t);
           }
-          if (valid) *reinterpret_cast<uint4*>(dst + c0 + c) = *reinterpret_cast<const uint4*>(o);
+          if (valid && dst) *reinterpret_cast<uint4*>(dst + c0 + c) = *reinterpret_cast<const uint4*>(o);
+          if constexpr (COUT == 32) {
+            if (a.head_out) {
+              float t = 0.f;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) t = fmaf(__bfloat162float(o[i]), __ldg(&a.head_w[c + i]), t);
+              zg[c >> 3] = t;
+            }
+          }
+        }
+      }
+      if constexpr (COUT == 32) {
+        if (a.head_out && valid) {
+          float z = __ldg(a.head_b);
+#pragma unroll
+          for (int k = 0; k < COUT / 8; ++k) z += zg[k];
+          a.head_out[pix] = 1.f / (1.f + expf(-z));
         }
       }
     }

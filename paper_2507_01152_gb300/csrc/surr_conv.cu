@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include "conv_halo.cuh"
+#include "surr_internal.h"
 #include "ussim_surrogate.h"
 #include "umma_tma.cuh"
 
@@ -668,7 +669,8 @@ cudaError_t gemm_bn(int bn, const Ld& ld, const Ep& ep, int M, int N, int K, uns
 // has no instantiation or the tensor map cannot describe the input.
 template <int CIN, int COUT>
 bool halo_fwd(cudaError_t& e, View x, const bf16* w, const float* bias, OutView y, int relu, int B, int H, int W,
-              unsigned* err, cudaStream_t st) {
+              unsigned* err, cudaStream_t st, const float* head_w = nullptr, const float* head_b = nullptr,
+              float* head_out = nullptr) {
   using Cf = HaloCfg<CIN, COUT>;
   CUtensorMap m;
   const uint64_t pitch = (uint64_t)x.cs * 2;
@@ -683,6 +685,9 @@ bool halo_fwd(cudaError_t& e, View x, const bf16* w, const float* bias, OutView 
   a.y_cs = y.cs;
   a.y_co = y.co;
   a.relu = relu;
+  a.head_w = head_w;
+  a.head_b = head_b;
+  a.head_out = head_out;
   a.B = B;
   a.H = H;
   a.W = W;
@@ -710,6 +715,23 @@ bool halo_fwd_any(cudaError_t& e, View x, int Cin, int Cout, const bf16* w, cons
   if (Cin == 64 && Cout == 32) return halo_fwd<64, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 32 && Cout == 64) return halo_fwd<32, 64>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 64 && Cout == 64) return halo_fwd<64, 64>(e, x, w, bias, y, relu, B, H, W, err, st);
+  return false;
+}
+
+bool aligned16(const void* p);
+
+bool conv3x3_head_fwd(cudaError_t& e, const uint16_t* x, int x_cs, int x_co, int Cin, const uint16_t* w,
+                      const float* bias, uint16_t* y, int y_cs, int y_co, int B, int H, int W, const float* head_w,
+                      const float* head_b, float* head_out, unsigned* err, cudaStream_t st) {
+  if (!x || !w || !bias || !head_w || !head_b || !head_out || (x_cs % 8) || (x_co % 8) || x_co + Cin > x_cs ||
+      !aligned16(x) || !aligned16(w) || (y && ((y_cs % 8) || (y_co % 8) || y_co + 32 > y_cs || !aligned16(y))))
+    return false;
+  const View xv{(const bf16*)x, x_cs, x_co};
+  const OutView yv{(bf16*)y, y_cs, y_co};
+  if (Cin == 32)
+    return halo_fwd<32, 32>(e, xv, (const bf16*)w, bias, yv, 1, B, H, W, err, st, head_w, head_b, head_out);
+  if (Cin == 64)
+    return halo_fwd<64, 32>(e, xv, (const bf16*)w, bias, yv, 1, B, H, W, err, st, head_w, head_b, head_out);
   return false;
 }
 

@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "surr_internal.h"
 #include "ussim_surrogate.h"
 
 namespace ussim {
@@ -42,8 +43,9 @@ struct LayerDesc {
 // ------------------------------------------------------------------ kernels
 
 // out[p] = sigmoid(sum_c f[p][c] w[c] + b); a pixel's channels are read
-// as 16-byte vectors (C a multiple of 8, rows 16-byte aligned), summed in
-// channel order
+// as 16-byte vectors (C a multiple of 8, rows 16-byte aligned).  Each group
+// of 8 channels is summed in channel order, then b and the group sums in
+// group order (the fused head of the last convolution sums the same way).
 __global__ void head_fwd(const bf16* f, int C, const float* w, const float* b, float* out, long long P) {
   __shared__ float sw[256];
   for (int i = threadIdx.x; i < C; i += blockDim.x) sw[i] = w[i];
@@ -55,8 +57,10 @@ __global__ void head_fwd(const bf16* f, int C, const float* w, const float* b, f
   for (int c8 = 0; c8 < C / 8; ++c8) {
     const uint4 q = __ldg(fp + c8);
     const bf16* h = reinterpret_cast<const bf16*>(&q);
+    float zg = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) z = fmaf(__bfloat162float(h[i]), sw[c8 * 8 + i], z);
+    for (int i = 0; i < 8; ++i) zg = fmaf(__bfloat162float(h[i]), sw[c8 * 8 + i], zg);
+    z += zg;
   }
   out[p] = 1.f / (1.f + expf(-z));
 }
@@ -621,13 +625,27 @@ std::vector<Wiring> wiring(const us_surr* s) {
   };
 }
 
-us_status forward_impl(us_surr* s, int B, cudaStream_t st) {
+// keep_act: store the last convolution's activation (the backward pass
+// reads it); without it the head may be fused into that convolution
+us_status forward_impl(us_surr* s, int B, cudaStream_t st, bool keep_act = true) {
   const auto wr = wiring(s);
+  const LayerDesc& hd = s->layers.back();
+  bool head_done = false;
   for (size_t i = 0; i + 1 < s->layers.size(); ++i) {
     const LayerDesc& d = s->layers[i];
     const auto& bi = s->bufs[wr[i].in];
     const auto& bo = s->bufs[wr[i].out];
     us_status r;
+    if (i + 2 == s->layers.size() && d.kind == 0 && d.stride == 1 && d.cout == 32 && hd.cin == 32) {
+      cudaError_t e = cudaSuccess;
+      if (surr::conv3x3_head_fwd(e, A(s, wr[i].in), bi.C, wr[i].in_co, d.cin, Wf(s, (int)i), s->p + d.b_off,
+                                 keep_act ? Aw(s, wr[i].out) : nullptr, bo.C, wr[i].out_co, B, d.hin, d.win,
+                                 s->p + hd.w_off, s->p + hd.b_off, s->out, s->err, st)) {
+        if (e != cudaSuccess) return cfail(s, e, "last convolution with the head");
+        head_done = true;
+        continue;
+      }
+    }
     if (d.kind == 0)
       r = us_conv3x3_fwd(A(s, wr[i].in), bi.C, wr[i].in_co, Wf(s, (int)i), s->p + d.b_off, Aw(s, wr[i].out), bo.C,
                          wr[i].out_co, B, d.hin, d.win, d.cin, d.cout, d.stride, 1, s->err, st);
@@ -636,9 +654,9 @@ us_status forward_impl(us_surr* s, int B, cudaStream_t st) {
                           wr[i].out_co, B, d.hin, d.win, d.cin, d.cout, 1, s->err, st);
     if (r != US_OK) return fail(s, r, "forward layer " + std::to_string(i));
   }
-  const LayerDesc& hd = s->layers.back();
   const long long P = (long long)B * s->cfg.height * s->cfg.width;
-  head_fwd<<<blocks(P), 256, 0, st>>>(s->bufs[B_X0].a, hd.cin, s->p + hd.w_off, s->p + hd.b_off, s->out, P);
+  if (!head_done)
+    head_fwd<<<blocks(P), 256, 0, st>>>(s->bufs[B_X0].a, hd.cin, s->p + hd.w_off, s->p + hd.b_off, s->out, P);
   const auto& e3 = s->bufs[B_E3];
   pool_features<<<B, 1024, 0, st>>>(e3.a, e3.H * e3.W, e3.C, s->feat);
   cudaError_t e = cudaGetLastError();
@@ -987,7 +1005,7 @@ us_status us_surr_forward(us_surr* s, const uint16_t* x, float* y, int32_t B, vo
   if (!x || !y || B < 1 || B > s->cfg.max_batch || !aligned16(x)) return fail(s, US_ERR_INVALID_ARG, "bad forward arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   s->bufs[B_IN].a = const_cast<bf16*>(reinterpret_cast<const bf16*>(x));
-  TRY(forward_impl(s, B, st));
+  TRY(forward_impl(s, B, st, false));
   const size_t P = (size_t)B * s->cfg.height * s->cfg.width;
   cudaError_t e = cudaMemcpyAsync(y, s->out, P * 4, cudaMemcpyDeviceToDevice, st);
   s->bufs[B_IN].a = nullptr;
