@@ -55,7 +55,7 @@ struct HaloCfg {
   static constexpr int S = (S0 > 8 ? 8 : S0) / X * X;
   static constexpr int kEpiGroups = 2;                          // epilogue groups of 4 warps, alternate tiles
   static constexpr int THREADS = 32 * (1 + X + 4 * kEpiGroups);
-  static constexpr uint32_t SMEM = WBYTES + S * STAGE + 128;   // + alignment slack
+  static constexpr uint32_t SMEM = WBYTES + S * STAGE + 4 * COUT + 128;   // + bias, alignment slack
   static_assert((CIN == 8 || CIN % 16 == 0) && (COUT == 32 || COUT == 64), "halo conv shapes");
   static_assert(S >= X, "stages do not fit");
   static_assert(2 * X * COUT <= 512, "accumulators exceed TMEM");
@@ -209,6 +209,11 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
     const int grp = (warp - 1 - X) >> 2;
     const int qd = warp & 3;               // TMEM lane quarter this warp may read
     const int m = qd * 32 + lane;          // tile row: pixel (m / 8, m % 8)
+    // the bias, staged once in shared memory (after the boxes) by the
+    // epilogue warps and read as broadcasts; named barrier 1 joins only them
+    float* sbias = reinterpret_cast<float*>(box + (size_t)S * C::STAGE);
+    for (int i = (warp - 1 - X) * 32 + lane; i < COUT; i += 32 * 4 * C::kEpiGroups) sbias[i] = __ldg(&a.bias[i]);
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * 4 * C::kEpiGroups));
     for (int g = grp; g < n_local; g += C::kEpiGroups) {
       const int w = g % X, j = g / X, q = j & 1;
       if (!wait_or_abort(&tfull[w][q], (uint32_t)((j / 2) & 1), &abort_flag, err)) break;
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
           __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const float t = __uint_as_float(r[c + i]) + __ldg(&a.bias[c0 + c + i]);
+            const float t = __uint_as_float(r[c + i]) + sbias[c0 + c + i];
             o[i] = __float2bfloat16_rn(a.relu ? fmaxf(t, 0.f) : t);
           }
           if (valid && dst) *reinterpret_cast<uint4*>(dst + c0 + c) = *reinterpret_cast<const uint4*>(o);
