@@ -114,16 +114,36 @@ struct ConvFwdLoader {
   }
 };
 
+// 16 consecutive bias values (the same addresses in every lane: broadcast
+// loads), four 16-byte loads where the run is 16-byte aligned
+__device__ __forceinline__ void load_bias16(const float* b, float* out) {
+  if ((reinterpret_cast<uintptr_t>(b) & 15u) == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(b) + i);
+      out[4 * i] = q.x;
+      out[4 * i + 1] = q.y;
+      out[4 * i + 2] = q.z;
+      out[4 * i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) out[i] = __ldg(b + i);
+  }
+}
+
 struct BiasActStore {
   OutView y;
   const float* bias;
   int relu;
   __device__ void store(int m, int n0, const float* v, bool valid) const {
     if (!valid) return;
+    float bv[16];
+    load_bias16(bias + n0, bv);
     __align__(16) bf16 o[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      float t = v[i] + __ldg(&bias[n0 + i]);
+      float t = v[i] + bv[i];
       o[i] = __float2bfloat16_rn(relu ? fmaxf(t, 0.f) : t);
     }
     uint4* dst = reinterpret_cast<uint4*>(y.p + (size_t)m * y.cs + y.co + n0);
@@ -279,10 +299,12 @@ struct ConvTStore {
     int b, yy, xx;
     in.pix(m, b, yy, xx);
     const size_t op = ((size_t)(b * 2 * in.H + 2 * yy + dyy) * (2 * in.W) + 2 * xx + dxx);
+    float bv[16];
+    load_bias16(bias + co, bv);
     __align__(16) bf16 o[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      float t = v[i] + __ldg(&bias[co + i]);
+      float t = v[i] + bv[i];
       o[i] = __float2bfloat16_rn(relu ? fmaxf(t, 0.f) : t);
     }
     uint4* dst = reinterpret_cast<uint4*>(y.p + op * y.cs + y.co + co);
