@@ -205,15 +205,18 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 // a batch signature's plan is per stream: renders of the same signature on
 // different streams get their own line buffer, synchronisation words, work
-// counter and graph, so they may overlap
-std::string plan_key(const us_env* envs, int B, cudaStream_t st) {
+// counter and graph, so they may overlap.  b0: the batch is envs b0 ..
+// b0 + B - 1 of a larger caller batch (noise counters and poses keep the
+// caller's indices)
+std::string plan_key(const us_env* envs, int B, cudaStream_t st, int b0) {
   std::string k(reinterpret_cast<const char*>(envs), (size_t)B * sizeof(us_env));
   k.append(reinterpret_cast<const char*>(&st), sizeof st);
+  k.append(reinterpret_cast<const char*>(&b0), sizeof b0);
   return k;
 }
 
-us_status get_plan(us_sim* s, const us_env* envs, int B, us_plan** out, cudaStream_t st) {
-  std::string key = plan_key(envs, B, st);
+us_status get_plan(us_sim* s, const us_env* envs, int B, us_plan** out, cudaStream_t st, int b0 = 0) {
+  std::string key = plan_key(envs, B, st, b0);
   auto it = s->plans.find(key);
   if (it != s->plans.end()) {
     *out = &it->second;
@@ -228,7 +231,7 @@ us_status get_plan(us_sim* s, const us_env* envs, int B, us_plan** out, cudaStre
       return fail(s, US_ERR_INVALID_ARG, "env " + std::to_string(b) + " has an out-of-range volume or probe id");
     const us_probe& p = s->probes[e.probe_id].desc;
     EnvItem item;
-    item.b = b;
+    item.b = b0 + b;
     item.vol = e.volume_id;
     item.probe = e.probe_id;
     item.pair = e.volume_id * n_probes + e.probe_id;
@@ -311,11 +314,11 @@ us_status check_render_args(us_sim* s, const us_env* envs, int B, const float* p
 
 us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, uint64_t seed, uint64_t step,
                     float* frames, float* envelope, float* logimg, int32_t* nn, uint8_t* label, int path,
-                    cudaStream_t st) {
+                    cudaStream_t st, int b0 = 0) {
   us_status r = check_render_args(s, envs, B, poses, frames);
   if (r != US_OK || B == 0) return r;
   us_plan* pl;
-  if ((r = get_plan(s, envs, B, &pl, st)) != US_OK) return r;
+  if ((r = get_plan(s, envs, B, &pl, st, b0)) != US_OK) return r;
   RenderParams p = base_params(s, poses, seed, step, frames);
   p.work = pl->d_work;
   p.envelope = envelope;
@@ -350,6 +353,9 @@ us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, ui
 void free_sim(us_sim* s) {
   if (!s) return;
   cudaDeviceSynchronize();
+  for (cudaEvent_t& ev : s->copy_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   for (auto& ph : s->probes) {
     cudaFree(ph.d_lines);
     cudaFree(ph.d_wax);
@@ -842,12 +848,54 @@ us_status us_sim_render_host(us_sim* s, const us_env* envs, int32_t B, const flo
   }
   if ((e = cudaMemcpyAsync(s->d_host_poses, poses_host, pose_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(s, e, "pose copy");
-  if ((r = do_render(s, envs, B, s->d_host_poses, seed, step, s->d_host_frames, nullptr, nullptr, nullptr, nullptr, 0,
-                     st)) != US_OK)
-    return r;
-  if ((e = cudaMemcpyAsync(frames_host, s->d_host_frames, frame_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-    return cuda_fail(s, e, "frame copy");
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e, "render");
+  // A large batch renders as up to four contiguous sub-batches (env ranges
+  // of about equal frame bytes, each keeping its envs' caller indices), and
+  // each sub-batch's frames go to the host on a copy stream while the next
+  // one renders.  A small batch renders in one piece: there the sub-batches'
+  // extra waves would cost more than the copy overlap gains.
+  constexpr size_t kSubBytes = 20u << 20;
+  const int n_sub = (int)std::min<size_t>({(size_t)us_sim::kHostSub, (size_t)B, std::max<size_t>(1, frame_bytes / kSubBytes)});
+  if (n_sub == 1) {
+    if ((r = do_render(s, envs, B, s->d_host_poses, seed, step, s->d_host_frames, nullptr, nullptr, nullptr, nullptr, 0,
+                       st)) != US_OK)
+      return r;
+    if ((e = cudaMemcpyAsync(frames_host, s->d_host_frames, frame_bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(s, e, "frame copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e, "render");
+    return US_OK;
+  }
+  if (!s->copy_stream) {
+    if ((e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(s, e, "copy stream");
+    for (int k = 0; k < us_sim::kHostSub; ++k)
+      if ((e = cudaEventCreateWithFlags(&s->copy_ev[k], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(s, e, "copy events");
+  }
+  const std::vector<EnvItem>& items = pl->items_batch;   // caller order, full-batch frame offsets
+  auto off_of = [&](int b) -> long long { return b < B ? items[b].frame_off : pl->frame_floats; };
+  int b0 = 0;
+  us_status rr = US_OK;
+  for (int k = 0; k < n_sub && b0 < B; ++k) {
+    int b1 = b0 + 1;
+    const long long target = (long long)(k + 1) * pl->frame_floats / n_sub;
+    while (b1 < B && (k + 1 == n_sub || off_of(b1) < target)) ++b1;
+    const long long f0 = off_of(b0), f1 = off_of(b1);
+    if ((rr = do_render(s, envs + b0, b1 - b0, s->d_host_poses, seed, step, s->d_host_frames + f0, nullptr, nullptr,
+                        nullptr, nullptr, 0, st, b0)) != US_OK)
+      break;
+    if ((e = cudaEventRecord(s->copy_ev[k], st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s->copy_stream, s->copy_ev[k], 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(frames_host + f0, s->d_host_frames + f0, (size_t)(f1 - f0) * sizeof(float),
+                             cudaMemcpyDeviceToHost, s->copy_stream)) != cudaSuccess) {
+      rr = cuda_fail(s, e, "frame copy");
+      break;
+    }
+    b0 = b1;
+  }
+  // both streams drain before the call returns, also after an error
+  const cudaError_t e1 = cudaStreamSynchronize(s->copy_stream), e2 = cudaStreamSynchronize(st);
+  if (rr != US_OK) return rr;
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(s, e1 != cudaSuccess ? e1 : e2, "render");
   return US_OK;
 }
 

@@ -267,10 +267,14 @@ struct us_sim {
   float* d_poses3d = nullptr;
   size_t poses3d_cap = 0;
 
-  // staging for us_sim_render_host
+  // staging for us_sim_render_host; its frame copies run on copy_stream,
+  // each sub-batch's after copy_ev[k] (created on first use)
   float* d_host_poses = nullptr;
   float* d_host_frames = nullptr;
   size_t host_poses_cap = 0, host_frames_cap = 0;
+  static constexpr int kHostSub = 4;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[kHostSub] = {};
 
   std::string last_error;
 };

@@ -551,3 +551,24 @@ def test_pass_b_wedge_widths_agree(nw, pers):
             sim.set_tuning(*bad)
         assert e.value.status == US_ERR_INVALID_ARG
     sim.close()
+
+
+def test_host_render_in_sub_batches_matches_device(c2):
+    """A batch whose frames pass 40 MB goes to the host in sub-batches (each
+    copied while the next renders): the frames equal a device render of the
+    whole batch bit for bit, into pinned and into pageable host memory."""
+    wl, sim = c2
+    B = 170                                    # 170 x 256 KB of frames: two sub-batches
+    envs = np.zeros((B, 2), np.int32)
+    poses = np.ascontiguousarray(np.stack([wl.poses[b % 64] for b in range(B)]), np.float32)
+    off = sim.frame_layout(envs)
+    assert int(off[-1]) * 4 > 40 * 2 ** 20
+    P = torch.from_numpy(poses).cuda()
+    dev = torch.empty(int(off[-1]), device="cuda")
+    sim.render(envs, P, 9, 4, dev)
+    torch.cuda.synchronize()
+    want = dev.cpu().numpy()
+    for pinned in (True, False):
+        host = torch.full((int(off[-1]),), -3.0).pin_memory() if pinned else torch.full((int(off[-1]),), -3.0)
+        sim.render_host(envs, poses, 9, 4, host.numpy())
+        assert np.array_equal(host.numpy(), want), pinned
