@@ -185,10 +185,18 @@ struct SplitCtx {
 
 // load the item of work unit `blk` (groups per item gpi) into shared memory;
 // returns false (for the whole block) if the block has no work
-__device__ __forceinline__ bool split_item(const RenderParams& p, int blk, int gpi, int G, SplitCtx& cx, int& group) {
+__device__ __forceinline__ bool split_item(const RenderParams& p, const SplitArgs& a, int blk, int G, SplitCtx& cx,
+                                           int& group) {
   const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
-  const int item = blk / gpi;
-  group = blk - item * gpi;
+  int item;
+  if (a.units) {
+    const int2 u = a.units[blk];
+    item = u.x;
+    group = u.y;
+  } else {
+    item = blk / a.gpi_lines;
+    group = blk - item * a.gpi_lines;
+  }
   if (threadIdx.x == 0) {
     cx.valid = 0;
     if (item < n_items) {
@@ -226,7 +234,7 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SplitCtx cx;
   int group;
-  if (!split_item(p, blk, a.gpi_lines, G, cx, group)) return;
+  if (!split_item(p, a, blk, G, cx, group)) return;
   const DevProbe& P = cx.P;
   const int NL = P.nl, NS = P.ns, KA = P.k_ax;
   const int RS = (NS + 2 * KA) | 1;
@@ -394,7 +402,15 @@ __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArg
   // every thread reads its item and probe (the same addresses: broadcast
   // loads); no block-wide set-up
   const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
-  const int item = blk / a.gpi_image, tile = blk - item * a.gpi_image;
+  int item, tile;
+  if (a.units) {
+    const int2 u = a.units[a.n_units_a + blk];
+    item = u.x;
+    tile = u.y;
+  } else {
+    item = blk / a.gpi_image;
+    tile = blk - item * a.gpi_image;
+  }
   if (item >= n_items) return;
   const EnvItem it = p.items[item];
   const DevProbe& P = p.probes[it.probe];
@@ -641,12 +657,15 @@ cudaError_t split_prepare(SplitShape& sh) {
 template <int G>
 static cudaError_t launch_g(const RenderParams& p, const SplitShape& sh, const SplitArgs& a, int max_items, int pass,
                             cudaStream_t st) {
+  const unsigned grid_a = a.units ? (unsigned)a.n_units_a : (unsigned)(max_items * a.gpi_lines);
+  const unsigned grid_b = a.units ? (unsigned)a.n_units_b : (unsigned)(max_items * a.gpi_image);
+  if ((pass == 0 && grid_a == 0) || (pass == 1 && grid_b == 0)) return cudaSuccess;
   if (pass == 0 && p.speckle_anchor)
-    split_lines<G, true><<<(unsigned)(max_items * a.gpi_lines), G * 32, sh.smem_lines, st>>>(p, a);
+    split_lines<G, true><<<grid_a, G * 32, sh.smem_lines, st>>>(p, a);
   else if (pass == 0)
-    split_lines<G, false><<<(unsigned)(max_items * a.gpi_lines), G * 32, sh.smem_lines, st>>>(p, a);
+    split_lines<G, false><<<grid_a, G * 32, sh.smem_lines, st>>>(p, a);
   else if (pass == 1)
-    split_image<<<(unsigned)(max_items * a.gpi_image), kImageThreads, sh.smem_image, st>>>(p, a);
+    split_image<<<grid_b, kImageThreads, sh.smem_image, st>>>(p, a);
   else {
     // persistent: as many blocks as are resident at once (launched as a
     // cooperative grid, so they all are), no more than there are units
@@ -669,9 +688,14 @@ static cudaError_t launch_g(const RenderParams& p, const SplitShape& sh, const S
 }
 
 cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems,
-                              unsigned* sync, int max_items, int pass, cudaStream_t st) {
+                              unsigned* sync, int max_items, int pass, cudaStream_t st, SplitUnits units) {
   SplitArgs a = sh.args;
   set_line_buffer(a, beam, beam_elems);
+  if (pass < 2 && units.d) {
+    a.units = units.d;
+    a.n_units_a = units.n_a;
+    a.n_units_b = units.n_b;
+  }
   if (pass >= 2) {
     // sync: the unit counter, then one completion flag per pass-A group
     // (pass 3: the caller has zeroed them)
@@ -712,10 +736,29 @@ cudaError_t launch_split_wait_selftest(const RenderParams& p, const SplitShape& 
 }
 
 cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems, unsigned* sync,
-                         int max_items, cudaStream_t st) {
+                         int max_items, cudaStream_t st, SplitUnits units) {
   if (sh.persistent) return launch_split_pass(p, sh, beam, beam_elems, sync, max_items, 2, st);
-  cudaError_t e = launch_split_pass(p, sh, beam, beam_elems, sync, max_items, 0, st);
-  return e == cudaSuccess ? launch_split_pass(p, sh, beam, beam_elems, sync, max_items, 1, st) : e;
+  cudaError_t e = launch_split_pass(p, sh, beam, beam_elems, sync, max_items, 0, st, units);
+  return e == cudaSuccess ? launch_split_pass(p, sh, beam, beam_elems, sync, max_items, 1, st, units) : e;
+}
+
+// the work units of a list of items (items in launch order) for a shape:
+// pass A (item, group) for the probe's groups, pass B (item, tile) for its
+// wedges x chunks
+void build_split_units(const std::vector<EnvItem>& items, const std::vector<ProbeHost>& probes, int G, int GB,
+                       std::vector<int2>& units, int& na, int& nb) {
+  units.clear();
+  for (int i = 0; i < (int)items.size(); ++i) {
+    const int NL = probes[items[i].probe].desc.n_lines;
+    for (int g = 0; g * G < NL; ++g) units.push_back(make_int2(i, g));
+  }
+  na = (int)units.size();
+  for (int i = 0; i < (int)items.size(); ++i) {
+    const us_probe& d = probes[items[i].probe].desc;
+    const int nchunk = (d.n_samples + kChunk - 1) / kChunk, nq = (d.n_lines + GB - 1) / GB;
+    for (int t = 0; t < nq * nchunk; ++t) units.push_back(make_int2(i, t));
+  }
+  nb = (int)units.size() - na;
 }
 
 // Pixels of a curvilinear probe's output grid, grouped by pass-B tile

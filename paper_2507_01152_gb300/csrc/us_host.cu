@@ -21,6 +21,7 @@ constexpr int kMaxMatchBins = 16384;   // histogram matching: bins of the refere
 us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream_t st);
 void drop_graph(us_plan& pl);
 static cudaError_t two_pass_buffers(us_plan* pl);
+static SplitUnits plan_units(us_sim* s, us_plan* pl, cudaStream_t st);
 
 us_status fail(us_sim* s, us_status st, const std::string& msg) {
   if (s) s->last_error = msg;
@@ -337,7 +338,8 @@ us_status do_render(us_sim* s, const us_env* envs, int B, const float* poses, ui
     if (st && cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
     if (s->tuning.use_graph && st && cap == cudaStreamCaptureStatusNone) return graph_launch(s, pl, p, st);
     if (two_pass) {
-      if ((e = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, st)) != cudaSuccess) return cuda_fail(s, e, "two-pass render launch");
+      if ((e = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, st, plan_units(s, pl, st))) != cudaSuccess)
+        return cuda_fail(s, e, "two-pass render launch");
       return US_OK;
     }
     if ((e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(s, e, "reset work counter");
@@ -382,6 +384,7 @@ void free_sim(us_sim* s) {
     cudaFree(kv.second.d_work);
     cudaFree(kv.second.d_beam);
     cudaFree(kv.second.d_sync);
+    cudaFree(kv.second.d_units);
     cudaFree(kv.second.d_slice_hu);
     cudaFree(kv.second.d_slice_fan);
   }
@@ -477,6 +480,37 @@ us_status apply_tuning(us_sim* s, const us_tuning& t) {
   return US_OK;
 }
 
+// the two grids' work units of the plan's items for the current shape,
+// rebuilt when the shape changes; empty (every item's full unit range) if
+// they cannot be uploaded, or must be rebuilt while st is being captured
+static SplitUnits plan_units(us_sim* s, us_plan* pl, cudaStream_t st) {
+  if (pl->units_G != s->split.G || pl->units_GB != s->split.GB || !pl->d_units) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (st && cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone)
+      return SplitUnits();
+    std::vector<int2> u;
+    int na = 0, nb = 0;
+    build_split_units(pl->items_sorted, s->probes, s->split.G, s->split.GB, u, na, nb);
+    cudaFree(pl->d_units);
+    pl->d_units = nullptr;
+    pl->units_G = pl->units_GB = 0;
+    if (u.empty() || upload(&pl->d_units, u.data(), u.size()) != cudaSuccess) {
+      cudaGetLastError();
+      pl->d_units = nullptr;
+      return SplitUnits();
+    }
+    pl->units_G = s->split.G;
+    pl->units_GB = s->split.GB;
+    pl->units_na = na;
+    pl->units_nb = nb;
+  }
+  SplitUnits su;
+  su.d = pl->d_units;
+  su.n_a = pl->units_na;
+  su.n_b = pl->units_nb;
+  return su;
+}
+
 // the two-pass path's per-plan buffers: filtered lines and the persistent
 // grid's synchronisation words
 static cudaError_t two_pass_buffers(us_plan* pl) {
@@ -519,10 +553,12 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
       pl->g_pers != s->tuning.persistent || pl->g_gb != s->split.GB) {
     drop_graph(*pl);
     cudaGraph_t g = nullptr;
+    // the work units are uploaded before the capture (no copies inside it)
+    const SplitUnits su = two_pass && !s->split.persistent ? plan_units(s, pl, st) : SplitUnits();
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(s, e, "graph capture");
     cudaError_t e1 = cudaSuccess, e2;
     if (two_pass) {
-      e2 = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, p.n_items, st);
+      e2 = launch_split(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, p.n_items, st, su);
     } else {
       e1 = cudaMemsetAsync(p.work, 0, sizeof(unsigned), st);
       e2 = launch_fused(p, s->shape, st);
@@ -1171,9 +1207,9 @@ us_status us_sim_render_timed(us_sim* s, const us_env* envs, int32_t B, const fl
     cudaEventRecord(ev[1], st);
   } else if (two_pass) {
     cudaEventRecord(ev[0], st);
-    e = launch_split_pass(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, 0, st);
+    e = launch_split_pass(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, 0, st, plan_units(s, pl, st));
     cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, 1, st);
+    if (e == cudaSuccess) e = launch_split_pass(p, s->split, pl->d_beam, pl->beam_elems, pl->d_sync, B, 1, st, plan_units(s, pl, st));
     cudaEventRecord(ev[2], st);
   } else {
     e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), st);

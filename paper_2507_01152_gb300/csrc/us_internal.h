@@ -89,8 +89,17 @@ struct SplitArgs {
   unsigned* done = nullptr;   // persistent grid: per pass-A group, 1 once its lines are written
   long long wait_cycles = 2000000000ll;   // persistent grid: bound of a tile's wait (SM clock cycles, ~1 s)
   int G = 32, GB = 32, gpi_lines = 0, gpi_image = 0;
+  // two grids: the launch's work units, pass A's (item, group) then pass B's
+  // (item, tile), only those inside each item's probe (null: every item has
+  // gpi_lines / gpi_image units, those past its probe exit at once)
+  const int2* units = nullptr;
+  int n_units_a = 0, n_units_b = 0;
   int off_r = 0, off_wax = 0, off_tis = 0, off_lab = 0;   // pass A byte offsets
   int off_y = 0, off_wlat = 0;                 // pass B byte offsets
+};
+struct SplitUnits {
+  const int2* d = nullptr;   // device: n_a pass-A units, then n_b pass-B units
+  int n_a = 0, n_b = 0;
 };
 struct SplitShape {
   int G = 32;    // pass A lines per block (the tuning's warps_per_cta)
@@ -116,13 +125,18 @@ cudaError_t split_prepare(SplitShape& sh);
 // both passes over the first max_items entries of p.items (fewer if
 // p.n_items_dev says so)
 cudaError_t launch_split(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems, unsigned* sync,
-                         int max_items, cudaStream_t st);
+                         int max_items, cudaStream_t st, SplitUnits units = SplitUnits());
 // one pass: 0 = lines (pass A), 1 = image (pass B)
 // pass 0: pass A, 1: pass B (separate grids); 2: both in the persistent
 // grid (resets `sync` first); 3: the persistent grid on a `sync` the
 // caller has zeroed
 cudaError_t launch_split_pass(const RenderParams& p, const SplitShape& sh, float* beam, long long beam_elems,
-                              unsigned* sync, int max_items, int pass, cudaStream_t st);
+                              unsigned* sync, int max_items, int pass, cudaStream_t st,
+                              SplitUnits units = SplitUnits());
+// the two grids' work units of items (in launch order) for pass-A groups of
+// G lines and pass-B tiles of GB lines
+void build_split_units(const std::vector<EnvItem>& items, const std::vector<ProbeHost>& probes, int G, int GB,
+                       std::vector<int2>& units, int& na, int& nb);
 // the persistent grid with its unit counter started past every pass-A group
 // and the given wait bound: no group publishes its lines, so every tile's
 // wait runs out (self-test of the bounded wait)
@@ -214,6 +228,8 @@ struct us_plan {
   float* d_beam = nullptr;                   // two-pass path: filtered lines of the batch
   int g_pers = -1;                           // captured graph's persistent flag
   unsigned* d_sync = nullptr;                // two-pass path: persistent grid's counter and flags
+  int2* d_units = nullptr;                   // two grids: work units of items_sorted for units_G / units_GB
+  int units_G = 0, units_GB = 0, units_na = 0, units_nb = 0;
   float* d_slice_hu = nullptr;               // slice sampling with histogram matching: raw HU
   uint8_t* d_slice_fan = nullptr;            //   and inside-fan flags of the batch's pixels
   size_t slice_px = 0;
