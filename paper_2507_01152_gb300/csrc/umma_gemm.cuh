@@ -37,10 +37,11 @@ namespace umma {
 constexpr int kBM = 128, kBK = 64;
 constexpr int kProducers = 256;                     // warps 0-7
 constexpr int kMmaWarp = kProducers / 32;           // first issuing warp: 8
-constexpr int kEpilogue = 128;                      // 4 warps after the issuers
+constexpr int kEpilogue = 128;                      // one epilogue group: 4 warps
+constexpr int kEpiGroups = 2;                       // groups after the issuers; group e drains TMEM buffer e
 template <int X>
 constexpr int gemm_threads() {
-  return kProducers + 32 * X + kEpilogue;
+  return kProducers + 32 * X + kEpiGroups * kEpilogue;
 }
 constexpr uint32_t kTileA = kBM * kBK * 2;          // bytes of one A tile of a stage
 template <int BN, int X = 1>
@@ -292,9 +293,13 @@ __global__ void __launch_bounds__(gemm_threads<X>(), 1)
   } else {
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3;   // TMEM lane quarter this warp may read
-    int j = 0;
+    // two groups of four warps: group e takes this CTA's tile groups j with
+    // j mod 2 = e, whose accumulators sit in TMEM buffer e
+    const int eg = (warp - kEpiWarp) >> 2;
+    int j = eg;
     bool ok = true;
-    for (int grp = blockIdx.x; grp < n_groups && ok; grp += gridDim.x, ++j) {
+    for (int grp = blockIdx.x + eg * (int)gridDim.x; grp < n_groups && ok; grp += kEpiGroups * (int)gridDim.x,
+             j += kEpiGroups) {
       const int a = j & 1;
       const int rem = grp % (mg * nt), ni = rem / mg, gi = rem - ni * mg;
       for (int w = 0; w < X; ++w) {
