@@ -631,6 +631,16 @@ def run_ours(args):
         poses3 = torch.from_numpy(np.ascontiguousarray(wl3.poses, np.float32)).cuda()
         render = lambda k: sim.render_3d(wl3.envs, poses3, scene.SURGERY3D_SLICES, scene.SURGERY3D_PITCH_MM, seed, k,
                                          frames, stream=stream)
+    if wl3 is None:
+        # the timed form (graph replays of the tuned shape) must render what
+        # the plain per-env kernels render: two replays checked bit for bit
+        check = torch.empty_like(frames)
+        for k in (11, 12):
+            render(k)
+            sim.render_plain(None, poses, seed, k, check, stream=stream, envs_c=envs_c)
+            stream.synchronize()
+            if not torch.equal(frames, check):
+                raise RuntimeError(f"tuned render {tuning} differs from the plain kernels (step {k})")
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()

@@ -491,6 +491,8 @@ static SplitUnits plan_units(us_sim* s, us_plan* pl, cudaStream_t st) {
     std::vector<int2> u;
     int na = 0, nb = 0;
     build_split_units(pl->items_sorted, s->probes, s->split.G, s->split.GB, u, na, nb);
+    // a captured graph holds the old list's address: capture again
+    drop_graph(*pl);
     cudaFree(pl->d_units);
     pl->d_units = nullptr;
     pl->units_G = pl->units_GB = 0;
@@ -543,18 +545,26 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
   const bool two_pass = s->tuning.cluster_size == 1;
   RenderParams pp = p;
   FusedLayout lay = s->shape.lay;
+  // the kernel arguments of a replay are those launch_split would pass: the
+  // persistent grid's counter and flags, or the two grids' work units (a
+  // rebuilt unit list drops the graph, so a replay's list is the captured one)
+  const SplitUnits su = two_pass && !s->split.persistent ? plan_units(s, pl, st) : SplitUnits();
   SplitArgs sa = s->split.args;
   set_line_buffer(sa, pl->d_beam, pl->beam_elems);
-  sa.work = pl->d_sync;
-  sa.done = pl->d_sync ? pl->d_sync + 1 : nullptr;
+  if (two_pass && s->split.persistent) {
+    sa.work = pl->d_sync;
+    sa.done = pl->d_sync ? pl->d_sync + 1 : nullptr;
+  } else if (su.d) {
+    sa.units = su.d;
+    sa.n_units_a = su.n_a;
+    sa.n_units_b = su.n_b;
+  }
   void* fargs[2] = {&pp, &lay};
   void* sargs[2] = {&pp, &sa};
   if (!pl->gexec || pl->g_cs != s->tuning.cluster_size || pl->g_nw != s->tuning.warps_per_cta ||
-      pl->g_pers != s->tuning.persistent || pl->g_gb != s->split.GB) {
+      pl->g_pers != s->tuning.persistent || pl->g_gb != s->split.GB || pl->g_units != su.d) {
     drop_graph(*pl);
     cudaGraph_t g = nullptr;
-    // the work units are uploaded before the capture (no copies inside it)
-    const SplitUnits su = two_pass && !s->split.persistent ? plan_units(s, pl, st) : SplitUnits();
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(s, e, "graph capture");
     cudaError_t e1 = cudaSuccess, e2;
     if (two_pass) {
@@ -594,6 +604,7 @@ us_status graph_launch(us_sim* s, us_plan* pl, const RenderParams& p, cudaStream
     pl->g_nw = s->tuning.warps_per_cta;
     pl->g_pers = s->tuning.persistent;
     pl->g_gb = s->split.GB;
+    pl->g_units = su.d;
     if ((e = cudaGraphLaunch(pl->gexec, st)) != cudaSuccess) return cuda_fail(s, e, "graph launch");
     return US_OK;
   }

@@ -240,6 +240,7 @@ struct us_plan {
   std::vector<cudaGraphNode_t> gnodes;
   std::vector<cudaKernelNodeParams> gkps;
   int g_cs = 0, g_nw = 0, g_gb = 0;   // captured graph's shape (pass B wedge lines)
+  const int2* g_units = nullptr;       // the work-unit list the captured graph's kernels read
 };
 
 struct us_sim {

@@ -572,3 +572,34 @@ def test_host_render_in_sub_batches_matches_device(c2):
         host = torch.full((int(off[-1]),), -3.0).pin_memory() if pinned else torch.full((int(off[-1]),), -3.0)
         sim.render_host(envs, poses, 9, 4, host.numpy())
         assert np.array_equal(host.numpy(), want), pinned
+
+
+@pytest.mark.parametrize("shape", [(1, 16, 1, 0, 32), (1, 8, 1, 0, 16), (1, 16, 1, 1, 32), (8, 32, 1, 0, 0)])
+def test_graph_replays_of_a_mixed_probe_batch_match_plain(shape):
+    """Graph capture and replay (an explicit stream) of a batch whose envs
+    use three probes of different sizes, so that the two grids launch only
+    each env's own work units: every replay, with fresh poses and steps,
+    equals the plain per-environment kernels bit for bit."""
+    spec = scene.VolumeSpec(128, 128, 128, 1.0, 2, 91)
+    lab, hu = scene.make_volume(spec)
+    probes = [scene.curvilinear_probe(128, 256, 80.0, 60.0, 40.0, 128, 128),
+              scene.curvilinear_probe(96, 192, 80.0, 60.0, 40.0, 96, 96), scene.linear_probe(64, 128, 80.0, 0.5)]
+    B = 24
+    envs = np.array([[0, (b * 7) % 3] for b in range(B)], np.int32)
+    poses = scene.dorsal_poses(spec, 3 * B, 13).reshape(3, B, 3, 4)
+    wl = scene.Workload("mix3", [(spec, lab, hu)], probes, envs, poses[0], seed=4)
+    sim = gpu_sim(wl)
+    sim.set_tuning(*shape)
+    st = torch.cuda.Stream()
+    off = sim.frame_layout(envs)
+    n = int(off[-1])
+    for k in range(3):
+        P = torch.from_numpy(np.ascontiguousarray(poses[k])).cuda()
+        got = torch.full((n,), -7.0, device="cuda")
+        sim.render(envs, P, 17, k, got, stream=st)
+        st.synchronize()
+        want = torch.full((n,), -7.0, device="cuda")
+        sim.render_plain(envs, P, 17, k, want, stream=st)
+        st.synchronize()
+        assert np.array_equal(got.cpu().numpy(), want.cpu().numpy()), (shape, k)
+    sim.close()
