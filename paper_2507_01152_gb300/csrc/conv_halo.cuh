@@ -21,7 +21,7 @@
 // issues the box copies of up to S tiles ahead; X issuing warps each own
 // every X-th tile of the CTA (one elected thread issues its 9 CIN / 16 MMAs
 // of 128 x COUT x 16 into one half of its double-buffered TMEM
-// accumulator); two groups of four epilogue warps, taking alternate tiles,
+// accumulator); four groups of four epilogue warps, tile g to group g mod 4,
 // add the bias, apply the ReLU and store BF16 pixels.  Every wait is bounded; a wait that runs out raises the
 // shared abort flag, the CTA drains its copies and MMAs, frees its TMEM and
 // reports kErrWaitTimeout.
@@ -53,12 +53,16 @@ struct HaloCfg {
   // and each issuer sees every phase of its stages' barriers in order
   static constexpr int S0 = (int)((225u * 1024u - WBYTES) / STAGE);
   static constexpr int S = (S0 > 8 ? 8 : S0) / X * X;
-  static constexpr int kEpiGroups = 2;                          // epilogue groups of 4 warps, alternate tiles
+  // epilogue groups of 4 warps; group g mod kEpiGroups takes tile g.  With
+  // kEpiGroups dividing X, every tile of one issuer goes to one group, which
+  // therefore sees each of that issuer's accumulator phases in order
+  static constexpr int kEpiGroups = 4;
   static constexpr int THREADS = 32 * (1 + X + 4 * kEpiGroups);
   static constexpr uint32_t SMEM = WBYTES + S * STAGE + 4 * COUT + 128;   // + bias, alignment slack
   static_assert((CIN == 8 || CIN % 16 == 0) && (COUT == 32 || COUT == 64), "halo conv shapes");
   static_assert(S >= X, "stages do not fit");
   static_assert(2 * X * COUT <= 512, "accumulators exceed TMEM");
+  static_assert(X % kEpiGroups == 0, "an issuer's tiles must all go to one epilogue group");
 };
 
 struct HaloArgs {
@@ -203,7 +207,7 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
     __syncwarp();
   } else {
     // ----------------------------------------------------------- epilogue
-    // two groups of four warps take alternate tiles; within a group, warp
+    // groups of four warps take tiles g with g mod kEpiGroups = group; within a group, warp
     // (index mod 4) reads its TMEM lane quarter, all of a tile's columns in
     // flight before one wait
     const int grp = (warp - 1 - X) >> 2;
