@@ -290,7 +290,7 @@ US_API us_status us_sim_render_debug(us_sim* sim, const us_env* envs, int32_t B,
 /* Render from HOST poses into HOST frames: copies the poses in and the
  * frames out through library-owned device buffers (grown on demand).
  * Returns after the frames are in host memory (synchronous).  A batch of
- * more than 40 MB of frames renders as two to four contiguous sub-batches
+ * 16 MB of frames or more renders as two to four contiguous sub-batches
  * (same frames: each env keeps its batch index), each copied out on a
  * library-owned stream while the next renders; the copies overlap the
  * renders when frames_host is pinned (page-locked) memory. */

@@ -895,12 +895,13 @@ us_status us_sim_render_host(us_sim* s, const us_env* envs, int32_t B, const flo
   }
   if ((e = cudaMemcpyAsync(s->d_host_poses, poses_host, pose_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(s, e, "pose copy");
-  // A large batch renders as up to four contiguous sub-batches (env ranges
-  // of about equal frame bytes, each keeping its envs' caller indices), and
-  // each sub-batch's frames go to the host on a copy stream while the next
-  // one renders.  A small batch renders in one piece: there the sub-batches'
-  // extra waves would cost more than the copy overlap gains.
-  constexpr size_t kSubBytes = 20u << 20;
+  // A batch of 16 MB of frames or more renders as up to four contiguous
+  // sub-batches (env ranges of about equal frame bytes, at least 8 MB each,
+  // each keeping its envs' caller indices), and each sub-batch's frames go
+  // to the host on a copy stream while the next one renders.  A smaller
+  // batch renders in one piece: there the sub-batches' extra waves would
+  // cost more than the copy overlap gains.
+  constexpr size_t kSubBytes = 8u << 20;
   const int n_sub = (int)std::min<size_t>({(size_t)us_sim::kHostSub, (size_t)B, std::max<size_t>(1, frame_bytes / kSubBytes)});
   if (n_sub == 1) {
     if ((r = do_render(s, envs, B, s->d_host_poses, seed, step, s->d_host_frames, nullptr, nullptr, nullptr, nullptr, 0,

@@ -554,11 +554,11 @@ def test_pass_b_wedge_widths_agree(nw, pers):
 
 
 def test_host_render_in_sub_batches_matches_device(c2):
-    """A batch whose frames pass 40 MB goes to the host in sub-batches (each
+    """A batch whose frames pass 16 MB goes to the host in sub-batches (each
     copied while the next renders): the frames equal a device render of the
     whole batch bit for bit, into pinned and into pageable host memory."""
     wl, sim = c2
-    B = 170                                    # 170 x 256 KB of frames: two sub-batches
+    B = 170                                    # 170 x 256 KB of frames: four sub-batches
     envs = np.zeros((B, 2), np.int32)
     poses = np.ascontiguousarray(np.stack([wl.poses[b % 64] for b in range(B)]), np.float32)
     off = sim.frame_layout(envs)
