@@ -169,6 +169,17 @@ def test_autotune_picks_a_shape_and_caches_it(c2, tmp_path):
     t1 = sim.get_tuning()
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and f"cs={t1['cluster_size']} nw={t1['warps_per_cta']}" in lines[0]
+    assert f"pg={t1['persistent']} wl={t1['wedge_lines']}" in lines[0]
+    # a cache line written before the pass-B tile width was a field reads as the widest tile
+    old_line = lines[0].split(" wl=")[0] + " ms=0.1\n"
+    cache2 = tmp_path / "tune_old.txt"
+    cache2.write_text(old_line)
+    sim.set_tuning(16, 16)
+    sim.autotune(envs, P, fr, str(cache2))
+    t2 = sim.get_tuning()
+    assert (t2["cluster_size"], t2["warps_per_cta"], t2["persistent"], t2["wedge_lines"]) == \
+        (t1["cluster_size"], t1["warps_per_cta"], t1["persistent"], 0)
+    assert len(cache2.read_text().splitlines()) == 1
     sim.set_tuning(16, 16)
     sim.autotune(envs, P, fr, str(cache))          # read back from the cache, no new entry
     assert sim.get_tuning() == t1 and len(cache.read_text().splitlines()) == 1
