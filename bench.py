@@ -175,6 +175,15 @@ def make_workload(name, copies=1):
         wl = scene.workload_c3(512 * copies, steps=1)
         wl.poses = wl.poses[0]
         return wl
+    if name == "c3v1":
+        # C3's probe mix on one of its volumes, 64 envs: a case small enough
+        # (about 1.5 GB on the device) for multi-pass profiler captures
+        spec = scene.c3_specs()[0]
+        lab, hu = scene.make_volume(spec)
+        envs = np.stack([np.zeros(64, np.int64), np.arange(64) % 3], axis=1).astype(np.int32)
+        poses = scene.random_walk_poses(spec, 64 * copies, 1, 3000)[0]
+        return scene.Workload("c3_probe_mix_1vol_64env", [(spec, lab, hu)], scene.c3_probes(),
+                              np.tile(envs, (copies, 1)), poses, seed=0x5EED0003)
     raise ValueError(name)
 
 
@@ -764,7 +773,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "paper", "surgery3d", "recon", "mixed"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1", "paper", "surgery3d", "recon", "mixed",
+                                                         "c3v1"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
