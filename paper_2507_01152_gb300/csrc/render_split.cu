@@ -1,26 +1,29 @@
 // Two-pass batched render without clusters.
 //
 // Pass A (split_lines): one block per (environment, group of G lines), one
-// warp per line.  The block takes the nearest labels of its lines and of the
-// lines the incidence stencil can reach on either side (at most kThetaDMax),
-// the impedance of its own lines, runs the scanline model (reflection
-// impulses R_imp, scatter pattern T, energy E), applies the axial PSF to
-// R_imp and T in place, and writes the filtered pair (AR, AT) and E to a
-// beam-layout line buffer in global memory.
+// warp per line.  The block takes the nearest labels of its lines (four
+// samples' loads in flight a lane) and of the lines the incidence stencil can
+// reach on either side (at most kThetaDMax), the impedance of its own lines,
+// runs the scanline model (reflection impulses R_imp, scatter pattern T,
+// energy E), applies the axial PSF to R_imp and T, and writes the filtered
+// pair (AR, AT) and E to a beam-layout line buffer in global memory.
 //
-// Pass B (split_image): one block per (environment, wedge of G lines).  The
-// block stages the filtered pairs its wedge needs (its lines, one more line
-// for the bilinear step, and the lateral PSF's reach on both sides) and the
-// energy of its own lines, forms the lateral PSF of both, the image
+// Pass B (split_image): one block per tile (environment, wedge of GB lines,
+// 128-sample chunk).  The block stages the filtered pairs its wedge needs
+// (its lines, one more line for the bilinear step, and the lateral PSF's
+// reach on both sides) and the energy of its own lines, forms the lateral
+// PSF of both, the image
 // I = (P (x) R_imp) + E (P (x) T) (App. B.2) and its log in shared memory, and
 // scan-converts the output pixels assigned to the wedge: a host-built list,
 // per probe, of the pixels whose bilinear footprint lies on the wedge's
 // lines (pixels outside the fan go to the wedge of the preceding in-fan
 // pixel of their row), so every read is local.
 //
-// Blocks are numbered item-major over the costliest-first work list; a
-// block whose group lies past its probe's lines, or whose item lies past a
-// device-side item count, exits at once.  Per-line arithmetic, tap order and
+// The two grids launch the plan's work units (each environment's own groups
+// and tiles, over the costliest-first work list).  Without a unit list,
+// blocks are numbered item-major and a block whose group lies past its
+// probe's lines, or whose item lies past a device-side item count, exits at
+// once.  Per-line arithmetic, tap order and
 // bilinear formula are those of the plain and cluster paths, so all three
 // produce identical frames.
 #include <algorithm>
@@ -395,47 +398,147 @@ __global__ void __launch_bounds__(G * 32, lines_min_blocks<G>()) split_lines(Ren
 // Pass B work unit `blk` = item * gpi_image + tile, run by NT threads.
 // With a.done set, the unit first waits (bounded) until the pass-A groups
 // holding its staged rows have published them.
+// One pass-B tile: its environment, lines and samples.
+struct TileCtx {
+  EnvItem it;
+  const DevProbe* P;
+  int item, tile, NL, NS, KL;
+  int w0, w1, y1;   // wedge lines w0 .. w1-1; log rows w0 .. y1-1
+  int s0, sw;       // staged samples s0 .. s0+sw-1
+  int r0, nrows;    // staged rows r0 .. r0+nrows-1 (zero outside the frame)
+  int a0, a1;       // rows present in the line buffer
+};
+
+// the tile of pass-B unit `blk`; false if the unit has no work (past the
+// item count or past its probe's tiles).  Every thread reads the same
+// addresses (broadcast loads); the result is uniform over the block.
+__device__ __forceinline__ bool tile_ctx(const RenderParams& p, const SplitArgs& a, int blk, TileCtx& t) {
+  const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
+  if (a.units) {
+    const int2 u = a.units[a.n_units_a + blk];
+    t.item = u.x;
+    t.tile = u.y;
+  } else {
+    t.item = blk / a.gpi_image;
+    t.tile = blk - t.item * a.gpi_image;
+  }
+  if (t.item >= n_items) return false;
+  t.it = p.items[t.item];
+  t.P = &p.probes[t.it.probe];
+  t.NL = t.P->nl;
+  t.NS = t.P->ns;
+  t.KL = t.P->k_lat;
+  const int nchunk = (t.NS + kChunk - 1) / kChunk;
+  const int q = t.tile / nchunk, k = t.tile - q * nchunk;
+  t.w0 = q * a.GB;
+  if (t.w0 >= t.NL) return false;
+  t.w1 = min(t.w0 + a.GB, t.NL);
+  t.y1 = min(t.w1 + 1, t.NL);
+  t.s0 = k * kChunk;
+  t.sw = min(kChunk + 1, t.NS - t.s0);
+  // zero rows outside the frame, past the last needed row and past the
+  // line's end, so that the lateral PSF needs no edge tests (adding w * 0
+  // leaves a sum unchanged exactly: the sums never hold -0)
+  t.r0 = t.w0 - t.KL;
+  t.nrows = (((t.y1 - t.w0) + kLatLines - 1) / kLatLines) * kLatLines + 2 * t.KL;
+  t.a0 = max(t.r0, 0);
+  t.a1 = min(t.y1 + t.KL, t.NL);
+  return true;
+}
+
+// Stage a tile into shared memory: the lateral taps (plain stores), the
+// (AR, AT) rows and the wedge's energies, as 16-byte cp.async copies where
+// the rows are 16-byte aligned (zero-filled past a row's end and for rows
+// outside the frame), else plain loads.  Commits one cp.async group in
+// every case; the caller waits for it.
+__device__ __forceinline__ void tile_stage(const SplitArgs& a, const TileCtx& t, float2* abuf, float* ybuf,
+                                           float* wlat, int tid, int NT) {
+  for (int i = tid; i < 2 * t.KL + 1; i += NT) wlat[i] = __ldg(&t.P->w_lat[i]);
+  const float2* src = a.beam + t.it.beam_off + t.s0;
+  const float* esrc = a.ebeam + t.it.beam_off + t.s0;
+  const int ne = t.y1 - t.w0, NS = t.NS;
+  if ((NS & 3) == 0 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) &&
+      ((reinterpret_cast<uintptr_t>(esrc) & 15u) == 0)) {
+    constexpr int PPA = kRowStride / 2;                            // 16-byte pieces per pair row
+    for (int i = tid; i < t.nrows * PPA; i += NT) {
+      const int r = i / PPA, c = (i - r * PPA) * 2;
+      const int line = t.r0 + r;
+      const bool present = line >= t.a0 && line < t.a1 && c < t.sw;
+      const float2* g = present ? src + (long long)line * NS + c : a.beam;
+      umma::cp_async16(abuf + r * kRowStride + c, g, present ? 16u : 0u);
+    }
+    constexpr int PPE = kRowStride / 4;                            // 16-byte pieces per energy row
+    for (int i = tid; i < ne * PPE; i += NT) {
+      const int r = i / PPE, c = (i - r * PPE) * 4;
+      const bool present = c < t.sw;
+      const float* g = present ? esrc + (long long)(t.w0 + r) * NS + c : a.ebeam;
+      umma::cp_async16(ybuf + r * kRowStride + c, g, present ? 16u : 0u);
+    }
+  } else {
+    for (int i = tid; i < t.nrows * kRowStride; i += NT) {
+      const int r = i / kRowStride, c = i - r * kRowStride;
+      const int line = t.r0 + r;
+      abuf[i] = line >= t.a0 && line < t.a1 && c < t.sw ? __ldcg(src + (long long)line * NS + c) : make_float2(0.f, 0.f);
+    }
+    for (int i = tid; i < ne * kRowStride; i += NT) {
+      const int r = i / kRowStride, c = i - r * kRowStride;
+      ybuf[i] = c < t.sw ? __ldcg(esrc + (long long)(t.w0 + r) * NS + c) : 0.f;
+    }
+  }
+  umma::cp_async_commit();
+}
+
+// A staged tile (visible to the block): lateral PSF, log image, then the
+// frame's pixels whose bilinear base falls in the tile.
+__device__ __forceinline__ void tile_compute(const RenderParams& p, const TileCtx& t, const float2* abuf, float* ybuf,
+                                             const float* wlat, int tid, int NT) {
+  const DevProbe& P = *t.P;
+  const int NL = t.NL, NS = t.NS, w0 = t.w0, w1 = t.w1, s0 = t.s0;
+  lateral_psf_any(p, P, t.it.beam_off, abuf, ybuf, wlat, NS, t.KL, w0, w1, t.y1, s0);
+  __syncthreads();
+  float* out = p.frames + t.it.frame_off;
+  const int se = min(s0 + kChunk, NS);
+  if (P.kind == 0) {
+    const int wl = w1 - w0, n = (se - s0) * wl;
+    for (int i = tid; i < n; i += NT) {
+      const int s = i / wl, j = i - s * wl;
+      __stcs(&out[(long long)(s0 + s) * NL + w0 + j], ybuf[j * kRowStride + s]);
+    }
+  } else {
+    const int e0 = P.wedge_off[t.tile], e1 = P.wedge_off[t.tile + 1];
+    for (int e = e0 + tid; e < e1; e += NT) {
+      const float4 qv = __ldg(&P.wedge[e]);
+      const int pix = __float_as_int(qv.x);
+      const float fl = qv.y, fs = qv.z;
+      float v = 0.f;
+      if (fl >= 0.f) {
+        const int la = min((int)fl, NL - 2), sa = min((int)fs, NS - 2);
+        const float al = fl - (float)la, bb = fs - (float)sa;
+        const float* r0p = ybuf + (la - w0) * kRowStride + (sa - s0);
+        const float* r1p = r0p + kRowStride;
+        const float y00 = r0p[0], y01 = r0p[1];
+        const float y10 = r1p[0], y11 = r1p[1];
+        const float top = fmaf(al, y10 - y00, y00), bot = fmaf(al, y11 - y01, y01);
+        v = fmaf(bb, bot - top, top);
+      }
+      __stcs(&out[pix], v);
+    }
+  }
+}
+
 template <int NT>
 __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArgs& a, int blk) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int GB = a.GB;
-  // every thread reads its item and probe (the same addresses: broadcast
-  // loads); no block-wide set-up
-  const int n_items = p.n_items_dev ? *p.n_items_dev : p.n_items;
-  int item, tile;
-  if (a.units) {
-    const int2 u = a.units[a.n_units_a + blk];
-    item = u.x;
-    tile = u.y;
-  } else {
-    item = blk / a.gpi_image;
-    tile = blk - item * a.gpi_image;
-  }
-  if (item >= n_items) return;
-  const EnvItem it = p.items[item];
-  const DevProbe& P = p.probes[it.probe];
-  const int NL = P.nl, NS = P.ns, KL = P.k_lat;
-  const int nchunk = (NS + kChunk - 1) / kChunk;
-  const int q = tile / nchunk, k = tile - q * nchunk;
-  const int w0 = q * GB, w1 = min(w0 + GB, NL);
-  if (w0 >= NL) return;   // past this probe's tiles (uniform)
-  const int y1 = min(w1 + 1, NL);                                    // log rows w0 .. y1-1
-  const int s0 = k * kChunk, sw = min(kChunk + 1, NS - s0);          // staged samples s0 .. s0+sw-1
-  // staged rows r0 = w0 - KL .. r0 + nrows - 1, zero outside the frame,
-  // past the last needed row and past the line's end, so that the lateral
-  // PSF needs no edge tests (adding w * 0 leaves a sum unchanged exactly:
-  // the sums never hold -0)
-  const int r0 = w0 - KL;
-  const int nrows = (((y1 - w0) + kLatLines - 1) / kLatLines) * kLatLines + 2 * KL;
-  const int a0 = max(r0, 0), a1 = min(y1 + KL, NL);                  // rows present in the line buffer
+  TileCtx t;
+  if (!tile_ctx(p, a, blk, t)) return;   // uniform over the block
   const int tid = threadIdx.x;
   if (a.done) {
     __shared__ int ready;
     if (tid == 0) {
       ready = 1;
       const int G = a.G;
-      for (int g = a0 / G; g <= (a1 - 1) / G && ready; ++g) {
-        const unsigned* f = a.done + (long long)item * a.gpi_lines + g;
+      for (int g = t.a0 / G; g <= (t.a1 - 1) / G && ready; ++g) {
+        const unsigned* f = a.done + (long long)t.item * a.gpi_lines + g;
         const long long t0 = clock64();
         unsigned v;
         for (;;) {
@@ -456,77 +559,10 @@ __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArg
   float2* abuf = reinterpret_cast<float2*>(smem);                    // [nrows][kRowStride] (AR, AT)
   float* ybuf = reinterpret_cast<float*>(smem + a.off_y);            // [y1 - w0][kRowStride]: E, then the log image
   float* wlat = reinterpret_cast<float*>(smem + a.off_wlat);
-  for (int t = tid; t < 2 * KL + 1; t += NT) wlat[t] = __ldg(&P.w_lat[t]);
-  {
-    const float2* src = a.beam + it.beam_off + s0;
-    const float* esrc = a.ebeam + it.beam_off + s0;
-    const int ne = y1 - w0;
-    if ((NS & 3) == 0 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) &&
-        ((reinterpret_cast<uintptr_t>(esrc) & 15u) == 0)) {
-      // asynchronous 16-byte copies (two pairs, four energies), zero-filled
-      // past the row's end and for rows outside the frame
-      constexpr int PPA = kRowStride / 2;                            // 16-byte pieces per pair row
-      for (int t = tid; t < nrows * PPA; t += NT) {
-        const int r = t / PPA, c = (t - r * PPA) * 2;
-        const int line = r0 + r;
-        const bool present = line >= a0 && line < a1 && c < sw;
-        const float2* g = present ? src + (long long)line * NS + c : a.beam;
-        umma::cp_async16(abuf + r * kRowStride + c, g, present ? 16u : 0u);
-      }
-      constexpr int PPE = kRowStride / 4;                            // 16-byte pieces per energy row
-      for (int t = tid; t < ne * PPE; t += NT) {
-        const int r = t / PPE, c = (t - r * PPE) * 4;
-        const bool present = c < sw;
-        const float* g = present ? esrc + (long long)(w0 + r) * NS + c : a.ebeam;
-        umma::cp_async16(ybuf + r * kRowStride + c, g, present ? 16u : 0u);
-      }
-      umma::cp_async_commit();
-      umma::cp_async_wait<0>();
-    } else {
-      for (int t = tid; t < nrows * kRowStride; t += NT) {
-        const int r = t / kRowStride, c = t - r * kRowStride;
-        const int line = r0 + r;
-        abuf[t] = line >= a0 && line < a1 && c < sw ? __ldcg(src + (long long)line * NS + c) : make_float2(0.f, 0.f);
-      }
-      for (int t = tid; t < ne * kRowStride; t += NT) {
-        const int r = t / kRowStride, c = t - r * kRowStride;
-        ybuf[t] = c < sw ? __ldcg(esrc + (long long)(w0 + r) * NS + c) : 0.f;
-      }
-    }
-  }
+  tile_stage(a, t, abuf, ybuf, wlat, tid, NT);
+  umma::cp_async_wait<0>();
   __syncthreads();
-
-  lateral_psf_any(p, P, it.beam_off, abuf, ybuf, wlat, NS, KL, w0, w1, y1, s0);
-  __syncthreads();
-
-  float* out = p.frames + it.frame_off;
-  const int se = min(s0 + kChunk, NS);
-  if (P.kind == 0) {
-    const int wl = w1 - w0, n = (se - s0) * wl;
-    for (int t = tid; t < n; t += NT) {
-      const int s = t / wl, j = t - s * wl;
-      __stcs(&out[(long long)(s0 + s) * NL + w0 + j], ybuf[j * kRowStride + s]);
-    }
-  } else {
-    const int e0 = P.wedge_off[tile], e1 = P.wedge_off[tile + 1];
-    for (int e = e0 + tid; e < e1; e += NT) {
-      const float4 qv = __ldg(&P.wedge[e]);
-      const int pix = __float_as_int(qv.x);
-      const float fl = qv.y, fs = qv.z;
-      float v = 0.f;
-      if (fl >= 0.f) {
-        const int la = min((int)fl, NL - 2), sa = min((int)fs, NS - 2);
-        const float al = fl - (float)la, bb = fs - (float)sa;
-        const float* r0p = ybuf + (la - w0) * kRowStride + (sa - s0);
-        const float* r1p = r0p + kRowStride;
-        const float y00 = r0p[0], y01 = r0p[1];
-        const float y10 = r1p[0], y11 = r1p[1];
-        const float top = fmaf(al, y10 - y00, y00), bot = fmaf(al, y11 - y01, y01);
-        v = fmaf(bb, bot - top, top);
-      }
-      __stcs(&out[pix], v);
-    }
-  }
+  tile_compute(p, t, abuf, ybuf, wlat, tid, NT);
 }
 
 __global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, SplitArgs a) {
