@@ -77,6 +77,10 @@ CONV_SHAPES = [
     (2, 64, 64, 128, 128, 1, 128, 0),       # enc2a/b, dec2b
     (2, 64, 64, 128, 256, 2, 128, 0),       # down3
     (2, 32, 32, 256, 256, 1, 256, 0),       # enc3a/b (bottleneck)
+    (2, 128, 128, 128, 64, 1, 128, 0),      # dec1a (the concatenated skip)
+    (2, 64, 64, 256, 128, 1, 256, 0),       # dec2a (the concatenated skip)
+    (2, 256, 256, 32, 64, 2, 64, 32),       # down1 reading the skip half of its concatenation buffer
+    (2, 256, 256, 32, 32, 1, 64, 32),       # a 32-channel haloed box read out of a 64-channel buffer
 ]
 
 
@@ -117,6 +121,27 @@ def test_conv3x3_elementwise_production_shapes(B, H, W, Cin, Cout, stride, cs_in
     call("us_conv3x3_wgrad", dev(xfull), cs_in, co_in, dev(dy), Cout, 0, gwt, B, H, W, Cin, Cout, stride, err)
     to_t = lambda t: t.permute(1, 2, 3, 0).reshape(9 * Cin, Cout)
     within(gwt.double().cpu(), to_t(gw), to_t(Aw), 1e-6, 1e-4, 1e-9, "weight gradient")
+    assert int(err.item()) == 0
+
+
+@pytest.mark.parametrize("Cin,Cout", [(32, 32), (8, 32), (64, 64)])
+def test_conv3x3_writes_a_channel_window_of_a_wider_buffer(Cin, Cout):
+    """The forward into channels [Cout, 2 Cout) of a 2 Cout-channel buffer
+    (the encoder's skip into its concatenation buffer): the window holds the
+    convolution, the other channels keep their contents."""
+    B, H, W = 2, 256, 256
+    g = torch.Generator().manual_seed(31 + Cin + Cout)
+    x = relu_input(g, (B, H, W, Cin))
+    w = bf(torch.randn((Cout, 3, 3, Cin), generator=g, dtype=torch.float64) * (2.0 / (9 * Cin)) ** 0.5)
+    bias = (torch.randn(Cout, generator=g, dtype=torch.float64) * 0.1).float().double()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = torch.full((B, H, W, 2 * Cout), 7.0, dtype=torch.bfloat16, device="cuda")
+    call("us_conv3x3_fwd", dev(x), Cin, 0, dev(w), bias.float().cuda(), y, 2 * Cout, Cout, B, H, W, Cin, Cout, 1, 1,
+         err)
+    ref = S.conv3x3(x, w, bias, 1, relu=True)
+    A = S.conv3x3(x.abs(), w.abs(), bias.abs(), 1, relu=False)
+    within(y[..., Cout:].double().cpu(), ref, A, 2.0 ** -8, 1e-4, 1e-6, "window")
+    assert bool((y[..., :Cout] == 7.0).all())
     assert int(err.item()) == 0
 
 
