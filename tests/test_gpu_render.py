@@ -614,3 +614,27 @@ def test_graph_replays_of_a_mixed_probe_batch_match_plain(shape):
         st.synchronize()
         assert np.array_equal(got.cpu().numpy(), want.cpu().numpy()), (shape, k)
     sim.close()
+
+
+def test_host_render_in_sub_batches_with_mixed_frame_sizes():
+    """Sub-batched host renders of a batch mixing three frame sizes (the
+    sub-batch boundaries fall between envs of different probes): equal to
+    the device render of the whole batch."""
+    spec = scene.VolumeSpec(128, 128, 128, 1.0, 2, 93)
+    lab, hu = scene.make_volume(spec)
+    probes = [scene.curvilinear_probe(128, 256, 80.0, 60.0, 40.0, 128, 128),
+              scene.curvilinear_probe(96, 192, 80.0, 60.0, 40.0, 96, 96), scene.linear_probe(64, 128, 80.0, 0.5)]
+    B = 420
+    envs = np.array([[0, (b * 5) % 3] for b in range(B)], np.int32)
+    poses = np.ascontiguousarray(scene.dorsal_poses(spec, B, 17), np.float32)
+    wl = scene.Workload("mix3h", [(spec, lab, hu)], probes, envs, poses, seed=6)
+    sim = gpu_sim(wl)
+    off = sim.frame_layout(envs)
+    assert int(off[-1]) * 4 >= 16 * 2 ** 20       # sub-batched
+    dev = torch.empty(int(off[-1]), device="cuda")
+    sim.render(envs, torch.from_numpy(poses).cuda(), 3, 9, dev)
+    torch.cuda.synchronize()
+    host = torch.full((int(off[-1]),), -3.0).pin_memory()
+    sim.render_host(envs, poses, 3, 9, host.numpy())
+    assert np.array_equal(host.numpy(), dev.cpu().numpy())
+    sim.close()

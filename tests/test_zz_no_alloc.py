@@ -6,6 +6,8 @@ fixed array compiled into the library, so its frames must equal those of
 us_sim_render_plain (same kernels, same parameters) call after call, even
 though every call reuses the same scratch, and for every option set: the
 volume-anchored scatter maps included."""
+import gc
+
 import numpy as np
 import pytest
 
@@ -59,6 +61,9 @@ def test_static_scratch_matches_allocating_path_two_calls(sim_and_inputs):
     # the first call on the device may load the library's module and with it
     # the static array; the calls after it must not change device memory
     got_a = _render(sim.render_plain_static, sim, envs, poses_a, 77, 1)
+    # tensors of earlier tests that wait for the garbage collector would
+    # otherwise leave torch's count during the loop below
+    gc.collect()
     alloc_before = torch.cuda.memory_allocated()
     unchanged = []
     for _ in range(2):
@@ -70,6 +75,7 @@ def test_static_scratch_matches_allocating_path_two_calls(sim_and_inputs):
         assert np.abs(got - ref).max() <= 1e-3          # the frame tolerance of the parity tests
         assert np.array_equal(got, ref)                 # same kernels: identical in fact
     assert np.any(got_a > 0) and np.any(got_b > 0)
+    gc.collect()
     assert torch.cuda.memory_allocated() == alloc_before
     # device-wide free memory also moves with other contexts on the GPU:
     # one unchanged reading around a call is enough
