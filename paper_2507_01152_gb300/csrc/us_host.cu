@@ -913,11 +913,20 @@ us_status us_sim_render_host(us_sim* s, const us_env* envs, int32_t B, const flo
     return US_OK;
   }
   if (!s->copy_stream) {
-    if ((e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    // all or nothing: a partial set is released, so the next call retries
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[us_sim::kHostSub] = {};
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int k = 0; k < us_sim::kHostSub && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+      if (cs) cudaStreamDestroy(cs);
       return cuda_fail(s, e, "copy stream");
-    for (int k = 0; k < us_sim::kHostSub; ++k)
-      if ((e = cudaEventCreateWithFlags(&s->copy_ev[k], cudaEventDisableTiming)) != cudaSuccess)
-        return cuda_fail(s, e, "copy events");
+    }
+    s->copy_stream = cs;
+    for (int k = 0; k < us_sim::kHostSub; ++k) s->copy_ev[k] = ev[k];
   }
   const std::vector<EnvItem>& items = pl->items_batch;   // caller order, full-batch frame offsets
   auto off_of = [&](int b) -> long long { return b < B ? items[b].frame_off : pl->frame_floats; };
