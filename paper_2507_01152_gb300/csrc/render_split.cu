@@ -35,46 +35,72 @@
 
 namespace ussim {
 
-// axial PSF of two padded rows (K zeros, NS samples, K zeros each): the
-// scatter pattern's and the reflection impulses', written as (P (x) R_imp,
-// P (x) T) pairs to dst[0 .. NS-1] (the line buffer).  KC > 0: the
-// half-width is the compile-time KC (== K) and the taps sit in registers;
-// KC = 0: any K, taps read from shared memory.  Same tap order as the plain
-// kernel.  rmask bit i: some reflection impulse of samples 32 i .. 32 i + 31
-// is not zero.  The impulses are >= 0, so an output chunk whose window
-// (chunks i - 1 .. i + 1, K <= 32) holds none is exactly +0, as the full
-// sum of zero taps would be: the warp skips its reflection taps there.
+// axial PSF of two padded rows (K zeros, NS samples, K zeros each, and one
+// more element): the scatter pattern's and the reflection impulses', written
+// as (P (x) R_imp, P (x) T) pairs to dst[0 .. NS-1] (the line buffer).
+// KC > 0: the half-width is the compile-time KC (== K), the taps sit in
+// registers and each lane filters two adjacent samples (s, s + 1) of a
+// 64-sample chunk from K + 1 8-byte loads of each row (rows 8-byte aligned
+// at even offsets), storing both pairs as one 16-byte store when dst is
+// 16-byte aligned; KC = 0: any K, one sample a lane, taps read from shared
+// memory.  Same tap order as the plain kernel.  rmask bit i: some
+// reflection impulse of samples 32 i .. 32 i + 31 is not zero.  The
+// impulses are >= 0, so an output chunk whose window holds none is exactly
+// +0, as the full sum of zero taps would be: the warp skips its reflection
+// taps there.
 template <int KC>
 __device__ __forceinline__ void axial_psf_rows(const float* pt, const float* pr, int NS, const float* w, int K,
                                                int lane, unsigned rmask, float2* dst) {
-  const int taps = 2 * K + 1;
-  float wr[KC > 0 ? 2 * KC + 1 : 1];
+  if constexpr (KC > 0) {
+    constexpr int TC = 2 * KC + 1, NV = KC + 1;   // taps; 8-byte loads covering s .. s + 2 KC + 1
+    float wr[TC];
 #pragma unroll
-  for (int k = 0; k < (KC > 0 ? 2 * KC + 1 : 0); ++k) wr[k] = w[k];
-  for (int c = 0; c < NS; c += 32) {
-    const int s = c + lane, ci = c >> 5;
-    const bool refl = ((ci == 0 ? rmask << 1 : rmask >> (ci - 1)) & 7u) != 0;   // warp-uniform
-    if (s < NS) {
-      float acc_t = 0.f, acc_r = 0.f;
-      const float* qt = pt + s;
-      const float* qr = pr + s;
-      if constexpr (KC > 0) {
-        if (refl) {
+    for (int k = 0; k < TC; ++k) wr[k] = w[k];
+    const bool wide = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;   // warp-uniform
+    // two filtered rows from one padded row: output s takes elements
+    // s + k, output s + 1 elements s + 1 + k (k = 0 .. 2 KC)
+    auto filter2 = [&](const float* q, float& o0, float& o1) {
+      float2 v[NV];
 #pragma unroll
-          for (int k = 0; k < 2 * KC + 1; ++k) {
-            acc_t = fmaf(wr[k], qt[k], acc_t);
-            acc_r = fmaf(wr[k], qr[k], acc_r);
-          }
+      for (int m = 0; m < NV; ++m) v[m] = reinterpret_cast<const float2*>(q)[m];
+      o0 = 0.f;
+      o1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < TC; ++k) {
+        o0 = fmaf(wr[k], (k & 1) ? v[k >> 1].y : v[k >> 1].x, o0);
+        o1 = fmaf(wr[k], (k & 1) ? v[(k + 1) >> 1].x : v[k >> 1].y, o1);
+      }
+    };
+    for (int c = 0; c < NS; c += 64) {
+      const int s = c + 2 * lane, ci = c >> 5;
+      // outputs c .. c + 63 read impulses c - KC .. c + 63 + KC: chunks ci - 1 .. ci + 2
+      const bool refl = ((ci == 0 ? rmask << 1 : rmask >> (ci - 1)) & 15u) != 0;   // warp-uniform
+      if (s < NS) {
+        float t0, t1, r0 = 0.f, r1 = 0.f;
+        filter2(pt + s, t0, t1);
+        if (refl) filter2(pr + s, r0, r1);
+        if (s + 1 < NS && wide) {
+          *reinterpret_cast<float4*>(dst + s) = make_float4(r0, t0, r1, t1);
         } else {
-#pragma unroll
-          for (int k = 0; k < 2 * KC + 1; ++k) acc_t = fmaf(wr[k], qt[k], acc_t);
+          dst[s] = make_float2(r0, t0);
+          if (s + 1 < NS) dst[s + 1] = make_float2(r1, t1);
         }
-      } else {
+      }
+    }
+  } else {
+    const int taps = 2 * K + 1;
+    for (int c = 0; c < NS; c += 32) {
+      const int s = c + lane, ci = c >> 5;
+      const bool refl = ((ci == 0 ? rmask << 1 : rmask >> (ci - 1)) & 7u) != 0;   // warp-uniform
+      if (s < NS) {
+        float acc_t = 0.f, acc_r = 0.f;
+        const float* qt = pt + s;
+        const float* qr = pr + s;
         for (int k = 0; k < taps; ++k) acc_t = fmaf(w[k], qt[k], acc_t);
         if (refl)
           for (int k = 0; k < taps; ++k) acc_r = fmaf(w[k], qr[k], acc_r);
+        dst[s] = make_float2(acc_r, acc_t);
       }
-      dst[s] = make_float2(acc_r, acc_t);
     }
   }
 }
@@ -240,7 +266,7 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
   if (!split_item(p, a, blk, G, cx, group)) return;
   const DevProbe& P = cx.P;
   const int NL = P.nl, NS = P.ns, KA = P.k_ax;
-  const int RS = (NS + 2 * KA) | 1;
+  const int RS = lines_row_stride(NS, KA);
   const int g0 = group * G, g1 = min(g0 + G, NL);
   const int L0 = max(g0 - cx.pair.dmax, 0), L1 = min(g1 + cx.pair.dmax, NL);   // labels the stencil can reach
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NW = blockDim.x >> 5;
@@ -313,6 +339,10 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
       prow[KA + NS + q] = 0.f;
       rrow[q] = 0.f;
       rrow[KA + NS + q] = 0.f;
+    }
+    if (lane == 0) {   // the element past the padded row, read by the two-output filter
+      prow[2 * KA + NS] = 0.f;
+      rrow[2 * KA + NS] = 0.f;
     }
   }
   {
@@ -602,7 +632,7 @@ bool split_shape_fits(SplitShape& sh, const std::vector<ProbeHost>& probes, int 
   int gl = 0;
   for (const ProbeHost& ph : probes) {
     const int NL = ph.desc.n_lines, NS = ph.desc.n_samples;
-    const int rs = (NS + 2 * ph.k_ax) | 1;
+    const int rs = lines_row_stride(NS, ph.k_ax);
     zb = std::max(zb, (long long)G * rs * 4);
     lab = std::max(lab, (long long)std::min(NL, G + 2 * kThetaDMax) * NS);
     gl = std::max(gl, (NL + G - 1) / G);

@@ -82,6 +82,11 @@ cudaError_t launch_fused(const RenderParams& p, const FusedShape& s, cudaStream_
 constexpr int kChunk = 128;
 constexpr int kImageThreads = 256;
 constexpr int kRowStride = kChunk + 4;   // shared row stride, floats (16-byte rows)
+// pass A's padded rows (K zeros, NS samples, K zeros) in floats: one more
+// element, which the two-output axial filter reads past an odd row's end,
+// rounded up to 16 bytes, so that every row starts 16-byte aligned and every
+// even sample offset of it is 8-byte aligned
+__host__ __device__ inline int lines_row_stride(int NS, int K) { return (NS + 2 * K + 1 + 3) & ~3; }
 struct SplitArgs {
   float2* beam = nullptr;   // axially filtered (AR, AT) pairs, beam layout (per item beam_off)
   float* ebeam = nullptr;   // energy E of every beam sample, same layout
