@@ -520,8 +520,9 @@ __device__ __forceinline__ void tile_stage(const SplitArgs& a, const TileCtx& t,
 
 // A staged tile (visible to the block): lateral PSF, log image, then the
 // frame's pixels whose bilinear base falls in the tile.
+template <int NT>
 __device__ __forceinline__ void tile_compute(const RenderParams& p, const TileCtx& t, const float2* abuf, float* ybuf,
-                                             const float* wlat, int tid, int NT) {
+                                             const float* wlat, int tid) {
   const DevProbe& P = *t.P;
   const int NL = t.NL, NS = t.NS, w0 = t.w0, w1 = t.w1, s0 = t.s0;
   lateral_psf_any(p, P, t.it.beam_off, abuf, ybuf, wlat, NS, t.KL, w0, w1, t.y1, s0);
@@ -529,29 +530,39 @@ __device__ __forceinline__ void tile_compute(const RenderParams& p, const TileCt
   float* out = p.frames + t.it.frame_off;
   const int se = min(s0 + kChunk, NS);
   if (P.kind == 0) {
-    const int wl = w1 - w0, n = (se - s0) * wl;
-    for (int i = tid; i < n; i += NT) {
-      const int s = i / wl, j = i - s * wl;
-      __stcs(&out[(long long)(s0 + s) * NL + w0 + j], ybuf[j * kRowStride + s]);
-    }
+    // one line a lane (wedges are at most 32 lines), one sample a warp row
+    static_assert(NT % 32 == 0, "whole warps");
+    const int wl = w1 - w0, j = tid & 31;
+    if (j < wl)
+      for (int s = tid >> 5; s < se - s0; s += NT >> 5)
+        __stcs(&out[(long long)(s0 + s) * NL + w0 + j], ybuf[j * kRowStride + s]);
   } else {
+    // kPixU pixels a thread per step, their list entries loaded before any is used
+    constexpr int kPixU = 4;
     const int e0 = P.wedge_off[t.tile], e1 = P.wedge_off[t.tile + 1];
-    for (int e = e0 + tid; e < e1; e += NT) {
-      const float4 qv = __ldg(&P.wedge[e]);
-      const int pix = __float_as_int(qv.x);
-      const float fl = qv.y, fs = qv.z;
-      float v = 0.f;
-      if (fl >= 0.f) {
-        const int la = min((int)fl, NL - 2), sa = min((int)fs, NS - 2);
-        const float al = fl - (float)la, bb = fs - (float)sa;
-        const float* r0p = ybuf + (la - w0) * kRowStride + (sa - s0);
-        const float* r1p = r0p + kRowStride;
-        const float y00 = r0p[0], y01 = r0p[1];
-        const float y10 = r1p[0], y11 = r1p[1];
-        const float top = fmaf(al, y10 - y00, y00), bot = fmaf(al, y11 - y01, y01);
-        v = fmaf(bb, bot - top, top);
+    for (int e = e0 + tid; e < e1; e += kPixU * NT) {
+      float4 qv[kPixU];
+#pragma unroll
+      for (int u = 0; u < kPixU; ++u)
+        qv[u] = e + u * NT < e1 ? __ldg(&P.wedge[e + u * NT]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < kPixU; ++u) {
+        if (e + u * NT >= e1) break;
+        const int pix = __float_as_int(qv[u].x);
+        const float fl = qv[u].y, fs = qv[u].z;
+        float v = 0.f;
+        if (fl >= 0.f) {
+          const int la = min((int)fl, NL - 2), sa = min((int)fs, NS - 2);
+          const float al = fl - (float)la, bb = fs - (float)sa;
+          const float* r0p = ybuf + (la - w0) * kRowStride + (sa - s0);
+          const float* r1p = r0p + kRowStride;
+          const float y00 = r0p[0], y01 = r0p[1];
+          const float y10 = r1p[0], y11 = r1p[1];
+          const float top = fmaf(al, y10 - y00, y00), bot = fmaf(al, y11 - y01, y01);
+          v = fmaf(bb, bot - top, top);
+        }
+        __stcs(&out[pix], v);
       }
-      __stcs(&out[pix], v);
     }
   }
 }
@@ -592,7 +603,7 @@ __device__ __forceinline__ void image_body(const RenderParams& p, const SplitArg
   tile_stage(a, t, abuf, ybuf, wlat, tid, NT);
   umma::cp_async_wait<0>();
   __syncthreads();
-  tile_compute(p, t, abuf, ybuf, wlat, tid, NT);
+  tile_compute<NT>(p, t, abuf, ybuf, wlat, tid);
 }
 
 __global__ void __launch_bounds__(kImageThreads, 4) split_image(RenderParams p, SplitArgs a) {
