@@ -291,9 +291,9 @@ US_API us_status us_sim_render_debug(us_sim* sim, const us_env* envs, int32_t B,
  * frames out through library-owned device buffers (grown on demand).
  * Returns after the frames are in host memory (synchronous).  A batch of
  * 16 MB of frames or more renders as two to four contiguous sub-batches
- * (same frames: each env keeps its batch index), each copied out on a
- * library-owned stream while the next renders; the copies overlap the
- * renders when frames_host is pinned (page-locked) memory. */
+ * of halving size (same frames: each env keeps its batch index), each
+ * copied out on a library-owned stream while the next renders; the copies
+ * overlap the renders when frames_host is pinned (page-locked) memory. */
 US_API us_status us_sim_render_host(us_sim* sim, const us_env* envs, int32_t B, const float* poses_host,
                              uint64_t seed, uint64_t step, float* frames_host, void* stream);
 

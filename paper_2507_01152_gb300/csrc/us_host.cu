@@ -896,12 +896,15 @@ us_status us_sim_render_host(us_sim* s, const us_env* envs, int32_t B, const flo
   if ((e = cudaMemcpyAsync(s->d_host_poses, poses_host, pose_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(s, e, "pose copy");
   // A batch of 16 MB of frames or more renders as up to four contiguous
-  // sub-batches (env ranges of about equal frame bytes, at least 8 MB each,
-  // each keeping its envs' caller indices), and each sub-batch's frames go
-  // to the host on a copy stream while the next one renders.  A smaller
-  // batch renders in one piece: there the sub-batches' extra waves would
-  // cost more than the copy overlap gains.
+  // sub-batches (env ranges, each keeping its envs' caller indices), and
+  // each sub-batch's frames go to the host on a copy stream while the next
+  // one renders.  Sub-batch k holds about kSubRatio^k of the frame bytes
+  // (normalised; at least 8 MB on average): the copy to host memory runs at
+  // about half the render's rate, so each copy still hides behind the next,
+  // half-size render, and the one copy left after the last render is short.  A smaller batch renders in one piece: there the sub-batches'
+  // extra waves would cost more than the copy overlap gains.
   constexpr size_t kSubBytes = 8u << 20;
+  constexpr double kSubRatio = 0.5;
   const int n_sub = (int)std::min<size_t>({(size_t)us_sim::kHostSub, (size_t)B, std::max<size_t>(1, frame_bytes / kSubBytes)});
   if (n_sub == 1) {
     if ((r = do_render(s, envs, B, s->d_host_poses, seed, step, s->d_host_frames, nullptr, nullptr, nullptr, nullptr, 0,
@@ -930,11 +933,16 @@ us_status us_sim_render_host(us_sim* s, const us_env* envs, int32_t B, const flo
   }
   const std::vector<EnvItem>& items = pl->items_batch;   // caller order, full-batch frame offsets
   auto off_of = [&](int b) -> long long { return b < B ? items[b].frame_off : pl->frame_floats; };
+  double wsum = 0, wk = 1;
+  for (int k = 0; k < n_sub; ++k, wk *= kSubRatio) wsum += wk;
   int b0 = 0;
   us_status rr = US_OK;
-  for (int k = 0; k < n_sub && b0 < B; ++k) {
+  double cum = 0;
+  wk = 1;
+  for (int k = 0; k < n_sub && b0 < B; ++k, wk *= kSubRatio) {
     int b1 = b0 + 1;
-    const long long target = (long long)(k + 1) * pl->frame_floats / n_sub;
+    cum += wk;
+    const long long target = (long long)((double)pl->frame_floats * (cum / wsum));
     while (b1 < B && (k + 1 == n_sub || off_of(b1) < target)) ++b1;
     const long long f0 = off_of(b0), f1 = off_of(b1);
     if ((rr = do_render(s, envs + b0, b1 - b0, s->d_host_poses, seed, step, s->d_host_frames + f0, nullptr, nullptr,
