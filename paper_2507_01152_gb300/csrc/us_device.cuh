@@ -127,9 +127,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// uniform in (0,1): odd multiple of 2^-24 from the top 23 bits (exact)
+// uniform in (0,1): odd multiple of 2^-24 from the top 23 bits k = w >> 9,
+// (2k + 1) 2^-24, formed exactly as (1 + k 2^-23) - (1 - 2^-24): the float
+// with exponent 0 and mantissa k, less a constant; the difference is
+// representable, so the subtraction is exact
 __device__ __forceinline__ float u01(unsigned w) {
-  return __int2float_rn((int)((w >> 9) * 2u + 1u)) * 5.9604644775390625e-08f;
+  return __uint_as_float(0x3F800000u | (w >> 9)) - 0.999999940395355224609375f;
 }
 
 // ---------------------------------------------------------- index path

@@ -81,6 +81,8 @@ CONV_SHAPES = [
     (2, 64, 64, 256, 128, 1, 256, 0),       # dec2a (the concatenated skip)
     (2, 256, 256, 32, 64, 2, 64, 32),       # down1 reading the skip half of its concatenation buffer
     (2, 256, 256, 32, 32, 1, 64, 32),       # a 32-channel haloed box read out of a 64-channel buffer
+    (1, 40, 20, 128, 128, 1, 128, 0),       # streamed weights, ragged tiles (40 = 16 + 16 + 8 rows, 20 = 8 + 8 + 4)
+    (3, 24, 36, 128, 128, 1, 256, 128),     # streamed weights, ragged, the upper half of a 256-channel buffer
 ]
 
 
