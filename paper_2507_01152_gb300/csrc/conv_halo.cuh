@@ -276,43 +276,50 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
 }
 
 // The same haloed-box forward for inputs too wide for resident weights
-// (CIN = 128; COUT = 64 or 128): the box of each tile is staged once, as
-// above, and the weights are streamed through a ring of R chunks, each the
-// COUT x 64 block of one tap and 64 input channels, copied by a 2-D tensor
-// copy with the 128-byte swizzle (rows of 64 BF16, read by the MMAs through
-// swizzled K-major descriptors).  Chunks go tap by tap, the 64-channel
-// blocks of a tap in order: a tile's 9 CIN / 64 chunks hold its whole
-// weight set, and the next tile's chunks follow in the same ring.  Roles:
-// warp 0 (one thread) copies the boxes, up to S tiles ahead; warp 1 (one
-// thread) copies the weight chunks, up to R ahead; warp 2 (one thread)
-// issues the 4 MMAs of 128 x COUT x 16 of each chunk into one half of the
-// double-buffered TMEM accumulator and releases the chunk's slot by a
-// commit; two groups of four epilogue warps, tile g to group g mod 2 (TMEM
-// buffer g mod 2), add the bias, apply the ReLU and store BF16 pixels.
-// Every wait is bounded, with the abort protocol of the kernel above.
+// (CIN a multiple of 64; COUT = 64 or 128).  A CTA takes its tiles in pairs
+// (local tiles 2p and 2p + 1; a missing second tile of the last pair reads
+// zeros and stores nothing), and the pair's two MMA issuers share every
+// weight chunk.  The weights stream through a ring of R chunks, each the
+// COUT x 64 block of one tap and one 64-channel block of the input, copied
+// by a 2-D tensor copy with the 128-byte swizzle (no repacking: a chunk is
+// a box of the [COUT][3][3][CIN] array) and read through swizzled K-major
+// descriptors; a slot is free again once both issuers' MMAs on it are
+// done.  Each tile's box is staged in its 64-channel blocks through two
+// block slots per issuer (block k of pair p is use u = p NKC + k, in slot
+// u mod 2), and the chunks run block-major (the 9 taps of block 0, then of
+// block 1, ...), so a block loads while the issuer works on the one
+// before.  Roles: warp 0 (one thread) copies the
+// box blocks, warp 1 (one thread) the weight chunks, warps 2 and 3 (one
+// thread each) issue the 4 MMAs of 128 x COUT x 16 of each chunk for tile
+// 2p and tile 2p + 1 into their double-buffered TMEM accumulators; two
+// groups of four epilogue warps take pairs p with p mod 2 = group (TMEM
+// buffer p mod 2 of both issuers), add the bias, apply the ReLU and store
+// BF16 pixels.  Every wait is bounded, with the abort protocol of the
+// kernel above.
 template <int CIN, int COUT>
 struct HaloStreamCfg {
   static constexpr int TY = 16, TX = 8;
   static constexpr int BY = TY + 2, BX = TX + 2;
-  static constexpr int NCH = CIN / 8;                              // 16-byte channel planes of the box
-  static constexpr uint32_t BOX = (uint32_t)BY * BX * 16;
+  static constexpr int NKC = CIN / 64;                             // 64-channel blocks
+  static constexpr int HPL = 8;                                    // 16-byte channel planes per block
+  static constexpr uint32_t BOX = (uint32_t)BY * BX * 16;          // bytes of one plane's copy
   static constexpr uint32_t PLANE = (BOX + 127u) / 128u * 128u;
-  static constexpr uint32_t STAGE = NCH * PLANE;
-  static constexpr int NKC = CIN / 64;                             // 64-channel blocks per tap
-  static constexpr int NCHUNK = 9 * NKC;                           // weight chunks per tile
+  static constexpr uint32_t HSTAGE = HPL * PLANE;                  // one block of one box
+  static constexpr int X = 2;                                      // issuers: tiles of a pair
+  static constexpr int NB = NKC < 2 ? NKC : 2;                     // block slots per issuer
+  static constexpr int NCHUNK = 9 * NKC;                           // weight chunks per pair
   static constexpr uint32_t WCH = (uint32_t)COUT * 128;            // bytes of one chunk
   static constexpr int R = 8;                                      // weight ring slots
   static constexpr uint32_t WRING = R * WCH;
-  static constexpr int S0 = (int)((226u * 1024u - WRING - 1024u - 4u * COUT) / STAGE);
-  static constexpr int S = S0 > 4 ? 4 : S0;                        // box stages
+  static constexpr uint32_t BOXES = (uint32_t)X * NB * HSTAGE;
   static constexpr int kEpiGroups = 2;
-  static constexpr int kEpiWarp = 3;
+  static constexpr int kEpiWarp = 2 + X;
   static constexpr int THREADS = 32 * (kEpiWarp + 4 * kEpiGroups);
-  static constexpr uint32_t NCOLS = 2 * COUT;                      // TMEM: two accumulators
-  static constexpr uint32_t SMEM = WRING + S * STAGE + 4 * COUT + 1024;   // + bias, 1024-byte alignment slack
+  static constexpr uint32_t NCOLS = 2u * X * COUT;                 // TMEM: two accumulators per issuer
+  static constexpr uint32_t SMEM = WRING + BOXES + 4 * COUT + 1024;   // + bias, 1024-byte alignment slack
   static_assert(CIN % 64 == 0 && (COUT == 64 || COUT == 128), "streamed halo conv shapes");
-  static_assert(S >= 2, "box stages do not fit");
-  static_assert(SMEM <= 227u * 1024u, "shared memory");
+  static_assert(NCOLS <= 512, "accumulators exceed TMEM");
+  static_assert(SMEM <= 226u * 1024u, "shared memory");
 };
 
 template <int CIN, int COUT>
@@ -320,14 +327,14 @@ __global__ void __launch_bounds__(HaloStreamCfg<CIN, COUT>::THREADS, 1)
     conv3x3_halo_stream_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw,
                                const HaloArgs a, unsigned* err) {
   using C = HaloStreamCfg<CIN, COUT>;
-  constexpr int S = C::S, R = C::R, NCH = C::NCH, NKC = C::NKC, NCHUNK = C::NCHUNK;
+  constexpr int R = C::R, NKC = C::NKC, NB = C::NB, HPL = C::HPL, NCHUNK = C::NCHUNK, X = C::X;
   constexpr uint32_t IDESC = idesc_bf16_f32(kBM, COUT);
   extern __shared__ __align__(1024) uint8_t smem_stream[];
   uint8_t* smem = smem_stream + ((1024u - (smem_u32(smem_stream) & 1023u)) & 1023u);
   uint8_t* wring = smem;                         // R weight chunks (1024-byte aligned swizzle atoms)
-  uint8_t* box = smem + C::WRING;                // S staged boxes
-  float* sbias = reinterpret_cast<float*>(box + (size_t)S * C::STAGE);
-  __shared__ uint64_t bfull[S], bempty[S], wfull[R], wempty[R], tfull[2], tempty[2], done;
+  uint8_t* box = smem + C::WRING;                // block slot j of issuer t at (t NB + j) HSTAGE
+  float* sbias = reinterpret_cast<float*>(box + C::BOXES);
+  __shared__ uint64_t hfull[X][NB], hempty[X][NB], wfull[R], wempty[R], tfull[X][2], tempty[X][2], done[X];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -337,19 +344,21 @@ __global__ void __launch_bounds__(HaloStreamCfg<CIN, COUT>::THREADS, 1)
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&bfull[s], 1);
-      mbar_init(&bempty[s], 1);
+    for (int t = 0; t < X; ++t) {
+      for (int j = 0; j < NB; ++j) {
+        mbar_init(&hfull[t][j], 1);
+        mbar_init(&hempty[t][j], 1);
+      }
+      for (int q = 0; q < 2; ++q) {
+        mbar_init(&tfull[t][q], 1);
+        mbar_init(&tempty[t][q], 128);   // the four warps of the epilogue group of buffer q
+      }
+      mbar_init(&done[t], 1);
     }
     for (int r = 0; r < R; ++r) {
       mbar_init(&wfull[r], 1);
-      mbar_init(&wempty[r], 1);
+      mbar_init(&wempty[r], X);          // both issuers release a chunk
     }
-    for (int q = 0; q < 2; ++q) {
-      mbar_init(&tfull[q], 1);
-      mbar_init(&tempty[q], 128);   // the four warps of the epilogue group of buffer q
-    }
-    mbar_init(&done, 1);
     abort_flag = 0;
     mbar_init_fence();
   }
@@ -358,6 +367,9 @@ __global__ void __launch_bounds__(HaloStreamCfg<CIN, COUT>::THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   const int n_local = a.n_tiles > (int)blockIdx.x ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int n_pairs = (n_local + 1) / 2;
+  // tile g of this CTA; g = n_local (the missing second tile of a last
+  // pair) lies past the batch, where the box copies read zeros
   auto tile_of = [&](int g, int& b, int& y0, int& x0) {
     const int t = (int)blockIdx.x + g * (int)gridDim.x;
     const int per = a.tiles_y * a.tiles_x;
@@ -368,127 +380,158 @@ __global__ void __launch_bounds__(HaloStreamCfg<CIN, COUT>::THREADS, 1)
   };
 
   if (warp == 0) {
-    // ------------------------------------------------------- box copies
+    // -------------------------------------------------------- box blocks
     if (lane == 0) {
-      int g = 0;
-      for (; g < n_local && !abort_flag; ++g) {
-        const int s = g % S;
-        if (g >= S && !wait_or_abort(&bempty[s], (uint32_t)((g / S - 1) & 1), &abort_flag, err)) break;
-        int b, y0, x0;
-        tile_of(g, b, y0, x0);
-        mbar_arrive_expect_tx(&bfull[s], NCH * C::BOX);
-        const uint32_t dst = smem_u32(box + (size_t)s * C::STAGE), bar = smem_u32(&bfull[s]);
+      int fills[X][NB] = {};   // copies issued into each slot
+      bool ok = true;
+      for (int p = 0; p < n_pairs && ok && !abort_flag; ++p) {
+        for (int k = 0; k < NKC && ok; ++k) {
+          const int u = p * NKC + k, j = u % NB, n = u / NB;   // n: this slot's fill index
+          for (int t = 0; t < X; ++t) {
+            if (n >= 1 && !wait_or_abort(&hempty[t][j], (uint32_t)((n - 1) & 1), &abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            int b, y0, x0;
+            tile_of(2 * p + t, b, y0, x0);
+            mbar_arrive_expect_tx(&hfull[t][j], HPL * C::BOX);
+            const uint32_t dst = smem_u32(box + (size_t)(t * NB + j) * C::HSTAGE), bar = smem_u32(&hfull[t][j]);
 #pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) tma_load_4d(dst + ch * C::PLANE, &tx, ch * 8, x0 - 1, y0 - 1, b, bar);
+            for (int pl = 0; pl < HPL; ++pl)
+              tma_load_4d(dst + pl * C::PLANE, &tx, (k * HPL + pl) * 8, x0 - 1, y0 - 1, b, bar);
+            ++fills[t][j];
+          }
+        }
       }
-      // every issued copy must land before the CTA may exit
-      for (int q = g > S ? g - S : 0; q < g; ++q)
-        if (!mbar_wait(&bfull[q % S], (uint32_t)((q / S) & 1))) atomicOr(err, kErrWaitTimeout);
+      // every issued copy must land before the CTA may exit: the last fill of each slot
+#pragma unroll
+      for (int t = 0; t < X; ++t)
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+          if (fills[t][j] > 0 && !mbar_wait(&hfull[t][j], (uint32_t)((fills[t][j] - 1) & 1)))
+            atomicOr(err, kErrWaitTimeout);
     }
     __syncwarp();
   } else if (warp == 1) {
     // ---------------------------------------------------- weight chunks
     if (lane == 0) {
-      const int nq = n_local * NCHUNK;
+      const int nq = n_pairs * NCHUNK;
       int q = 0;
       for (; q < nq && !abort_flag; ++q) {
         const int r = q % R;
         if (q >= R && !wait_or_abort(&wempty[r], (uint32_t)((q / R - 1) & 1), &abort_flag, err)) break;
-        const int c = q % NCHUNK, tap = c / NKC, kc = c - tap * NKC;
+        const int c = q % NCHUNK, k = c / 9, tap = c - 9 * k;
         mbar_arrive_expect_tx(&wfull[r], C::WCH);
-        tma_load_2d(smem_u32(wring + (size_t)r * C::WCH), &tw, tap * CIN + kc * 64, 0, smem_u32(&wfull[r]));
+        tma_load_2d(smem_u32(wring + (size_t)r * C::WCH), &tw, tap * CIN + k * 64, 0, smem_u32(&wfull[r]));
       }
       for (int p = q > R ? q - R : 0; p < q; ++p)
         if (!mbar_wait(&wfull[p % R], (uint32_t)((p / R) & 1))) atomicOr(err, kErrWaitTimeout);
     }
     __syncwarp();
-  } else if (warp == 2) {
+  } else if (warp < C::kEpiWarp) {
     // ------------------------------------------------------- MMA issue
-    // The chunk loop is unrolled: every A descriptor is the box's base
-    // descriptor plus a constant offset (in 16-byte units, added to the low
-    // word: addresses stay below 256 KB, so the address field cannot carry),
-    // and every B descriptor the ring slot's plus 2 per K step of 16.
+    // issuer t takes tile 2p + t of every pair.  The chunk loop is
+    // unrolled: every A descriptor is the block slot's base descriptor plus
+    // a constant offset (in 16-byte units, added to the low word: addresses
+    // stay below 256 KB, so the address field cannot carry), every B
+    // descriptor the ring slot's plus 2 per K step of 16.
+    const int t = warp - 2;
     if (lane == 0) {
-      const uint32_t wring_u = smem_u32(wring);
-      const uint64_t bdesc0 = smem_desc_sw128(wring_u);
+      const uint64_t bdesc0 = smem_desc_sw128(smem_u32(wring));
       const uint32_t b_hi = (uint32_t)(bdesc0 >> 32);
-      for (int g = 0; g < n_local && !abort_flag; ++g) {
-        const int s = g % S, buf = g & 1, j = g >> 1;
-        if (g >= 2 && !wait_or_abort(&tempty[buf], (uint32_t)((j - 1) & 1), &abort_flag, err)) break;
-        if (!wait_or_abort(&bfull[s], (uint32_t)((g / S) & 1), &abort_flag, err)) break;
-        tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)buf * COUT;
-        const uint64_t adesc0 = smem_desc_kmajor(smem_u32(box + (size_t)s * C::STAGE), C::PLANE, (uint32_t)C::BX * 16u);
-        const uint32_t a_lo = (uint32_t)adesc0, a_hi = (uint32_t)(adesc0 >> 32);
-        const unsigned q0 = (unsigned)g * NCHUNK;   // ring position of the tile's first chunk
+      for (int p = 0; p < n_pairs && !abort_flag; ++p) {
+        const int buf = p & 1, jp = p >> 1;
+        if (p >= 2 && !wait_or_abort(&tempty[t][buf], (uint32_t)((jp - 1) & 1), &abort_flag, err)) break;
+        const uint32_t acc = tmem + (uint32_t)(t * 2 + buf) * COUT;
+        const unsigned q0 = (unsigned)p * NCHUNK;   // ring position of the pair's first chunk
         bool ok = true;
 #pragma unroll
-        for (int c = 0; c < NCHUNK; ++c) {
-          const unsigned q = q0 + (unsigned)c, r = q % R;
-          if (!wait_or_abort(&wfull[r], (q / R) & 1u, &abort_flag, err)) {
+        for (int k = 0; k < NKC && ok; ++k) {
+          const unsigned u = (unsigned)p * NKC + (unsigned)k, j = u % NB;
+          if (!wait_or_abort(&hfull[t][j], (u / NB) & 1u, &abort_flag, err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          constexpr uint32_t kWchUnits = C::WCH >> 4;
-          const uint32_t b_lo = (uint32_t)bdesc0 + (uint32_t)r * kWchUnits;
-          const int tap = c / NKC, kc = c - tap * NKC, ky = tap / 3, kx = tap - 3 * ky;
+          const uint64_t adesc0 = smem_desc_kmajor(smem_u32(box + (size_t)(t * NB + j) * C::HSTAGE), C::PLANE,
+                                                   (uint32_t)C::BX * 16u);
+          const uint32_t a_lo = (uint32_t)adesc0, a_hi = (uint32_t)(adesc0 >> 32);
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const uint32_t aoff = ((uint32_t)(kc * 8 + 2 * jj) * C::PLANE + (uint32_t)(ky * C::BX + kx) * 16u) >> 4;
-            const uint64_t ad = ((uint64_t)a_hi << 32) | (uint64_t)(a_lo + aoff);
-            const uint64_t bd = ((uint64_t)b_hi << 32) | (uint64_t)(b_lo + 2u * (uint32_t)jj);
-            mma_bf16(acc, ad, bd, IDESC, (c > 0 || jj > 0) ? 1u : 0u);
+          for (int tap = 0; tap < 9; ++tap) {
+            const int c = k * 9 + tap, ky = tap / 3, kx = tap - 3 * ky;
+            const unsigned q = q0 + (unsigned)c, r = q % R;
+            if (!wait_or_abort(&wfull[r], (q / R) & 1u, &abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t b_lo = (uint32_t)bdesc0 + r * (C::WCH >> 4);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const uint32_t aoff = ((uint32_t)(2 * jj) * C::PLANE + (uint32_t)(ky * C::BX + kx) * 16u) >> 4;
+              const uint64_t ad = ((uint64_t)a_hi << 32) | (uint64_t)(a_lo + aoff);
+              const uint64_t bd = ((uint64_t)b_hi << 32) | (uint64_t)(b_lo + 2u * (uint32_t)jj);
+              mma_bf16(acc, ad, bd, IDESC, (c > 0 || jj > 0) ? 1u : 0u);
+            }
+            mma_commit(&wempty[r]);
           }
-          mma_commit(&wempty[r]);
+          if (!ok) break;
+          mma_commit(&hempty[t][j]);
         }
         if (!ok) break;
-        mma_commit(&bempty[s]);
-        mma_commit(&tfull[buf]);
+        mma_commit(&tfull[t][buf]);
       }
-      mma_commit(&done);   // tracks every MMA this thread issued
-      if (!mbar_wait(&done, 0)) atomicOr(err, kErrWaitTimeout);
+      mma_commit(&done[t]);   // tracks every MMA this thread issued
+      if (!mbar_wait(&done[t], 0)) atomicOr(err, kErrWaitTimeout);
     }
     __syncwarp();
   } else {
     // -------------------------------------------------------- epilogue
-    // group e takes tiles g with g mod 2 = e, whose accumulators sit in
-    // TMEM buffer e; warp (index mod 4) reads its TMEM lane quarter
+    // group e takes pairs p with p mod 2 = e, whose accumulators sit in
+    // TMEM buffer e of both issuers; warp (index mod 4) reads its TMEM
+    // lane quarter
     const int e = (warp - C::kEpiWarp) >> 2;
     const int qd = warp & 3;
     const int m = qd * 32 + lane;          // tile row: pixel (m / 8, m % 8)
     for (int i = (warp - C::kEpiWarp) * 32 + lane; i < COUT; i += 32 * 4 * C::kEpiGroups) sbias[i] = __ldg(&a.bias[i]);
     asm volatile("bar.sync 1, %0;" ::"r"(32 * 4 * C::kEpiGroups));
-    for (int g = e; g < n_local; g += 2) {
-      const int j = g >> 1;
-      if (!wait_or_abort(&tfull[e], (uint32_t)(j & 1), &abort_flag, err)) break;
-      tc_fence_after();
-      int b, y0, x0;
-      tile_of(g, b, y0, x0);
-      const int yy = y0 + (m >> 3), xx = x0 + (m & 7);
-      const bool valid = yy < a.H && xx < a.W;
-      const size_t pix = (size_t)((size_t)b * a.H + yy) * a.W + xx;
-      __nv_bfloat16* dst = a.y ? a.y + pix * a.y_cs + a.y_co : nullptr;
-      const uint32_t acc = tmem + (uint32_t)e * COUT + ((uint32_t)(qd * 32) << 16);
-#pragma unroll
-      for (int c0 = 0; c0 < COUT; c0 += 32) {
-        uint32_t rr[32];
-        tmem_ld16_nowait(acc + (uint32_t)c0, rr);
-        tmem_ld16_nowait(acc + (uint32_t)c0 + 16u, rr + 16);
-        tmem_wait_ld();
-        if (c0 + 32 >= COUT) {
-          tc_fence_before();
-          mbar_arrive(&tempty[e]);         // the accumulator is free once it is in registers
+    bool ok = true;
+    for (int p = e; p < n_pairs && ok; p += 2) {
+      const int jp = p >> 1;
+      for (int t = 0; t < X; ++t) {
+        if (!wait_or_abort(&tfull[t][e], (uint32_t)(jp & 1), &abort_flag, err)) {
+          ok = false;
+          break;
         }
+        tc_fence_after();
+        const int g = 2 * p + t;
+        int b, y0, x0;
+        tile_of(g, b, y0, x0);
+        const int yy = y0 + (m >> 3), xx = x0 + (m & 7);
+        const bool valid = g < n_local && yy < a.H && xx < a.W;
+        const size_t pix = valid ? (size_t)((size_t)b * a.H + yy) * a.W + xx : 0;
+        __nv_bfloat16* dst = a.y ? a.y + pix * a.y_cs + a.y_co : nullptr;
+        const uint32_t acc = tmem + (uint32_t)(t * 2 + e) * COUT + ((uint32_t)(qd * 32) << 16);
 #pragma unroll
-        for (int c = 0; c < 32; c += 8) {
-          __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float t = __uint_as_float(rr[c + i]) + sbias[c0 + c + i];
-            o[i] = __float2bfloat16_rn(a.relu ? fmaxf(t, 0.f) : t);
+        for (int c0 = 0; c0 < COUT; c0 += 32) {
+          uint32_t rr[32];
+          tmem_ld16_nowait(acc + (uint32_t)c0, rr);
+          tmem_ld16_nowait(acc + (uint32_t)c0 + 16u, rr + 16);
+          tmem_wait_ld();
+          if (c0 + 32 >= COUT) {
+            tc_fence_before();
+            mbar_arrive(&tempty[t][e]);      // the accumulator is free once it is in registers
           }
-          if (valid && dst) *reinterpret_cast<uint4*>(dst + c0 + c) = *reinterpret_cast<const uint4*>(o);
+#pragma unroll
+          for (int c = 0; c < 32; c += 8) {
+            __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float v = __uint_as_float(rr[c + i]) + sbias[c0 + c + i];
+              o[i] = __float2bfloat16_rn(a.relu ? fmaxf(v, 0.f) : v);
+            }
+            if (valid && dst) *reinterpret_cast<uint4*>(dst + c0 + c) = *reinterpret_cast<const uint4*>(o);
+          }
         }
       }
     }

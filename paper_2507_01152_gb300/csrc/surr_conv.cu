@@ -730,7 +730,7 @@ bool halo_fwd(cudaError_t& e, View x, const bf16* w, const float* bias, OutView 
   return true;
 }
 
-// Stride-1 forward of a wide-input layer (CIN = 128; COUT 64 or 128)
+// Stride-1 forward of a wide-input layer (CIN 128 or 256; COUT 64 or 128)
 // through the haloed-box kernel with streamed weights.  False (e untouched)
 // if a tensor map cannot describe the operands.
 template <int CIN, int COUT>
@@ -774,10 +774,11 @@ bool halo_stream_fwd(cudaError_t& e, View x, const bf16* w, const float* bias, O
 
 bool halo_fwd_any(cudaError_t& e, View x, int Cin, int Cout, const bf16* w, const float* bias, OutView y, int relu,
                   int B, int H, int W, unsigned* err, cudaStream_t st) {
-  // 128 -> 128 (level 2 at 64 x 64, 512 frames): 1,122 TFLOP/s here against 1,053 tap by tap.  The
-  // 128 -> 64 layer stays tap by tap: with N = 64 this kernel's single MMA issuer runs it at 645
-  // against 701 TFLOP/s.
+  // 512 frames: 128 -> 128 at 64 x 64, 1,385 TFLOP/s here against 1,053 tap by tap; 128 -> 64 at
+  // 128 x 128, 1,057 against 701
   if (Cin == 128 && Cout == 128) return halo_stream_fwd<128, 128>(e, x, w, bias, y, relu, B, H, W, err, st);
+  if (Cin == 128 && Cout == 64) return halo_stream_fwd<128, 64>(e, x, w, bias, y, relu, B, H, W, err, st);
+  if (Cin == 256 && Cout == 128) return halo_stream_fwd<256, 128>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 8 && Cout == 32) return halo_fwd<8, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 32 && Cout == 32) return halo_fwd<32, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 64 && Cout == 32) return halo_fwd<64, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
