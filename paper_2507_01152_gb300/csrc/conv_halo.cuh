@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
 }
 
 // The same haloed-box forward for inputs too wide for resident weights
-// (CIN a multiple of 64; COUT = 64 or 128).  A CTA takes its tiles in pairs
+// (CIN a multiple of 64; COUT = 64, 128 or 256).  A CTA takes its tiles in pairs
 // (local tiles 2p and 2p + 1; a missing second tile of the last pair reads
 // zeros and stores nothing), and the pair's two MMA issuers share every
 // weight chunk.  The weights stream through a ring of R chunks, each the
@@ -291,11 +291,11 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
 // before.  Roles: warp 0 (one thread) copies the
 // box blocks, warp 1 (one thread) the weight chunks, warps 2 and 3 (one
 // thread each) issue the 4 MMAs of 128 x COUT x 16 of each chunk for tile
-// 2p and tile 2p + 1 into their double-buffered TMEM accumulators; two
-// groups of four epilogue warps take pairs p with p mod 2 = group (TMEM
-// buffer p mod 2 of both issuers), add the bias, apply the ReLU and store
-// BF16 pixels.  Every wait is bounded, with the abort protocol of the
-// kernel above.
+// 2p and tile 2p + 1 into their TMEM accumulators (double-buffered while
+// 2 x 2 x COUT columns fit in TMEM, else single); epilogue group t (four
+// warps) drains issuer t's accumulator of every pair, adds the bias,
+// applies the ReLU and stores BF16 pixels.  Every wait is bounded, with
+// the abort protocol of the kernel above.
 template <int CIN, int COUT>
 struct HaloStreamCfg {
   static constexpr int TY = 16, TX = 8;
@@ -309,15 +309,18 @@ struct HaloStreamCfg {
   static constexpr int NB = NKC < 2 ? NKC : 2;                     // block slots per issuer
   static constexpr int NCHUNK = 9 * NKC;                           // weight chunks per pair
   static constexpr uint32_t WCH = (uint32_t)COUT * 128;            // bytes of one chunk
-  static constexpr int R = 8;                                      // weight ring slots
-  static constexpr uint32_t WRING = R * WCH;
   static constexpr uint32_t BOXES = (uint32_t)X * NB * HSTAGE;
-  static constexpr int kEpiGroups = 2;
+  static constexpr int R0 = (int)((226u * 1024u - 1024u - 4u * COUT - BOXES) / WCH);
+  static constexpr int R = R0 > 8 ? 8 : R0;                        // weight ring slots
+  static constexpr uint32_t WRING = R * WCH;
+  static constexpr int kEpiGroups = X;                             // group t drains issuer t
   static constexpr int kEpiWarp = 2 + X;
   static constexpr int THREADS = 32 * (kEpiWarp + 4 * kEpiGroups);
-  static constexpr uint32_t NCOLS = 2u * X * COUT;                 // TMEM: two accumulators per issuer
+  static constexpr int NBUF = 2 * X * COUT <= 512 ? 2 : 1;         // accumulators per issuer
+  static constexpr uint32_t NCOLS = (uint32_t)NBUF * X * COUT;
   static constexpr uint32_t SMEM = WRING + BOXES + 4 * COUT + 1024;   // + bias, 1024-byte alignment slack
-  static_assert(CIN % 64 == 0 && (COUT == 64 || COUT == 128), "streamed halo conv shapes");
+  static_assert(CIN % 64 == 0 && (COUT == 64 || COUT == 128 || COUT == 256), "streamed halo conv shapes");
+  static_assert(R >= 4, "weight ring too shallow");
   static_assert(NCOLS <= 512, "accumulators exceed TMEM");
   static_assert(SMEM <= 226u * 1024u, "shared memory");
 };
@@ -327,14 +330,14 @@ __global__ void __launch_bounds__(HaloStreamCfg<CIN, COUT>::THREADS, 1)
     conv3x3_halo_stream_kernel(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw,
                                const HaloArgs a, unsigned* err) {
   using C = HaloStreamCfg<CIN, COUT>;
-  constexpr int R = C::R, NKC = C::NKC, NB = C::NB, HPL = C::HPL, NCHUNK = C::NCHUNK, X = C::X;
+  constexpr int R = C::R, NKC = C::NKC, NB = C::NB, HPL = C::HPL, NCHUNK = C::NCHUNK, X = C::X, NBUF = C::NBUF;
   constexpr uint32_t IDESC = idesc_bf16_f32(kBM, COUT);
   extern __shared__ __align__(1024) uint8_t smem_stream[];
   uint8_t* smem = smem_stream + ((1024u - (smem_u32(smem_stream) & 1023u)) & 1023u);
   uint8_t* wring = smem;                         // R weight chunks (1024-byte aligned swizzle atoms)
   uint8_t* box = smem + C::WRING;                // block slot j of issuer t at (t NB + j) HSTAGE
   float* sbias = reinterpret_cast<float*>(box + C::BOXES);
-  __shared__ uint64_t hfull[X][NB], hempty[X][NB], wfull[R], wempty[R], tfull[X][2], tempty[X][2], done[X];
+  __shared__ uint64_t hfull[X][NB], hempty[X][NB], wfull[R], wempty[R], tfull[X][NBUF], tempty[X][NBUF], done[X];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -349,9 +352,9 @@ __global__ void __launch_bounds__(HaloStreamCfg<CIN, COUT>::THREADS, 1)
         mbar_init(&hfull[t][j], 1);
         mbar_init(&hempty[t][j], 1);
       }
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < NBUF; ++q) {
         mbar_init(&tfull[t][q], 1);
-        mbar_init(&tempty[t][q], 128);   // the four warps of the epilogue group of buffer q
+        mbar_init(&tempty[t][q], 128);   // the four warps of epilogue group t
       }
       mbar_init(&done[t], 1);
     }
@@ -440,9 +443,9 @@ __global__ void __launch_bounds__(HaloStreamCfg<CIN, COUT>::THREADS, 1)
       const uint64_t bdesc0 = smem_desc_sw128(smem_u32(wring));
       const uint32_t b_hi = (uint32_t)(bdesc0 >> 32);
       for (int p = 0; p < n_pairs && !abort_flag; ++p) {
-        const int buf = p & 1, jp = p >> 1;
-        if (p >= 2 && !wait_or_abort(&tempty[t][buf], (uint32_t)((jp - 1) & 1), &abort_flag, err)) break;
-        const uint32_t acc = tmem + (uint32_t)(t * 2 + buf) * COUT;
+        const int buf = p % NBUF, jp = p / NBUF;   // accumulator, and its use index
+        if (p >= NBUF && !wait_or_abort(&tempty[t][buf], (uint32_t)((jp - 1) & 1), &abort_flag, err)) break;
+        const uint32_t acc = tmem + (uint32_t)(t * NBUF + buf) * COUT;
         const unsigned q0 = (unsigned)p * NCHUNK;   // ring position of the pair's first chunk
         bool ok = true;
 #pragma unroll
@@ -487,51 +490,49 @@ __global__ void __launch_bounds__(HaloStreamCfg<CIN, COUT>::THREADS, 1)
     __syncwarp();
   } else {
     // -------------------------------------------------------- epilogue
-    // group e takes pairs p with p mod 2 = e, whose accumulators sit in
-    // TMEM buffer e of both issuers; warp (index mod 4) reads its TMEM
-    // lane quarter
+    // group e drains issuer e's accumulator of every pair (tile 2p + e),
+    // so it sees each accumulator's phases in order; warp (index mod 4)
+    // reads its TMEM lane quarter
     const int e = (warp - C::kEpiWarp) >> 2;
     const int qd = warp & 3;
     const int m = qd * 32 + lane;          // tile row: pixel (m / 8, m % 8)
     for (int i = (warp - C::kEpiWarp) * 32 + lane; i < COUT; i += 32 * 4 * C::kEpiGroups) sbias[i] = __ldg(&a.bias[i]);
     asm volatile("bar.sync 1, %0;" ::"r"(32 * 4 * C::kEpiGroups));
     bool ok = true;
-    for (int p = e; p < n_pairs && ok; p += 2) {
-      const int jp = p >> 1;
-      for (int t = 0; t < X; ++t) {
-        if (!wait_or_abort(&tfull[t][e], (uint32_t)(jp & 1), &abort_flag, err)) {
-          ok = false;
-          break;
+    for (int p = 0; p < n_pairs && ok; ++p) {
+      const int buf = p % NBUF, jp = p / NBUF;
+      if (!wait_or_abort(&tfull[e][buf], (uint32_t)(jp & 1), &abort_flag, err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const int g = 2 * p + e;
+      int b, y0, x0;
+      tile_of(g, b, y0, x0);
+      const int yy = y0 + (m >> 3), xx = x0 + (m & 7);
+      const bool valid = g < n_local && yy < a.H && xx < a.W;
+      const size_t pix = valid ? (size_t)((size_t)b * a.H + yy) * a.W + xx : 0;
+      __nv_bfloat16* dst = a.y ? a.y + pix * a.y_cs + a.y_co : nullptr;
+      const uint32_t acc = tmem + (uint32_t)(e * NBUF + buf) * COUT + ((uint32_t)(qd * 32) << 16);
+#pragma unroll
+      for (int c0 = 0; c0 < COUT; c0 += 32) {
+        uint32_t rr[32];
+        tmem_ld16_nowait(acc + (uint32_t)c0, rr);
+        tmem_ld16_nowait(acc + (uint32_t)c0 + 16u, rr + 16);
+        tmem_wait_ld();
+        if (c0 + 32 >= COUT) {
+          tc_fence_before();
+          mbar_arrive(&tempty[e][buf]);    // the accumulator is free once it is in registers
         }
-        tc_fence_after();
-        const int g = 2 * p + t;
-        int b, y0, x0;
-        tile_of(g, b, y0, x0);
-        const int yy = y0 + (m >> 3), xx = x0 + (m & 7);
-        const bool valid = g < n_local && yy < a.H && xx < a.W;
-        const size_t pix = valid ? (size_t)((size_t)b * a.H + yy) * a.W + xx : 0;
-        __nv_bfloat16* dst = a.y ? a.y + pix * a.y_cs + a.y_co : nullptr;
-        const uint32_t acc = tmem + (uint32_t)(t * 2 + e) * COUT + ((uint32_t)(qd * 32) << 16);
 #pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 32) {
-          uint32_t rr[32];
-          tmem_ld16_nowait(acc + (uint32_t)c0, rr);
-          tmem_ld16_nowait(acc + (uint32_t)c0 + 16u, rr + 16);
-          tmem_wait_ld();
-          if (c0 + 32 >= COUT) {
-            tc_fence_before();
-            mbar_arrive(&tempty[t][e]);      // the accumulator is free once it is in registers
+        for (int c = 0; c < 32; c += 8) {
+          __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float v = __uint_as_float(rr[c + i]) + sbias[c0 + c + i];
+            o[i] = __float2bfloat16_rn(a.relu ? fmaxf(v, 0.f) : v);
           }
-#pragma unroll
-          for (int c = 0; c < 32; c += 8) {
-            __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const float v = __uint_as_float(rr[c + i]) + sbias[c0 + c + i];
-              o[i] = __float2bfloat16_rn(a.relu ? fmaxf(v, 0.f) : v);
-            }
-            if (valid && dst) *reinterpret_cast<uint4*>(dst + c0 + c) = *reinterpret_cast<const uint4*>(o);
-          }
+          if (valid && dst) *reinterpret_cast<uint4*>(dst + c0 + c) = *reinterpret_cast<const uint4*>(o);
         }
       }
     }

@@ -730,7 +730,7 @@ bool halo_fwd(cudaError_t& e, View x, const bf16* w, const float* bias, OutView 
   return true;
 }
 
-// Stride-1 forward of a wide-input layer (CIN 128 or 256; COUT 64 or 128)
+// Stride-1 forward of a wide-input layer (CIN 128 or 256; COUT 64, 128 or 256)
 // through the haloed-box kernel with streamed weights.  False (e untouched)
 // if a tensor map cannot describe the operands.
 template <int CIN, int COUT>
@@ -779,6 +779,7 @@ bool halo_fwd_any(cudaError_t& e, View x, int Cin, int Cout, const bf16* w, cons
   if (Cin == 128 && Cout == 128) return halo_stream_fwd<128, 128>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 128 && Cout == 64) return halo_stream_fwd<128, 64>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 256 && Cout == 128) return halo_stream_fwd<256, 128>(e, x, w, bias, y, relu, B, H, W, err, st);
+  if (Cin == 256 && Cout == 256) return halo_stream_fwd<256, 256>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 8 && Cout == 32) return halo_fwd<8, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 32 && Cout == 32) return halo_fwd<32, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
   if (Cin == 64 && Cout == 32) return halo_fwd<64, 32>(e, x, w, bias, y, relu, B, H, W, err, st);
