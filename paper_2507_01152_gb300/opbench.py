@@ -128,7 +128,39 @@ def surrogate_forward(B: int, reps: int = 5, c: int = 32, H: int = 256):
     return ms, B / ms * 1e3, 2 * macs * B / ms / 1e9
 
 
+def surrogate_train(B: int, reps: int = 3, c: int = 32, H: int = 256):
+    """one training step of the surrogate (forward, L1 + 1 - SSIM, full
+    backward, Adam) on B random BF16 slices and targets: ms per step"""
+    import torch
+    from . import build, scene
+    from .ussim import Surrogate
+    build.build()
+    off, size, fan = Surrogate.segments(c, H, H)
+    net = Surrogate(c, H, H, B, scene.surrogate_init(size, fan, 0))
+    g = torch.Generator(device="cuda").manual_seed(2)
+    x = torch.rand((B, H, H, 8), device="cuda", generator=g).to(torch.bfloat16)
+    y = torch.rand((B, H, H), device="cuda", generator=g)
+    loss = torch.zeros(1 + 2 * B, device="cuda")
+    for _ in range(2):
+        net.train_step(x, y, loss, update=True)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        net.train_step(x, y, loss, update=True)
+    e.record()
+    e.synchronize()
+    net.check()
+    net.close()
+    return a.elapsed_time(e) / reps
+
+
 def main(argv):
+    if argv[0] == "train":
+        B = int(argv[1])
+        reps = int(argv[2]) if len(argv) > 2 else 3
+        print(f"surrogate train step B={B} c=32 256x256: {surrogate_train(B, reps):.3f} ms", flush=True)
+        return
     if argv[0] == "surrogate":
         B = int(argv[1])
         reps = int(argv[2]) if len(argv) > 2 else 5
