@@ -348,6 +348,10 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
   {
     // two 32-sample units a warp per step, both loads issued first
     const int nl_left = g0 - L0, nh = nl_left + (L1 - g1), cpl = (NS + 31) >> 5, nu = nh * cpl;
+    // t / nh as floor((t + 1/2) / nh) in FP32: (t + 1/2) / nh lies at least
+    // 1 / (2 nh) from an integer and below cpl <= 32, far beyond the
+    // product's rounding error, so the quotient is exact
+    const float inv_nh = 1.f / (float)max(nh, 1);
     for (int t0 = warp; t0 < nu; t0 += 2 * NW) {
       int at[2];
       uint8_t lv[2];
@@ -357,7 +361,7 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
         at[j] = -1;
         lv[j] = 0;
         if (t < nu) {
-          const int c = t / nh, h = t - c * nh;
+          const int c = __float2int_rz(((float)t + 0.5f) * inv_nh), h = t - c * nh;
           const int l = h < nl_left ? L0 + h : g1 + (h - nl_left);
           const int lim = cx.pair.ext[l < g0 ? g0 - l : l - g1 + 1];
           const int s = (c << 5) + lane;
