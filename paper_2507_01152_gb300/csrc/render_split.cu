@@ -284,11 +284,17 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
   // the halo lines' labels in 32-sample chunks spread over the warps: a line
   // d lines beyond the group is labelled only below ext[d], the stencil's
   // reach, so the short halo lines do not load a few warps
+  // the label passes read the pose, volume and probe fields from register
+  // copies: through the shared context they were reloaded for every sample
+  // (2% of pass A)
+  const Pose Mr = cx.M;
+  const DevVolume Vr = cx.V;
+  const DevProbe Pr = cx.P;
   auto label_of = [&](float2 ln, int s, float3& u, int& vi) -> uint8_t {
     float x, z;
-    beam_point(P, ln, s, x, z);
-    u = to_voxel(cx.M, cx.V.inv_h, x, z);
-    return nearest_label(cx.V, u, vi);
+    beam_point(Pr, ln, s, x, z);
+    u = to_voxel(Mr, Vr.inv_h, x, z);
+    return nearest_label(Vr, u, vi);
   };
   // Own lines take kLabU samples a lane per step (s, s + 32, ...): every
   // sample's label and corner-record loads are issued before any is used.
@@ -309,7 +315,7 @@ __device__ __forceinline__ void lines_body(const RenderParams& p, const SplitArg
       if (cells) {
         HuCell c[kLabU];
 #pragma unroll
-        for (int j = 0; j < kLabU; ++j) c[j] = hu_cell_fetch(cx.V, u[j]);
+        for (int j = 0; j < kLabU; ++j) c[j] = hu_cell_fetch(Vr, u[j]);
 #pragma unroll
         for (int j = 0; j < kLabU; ++j) zv[j] = fmaxf(hu_cell_value(c[j]) + 1024.f, 1.f);
       } else {
