@@ -276,26 +276,25 @@ __global__ void __launch_bounds__(HaloCfg<CIN, COUT>::THREADS, 1)
 }
 
 // The same haloed-box forward for inputs too wide for resident weights
-// (CIN a multiple of 64; COUT = 64, 128 or 256).  A CTA takes its tiles in pairs
-// (local tiles 2p and 2p + 1; a missing second tile of the last pair reads
-// zeros and stores nothing), and the pair's two MMA issuers share every
-// weight chunk.  The weights stream through a ring of R chunks, each the
-// COUT x 64 block of one tap and one 64-channel block of the input, copied
-// by a 2-D tensor copy with the 128-byte swizzle (no repacking: a chunk is
-// a box of the [COUT][3][3][CIN] array) and read through swizzled K-major
-// descriptors; a slot is free again once both issuers' MMAs on it are
-// done.  Each tile's box is staged in its 64-channel blocks through two
+// (CIN a multiple of 64; COUT = 64, 128 or 256).  A CTA takes its tiles in
+// pairs (local tiles 2p and 2p + 1; a missing second tile of the last pair
+// reads zeros and stores nothing), and the pair's two MMA issuers share
+// every weight chunk.  The weights stream through a ring of R chunks, each
+// the COUT x 64 block of one tap and one 64-channel block of the input,
+// copied by a 2-D tensor copy with the 128-byte swizzle (no repacking: a
+// chunk is a box of the [COUT][3][3][CIN] array) and read through swizzled
+// K-major descriptors; a slot is free again once both issuers' MMAs on it
+// are done.  Each tile's box is staged in its 64-channel blocks through two
 // block slots per issuer (block k of pair p is use u = p NKC + k, in slot
 // u mod 2), and the chunks run block-major (the 9 taps of block 0, then of
-// block 1, ...), so a block loads while the issuer works on the one
-// before.  Roles: warp 0 (one thread) copies the
-// box blocks, warp 1 (one thread) the weight chunks, warps 2 and 3 (one
-// thread each) issue the 4 MMAs of 128 x COUT x 16 of each chunk for tile
-// 2p and tile 2p + 1 into their TMEM accumulators (double-buffered while
-// 2 x 2 x COUT columns fit in TMEM, else single); epilogue group t (four
-// warps) drains issuer t's accumulator of every pair, adds the bias,
-// applies the ReLU and stores BF16 pixels.  Every wait is bounded, with
-// the abort protocol of the kernel above.
+// block 1, ...), so a block loads while the issuer works on the one before.
+// Roles: warp 0 (one thread) copies the box blocks, warp 1 (one thread) the
+// weight chunks, warps 2 and 3 (one thread each) issue the 4 MMAs of
+// 128 x COUT x 16 of each chunk for tile 2p and tile 2p + 1 into their TMEM
+// accumulators (double-buffered while 2 x 2 x COUT columns fit in TMEM,
+// else single); epilogue group t (four warps) drains issuer t's accumulator
+// of every pair, adds the bias, applies the ReLU and stores BF16 pixels.
+// Every wait is bounded, with the abort protocol of the kernel above.
 template <int CIN, int COUT>
 struct HaloStreamCfg {
   static constexpr int TY = 16, TX = 8;
