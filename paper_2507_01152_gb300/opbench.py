@@ -3,6 +3,7 @@
     python -m paper_2507_01152_gb300.opbench fwd|dgrad|wgrad B H Cin Cout [stride] [reps]
     python -m paper_2507_01152_gb300.opbench hist B H [reps]
     python -m paper_2507_01152_gb300.opbench surrogate B [reps]
+    python -m paper_2507_01152_gb300.opbench train B [reps]
 
 fwd / dgrad / wgrad: one 3x3 convolution pass of the tcgen05 implicit GEMM
 on B images of H x H pixels (input grid), NHWC BF16 activations with random
@@ -12,6 +13,9 @@ TFLOP/s (2 x 9 x Cin x Cout multiply-adds per output pixel).
 surrogate: the whole surrogate forward (base 32 channels, 256 x 256
 frames) on B random input slices; prints the time per call, frames/s and
 TFLOP/s (2 x 10.74 G multiply-adds per frame).
+
+train: one surrogate training step (forward, L1 + 1 - SSIM, full backward,
+Adam) on B random slices and targets; prints the time per step.
 
 hist: CT histogram matching (us_sim_hist_match) of B images of H x H FP32
 values (normal, 300 HU spread, every pixel considered) to a reference of
